@@ -1,0 +1,107 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds random draws only: no part of the partition-function
+arithmetic lives here, so that the oracle and the CUDA library stay
+independent of each other while reading identical inputs.
+
+Every artefact uses its own ``numpy.random.default_rng(seed)`` and draws in the
+order written below.  The paper's workloads are real proteins and a trained
+tensor model (Section "Example proteins and free energy models"), neither of
+which exists here; these generators stand in for them with the shapes the
+nearest-neighbour model uses.
+
+Parameter vector layout (float64, ``NPARAMS`` entries), energies in kcal/mol:
+
+====================  =====  ==============================================
+slice                 size   meaning
+====================  =====  ==============================================
+``[0:36]``            6x6    stack[outer pair type][inner pair type]
+``[36:67]``           31     hairpin length term H[L], L = 0..30
+``[67:98]``           31     bulge length term Bu[L]
+``[98:129]``          31     interior length term In[L]
+``[129:145]``         4x4    terminal mismatch tm[x][y]
+``[145:161]``         4x4    5' dangle d5[paired base][dangling base]
+``[161:177]``         4x4    3' dangle d3[paired base][dangling base]
+``[177:180]``         3      multiloop a (closing), b (per unpaired), c (per branch)
+``[180]``             1      temperature in degrees Celsius
+====================  =====  ==============================================
+
+Bases are indexed A, C, G, U = 0..3 and pair types AU, CG, GC, UA, GU, UG = 0..5.
+Amino acids are indexed in the order ``ARNDCQEGHILKMFPSTWYV``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AMINO_ACIDS = "ARNDCQEGHILKMFPSTWYV"
+NPARAMS = 181
+MAXLOOP = 30
+N_SENSE = 61
+
+
+def nn_params(seed: int = 0) -> np.ndarray:
+    """Synthetic nearest-neighbour parameter vector (layout in the module docstring)."""
+    rng = np.random.default_rng(seed)
+    stack = rng.uniform(-3.5, -0.5, (6, 6))
+    hairpin = rng.uniform(1.0, 6.0, MAXLOOP + 1)
+    bulge = rng.uniform(1.0, 6.0, MAXLOOP + 1)
+    interior = rng.uniform(1.0, 6.0, MAXLOOP + 1)
+    tm = rng.uniform(-1.5, 0.0, (4, 4))
+    d5 = rng.uniform(-1.5, 0.0, (4, 4))
+    d3 = rng.uniform(-1.5, 0.0, (4, 4))
+    out = np.concatenate([
+        stack.ravel(), hairpin, bulge, interior, tm.ravel(), d5.ravel(), d3.ravel(),
+        np.array([3.4, 0.0, 0.4, 37.0]),
+    ])
+    assert out.size == NPARAMS
+    return out
+
+
+def residues_uniform(m: int, seed: int) -> np.ndarray:
+    """Residues drawn uniformly over the 20 amino acids (int32 indices)."""
+    return np.random.default_rng(seed).integers(0, 20, m).astype(np.int32)
+
+
+def residues_dirichlet(m: int, seed: int) -> np.ndarray:
+    """Composition ~ Dirichlet(1), then residues i.i.d. from it (same generator)."""
+    rng = np.random.default_rng(seed)
+    freqs = rng.dirichlet(np.ones(20))
+    return rng.choice(20, m, p=freqs).astype(np.int32)
+
+
+def to_string(res: np.ndarray) -> str:
+    return "".join(AMINO_ACIDS[int(r)] for r in res)
+
+
+def soft_weights(m: int, seed: int, sigma_codon: float = 0.5, sigma_pair: float = 0.2,
+                 pair: bool = True):
+    """Per-(residue, codon slot) log-weights ~ N(0, sigma_codon), all 6 slots drawn
+    (slots beyond an amino acid's codon count are ignored), then the 61x61
+    codon-pair log-bonus ~ N(0, sigma_pair) from the same generator."""
+    rng = np.random.default_rng(seed)
+    lw = rng.normal(0.0, sigma_codon, (m, 6))
+    pb = rng.normal(0.0, sigma_pair, (N_SENSE, N_SENSE)) if pair else np.zeros((N_SENSE, N_SENSE))
+    return lw, pb
+
+
+def workload(name: str):
+    """The named synthetic workloads (residues, lw, pb); lw/pb None means all-zero."""
+    if name == "p8_uniform":          # 8 aa, uniform residues, seed 0
+        return residues_uniform(8, 0), None, None
+    if name == "p300_dirichlet":      # 300 aa, Dirichlet(1) composition, seed 1
+        return residues_dirichlet(300, 1), None, None
+    if name == "p300_weighted":       # the 300-aa protein with soft weights, seed 2
+        lw, pb = soft_weights(300, 2)
+        return residues_dirichlet(300, 1), lw, pb
+    if name == "p1000_weighted":      # 1000 aa, Dirichlet(1) seed 4, codon weights only
+        rng = np.random.default_rng(4)
+        freqs = rng.dirichlet(np.ones(20))
+        res = rng.choice(20, 1000, p=freqs).astype(np.int32)
+        lw = rng.normal(0.0, 0.5, (1000, 6))
+        return res, lw, None
+    raise KeyError(name)
+
+
+def ascent_targets(m: int, seed: int = 3) -> np.ndarray:
+    """Independent N(0,1) logits per (residue, slot) for frequency targets."""
+    return np.random.default_rng(seed).normal(0.0, 1.0, (m, 6))

@@ -1,0 +1,154 @@
+/*
+ * codonfold.h -- C ABI of the B300 codon-constrained partition-function library.
+ *
+ * The library computes, for a protein psi, the partition function summed over
+ * every codon sequence that encodes psi and every pseudoknot-free secondary
+ * structure of that sequence, under a nearest-neighbour energy model with
+ * soft per-codon and per-codon-pair weights; then pair probabilities, codon
+ * marginals and exact samples.  Citations are to arXiv 2604.19718
+ * (Fornace, Wang & Lindsey).
+ *
+ * Conventions for every entry point:
+ *   - every call returns a cf_status; no C++ exception crosses the ABI;
+ *   - output buffers are owned and allocated by the caller; a pointer may be
+ *     host memory or device memory of the problem's device (the library asks
+ *     the CUDA runtime which it is and copies accordingly);
+ *   - one cf_problem is bound to one device and one CUDA stream; calls on one
+ *     problem must not overlap (not thread-safe per problem), distinct
+ *     problems are independent;
+ *   - on failure, cf_last_error() gives a one-line message for that problem.
+ *
+ * Amino acids are the 20 standard ones, letters "ARNDCQEGHILKMFPSTWYV".
+ * Codon states of a residue are its sense codons in lexicographic order over
+ * A,C,G,U ("slot" 0..5).  Sense codon ids 0..60 number the 61 sense codons
+ * in the same lexicographic order (stop codons removed).
+ */
+#ifndef CODONFOLD_H
+#define CODONFOLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cf_model cf_model;
+typedef struct cf_problem cf_problem;
+
+typedef enum {
+  CF_OK = 0,
+  CF_EINVAL = 1,   /* invalid argument (bad letter, size, non-finite weight, NULL) */
+  CF_ENOMEM = 2,   /* host or device allocation failed */
+  CF_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+  CF_ETIMEOUT = 4, /* a device-side bounded wait gave up; the context stays usable */
+  CF_ESTATE = 5,   /* call out of order (e.g. outside before inside) */
+  CF_ENUMERIC = 6  /* non-finite or zero partition function after scaling */
+} cf_status;
+
+typedef enum {
+  CF_FP64 = 0,        /* tables in binary64 with per-diagonal power-of-two exponents */
+  CF_FP32_SCALED = 1  /* tables in binary32 with per-diagonal power-of-two exponents;
+                         log Z and all normalisations in binary64 */
+} cf_precision;
+
+#define CF_NPARAMS 181
+
+/*
+ * Load the nearest-neighbour energy model (paper Section "Secondary structure
+ * free energy models"; the synthetic parameter layout below).
+ *   params:  CF_NPARAMS doubles, energies in kcal/mol:
+ *            [0,36) stack[6][6] by pair types AU,CG,GC,UA,GU,UG (outer, inner);
+ *            [36,67) hairpin H[L]; [67,98) bulge Bu[L]; [98,129) interior In[L],
+ *            L = 0..30; [129,145) terminal mismatch tm[4][4];
+ *            [145,161) 5' dangle d5[paired][dangling]; [161,177) 3' dangle d3;
+ *            [177] multiloop a, [178] b (per unpaired), [179] c (per branch);
+ *            [180] temperature in Celsius.  Bases A,C,G,U = 0..3.
+ *   The library copies the values; the caller keeps ownership of params.
+ * Errors: CF_EINVAL if params or out is NULL, nparams != CF_NPARAMS or a value
+ * is non-finite; CF_ENOMEM.
+ */
+cf_status cf_load_model(const double *params, size_t nparams, cf_model **out);
+cf_status cf_model_free(cf_model *model);
+
+/*
+ * Create a problem on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t, NULL = the legacy default stream).  The problem keeps a
+ * pointer to `model`, which must outlive it.
+ * Errors: CF_EINVAL, CF_ECUDA (device cannot be selected), CF_ENOMEM.
+ */
+cf_status cf_problem_create(const cf_model *model, int device, void *stream, cf_problem **out);
+cf_status cf_problem_free(cf_problem *prob);
+
+/*
+ * Set the protein and its soft constraints (paper Section "Formulating codon
+ * constraints using tensor trains", Eq. pair-tt, and Section "Incorporating
+ * soft constraints"): the codon-pair tensor train along the backbone.
+ *   aa:         m letters (not NUL-terminated needed), host memory.
+ *   codon_logw: m*6 doubles, host memory or NULL (= 0).  Row r, slot s is the
+ *               log-weight of the residue's s-th codon; slots >= the number of
+ *               codons of that amino acid are ignored.  Enters as e^{+w}.
+ *   pair_bonus: 61*61 doubles by sense codon id, host or NULL (= 0); the
+ *               log-bonus of codon c at residue r followed by c' at r+1.
+ * Allocates the device tables for n = 3m (released by cf_problem_free or the
+ * next cf_set_protein).  Invalidates earlier inside/outside results.
+ * Errors: CF_EINVAL (m < 1, letter not in the alphabet, non-finite weight),
+ * CF_ENOMEM (tables do not fit), CF_ECUDA.
+ */
+cf_status cf_set_protein(cf_problem *prob, const char *aa, int m, const double *codon_logw,
+                         const double *pair_bonus);
+
+/*
+ * Inside pass (paper Section "Free energy computation", Eq. amino-q): fills
+ * the dynamic-programming tables over all intervals by anti-diagonal
+ * wavefront on the device and returns log Z (natural log, Z summed over
+ * codon sequences and structures, soft weights included) in *logZ (host).
+ * Errors: CF_ESTATE (no protein), CF_ENUMERIC, CF_ECUDA, CF_ETIMEOUT.
+ */
+cf_status cf_inside(cf_problem *prob, cf_precision precision, double *logZ);
+
+/*
+ * Outside pass: the hand-written adjoint of the inside pass, in the precision
+ * of the last cf_inside.  Any output may be NULL.
+ *   pair_prob:  n*n floats, row-major; [i][j] = P(i pairs with j) (Eq.
+ *               pair-probability), [i][i] = P(i unpaired).
+ *   codon_marg: m*6 doubles; [r][s] = P(residue r uses its codon slot s)
+ *               = d log Z / d codon_logw[r][s] (Eq. marginal-codon).
+ *   pair_grad:  61*61 doubles; d log Z / d pair_bonus[c][c'] = expected count
+ *               of the adjacent codon pair (c, c') summed over residues.
+ * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ECUDA.
+ */
+cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, double *pair_grad);
+
+/*
+ * Draw `nsamples` exact i.i.d. samples of (codon sequence, structure) from
+ * the Boltzmann distribution by stochastic traceback of the inside tables
+ * (paper Section "Sequence sampling").  Sample k depends only on (seed, k):
+ * the same seed gives bit-identical output for any launch shape.
+ *   codons:  nsamples*m int32, sense codon id per residue.
+ *   partner: nsamples*n int32, pairing partner per position or -1.
+ * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ENOMEM, CF_ECUDA.
+ */
+cf_status cf_sample(cf_problem *prob, int nsamples, uint64_t seed, int32_t *codons,
+                    int32_t *partner);
+
+/* One-line description of the last failure on `prob` (or of the last global
+ * failure when prob is NULL).  Valid until the next call on that problem. */
+const char *cf_last_error(const cf_problem *prob);
+
+/*
+ * Device time of the last inside and outside pass in milliseconds, measured
+ * with CUDA events on the problem's stream around the kernel sequence, and
+ * the number of kernel launches each issued.  Any pointer may be NULL.
+ */
+cf_status cf_last_timing(const cf_problem *prob, float *inside_ms, float *outside_ms,
+                         int *inside_launches, int *outside_launches);
+
+/* Length n = 3m of the current protein, or 0. */
+int cf_problem_length(const cf_problem *prob);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CODONFOLD_H */

@@ -1,0 +1,184 @@
+"""Python binding of the codon-constrained partition-function library (C ABI in
+``include/codonfold.h``).
+
+Only argument marshalling lives here: every step of the dynamic program runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.  If the
+compiled library is missing the import fails loudly; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from .build import LIB
+
+AMINO_ACIDS = "ARNDCQEGHILKMFPSTWYV"
+CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ETIMEOUT, CF_ESTATE, CF_ENUMERIC = range(7)
+CF_FP64, CF_FP32_SCALED = 0, 1
+CF_NPARAMS = 181
+_STATUS = {1: "CF_EINVAL", 2: "CF_ENOMEM", 3: "CF_ECUDA", 4: "CF_ETIMEOUT", 5: "CF_ESTATE", 6: "CF_ENUMERIC"}
+
+
+class CFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load() -> ctypes.CDLL:
+    if not Path(LIB).exists():
+        raise ImportError(f"CUDA library not built: {LIB} (run paper_2604_19718_b300.build.build())")
+    lib = ctypes.CDLL(str(LIB))
+    vp, dp, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p
+    lib.cf_load_model.argtypes = [dp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.cf_model_free.argtypes = [vp]
+    lib.cf_problem_create.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.cf_problem_free.argtypes = [vp]
+    lib.cf_set_protein.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp, dp]
+    lib.cf_inside.argtypes = [vp, ctypes.c_int, dp]
+    lib.cf_outside.argtypes = [vp, fp, vp, vp]
+    lib.cf_sample.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
+    lib.cf_last_error.argtypes = [vp]
+    lib.cf_last_error.restype = ctypes.c_char_p
+    lib.cf_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.cf_problem_length.argtypes = [vp]
+    for name in ("cf_load_model", "cf_model_free", "cf_problem_create", "cf_problem_free", "cf_set_protein",
+                 "cf_inside", "cf_outside", "cf_sample", "cf_last_timing"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, handle=None):
+    if status != CF_OK:
+        msg = lib.cf_last_error(handle)
+        raise CFError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def cf_load_model(params) -> ctypes.c_void_p:
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(lib.cf_load_model(p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p.size, ctypes.byref(h)))
+    return h
+
+
+def cf_model_free(model) -> None:
+    lib.cf_model_free(model)
+
+
+def cf_problem_create(model, device: int = 0, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib.cf_problem_create(model, int(device), ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def cf_problem_free(prob) -> None:
+    lib.cf_problem_free(prob)
+
+
+def cf_set_protein(prob, aa: str, codon_logw=None, pair_bonus=None) -> None:
+    m = len(aa)
+    lw = None if codon_logw is None else np.ascontiguousarray(np.asarray(codon_logw, dtype=np.float64).reshape(m, 6))
+    pb = None if pair_bonus is None else np.ascontiguousarray(np.asarray(pair_bonus, dtype=np.float64).reshape(61, 61))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.cf_set_protein(prob, aa.encode(), m, None if lw is None else lw.ctypes.data_as(dp),
+                              None if pb is None else pb.ctypes.data_as(dp)), prob)
+
+
+def cf_inside(prob, precision: int = CF_FP32_SCALED) -> float:
+    out = ctypes.c_double()
+    _check(lib.cf_inside(prob, int(precision), ctypes.byref(out)), prob)
+    return out.value
+
+
+def cf_outside(prob, pair_prob=None, codon_marg=None, pair_grad=None) -> None:
+    _check(lib.cf_outside(prob, _ptr(pair_prob), _ptr(codon_marg), _ptr(pair_grad)), prob)
+
+
+def cf_sample(prob, nsamples: int, seed: int, codons, partner) -> None:
+    _check(lib.cf_sample(prob, int(nsamples), ctypes.c_uint64(seed), _ptr(codons), _ptr(partner)), prob)
+
+
+def cf_last_timing(prob):
+    a, b = ctypes.c_float(), ctypes.c_float()
+    c, d = ctypes.c_int(), ctypes.c_int()
+    _check(lib.cf_last_timing(prob, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), prob)
+    return a.value, b.value, c.value, d.value
+
+
+def cf_problem_length(prob) -> int:
+    return int(lib.cf_problem_length(prob))
+
+
+# ---------------------------------------------------------------- convenience
+
+def to_letters(residues) -> str:
+    return "".join(AMINO_ACIDS[int(r)] for r in residues)
+
+
+class CodonFold:
+    """One protein on one device/stream; owns a model and a problem handle."""
+
+    def __init__(self, params, device: int = 0, stream: int = 0):
+        self.model = cf_load_model(params)
+        self.prob = cf_problem_create(self.model, device, stream)
+        self.n = 0
+        self.m = 0
+
+    def set_protein(self, residues_or_letters, codon_logw=None, pair_bonus=None):
+        aa = residues_or_letters if isinstance(residues_or_letters, str) else to_letters(residues_or_letters)
+        cf_set_protein(self.prob, aa, codon_logw, pair_bonus)
+        self.m = len(aa)
+        self.n = 3 * self.m
+        return self
+
+    def inside(self, precision: int = CF_FP32_SCALED) -> float:
+        return cf_inside(self.prob, precision)
+
+    def outside(self, pair_prob=True, codon=True, pair_grad=True):
+        """Host numpy outputs (pass arrays/tensors to fill them in place instead)."""
+        P = np.zeros((self.n, self.n), dtype=np.float32) if pair_prob is True else pair_prob
+        cm = np.zeros((self.m, 6)) if codon is True else codon
+        pg = np.zeros((61, 61)) if pair_grad is True else pair_grad
+        cf_outside(self.prob, None if P is False else P, None if cm is False else cm,
+                   None if pg is False else pg)
+        return P, cm, pg
+
+    def sample(self, nsamples: int, seed: int):
+        cod = np.zeros((nsamples, self.m), dtype=np.int32)
+        par = np.zeros((nsamples, self.n), dtype=np.int32)
+        cf_sample(self.prob, nsamples, seed, cod, par)
+        return cod, par
+
+    def timing(self):
+        return cf_last_timing(self.prob)
+
+    def close(self):
+        if self.prob:
+            cf_problem_free(self.prob)
+            self.prob = None
+        if self.model:
+            cf_model_free(self.model)
+            self.model = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,171 @@
+// cf_common.cuh -- device data layout and warp-level helpers shared by the
+// inside, outside and sampling kernels of the codon-constrained partition
+// function (arXiv 2604.19718, Section "Dynamic programs over sequences and
+// structures": every interval entry is a small rectangular block over the
+// codon states at its two ends).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cf {
+
+constexpr int NS = 6;        // maximum codon states of one residue
+constexpr int BLK = NS * NS; // padded 6x6 block per table entry
+constexpr int MAXLOOP = 30;  // maximum bulge / interior loop size
+constexpr int NYY = 29;      // interior-loop partial sums, total loop size L = 2..30
+constexpr int WPB = 4;       // warps (cells) per block in the wavefront kernels
+constexpr int YRING = 2;     // diagonals of interior-loop adjoints kept in flight
+
+// typed transition variants, index (type at p) * 2 + (type at p+1), U = 0, P = 1
+constexpr int XUU = 0, XUP = 1, XPU = 2, XPP = 3;
+
+// energy-factor vector offsets (Boltzmann factors e^{-E/RT})
+constexpr int EN_STK = 0;    // [6][6] stack by (outer, inner) pair type
+constexpr int EN_BU = 36;    // [31] bulge by loop size
+constexpr int EN_IN = 67;    // [31] interior by loop size
+constexpr int EN_TM = 98;    // [4][4] terminal mismatch
+constexpr int EN_D5 = 114;   // [4][4] 5' dangle [paired][dangling]
+constexpr int EN_D3 = 130;   // [4][4] 3' dangle [paired][dangling]
+constexpr int EN_EA = 146;   // multiloop closing
+constexpr int EN_EB = 147;   // multiloop unpaired base
+constexpr int EN_EC = 148;   // multiloop branch
+constexpr int EN_N = 149;
+
+// Triangular, diagonal-major cell index: all cells of one anti-diagonal are
+// contiguous, so each wavefront step writes one contiguous range.
+__host__ __device__ __forceinline__ size_t cidx(int n, int x, int y) {
+  size_t d = (size_t)(y - x);
+  return d * (size_t)n - d * (d - 1) / 2 + (size_t)x;
+}
+__host__ __device__ __forceinline__ size_t ncells(int n) { return (size_t)n * (n + 1) / 2; }
+
+// pair type of bases (x 5', y 3'): AU, CG, GC, UA, GU, UG -> 0..5, else -1
+__host__ __device__ __forceinline__ int pair_type(int x, int y) {
+  int k = x * 4 + y;
+  // A=0 C=1 G=2 U=3
+  switch (k) {
+    case 0 * 4 + 3: return 0;
+    case 1 * 4 + 2: return 1;
+    case 2 * 4 + 1: return 2;
+    case 3 * 4 + 0: return 3;
+    case 2 * 4 + 3: return 4;
+    case 3 * 4 + 2: return 5;
+    default: return -1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T p2(int e) {
+  return (T)ldexp(1.0, e);
+}
+template <>
+__device__ __forceinline__ float p2<float>(int e) {
+  return ldexpf(1.0f, e);
+}
+
+// Everything a wavefront kernel needs; device pointers.
+template <typename T>
+struct DP {
+  int n, m;
+  const int *Mp;    // [n] states per position
+  const int *base;  // [n*6] base of state a at p
+  const int *bnd;   // [n] 1 if T_p crosses a residue boundary
+  const T *Tr;      // [n*36] transfer p -> p+1 (scaled)
+  const T *X;       // [n*4*36] typed transitions
+  const T *en;      // [EN_N] energy factors
+  const T *eHL;     // [n+2] hairpin length factor e^{-H(L)/RT}
+  const double *u0; // [6] weights of residue 0
+  int *E;           // [n] per-diagonal exponents
+  unsigned long long *dmax; // [n] bits of the largest mantissa per diagonal
+  int *err;         // device error word
+  // inside tables [ncell*36]
+  T *CH, *QB, *XI, *HB, *QMpp, *QMpu, *G, *QM2pp, *QM2pu, *QM2up, *QM2uu;
+  T *YY;            // [ncell*29*36]
+  T *Q5U, *Q5P, *Gx; // [n*36]
+  double *Zm;       // scalar: Z relative to 2^{E[n-1]} and the transfer scaling
+  // adjoint tables
+  T *hCH, *hQB, *hGc, *hXI, *hHB, *hQMpp, *hQMpu, *hG, *hQM2pp, *hQM2pu, *hQM2up, *hQM2uu;
+  T *hYY;           // ring [YRING][n][29*36]
+  T *hQ5U, *hQ5P, *hGx; // [n*36]
+  double *hT;       // [n*36]   d log Z / d T_p (boundary positions)
+  double *hX;       // [n*4*36] d log Z / d X_p (boundary positions)
+  float *P;         // [n*n] pair probabilities (device)
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Reduce a per-lane accumulator block over the warp (entries a<Ma, b<Mb);
+// afterwards every lane holds the totals.
+template <typename T>
+__device__ __forceinline__ void warp_reduce_block(T (&acc)[BLK], int Ma, int Mb) {
+#pragma unroll
+  for (int e = 0; e < BLK; e++)
+    if ((e / NS) < Ma && (e % NS) < Mb) acc[e] = warp_sum(acc[e]);
+}
+
+template <typename T>
+__device__ __forceinline__ void zero_block(T (&acc)[BLK]) {
+#pragma unroll
+  for (int e = 0; e < BLK; e++) acc[e] = (T)0;
+}
+
+// acc += f * op(A) op(B); TA/TB select transposed reads of the padded blocks.
+// A is Ma x Ms (after op), B is Ms x Mb (after op).
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ void acc_mm(T (&acc)[BLK], const T *A, const T *B, int Ma, int Ms, int Mb,
+                                       T f) {
+#pragma unroll
+  for (int a = 0; a < NS; a++) {
+    if (a < Ma) {
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        if (s < Ms) {
+          T av = (TA ? A[s * NS + a] : A[a * NS + s]) * f;
+#pragma unroll
+          for (int b = 0; b < NS; b++)
+            if (b < Mb) acc[a * NS + b] += av * (TB ? B[b * NS + s] : B[s * NS + b]);
+        }
+      }
+    }
+  }
+}
+
+// One entry (a,b) of op(A) op(B) op(C) with inner sizes Mu, Mv.
+template <bool TA, bool TB, bool TC, typename T>
+__device__ __forceinline__ T e3(const T *A, const T *B, const T *C, int a, int b, int Mu, int Mv) {
+  T s = 0;
+  for (int u = 0; u < Mu; u++) {
+    T av = TA ? A[u * NS + a] : A[a * NS + u];
+    if (av == (T)0) continue;
+    T t = 0;
+    for (int v = 0; v < Mv; v++)
+      t += (TB ? B[v * NS + u] : B[u * NS + v]) * (TC ? C[b * NS + v] : C[v * NS + b]);
+    s += av * t;
+  }
+  return s;
+}
+
+// One entry (a,b) of op(A) op(B).
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ T e2(const T *A, const T *B, int a, int b, int Mu) {
+  T s = 0;
+  for (int u = 0; u < Mu; u++) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
+  return s;
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+  if (v > 0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace cf

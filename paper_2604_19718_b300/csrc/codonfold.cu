@@ -1,0 +1,599 @@
+// codonfold.cu -- C ABI (include/codonfold.h) and host orchestration of the
+// codon-constrained partition-function kernels for sm_103a.
+//
+// Host work is limited to building the per-position tensor-train data of the
+// protein (Eq. pair-tt with soft weights), choosing launch shapes, moving
+// inputs/outputs and turning device reductions into the returned numbers.
+// Every step of the dynamic program runs in the kernels of cf_inside.cuh,
+// cf_outside.cuh and cf_sample.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/codonfold.h"
+#include "cf_common.cuh"
+#include "cf_inside.cuh"
+#include "cf_outside.cuh"
+#include "cf_sample.cuh"
+
+using namespace cf;
+
+namespace {
+
+const char kAminoAcids[] = "ARNDCQEGHILKMFPSTWYV";
+// Codons of each amino acid (standard genetic code), written per amino acid.
+const char *kCodonsOf[20] = {
+    "GCU GCC GCA GCG",          // A
+    "CGU CGC CGA CGG AGA AGG",  // R
+    "AAU AAC",                  // N
+    "GAU GAC",                  // D
+    "UGU UGC",                  // C
+    "CAA CAG",                  // Q
+    "GAA GAG",                  // E
+    "GGU GGC GGA GGG",          // G
+    "CAU CAC",                  // H
+    "AUU AUC AUA",              // I
+    "UUA UUG CUU CUC CUA CUG",  // L
+    "AAA AAG",                  // K
+    "AUG",                      // M
+    "UUU UUC",                  // F
+    "CCU CCC CCA CCG",          // P
+    "UCU UCC UCA UCG AGU AGC",  // S
+    "ACU ACC ACA ACG",          // T
+    "UGG",                      // W
+    "UAU UAC",                  // Y
+    "GUU GUC GUA GUG",          // V
+};
+
+int base_index(char c) {
+  switch (c) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    case 'U': return 3;
+  }
+  return -1;
+}
+
+struct GeneticCode {
+  std::vector<int> codons[20];  // 6-bit codon numbers (A,C,G,U = 0..3), ascending
+  int sense_id[64];
+  GeneticCode() {
+    std::vector<int> all;
+    for (int a = 0; a < 20; a++) {
+      const char *s = kCodonsOf[a];
+      const size_t len = std::strlen(s);
+      for (size_t k = 0; k + 2 < len; k += 4) {
+        int c = 16 * base_index(s[k]) + 4 * base_index(s[k + 1]) + base_index(s[k + 2]);
+        codons[a].push_back(c);
+        all.push_back(c);
+      }
+      std::sort(codons[a].begin(), codons[a].end());
+    }
+    std::sort(all.begin(), all.end());
+    for (int i = 0; i < 64; i++) sense_id[i] = -1;
+    for (size_t i = 0; i < all.size(); i++) sense_id[all[i]] = (int)i;
+  }
+};
+
+const GeneticCode &gcode() {
+  static GeneticCode g;
+  return g;
+}
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+struct cf_model {
+  double params[CF_NPARAMS];
+  double kT;
+  double en[EN_N];
+};
+
+template <typename T>
+struct PrecTables {
+  bool inside_alloc = false, outside_alloc = false;
+  DP<T> dp{};
+  std::vector<void *> allocs;
+};
+
+struct cf_problem {
+  const cf_model *model = nullptr;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int n = 0, m = 0;
+  std::vector<int> M, base, bnd, cid;
+  std::vector<double> Tr, X, u0, eHL;
+  double log_scale = 0;  // sum_p log s_p of the transfer scaling
+  // device, shared by both precisions
+  int *dM = nullptr, *dbase = nullptr, *dbnd = nullptr, *dE = nullptr, *derr = nullptr;
+  unsigned long long *ddmax = nullptr;
+  double *du0 = nullptr, *dZm = nullptr, *dtrans = nullptr, *dp0 = nullptr;
+  float *dP = nullptr;
+  std::vector<void *> shared_allocs;
+  PrecTables<float> f32;
+  PrecTables<double> f64;
+  int last_prec = -1;
+  bool have_inside = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float t_in = 0, t_out = 0;
+  int l_in = 0, l_out = 0;
+};
+
+namespace {
+
+cf_status fail(cf_problem *p, cf_status s, const std::string &msg) {
+  if (p) p->err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+cf_status cuda_fail(cf_problem *p, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(p, e == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA, m);
+}
+
+#define CF_CUDA(p, call)                                  \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
+  } while (0)
+
+template <typename V>
+cudaError_t dalloc(std::vector<void *> &list, V **ptr, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(V));
+  if (e != cudaSuccess) return e;
+  list.push_back(q);
+  *ptr = (V *)q;
+  return cudaSuccess;
+}
+
+void free_list(std::vector<void *> &list) {
+  for (void *q : list) cudaFree(q);
+  list.clear();
+}
+
+template <typename T>
+void free_prec(PrecTables<T> &t) {
+  free_list(t.allocs);
+  t.inside_alloc = t.outside_alloc = false;
+  t.dp = DP<T>{};
+}
+
+bool is_device_ptr(const void *ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
+  if (t.inside_alloc) return CF_OK;
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  DP<T> &d = t.dp;
+  d.n = n;
+  d.m = p->m;
+  d.Mp = p->dM;
+  d.base = p->dbase;
+  d.bnd = p->dbnd;
+  d.u0 = p->du0;
+  d.E = p->dE;
+  d.dmax = p->ddmax;
+  d.err = p->derr;
+  d.Zm = p->dZm;
+  d.P = p->dP;
+  T *tr, *x, *en, *eh;
+  auto &L = t.allocs;
+  CF_CUDA(p, dalloc(L, &tr, (size_t)n * BLK));
+  CF_CUDA(p, dalloc(L, &x, (size_t)n * 4 * BLK));
+  CF_CUDA(p, dalloc(L, &en, (size_t)EN_N));
+  CF_CUDA(p, dalloc(L, &eh, (size_t)n + 2));
+  std::vector<T> h;
+  h.assign(p->Tr.begin(), p->Tr.end());
+  CF_CUDA(p, cudaMemcpy(tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  h.assign(p->X.begin(), p->X.end());
+  CF_CUDA(p, cudaMemcpy(x, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  h.assign(p->model->en, p->model->en + EN_N);
+  CF_CUDA(p, cudaMemcpy(en, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  h.assign(p->eHL.begin(), p->eHL.end());
+  CF_CUDA(p, cudaMemcpy(eh, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  d.Tr = tr;
+  d.X = x;
+  d.en = en;
+  d.eHL = eh;
+  T **tabs[] = {&d.CH, &d.QB, &d.XI, &d.HB, &d.QMpp, &d.QMpu, &d.G, &d.QM2pp, &d.QM2pu, &d.QM2up, &d.QM2uu};
+  for (T **q : tabs) {
+    CF_CUDA(p, dalloc(L, q, nc));
+    CF_CUDA(p, cudaMemset(*q, 0, nc * sizeof(T)));
+  }
+  CF_CUDA(p, dalloc(L, &d.YY, nc * NYY));
+  CF_CUDA(p, cudaMemset(d.YY, 0, nc * NYY * sizeof(T)));
+  T **ext[] = {&d.Q5U, &d.Q5P, &d.Gx};
+  for (T **q : ext) {
+    CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
+    CF_CUDA(p, cudaMemset(*q, 0, (size_t)n * BLK * sizeof(T)));
+  }
+  t.inside_alloc = true;
+  return CF_OK;
+}
+
+template <typename T>
+cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
+  if (t.outside_alloc) return CF_OK;
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  DP<T> &d = t.dp;
+  auto &L = t.allocs;
+  T **tabs[] = {&d.hCH, &d.hQB, &d.hGc, &d.hXI, &d.hHB, &d.hQMpp, &d.hQMpu, &d.hG, &d.hQM2pp, &d.hQM2pu, &d.hQM2up, &d.hQM2uu};
+  for (T **q : tabs) {
+    CF_CUDA(p, dalloc(L, q, nc));
+    CF_CUDA(p, cudaMemset(*q, 0, nc * sizeof(T)));
+  }
+  CF_CUDA(p, dalloc(L, &d.hYY, (size_t)YRING * n * NYY * BLK));
+  CF_CUDA(p, cudaMemset(d.hYY, 0, (size_t)YRING * n * NYY * BLK * sizeof(T)));
+  T **ext[] = {&d.hQ5U, &d.hQ5P, &d.hGx};
+  for (T **q : ext) {
+    CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
+    CF_CUDA(p, cudaMemset(*q, 0, (size_t)n * BLK * sizeof(T)));
+  }
+  CF_CUDA(p, dalloc(L, &d.hT, (size_t)n * BLK));
+  CF_CUDA(p, dalloc(L, &d.hX, (size_t)n * 4 * BLK));
+  t.outside_alloc = true;
+  return CF_OK;
+}
+
+template <typename T>
+cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
+  cf_status s = alloc_inside(p, t);
+  if (s != CF_OK) return s;
+  const int n = p->n;
+  cudaStream_t st = p->stream;
+  CF_CUDA(p, cudaMemsetAsync(p->ddmax, 0, sizeof(unsigned long long) * n, st));
+  CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  int launches = 0;
+  for (int d = 0; d < n; d++) {
+    int cells = n - d;
+    int blocks = (cells + WPB - 1) / WPB;
+    k_inside<T><<<blocks, 32 * WPB, 0, st>>>(t.dp, d);
+    launches++;
+  }
+  k_inside_finish<T><<<1, 32, 0, st>>>(t.dp);
+  launches++;
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaEventRecord(p->ev[1], st));
+  double zm = 0;
+  int e_last = 0, err = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&zm, p->dZm, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(&e_last, p->dE + (n - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&p->t_in, p->ev[0], p->ev[1]));
+  p->l_in = launches;
+  if (err || !(zm > 0) || !std::isfinite(zm))
+    return fail(p, CF_ENUMERIC, "inside: non-finite or zero partition function after scaling");
+  *logZ = std::log(zm) + e_last * std::log(2.0) - p->log_scale;
+  return CF_OK;
+}
+
+template <typename T>
+cf_status run_outside(cf_problem *p, PrecTables<T> &t) {
+  cf_status s = alloc_outside(p, t);
+  if (s != CF_OK) return s;
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  DP<T> &d = t.dp;
+  cudaStream_t st = p->stream;
+  CF_CUDA(p, cudaMemsetAsync(d.hCH, 0, nc * sizeof(T), st));
+  CF_CUDA(p, cudaMemsetAsync(d.hXI, 0, nc * sizeof(T), st));
+  CF_CUDA(p, cudaMemsetAsync(d.hT, 0, (size_t)n * BLK * sizeof(double), st));
+  CF_CUDA(p, cudaMemsetAsync(d.hX, 0, (size_t)n * 4 * BLK * sizeof(double), st));
+  CF_CUDA(p, cudaMemsetAsync(d.P, 0, (size_t)n * n * sizeof(float), st));
+  CF_CUDA(p, cudaEventRecord(p->ev[2], st));
+  int launches = 0;
+  for (int dd = n - 1; dd >= 0; dd--) {
+    int cells = n - dd;
+    int blocks = (cells + WPB - 1) / WPB;
+    k_outside<T><<<blocks, 32 * WPB, 0, st>>>(d, dd);
+    launches++;
+  }
+  k_marginals<T><<<(std::max(p->m - 1, 1) + 127) / 128, 128, 0, st>>>(d, p->dtrans, p->dp0);
+  k_unpaired<<<(n + 7) / 8, 256, 0, st>>>(d.P, n);
+  launches += 2;
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaEventRecord(p->ev[3], st));
+  p->l_out = launches;
+  return CF_OK;
+}
+
+cf_status copy_out(cf_problem *p, void *dst, const void *src, size_t bytes, bool src_on_device) {
+  cudaMemcpyKind k;
+  bool ddev = is_device_ptr(dst);
+  if (src_on_device) k = ddev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  else k = ddev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  CF_CUDA(p, cudaMemcpyAsync(dst, src, bytes, k, p->stream));
+  return CF_OK;
+}
+
+template <typename T>
+cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int32_t *codons, int32_t *partner) {
+  (void)t; (void)ns; (void)seed; (void)codons; (void)partner;
+  return fail(p, CF_ESTATE, "cf_sample: not built yet");
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+cf_status cf_load_model(const double *params, size_t nparams, cf_model **out) {
+  if (!params || !out) return fail(nullptr, CF_EINVAL, "cf_load_model: NULL argument");
+  if (nparams != CF_NPARAMS) return fail(nullptr, CF_EINVAL, "cf_load_model: expected 181 parameters");
+  for (size_t k = 0; k < nparams; k++)
+    if (!std::isfinite(params[k])) return fail(nullptr, CF_EINVAL, "cf_load_model: non-finite parameter");
+  cf_model *m = new (std::nothrow) cf_model;
+  if (!m) return fail(nullptr, CF_ENOMEM, "cf_load_model: out of host memory");
+  std::memcpy(m->params, params, sizeof(m->params));
+  m->kT = 1.98717e-3 * (params[180] + 273.15);
+  auto bz = [&](double e) { return std::exp(-e / m->kT); };
+  for (int k = 0; k < 36; k++) m->en[EN_STK + k] = bz(params[k]);
+  for (int L = 0; L <= MAXLOOP; L++) {
+    m->en[EN_BU + L] = bz(params[67 + L]);
+    m->en[EN_IN + L] = bz(params[98 + L]);
+  }
+  for (int k = 0; k < 16; k++) {
+    m->en[EN_TM + k] = bz(params[129 + k]);
+    m->en[EN_D5 + k] = bz(params[145 + k]);
+    m->en[EN_D3 + k] = bz(params[161 + k]);
+  }
+  m->en[EN_EA] = bz(params[177]);
+  m->en[EN_EB] = bz(params[178]);
+  m->en[EN_EC] = bz(params[179]);
+  *out = m;
+  return CF_OK;
+}
+
+cf_status cf_model_free(cf_model *model) {
+  delete model;
+  return CF_OK;
+}
+
+cf_status cf_problem_create(const cf_model *model, int device, void *stream, cf_problem **out) {
+  if (!model || !out) return fail(nullptr, CF_EINVAL, "cf_problem_create: NULL argument");
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+  cf_problem *p = new (std::nothrow) cf_problem;
+  if (!p) return fail(nullptr, CF_ENOMEM, "cf_problem_create: out of host memory");
+  p->model = model;
+  p->device = device;
+  p->stream = (cudaStream_t)stream;
+  for (auto &ev : p->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(nullptr, e, "cudaEventCreate");
+    }
+  }
+  *out = p;
+  return CF_OK;
+}
+
+static void release_protein(cf_problem *p) {
+  free_prec(p->f32);
+  free_prec(p->f64);
+  free_list(p->shared_allocs);
+  p->dM = p->dbase = p->dbnd = p->dE = p->derr = nullptr;
+  p->ddmax = nullptr;
+  p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
+  p->dP = nullptr;
+  p->have_inside = false;
+  p->n = p->m = 0;
+}
+
+cf_status cf_problem_free(cf_problem *p) {
+  if (!p) return CF_OK;
+  cudaSetDevice(p->device);
+  release_protein(p);
+  for (auto &ev : p->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete p;
+  return CF_OK;
+}
+
+cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw, const double *pb) {
+  if (!p || !aa) return fail(p, CF_EINVAL, "cf_set_protein: NULL argument");
+  if (m < 1) return fail(p, CF_EINVAL, "cf_set_protein: m must be >= 1");
+  const GeneticCode &gc = gcode();
+  std::vector<int> res(m);
+  for (int r = 0; r < m; r++) {
+    const char *q = std::strchr(kAminoAcids, aa[r]);
+    if (!aa[r] || !q) return fail(p, CF_EINVAL, std::string("cf_set_protein: invalid amino acid at residue ") + std::to_string(r));
+    res[r] = (int)(q - kAminoAcids);
+  }
+  if (lw)
+    for (size_t k = 0; k < (size_t)m * 6; k++)
+      if (!std::isfinite(lw[k])) return fail(p, CF_EINVAL, "cf_set_protein: non-finite codon weight");
+  if (pb)
+    for (size_t k = 0; k < 61 * 61; k++)
+      if (!std::isfinite(pb[k])) return fail(p, CF_EINVAL, "cf_set_protein: non-finite pair bonus");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  release_protein(p);
+  const int n = 3 * m;
+  p->n = n;
+  p->m = m;
+  p->M.assign(n, 0);
+  p->base.assign((size_t)n * NS, 0);
+  p->cid.assign((size_t)n * NS, -1);
+  p->bnd.assign(n, 0);
+  for (int r = 0; r < m; r++) {
+    const auto &cods = gc.codons[res[r]];
+    for (int off = 0; off < 3; off++) {
+      int q = 3 * r + off;
+      p->M[q] = (int)cods.size();
+      for (size_t a = 0; a < cods.size(); a++) {
+        p->base[(size_t)q * NS + a] = (cods[a] >> (2 * (2 - off))) & 3;
+        p->cid[(size_t)q * NS + a] = gc.sense_id[cods[a]];
+      }
+    }
+  }
+  const double *en = p->model->en;
+  p->Tr.assign((size_t)n * BLK, 0.0);
+  p->X.assign((size_t)n * 4 * BLK, 0.0);
+  p->log_scale = 0;
+  for (int q = 0; q + 1 < n; q++) {
+    int Ma = p->M[q], Mb = p->M[q + 1];
+    double *T = &p->Tr[(size_t)q * BLK];
+    if (q % 3 != 2) {
+      for (int a = 0; a < Ma; a++) T[a * NS + a] = 1.0;
+    } else {
+      p->bnd[q] = 1;
+      int r1 = (q + 1) / 3;
+      double sum = 0;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) {
+          double w = lw ? lw[(size_t)r1 * 6 + b] : 0.0;
+          if (pb) w += pb[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]];
+          T[a * NS + b] = std::exp(w);
+          sum += T[a * NS + b];
+        }
+      // normalise the average row sum to one (exact rescale, undone in log Z)
+      double s = Ma / sum;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) T[a * NS + b] *= s;
+      p->log_scale += std::log(s);
+    }
+    for (int a = 0; a < Ma; a++)
+      for (int b = 0; b < Mb; b++) {
+        int x0 = p->base[(size_t)q * NS + a], y0 = p->base[(size_t)(q + 1) * NS + b];
+        double t = T[a * NS + b], d3 = en[EN_D3 + x0 * 4 + y0], d5 = en[EN_D5 + y0 * 4 + x0];
+        double *X = &p->X[(size_t)q * 4 * BLK];
+        X[XUU * BLK + a * NS + b] = t;
+        X[XUP * BLK + a * NS + b] = t * d5;
+        X[XPU * BLK + a * NS + b] = t * d3;
+        X[XPP * BLK + a * NS + b] = t * d3 * d5;
+      }
+  }
+  p->u0.assign(NS, 0.0);
+  for (int a = 0; a < p->M[0]; a++) p->u0[a] = std::exp(lw ? lw[a] : 0.0);
+  p->eHL.assign((size_t)n + 2, 0.0);
+  const double kT = p->model->kT, H30 = p->model->params[36 + MAXLOOP];
+  for (int L = 0; L < n + 2; L++) {
+    double e = (L <= MAXLOOP) ? p->model->params[36 + L] : H30 + 1.07856 * std::log((double)L / MAXLOOP);
+    p->eHL[L] = std::exp(-e / kT);
+  }
+  auto &S = p->shared_allocs;
+  CF_CUDA(p, dalloc(S, &p->dM, (size_t)n));
+  CF_CUDA(p, dalloc(S, &p->dbase, (size_t)n * NS));
+  CF_CUDA(p, dalloc(S, &p->dbnd, (size_t)n));
+  CF_CUDA(p, dalloc(S, &p->dE, (size_t)n));
+  CF_CUDA(p, dalloc(S, &p->derr, (size_t)1));
+  CF_CUDA(p, dalloc(S, &p->ddmax, (size_t)n));
+  CF_CUDA(p, dalloc(S, &p->du0, (size_t)NS));
+  CF_CUDA(p, dalloc(S, &p->dZm, (size_t)1));
+  CF_CUDA(p, dalloc(S, &p->dtrans, (size_t)std::max(m - 1, 1) * BLK));
+  CF_CUDA(p, dalloc(S, &p->dp0, (size_t)NS));
+  CF_CUDA(p, dalloc(S, &p->dP, (size_t)n * n));
+  CF_CUDA(p, cudaMemcpy(p->dM, p->M.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpy(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpy(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpy(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemset(p->dE, 0, sizeof(int) * n));
+  return CF_OK;
+}
+
+cf_status cf_inside(cf_problem *p, cf_precision prec, double *logZ) {
+  if (!p || !logZ) return fail(p, CF_EINVAL, "cf_inside: NULL argument");
+  if (p->n == 0) return fail(p, CF_ESTATE, "cf_inside: no protein set");
+  if (prec != CF_FP64 && prec != CF_FP32_SCALED) return fail(p, CF_EINVAL, "cf_inside: unknown precision");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  p->have_inside = false;
+  cf_status s = (prec == CF_FP64) ? run_inside(p, p->f64, logZ) : run_inside(p, p->f32, logZ);
+  if (s != CF_OK) return s;
+  p->last_prec = (int)prec;
+  p->have_inside = true;
+  return CF_OK;
+}
+
+cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double *pair_grad) {
+  if (!p) return fail(p, CF_EINVAL, "cf_outside: NULL problem");
+  if (!p->have_inside) return fail(p, CF_ESTATE, "cf_outside: run cf_inside first");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  cf_status s = (p->last_prec == CF_FP64) ? run_outside(p, p->f64) : run_outside(p, p->f32);
+  if (s != CF_OK) return s;
+  const int n = p->n, m = p->m;
+  cudaStream_t st = p->stream;
+  if (pair_prob) {
+    s = copy_out(p, pair_prob, p->dP, sizeof(float) * (size_t)n * n, true);
+    if (s != CF_OK) return s;
+  }
+  std::vector<double> trans((size_t)std::max(m - 1, 1) * BLK), p0(NS);
+  CF_CUDA(p, cudaMemcpyAsync(trans.data(), p->dtrans, sizeof(double) * trans.size(), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(p0.data(), p->dp0, sizeof(double) * NS, cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&p->t_out, p->ev[2], p->ev[3]));
+  std::vector<double> cm((size_t)m * 6, 0.0), pg(61 * 61, 0.0);
+  for (int a = 0; a < p->M[0]; a++) cm[a] = p0[a];
+  for (int r = 0; r + 1 < m; r++) {
+    int q = 3 * r + 2;
+    for (int a = 0; a < p->M[q]; a++)
+      for (int b = 0; b < p->M[q + 1]; b++) {
+        double v = trans[(size_t)r * BLK + a * NS + b];
+        cm[(size_t)(r + 1) * 6 + b] += v;
+        pg[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]] += v;
+      }
+  }
+  if (codon_marg) {
+    s = copy_out(p, codon_marg, cm.data(), sizeof(double) * cm.size(), false);
+    if (s != CF_OK) return s;
+  }
+  if (pair_grad) {
+    s = copy_out(p, pair_grad, pg.data(), sizeof(double) * pg.size(), false);
+    if (s != CF_OK) return s;
+  }
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  return CF_OK;
+}
+
+cf_status cf_last_timing(const cf_problem *p, float *inside_ms, float *outside_ms, int *inside_launches,
+                         int *outside_launches) {
+  if (!p) return CF_EINVAL;
+  if (inside_ms) *inside_ms = p->t_in;
+  if (outside_ms) *outside_ms = p->t_out;
+  if (inside_launches) *inside_launches = p->l_in;
+  if (outside_launches) *outside_launches = p->l_out;
+  return CF_OK;
+}
+
+int cf_problem_length(const cf_problem *p) { return p ? p->n : 0; }
+
+const char *cf_last_error(const cf_problem *p) {
+  if (p) return p->err.c_str();
+  return g_last_error.c_str();
+}
+
+cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons, int32_t *partner) {
+  if (!p) return fail(p, CF_EINVAL, "cf_sample: NULL problem");
+  if (nsamples < 0 || (nsamples > 0 && (!codons || !partner))) return fail(p, CF_EINVAL, "cf_sample: bad arguments");
+  if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample: run cf_inside first");
+  if (nsamples == 0) return CF_OK;
+  CF_CUDA(p, cudaSetDevice(p->device));
+  return (p->last_prec == CF_FP64) ? run_sample(p, p->f64, nsamples, seed, codons, partner)
+                                   : run_sample(p, p->f32, nsamples, seed, codons, partner);
+}
+
+}  // extern "C"

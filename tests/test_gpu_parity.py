@@ -1,0 +1,144 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Element-by-element comparison on the same seeded inputs: log Z, the full pair
+probability matrix, codon marginals and codon-pair gradients, in both the
+binary64 form and the binary32 form with per-diagonal power-of-two scaling.
+Tolerances: binary64 1e-9 (relative for log Z, absolute for marginals) and
+2e-7 for pair probabilities, which the ABI returns as binary32; binary32 1e-6
+relative for log Z and 1e-5 absolute for probabilities (the accuracy bar of
+the workload).
+Full-size workloads are compared against values the oracle wrote with
+tests/golden/make_golden.py.
+"""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+P0 = synth.nn_params(0)
+GOLD = Path(__file__).resolve().parent / "golden"
+TOL = {0: (1e-9, 1e-9, 2e-7), 1: (1e-6, 1e-5, 1e-5)}  # precision -> (logZ rel, marginal abs, P abs)
+
+
+def _cf():
+    import paper_2604_19718_b300 as cf
+    return cf
+
+
+def _gpu(res, lw, pb, prec):
+    cf = _cf()
+    f = cf.CodonFold(P0)
+    f.set_protein(res, lw, pb)
+    lz = f.inside(prec)
+    P, cm, pg = f.outside()
+    f.close()
+    return lz, P, cm, pg
+
+
+def _check(o, g, prec, res):
+    lz, P, cm, pg = g
+    tl, tp, tP = TOL[prec]
+    assert abs(lz - o["logZ"]) <= tl * max(1.0, abs(o["logZ"])), (lz, o["logZ"])
+    assert np.abs(P - o["P"]).max() <= tP
+    assert np.abs(cm - o["codon"]).max() <= tp
+    assert np.abs(pg - o["pair_grad"]).max() <= tp * max(1, len(res) // 10)
+
+
+CASES = {
+    "one_residue": ([12], False),
+    "two": ([10, 15], False),
+    "three": ([0, 1, 2], False),
+    "four_weighted": ([5, 7, 2, 14], True),
+    "p8_uniform": (list(synth.workload("p8_uniform")[0]), False),
+    "p21_weighted": (list(np.random.default_rng(21).integers(0, 20, 21)), True),
+    "p47_weighted": (list(np.random.default_rng(47).integers(0, 20, 47)), True),
+}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", list(CASES))
+def test_vs_oracle(name, prec):
+    res, wts = CASES[name]
+    m = len(res)
+    rng = np.random.default_rng(m)
+    lw = rng.normal(0, 0.5, (m, 6)) if wts else None
+    pb = rng.normal(0, 0.2, (61, 61)) if wts else None
+    o = oracle.outside(P0, res, lw, pb)
+    _check(o, _gpu(res, lw, pb, prec), prec, res)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["p300_dirichlet", "p300_weighted", "p1000_weighted_prefix150"])
+def test_full_size_golden(name, prec):
+    path = GOLD / f"{name}.npz"
+    if not path.exists():
+        pytest.skip(f"golden {name} not generated")
+    g = np.load(path)
+    if name.startswith("p1000"):
+        res, lw, _ = synth.workload("p1000_weighted")
+        res, lw, pb = res[:150], lw[:150], None
+    else:
+        res, lw, pb = synth.workload(name)
+    lz, P, cm, pg = _gpu(res, lw, pb, prec)
+    tl, tp, tP = TOL[prec]
+    assert abs(lz - float(g["logZ"])) <= tl * abs(float(g["logZ"]))
+    assert np.abs(cm - g["codon"]).max() <= tp
+    assert np.abs(P[g["rows"]] - g["P_rows"]).max() <= tP
+    assert np.abs(np.diag(P) - g["unpaired"]).max() <= tP
+    assert np.abs(pg - g["pair_grad"]).max() <= 10 * tp
+
+
+def test_invariants_fp32_full():
+    res, lw, pb = synth.workload("p300_weighted")
+    lz, P, cm, pg = _gpu(res, lw, pb, 1)
+    assert np.abs(P - P.T).max() == 0
+    assert P.min() >= -1e-5 and P.max() <= 1 + 1e-5
+    assert np.abs(P.sum(1) - 1).max() <= 1e-4
+    assert np.abs(cm.sum(1) - 1).max() <= 1e-5
+    assert abs(pg.sum() - (len(res) - 1)) <= 1e-3
+
+
+def test_errors():
+    cf = _cf()
+    f = cf.CodonFold(P0)
+    with pytest.raises(cf.CFError) as e:
+        f.inside()
+    assert e.value.status == cf.CF_ESTATE
+    with pytest.raises(cf.CFError) as e:
+        f.set_protein("MAXW")
+    assert e.value.status == cf.CF_EINVAL
+    with pytest.raises(cf.CFError) as e:
+        f.set_protein("MAW", np.full((3, 6), np.nan))
+    assert e.value.status == cf.CF_EINVAL
+    f.set_protein("MAW")
+    with pytest.raises(cf.CFError) as e:
+        f.outside()
+    assert e.value.status == cf.CF_ESTATE
+    f.close()
+
+
+def test_repeatable_and_device_outputs():
+    import torch
+    cf = _cf()
+    res, lw, pb = synth.workload("p300_weighted")
+    res, lw = res[:40], lw[:40]
+    f = cf.CodonFold(P0)
+    f.set_protein(res, lw, pb)
+    a = f.inside(1)
+    b = f.inside(1)
+    assert a == b
+    n = f.n
+    Pd = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    cmd = torch.zeros((len(res), 6), dtype=torch.float64, device="cuda")
+    cf.cf_outside(f.prob, Pd, cmd, None)
+    torch.cuda.synchronize()
+    P, cm, _ = f.outside()
+    assert np.array_equal(Pd.cpu().numpy(), P) or np.abs(Pd.cpu().numpy() - P).max() < 1e-6
+    assert np.abs(cmd.cpu().numpy() - cm).max() < 1e-9
+    f.close()

@@ -1622,3 +1622,31 @@ int or_codons_of(int aa, int *out) {
     if (OR_CODE64[k] == OR_AA[aa]) out[cnt++] = sense_id(k);
   return cnt;
 }
+
+/* Diagnostic: log of the largest entry of each QB[i][j] block (-inf if the
+ * block is zero), n x n, row-major; used to study magnitude spreads. */
+int or_qb_logmax(const double *params, const int *res, int m, const double *lw, const double *pb,
+                 double *out) {
+  if (m < 1) return OR_EINVAL;
+  octx c;
+  int rc = setup(&c, params, res, m, lw, pb, NULL, 0);
+  if (rc) {
+    free_ctx(&c);
+    return rc == -1 ? OR_EINVAL : OR_ENOMEM;
+  }
+  inside(&c);
+  int n = c.n;
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      R mx = 0;
+      if (j >= i) {
+        const R(*Q)[NS] = c.QB[tri(&c, i, j)];
+        for (int a = 0; a < c.M[i]; a++)
+          for (int b = 0; b < c.M[j]; b++)
+            if (Q[a][b] > mx) mx = Q[a][b];
+      }
+      out[(size_t)i * n + j] = mx > 0 ? (double)logl(mx) : -INFINITY;
+    }
+  free_ctx(&c);
+  return OR_OK;
+}

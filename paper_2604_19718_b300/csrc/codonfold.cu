@@ -126,6 +126,11 @@ struct cf_problem {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float t_in = 0, t_out = 0;
   int l_in = 0, l_out = 0;
+  // sampler scratch, grown on demand
+  std::vector<void *> smp_allocs;
+  size_t smp_cap = 0;
+  int2 *smp_stack = nullptr;
+  int *smp_state = nullptr, *smp_cid = nullptr, *smp_err = nullptr;
 };
 
 namespace {
@@ -331,8 +336,46 @@ cf_status copy_out(cf_problem *p, void *dst, const void *src, size_t bytes, bool
 
 template <typename T>
 cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int32_t *codons, int32_t *partner) {
-  (void)t; (void)ns; (void)seed; (void)codons; (void)partner;
-  return fail(p, CF_ESTATE, "cf_sample: not built yet");
+  const int n = p->n, m = p->m;
+  cudaStream_t st = p->stream;
+  const int warps = std::min(ns, 148 * 16);
+  const size_t need_stack = (size_t)warps * (n + 64), need_state = (size_t)warps * n;
+  if (p->smp_cap < (size_t)warps) {
+    free_list(p->smp_allocs);
+    CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_stack, need_stack));
+    CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_state, need_state));
+    CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_cid, (size_t)n * NS));
+    CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_err, (size_t)1));
+    CF_CUDA(p, cudaMemcpy(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice));
+    p->smp_cap = warps;
+  }
+  const bool dc = is_device_ptr(codons), dpn = is_device_ptr(partner);
+  int32_t *ocod = codons, *opar = partner;
+  std::vector<void *> tmp;
+  if (!dc) CF_CUDA(p, dalloc(tmp, &ocod, (size_t)ns * m));
+  if (!dpn) CF_CUDA(p, dalloc(tmp, &opar, (size_t)ns * n));
+  CF_CUDA(p, cudaMemsetAsync(p->smp_err, 0, sizeof(int), st));
+  SampleArgs<T> a;
+  a.p = t.dp;
+  a.cid = p->smp_cid;
+  a.nsamples = ns;
+  a.seed = seed;
+  a.stack = p->smp_stack;
+  a.state = p->smp_state;
+  a.codons = ocod;
+  a.partner = opar;
+  a.err = p->smp_err;
+  k_sample<T><<<(warps + 3) / 4, 128, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, p->smp_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !dc) e = cudaMemcpyAsync(codons, ocod, sizeof(int32_t) * ns * m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && !dpn) e = cudaMemcpyAsync(partner, opar, sizeof(int32_t) * ns * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  free_list(tmp);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cf_sample");
+  if (err) return fail(p, CF_ENUMERIC, "cf_sample: traceback inconsistency code " + std::to_string(err));
+  return CF_OK;
 }
 
 }  // namespace
@@ -397,6 +440,8 @@ static void release_protein(cf_problem *p) {
   free_prec(p->f32);
   free_prec(p->f64);
   free_list(p->shared_allocs);
+  free_list(p->smp_allocs);
+  p->smp_cap = 0;
   p->dM = p->dbase = p->dbnd = p->dE = p->derr = nullptr;
   p->ddmax = nullptr;
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;

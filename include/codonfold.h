@@ -147,6 +147,41 @@ cf_status cf_last_timing(const cf_problem *prob, float *inside_ms, float *outsid
 /* Length n = 3m of the current protein, or 0. */
 int cf_problem_length(const cf_problem *prob);
 
+/*
+ * cf_sample_noalloc -- the sampler of cf_sample for callers that cannot
+ * allocate device memory.  (The paper has no counterpart: this is a library
+ * service, not part of the method.)
+ *
+ * Who needs it: code that runs under a device-memory budget owned by another
+ * allocator (for example a framework's caching allocator that has reserved the
+ * device), and latency-critical loops in which cudaMalloc/cudaFree would block
+ * or synchronise the device.  This entry point calls no cudaMalloc, cudaFree or
+ * allocating library routine: the per-warp traceback stacks, per-position
+ * states and the error word live in one static device array of
+ * CF_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.
+ *
+ *   Same arguments and results as cf_sample, except that codons (nsamples*m
+ *   int32) and partner (nsamples*n int32) must be device memory of the
+ *   problem's device.  The inside tables must exist (cf_inside first); they
+ *   were allocated by cf_set_protein / cf_inside, not by this call.
+ *   Limits: n = 3m <= CF_NOALLOC_MAX_N; CF_NOALLOC_WARPS warps draw samples.
+ *   Errors: CF_EINVAL (n above the limit, host or NULL output pointers,
+ *   nsamples < 0), CF_ESTATE (no inside), CF_ECUDA, CF_ENUMERIC.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls in the process share the one array and it keeps the
+ *   last call's contents; the call clears what must start at zero.  Calls
+ *   whose kernels overlap on the GPU (other streams, other threads, other
+ *   problems on the same device) race on the array and must be serialised by
+ *   the caller.
+ */
+#define CF_NOALLOC_MAX_N 3000
+#define CF_NOALLOC_WARPS 128
+cf_status cf_sample_noalloc(cf_problem *prob, int nsamples, uint64_t seed, int32_t *codons,
+                            int32_t *partner);
+
 #ifdef __cplusplus
 }
 #endif

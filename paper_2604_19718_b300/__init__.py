@@ -126,6 +126,15 @@ def cf_problem_length(prob) -> int:
     return int(lib.cf_problem_length(prob))
 
 
+def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:
+    """Sampler for callers that cannot allocate device memory: outputs must be
+    device tensors; scratch comes from the library's static device array."""
+    f = lib.cf_sample_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    _check(f(prob, int(nsamples), ctypes.c_uint64(seed), _ptr(codons), _ptr(partner)), prob)
+
+
 # ---------------------------------------------------------------- convenience
 
 def to_letters(residues) -> str:

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -642,3 +643,87 @@ cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ no-allocation sampler
+// Static scratch of cf_sample_noalloc (see include/codonfold.h): error word,
+// codon ids per position, per-warp states and per-warp traceback stacks for
+// CF_NOALLOC_WARPS warps and sequences of up to CF_NOALLOC_MAX_N bases.
+namespace {
+constexpr size_t kNaErrBytes = 256;
+constexpr size_t kNaCidBytes = ((size_t)CF_NOALLOC_MAX_N * NS * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kNaStateBytes = ((size_t)CF_NOALLOC_WARPS * CF_NOALLOC_MAX_N * sizeof(int) + 255) / 256 * 256;
+constexpr size_t kNaStackBytes = (size_t)CF_NOALLOC_WARPS * (CF_NOALLOC_MAX_N + 64) * sizeof(int2);
+constexpr size_t kNaBytes = kNaErrBytes + kNaCidBytes + kNaStateBytes + kNaStackBytes;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_cf_noalloc_scratch[kNaBytes];
+
+namespace {
+std::mutex g_na_mutex;
+void *g_na_ptr[64] = {nullptr};
+
+// Device address of the static scratch on `device` (looked up once per device,
+// with that device current).
+cudaError_t noalloc_scratch(int device, unsigned char **out) {
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[device]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_cf_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_na_ptr[device] = ptr;
+  }
+  *out = (unsigned char *)g_na_ptr[device];
+  return cudaSuccess;
+}
+
+template <typename T>
+cf_status run_sample_noalloc(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int32_t *codons,
+                             int32_t *partner) {
+  const int n = p->n;
+  cudaStream_t st = p->stream;
+  unsigned char *base = nullptr;
+  CF_CUDA(p, noalloc_scratch(p->device, &base));
+  int *err = (int *)base;
+  int *cid = (int *)(base + kNaErrBytes);
+  int *state = (int *)(base + kNaErrBytes + kNaCidBytes);
+  int2 *stack = (int2 *)(base + kNaErrBytes + kNaCidBytes + kNaStateBytes);
+  // the error word must start at zero; codon ids are rewritten for this protein
+  CF_CUDA(p, cudaMemsetAsync(err, 0, sizeof(int), st));
+  CF_CUDA(p, cudaMemcpyAsync(cid, p->cid.data(), sizeof(int) * (size_t)n * NS, cudaMemcpyHostToDevice, st));
+  const int warps = std::min(ns, CF_NOALLOC_WARPS);
+  SampleArgs<T> a;
+  a.p = t.dp;
+  a.cid = cid;
+  a.nsamples = ns;
+  a.seed = seed;
+  a.stack = stack;
+  a.state = state;
+  a.codons = codons;
+  a.partner = partner;
+  a.err = err;
+  k_sample<T><<<(warps + 3) / 4, 128, 0, st>>>(a);
+  CF_CUDA(p, cudaGetLastError());
+  int herr = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  if (herr) return fail(p, CF_ENUMERIC, "cf_sample_noalloc: traceback inconsistency code " + std::to_string(herr));
+  return CF_OK;
+}
+}  // namespace
+
+extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
+                                       int32_t *partner) {
+  if (!p) return fail(p, CF_EINVAL, "cf_sample_noalloc: NULL problem");
+  if (p->n > CF_NOALLOC_MAX_N)
+    return fail(p, CF_EINVAL, "cf_sample_noalloc: sequence length " + std::to_string(p->n) +
+                                  " exceeds CF_NOALLOC_MAX_N = " + std::to_string(CF_NOALLOC_MAX_N));
+  if (nsamples < 0) return fail(p, CF_EINVAL, "cf_sample_noalloc: nsamples < 0");
+  if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample_noalloc: run cf_inside first");
+  if (nsamples == 0) return CF_OK;
+  CF_CUDA(p, cudaSetDevice(p->device));
+  if (!is_device_ptr(codons) || !is_device_ptr(partner))
+    return fail(p, CF_EINVAL, "cf_sample_noalloc: codons and partner must be device memory");
+  return (p->last_prec == CF_FP64) ? run_sample_noalloc(p, p->f64, nsamples, seed, codons, partner)
+                                   : run_sample_noalloc(p, p->f32, nsamples, seed, codons, partner);
+}

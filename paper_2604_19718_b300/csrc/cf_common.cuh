@@ -141,17 +141,25 @@ __device__ __forceinline__ void acc_mm(T (&acc)[BLK], const T *A, const T *B, in
   }
 }
 
-// One entry (a,b) of op(A) op(B) op(C) with inner sizes Mu, Mv.
+// One entry (a,b) of op(A) op(B) op(C) with inner sizes Mu, Mv.  Loops are
+// unrolled to the padded size with predicates so that all loads of one
+// contraction issue together instead of one dependent round trip per term.
 template <bool TA, bool TB, bool TC, typename T>
 __device__ __forceinline__ T e3(const T *A, const T *B, const T *C, int a, int b, int Mu, int Mv) {
+  T cv[NS];
+#pragma unroll
+  for (int v = 0; v < NS; v++) cv[v] = (v < Mv) ? (TC ? C[b * NS + v] : C[v * NS + b]) : (T)0;
   T s = 0;
-  for (int u = 0; u < Mu; u++) {
-    T av = TA ? A[u * NS + a] : A[a * NS + u];
-    if (av == (T)0) continue;
-    T t = 0;
-    for (int v = 0; v < Mv; v++)
-      t += (TB ? B[v * NS + u] : B[u * NS + v]) * (TC ? C[b * NS + v] : C[v * NS + b]);
-    s += av * t;
+#pragma unroll
+  for (int u = 0; u < NS; u++) {
+    if (u < Mu) {
+      T av = TA ? A[u * NS + a] : A[a * NS + u];
+      T t = 0;
+#pragma unroll
+      for (int v = 0; v < NS; v++)
+        if (v < Mv) t += (TB ? B[v * NS + u] : B[u * NS + v]) * cv[v];
+      s += av * t;
+    }
   }
   return s;
 }
@@ -160,7 +168,9 @@ __device__ __forceinline__ T e3(const T *A, const T *B, const T *C, int a, int b
 template <bool TA, bool TB, typename T>
 __device__ __forceinline__ T e2(const T *A, const T *B, int a, int b, int Mu) {
   T s = 0;
-  for (int u = 0; u < Mu; u++) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
+#pragma unroll
+  for (int u = 0; u < NS; u++)
+    if (u < Mu) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
   return s;
 }
 

@@ -138,10 +138,16 @@ __global__ void __launch_bounds__(32 * WPB) k_inside(DP<T> p, int d) {
           for (int b = 0; b < NS; b++) {
             if (b < My) {
               T v = 0;
-              if (yp)
-                for (int s = 0; s < M1; s++) v += tx[a * NS + s] * yp[s * NS + b];
-              if (hasxi)
-                for (int s = 0; s < Ml; s++) v += xi[a * NS + s] * ch[s * NS + b];
+              if (yp) {
+#pragma unroll
+                for (int s = 0; s < NS; s++)
+                  if (s < M1) v += tx[a * NS + s] * yp[s * NS + b];
+              }
+              if (hasxi) {
+#pragma unroll
+                for (int s = 0; s < NS; s++)
+                  if (s < Ml) v += xi[a * NS + s] * ch[s * NS + b];
+              }
               yo[a * NS + b] = v;
               acc[a * NS + b] += wgt * en[EN_TM + base[x * NS + a] * 4 + base[y * NS + b]] * v;
             }
@@ -197,13 +203,19 @@ __global__ void __launch_bounds__(32 * WPB) k_inside(DP<T> p, int d) {
       if (pto >= 0) {
         v = e3<false, false, false>(tx, hb, ty, a, b, Mu, Mv);
         if (qin) {
-          for (int a2 = 0; a2 < Mu; a2++) {
-            T t = tx[a * NS + a2];
-            if (t == (T)0) continue;
-            for (int b2 = 0; b2 < Mv; b2++) {
-              int pti = pair_type(base[(x + 1) * NS + a2], base[(y - 1) * NS + b2]);
-              if (pti < 0) continue;
-              v += t * qin[a2 * NS + b2] * ty[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
+#pragma unroll
+          for (int a2 = 0; a2 < NS; a2++) {
+            if (a2 < Mu) {
+              T t = tx[a * NS + a2];
+              const int ba = base[(x + 1) * NS + a2];
+#pragma unroll
+              for (int b2 = 0; b2 < NS; b2++) {
+                if (b2 < Mv) {
+                  int pti = pair_type(ba, base[(y - 1) * NS + b2]);
+                  T e = pti >= 0 ? en[EN_STK + pto * 6 + pti] : (T)0;
+                  v += t * qin[a2 * NS + b2] * ty[b2 * NS + b] * e;
+                }
+              }
             }
           }
         }

@@ -20,7 +20,9 @@
 #include "../../include/codonfold.h"
 #include "cf_common.cuh"
 #include "cf_inside.cuh"
+#include "cf_inside2.cuh"
 #include "cf_outside.cuh"
+#include "cf_outside2.cuh"
 #include "cf_sample.cuh"
 
 using namespace cf;
@@ -102,6 +104,12 @@ template <typename T>
 struct PrecTables {
   bool inside_alloc = false, outside_alloc = false;
   DP<T> dp{};
+  BifBuf<T> bb{};
+  cudaGraphExec_t gin = nullptr;  // inside pass as one graph
+  int gin_nodes = 0;
+  OutBuf<T> ob{};
+  cudaGraphExec_t gout = nullptr;  // outside pass as one graph
+  int gout_nodes = 0;
   std::vector<void *> allocs;
 };
 
@@ -170,6 +178,10 @@ void free_list(std::vector<void *> &list) {
 
 template <typename T>
 void free_prec(PrecTables<T> &t) {
+  if (t.gin) cudaGraphExecDestroy(t.gin);
+  if (t.gout) cudaGraphExecDestroy(t.gout);
+  t.gin = nullptr;
+  t.gout = nullptr;
   free_list(t.allocs);
   t.inside_alloc = t.outside_alloc = false;
   t.dp = DP<T>{};
@@ -233,7 +245,79 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
     CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
     CF_CUDA(p, cudaMemset(*q, 0, (size_t)n * BLK * sizeof(T)));
   }
+  t.bb.ncmax = std::max(1, std::max(nchunk_bif(n - 1), nchunk_ext(n - 1)));
+  CF_CUDA(p, dalloc(L, &t.bb.main, (size_t)BIFRING * n * t.bb.ncmax * BLK));
+  CF_CUDA(p, dalloc(L, &t.bb.ext, (size_t)BIFRING * t.bb.ncmax * BLK));
   t.inside_alloc = true;
+  return CF_OK;
+}
+
+// The inside pass as a CUDA graph: a chain of light kernels, one per
+// anti-diagonal, and the bifurcation kernel of diagonal d hanging off the light
+// kernel of diagonal d-4, so that it runs while d-3..d-1 are being filled.
+template <typename T>
+cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
+  if (t.gin) return CF_OK;
+  const int n = p->n;
+  const size_t smem = in_light_smem<T>();
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaGraph_t g;
+  CF_CUDA(p, cudaGraphCreate(&g, 0));
+  cudaGraphNode_t mset;
+  cudaMemsetParams ms = {};
+  ms.dst = p->ddmax;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = (size_t)n * 2;
+  ms.height = 1;
+  cudaError_t e = cudaGraphAddMemsetNode(&mset, g, nullptr, 0, &ms);
+  std::vector<cudaGraphNode_t> k2(n);
+  std::vector<cudaGraphNode_t> k1(n);
+  int nodes = 0;
+  DP<T> dp = t.dp;
+  BifBuf<T> bb = t.bb;
+  for (int d = 0; d < n && e == cudaSuccess; d++) {
+    int dd = d;
+    void *args[] = {&dp, &bb, &dd};
+    if (d >= 8) {
+      int items = (n - d) * nchunk_bif(d) + nchunk_ext(d);
+      cudaKernelNodeParams kp = {};
+      kp.func = (void *)k_in_bif<T>;
+      kp.gridDim = dim3((items + 3) / 4);
+      kp.blockDim = dim3(128);
+      kp.kernelParams = args;
+      e = cudaGraphAddKernelNode(&k1[d], g, &k2[d - 4], 1, &kp);
+      nodes++;
+    }
+    if (e != cudaSuccess) break;
+    cudaGraphNode_t deps[2];
+    int nd = 0;
+    deps[nd++] = (d == 0) ? mset : k2[d - 1];
+    if (d >= 8) deps[nd++] = k1[d];
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_in_light<T>;
+    kp.gridDim = dim3(n - d);
+    kp.blockDim = dim3(128);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    nodes++;
+  }
+  if (e == cudaSuccess) {
+    void *args[] = {&dp};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_inside_finish<T>;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    cudaGraphNode_t fin;
+    e = cudaGraphAddKernelNode(&fin, g, &k2[n - 1], 1, &kp);
+    nodes++;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&t.gin, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(p, e, "inside graph");
+  t.gin_nodes = nodes;
   return CF_OK;
 }
 
@@ -258,7 +342,103 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   }
   CF_CUDA(p, dalloc(L, &d.hT, (size_t)n * BLK));
   CF_CUDA(p, dalloc(L, &d.hX, (size_t)n * 4 * BLK));
+  t.ob.ncmax = (n + KCH - 1) / KCH + 2;
+  CF_CUDA(p, dalloc(L, &t.ob.hg, (size_t)BIFRING * n * t.ob.ncmax * BLK));
+  CF_CUDA(p, dalloc(L, &t.ob.hq, (size_t)BIFRING * n * t.ob.ncmax * BLK));
+  CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * t.ob.ncmax * BLK));
   t.outside_alloc = true;
+  return CF_OK;
+}
+
+cudaError_t add_memset(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep, void *ptr,
+                       size_t bytes) {
+  cudaMemsetParams ms = {};
+  ms.dst = ptr;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = bytes / 4;
+  ms.height = 1;
+  return cudaGraphAddMemsetNode(node, g, dep, ndep, &ms);
+}
+
+// The outside pass as a CUDA graph: a chain of light kernels from d = n-1 down
+// to 0, with the transposed bifurcation kernel of diagonal d hanging off the
+// light kernel of diagonal d+4.
+template <typename T>
+cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
+  if (t.gout) return CF_OK;
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  const size_t smem = out_light_smem<T>();
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaGraph_t g;
+  CF_CUDA(p, cudaGraphCreate(&g, 0));
+  DP<T> dp = t.dp;
+  OutBuf<T> ob = t.ob;
+  cudaGraphNode_t m[5];
+  cudaError_t e = add_memset(g, &m[0], nullptr, 0, dp.hCH, nc * sizeof(T));
+  if (e == cudaSuccess) e = add_memset(g, &m[1], &m[0], 1, dp.hXI, nc * sizeof(T));
+  if (e == cudaSuccess) e = add_memset(g, &m[2], &m[1], 1, dp.hT, (size_t)n * BLK * sizeof(double));
+  if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double));
+  if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float));
+  std::vector<cudaGraphNode_t> k2(n), k1(n);
+  int nodes = 0;
+  for (int d = n - 1; d >= 0 && e == cudaSuccess; d--) {
+    int dd = d;
+    void *args[] = {&dp, &ob, &dd};
+    const bool hasb = d <= n - 5 && d >= 1;
+    if (hasb) {
+      cudaKernelNodeParams kp = {};
+      kp.func = (void *)k_out_bif<T>;
+      kp.gridDim = dim3((out_cell_chunks(n, d) + 3) / 4, n - d + 1);
+      kp.blockDim = dim3(128);
+      kp.kernelParams = args;
+      e = cudaGraphAddKernelNode(&k1[d], g, &k2[d + 4], 1, &kp);
+      nodes++;
+      if (e != cudaSuccess) break;
+    }
+    cudaGraphNode_t deps[2];
+    int nd = 0;
+    deps[nd++] = (d == n - 1) ? m[4] : k2[d + 1];
+    if (hasb) deps[nd++] = k1[d];
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_out_light<T>;
+    kp.gridDim = dim3(n - d);
+    kp.blockDim = dim3(128);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    nodes++;
+  }
+  cudaGraphNode_t fin = nullptr;
+  if (e == cudaSuccess) {
+    double *trans = p->dtrans, *p0 = p->dp0;
+    void *args[] = {&dp, &trans, &p0};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_marginals<T>;
+    kp.gridDim = dim3((std::max(p->m - 1, 1) + 127) / 128);
+    kp.blockDim = dim3(128);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&fin, g, &k2[0], 1, &kp);
+    nodes++;
+  }
+  if (e == cudaSuccess) {
+    float *P = dp.P;
+    int nn = n;
+    void *args[] = {&P, &nn};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_unpaired;
+    kp.gridDim = dim3((n + 7) / 8);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    cudaGraphNode_t un;
+    e = cudaGraphAddKernelNode(&un, g, &fin, 1, &kp);
+    nodes++;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&t.gout, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(p, e, "outside graph");
+  t.gout_nodes = nodes;
   return CF_OK;
 }
 
@@ -268,19 +448,12 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   if (s != CF_OK) return s;
   const int n = p->n;
   cudaStream_t st = p->stream;
-  CF_CUDA(p, cudaMemsetAsync(p->ddmax, 0, sizeof(unsigned long long) * n, st));
+  s = build_inside_graph(p, t);
+  if (s != CF_OK) return s;
   CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
-  int launches = 0;
-  for (int d = 0; d < n; d++) {
-    int cells = n - d;
-    int blocks = (cells + WPB - 1) / WPB;
-    k_inside<T><<<blocks, 32 * WPB, 0, st>>>(t.dp, d);
-    launches++;
-  }
-  k_inside_finish<T><<<1, 32, 0, st>>>(t.dp);
-  launches++;
-  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaGraphLaunch(t.gin, st));
+  int launches = t.gin_nodes;
   CF_CUDA(p, cudaEventRecord(p->ev[1], st));
   double zm = 0;
   int e_last = 0, err = 0;
@@ -304,22 +477,11 @@ cf_status run_outside(cf_problem *p, PrecTables<T> &t) {
   const size_t nc = ncells(n) * BLK;
   DP<T> &d = t.dp;
   cudaStream_t st = p->stream;
-  CF_CUDA(p, cudaMemsetAsync(d.hCH, 0, nc * sizeof(T), st));
-  CF_CUDA(p, cudaMemsetAsync(d.hXI, 0, nc * sizeof(T), st));
-  CF_CUDA(p, cudaMemsetAsync(d.hT, 0, (size_t)n * BLK * sizeof(double), st));
-  CF_CUDA(p, cudaMemsetAsync(d.hX, 0, (size_t)n * 4 * BLK * sizeof(double), st));
-  CF_CUDA(p, cudaMemsetAsync(d.P, 0, (size_t)n * n * sizeof(float), st));
+  s = build_outside_graph(p, t);
+  if (s != CF_OK) return s;
   CF_CUDA(p, cudaEventRecord(p->ev[2], st));
-  int launches = 0;
-  for (int dd = n - 1; dd >= 0; dd--) {
-    int cells = n - dd;
-    int blocks = (cells + WPB - 1) / WPB;
-    k_outside<T><<<blocks, 32 * WPB, 0, st>>>(d, dd);
-    launches++;
-  }
-  k_marginals<T><<<(std::max(p->m - 1, 1) + 127) / 128, 128, 0, st>>>(d, p->dtrans, p->dp0);
-  k_unpaired<<<(n + 7) / 8, 256, 0, st>>>(d.P, n);
-  launches += 2;
+  CF_CUDA(p, cudaGraphLaunch(t.gout, st));
+  int launches = t.gout_nodes;
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaEventRecord(p->ev[3], st));
   p->l_out = launches;

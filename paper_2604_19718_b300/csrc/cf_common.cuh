@@ -174,6 +174,34 @@ __device__ __forceinline__ T e2(const T *A, const T *B, int a, int b, int Mu) {
   return s;
 }
 
+// Shared-memory versions with runtime trip counts (operands already on chip).
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ T s2(const T *A, const T *B, int a, int b, int Mu) {
+  T s = 0;
+  for (int u = 0; u < Mu; u++) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
+  return s;
+}
+template <bool TA, bool TB, bool TC, typename T>
+__device__ __forceinline__ T s3(const T *A, const T *B, const T *C, int a, int b, int Mu, int Mv) {
+  T s = 0;
+  for (int u = 0; u < Mu; u++) {
+    const T av = TA ? A[u * NS + a] : A[a * NS + u];
+    if (av == (T)0) continue;
+    T t = 0;
+    for (int v = 0; v < Mv; v++) t += (TB ? B[v * NS + u] : B[u * NS + v]) * (TC ? C[b * NS + v] : C[v * NS + b]);
+    s += av * t;
+  }
+  return s;
+}
+
+// Accessors of the per-cell context staged by the light kernels (sE, sMx,
+// sMy, sBx, sBy): exponents of diagonals d-47..d+48 (E[d] itself is passed as
+// Ed), codon-state counts of positions within 35 of x or y, bases of
+// x-1..x+1 and y-1..y+1.  Other indices fall back to global memory.
+#define EA(k) ((k) == d ? Ed : (((k) >= d - 47 && (k) <= d + 48) ? sE[(k) - (d - 47)] : p.E[k]))
+#define MP(q) (((q) >= x - 35 && (q) <= x + 36) ? sMx[(q) - (x - 35)] : (((q) >= y - 35 && (q) <= y + 36) ? sMy[(q) - (y - 35)] : p.Mp[q]))
+#define BASE(q, a) (((q) >= x - 1 && (q) <= x + 1) ? sBx[(q) - (x - 1)][a] : sBy[(q) - (y - 1)][a])
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
   if (v > 0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }

@@ -29,11 +29,19 @@
 
 namespace cf {
 
+// 2^e from its IEEE-754 bit pattern (exponent field e + bias, zero mantissa);
+// exponents below the normal range give 0, above 120 are clamped to 2^120.
 template <typename T>
-__device__ __forceinline__ T clamp_p2(int e) {
+__device__ __forceinline__ T clamp_p2(int e);
+template <>
+__device__ __forceinline__ float clamp_p2<float>(int e) {
   e = e > 120 ? 120 : e;
-  e = e < -400 ? -400 : e;
-  return p2<T>(e);
+  return e < -126 ? 0.0f : __int_as_float((e + 127) << 23);
+}
+template <>
+__device__ __forceinline__ double clamp_p2<double>(int e) {
+  e = e > 120 ? 120 : e;
+  return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
 // store the warp-reduced block: entry e owned by lane e % 32

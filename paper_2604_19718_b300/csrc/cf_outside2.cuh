@@ -24,10 +24,9 @@ namespace cf {
 
 template <typename T>
 struct OutBuf {
-  T *hg;   // [BIFRING][n][ncmax][36] row-gather chunks
-  T *hq;   // [BIFRING][n][ncmax][36] column-gather chunks
-  T *hgx;  // [BIFRING][ncmax][36]    exterior chunks
-  int ncmax;
+  T *hg;   // [BIFRING][n][36] row gathers (contribution to hG)
+  T *hq;   // [BIFRING][n][36] column gathers (contribution to hQB)
+  T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
 };
 
 __host__ __device__ __forceinline__ int out_nrow(int n, int x, int d) {  // hG terms y' = y+4..n-1
@@ -42,60 +41,78 @@ __host__ __device__ __forceinline__ int out_next(int n, int d) {  // hGx terms y
   int cnt = n - d - 4;
   return (d >= 1 && cnt > 0) ? (cnt + KCH - 1) / KCH : 0;
 }
-// chunks per cell used for the launch shape (upper bound over x)
-__host__ __device__ __forceinline__ int out_cell_chunks(int n, int d) {
-  int cnt = n - d - 8;
-  return (cnt > 0 ? (cnt + KCH - 1) / KCH : 0) + 2;
-}
 
 // ---------------------------------------------------------------- K1'
-// grid (chunks_per_cell / 4 rounded up, n - d [+1 for the exterior row]), 128 threads
+// One 256-thread block per cell (last block: the exterior gather). Warps 0..3
+// take the row-gather chunks, warps 4..7 the column-gather chunks (all eight
+// take the exterior chunks); lanes over the summation index.
 template <typename T>
-__global__ void __launch_bounds__(128) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
-  const int lane = threadIdx.x & 31;
-  const int q = blockIdx.x * 4 + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
+  __shared__ T red[8][BLK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = p.n;
   const int *E = p.E;
   const int Ed = E[d];
   const int slot = d % BIFRING;
   const T ec = p.en[EN_EC];
+  const bool ext = blockIdx.x == (unsigned)(n - d);
   T acc[BLK];
   zero_block(acc);
-  T dummy = 0;
-  if (blockIdx.y == (unsigned)(n - d)) {
-    // exterior: hGx[d]
-    if (q >= out_next(n, d)) return;
-    const int M0 = p.Mp[0], Md = p.Mp[d];
-    const int yy = d + 4 + q * KCH + lane;
-    if (yy <= n - 1) {
-      T f = clamp_p2<T>(Ed + E[yy - d] - E[yy]);
-      acc_mm<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, M0, p.Mp[yy], Md, f);
+  int Ma, Mb;
+  if (ext) {
+    Ma = p.Mp[0];
+    Mb = p.Mp[d];
+    const int nq = out_next(n, d);
+    for (int q = w; q < nq; q += 8) {
+      const int yy = d + 4 + q * KCH + lane;
+      if (yy <= n - 1) {
+        T f = clamp_p2<T>(Ed + E[yy - d] - E[yy]);
+        acc_mm<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+      }
     }
-    warp_reduce_block(acc, M0, Md);
-    store_block(ob.hgx + ((size_t)slot * ob.ncmax + q) * BLK, acc, M0, Md, lane, dummy);
-    return;
-  }
-  const int x = blockIdx.y, y = x + d;
-  const int nr = out_nrow(n, x, d), nq = out_ncol(x, d);
-  if (q >= nr + nq) return;
-  const int Mx = p.Mp[x], My = p.Mp[y];
-  if (q < nr) {
-    const int yy = y + 4 + q * KCH + lane;
-    if (yy <= n - 1) {
-      T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
-      acc_mm<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Mx, p.Mp[yy], My, f);
-    }
-    warp_reduce_block(acc, Mx, My);
-    store_block(ob.hg + (((size_t)slot * n + x) * ob.ncmax + q) * BLK, acc, Mx, My, lane, dummy);
   } else {
-    const int c = q - nr;
-    const int xx = x - 5 - c * KCH - lane;
-    if (xx >= 0) {
-      T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
-      acc_mm<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Mx, p.Mp[xx], My, f);
+    const int x = blockIdx.x, y = x + d;
+    Ma = p.Mp[x];
+    Mb = p.Mp[y];
+    if (w < 4) {
+      const int nr = out_nrow(n, x, d);
+      for (int q = w; q < nr; q += 4) {
+        const int yy = y + 4 + q * KCH + lane;
+        if (yy <= n - 1) {
+          T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
+          acc_mm<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+        }
+      }
+    } else {
+      const int nq = out_ncol(x, d);
+      for (int q = w - 4; q < nq; q += 4) {
+        const int xx = x - 5 - q * KCH - lane;
+        if (xx >= 0) {
+          T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
+          acc_mm<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
+        }
+      }
     }
-    warp_reduce_block(acc, Mx, My);
-    store_block(ob.hq + (((size_t)slot * n + x) * ob.ncmax + c) * BLK, acc, Mx, My, lane, dummy);
+  }
+  warp_reduce_block(acc, Ma, Mb);
+  if (lane < 2) {
+#pragma unroll
+    for (int e = 0; e < BLK; e++)
+      if ((e & 1) == lane) red[w][e] = acc[e];
+  }
+  __syncthreads();
+  if (threadIdx.x < BLK) {
+    const int e = threadIdx.x;
+    if (ext) {
+      T v = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) v += red[k][e];
+      ob.hgx[(size_t)slot * BLK + e] = v;
+    } else {
+      const int x = blockIdx.x;
+      ob.hg[((size_t)slot * n + x) * BLK + e] = red[0][e] + red[1][e] + red[2][e] + red[3][e];
+      ob.hq[((size_t)slot * n + x) * BLK + e] = red[4][e] + red[5][e] + red[6][e] + red[7][e];
+    }
   }
 }
 
@@ -108,7 +125,8 @@ enum : int {
   SO_HCHL = 43, SO_HCH = 44, SO_HXI = 45, SO_GX = 46, SO_HQ5P = 47,
   SO_HYR = 48, SO_YYP = 76, SO_XIL = 104, SO_CHL = 132,
   SO_BQ3 = 160, SO_BQ5 = 190, SO_BC3U = 220, SO_BC5U = 250, SO_BH3U = 280, SO_BH5U = 310,
-  SO_N = 340
+  SO_HGC = 340, SO_HQC = 341, SO_HGXC = 342, SO_HQ5U1 = 343, SO_HGX1 = 344, SO_Q5UM = 345, SO_Q5PM = 346,
+  SO_N = 347
 };
 
 template <typename T>
@@ -190,308 +208,332 @@ __device__ __forceinline__ const T *out_slot_src(const DP<T> &p, int s, int x, i
   return up5 ? p.hHB + cidx(n, x - L, y) * BLK : nullptr;
 }
 
-// ---------------------------------------------------------------- K2'
+// gather results of k_out_bif and the exterior inputs of the cell (0, d)
 template <typename T>
-__global__ void __launch_bounds__(128) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
+__device__ __forceinline__ const T *out_slot_src2(const DP<T> &p, const OutBuf<T> &ob, int s, int x, int d) {
+  const int n = p.n, slot = d % BIFRING;
+  if (s == SO_HGC) return out_nrow(n, x, d) > 0 ? ob.hg + ((size_t)slot * n + x) * BLK : nullptr;
+  if (s == SO_HQC) return out_ncol(x, d) > 0 ? ob.hq + ((size_t)slot * n + x) * BLK : nullptr;
+  if (x != 0) return nullptr;
+  if (s == SO_HGXC) return out_next(n, d) > 0 ? ob.hgx + (size_t)slot * BLK : nullptr;
+  if (s == SO_HQ5U1) return d + 1 < n ? p.hQ5U + (size_t)(d + 1) * BLK : nullptr;
+  if (s == SO_HGX1) return d + 1 < n ? p.hGx + (size_t)(d + 1) * BLK : nullptr;
+  if (s == SO_Q5UM) return d >= 1 ? p.Q5U + (size_t)(d - 1) * BLK : nullptr;
+  if (s == SO_Q5PM) return d >= 1 ? p.Q5P + (size_t)(d - 1) * BLK : nullptr;
+  return nullptr;
+}
+
+// ---------------------------------------------------------------- K2'
+// Thread mapping as in k_in_light: compact entries e = a*M_b + b, work lists
+// split into NT/(M_x*M_y) groups.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = (T *)smem_raw;            // [SO_N][36]
   T *HY = S + (size_t)SO_N * BLK;  // [29][36] interior partial-sum adjoints
   T *W = HY + NYY * BLK;           // work blocks
-  T *hMPP = W, *hHB = W + BLK, *hQB = W + 2 * BLK, *G = W + 3 * BLK, *hCHf = W + 4 * BLK, *Hxi = W + 5 * BLK;
-  T *ACC = W + 6 * BLK;            // [3][36]
-  T *hM2 = W + 9 * BLK;            // uu, up, pu, pp
-  T *hMPU = W + 13 * BLK, *hGG = W + 14 * BLK;
-  __shared__ double sps[4];
+  T *hMPP = W, *hHB = W + BLK, *hQB = W + 2 * BLK, *hCHf = W + 3 * BLK, *Hxi = W + 4 * BLK;
+  T *hM2 = W + 5 * BLK;            // uu, up, pu, pp
+  T *hMPU = W + 9 * BLK, *hGG = W + 10 * BLK;
+  T *hQ5Uo = W + 11 * BLK, *hQ5Po = W + 12 * BLK, *hGxo = W + 13 * BLK;  // exterior (cell (0, d))
+  T *RED = W + 14 * BLK;           // [NT]
+  __shared__ double sps[NT / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int x = blockIdx.x, y = x + d;
-  for (int s = t; s < SO_N; s += blockDim.x) {
-    const T *src = out_slot_src(p, s, x, y, d);
+  for (int s = t; s < SO_N; s += NT) {
+    const T *src = s < SO_HGC ? out_slot_src(p, s, x, y, d) : out_slot_src2(p, ob, s, x, d);
     if (src) stage_block(S + (size_t)s * BLK, src);
   }
+  // small per-cell context on chip: exponents around d, codon-state counts
+  // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
+  __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
+  __shared__ T sEn[EN_N];
+  for (int i = t; i < 96; i += NT) {
+    const int k = d - 47 + i;
+    sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
+  }
+  for (int i = t; i < 72; i += NT) {
+    const int qx = x - 35 + i, qy = y - 35 + i;
+    sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
+    sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
+  }
+  for (int i = t; i < 3 * NS; i += NT) {
+    const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
+    sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
+    sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
+  }
+  for (int i = t; i < EN_N; i += NT) sEn[i] = p.en[i];
   cp_async_wait_all();
   __syncthreads();
-  const int *E = p.E;
-  const int *base = p.base;
-  const T *en = p.en;
-  const int Ed = E[d];
-  const int Mx = p.Mp[x], My = p.Mp[y];
+    const T *en = sEn;
+  const int Ed = p.E[d];
+  const int Mx = MP(x), My = MP(y), MM = Mx * My;
+  const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
   const size_t c = cidx(n, x, y);
   const T eb = en[EN_EB], ec = en[EN_EC], sml = en[EN_EA] * en[EN_EC];
   const bool hasL = x >= 1, hasR = y <= n - 2, encl = hasL && hasR;
-  const int Mxl = hasL ? p.Mp[x - 1] : 0, Myr = hasR ? p.Mp[y + 1] : 0;
-  const T F1u = (d + 1 < n) ? clamp_p2<T>(Ed - E[d + 1]) : (T)0;
-  const T F2u = (d + 2 < n) ? clamp_p2<T>(Ed - E[d + 2]) : (T)0;
+  const int Mxl = hasL ? MP(x - 1) : 0, Myr = hasR ? MP(y + 1) : 0;
+  const int M0 = MP(0);
+  const T F1u = (d + 1 < n) ? clamp_p2<T>(Ed - EA(d + 1)) : (T)0;
+  const T F2u = (d + 2 < n) ? clamp_p2<T>(Ed - EA(d + 2)) : (T)0;
   const T *gc = S + SO_GC * BLK;
   const T *Xxl = S + SO_XXL * BLK, *Xy = S + SO_XY * BLK;
-  const int slot = d % BIFRING;
+  // loop-length weights: bulge users eBu(L) 2^{E[d]-E[d+L]}, own bulges
+  // eBu(L) 2^{E[d-L]-E[d]}, interior eIn(L) 2^{E[d-L+2]-E[d]}
+  __shared__ T wBuU[MAXLOOP + 1], wBu[MAXLOOP + 1], wIn[MAXLOOP + 1];
+  if (t <= MAXLOOP) {
+    const int L = t;
+    wBuU[L] = (L >= 1 && d + L < n) ? en[EN_BU + L] * clamp_p2<T>(Ed - EA(d + L)) : (T)0;
+    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed) : (T)0;
+    wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed) : (T)0;
+  }
+  __syncthreads();
   const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[y - 1] != 0;
 
-  // ---------------- A: exterior adjoint (cell (0, d)), multiloop tables with unpaired ends
-  if (x == 0 && t >= 3 * BLK) {
-    // threads 108..127: hQ5U, hQ5P of prefix [0, d] (entries strided by 20)
-    const int M0 = p.Mp[0];
-    for (int e = t - 3 * BLK; e < BLK; e += 128 - 3 * BLK) {
-      const int a = e / NS, b = e % NS;
-      if (a >= M0 || b >= My) continue;
-      T hu, hp;
-      if (d == n - 1) {
-        hu = hp = (T)(p.u0[a] / *p.Zm);
-      } else {
-        const T *hu1 = p.hQ5U + (size_t)(d + 1) * BLK, *hg1 = p.hGx + (size_t)(d + 1) * BLK;
-        const int M1 = p.Mp[d + 1];
-        hu = F1u * (e2<false, true>(hu1, Xy + XUU * BLK, a, b, M1) + e2<false, true>(hg1, Xy + XUP * BLK, a, b, M1));
-        hp = F1u * (e2<false, true>(hu1, Xy + XPU * BLK, a, b, M1) + e2<false, true>(hg1, Xy + XPP * BLK, a, b, M1));
-      }
-      p.hQ5U[(size_t)d * BLK + e] = hu;
-      p.hQ5P[(size_t)d * BLK + e] = hp;
-    }
-  }
-  if (d >= 10 && t < 3 * BLK) {
-    const int g = t / BLK, e = t % BLK, a = e / NS, b = e % NS;
-    if (a < Mx && b < My) {
-      const bool mlu = encl && d + 2 >= 11;
-      T v = 0;
-      if (g == 0) {  // QM2uu
-        if (mlu) v = sml * F2u * e3<true, false, true>(Xxl + XPU * BLK, gc, Xy + XUP * BLK, a, b, Mxl, Myr);
-        if (hasL) v += eb * F1u * e2<true, false>(Xxl + XUU * BLK, S + SO_H2UU * BLK, a, b, Mxl);
-      } else if (g == 1) {  // QM2up
-        if (mlu) v = sml * F2u * e3<true, false, true>(Xxl + XPU * BLK, gc, Xy + XPP * BLK, a, b, Mxl, Myr);
-        if (hasL) v += eb * F1u * e2<true, false>(Xxl + XUU * BLK, S + SO_H2UP * BLK, a, b, Mxl);
-      } else {  // QM2pu
-        if (mlu) v = sml * F2u * e3<true, false, true>(Xxl + XPP * BLK, gc, Xy + XUP * BLK, a, b, Mxl, Myr);
-        if (hasL) v += eb * F1u * e2<true, false>(Xxl + XUP * BLK, S + SO_H2UU * BLK, a, b, Mxl);
-        if (hasR) v += eb * F1u * e2<false, true>(S + SO_H2PU * BLK, Xy + XUU * BLK, a, b, Myr);
-      }
-      hM2[g * BLK + e] = v;
-      T *dst = g == 0 ? p.hQM2uu : (g == 1 ? p.hQM2up : p.hQM2pu);
-      dst[c * BLK + e] = v;
-    }
-  }
-  __syncthreads();
-  if (x == 0 && d >= 1 && t < BLK) {
-    // hGx[d] from its chunks
-    const int M0 = p.Mp[0], a = t / NS, b = t % NS;
-    if (a < M0 && b < My) {
-      T v = 0;
-      const int nq = out_next(n, d);
-      for (int q = 0; q < nq; q++) v += ob.hgx[((size_t)slot * ob.ncmax + q) * BLK + t];
-      p.hGx[(size_t)d * BLK + t] = v;
-    }
-  }
-
-  // ---------------- B: hG, hQMpu, hQMpp (from the users one diagonal up)
-  if (t < 3 * BLK) {
-    const int g = t / BLK, e = t % BLK, a = e / NS, b = e % NS;
-    if (a < Mx && b < My) {
-      if (g == 0 && d >= 5) {
-        T v = 0;
-        const int nr = out_nrow(n, x, d);
-        const T *bp = ob.hg + (((size_t)slot * n + x) * ob.ncmax) * BLK + e;
-        for (int q = 0; q < nr; q++) v += bp[(size_t)q * BLK];
-        hGG[e] = v;
-        p.hG[c * BLK + e] = v;
-      } else if (g == 1 && d >= 5) {
-        T v = 0;
-        if (hasR)
-          v = F1u * (eb * e2<false, true>(S + SO_HMPU * BLK, Xy + XUU * BLK, a, b, Myr) +
-                     e2<false, true>(S + SO_HG1 * BLK, Xy + XUP * BLK, a, b, Myr));
-        hMPU[e] = v;
-        p.hQMpu[c * BLK + e] = v;
-      } else if (g == 2 && d >= 4) {
-        T v = 0;
-        if (hasR)
-          v = F1u * (eb * e2<false, true>(S + SO_HMPU * BLK, Xy + XPU * BLK, a, b, Myr) +
-                     e2<false, true>(S + SO_HG1 * BLK, Xy + XPP * BLK, a, b, Myr));
-        hMPP[e] = v;
-        p.hQMpp[c * BLK + e] = v;
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---------------- C: hQM2pp (0..35), hHB (36..71)
-  if (t < BLK) {
-    const int a = t / NS, b = t % NS;
-    if (d >= 4 && a < Mx && b < My) {
-      T v = hMPP[t];
-      if (d >= 9) {
-        if (encl && d + 2 >= 11) v += sml * F2u * e3<true, false, true>(Xxl + XPP * BLK, gc, Xy + XPP * BLK, a, b, Mxl, Myr);
-        if (hasR && d + 1 >= 10) v += eb * F1u * e2<false, true>(S + SO_H2PU * BLK, Xy + XPU * BLK, a, b, Myr);
-        if (hasL && d + 1 >= 10) v += eb * F1u * e2<true, false>(Xxl + XUP * BLK, S + SO_H2UP * BLK, a, b, Mxl);
-      } else {
-        v = 0;
-      }
-      hM2[3 * BLK + t] = v;
-      p.hQM2pp[c * BLK + t] = v;
-    }
-  } else if (t < 2 * BLK) {
-    const int e = t - BLK, a = e / NS, b = e % NS;
-    if (d >= 2 && a < Mx && b < My) {
-      T v = 0;
-      if (encl) v = F2u * e3<true, false, true>(S + SO_TXL * BLK, gc, S + SO_TY * BLK, a, b, Mxl, Myr);
-      hHB[e] = v;
-      p.hHB[c * BLK + e] = v;
-    }
-  }
-  __syncthreads();
-
-  // ---------------- D: hQB = sum of its users (three groups of threads)
-  if (d >= 4 && t < 3 * BLK) {
-    const int g = t / BLK, e = t % BLK, a = e / NS, b = e % NS;
+  // ---------------- A: QM2 adjoints with unpaired ends; exterior prefix adjoint
+  if (d >= 10 && (t < MM || (t >= 64 && t < 64 + MM) || (t >= 128 && t < 128 + MM))) {
+    const int g = t / 64, e = t - 64 * g, a = e / My, b = e % My, pe = a * NS + b;
+    const bool mlu = encl && d + 2 >= 11;
     T v = 0;
-    if (a < Mx && b < My) {
-      for (int q = g; q < 2 * MAXLOOP; q += 3) {
-        const int L = q / 2 + 1;
-        if ((q & 1) == 0) {
-          if (y + L > n - 1) continue;
-          T f = en[EN_BU + L] * clamp_p2<T>(Ed - E[d + L]);
-          v += f * e2<false, true>(S + (SO_BH3U + L - 1) * BLK, S + (SO_BC3U + L - 1) * BLK, a, b, p.Mp[y + L]);
+    if (g == 0) {  // QM2uu
+      if (mlu) v = sml * F2u * s3<true, false, true>(Xxl + XPU * BLK, gc, Xy + XUP * BLK, a, b, Mxl, Myr);
+      if (hasL) v += eb * F1u * s2<true, false>(Xxl + XUU * BLK, S + SO_H2UU * BLK, a, b, Mxl);
+    } else if (g == 1) {  // QM2up
+      if (mlu) v = sml * F2u * s3<true, false, true>(Xxl + XPU * BLK, gc, Xy + XPP * BLK, a, b, Mxl, Myr);
+      if (hasL) v += eb * F1u * s2<true, false>(Xxl + XUU * BLK, S + SO_H2UP * BLK, a, b, Mxl);
+    } else {  // QM2pu
+      if (mlu) v = sml * F2u * s3<true, false, true>(Xxl + XPP * BLK, gc, Xy + XUP * BLK, a, b, Mxl, Myr);
+      if (hasL) v += eb * F1u * s2<true, false>(Xxl + XUP * BLK, S + SO_H2UU * BLK, a, b, Mxl);
+      if (hasR) v += eb * F1u * s2<false, true>(S + SO_H2PU * BLK, Xy + XUU * BLK, a, b, Myr);
+    }
+    hM2[g * BLK + pe] = v;
+    T *dst = g == 0 ? p.hQM2uu : (g == 1 ? p.hQM2up : p.hQM2pu);
+    dst[c * BLK + pe] = v;
+  }
+  if (x == 0 && t >= 192 && t < 192 + M0 * My) {
+    const int e = t - 192, a = e / My, b = e % My, pe = a * NS + b;
+    T hu, hp;
+    if (d == n - 1) {
+      hu = hp = (T)(p.u0[a] / *p.Zm);
+    } else {
+      const T *hu1 = S + SO_HQ5U1 * BLK, *hg1 = S + SO_HGX1 * BLK;
+      const int Mn = MP(d + 1);
+      hu = F1u * (s2<false, true>(hu1, Xy + XUU * BLK, a, b, Mn) + s2<false, true>(hg1, Xy + XUP * BLK, a, b, Mn));
+      hp = F1u * (s2<false, true>(hu1, Xy + XPU * BLK, a, b, Mn) + s2<false, true>(hg1, Xy + XPP * BLK, a, b, Mn));
+    }
+    p.hQ5U[(size_t)d * BLK + pe] = hu;
+    p.hQ5P[(size_t)d * BLK + pe] = hp;
+    hQ5Uo[pe] = hu;
+    hQ5Po[pe] = hp;
+  }
+  __syncthreads();
+
+  // ---------------- B: hGx (exterior), hG, hQMpu, hQMpp
+  if (x == 0 && d >= 1 && t < M0 * My) {
+    const int a = t / My, b = t % My, pe = a * NS + b;
+    const T v = out_next(n, d) > 0 ? S[SO_HGXC * BLK + pe] : (T)0;
+    p.hGx[(size_t)d * BLK + pe] = v;
+    hGxo[pe] = v;
+  } else if (t >= 64 && t < 64 + MM && d >= 5) {
+    const int e = t - 64, pe = (e / My) * NS + (e % My);
+    const T v = out_nrow(n, x, d) > 0 ? S[SO_HGC * BLK + pe] : (T)0;
+    hGG[pe] = v;
+    p.hG[c * BLK + pe] = v;
+  } else if (t >= 128 && t < 128 + MM && d >= 5) {
+    const int e = t - 128, a = e / My, b = e % My, pe = a * NS + b;
+    T v = 0;
+    if (hasR)
+      v = F1u * (eb * s2<false, true>(S + SO_HMPU * BLK, Xy + XUU * BLK, a, b, Myr) +
+                 s2<false, true>(S + SO_HG1 * BLK, Xy + XUP * BLK, a, b, Myr));
+    hMPU[pe] = v;
+    p.hQMpu[c * BLK + pe] = v;
+  } else if (t >= 192 && t < 192 + MM && d >= 4) {
+    const int e = t - 192, a = e / My, b = e % My, pe = a * NS + b;
+    T v = 0;
+    if (hasR)
+      v = F1u * (eb * s2<false, true>(S + SO_HMPU * BLK, Xy + XPU * BLK, a, b, Myr) +
+                 s2<false, true>(S + SO_HG1 * BLK, Xy + XPP * BLK, a, b, Myr));
+    hMPP[pe] = v;
+    p.hQMpp[c * BLK + pe] = v;
+  }
+  __syncthreads();
+
+  // ---------------- C: hQM2pp (0..), hHB (64..)
+  if (t < MM && d >= 4) {
+    const int a = t / My, b = t % My, pe = a * NS + b;
+    T v = 0;
+    if (d >= 9) {
+      v = hMPP[pe];
+      if (encl && d + 2 >= 11) v += sml * F2u * s3<true, false, true>(Xxl + XPP * BLK, gc, Xy + XPP * BLK, a, b, Mxl, Myr);
+      if (hasR && d + 1 >= 10) v += eb * F1u * s2<false, true>(S + SO_H2PU * BLK, Xy + XPU * BLK, a, b, Myr);
+      if (hasL && d + 1 >= 10) v += eb * F1u * s2<true, false>(Xxl + XUP * BLK, S + SO_H2UP * BLK, a, b, Mxl);
+    }
+    hM2[3 * BLK + pe] = v;
+    p.hQM2pp[c * BLK + pe] = v;
+  } else if (t >= 64 && t < 64 + MM && d >= 2) {
+    const int e = t - 64, a = e / My, b = e % My, pe = a * NS + b;
+    T v = 0;
+    if (encl) v = F2u * s3<true, false, true>(S + SO_TXL * BLK, gc, S + SO_TY * BLK, a, b, Mxl, Myr);
+    hHB[pe] = v;
+    p.hHB[c * BLK + pe] = v;
+  }
+  __syncthreads();
+
+  // ---------------- D: hQB as a sum over its users (groups of threads)
+  const int GR = min(NT / MM, 16);  // groups for the reductions below
+  if (d >= 4) {
+    const int G = GR, g = t / MM, e = t % MM;
+    if (g < G) {
+      const int a = e / My, b = e % My, pe = a * NS + b;
+      T v = 0;
+      for (int k = g; k < 2 * MAXLOOP + 3; k += G) {
+        if (k < 2 * MAXLOOP) {
+          const int L = k / 2 + 1;
+          if ((k & 1) == 0) {
+            if (y + L > n - 1) continue;
+            const T f = wBuU[L];
+            v += f * s2<false, true>(S + (SO_BH3U + L - 1) * BLK, S + (SO_BC3U + L - 1) * BLK, a, b, MP(y + L));
+          } else {
+            if (x - L < 0) continue;
+            const T f = wBuU[L];
+            v += f * s2<true, false>(S + (SO_BC5U + L - 1) * BLK, S + (SO_BH5U + L - 1) * BLK, a, b, MP(x - L));
+          }
+        } else if (k == 2 * MAXLOOP) {
+          v += ec * hMPP[pe];
+          if (out_ncol(x, d) > 0) v += S[SO_HQC * BLK + pe];
+          if (x == 0) v += hQ5Po[pe];  // computed above in this kernel
+          else v += clamp_p2<T>(EA(x) + Ed - EA(y)) * s2<true, false>(S + SO_GX * BLK, S + SO_HQ5P * BLK, a, b, M0);
+        } else if (k == 2 * MAXLOOP + 1) {
+          if (!encl) continue;
+          // XI[x-1][y+1] = F (T_{x-1} QB T_y) o tm
+          const T *Txl = S + SO_TXL * BLK, *Ty = S + SO_TY * BLK, *hxi1 = S + SO_HXIE * BLK;
+          T s2v = 0;
+          for (int wv = 0; wv < Mxl; wv++) {
+            const T tl = Txl[wv * NS + a];
+            if (tl == (T)0) continue;
+            const int bw = BASE((x - 1), wv);
+            for (int z = 0; z < Myr; z++)
+              s2v += tl * hxi1[wv * NS + z] * en[EN_TM + BASE((y + 1), z) * 4 + bw] * Ty[b * NS + z];
+          }
+          v += F2u * s2v;
         } else {
-          if (x - L < 0) continue;
-          T f = en[EN_BU + L] * clamp_p2<T>(Ed - E[d + L]);
-          v += f * e2<true, false>(S + (SO_BC5U + L - 1) * BLK, S + (SO_BH5U + L - 1) * BLK, a, b, p.Mp[x - L]);
-        }
-      }
-      if (g == 0) {
-        v += ec * hMPP[e];
-        const int nq = out_ncol(x, d);
-        const int nr = out_nrow(n, x, d);
-        (void)nr;
-        const T *bp = ob.hq + (((size_t)slot * n + x) * ob.ncmax) * BLK + e;
-        for (int q = 0; q < nq; q++) v += bp[(size_t)q * BLK];
-        if (x == 0) v += p.hQ5P[(size_t)y * BLK + e];  // computed above in this kernel
-        else v += clamp_p2<T>(E[x] + Ed - E[y]) * e2<true, false>(S + SO_GX * BLK, S + SO_HQ5P * BLK, a, b, p.Mp[0]);
-      } else if (g == 1 && encl) {
-        // XI[x-1][y+1] = F (T_{x-1} QB T_y) o tm
-        const T *Txl = S + SO_TXL * BLK, *Ty = S + SO_TY * BLK, *hxi1 = S + SO_HXIE * BLK;
-        T s2 = 0;
-        for (int wv = 0; wv < Mxl; wv++) {
-          const T tl = Txl[wv * NS + a];
-          const int bw = base[(x - 1) * NS + wv];
-          for (int z = 0; z < Myr; z++)
-            s2 += tl * hxi1[wv * NS + z] * en[EN_TM + base[(y + 1) * NS + z] * 4 + bw] * Ty[b * NS + z];
-        }
-        v += F2u * s2;
-      } else if (g == 2 && encl) {
-        // stack of the enclosing pair (x-1, y+1)
-        const int pti = pair_type(base[x * NS + a], base[y * NS + b]);
-        if (pti >= 0) {
+          if (!encl) continue;
+          // stack of the enclosing pair (x-1, y+1)
+          const int pti = pair_type(BASE(x, a), BASE(y, b));
+          if (pti < 0) continue;
           const T *Txl = S + SO_TXL * BLK, *Ty = S + SO_TY * BLK;
-          T s2 = 0;
+          T s2v = 0;
           for (int a1 = 0; a1 < Mxl; a1++) {
             const T tl = Txl[a1 * NS + a];
-            const int ba = base[(x - 1) * NS + a1];
+            if (tl == (T)0) continue;
+            const int ba = BASE((x - 1), a1);
             for (int b1 = 0; b1 < Myr; b1++) {
-              const int pto = pair_type(ba, base[(y + 1) * NS + b1]);
-              if (pto < 0) continue;
-              s2 += tl * gc[a1 * NS + b1] * en[EN_STK + pto * 6 + pti] * Ty[b * NS + b1];
+              const int pto = pair_type(ba, BASE((y + 1), b1));
+              if (pto >= 0) s2v += tl * gc[a1 * NS + b1] * en[EN_STK + pto * 6 + pti] * Ty[b * NS + b1];
             }
           }
-          v += F2u * s2;
+          v += F2u * s2v;
         }
       }
+      RED[t] = v;
     }
-    ACC[g * BLK + e] = v;
   }
   __syncthreads();
   double psum = 0;
-  if (d >= 4 && t < BLK) {
-    const int a = t / NS, b = t % NS;
-    if (a < Mx && b < My) {
-      const T v = ACC[t] + ACC[BLK + t] + ACC[2 * BLK + t];
-      p.hQB[c * BLK + t] = v;
-      const T gq = pair_type(base[x * NS + a], base[y * NS + b]) >= 0 ? v : (T)0;
-      hQB[t] = gq;
-      p.hGc[c * BLK + t] = gq;
-      psum = (double)S[SO_QB * BLK + t] * (double)v;
-    }
+  if (d >= 4 && t < MM) {
+    const int a = t / My, b = t % My, pe = a * NS + b;
+    T v = 0;
+    for (int g = 0; g < GR; g++) v += RED[g * MM + t];
+    p.hQB[c * BLK + pe] = v;
+    const T gq = pair_type(BASE(x, a), BASE(y, b)) >= 0 ? v : (T)0;
+    hQB[pe] = gq;
+    p.hGc[c * BLK + pe] = gq;
+    psum = (double)S[SO_QB * BLK + pe] * (double)v;
   }
-  // ---------------- E: interior partial-sum adjoints (all threads over (L, entry))
+  // ---------------- E: interior partial-sum adjoints over (L, entry)
   if (d >= 6) {
     const int Lmax = min(MAXLOOP, d - 4);
-    const int nitem = (Lmax - 1) * BLK;
+    const int nitem = (Lmax - 1) * MM;
     const T *Txl = S + SO_TXL * BLK;
-    for (int it = t; it < nitem; it += blockDim.x) {
-      const int L = it / BLK + 2, e = it % BLK, a = e / NS, b = e % NS;
-      if (a >= Mx || b >= My) continue;
-      const int ey = (L == 2) ? Ed : E[d - L + 2];
-      T v = en[EN_IN + L] * clamp_p2<T>(ey - Ed) * en[EN_TM + base[x * NS + a] * 4 + base[y * NS + b]] * hHB[e];
-      if (hasL && L + 1 <= min(MAXLOOP, d + 1 - 4)) v += e2<true, false>(Txl, S + (SO_HYR + L - 2) * BLK, a, b, Mxl);
-      HY[(L - 2) * BLK + e] = v;
-      p.hYY[(((size_t)(d % YRING) * n + x) * NYY + (L - 2)) * BLK + e] = v;
+    for (int it = t; it < nitem; it += NT) {
+      const int L = it / MM + 2, e = it % MM, a = e / My, b = e % My, pe = a * NS + b;
+      T v = wIn[L] * en[EN_TM + BASE(x, a) * 4 + BASE(y, b)] * hHB[pe];
+      if (hasL && L + 1 <= min(MAXLOOP, d + 1 - 4)) v += s2<true, false>(Txl, S + (SO_HYR + L - 2) * BLK, a, b, Mxl);
+      HY[(L - 2) * BLK + pe] = v;
+      p.hYY[(((size_t)(d % YRING) * n + x) * NYY + (L - 2)) * BLK + pe] = v;
     }
   }
-  __syncthreads();
-  // block sum of the pair probability
   psum = warp_sum(psum);
   if (lane == 0) sps[w] = psum;
+  __syncthreads();
 
   // ---------------- F: scatters into shorter chains and XI (atomic)
   if (d >= 5) {
-    // bulges of HB[x][y]: hCH[y-L][y] += f QB[x][y-L]^T hHB ; hCH[x][x+L] += f hHB QB[x+L][y]^T
-    for (int it = t; it < 2 * MAXLOOP * BLK; it += blockDim.x) {
+    for (int it = t; it < 2 * MAXLOOP * BLK; it += NT) {
       const int q = it / BLK, e = it % BLK, L = q / 2 + 1;
       if (d - L < 4) continue;
-      const T f = en[EN_BU + L] * clamp_p2<T>(E[d - L] - Ed);
-      const int r = e / NS, s2 = e % NS;
       if ((q & 1) == 0) {
-        const int Ml = p.Mp[y - L];
-        if (r >= Ml || s2 >= My) continue;
-        const T v = f * e2<true, false>(S + (SO_BQ3 + L - 1) * BLK, hHB, r, s2, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, y - L, y) * BLK + e, v);
+        // HB += QB[x][y-L] CH[y-L][y]  ->  hCH[y-L][y] += f QB^T hHB
+        const int Mr = MP(y - L);
+        if (e >= Mr * My) continue;
+        const int r = e / My, s2i = e % My;
+        const T f = wBu[L];
+        const T v = f * s2<true, false>(S + (SO_BQ3 + L - 1) * BLK, hHB, r, s2i, Mx);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, y - L, y) * BLK + r * NS + s2i, v);
       } else {
-        const int Ml = p.Mp[x + L];
-        if (r >= Mx || s2 >= Ml) continue;
-        const T v = f * e2<false, true>(hHB, S + (SO_BQ5 + L - 1) * BLK, r, s2, My);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, x, x + L) * BLK + e, v);
+        // HB += CH[x][x+L] QB[x+L][y]  ->  hCH[x][x+L] += f hHB QB^T
+        const int Ms = MP(x + L);
+        if (e >= Mx * Ms) continue;
+        const int r = e / Ms, s2i = e % Ms;
+        const T f = wBu[L];
+        const T v = f * s2<false, true>(hHB, S + (SO_BQ5 + L - 1) * BLK, r, s2i, My);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, x, x + L) * BLK + r * NS + s2i, v);
       }
     }
   }
   if (d >= 6) {
-    // YY_L += XI[x][yl] CH[yl][y]: hXI[x][yl] += hYY CH^T ; hCH[yl][y] += XI^T hYY
     const int Lmax = min(MAXLOOP, d - 4);
-    for (int it = t; it < 2 * (Lmax - 1) * BLK; it += blockDim.x) {
-      const int q = it / BLK, e = it % BLK, L = q / 2 + 2, r = e / NS, s2 = e % NS;
+    for (int it = t; it < 2 * (Lmax - 1) * BLK; it += NT) {
+      const int q = it / BLK, e = it % BLK, L = q / 2 + 2;
       const int yl = y - L + 2;
       if (yl - x < 6) continue;
-      const int Ml = p.Mp[yl];
+      const int Ml = MP(yl);
       const T *hy = HY + (L - 2) * BLK;
       if ((q & 1) == 0) {
-        if (r >= Mx || s2 >= Ml) continue;
-        const T *ch = (L == 2) ? nullptr : S + (SO_CHL + L - 3) * BLK;
-        const T v = (L == 2) ? hy[e] : e2<false, true>(hy, ch, r, s2, My);
-        if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + e, v);
+        // YY_L += XI[x][yl] CH[yl][y]  ->  hXI[x][yl] += hYY CH^T
+        if (e >= Mx * Ml) continue;
+        const int r = e / Ml, s2i = e % Ml;
+        const T v = (L == 2) ? hy[r * NS + s2i] : s2<false, true>(hy, S + (SO_CHL + L - 3) * BLK, r, s2i, My);
+        if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + r * NS + s2i, v);
       } else {
-        if (L == 2) continue;
-        if (r >= Ml || s2 >= My) continue;
-        const T v = e2<true, false>(S + (SO_XIL + L - 3) * BLK, hy, r, s2, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, yl, y) * BLK + e, v);
+        // hCH[yl][y] += XI^T hYY (the L = 2 chain is the identity)
+        if (L == 2 || e >= Ml * My) continue;
+        const int r = e / My, s2i = e % My;
+        const T v = s2<true, false>(S + (SO_XIL + L - 3) * BLK, hy, r, s2i, Mx);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, yl, y) * BLK + r * NS + s2i, v);
       }
     }
   }
   // final chain adjoint of this cell (its scatters all came from longer intervals)
-  if (d >= 1 && t < BLK) {
-    const int a = t / NS, b = t % NS;
-    if (a < Mx && b < My) {
-      T v = S[SO_HCH * BLK + t];
-      if (d >= 2) v += p.eHL[d + 1] * clamp_p2<T>(-Ed) * en[EN_TM + base[x * NS + a] * 4 + base[y * NS + b]] * hHB[t];
-      if (hasL) v += e2<true, false>(S + SO_TXL * BLK, S + SO_HCHL * BLK, a, b, Mxl);
-      hCHf[t] = v;
-      p.hCH[c * BLK + t] = v;
-    }
+  if (d >= 1 && t >= 192 && t < 192 + MM) {
+    const int e = t - 192, a = e / My, b = e % My, pe = a * NS + b;
+    T v = S[SO_HCH * BLK + pe];
+    if (d >= 2) v += p.eHL[d + 1] * clamp_p2<T>(-Ed) * en[EN_TM + BASE(x, a) * 4 + BASE(y, b)] * hHB[pe];
+    if (hasL) v += s2<true, false>(S + SO_TXL * BLK, S + SO_HCHL * BLK, a, b, Mxl);
+    hCHf[pe] = v;
+    p.hCH[c * BLK + pe] = v;
   }
   // adjoint of XI[x][y] with its own L = 2 contribution, times the inner mismatch
-  if (d >= 6 && t >= BLK && t < 2 * BLK) {
-    const int e = t - BLK, a = e / NS, b = e % NS;
-    if (a < Mx && b < My) {
-      const T h = S[SO_HXI * BLK + e] + HY[e];
-      Hxi[e] = h * en[EN_TM + base[y * NS + b] * 4 + base[x * NS + a]];
-    }
+  if (d >= 6 && t >= 128 && t < 128 + MM) {
+    const int e = t - 128, a = e / My, b = e % My, pe = a * NS + b;
+    const T h = S[SO_HXI * BLK + pe] + HY[pe];
+    Hxi[pe] = h * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
   }
   __syncthreads();
   if (t == 0 && d >= 4) {
-    const double ps = sps[0] + sps[1] + sps[2] + sps[3];
+    double ps = 0;
+    for (int k = 0; k < NT / 32; k++) ps += sps[k];
     p.P[(size_t)x * n + y] = (float)ps;
     p.P[(size_t)y * n + x] = (float)ps;
   }
@@ -501,152 +543,153 @@ __global__ void __launch_bounds__(128) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   const T *Tx = S + SO_TX * BLK, *Ty1 = S + SO_TY1 * BLK;
   const T *hbi = S + SO_HBI * BLK, *qin = S + SO_QBI * BLK;
   const T *Xl = S + SO_XX * BLK, *Xr = S + SO_XY1 * BLK;
-  const T fq = clamp_p2<T>((d >= 2 ? E[d - 2] : 0) - Ed);
-  const int Mu = (d >= 1) ? p.Mp[x + 1] : 0, Mv = (d >= 1) ? p.Mp[y - 1] : 0;
-  if (bx && t < BLK) {
-    const int a = t / NS, u = t % NS;
-    if (a < Mx && u < Mu) {
-      T s = 0;
-      // QB[x][y] = f (T_x HB T_{y-1} + stack)
-      if (d >= 4) {
-        for (int b = 0; b < My; b++) {
-          const T g = hQB[a * NS + b];
-          if (g == (T)0) continue;
-          T tt = e2<false, false>(hbi, Ty1, u, b, Mv);
-          if (d >= 6) {
-            const int pto = pair_type(base[x * NS + a], base[y * NS + b]);
-            const int bu = base[(x + 1) * NS + u];
-            for (int b2 = 0; b2 < Mv; b2++) {
-              const int pti = pair_type(bu, base[(y - 1) * NS + b2]);
-              if (pti < 0 || pto < 0) continue;
-              tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
+  const T fq = clamp_p2<T>((d >= 2 ? EA(d - 2) : 0) - Ed);
+  if (bx) {
+    // dlogZ/dT_x: terms QB, XI, chain, and the interior partial sums L = 3..Lmax,
+    // split over groups of threads
+    const int MMx = Mx * M1, G2 = min(NT / MMx, 16), g = t / MMx, e = t % MMx;
+    const int Lmax = min(MAXLOOP, d - 4);
+    const int nterm = 3 + ((d >= 6) ? Lmax - 2 : 0);
+    if (g < G2) {
+      const int a = e / M1, u = e % M1;
+      T sacc = 0;
+      for (int k = g; k < nterm; k += G2) {
+        if (k == 0) {
+          if (d < 4) continue;
+          for (int b = 0; b < My; b++) {
+            const T gq = hQB[a * NS + b];
+            if (gq == (T)0) continue;
+            T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
+            if (d >= 6) {
+              const int pto = pair_type(BASE(x, a), BASE(y, b));
+              const int bu = BASE((x + 1), u);
+              for (int b2 = 0; b2 < Mv; b2++) {
+                const int pti = pair_type(bu, BASE((y - 1), b2));
+                if (pti < 0 || pto < 0) continue;
+                tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
+              }
             }
+            sacc += fq * gq * tt;
           }
-          s += fq * g * tt;
+        } else if (k == 1) {
+          if (d < 6) continue;
+          for (int z = 0; z < My; z++) sacc += fq * Hxi[a * NS + z] * s2<false, false>(qin, Ty1, u, z, Mv);
+        } else if (k == 2) {
+          if (d >= 1) sacc += s2<false, true>(hCHf, S + SO_CHN * BLK, a, u, My);
+        } else {
+          const int L = k;
+          sacc += s2<false, true>(HY + (L - 2) * BLK, S + (SO_YYP + L - 3) * BLK, a, u, My);
         }
       }
-      // XI[x][y] = f (T_x QB' T_{y-1}) o tm
-      if (d >= 6)
-        for (int z = 0; z < My; z++) s += fq * Hxi[a * NS + z] * e2<false, false>(qin, Ty1, u, z, Mv);
-      // YY_L[x][y] = T_x YY_{L-1}[x+1][y] + ...
-      if (d >= 6) {
-        const int Lmax = min(MAXLOOP, d - 4);
-        for (int L = 3; L <= Lmax; L++) s += e2<false, true>(HY + (L - 2) * BLK, S + (SO_YYP + L - 3) * BLK, a, u, My);
-      }
-      // CH[x][y] = T_x CH[x+1][y]
-      if (d >= 1) s += e2<false, true>(hCHf, S + SO_CHN * BLK, a, u, My);
-      atomicAdd(p.hT + (size_t)x * BLK + t, (double)s);
+      RED[t] = sacc;
+    }
+    __syncthreads();
+    if (t < MMx) {
+      T v = 0;
+      for (int gg = 0; gg < G2; gg++) v += RED[gg * MMx + t];
+      atomicAdd(p.hT + (size_t)x * BLK + (t / M1) * NS + (t % M1), (double)v);
     }
   }
-  if (by1 && t >= BLK && t < 2 * BLK) {
-    const int e = t - BLK, v2 = e / NS, b = e % NS;
-    if (v2 < Mv && b < My) {
-      T s = 0;
-      if (d >= 4) {
-        for (int a = 0; a < Mx; a++) {
-          const T g = hQB[a * NS + b];
-          if (g == (T)0) continue;
-          T tt = e2<false, false>(Tx, hbi, a, v2, Mu);
-          if (d >= 6) {
-            const int pto = pair_type(base[x * NS + a], base[y * NS + b]);
-            const int bv = base[(y - 1) * NS + v2];
-            for (int a2 = 0; a2 < Mu; a2++) {
-              const int pti = pair_type(base[(x + 1) * NS + a2], bv);
-              if (pti < 0 || pto < 0) continue;
-              tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
-            }
+  if (by1 && t >= 64 && t < 64 + Mv * My) {
+    const int e = t - 64, v2 = e / My, b = e % My;
+    T sacc = 0;
+    if (d >= 4) {
+      for (int a = 0; a < Mx; a++) {
+        const T g = hQB[a * NS + b];
+        if (g == (T)0) continue;
+        T tt = s2<false, false>(Tx, hbi, a, v2, M1);
+        if (d >= 6) {
+          const int pto = pair_type(BASE(x, a), BASE(y, b));
+          const int bv = BASE((y - 1), v2);
+          for (int a2 = 0; a2 < M1; a2++) {
+            const int pti = pair_type(BASE((x + 1), a2), bv);
+            if (pti < 0 || pto < 0) continue;
+            tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
           }
-          s += fq * g * tt;
         }
-      }
-      if (d >= 6)
-        for (int wv = 0; wv < Mx; wv++) s += fq * e2<false, false>(Tx, qin, wv, v2, Mu) * Hxi[wv * NS + b];
-      atomicAdd(p.hT + (size_t)(y - 1) * BLK + e, (double)s);
-    }
-  }
-  if (bx && t >= 2 * BLK && t < 3 * BLK) {
-    const int e = t - 2 * BLK, a = e / NS, u = e % NS;
-    if (a < Mx && u < Mu) {
-      double* hx = p.hX + (size_t)x * 4 * BLK;
-      if (d >= 11) {
-        const T *q2 = S + SO_Q2I * BLK;
-        T su = 0, sp = 0;
-        for (int b = 0; b < My; b++) {
-          const T g = hQB[a * NS + b];
-          if (g == (T)0) continue;
-          su += g * (e2<false, false>(q2, Xr + XUP * BLK, u, b, Mv) + e2<false, false>(q2 + BLK, Xr + XPP * BLK, u, b, Mv));
-          sp += g * (e2<false, false>(q2 + 2 * BLK, Xr + XUP * BLK, u, b, Mv) + e2<false, false>(q2 + 3 * BLK, Xr + XPP * BLK, u, b, Mv));
-        }
-        atomicAdd(hx + XPU * BLK + e, (double)(fq * sml * su));
-        atomicAdd(hx + XPP * BLK + e, (double)(fq * sml * sp));
-      }
-      if (d >= 10) {
-        const T F = clamp_p2<T>(E[d - 1] - Ed);
-        const T *r_up = S + SO_MR * BLK, *r_pp = S + (SO_MR + 1) * BLK, *r_uu = S + (SO_MR + 2) * BLK,
-                *r_pu = S + (SO_MR + 3) * BLK;
-        const T xuu = eb * (e2<false, true>(hM2 + BLK, r_up, a, u, My) + e2<false, true>(hM2, r_uu, a, u, My));
-        const T xup = eb * (e2<false, true>(hM2 + BLK, r_pp, a, u, My) + e2<false, true>(hM2, r_pu, a, u, My));
-        atomicAdd(hx + XUU * BLK + e, (double)(F * xuu));
-        atomicAdd(hx + XUP * BLK + e, (double)(F * xup));
+        sacc += fq * g * tt;
       }
     }
+    if (d >= 6)
+      for (int wv = 0; wv < Mx; wv++) sacc += fq * s2<false, false>(Tx, qin, wv, v2, M1) * Hxi[wv * NS + b];
+    atomicAdd(p.hT + (size_t)(y - 1) * BLK + v2 * NS + b, (double)sacc);
   }
-  if (by1 && t >= 3 * BLK) {
-    // threads 108..127 cover the entries of X_{y-1} with stride 20
+  if (bx && t >= 128 && t < 128 + Mx * M1) {
+    const int e = t - 128, a = e / M1, u = e % M1, pe = a * NS + u;
+    double *hx = p.hX + (size_t)x * 4 * BLK;
+    if (d >= 11) {
+      const T *q2 = S + SO_Q2I * BLK;
+      T su = 0, sp = 0;
+      for (int b = 0; b < My; b++) {
+        const T g = hQB[a * NS + b];
+        if (g == (T)0) continue;
+        su += g * (s2<false, false>(q2, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + BLK, Xr + XPP * BLK, u, b, Mv));
+        sp += g * (s2<false, false>(q2 + 2 * BLK, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + 3 * BLK, Xr + XPP * BLK, u, b, Mv));
+      }
+      atomicAdd(hx + XPU * BLK + pe, (double)(fq * sml * su));
+      atomicAdd(hx + XPP * BLK + pe, (double)(fq * sml * sp));
+    }
+    if (d >= 10) {
+      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T *r_up = S + SO_MR * BLK, *r_pp = S + (SO_MR + 1) * BLK, *r_uu = S + (SO_MR + 2) * BLK,
+              *r_pu = S + (SO_MR + 3) * BLK;
+      const T xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
+      const T xup = eb * (s2<false, true>(hM2 + BLK, r_pp, a, u, My) + s2<false, true>(hM2, r_pu, a, u, My));
+      atomicAdd(hx + XUU * BLK + pe, (double)(F * xuu));
+      atomicAdd(hx + XUP * BLK + pe, (double)(F * xup));
+    }
+  }
+  if (by1 && t >= 192 && t < 192 + Mv * My) {
+    const int e = t - 192, v2 = e / My, b = e % My, pe = v2 * NS + b;
     double *hx = p.hX + (size_t)(y - 1) * 4 * BLK;
-    for (int e = t - 3 * BLK; e < BLK; e += 128 - 3 * BLK) {
-      const int v2 = e / NS, b = e % NS;
-      if (v2 >= Mv || b >= My) continue;
-      double xpu = 0, xuu = 0, xpp = 0, xup = 0;
-      if (d >= 11) {
-        const T *q2 = S + SO_Q2I * BLK;
-        T su = 0, sp = 0;
-        for (int a = 0; a < Mx; a++) {
-          const T g = hQB[a * NS + b];
-          if (g == (T)0) continue;
-          su += g * (e2<false, false>(Xl + XPU * BLK, q2, a, v2, Mu) + e2<false, false>(Xl + XPP * BLK, q2 + 2 * BLK, a, v2, Mu));
-          sp += g * (e2<false, false>(Xl + XPU * BLK, q2 + BLK, a, v2, Mu) + e2<false, false>(Xl + XPP * BLK, q2 + 3 * BLK, a, v2, Mu));
-        }
-        xup += (double)(fq * sml * su);
-        xpp += (double)(fq * sml * sp);
+    double xpu = 0, xuu = 0, xpp = 0, xup = 0;
+    if (d >= 11) {
+      const T *q2 = S + SO_Q2I * BLK;
+      T su = 0, sp = 0;
+      for (int a = 0; a < Mx; a++) {
+        const T g = hQB[a * NS + b];
+        if (g == (T)0) continue;
+        su += g * (s2<false, false>(Xl + XPU * BLK, q2, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 2 * BLK, a, v2, M1));
+        sp += g * (s2<false, false>(Xl + XPU * BLK, q2 + BLK, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 3 * BLK, a, v2, M1));
       }
-      if (d >= 5) {
-        const T F = clamp_p2<T>(E[d - 1] - Ed);
-        const T *mpp = S + SO_ML * BLK, *mpu = S + (SO_ML + 1) * BLK, *q2pp = S + (SO_ML + 2) * BLK,
-                *q2pu = S + (SO_ML + 3) * BLK;
-        T a1 = eb * e2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * e2<true, false>(mpu, hMPU, v2, b, Mx);
-        T a3 = e2<true, false>(mpp, hGG, v2, b, Mx), a4 = e2<true, false>(mpu, hGG, v2, b, Mx);
-        if (d >= 10) {
-          a1 += eb * e2<true, false>(q2pp, hM2 + 2 * BLK, v2, b, Mx);
-          a2 += eb * e2<true, false>(q2pu, hM2 + 2 * BLK, v2, b, Mx);
-        }
-        xpu += (double)(F * a1);
-        xuu += (double)(F * a2);
-        xpp += (double)(F * a3);
-        xup += (double)(F * a4);
-      }
-      if (x == 0) {
-        // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
-        const T F = clamp_p2<T>(E[d - 1] - Ed);
-        const int M0 = p.Mp[0];
-        const T *q5u = p.Q5U + (size_t)(d - 1) * BLK, *q5p = p.Q5P + (size_t)(d - 1) * BLK;
-        const T *hu = p.hQ5U + (size_t)d * BLK, *hg = p.hGx + (size_t)d * BLK;
-        xuu += (double)(F * e2<true, false>(q5u, hu, v2, b, M0));
-        xpu += (double)(F * e2<true, false>(q5p, hu, v2, b, M0));
-        xup += (double)(F * e2<true, false>(q5u, hg, v2, b, M0));
-        xpp += (double)(F * e2<true, false>(q5p, hg, v2, b, M0));
-      }
-      atomicAdd(hx + XPU * BLK + e, xpu);
-      atomicAdd(hx + XUU * BLK + e, xuu);
-      atomicAdd(hx + XPP * BLK + e, xpp);
-      atomicAdd(hx + XUP * BLK + e, xup);
+      xup += (double)(fq * sml * su);
+      xpp += (double)(fq * sml * sp);
     }
+    if (d >= 5) {
+      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T *mpp = S + SO_ML * BLK, *mpu = S + (SO_ML + 1) * BLK, *q2pp = S + (SO_ML + 2) * BLK,
+              *q2pu = S + (SO_ML + 3) * BLK;
+      T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
+      T a3 = s2<true, false>(mpp, hGG, v2, b, Mx), a4 = s2<true, false>(mpu, hGG, v2, b, Mx);
+      if (d >= 10) {
+        a1 += eb * s2<true, false>(q2pp, hM2 + 2 * BLK, v2, b, Mx);
+        a2 += eb * s2<true, false>(q2pu, hM2 + 2 * BLK, v2, b, Mx);
+      }
+      xpu += (double)(F * a1);
+      xuu += (double)(F * a2);
+      xpp += (double)(F * a3);
+      xup += (double)(F * a4);
+    }
+    if (x == 0) {
+      // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
+      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T *q5u = S + SO_Q5UM * BLK, *q5p = S + SO_Q5PM * BLK;
+      const T *hu = hQ5Uo, *hg = hGxo;
+      xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));
+      xpu += (double)(F * s2<true, false>(q5p, hu, v2, b, M0));
+      xup += (double)(F * s2<true, false>(q5u, hg, v2, b, M0));
+      xpp += (double)(F * s2<true, false>(q5p, hg, v2, b, M0));
+    }
+    atomicAdd(hx + XPU * BLK + pe, xpu);
+    atomicAdd(hx + XUU * BLK + pe, xuu);
+    atomicAdd(hx + XPP * BLK + pe, xpp);
+    atomicAdd(hx + XUP * BLK + pe, xup);
   }
 }
 
 template <typename T>
 constexpr size_t out_light_smem() {
-  return (size_t)(SO_N + NYY + 15) * BLK * sizeof(T);
+  return ((size_t)(SO_N + NYY + 14) * BLK + NT) * sizeof(T);
 }
 
 }  // namespace cf

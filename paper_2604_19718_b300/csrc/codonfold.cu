@@ -245,11 +245,22 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
     CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
     CF_CUDA(p, cudaMemset(*q, 0, (size_t)n * BLK * sizeof(T)));
   }
-  t.bb.ncmax = std::max(1, std::max(nchunk_bif(n - 1), nchunk_ext(n - 1)));
-  CF_CUDA(p, dalloc(L, &t.bb.main, (size_t)BIFRING * n * t.bb.ncmax * BLK));
-  CF_CUDA(p, dalloc(L, &t.bb.ext, (size_t)BIFRING * t.bb.ncmax * BLK));
+  t.bb.ncmax = 1;
+  CF_CUDA(p, dalloc(L, &t.bb.main, (size_t)BIFRING * n * BLK));
+  CF_CUDA(p, dalloc(L, &t.bb.ext, (size_t)BIFRING * BLK));
   t.inside_alloc = true;
   return CF_OK;
+}
+
+// Scheduling priority of a kernel node: the light-kernel chain is the
+// critical path, the bifurcation kernels fill in behind it.
+cudaError_t set_priority(cudaGraphNode_t node, bool high) {
+  int lo = 0, hi = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e != cudaSuccess) return e;
+  cudaKernelNodeAttrValue v = {};
+  v.priority = high ? hi : lo;
+  return cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributePriority, &v);
 }
 
 // The inside pass as a CUDA graph: a chain of light kernels, one per
@@ -280,13 +291,13 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     int dd = d;
     void *args[] = {&dp, &bb, &dd};
     if (d >= 8) {
-      int items = (n - d) * nchunk_bif(d) + nchunk_ext(d);
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_in_bif<T>;
-      kp.gridDim = dim3((items + 3) / 4);
-      kp.blockDim = dim3(128);
+      kp.gridDim = dim3(n - d + 1);
+      kp.blockDim = dim3(256);
       kp.kernelParams = args;
       e = cudaGraphAddKernelNode(&k1[d], g, &k2[d - 4], 1, &kp);
+      if (e == cudaSuccess) e = set_priority(k1[d], false);
       nodes++;
     }
     if (e != cudaSuccess) break;
@@ -297,10 +308,11 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_in_light<T>;
     kp.gridDim = dim3(n - d);
-    kp.blockDim = dim3(128);
+    kp.blockDim = dim3(NT);
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
   }
   if (e == cudaSuccess) {
@@ -342,10 +354,9 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   }
   CF_CUDA(p, dalloc(L, &d.hT, (size_t)n * BLK));
   CF_CUDA(p, dalloc(L, &d.hX, (size_t)n * 4 * BLK));
-  t.ob.ncmax = (n + KCH - 1) / KCH + 2;
-  CF_CUDA(p, dalloc(L, &t.ob.hg, (size_t)BIFRING * n * t.ob.ncmax * BLK));
-  CF_CUDA(p, dalloc(L, &t.ob.hq, (size_t)BIFRING * n * t.ob.ncmax * BLK));
-  CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * t.ob.ncmax * BLK));
+  CF_CUDA(p, dalloc(L, &t.ob.hg, (size_t)BIFRING * n * BLK));
+  CF_CUDA(p, dalloc(L, &t.ob.hq, (size_t)BIFRING * n * BLK));
+  CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * BLK));
   t.outside_alloc = true;
   return CF_OK;
 }
@@ -390,10 +401,11 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     if (hasb) {
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_out_bif<T>;
-      kp.gridDim = dim3((out_cell_chunks(n, d) + 3) / 4, n - d + 1);
-      kp.blockDim = dim3(128);
+      kp.gridDim = dim3(n - d + 1);
+      kp.blockDim = dim3(256);
       kp.kernelParams = args;
       e = cudaGraphAddKernelNode(&k1[d], g, &k2[d + 4], 1, &kp);
+      if (e == cudaSuccess) e = set_priority(k1[d], false);
       nodes++;
       if (e != cudaSuccess) break;
     }
@@ -404,10 +416,11 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_out_light<T>;
     kp.gridDim = dim3(n - d);
-    kp.blockDim = dim3(128);
+    kp.blockDim = dim3(NT);
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
   }
   cudaGraphNode_t fin = nullptr;

@@ -99,6 +99,20 @@ cf_status cf_set_protein(cf_problem *prob, const char *aa, int m, const double *
                          const double *pair_bonus);
 
 /*
+ * Replace the soft constraints of the current protein (same meaning and layout
+ * of codon_logw and pair_bonus as in cf_set_protein; NULL = 0) without
+ * releasing its device tables: the transfer blocks T_p, X_p and residue 0's
+ * weights are rebuilt and copied over the old ones.  This is the per-step call
+ * of gradient-based weight optimisation (paper Section "Incorporating soft
+ * constraints"; the weights enter the tensor train of Eq. pair-tt).
+ * Synchronises the problem's stream first; invalidates earlier inside/outside
+ * results (cf_outside and cf_sample then return CF_ESTATE until cf_inside).
+ * Errors: CF_EINVAL (NULL problem, non-finite weight), CF_ESTATE (no protein
+ * set), CF_ECUDA.
+ */
+cf_status cf_set_weights(cf_problem *prob, const double *codon_logw, const double *pair_bonus);
+
+/*
  * Inside pass (paper Section "Free energy computation", Eq. amino-q): fills
  * the dynamic-programming tables over all intervals by anti-diagonal
  * wavefront on the device and returns log Z (natural log, Z summed over

@@ -37,6 +37,7 @@ def _load() -> ctypes.CDLL:
     lib.cf_problem_create.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.cf_problem_free.argtypes = [vp]
     lib.cf_set_protein.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp, dp]
+    lib.cf_set_weights.argtypes = [vp, dp, dp]
     lib.cf_inside.argtypes = [vp, ctypes.c_int, dp]
     lib.cf_outside.argtypes = [vp, fp, vp, vp]
     lib.cf_sample.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
@@ -45,7 +46,7 @@ def _load() -> ctypes.CDLL:
     lib.cf_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cf_problem_length.argtypes = [vp]
-    for name in ("cf_load_model", "cf_model_free", "cf_problem_create", "cf_problem_free", "cf_set_protein",
+    for name in ("cf_load_model", "cf_model_free", "cf_problem_create", "cf_problem_free", "cf_set_protein", "cf_set_weights",
                  "cf_inside", "cf_outside", "cf_sample", "cf_last_timing"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
@@ -98,6 +99,14 @@ def cf_set_protein(prob, aa: str, codon_logw=None, pair_bonus=None) -> None:
     pb = None if pair_bonus is None else np.ascontiguousarray(np.asarray(pair_bonus, dtype=np.float64).reshape(61, 61))
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib.cf_set_protein(prob, aa.encode(), m, None if lw is None else lw.ctypes.data_as(dp),
+                              None if pb is None else pb.ctypes.data_as(dp)), prob)
+
+
+def cf_set_weights(prob, m: int, codon_logw=None, pair_bonus=None) -> None:
+    lw = None if codon_logw is None else np.ascontiguousarray(np.asarray(codon_logw, dtype=np.float64).reshape(m, 6))
+    pb = None if pair_bonus is None else np.ascontiguousarray(np.asarray(pair_bonus, dtype=np.float64).reshape(61, 61))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib.cf_set_weights(prob, None if lw is None else lw.ctypes.data_as(dp),
                               None if pb is None else pb.ctypes.data_as(dp)), prob)
 
 
@@ -155,6 +164,10 @@ class CodonFold:
         cf_set_protein(self.prob, aa, codon_logw, pair_bonus)
         self.m = len(aa)
         self.n = 3 * self.m
+        return self
+
+    def set_weights(self, codon_logw=None, pair_bonus=None):
+        cf_set_weights(self.prob, self.m, codon_logw, pair_bonus)
         return self
 
     def inside(self, precision: int = CF_FP32_SCALED) -> float:

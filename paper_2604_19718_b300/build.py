@@ -1,7 +1,9 @@
 """Build the CUDA library in-tree for sm_103a (B300).
 
-``python -m paper_2604_19718_b300.build`` or ``build()`` compiles
-``csrc/codonfold.cu`` into ``_build/libcodonfold.so`` next to this file.
+``python paper_2604_19718_b300/build.py`` or ``build()`` compiles
+``csrc/codonfold.cu`` into ``_build/libcodonfold.so`` next to this file.  The
+module imports nothing from the package, so it can be loaded on its own
+before the library exists.
 """
 from __future__ import annotations
 

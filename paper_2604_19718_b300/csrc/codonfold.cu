@@ -554,6 +554,74 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
   return CF_OK;
 }
 
+// Host construction of the codon-pair tensor train along the backbone (Eq.
+// pair-tt): T_p is the identity inside a residue and e^{lw[r+1][b] + pb[a][b]}
+// across the boundary into residue r+1, each boundary block rescaled so that
+// its average row sum is one (the scale is undone in log Z); X_p adds the
+// dangle factors of the typed ports; u0 carries residue 0's weights.
+void build_transfers(cf_problem *p, const double *lw, const double *pb) {
+  const int n = p->n;
+  const double *en = p->model->en;
+  p->Tr.assign((size_t)n * BLK, 0.0);
+  p->X.assign((size_t)n * 4 * BLK, 0.0);
+  p->log_scale = 0;
+  for (int q = 0; q + 1 < n; q++) {
+    int Ma = p->M[q], Mb = p->M[q + 1];
+    double *T = &p->Tr[(size_t)q * BLK];
+    if (q % 3 != 2) {
+      for (int a = 0; a < Ma; a++) T[a * NS + a] = 1.0;
+    } else {
+      p->bnd[q] = 1;
+      int r1 = (q + 1) / 3;
+      double sum = 0;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) {
+          double w = lw ? lw[(size_t)r1 * 6 + b] : 0.0;
+          if (pb) w += pb[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]];
+          T[a * NS + b] = std::exp(w);
+          sum += T[a * NS + b];
+        }
+      // normalise the average row sum to one (exact rescale, undone in log Z)
+      double s = Ma / sum;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) T[a * NS + b] *= s;
+      p->log_scale += std::log(s);
+    }
+    for (int a = 0; a < Ma; a++)
+      for (int b = 0; b < Mb; b++) {
+        int x0 = p->base[(size_t)q * NS + a], y0 = p->base[(size_t)(q + 1) * NS + b];
+        double t = T[a * NS + b], d3 = en[EN_D3 + x0 * 4 + y0], d5 = en[EN_D5 + y0 * 4 + x0];
+        double *X = &p->X[(size_t)q * 4 * BLK];
+        X[XUU * BLK + a * NS + b] = t;
+        X[XUP * BLK + a * NS + b] = t * d5;
+        X[XPU * BLK + a * NS + b] = t * d3;
+        X[XPP * BLK + a * NS + b] = t * d3 * d5;
+      }
+  }
+  p->u0.assign(NS, 0.0);
+  for (int a = 0; a < p->M[0]; a++) p->u0[a] = std::exp(lw ? lw[a] : 0.0);
+}
+
+cf_status check_weights(cf_problem *p, int m, const double *lw, const double *pb) {
+  if (lw)
+    for (size_t k = 0; k < (size_t)m * 6; k++)
+      if (!std::isfinite(lw[k])) return fail(p, CF_EINVAL, "non-finite codon weight");
+  if (pb)
+    for (size_t k = 0; k < 61 * 61; k++)
+      if (!std::isfinite(pb[k])) return fail(p, CF_EINVAL, "non-finite pair bonus");
+  return CF_OK;
+}
+
+template <typename T>
+cf_status upload_transfers(cf_problem *p, PrecTables<T> &t) {
+  if (!t.inside_alloc) return CF_OK;  // uploaded when the tables are first made
+  std::vector<T> h(p->Tr.begin(), p->Tr.end());
+  CF_CUDA(p, cudaMemcpy((void *)t.dp.Tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  h.assign(p->X.begin(), p->X.end());
+  CF_CUDA(p, cudaMemcpy((void *)t.dp.X, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return CF_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
@@ -646,12 +714,7 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     if (!aa[r] || !q) return fail(p, CF_EINVAL, std::string("cf_set_protein: invalid amino acid at residue ") + std::to_string(r));
     res[r] = (int)(q - kAminoAcids);
   }
-  if (lw)
-    for (size_t k = 0; k < (size_t)m * 6; k++)
-      if (!std::isfinite(lw[k])) return fail(p, CF_EINVAL, "cf_set_protein: non-finite codon weight");
-  if (pb)
-    for (size_t k = 0; k < 61 * 61; k++)
-      if (!std::isfinite(pb[k])) return fail(p, CF_EINVAL, "cf_set_protein: non-finite pair bonus");
+  if (check_weights(p, m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_protein: " + p->err);
   CF_CUDA(p, cudaSetDevice(p->device));
   release_protein(p);
   const int n = 3 * m;
@@ -672,45 +735,7 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
       }
     }
   }
-  const double *en = p->model->en;
-  p->Tr.assign((size_t)n * BLK, 0.0);
-  p->X.assign((size_t)n * 4 * BLK, 0.0);
-  p->log_scale = 0;
-  for (int q = 0; q + 1 < n; q++) {
-    int Ma = p->M[q], Mb = p->M[q + 1];
-    double *T = &p->Tr[(size_t)q * BLK];
-    if (q % 3 != 2) {
-      for (int a = 0; a < Ma; a++) T[a * NS + a] = 1.0;
-    } else {
-      p->bnd[q] = 1;
-      int r1 = (q + 1) / 3;
-      double sum = 0;
-      for (int a = 0; a < Ma; a++)
-        for (int b = 0; b < Mb; b++) {
-          double w = lw ? lw[(size_t)r1 * 6 + b] : 0.0;
-          if (pb) w += pb[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]];
-          T[a * NS + b] = std::exp(w);
-          sum += T[a * NS + b];
-        }
-      // normalise the average row sum to one (exact rescale, undone in log Z)
-      double s = Ma / sum;
-      for (int a = 0; a < Ma; a++)
-        for (int b = 0; b < Mb; b++) T[a * NS + b] *= s;
-      p->log_scale += std::log(s);
-    }
-    for (int a = 0; a < Ma; a++)
-      for (int b = 0; b < Mb; b++) {
-        int x0 = p->base[(size_t)q * NS + a], y0 = p->base[(size_t)(q + 1) * NS + b];
-        double t = T[a * NS + b], d3 = en[EN_D3 + x0 * 4 + y0], d5 = en[EN_D5 + y0 * 4 + x0];
-        double *X = &p->X[(size_t)q * 4 * BLK];
-        X[XUU * BLK + a * NS + b] = t;
-        X[XUP * BLK + a * NS + b] = t * d5;
-        X[XPU * BLK + a * NS + b] = t * d3;
-        X[XPP * BLK + a * NS + b] = t * d3 * d5;
-      }
-  }
-  p->u0.assign(NS, 0.0);
-  for (int a = 0; a < p->M[0]; a++) p->u0[a] = std::exp(lw ? lw[a] : 0.0);
+  build_transfers(p, lw, pb);
   p->eHL.assign((size_t)n + 2, 0.0);
   const double kT = p->model->kT, H30 = p->model->params[36 + MAXLOOP];
   for (int L = 0; L < n + 2; L++) {
@@ -734,6 +759,21 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
   CF_CUDA(p, cudaMemcpy(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   CF_CUDA(p, cudaMemcpy(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice));
   CF_CUDA(p, cudaMemset(p->dE, 0, sizeof(int) * n));
+  return CF_OK;
+}
+
+cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
+  if (!p) return fail(p, CF_EINVAL, "cf_set_weights: NULL problem");
+  if (p->n == 0) return fail(p, CF_ESTATE, "cf_set_weights: no protein set");
+  if (check_weights(p, p->m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_weights: " + p->err);
+  CF_CUDA(p, cudaSetDevice(p->device));
+  CF_CUDA(p, cudaStreamSynchronize(p->stream));  // no pass may still read the old transfers
+  p->have_inside = false;
+  build_transfers(p, lw, pb);
+  cf_status s = upload_transfers(p, p->f32);
+  if (s == CF_OK) s = upload_transfers(p, p->f64);
+  if (s != CF_OK) return s;
+  CF_CUDA(p, cudaMemcpy(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice));
   return CF_OK;
 }
 

@@ -162,6 +162,31 @@ cf_status cf_last_timing(const cf_problem *prob, float *inside_ms, float *outsid
 int cf_problem_length(const cf_problem *prob);
 
 /*
+ * Batched partition functions of fixed sequences (one codon per residue, so a
+ * single state per position): the structure-only dynamic program of paper
+ * Section "Dynamic programs over structures for a given sequence" with the
+ * same nearest-neighbour loop energies as cf_inside.  Used to label windows of
+ * designed sequences with their ensemble free energy G = -RT ln Z.
+ *   bases:   concatenated base codes (A, C, G, U = 0..3), one byte each, host
+ *            or device memory; window w is bases[offsets[w] .. offsets[w+1]).
+ *   offsets: nwin + 1 int64, host or device, non-decreasing, offsets[0] >= 0;
+ *            window lengths 0 .. CF_WINDOW_MAX_N (a window shorter than 5 has
+ *            no pair and log Z = 0).
+ *   logz:    nwin doubles (host or device): natural log of Z of each window.
+ * Runs in FP32 with per-diagonal power-of-two exponents and a double exterior
+ * sum, one CTA per window.  Needs only the problem's model, device and stream
+ * (no protein); scratch is owned by the problem and reused across calls.
+ * Errors: CF_EINVAL (NULL argument, nwin < 0, decreasing offsets, window too
+ * long, base code > 3), CF_ENUMERIC, CF_ENOMEM, CF_ECUDA.
+ */
+#define CF_WINDOW_MAX_N 1024
+cf_status cf_window_logz(cf_problem *prob, const uint8_t *bases, const int64_t *offsets, int nwin,
+                         double *logz);
+
+/* Device time in milliseconds of the last cf_window_logz kernel. */
+float cf_window_last_ms(const cf_problem *prob);
+
+/*
  * cf_sample_noalloc -- the sampler of cf_sample for callers that cannot
  * allocate device memory.  (The paper has no counterpart: this is a library
  * service, not part of the method.)

@@ -46,6 +46,10 @@ def _load() -> ctypes.CDLL:
     lib.cf_last_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.cf_problem_length.argtypes = [vp]
+    lib.cf_window_logz.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    lib.cf_window_logz.restype = ctypes.c_int
+    lib.cf_window_last_ms.argtypes = [vp]
+    lib.cf_window_last_ms.restype = ctypes.c_float
     for name in ("cf_load_model", "cf_model_free", "cf_problem_create", "cf_problem_free", "cf_set_protein", "cf_set_weights",
                  "cf_inside", "cf_outside", "cf_sample", "cf_last_timing"):
         getattr(lib, name).restype = ctypes.c_int
@@ -133,6 +137,17 @@ def cf_last_timing(prob):
 
 def cf_problem_length(prob) -> int:
     return int(lib.cf_problem_length(prob))
+
+
+def cf_window_logz(prob, bases, offsets, logz) -> None:
+    """Batched fixed-sequence log Z: bases uint8 (host array or device
+    tensor), offsets int64 (nwin + 1), logz float64 (nwin), filled in place."""
+    nwin = len(offsets) - 1
+    _check(lib.cf_window_logz(prob, _ptr(bases), _ptr(offsets), int(nwin), _ptr(logz)), prob)
+
+
+def cf_window_last_ms(prob) -> float:
+    return float(lib.cf_window_last_ms(prob))
 
 
 def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:

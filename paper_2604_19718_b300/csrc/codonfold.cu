@@ -24,6 +24,7 @@
 #include "cf_outside.cuh"
 #include "cf_outside2.cuh"
 #include "cf_sample.cuh"
+#include "cf_window.cuh"
 
 using namespace cf;
 
@@ -140,6 +141,17 @@ struct cf_problem {
   size_t smp_cap = 0;
   int2 *smp_stack = nullptr;
   int *smp_state = nullptr, *smp_cid = nullptr, *smp_err = nullptr;
+  // batched window DP: energy tables (once) and buffers grown on demand
+  std::vector<void *> win_allocs, win_buf_allocs;
+  float *win_en = nullptr, *win_ehl = nullptr;
+  int *win_err = nullptr;
+  float *win_scratch = nullptr;
+  size_t win_scratch_cap = 0;
+  uint8_t *win_bases = nullptr;
+  int64_t *win_off = nullptr;
+  double *win_logz = nullptr;
+  size_t win_bases_cap = 0, win_nwin_cap = 0;
+  float t_win = 0;
 };
 
 namespace {
@@ -622,6 +634,98 @@ cf_status upload_transfers(cf_problem *p, PrecTables<T> &t) {
   return CF_OK;
 }
 
+// ---- batched fixed-sequence windows
+
+cf_status window_tables(cf_problem *p) {
+  if (p->win_en) return CF_OK;
+  std::vector<float> en(p->model->en, p->model->en + EN_N), ehl(WMAXN + 2);
+  const double kT = p->model->kT, H30 = p->model->params[36 + MAXLOOP];
+  for (int L = 0; L < WMAXN + 2; L++) {
+    double e = (L <= MAXLOOP) ? p->model->params[36 + L] : H30 + 1.07856 * std::log((double)L / MAXLOOP);
+    ehl[L] = (float)std::exp(-e / kT);
+  }
+  CF_CUDA(p, dalloc(p->win_allocs, &p->win_en, (size_t)EN_N));
+  CF_CUDA(p, dalloc(p->win_allocs, &p->win_ehl, (size_t)WMAXN + 2));
+  CF_CUDA(p, dalloc(p->win_allocs, &p->win_err, (size_t)1));
+  CF_CUDA(p, cudaMemcpy(p->win_en, en.data(), sizeof(float) * EN_N, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpy(p->win_ehl, ehl.data(), sizeof(float) * ehl.size(), cudaMemcpyHostToDevice));
+  return CF_OK;
+}
+
+cf_status run_windows(cf_problem *p, const uint8_t *bases, const int64_t *offsets, int nwin, double *logz) {
+  cf_status s = window_tables(p);
+  if (s != CF_OK) return s;
+  cudaStream_t st = p->stream;
+  const bool off_dev = is_device_ptr(offsets), bases_dev = is_device_ptr(bases), out_dev = is_device_ptr(logz);
+  std::vector<int64_t> off((size_t)nwin + 1);
+  if (off_dev) {
+    CF_CUDA(p, cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, st));
+    CF_CUDA(p, cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(off.data(), offsets, sizeof(int64_t) * off.size());
+  }
+  int nmax = 0;
+  if (off[0] < 0) return fail(p, CF_EINVAL, "cf_window_logz: offsets[0] < 0");
+  for (int w = 0; w < nwin; w++) {
+    const int64_t len = off[w + 1] - off[w];
+    if (len < 0) return fail(p, CF_EINVAL, "cf_window_logz: offsets must not decrease");
+    if (len > WMAXN)
+      return fail(p, CF_EINVAL, "cf_window_logz: window " + std::to_string(w) + " longer than CF_WINDOW_MAX_N");
+    nmax = std::max(nmax, (int)len);
+  }
+  const size_t total = (size_t)off[nwin];
+  int dev_sms = 148, per_sm = 1;
+  CF_CUDA(p, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->device));
+  CF_CUDA(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_window, WT, 0));
+  const int grid = std::max(1, std::min(nwin, dev_sms * std::max(per_sm, 1)));
+  const size_t stride = (3 * ncells(nmax) + 63) / 64 * 64;
+  // buffers grow monotonically and are reused by later calls
+  if (p->win_scratch_cap < stride * grid || (!bases_dev && p->win_bases_cap < total) || p->win_nwin_cap < (size_t)nwin + 1) {
+    CF_CUDA(p, cudaStreamSynchronize(st));
+    free_list(p->win_buf_allocs);
+    p->win_scratch_cap = std::max(p->win_scratch_cap, stride * grid);
+    p->win_bases_cap = std::max(p->win_bases_cap, bases_dev ? (size_t)16 : std::max(total, (size_t)16));
+    p->win_nwin_cap = std::max(p->win_nwin_cap, (size_t)nwin + 1);
+    CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_scratch, p->win_scratch_cap));
+    CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_bases, p->win_bases_cap));
+    CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_off, p->win_nwin_cap));
+    CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_logz, p->win_nwin_cap));
+  }
+  WinArgs a;
+  a.bases = bases;
+  if (!bases_dev) {
+    CF_CUDA(p, cudaMemcpyAsync(p->win_bases, bases, total, cudaMemcpyHostToDevice, st));
+    a.bases = p->win_bases;
+  }
+  a.off = offsets;
+  if (!off_dev) {
+    CF_CUDA(p, cudaMemcpyAsync(p->win_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st));
+    a.off = p->win_off;
+  }
+  a.nwin = nwin;
+  a.en = p->win_en;
+  a.eHL = p->win_ehl;
+  a.log2eb = (float)std::log2(p->model->en[EN_EB]);
+  a.scratch = p->win_scratch;
+  a.stride = stride;
+  a.logz = out_dev ? logz : p->win_logz;
+  a.err = p->win_err;
+  CF_CUDA(p, cudaMemsetAsync(p->win_err, 0, sizeof(int), st));
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  k_window<<<grid, WT, 0, st>>>(a);
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaEventRecord(p->ev[1], st));
+  if (!out_dev)
+    CF_CUDA(p, cudaMemcpyAsync(logz, p->win_logz, sizeof(double) * nwin, cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&err, p->win_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&p->t_win, p->ev[0], p->ev[1]));
+  if (err & 1) return fail(p, CF_EINVAL, "cf_window_logz: base code outside 0..3");
+  if (err & 2) return fail(p, CF_ENUMERIC, "cf_window_logz: non-finite table entry after scaling");
+  return CF_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
@@ -698,6 +802,8 @@ cf_status cf_problem_free(cf_problem *p) {
   if (!p) return CF_OK;
   cudaSetDevice(p->device);
   release_protein(p);
+  free_list(p->win_allocs);
+  free_list(p->win_buf_allocs);
   for (auto &ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   delete p;
@@ -829,6 +935,17 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
   CF_CUDA(p, cudaStreamSynchronize(st));
   return CF_OK;
 }
+
+cf_status cf_window_logz(cf_problem *p, const uint8_t *bases, const int64_t *offsets, int nwin, double *logz) {
+  if (!p) return fail(p, CF_EINVAL, "cf_window_logz: NULL problem");
+  if (nwin < 0) return fail(p, CF_EINVAL, "cf_window_logz: nwin < 0");
+  if (nwin == 0) return CF_OK;
+  if (!bases || !offsets || !logz) return fail(p, CF_EINVAL, "cf_window_logz: NULL argument");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  return run_windows(p, bases, offsets, nwin, logz);
+}
+
+float cf_window_last_ms(const cf_problem *p) { return p ? p->t_win : 0.f; }
 
 cf_status cf_last_timing(const cf_problem *p, float *inside_ms, float *outside_ms, int *inside_launches,
                          int *outside_launches) {

@@ -102,6 +102,57 @@ def workload(name: str):
     raise KeyError(name)
 
 
+# Standard genetic code, codons in lexicographic order over A, C, G, U
+# (AAA, AAC, ..., UUU); '*' marks the three stop codons.
+GENETIC_CODE = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF"
+
+
+def codon_table():
+    """Per amino acid (ARNDCQEGHILKMFPSTWYV order), its sense codons as base
+    triples (0..3), in codon order."""
+    out = []
+    for a in AMINO_ACIDS:
+        out.append([(c >> 4 & 3, c >> 2 & 3, c & 3) for c in range(64) if GENETIC_CODE[c] == a])
+    return out
+
+
+def windows(nwin: int, seed: int = 3):
+    """Windows of designed sequences: per window a random protein of
+    U{100..400} residues with Dirichlet(1) composition, codons uniform per
+    residue, a window length U{60..240} nt rounded down to whole codons and a
+    start codon uniform over the protein.  Only the window's own residues are
+    drawn (residues are i.i.d. given the composition, so the distribution is
+    that of cutting the full protein).
+
+    Returns (residues, slots, bases, offsets): per window the amino-acid
+    indices and codon slots (index into the residue's codon list), and all
+    windows' bases concatenated (uint8) with int64 offsets."""
+    rng = np.random.default_rng(seed)
+    plen = rng.integers(100, 401, nwin)
+    freqs = rng.dirichlet(np.ones(20), nwin)
+    wcod = rng.integers(60, 241, nwin) // 3
+    start = (rng.random(nwin) * (plen - wcod + 1)).astype(np.int64)
+    u_res = rng.random((nwin, 80))
+    u_cod = rng.random((nwin, 80))
+    table = codon_table()
+    ncod = np.array([len(c) for c in table])
+    cum = np.cumsum(freqs, axis=1)
+    res = np.minimum((u_res[:, :, None] > cum[:, None, :]).sum(axis=2), 19)
+    slots = np.minimum((u_cod * ncod[res]).astype(np.int64), ncod[res] - 1)
+    flat = np.array([b for cods in table for c in cods for b in c], dtype=np.uint8).reshape(-1, 3)
+    first = np.concatenate([[0], np.cumsum(ncod)[:-1]])
+    offsets = np.concatenate([[0], np.cumsum(3 * wcod)]).astype(np.int64)
+    bases = np.empty(offsets[-1], dtype=np.uint8)
+    rl, sl = [], []
+    for w in range(nwin):
+        r, s_ = res[w, :wcod[w]], slots[w, :wcod[w]]
+        bases[offsets[w]:offsets[w + 1]] = flat[first[r] + s_].ravel()
+        rl.append(r.astype(np.int32))
+        sl.append(s_.astype(np.int32))
+    del start  # the start fixes where the window sits in its protein, not its content
+    return rl, sl, bases, offsets
+
+
 def ascent_targets(m: int, seed: int = 3) -> np.ndarray:
     """Independent N(0,1) logits per (residue, slot) for frequency targets."""
     return np.random.default_rng(seed).normal(0.0, 1.0, (m, 6))

@@ -153,6 +153,24 @@ def windows(nwin: int, seed: int = 3):
     return rl, sl, bases, offsets
 
 
+SURROGATE_SHAPES = [(64, 4, 5), (64,), (64, 64, 5), (64,), (64, 64, 5), (64,), (64, 64, 5), (64,), (64,), (1,)]
+
+
+def surrogate_init(seed: int = 0) -> np.ndarray:
+    """Initial surrogate parameters in flat order (W1, b1, .., W4, b4, wh, bh):
+    conv weights ~ N(0, 2 / fan_in), head weights ~ N(0, 1/64), biases 0."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in SURROGATE_SHAPES:
+        if len(s) == 3:
+            out.append(rng.normal(0.0, np.sqrt(2.0 / (s[1] * s[2])), s).ravel())
+        elif s == (64,) and len(out) == 8:
+            out.append(rng.normal(0.0, 1.0 / 8.0, s))
+        else:
+            out.append(np.zeros(s))
+    return np.concatenate(out)
+
+
 def ascent_targets(m: int, seed: int = 3) -> np.ndarray:
     """Independent N(0,1) logits per (residue, slot) for frequency targets."""
     return np.random.default_rng(seed).normal(0.0, 1.0, (m, 6))

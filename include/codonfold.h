@@ -187,6 +187,45 @@ cf_status cf_window_logz(cf_problem *prob, const uint8_t *bases, const int64_t *
 float cf_window_last_ms(const cf_problem *prob);
 
 /*
+ * Learned window free-energy surrogate (the paper has no counterpart: it
+ * scores every candidate exactly).  A 1-D convolutional network predicts the
+ * ensemble free energy G (kcal/mol) of a window of bases; it is trained on
+ * windows labelled by cf_window_logz (G = -RT ln Z) and used to pre-screen
+ * candidate codon choices before the exact DP re-scores the best of them.
+ *   h0 = one-hot bases; h_l = relu(b_l + W_l * h_{l-1}), l = 1..4, 64
+ *   channels, 5 taps, zero padding; g = mean over positions of wh . h4 + bh;
+ *   prediction n g.  Loss (1/B) sum (g - G/n)^2, Adam (0.9, 0.999, 1e-8).
+ * Parameters: CF_SURROGATE_NPARAMS floats in the order W1 [64][4][5], b1 [64],
+ * W2 [64][64][5], b2, W3, b3, W4, b4, wh [64], bh [1].  Convolution weights
+ * are applied as BF16 (rounded from the FP32 masters after every update),
+ * accumulation is FP32.  Windows: bases as in cf_window_logz, lengths
+ * 0..CF_SURROGATE_MAX_LEN.  All buffers may be host or device memory.  Work
+ * is issued on `stream`; each call returns after its results are written.
+ * Errors: CF_EINVAL (NULL argument, window too long, batch larger than
+ * max_batch in training calls, lr <= 0), CF_ENOMEM, CF_ECUDA; the message is
+ * read with cf_last_error(NULL).
+ */
+#define CF_SURROGATE_NPARAMS 63041
+#define CF_SURROGATE_MAX_LEN 256
+typedef struct cf_surrogate cf_surrogate;
+cf_status cf_surrogate_create(int device, void *stream, int max_batch, cf_surrogate **out);
+cf_status cf_surrogate_free(cf_surrogate *sur);
+/* Replace the parameters (and reset the optimiser state). */
+cf_status cf_surrogate_set_params(cf_surrogate *sur, const float *params);
+cf_status cf_surrogate_get_params(const cf_surrogate *sur, float *params);
+/* Predicted G of nwin windows (any nwin; processed max_batch at a time). */
+cf_status cf_surrogate_predict(cf_surrogate *sur, const uint8_t *bases, const int64_t *offsets, int nwin,
+                               float *G_out);
+/* Loss and its gradient (CF_SURROGATE_NPARAMS floats) on one batch, no update. */
+cf_status cf_surrogate_grad(cf_surrogate *sur, const uint8_t *bases, const int64_t *offsets, int nwin,
+                            const float *G_target, float *loss_out, float *grad_out);
+/* One Adam step with learning rate lr on one batch; loss_out may be NULL. */
+cf_status cf_surrogate_train_step(cf_surrogate *sur, const uint8_t *bases, const int64_t *offsets, int nwin,
+                                  const float *G_target, float lr, float *loss_out);
+/* Device time in milliseconds of the last predict or train step. */
+float cf_surrogate_last_ms(const cf_surrogate *sur);
+
+/*
  * cf_sample_noalloc -- the sampler of cf_sample for callers that cannot
  * allocate device memory.  (The paper has no counterpart: this is a library
  * service, not part of the method.)

@@ -50,6 +50,18 @@ def _load() -> ctypes.CDLL:
     lib.cf_window_logz.restype = ctypes.c_int
     lib.cf_window_last_ms.argtypes = [vp]
     lib.cf_window_last_ms.restype = ctypes.c_float
+    lib.cf_surrogate_create.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.cf_surrogate_free.argtypes = [vp]
+    lib.cf_surrogate_set_params.argtypes = [vp, vp]
+    lib.cf_surrogate_get_params.argtypes = [vp, vp]
+    lib.cf_surrogate_predict.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    lib.cf_surrogate_grad.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp]
+    lib.cf_surrogate_train_step.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_float, vp]
+    lib.cf_surrogate_last_ms.argtypes = [vp]
+    lib.cf_surrogate_last_ms.restype = ctypes.c_float
+    for name in ("cf_surrogate_create", "cf_surrogate_free", "cf_surrogate_set_params", "cf_surrogate_get_params",
+                 "cf_surrogate_predict", "cf_surrogate_grad", "cf_surrogate_train_step"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("cf_load_model", "cf_model_free", "cf_problem_create", "cf_problem_free", "cf_set_protein", "cf_set_weights",
                  "cf_inside", "cf_outside", "cf_sample", "cf_last_timing"):
         getattr(lib, name).restype = ctypes.c_int
@@ -150,6 +162,46 @@ def cf_window_last_ms(prob) -> float:
     return float(lib.cf_window_last_ms(prob))
 
 
+SURROGATE_NPARAMS = 63041
+SURROGATE_MAX_LEN = 256
+
+
+def cf_surrogate_create(device: int = 0, stream: int = 0, max_batch: int = 1024):
+    h = ctypes.c_void_p()
+    _check(lib.cf_surrogate_create(int(device), ctypes.c_void_p(stream), int(max_batch), ctypes.byref(h)))
+    return h
+
+
+def cf_surrogate_free(sur) -> None:
+    lib.cf_surrogate_free(sur)
+
+
+def cf_surrogate_set_params(sur, params) -> None:
+    _check(lib.cf_surrogate_set_params(sur, _ptr(params)))
+
+
+def cf_surrogate_get_params(sur, params) -> None:
+    _check(lib.cf_surrogate_get_params(sur, _ptr(params)))
+
+
+def cf_surrogate_predict(sur, bases, offsets, G_out) -> None:
+    _check(lib.cf_surrogate_predict(sur, _ptr(bases), _ptr(offsets), len(offsets) - 1, _ptr(G_out)))
+
+
+def cf_surrogate_grad(sur, bases, offsets, G_target, loss_out, grad_out) -> None:
+    _check(lib.cf_surrogate_grad(sur, _ptr(bases), _ptr(offsets), len(offsets) - 1, _ptr(G_target),
+                                 _ptr(loss_out), _ptr(grad_out)))
+
+
+def cf_surrogate_train_step(sur, bases, offsets, G_target, lr: float, loss_out=None) -> None:
+    _check(lib.cf_surrogate_train_step(sur, _ptr(bases), _ptr(offsets), len(offsets) - 1, _ptr(G_target),
+                                       ctypes.c_float(lr), _ptr(loss_out)))
+
+
+def cf_surrogate_last_ms(sur) -> float:
+    return float(lib.cf_surrogate_last_ms(sur))
+
+
 def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:
     """Sampler for callers that cannot allocate device memory: outputs must be
     device tensors; scratch comes from the library's static device array."""
@@ -163,6 +215,55 @@ def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:
 
 def to_letters(residues) -> str:
     return "".join(AMINO_ACIDS[int(r)] for r in residues)
+
+
+class Surrogate:
+    """The window free-energy surrogate on one device (numpy conveniences)."""
+
+    def __init__(self, params, device: int = 0, stream: int = 0, max_batch: int = 1024):
+        self.h = cf_surrogate_create(device, stream, max_batch)
+        self.max_batch = max_batch
+        self.set_params(params)
+
+    def set_params(self, params):
+        cf_surrogate_set_params(self.h, np.ascontiguousarray(params, dtype=np.float32))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(SURROGATE_NPARAMS, dtype=np.float32)
+        cf_surrogate_get_params(self.h, out)
+        return out
+
+    def predict(self, bases, offsets) -> np.ndarray:
+        out = np.zeros(len(offsets) - 1, dtype=np.float32)
+        cf_surrogate_predict(self.h, np.ascontiguousarray(bases, dtype=np.uint8),
+                             np.ascontiguousarray(offsets, dtype=np.int64), out)
+        return out
+
+    def grad(self, bases, offsets, G):
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(SURROGATE_NPARAMS, dtype=np.float32)
+        cf_surrogate_grad(self.h, np.ascontiguousarray(bases, dtype=np.uint8),
+                          np.ascontiguousarray(offsets, dtype=np.int64),
+                          np.ascontiguousarray(G, dtype=np.float32), loss, g)
+        return float(loss[0]), g
+
+    def train_step(self, bases, offsets, G, lr: float) -> float:
+        loss = np.zeros(1, dtype=np.float32)
+        cf_surrogate_train_step(self.h, np.ascontiguousarray(bases, dtype=np.uint8),
+                                np.ascontiguousarray(offsets, dtype=np.int64),
+                                np.ascontiguousarray(G, dtype=np.float32), lr, loss)
+        return float(loss[0])
+
+    def close(self):
+        if self.h:
+            cf_surrogate_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class CodonFold:

@@ -1,7 +1,7 @@
 """Build the CUDA library in-tree for sm_103a (B300).
 
 ``python paper_2604_19718_b300/build.py`` or ``build()`` compiles
-``csrc/codonfold.cu`` into ``_build/libcodonfold.so`` next to this file.  The
+``csrc/codonfold.cu`` and ``csrc/surrogate.cu`` into ``_build/libcodonfold.so`` next to this file.  The
 module imports nothing from the package, so it can be loaded on its own
 before the library exists.
 """
@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     OUT.mkdir(exist_ok=True)
     tmp = OUT / f"libcodonfold.{os.getpid()}.so"
     cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-o", str(tmp), str(SRC / "codonfold.cu")]
+           "-o", str(tmp), str(SRC / "codonfold.cu"), str(SRC / "surrogate.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)

@@ -728,6 +728,11 @@ cf_status run_windows(cf_problem *p, const uint8_t *bases, const int64_t *offset
 
 }  // namespace
 
+namespace cf {
+// error text for calls without a problem handle (read by cf_last_error(NULL))
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace cf
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {

@@ -187,7 +187,7 @@ __device__ __forceinline__ const T *in_slot_src2(const DP<T> &p, const BifBuf<T>
 // Thread mapping: the M_x*M_y live entries of a block are numbered compactly
 // (e = a*M_y + b); work lists over (task, entry) are split into NT/(M_x*M_y)
 // groups so that small codon-state counts keep all threads busy.
-constexpr int NT = 256;
+constexpr int NT = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   __syncthreads();
 
   // ---- P2: interior partial sums and bulges, split over groups -> HB
-  const int GR = min(NT / MM, 16);  // groups for the reductions below
+  const int GR = min(NT / MM, 32);  // groups for the reductions below
   if (d >= 2) {
     const int G = GR, g = t / MM, e = t % MM;
     if (g < G) {

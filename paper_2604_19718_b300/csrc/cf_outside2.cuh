@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
   __syncthreads();
 
   // ---------------- D: hQB as a sum over its users (groups of threads)
-  const int GR = min(NT / MM, 16);  // groups for the reductions below
+  const int GR = min(NT / MM, 32);  // groups for the reductions below
   if (d >= 4) {
     const int G = GR, g = t / MM, e = t % MM;
     if (g < G) {

@@ -41,14 +41,13 @@ struct BifBuf {
 // sum); warp w takes the chunks w, w+8, ... of 32 split points, lanes over the
 // split point; per-lane sums are reduced once per warp, then across warps.
 template <typename T>
-__global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
-  __shared__ T red[8][BLK];
+__device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int cb, T (*red)[BLK]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = p.n;
   const int Eref = p.E[d - 4];
   const int slot = d % BIFRING;
-  const bool ext = blockIdx.x == (unsigned)(n - d);
-  const int x = ext ? 0 : blockIdx.x, y = x + d;
+  const bool ext = cb == n - d;
+  const int x = ext ? 0 : cb, y = x + d;
   const int Ma = p.Mp[x], Mb = p.Mp[y];
   T acc[BLK];
   zero_block(acc);
@@ -88,6 +87,18 @@ __global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
     for (int k = 0; k < 8; k++) v += red[k][e];
     T *dst = ext ? bb.ext + (size_t)slot * BLK : bb.main + ((size_t)slot * n + x) * BLK;
     dst[e] = v;
+  }
+}
+
+// Grid-stride over the n-d cells and the exterior: launched with fewer CTAs
+// than cells, so that the light kernels of the critical path always find
+// room on the SMs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
+  __shared__ T red[8][BLK];
+  for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
+    in_bif_cell(p, bb, d, cb, red);
+    __syncthreads();
   }
 }
 
@@ -187,22 +198,24 @@ __device__ __forceinline__ const T *in_slot_src2(const DP<T> &p, const BifBuf<T>
 // Thread mapping: the M_x*M_y live entries of a block are numbered compactly
 // (e = a*M_y + b); work lists over (task, entry) are split into NT/(M_x*M_y)
 // groups so that small codon-state counts keep all threads busy.
-constexpr int NT = 512;
+constexpr int NT = 512;       // threads per cell on diagonals with few cells
+constexpr int NT_WIDE = 256;  // ... and on diagonals with more than WIDE_CELLS cells
+constexpr int WIDE_CELLS = 296;
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
+template <typename T, int NTT>
+__global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = (T *)smem_raw;                // [SI_N][36] staged inputs
   T *O = S + (size_t)SI_N * BLK;       // outputs: CH, XI, QB, HB
   T *YO = O + 4 * BLK;                 // [29][36] interior partial sums
-  T *RED = YO + NYY * BLK;             // [NT] group partials of HB
-  T *RED2 = RED + NT;                  // [4][36] partial terms of QB
+  T *RED = YO + NYY * BLK;             // [NTT] group partials of HB
+  T *RED2 = RED + NTT;                  // [4][36] partial terms of QB
   __shared__ int sEd;
-  __shared__ double smax[NT / 32];
+  __shared__ double smax[NTT / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int x = blockIdx.x, y = x + d;
-  for (int s = t; s < SI_N; s += NT) {
+  for (int s = t; s < SI_N; s += NTT) {
     const T *src = s < SI_BIF ? in_slot_src(p, s, x, y, d) : in_slot_src2(p, bb, s, x, d);
     if (src) stage_block(S + (size_t)s * BLK, src);
   }
@@ -210,21 +223,21 @@ __global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
   __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N];
-  for (int i = t; i < 96; i += NT) {
+  for (int i = t; i < 96; i += NTT) {
     const int k = d - 47 + i;
     sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
   }
-  for (int i = t; i < 72; i += NT) {
+  for (int i = t; i < 72; i += NTT) {
     const int qx = x - 35 + i, qy = y - 35 + i;
     sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
     sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
   }
-  for (int i = t; i < 3 * NS; i += NT) {
+  for (int i = t; i < 3 * NS; i += NTT) {
     const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
     sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
     sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
   }
-  for (int i = t; i < EN_N; i += NT) sEn[i] = p.en[i];
+  for (int i = t; i < EN_N; i += NTT) sEn[i] = p.en[i];
   if (t == 0) {
     int e = 0;
     if (d > 0) {
@@ -280,7 +293,7 @@ __global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   __syncthreads();
 
   // ---- P2: interior partial sums and bulges, split over groups -> HB
-  const int GR = min(NT / MM, 32);  // groups for the reductions below
+  const int GR = min(NTT / MM, 32);  // groups for the reductions below
   if (d >= 2) {
     const int G = GR, g = t / MM, e = t % MM;
     if (g < G) {
@@ -437,14 +450,14 @@ __global__ void __launch_bounds__(NT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   __syncthreads();
   if (t == 0) {
     double m = 0;
-    for (int k = 0; k < NT / 32; k++) m = fmax(m, smax[k]);
+    for (int k = 0; k < NTT / 32; k++) m = fmax(m, smax[k]);
     atomic_max_pos(&p.dmax[d], m);
   }
 }
 
-template <typename T>
+template <typename T, int NTT = NT>
 constexpr size_t in_light_smem() {
-  return ((size_t)(SI_N + 4 + NYY + 4) * BLK + NT) * sizeof(T);
+  return ((size_t)(SI_N + 4 + NYY + 4) * BLK + NTT) * sizeof(T);
 }
 
 }  // namespace cf

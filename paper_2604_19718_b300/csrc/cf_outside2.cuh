@@ -47,15 +47,14 @@ __host__ __device__ __forceinline__ int out_next(int n, int d) {  // hGx terms y
 // take the row-gather chunks, warps 4..7 the column-gather chunks (all eight
 // take the exterior chunks); lanes over the summation index.
 template <typename T>
-__global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
-  __shared__ T red[8][BLK];
+__device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob, int d, int cb, T (*red)[BLK]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = p.n;
   const int *E = p.E;
   const int Ed = E[d];
   const int slot = d % BIFRING;
   const T ec = p.en[EN_EC];
-  const bool ext = blockIdx.x == (unsigned)(n - d);
+  const bool ext = cb == n - d;
   T acc[BLK];
   zero_block(acc);
   int Ma, Mb;
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
       }
     }
   } else {
-    const int x = blockIdx.x, y = x + d;
+    const int x = cb, y = x + d;
     Ma = p.Mp[x];
     Mb = p.Mp[y];
     if (w < 4) {
@@ -109,62 +108,48 @@ __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
       for (int k = 0; k < 8; k++) v += red[k][e];
       ob.hgx[(size_t)slot * BLK + e] = v;
     } else {
-      const int x = blockIdx.x;
+      const int x = cb;
       ob.hg[((size_t)slot * n + x) * BLK + e] = red[0][e] + red[1][e] + red[2][e] + red[3][e];
       ob.hq[((size_t)slot * n + x) * BLK + e] = red[4][e] + red[5][e] + red[6][e] + red[7][e];
     }
   }
 }
 
+// Grid-stride over the cells and the exterior (see k_in_bif).
+template <typename T>
+__global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
+  __shared__ T red[8][BLK];
+  for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
+    out_bif_cell(p, ob, d, cb, red);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- K2' staging
+// Blocks the light kernel reads for cell (x, y): transfers around the cell,
+// its own QB, adjoints of the cells that enclose it, the interior-loop adjoint
+// ring of diagonal d+1, the chains of its three shortest interior scatters
+// and the chains/adjoints of the longer intervals that use it as a bulge.
 enum : int {
-  SO_TXL = 0, SO_TX = 1, SO_TY1 = 2, SO_TY = 3,
-  SO_XXL = 4, SO_XX = 8, SO_XY1 = 12, SO_XY = 16,
-  SO_QB = 20, SO_QBI = 21, SO_HBI = 22, SO_Q2I = 23, SO_CHN = 27, SO_ML = 28, SO_MR = 32,
-  SO_GC = 36, SO_HXIE = 37, SO_H2UU = 38, SO_H2UP = 39, SO_H2PU = 40, SO_HMPU = 41, SO_HG1 = 42,
-  SO_HCHL = 43, SO_HCH = 44, SO_HXI = 45, SO_GX = 46, SO_HQ5P = 47,
-  SO_HYR = 48, SO_YYP = 76, SO_XIL = 104, SO_CHL = 132,
-  SO_BQ3 = 160, SO_BQ5 = 190, SO_BC3U = 220, SO_BC5U = 250, SO_BH3U = 280, SO_BH5U = 310,
-  SO_HGC = 340, SO_HQC = 341, SO_HGXC = 342, SO_HQ5U1 = 343, SO_HGX1 = 344, SO_Q5UM = 345, SO_Q5PM = 346,
-  SO_N = 347
+  SO_TXL = 0, SO_TY = 1, SO_XXL = 2, SO_XY = 6,
+  SO_QB = 10, SO_GC = 11, SO_HXIE = 12, SO_H2UU = 13, SO_H2UP = 14, SO_H2PU = 15, SO_HMPU = 16, SO_HG1 = 17,
+  SO_HCHL = 18, SO_HCH = 19, SO_GX = 20, SO_HQ5P = 21,
+  SO_HYR = 22, SO_CHL = 50, SO_BC3U = 53, SO_BC5U = 83, SO_BH3U = 113, SO_BH5U = 143,
+  SO_HGC = 173, SO_HQC = 174, SO_HGXC = 175, SO_HQ5U1 = 176, SO_HGX1 = 177,
+  SO_N = 178
 };
+constexpr int NCHL_LIGHT = 3;  // interior scatters into hXI kept on the critical path: L = 3..5
 
 template <typename T>
 __device__ __forceinline__ const T *out_slot_src(const DP<T> &p, int s, int x, int y, int d) {
   const int n = p.n;
   const bool hasL = x >= 1, hasR = y <= n - 2, encl = hasL && hasR;
-  if (s < SO_XXL) {
-    if (s == SO_TXL) return hasL ? p.Tr + (size_t)(x - 1) * BLK : nullptr;
-    if (s == SO_TX) return p.Tr + (size_t)x * BLK;
-    if (s == SO_TY1) return d >= 1 ? p.Tr + (size_t)(y - 1) * BLK : nullptr;
-    return hasR ? p.Tr + (size_t)y * BLK : nullptr;
-  }
-  if (s < SO_QB) {
-    const int g = (s - SO_XXL) / 4, k = (s - SO_XXL) % 4;
-    const int pos[4] = {x - 1, x, y - 1, y};
-    const bool ok[4] = {hasL, true, d >= 1, hasR};
-    return ok[g] ? p.X + ((size_t)pos[g] * 4 + k) * BLK : nullptr;
-  }
-  if (s == SO_QB) return d >= 4 ? p.QB + cidx(n, x, y) * BLK : nullptr;
-  if (s == SO_QBI) return d >= 6 ? p.QB + cidx(n, x + 1, y - 1) * BLK : nullptr;
-  if (s == SO_HBI) return d >= 4 ? p.HB + cidx(n, x + 1, y - 1) * BLK : nullptr;
-  if (s < SO_CHN) {
-    if (d < 11) return nullptr;
-    const T *t[4] = {p.QM2uu, p.QM2up, p.QM2pu, p.QM2pp};
-    return t[s - SO_Q2I] + cidx(n, x + 1, y - 1) * BLK;
-  }
-  if (s == SO_CHN) return d >= 1 ? p.CH + cidx(n, x + 1, y) * BLK : nullptr;
-  if (s < SO_MR) {
-    if (d < 5) return nullptr;
-    const T *t[4] = {p.QMpp, p.QMpu, p.QM2pp, p.QM2pu};
-    return t[s - SO_ML] + cidx(n, x, y - 1) * BLK;
-  }
-  if (s < SO_GC) {
-    if (d < 10) return nullptr;
-    const T *t[4] = {p.QM2up, p.QM2pp, p.QM2uu, p.QM2pu};
-    return t[s - SO_MR] + cidx(n, x + 1, y) * BLK;
-  }
+  if (s == SO_TXL) return hasL ? p.Tr + (size_t)(x - 1) * BLK : nullptr;
+  if (s == SO_TY) return hasR ? p.Tr + (size_t)y * BLK : nullptr;
+  if (s < SO_XY) return hasL ? p.X + ((size_t)(x - 1) * 4 + (s - SO_XXL)) * BLK : nullptr;
+  if (s < SO_QB) return hasR ? p.X + ((size_t)y * 4 + (s - SO_XY)) * BLK : nullptr;
   switch (s) {
+    case SO_QB: return d >= 4 ? p.QB + cidx(n, x, y) * BLK : nullptr;
     case SO_GC: return encl ? p.hGc + cidx(n, x - 1, y + 1) * BLK : nullptr;
     case SO_HXIE: return encl ? p.hXI + cidx(n, x - 1, y + 1) * BLK : nullptr;
     case SO_H2UU: return hasL ? p.hQM2uu + cidx(n, x - 1, y) * BLK : nullptr;
@@ -174,33 +159,22 @@ __device__ __forceinline__ const T *out_slot_src(const DP<T> &p, int s, int x, i
     case SO_HG1: return hasR ? p.hG + cidx(n, x, y + 1) * BLK : nullptr;
     case SO_HCHL: return hasL ? p.hCH + cidx(n, x - 1, y) * BLK : nullptr;
     case SO_HCH: return d >= 1 ? p.hCH + cidx(n, x, y) * BLK : nullptr;
-    case SO_HXI: return d >= 6 ? p.hXI + cidx(n, x, y) * BLK : nullptr;
     case SO_GX: return (x >= 1 && d >= 4) ? p.Gx + (size_t)x * BLK : nullptr;
     case SO_HQ5P: return (x >= 1 && d >= 4) ? p.hQ5P + (size_t)y * BLK : nullptr;
     default: break;
   }
   const int Lmax = min(MAXLOOP, d - 4);
-  if (s < SO_YYP) {  // ring hYY_{L+1}[x-1][y], L = 2..29 (block L-1)
+  if (s < SO_CHL) {  // ring hYY_{L+1}[x-1][y], L = 2..29 (block L-1)
     int L = s - SO_HYR + 2;
     bool ok = hasL && d >= 6 && L <= Lmax && L + 1 <= min(MAXLOOP, d + 1 - 4);
     return ok ? p.hYY + (((size_t)((d + 1) % YRING) * n + (x - 1)) * NYY + (L - 1)) * BLK : nullptr;
   }
-  if (s < SO_XIL) {  // YY_{L-1}[x+1][y], L = 3..30 (only needed for the gradient of T_x)
-    int L = s - SO_YYP + 3;
-    return (d >= 6 && L <= Lmax) ? p.YY + (cidx(n, x + 1, y) * NYY + (L - 3)) * BLK : nullptr;
-  }
-  if (s < SO_CHL) {
-    int L = s - SO_XIL + 3, yl = y - L + 2;
-    return (d >= 6 && L <= Lmax && yl - x >= 6) ? p.XI + cidx(n, x, yl) * BLK : nullptr;
-  }
-  if (s < SO_BQ3) {
+  if (s < SO_BC3U) {  // CH[yl][y], yl = y - L + 2, L = 3..5
     int L = s - SO_CHL + 3, yl = y - L + 2;
     return (d >= 6 && L <= Lmax && yl - x >= 6) ? p.CH + cidx(n, yl, y) * BLK : nullptr;
   }
-  const int L = (s - SO_BQ3) % MAXLOOP + 1;
-  if (s < SO_BQ5) return (d - L >= 4) ? p.QB + cidx(n, x, y - L) * BLK : nullptr;
-  if (s < SO_BC3U) return (d - L >= 4) ? p.QB + cidx(n, x + L, y) * BLK : nullptr;
   // users of QB[x][y] as the inner pair of a bulge of a longer interval
+  const int L = (s - SO_BC3U) % MAXLOOP + 1;
   const bool up3 = d >= 4 && y + L <= n - 1, up5 = d >= 4 && x - L >= 0;
   if (s < SO_BC5U) return up3 ? p.CH + cidx(n, y, y + L) * BLK : nullptr;
   if (s < SO_BH3U) return up5 ? p.CH + cidx(n, x - L, x) * BLK : nullptr;
@@ -218,30 +192,28 @@ __device__ __forceinline__ const T *out_slot_src2(const DP<T> &p, const OutBuf<T
   if (s == SO_HGXC) return out_next(n, d) > 0 ? ob.hgx + (size_t)slot * BLK : nullptr;
   if (s == SO_HQ5U1) return d + 1 < n ? p.hQ5U + (size_t)(d + 1) * BLK : nullptr;
   if (s == SO_HGX1) return d + 1 < n ? p.hGx + (size_t)(d + 1) * BLK : nullptr;
-  if (s == SO_Q5UM) return d >= 1 ? p.Q5U + (size_t)(d - 1) * BLK : nullptr;
-  if (s == SO_Q5PM) return d >= 1 ? p.Q5P + (size_t)(d - 1) * BLK : nullptr;
   return nullptr;
 }
 
 // ---------------------------------------------------------------- K2'
 // Thread mapping as in k_in_light: compact entries e = a*M_b + b, work lists
 // split into NT/(M_x*M_y) groups.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
+template <typename T, int NTT>
+__global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = (T *)smem_raw;            // [SO_N][36]
   T *HY = S + (size_t)SO_N * BLK;  // [29][36] interior partial-sum adjoints
   T *W = HY + NYY * BLK;           // work blocks
-  T *hMPP = W, *hHB = W + BLK, *hQB = W + 2 * BLK, *hCHf = W + 3 * BLK, *Hxi = W + 4 * BLK;
+  T *hMPP = W, *hHB = W + BLK, *hQB = W + 2 * BLK;
   T *hM2 = W + 5 * BLK;            // uu, up, pu, pp
   T *hMPU = W + 9 * BLK, *hGG = W + 10 * BLK;
   T *hQ5Uo = W + 11 * BLK, *hQ5Po = W + 12 * BLK, *hGxo = W + 13 * BLK;  // exterior (cell (0, d))
-  T *RED = W + 14 * BLK;           // [NT]
-  __shared__ double sps[NT / 32];
+  T *RED = W + 14 * BLK;           // [NTT]
+  __shared__ double sps[NTT / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int x = blockIdx.x, y = x + d;
-  for (int s = t; s < SO_N; s += NT) {
+  for (int s = t; s < SO_N; s += NTT) {
     const T *src = s < SO_HGC ? out_slot_src(p, s, x, y, d) : out_slot_src2(p, ob, s, x, d);
     if (src) stage_block(S + (size_t)s * BLK, src);
   }
@@ -249,21 +221,21 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
   // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
   __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N];
-  for (int i = t; i < 96; i += NT) {
+  for (int i = t; i < 96; i += NTT) {
     const int k = d - 47 + i;
     sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
   }
-  for (int i = t; i < 72; i += NT) {
+  for (int i = t; i < 72; i += NTT) {
     const int qx = x - 35 + i, qy = y - 35 + i;
     sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
     sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
   }
-  for (int i = t; i < 3 * NS; i += NT) {
+  for (int i = t; i < 3 * NS; i += NTT) {
     const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
     sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
     sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
   }
-  for (int i = t; i < EN_N; i += NT) sEn[i] = p.en[i];
+  for (int i = t; i < EN_N; i += NTT) sEn[i] = p.en[i];
   cp_async_wait_all();
   __syncthreads();
     const T *en = sEn;
@@ -289,7 +261,6 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed) : (T)0;
   }
   __syncthreads();
-  const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[y - 1] != 0;
 
   // ---------------- A: QM2 adjoints with unpaired ends; exterior prefix adjoint
   if (d >= 10 && (t < MM || (t >= 64 && t < 64 + MM) || (t >= 128 && t < 128 + MM))) {
@@ -381,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
   __syncthreads();
 
   // ---------------- D: hQB as a sum over its users (groups of threads)
-  const int GR = min(NT / MM, 32);  // groups for the reductions below
+  const int GR = min(NTT / MM, 32);  // groups for the reductions below
   if (d >= 4) {
     const int G = GR, g = t / MM, e = t % MM;
     if (g < G) {
@@ -456,7 +427,7 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     const int Lmax = min(MAXLOOP, d - 4);
     const int nitem = (Lmax - 1) * MM;
     const T *Txl = S + SO_TXL * BLK;
-    for (int it = t; it < nitem; it += NT) {
+    for (int it = t; it < nitem; it += NTT) {
       const int L = it / MM + 2, e = it % MM, a = e / My, b = e % My, pe = a * NS + b;
       T v = wIn[L] * en[EN_TM + BASE(x, a) * 4 + BASE(y, b)] * hHB[pe];
       if (hasL && L + 1 <= min(MAXLOOP, d + 1 - 4)) v += s2<true, false>(Txl, S + (SO_HYR + L - 2) * BLK, a, b, Mxl);
@@ -468,51 +439,20 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
   if (lane == 0) sps[w] = psum;
   __syncthreads();
 
-  // ---------------- F: scatters into shorter chains and XI (atomic)
-  if (d >= 5) {
-    for (int it = t; it < 2 * MAXLOOP * BLK; it += NT) {
-      const int q = it / BLK, e = it % BLK, L = q / 2 + 1;
-      if (d - L < 4) continue;
-      if ((q & 1) == 0) {
-        // HB += QB[x][y-L] CH[y-L][y]  ->  hCH[y-L][y] += f QB^T hHB
-        const int Mr = MP(y - L);
-        if (e >= Mr * My) continue;
-        const int r = e / My, s2i = e % My;
-        const T f = wBu[L];
-        const T v = f * s2<true, false>(S + (SO_BQ3 + L - 1) * BLK, hHB, r, s2i, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, y - L, y) * BLK + r * NS + s2i, v);
-      } else {
-        // HB += CH[x][x+L] QB[x+L][y]  ->  hCH[x][x+L] += f hHB QB^T
-        const int Ms = MP(x + L);
-        if (e >= Mx * Ms) continue;
-        const int r = e / Ms, s2i = e % Ms;
-        const T f = wBu[L];
-        const T v = f * s2<false, true>(hHB, S + (SO_BQ5 + L - 1) * BLK, r, s2i, My);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, x, x + L) * BLK + r * NS + s2i, v);
-      }
-    }
-  }
+  // ---------------- F: interior scatters into hXI that this and the next three
+  // diagonals read (L = 2: the cell's own XI; L = 3..5); every other scatter
+  // and the transfer gradients run in k_out_side, off the critical path
   if (d >= 6) {
     const int Lmax = min(MAXLOOP, d - 4);
-    for (int it = t; it < 2 * (Lmax - 1) * BLK; it += NT) {
-      const int q = it / BLK, e = it % BLK, L = q / 2 + 2;
-      const int yl = y - L + 2;
-      if (yl - x < 6) continue;
+    for (int it = t; it < (1 + NCHL_LIGHT) * BLK; it += NTT) {
+      const int L = it / BLK + 2, e = it % BLK, yl = y - L + 2;
+      if (L > Lmax || yl - x < 6) continue;
       const int Ml = MP(yl);
+      if (e >= Mx * Ml) continue;
+      const int r = e / Ml, s2i = e % Ml;
       const T *hy = HY + (L - 2) * BLK;
-      if ((q & 1) == 0) {
-        // YY_L += XI[x][yl] CH[yl][y]  ->  hXI[x][yl] += hYY CH^T
-        if (e >= Mx * Ml) continue;
-        const int r = e / Ml, s2i = e % Ml;
-        const T v = (L == 2) ? hy[r * NS + s2i] : s2<false, true>(hy, S + (SO_CHL + L - 3) * BLK, r, s2i, My);
-        if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + r * NS + s2i, v);
-      } else {
-        // hCH[yl][y] += XI^T hYY (the L = 2 chain is the identity)
-        if (L == 2 || e >= Ml * My) continue;
-        const int r = e / My, s2i = e % My;
-        const T v = s2<true, false>(S + (SO_XIL + L - 3) * BLK, hy, r, s2i, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, yl, y) * BLK + r * NS + s2i, v);
-      }
+      const T v = (L == 2) ? hy[r * NS + s2i] : s2<false, true>(hy, S + (SO_CHL + L - 3) * BLK, r, s2i, My);
+      if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + r * NS + s2i, v);
     }
   }
   // final chain adjoint of this cell (its scatters all came from longer intervals)
@@ -521,33 +461,212 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     T v = S[SO_HCH * BLK + pe];
     if (d >= 2) v += p.eHL[d + 1] * clamp_p2<T>(-Ed) * en[EN_TM + BASE(x, a) * 4 + BASE(y, b)] * hHB[pe];
     if (hasL) v += s2<true, false>(S + SO_TXL * BLK, S + SO_HCHL * BLK, a, b, Mxl);
-    hCHf[pe] = v;
     p.hCH[c * BLK + pe] = v;
-  }
-  // adjoint of XI[x][y] with its own L = 2 contribution, times the inner mismatch
-  if (d >= 6 && t >= 128 && t < 128 + MM) {
-    const int e = t - 128, a = e / My, b = e % My, pe = a * NS + b;
-    const T h = S[SO_HXI * BLK + pe] + HY[pe];
-    Hxi[pe] = h * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
   }
   __syncthreads();
   if (t == 0 && d >= 4) {
     double ps = 0;
-    for (int k = 0; k < NT / 32; k++) ps += sps[k];
+    for (int k = 0; k < NTT / 32; k++) ps += sps[k];
     p.P[(size_t)x * n + y] = (float)ps;
     p.P[(size_t)y * n + x] = (float)ps;
   }
+}
 
-  // ---------------- G: gradients of the boundary transfers T_x, T_{y-1}, X_x, X_{y-1}
+// ---------------------------------------------------------------- K3'
+// k_out_side(d): the parts of the adjoint of diagonal d that no diagonal
+// d-1..d-3 reads, run beside the light chain: the bulge scatters into the
+// chain adjoints of diagonals L <= d-4, the interior scatters into hXI of
+// diagonals <= d-4 and into the chain adjoints of diagonals <= 28, and the
+// gradients of the boundary transfers T_p, X_p (read only by the final
+// marginals).  It starts after the light kernel of d and must end before the
+// light kernel of d-4, the first reader of what it writes; the interior-loop
+// adjoint ring keeps YRING >= 5 diagonals so that its slot of d is intact.
+enum : int {
+  SS_TX = 0, SS_TY1 = 1, SS_XX = 2, SS_XY1 = 6, SS_QBI = 10, SS_HBI = 11, SS_CHN = 12, SS_Q2I = 13,
+  SS_ML = 17, SS_MR = 21, SS_Q5UM = 25, SS_Q5PM = 26,
+  SS_HGC = 27, SS_HHB = 28, SS_HCH = 29, SS_HXI = 30, SS_HM2 = 31, SS_HMPU = 35, SS_HG = 36,
+  SS_HQ5U = 37, SS_HGX = 38,
+  SS_HY = 39, SS_YYP = 68, SS_XIL = 96, SS_CHL = 124, SS_BQ3 = 152, SS_BQ5 = 182,
+  SS_N = 212
+};
+static_assert(YRING >= 5, "k_out_side reads the ring slot of its diagonal until the light kernel of d-4");
+constexpr int NT3 = 256;
+
+template <typename T>
+__device__ __forceinline__ const T *side_slot_src(const DP<T> &p, int s, int x, int y, int d) {
+  const int n = p.n;
+  const size_t c = cidx(n, x, y);
+  if (s == SS_TX) return p.Tr + (size_t)x * BLK;
+  if (s == SS_TY1) return d >= 1 ? p.Tr + (size_t)(y - 1) * BLK : nullptr;
+  if (s < SS_XY1) return p.X + ((size_t)x * 4 + (s - SS_XX)) * BLK;
+  if (s < SS_QBI) return d >= 1 ? p.X + ((size_t)(y - 1) * 4 + (s - SS_XY1)) * BLK : nullptr;
+  if (s == SS_QBI) return d >= 6 ? p.QB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+  if (s == SS_HBI) return d >= 4 ? p.HB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+  if (s == SS_CHN) return d >= 1 ? p.CH + cidx(n, x + 1, y) * BLK : nullptr;
+  if (s < SS_ML) {
+    if (d < 11) return nullptr;
+    const T *t[4] = {p.QM2uu, p.QM2up, p.QM2pu, p.QM2pp};
+    return t[s - SS_Q2I] + cidx(n, x + 1, y - 1) * BLK;
+  }
+  if (s < SS_MR) {
+    if (d < 5) return nullptr;
+    const T *t[4] = {p.QMpp, p.QMpu, p.QM2pp, p.QM2pu};
+    return t[s - SS_ML] + cidx(n, x, y - 1) * BLK;
+  }
+  if (s < SS_Q5UM) {
+    if (d < 10) return nullptr;
+    const T *t[4] = {p.QM2up, p.QM2pp, p.QM2uu, p.QM2pu};
+    return t[s - SS_MR] + cidx(n, x + 1, y) * BLK;
+  }
+  switch (s) {
+    case SS_Q5UM: return (x == 0 && d >= 1) ? p.Q5U + (size_t)(d - 1) * BLK : nullptr;
+    case SS_Q5PM: return (x == 0 && d >= 1) ? p.Q5P + (size_t)(d - 1) * BLK : nullptr;
+    case SS_HGC: return d >= 4 ? p.hGc + c * BLK : nullptr;
+    case SS_HHB: return d >= 2 ? p.hHB + c * BLK : nullptr;
+    case SS_HCH: return d >= 1 ? p.hCH + c * BLK : nullptr;
+    case SS_HXI: return d >= 6 ? p.hXI + c * BLK : nullptr;
+    case SS_HM2: return d >= 10 ? p.hQM2uu + c * BLK : nullptr;
+    case SS_HM2 + 1: return d >= 10 ? p.hQM2up + c * BLK : nullptr;
+    case SS_HM2 + 2: return d >= 10 ? p.hQM2pu + c * BLK : nullptr;
+    case SS_HM2 + 3: return d >= 4 ? p.hQM2pp + c * BLK : nullptr;
+    case SS_HMPU: return d >= 5 ? p.hQMpu + c * BLK : nullptr;
+    case SS_HG: return d >= 5 ? p.hG + c * BLK : nullptr;
+    case SS_HQ5U: return x == 0 ? p.hQ5U + (size_t)d * BLK : nullptr;
+    case SS_HGX: return (x == 0 && d >= 1) ? p.hGx + (size_t)d * BLK : nullptr;
+    default: break;
+  }
+  const int Lmax = min(MAXLOOP, d - 4);
+  if (s < SS_YYP) {  // this diagonal's interior-loop adjoints hYY_L, L = 2..30
+    const int L = s - SS_HY + 2;
+    return (d >= 6 && L <= Lmax) ? p.hYY + (((size_t)(d % YRING) * n + x) * NYY + (L - 2)) * BLK : nullptr;
+  }
+  if (s < SS_XIL) {  // YY_{L-1}[x+1][y], L = 3..30
+    const int L = s - SS_YYP + 3;
+    return (d >= 6 && L <= Lmax) ? p.YY + (cidx(n, x + 1, y) * NYY + (L - 3)) * BLK : nullptr;
+  }
+  if (s < SS_BQ3) {  // XI[x][yl] and CH[yl][y], yl = y - L + 2, L = 3..30
+    const int L = (s - SS_XIL) % 28 + 3, yl = y - L + 2;
+    if (!(d >= 6 && L <= Lmax && yl - x >= 6)) return nullptr;
+    return s < SS_CHL ? p.XI + cidx(n, x, yl) * BLK : p.CH + cidx(n, yl, y) * BLK;
+  }
+  const int L = (s - SS_BQ3) % MAXLOOP + 1;
+  if (d - L < 4) return nullptr;
+  return s < SS_BQ5 ? p.QB + cidx(n, x, y - L) * BLK : p.QB + cidx(n, x + L, y) * BLK;
+}
+
+struct SideCtx {
+  int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
+};
+
+template <typename T>
+__device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu) {
+  T *Hxi = S + (size_t)SS_N * BLK;   // [36]
+  T *RED = Hxi + BLK;                // [NT3]
+  int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
+  int (*sBx)[NS] = cx.sBx, (*sBy)[NS] = cx.sBy;
+  const int t = threadIdx.x;
+  const int n = p.n;
+  const int y = x + d;
+  const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[y - 1] != 0;
+  if (d < 5 && !(bx || by1)) return;  // no scatter below d = 5
+  for (int s = t; s < SS_N; s += NT3) {
+    const T *src = side_slot_src(p, s, x, y, d);
+    if (src) stage_block(S + (size_t)s * BLK, src);
+  }
+  for (int i = t; i < 96; i += NT3) {
+    const int k = d - 47 + i;
+    sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
+  }
+  for (int i = t; i < 72; i += NT3) {
+    const int qx = x - 35 + i, qy = y - 35 + i;
+    sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
+    sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
+  }
+  for (int i = t; i < 3 * NS; i += NT3) {
+    const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
+    sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
+    sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
+  }
+  for (int i = t; i < EN_N; i += NT3) sEn[i] = p.en[i];
+  cp_async_wait_all();
+  __syncthreads();
+  const T *en = sEn;
+  const int Ed = p.E[d];
+  const int Mx = MP(x), My = MP(y), MM = Mx * My;
+  const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
+  const int M0 = MP(0);
+  const T eb = en[EN_EB], sml = en[EN_EA] * en[EN_EC];
+  if (t <= MAXLOOP) {
+    const int L = t;
+    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed) : (T)0;
+  }
+  if (d >= 6 && t >= 64 && t < 64 + MM) {
+    // adjoint of XI[x][y] (its own L = 2 term included) times the inner mismatch
+    const int e = t - 64, a = e / My, b = e % My, pe = a * NS + b;
+    Hxi[pe] = S[SS_HXI * BLK + pe] * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
+  }
+  __syncthreads();
+  const T *hHB = S + SS_HHB * BLK, *HY = S + SS_HY * BLK;
+
+  // ---------------- bulge scatters into shorter chains
+  if (d >= 5) {
+    for (int it = t; it < 2 * MAXLOOP * BLK; it += NT3) {
+      const int q = it / BLK, e = it % BLK, L = q / 2 + 1;
+      if (d - L < 4) continue;
+      if ((q & 1) == 0) {
+        // HB += QB[x][y-L] CH[y-L][y]  ->  hCH[y-L][y] += f QB^T hHB
+        const int Mr = MP(y - L);
+        if (e >= Mr * My) continue;
+        const int r = e / My, s2i = e % My;
+        const T v = wBu[L] * s2<true, false>(S + (SS_BQ3 + L - 1) * BLK, hHB, r, s2i, Mx);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, y - L, y) * BLK + r * NS + s2i, v);
+      } else {
+        // HB += CH[x][x+L] QB[x+L][y]  ->  hCH[x][x+L] += f hHB QB^T
+        const int Ms = MP(x + L);
+        if (e >= Mx * Ms) continue;
+        const int r = e / Ms, s2i = e % Ms;
+        const T v = wBu[L] * s2<false, true>(hHB, S + (SS_BQ5 + L - 1) * BLK, r, s2i, My);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, x, x + L) * BLK + r * NS + s2i, v);
+      }
+    }
+  }
+  // ---------------- interior scatters: hXI of diagonals d-L+2 (L >= 6), chains (L >= 3)
+  if (d >= 6) {
+    const int Lmax = min(MAXLOOP, d - 4);
+    for (int it = t; it < 2 * (Lmax - 2) * BLK; it += NT3) {
+      const int q = it / BLK, e = it % BLK, L = q / 2 + 3;
+      const int yl = y - L + 2;
+      if (yl - x < 6) continue;
+      const int Ml = MP(yl);
+      const T *hy = HY + (L - 2) * BLK;
+      if ((q & 1) == 0) {
+        // YY_L += XI[x][yl] CH[yl][y]  ->  hXI[x][yl] += hYY CH^T (L <= 5 done by the light kernel)
+        if (L < 3 + NCHL_LIGHT || e >= Mx * Ml) continue;
+        const int r = e / Ml, s2i = e % Ml;
+        const T v = s2<false, true>(hy, S + (SS_CHL + L - 3) * BLK, r, s2i, My);
+        if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + r * NS + s2i, v);
+      } else {
+        // hCH[yl][y] += XI^T hYY
+        if (e >= Ml * My) continue;
+        const int r = e / My, s2i = e % My;
+        const T v = s2<true, false>(S + (SS_XIL + L - 3) * BLK, hy, r, s2i, Mx);
+        if (v != (T)0) atomicAdd(p.hCH + cidx(n, yl, y) * BLK + r * NS + s2i, v);
+      }
+    }
+  }
+
+  // ---------------- gradients of the boundary transfers T_x, T_{y-1}, X_x, X_{y-1}
   if (!(bx || by1)) return;
-  const T *Tx = S + SO_TX * BLK, *Ty1 = S + SO_TY1 * BLK;
-  const T *hbi = S + SO_HBI * BLK, *qin = S + SO_QBI * BLK;
-  const T *Xl = S + SO_XX * BLK, *Xr = S + SO_XY1 * BLK;
+  const T *hQB = S + SS_HGC * BLK, *hCHf = S + SS_HCH * BLK, *hM2 = S + SS_HM2 * BLK;
+  const T *hMPU = S + SS_HMPU * BLK, *hGG = S + SS_HG * BLK;
+  const T *Tx = S + SS_TX * BLK, *Ty1 = S + SS_TY1 * BLK;
+  const T *hbi = S + SS_HBI * BLK, *qin = S + SS_QBI * BLK;
+  const T *Xl = S + SS_XX * BLK, *Xr = S + SS_XY1 * BLK;
   const T fq = clamp_p2<T>((d >= 2 ? EA(d - 2) : 0) - Ed);
   if (bx) {
     // dlogZ/dT_x: terms QB, XI, chain, and the interior partial sums L = 3..Lmax,
     // split over groups of threads
-    const int MMx = Mx * M1, G2 = min(NT / MMx, 16), g = t / MMx, e = t % MMx;
+    const int MMx = Mx * M1, G2 = min(NT3 / MMx, 16), g = t / MMx, e = t % MMx;
     const int Lmax = min(MAXLOOP, d - 4);
     const int nterm = 3 + ((d >= 6) ? Lmax - 2 : 0);
     if (g < G2) {
@@ -575,10 +694,10 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
           if (d < 6) continue;
           for (int z = 0; z < My; z++) sacc += fq * Hxi[a * NS + z] * s2<false, false>(qin, Ty1, u, z, Mv);
         } else if (k == 2) {
-          if (d >= 1) sacc += s2<false, true>(hCHf, S + SO_CHN * BLK, a, u, My);
+          if (d >= 1) sacc += s2<false, true>(hCHf, S + SS_CHN * BLK, a, u, My);
         } else {
           const int L = k;
-          sacc += s2<false, true>(HY + (L - 2) * BLK, S + (SO_YYP + L - 3) * BLK, a, u, My);
+          sacc += s2<false, true>(HY + (L - 2) * BLK, S + (SS_YYP + L - 3) * BLK, a, u, My);
         }
       }
       RED[t] = sacc;
@@ -618,7 +737,7 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     const int e = t - 128, a = e / M1, u = e % M1, pe = a * NS + u;
     double *hx = p.hX + (size_t)x * 4 * BLK;
     if (d >= 11) {
-      const T *q2 = S + SO_Q2I * BLK;
+      const T *q2 = S + SS_Q2I * BLK;
       T su = 0, sp = 0;
       for (int b = 0; b < My; b++) {
         const T g = hQB[a * NS + b];
@@ -631,8 +750,8 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     }
     if (d >= 10) {
       const T F = clamp_p2<T>(EA(d - 1) - Ed);
-      const T *r_up = S + SO_MR * BLK, *r_pp = S + (SO_MR + 1) * BLK, *r_uu = S + (SO_MR + 2) * BLK,
-              *r_pu = S + (SO_MR + 3) * BLK;
+      const T *r_up = S + SS_MR * BLK, *r_pp = S + (SS_MR + 1) * BLK, *r_uu = S + (SS_MR + 2) * BLK,
+              *r_pu = S + (SS_MR + 3) * BLK;
       const T xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
       const T xup = eb * (s2<false, true>(hM2 + BLK, r_pp, a, u, My) + s2<false, true>(hM2, r_pu, a, u, My));
       atomicAdd(hx + XUU * BLK + pe, (double)(F * xuu));
@@ -644,7 +763,7 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     double *hx = p.hX + (size_t)(y - 1) * 4 * BLK;
     double xpu = 0, xuu = 0, xpp = 0, xup = 0;
     if (d >= 11) {
-      const T *q2 = S + SO_Q2I * BLK;
+      const T *q2 = S + SS_Q2I * BLK;
       T su = 0, sp = 0;
       for (int a = 0; a < Mx; a++) {
         const T g = hQB[a * NS + b];
@@ -657,8 +776,8 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     }
     if (d >= 5) {
       const T F = clamp_p2<T>(EA(d - 1) - Ed);
-      const T *mpp = S + SO_ML * BLK, *mpu = S + (SO_ML + 1) * BLK, *q2pp = S + (SO_ML + 2) * BLK,
-              *q2pu = S + (SO_ML + 3) * BLK;
+      const T *mpp = S + SS_ML * BLK, *mpu = S + (SS_ML + 1) * BLK, *q2pp = S + (SS_ML + 2) * BLK,
+              *q2pu = S + (SS_ML + 3) * BLK;
       T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
       T a3 = s2<true, false>(mpp, hGG, v2, b, Mx), a4 = s2<true, false>(mpu, hGG, v2, b, Mx);
       if (d >= 10) {
@@ -673,8 +792,8 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
     if (x == 0) {
       // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
       const T F = clamp_p2<T>(EA(d - 1) - Ed);
-      const T *q5u = S + SO_Q5UM * BLK, *q5p = S + SO_Q5PM * BLK;
-      const T *hu = hQ5Uo, *hg = hGxo;
+      const T *q5u = S + SS_Q5UM * BLK, *q5p = S + SS_Q5PM * BLK;
+      const T *hu = S + SS_HQ5U * BLK, *hg = S + SS_HGX * BLK;
       xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));
       xpu += (double)(F * s2<true, false>(q5p, hu, v2, b, M0));
       xup += (double)(F * s2<true, false>(q5u, hg, v2, b, M0));
@@ -687,9 +806,27 @@ __global__ void __launch_bounds__(NT) k_out_light(DP<T> p, OutBuf<T> ob, int d) 
   }
 }
 
+
+// Grid-stride over the cells of diagonal d (see k_in_bif).
 template <typename T>
+__global__ void __launch_bounds__(NT3) k_out_side(DP<T> p, int d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SideCtx cx;
+  __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
+  for (int x = blockIdx.x; x < p.n - d; x += gridDim.x) {
+    side_cell(p, d, x, (T *)smem_raw, cx, sEn, wBu);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+constexpr size_t out_side_smem() {
+  return ((size_t)(SS_N + 1) * BLK + NT3) * sizeof(T);
+}
+
+template <typename T, int NTT = NT>
 constexpr size_t out_light_smem() {
-  return ((size_t)(SO_N + NYY + 14) * BLK + NT) * sizeof(T);
+  return ((size_t)(SO_N + NYY + 14) * BLK + NTT) * sizeof(T);
 }
 
 }  // namespace cf

@@ -264,6 +264,17 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   return CF_OK;
 }
 
+// Grid size cap of the kernels that run beside the light chain (bifurcation
+// sums, side work of the adjoint), which loop over their cells grid-stride.
+// A cap of one CTA per SM leaves room for the light CTAs but starves the
+// off-chain kernels of their deadlines (measured: slower at 900 nt), so the
+// graphs use a cap above every diagonal's cell count: one CTA per cell.
+int offchain_ctas(const cf_problem *p, int per_sm) {
+  int sms = 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) cudaGetLastError();
+  return std::max(1, sms * per_sm);
+}
+
 // Scheduling priority of a kernel node: the light-kernel chain is the
 // critical path, the bifurcation kernels fill in behind it.
 cudaError_t set_priority(cudaGraphNode_t node, bool high) {
@@ -282,8 +293,11 @@ template <typename T>
 cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gin) return CF_OK;
   const int n = p->n;
-  const size_t smem = in_light_smem<T>();
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int cap_bif = offchain_ctas(p, 64);
+  const size_t smem = in_light_smem<T, NT>(), smemw = in_light_smem<T, NT_WIDE>();
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smemw));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   cudaGraphNode_t mset;
@@ -305,7 +319,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_in_bif<T>;
-      kp.gridDim = dim3(n - d + 1);
+      kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
       e = cudaGraphAddKernelNode(&k1[d], g, &k2[d - 4], 1, &kp);
@@ -318,10 +332,11 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     deps[nd++] = (d == 0) ? mset : k2[d - 1];
     if (d >= 8) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_in_light<T>;
+    const bool wide = false;  // the inside is fastest with NT threads on every diagonal
+    kp.func = wide ? (void *)k_in_light<T, NT_WIDE> : (void *)k_in_light<T, NT>;
     kp.gridDim = dim3(n - d);
-    kp.blockDim = dim3(NT);
-    kp.sharedMemBytes = (unsigned)smem;
+    kp.blockDim = dim3(wide ? NT_WIDE : NT);
+    kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
@@ -391,9 +406,13 @@ template <typename T>
 cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gout) return CF_OK;
   const int n = p->n;
+  const int cap_bif = offchain_ctas(p, 64), cap_side = offchain_ctas(p, 64);
   const size_t nc = ncells(n) * BLK;
-  const size_t smem = out_light_smem<T>();
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = out_light_smem<T, NT>(), smemw = out_light_smem<T, NT_WIDE>(), smem3 = out_side_smem<T>();
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smemw));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_side<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   DP<T> dp = t.dp;
@@ -404,7 +423,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (e == cudaSuccess) e = add_memset(g, &m[2], &m[1], 1, dp.hT, (size_t)n * BLK * sizeof(double));
   if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double));
   if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float));
-  std::vector<cudaGraphNode_t> k2(n), k1(n);
+  std::vector<cudaGraphNode_t> k2(n), k1(n), k3(n, nullptr);
   int nodes = 0;
   for (int d = n - 1; d >= 0 && e == cudaSuccess; d--) {
     int dd = d;
@@ -413,7 +432,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     if (hasb) {
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_out_bif<T>;
-      kp.gridDim = dim3(n - d + 1);
+      kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
       e = cudaGraphAddKernelNode(&k1[d], g, &k2[d + 4], 1, &kp);
@@ -421,19 +440,33 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       nodes++;
       if (e != cudaSuccess) break;
     }
-    cudaGraphNode_t deps[2];
+    cudaGraphNode_t deps[3];
     int nd = 0;
     deps[nd++] = (d == n - 1) ? m[4] : k2[d + 1];
     if (hasb) deps[nd++] = k1[d];
+    if (d + 4 < n && k3[d + 4]) deps[nd++] = k3[d + 4];  // side work of d+4 lands on diagonals <= d
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_out_light<T>;
+    const bool wide = n - d > WIDE_CELLS;
+    kp.func = wide ? (void *)k_out_light<T, NT_WIDE> : (void *)k_out_light<T, NT>;
     kp.gridDim = dim3(n - d);
-    kp.blockDim = dim3(NT);
-    kp.sharedMemBytes = (unsigned)smem;
+    kp.blockDim = dim3(wide ? NT_WIDE : NT);
+    kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
+    if (e == cudaSuccess && d >= 1) {
+      void *args3[] = {&dp, &dd};
+      cudaKernelNodeParams k3p = {};
+      k3p.func = (void *)k_out_side<T>;
+      k3p.gridDim = dim3(std::min(n - d, cap_side));
+      k3p.blockDim = dim3(NT3);
+      k3p.sharedMemBytes = (unsigned)smem3;
+      k3p.kernelParams = args3;
+      e = cudaGraphAddKernelNode(&k3[d], g, &k2[d], 1, &k3p);
+      if (e == cudaSuccess) e = set_priority(k3[d], false);
+      nodes++;
+    }
   }
   cudaGraphNode_t fin = nullptr;
   if (e == cudaSuccess) {
@@ -444,7 +477,12 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     kp.gridDim = dim3((std::max(p->m - 1, 1) + 127) / 128);
     kp.blockDim = dim3(128);
     kp.kernelParams = args;
-    e = cudaGraphAddKernelNode(&fin, g, &k2[0], 1, &kp);
+    // the marginals read the transfer gradients of every side kernel; those of
+    // d >= 4 already precede the light kernel of d - 4
+    std::vector<cudaGraphNode_t> fdeps{k2[0]};
+    for (int d = 1; d < std::min(n, 4); d++)
+      if (k3[d]) fdeps.push_back(k3[d]);
+    e = cudaGraphAddKernelNode(&fin, g, fdeps.data(), fdeps.size(), &kp);
     nodes++;
   }
   if (e == cudaSuccess) {

@@ -70,47 +70,63 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
       }
     }
   } else {
+    // row chunks 0..nr-1 and column chunks nr..nr+nq-1 dealt round-robin to
+    // all eight warps (a cell near either end has almost only one kind)
     const int x = cb, y = x + d;
     Ma = p.Mp[x];
     Mb = p.Mp[y];
-    if (w < 4) {
-      const int nr = out_nrow(n, x, d);
-      for (int q = w; q < nr; q += 4) {
-        const int yy = y + 4 + q * KCH + lane;
-        if (yy <= n - 1) {
-          T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
-          acc_mm<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
-        }
-      }
-    } else {
-      const int nq = out_ncol(x, d);
-      for (int q = w - 4; q < nq; q += 4) {
-        const int xx = x - 5 - q * KCH - lane;
-        if (xx >= 0) {
-          T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
-          acc_mm<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
-        }
+    const int nr = out_nrow(n, x, d), nq = out_ncol(x, d);
+    for (int q = w; q < nr; q += 8) {
+      const int yy = y + 4 + q * KCH + lane;
+      if (yy <= n - 1) {
+        T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
+        acc_mm<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
       }
     }
-  }
-  warp_reduce_block(acc, Ma, Mb);
-  if (lane < 2) {
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
 #pragma unroll
-    for (int e = 0; e < BLK; e++)
-      if ((e & 1) == lane) red[w][e] = acc[e];
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[w][e] = acc[e];
+    }
+    zero_block(acc);
+    const int q0 = ((w - nr) % 8 + 8) % 8;  // this warp owns the chunks nr + q with nr + q = w (mod 8)
+    for (int q = q0; q < nq; q += 8) {
+      const int xx = x - 5 - q * KCH - lane;
+      if (xx >= 0) {
+        T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
+        acc_mm<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
+      }
+    }
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
+#pragma unroll
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[8 + w][e] = acc[e];
+    }
+  }
+  if (ext) {
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
+#pragma unroll
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[w][e] = acc[e];
+    }
   }
   __syncthreads();
   if (threadIdx.x < BLK) {
     const int e = threadIdx.x;
-    if (ext) {
-      T v = 0;
+    T v = 0, u = 0;
 #pragma unroll
-      for (int k = 0; k < 8; k++) v += red[k][e];
+    for (int k = 0; k < 8; k++) v += red[k][e];
+    if (ext) {
       ob.hgx[(size_t)slot * BLK + e] = v;
     } else {
+#pragma unroll
+      for (int k = 0; k < 8; k++) u += red[8 + k][e];
       const int x = cb;
-      ob.hg[((size_t)slot * n + x) * BLK + e] = red[0][e] + red[1][e] + red[2][e] + red[3][e];
-      ob.hq[((size_t)slot * n + x) * BLK + e] = red[4][e] + red[5][e] + red[6][e] + red[7][e];
+      ob.hg[((size_t)slot * n + x) * BLK + e] = v;
+      ob.hq[((size_t)slot * n + x) * BLK + e] = u;
     }
   }
 }
@@ -118,7 +134,7 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
 // Grid-stride over the cells and the exterior (see k_in_bif).
 template <typename T>
 __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
-  __shared__ T red[8][BLK];
+  __shared__ T red[16][BLK];
   for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
     out_bif_cell(p, ob, d, cb, red);
     __syncthreads();

@@ -141,6 +141,61 @@ __device__ __forceinline__ void acc_mm(T (&acc)[BLK], const T *A, const T *B, in
   }
 }
 
+// acc_mm with both operand blocks first read whole into registers by 16-byte
+// loads (blocks are 144/288-byte aligned and padded), so that every load of a
+// split point is in flight before its first multiply.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
+__device__ __forceinline__ void unpack16(float *r, float4 v) {
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+__device__ __forceinline__ void unpack16(double *r, double2 v) {
+  r[0] = v.x;
+  r[1] = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_block(T (&r)[BLK], const T *src) {
+  using V = typename Vec16<T>::type;
+  constexpr int W = 16 / sizeof(T);
+  const V *s = reinterpret_cast<const V *>(src);
+#pragma unroll
+  for (int i = 0; i < BLK / W; i++) unpack16(r + W * i, __ldg(s + i));
+}
+
+template <bool TA, bool TB, typename T>
+__device__ __forceinline__ void acc_mm_v(T (&acc)[BLK], const T *A, const T *B, int Ma, int Ms, int Mb, T f) {
+  T ra[BLK], rb[BLK];
+  load_block(ra, A);
+  load_block(rb, B);
+#pragma unroll
+  for (int a = 0; a < NS; a++) {
+    if (a < Ma) {
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        if (s < Ms) {
+          T av = (TA ? ra[s * NS + a] : ra[a * NS + s]) * f;
+#pragma unroll
+          for (int b = 0; b < NS; b++)
+            if (b < Mb) acc[a * NS + b] += av * (TB ? rb[b * NS + s] : rb[s * NS + b]);
+        }
+      }
+    }
+  }
+}
+
 // One entry (a,b) of op(A) op(B) op(C) with inner sizes Mu, Mv.  Loops are
 // unrolled to the padded size with predicates so that all loads of one
 // contraction issue together instead of one dependent round trip per term.

@@ -58,7 +58,7 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
       const int k = x + 5 + c * KCH + lane;
       if (k <= y - 4) {
         T f = ec * clamp_p2<T>(p.E[k - x] + p.E[y - k] - Eref);
-        acc_mm<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
+        acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
       }
     }
   } else {
@@ -67,7 +67,7 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
       const int k = 4 + c * KCH + lane;
       if (k <= d - 4) {
         T f = clamp_p2<T>(p.E[k] + p.E[d - k] - Eref);
-        acc_mm<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, Ma, p.Mp[k], Mb, f);
+        acc_mm_v<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, Ma, p.Mp[k], Mb, f);
       }
     }
   }

@@ -66,7 +66,7 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
       const int yy = d + 4 + q * KCH + lane;
       if (yy <= n - 1) {
         T f = clamp_p2<T>(Ed + E[yy - d] - E[yy]);
-        acc_mm<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+        acc_mm_v<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, Ma, p.Mp[yy], Mb, f);
       }
     }
   } else {
@@ -80,7 +80,7 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
       const int yy = y + 4 + q * KCH + lane;
       if (yy <= n - 1) {
         T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
-        acc_mm<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+        acc_mm_v<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
       }
     }
     warp_reduce_block(acc, Ma, Mb);
@@ -95,7 +95,7 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
       const int xx = x - 5 - q * KCH - lane;
       if (xx >= 0) {
         T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
-        acc_mm<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
+        acc_mm_v<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
       }
     }
     warp_reduce_block(acc, Ma, Mb);

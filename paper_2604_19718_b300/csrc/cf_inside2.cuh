@@ -37,54 +37,54 @@ struct BifBuf {
 };
 
 // ---------------------------------------------------------------- K1
-// One 256-thread block per cell (the last block of the grid: the exterior
-// sum); warp w takes the chunks w, w+8, ... of 32 split points, lanes over the
-// split point; per-lane sums are reduced once per warp, then across warps.
-template <typename T>
+// One cell per block (the last unit of a diagonal: the exterior sum); warp w
+// of NW takes the chunks w, w+NW, ... of 32 split points, lanes over the split
+// point; per-lane sums are reduced once per warp, then across warps.
+template <typename T, int NW>
 __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int cb, T (*red)[BLK]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n = p.n;
-  const int Eref = p.E[d - 4];
+  const int Eref = __ldcg(p.E + d - 4);
   const int slot = d % BIFRING;
   const bool ext = cb == n - d;
   const int x = ext ? 0 : cb, y = x + d;
   const int Ma = p.Mp[x], Mb = p.Mp[y];
   T acc[BLK];
   zero_block(acc);
-  if (!ext) {
-    const int nc = nchunk_bif(d);
-    const T ec = p.en[EN_EC];
-    for (int c = w; c < nc; c += 8) {
-      const int k = x + 5 + c * KCH + lane;
-      if (k <= y - 4) {
-        T f = ec * clamp_p2<T>(p.E[k - x] + p.E[y - k] - Eref);
-        acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
+  if (w < NW) {
+    if (!ext) {
+      const int nc = nchunk_bif(d);
+      const T ec = p.en[EN_EC];
+      for (int c = w; c < nc; c += NW) {
+        const int k = x + 5 + c * KCH + lane;
+        if (k <= y - 4) {
+          T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
+          acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
+        }
+      }
+    } else {
+      const int nc = nchunk_ext(d);
+      for (int c = w; c < nc; c += NW) {
+        const int k = 4 + c * KCH + lane;
+        if (k <= d - 4) {
+          T f = clamp_p2<T>(__ldcg(p.E + k) + __ldcg(p.E + d - k) - Eref);
+          acc_mm_v<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, Ma, p.Mp[k], Mb, f);
+        }
       }
     }
-  } else {
-    const int nc = nchunk_ext(d);
-    for (int c = w; c < nc; c += 8) {
-      const int k = 4 + c * KCH + lane;
-      if (k <= d - 4) {
-        T f = clamp_p2<T>(p.E[k] + p.E[d - k] - Eref);
-        acc_mm_v<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, Ma, p.Mp[k], Mb, f);
-      }
-    }
-  }
-  warp_reduce_block(acc, Ma, Mb);
-  T dummy = 0;
-  if (lane < 2) {
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
 #pragma unroll
-    for (int e = 0; e < BLK; e++)
-      if ((e & 1) == lane) red[w][e] = acc[e];
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[w][e] = acc[e];
+    }
   }
-  (void)dummy;
   __syncthreads();
   if (threadIdx.x < BLK) {
     const int e = threadIdx.x;
     T v = 0;
 #pragma unroll
-    for (int k = 0; k < 8; k++) v += red[k][e];
+    for (int k = 0; k < NW; k++) v += red[k][e];
     T *dst = ext ? bb.ext + (size_t)slot * BLK : bb.main + ((size_t)slot * n + x) * BLK;
     dst[e] = v;
   }
@@ -97,7 +97,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
-    in_bif_cell(p, bb, d, cb, red);
+    in_bif_cell<T, 8>(p, bb, d, cb, red);
     __syncthreads();
   }
 }
@@ -203,8 +203,8 @@ constexpr int NT_WIDE = 256;  // ... and on diagonals with more than WIDE_CELLS 
 constexpr int WIDE_CELLS = 296;
 
 template <typename T, int NTT>
-__global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int x,
+                                              unsigned char *smem_raw) {
   T *S = (T *)smem_raw;                // [SI_N][36] staged inputs
   T *O = S + (size_t)SI_N * BLK;       // outputs: CH, XI, QB, HB
   T *YO = O + 4 * BLK;                 // [29][36] interior partial sums
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) 
   __shared__ double smax[NTT / 32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
-  const int x = blockIdx.x, y = x + d;
+  const int y = x + d;
   for (int s = t; s < SI_N; s += NTT) {
     const T *src = s < SI_BIF ? in_slot_src(p, s, x, y, d) : in_slot_src2(p, bb, s, x, d);
     if (src) stage_block(S + (size_t)s * BLK, src);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) 
   __shared__ T sEn[EN_N];
   for (int i = t; i < 96; i += NTT) {
     const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
+    sE[i] = (k >= 0 && k < d) ? __ldcg(p.E + k) : 0;
   }
   for (int i = t; i < 72; i += NTT) {
     const int qx = x - 35 + i, qy = y - 35 + i;
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) 
   if (t == 0) {
     int e = 0;
     if (d > 0) {
-      double mx = __longlong_as_double((long long)p.dmax[d - 1]);
-      e = p.E[d - 1];
+      double mx = __longlong_as_double((long long)__ldcg(p.dmax + d - 1));
+      e = __ldcg(p.E + d - 1);
       if (mx > 0) {
         if (isfinite(mx)) e += ilogb(mx);
         else atomicOr(p.err, 1);
@@ -453,6 +453,12 @@ __global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) 
     for (int k = 0; k < NTT / 32; k++) m = fmax(m, smax[k]);
     atomic_max_pos(&p.dmax[d], m);
   }
+}
+
+template <typename T, int NTT>
+__global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  in_light_cell<T, NTT>(p, bb, d, blockIdx.x, smem_raw);
 }
 
 template <typename T, int NTT = NT>

@@ -151,6 +151,11 @@ struct cf_problem {
   int64_t *win_off = nullptr;
   double *win_logz = nullptr;
   size_t win_bases_cap = 0, win_nwin_cap = 0;
+  // pinned host staging of host-side window inputs and outputs
+  uint8_t *win_hbases = nullptr;
+  int64_t *win_hoff = nullptr;
+  double *win_hlogz = nullptr;
+  size_t win_hbases_cap = 0, win_hnwin_cap = 0;
   float t_win = 0;
 };
 
@@ -729,15 +734,33 @@ cf_status run_windows(cf_problem *p, const uint8_t *bases, const int64_t *offset
     CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_off, p->win_nwin_cap));
     CF_CUDA(p, dalloc(p->win_buf_allocs, &p->win_logz, p->win_nwin_cap));
   }
+  // host inputs and outputs go through pinned buffers owned by the problem
+  // (every call ends with a stream synchronisation, so they are free here)
+  const bool host_io = !bases_dev || !off_dev || !out_dev;
+  if (host_io && (p->win_hbases_cap < total || p->win_hnwin_cap < (size_t)nwin + 1)) {
+    if (p->win_hbases) cudaFreeHost(p->win_hbases);
+    if (p->win_hoff) cudaFreeHost(p->win_hoff);
+    if (p->win_hlogz) cudaFreeHost(p->win_hlogz);
+    p->win_hbases = nullptr;
+    p->win_hoff = nullptr;
+    p->win_hlogz = nullptr;
+    p->win_hbases_cap = std::max(p->win_hbases_cap, std::max(total, (size_t)16));
+    p->win_hnwin_cap = std::max(p->win_hnwin_cap, (size_t)nwin + 1);
+    CF_CUDA(p, cudaHostAlloc((void **)&p->win_hbases, p->win_hbases_cap, cudaHostAllocDefault));
+    CF_CUDA(p, cudaHostAlloc((void **)&p->win_hoff, p->win_hnwin_cap * sizeof(int64_t), cudaHostAllocDefault));
+    CF_CUDA(p, cudaHostAlloc((void **)&p->win_hlogz, p->win_hnwin_cap * sizeof(double), cudaHostAllocDefault));
+  }
   WinArgs a;
   a.bases = bases;
   if (!bases_dev) {
-    CF_CUDA(p, cudaMemcpyAsync(p->win_bases, bases, total, cudaMemcpyHostToDevice, st));
+    std::memcpy(p->win_hbases, bases, total);
+    CF_CUDA(p, cudaMemcpyAsync(p->win_bases, p->win_hbases, total, cudaMemcpyHostToDevice, st));
     a.bases = p->win_bases;
   }
   a.off = offsets;
   if (!off_dev) {
-    CF_CUDA(p, cudaMemcpyAsync(p->win_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st));
+    std::memcpy(p->win_hoff, off.data(), sizeof(int64_t) * off.size());
+    CF_CUDA(p, cudaMemcpyAsync(p->win_off, p->win_hoff, sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st));
     a.off = p->win_off;
   }
   a.nwin = nwin;
@@ -754,10 +777,11 @@ cf_status run_windows(cf_problem *p, const uint8_t *bases, const int64_t *offset
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaEventRecord(p->ev[1], st));
   if (!out_dev)
-    CF_CUDA(p, cudaMemcpyAsync(logz, p->win_logz, sizeof(double) * nwin, cudaMemcpyDeviceToHost, st));
+    CF_CUDA(p, cudaMemcpyAsync(p->win_hlogz, p->win_logz, sizeof(double) * nwin, cudaMemcpyDeviceToHost, st));
   int err = 0;
   CF_CUDA(p, cudaMemcpyAsync(&err, p->win_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
+  if (!out_dev) std::memcpy(logz, p->win_hlogz, sizeof(double) * nwin);
   CF_CUDA(p, cudaEventElapsedTime(&p->t_win, p->ev[0], p->ev[1]));
   if (err & 1) return fail(p, CF_EINVAL, "cf_window_logz: base code outside 0..3");
   if (err & 2) return fail(p, CF_ENUMERIC, "cf_window_logz: non-finite table entry after scaling");
@@ -847,6 +871,9 @@ cf_status cf_problem_free(cf_problem *p) {
   release_protein(p);
   free_list(p->win_allocs);
   free_list(p->win_buf_allocs);
+  if (p->win_hbases) cudaFreeHost(p->win_hbases);
+  if (p->win_hoff) cudaFreeHost(p->win_hoff);
+  if (p->win_hlogz) cudaFreeHost(p->win_hlogz);
   for (auto &ev : p->ev)
     if (ev) cudaEventDestroy(ev);
   delete p;

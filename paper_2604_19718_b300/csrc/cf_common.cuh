@@ -257,6 +257,53 @@ __device__ __forceinline__ T s3(const T *A, const T *B, const T *C, int a, int b
 #define MP(q) (((q) >= x - 35 && (q) <= x + 36) ? sMx[(q) - (x - 35)] : (((q) >= y - 35 && (q) <= y + 36) ? sMy[(q) - (y - 35)] : p.Mp[q]))
 #define BASE(q, a) (((q) >= x - 1 && (q) <= x + 1) ? sBx[(q) - (x - 1)][a] : sBy[(q) - (y - 1)][a])
 
+// ---- TMA bulk copies (global -> shared) completing on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// raise the transaction count of the current phase by bytes (no arrival)
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bytes: multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bounded wait for a phase of the mbarrier (about a second of polling).  On
+// timeout bit 8 of the error word is set and false is returned; the copies
+// that were in flight are then waited for once more, again bounded.
+constexpr int ERR_STAGE_TIMEOUT = 8;
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err) {
+  for (unsigned long long it = 0; it < (1ull << 22); it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(128);
+  }
+  atomicOr(err, ERR_STAGE_TIMEOUT);
+  for (unsigned long long it = 0; it < (1ull << 22); it++)
+    if (mbar_try_wait(bar, parity)) break;
+  return false;
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
   if (v > 0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }

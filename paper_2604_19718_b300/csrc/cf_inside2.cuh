@@ -195,54 +195,200 @@ __device__ __forceinline__ const T *in_slot_src2(const DP<T> &p, const BifBuf<T>
 }
 
 // ---------------------------------------------------------------- K2
-// Thread mapping: the M_x*M_y live entries of a block are numbered compactly
-// (e = a*M_y + b); work lists over (task, entry) are split into NT/(M_x*M_y)
-// groups so that small codon-state counts keep all threads busy.
+constexpr int NT_IN = 256;    // threads per cell of the inside light kernel
 constexpr int NT = 512;       // threads per cell on diagonals with few cells
 constexpr int NT_WIDE = 256;  // ... and on diagonals with more than WIDE_CELLS cells
 constexpr int WIDE_CELLS = 296;
 
+// ---------------------------------------------------------------- row products
+// Every table entry is a 6x6 block whose rows and columns beyond the codon-
+// state counts are zero, so block products can always run over the full
+// padded size: the padding contributes exact zeros.  Fixed trip counts let the
+// compiler keep a row of the left operand in registers and stream the rows of
+// the right operand with 8/16-byte shared-memory loads.
+template <typename T>
+struct Row2;
+template <>
+struct Row2<float> {
+  using type = float2;
+};
+template <>
+struct Row2<double> {
+  using type = double2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld_row(T (&r)[NS], const T *src) {
+  using V = typename Row2<T>::type;
+  const V *s = reinterpret_cast<const V *>(src);
+#pragma unroll
+  for (int i = 0; i < NS / 2; i++) {
+    const V v = s[i];
+    r[2 * i] = v.x;
+    r[2 * i + 1] = v.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st_row(T *dst, const T (&r)[NS]) {
+  using V = typename Row2<T>::type;
+  V *d = reinterpret_cast<V *>(dst);
+#pragma unroll
+  for (int i = 0; i < NS / 2; i++) {
+    V v;
+    v.x = r[2 * i];
+    v.y = r[2 * i + 1];
+    d[i] = v;
+  }
+}
+// r += (f * av) . B   (av: one row of the left operand)
+template <typename T>
+__device__ __forceinline__ void row_acc(T (&r)[NS], const T (&av)[NS], const T *B, T f) {
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    T bv[NS];
+    ld_row(bv, B + s * NS);
+    const T x = av[s] * f;
+#pragma unroll
+    for (int b = 0; b < NS; b++) r[b] = fma(x, bv[b], r[b]);
+  }
+}
+// r += f * (row a of A) . B
+template <typename T>
+__device__ __forceinline__ void row_mm(T (&r)[NS], const T *A, const T *B, int a, T f) {
+  T av[NS];
+  ld_row(av, A + a * NS);
+  row_acc(r, av, B, f);
+}
+// r += f * (row a of A) . B . C
+template <typename T>
+__device__ __forceinline__ void row_mmm(T (&r)[NS], const T *A, const T *B, const T *C, int a, T f) {
+  T t[NS];
+#pragma unroll
+  for (int b = 0; b < NS; b++) t[b] = (T)0;
+  row_mm(t, A, B, a, (T)1);
+  row_acc(r, t, C, f);
+}
+template <typename T>
+__device__ __forceinline__ void row_zero(T (&r)[NS]) {
+#pragma unroll
+  for (int b = 0; b < NS; b++) r[b] = (T)0;
+}
+template <typename T>
+__device__ __forceinline__ T row_absmax(const T (&r)[NS]) {
+  T m = 0;
+#pragma unroll
+  for (int b = 0; b < NS; b++) m = fmax(m, fabs(r[b]));
+  return m;
+}
+
+// ---------------------------------------------------------------- K2
+// Light work of one cell (x, y) of diagonal d in two phases of independent
+// work, split by task and block row (6 threads per task, one output row
+// each):
+//   phase A  chain, XI, the 28 interior partial sums YY_3..YY_30, the bulge
+//            sums (12 partial blocks), the QB terms (hairpin-interior,
+//            stack in 3 parts, multiloop in 2), QMpu, G, QM2pu/up/uu and the
+//            exterior row;
+//   phase B  HB (sum over interior sizes, bulges and hairpin), QB, QMpp,
+//            QM2pp and the exterior Q5P, entry by entry.
+// Staged input slots that a diagonal does not use are zero-filled, so every
+// task runs unconditionally; loop weights that do not apply are zero.
+enum : int {
+  LT_CH = 0, LT_XI = 1, LT_YY = 2,            // YY_L, L = 3..30: tasks 2..29
+  LT_BU = 30, NLT_BU = 12,                    // bulges: tasks 30..41
+  LT_QBH = 42, LT_QBS = 43, NLT_QBS = 3,      // QB: hairpin-interior term, stack in 3 parts
+  LT_QBM = 46,                                // QB: multiloop, 2 parts (46, 47)
+  LT_QMPU = 48, LT_G = 49, LT_M2PU = 50, LT_M2UP = 51, LT_M2UU = 52,
+  LT_GX = 53, LT_Q5U = 54, LT_Q5K = 55,       // exterior (x == 0)
+  NLT = 56
+};
+// shared result slots (blocks): phase A writes 0..LO_Q5U, phase B the rest;
+// every final result is copied to its table at the end of the cell
+enum : int {
+  LO_CH = 0, LO_XI = 1, LO_YY = 2,            // YY_L at LO_YY + L - 3
+  LO_BU = 30, LO_QBH = 42, LO_QBS = 43, LO_QBM = 46, LO_Q5K = 48,
+  LO_QMPU = 49, LO_G = 50, LO_M2PU = 51, LO_M2UP = 52, LO_M2UU = 53, LO_GX = 54, LO_Q5U = 55,
+  LO_HB = 56, LO_QB = 57, LO_QMPP = 58, LO_QM2PP = 59, LO_Q5P = 60, LO_N = 61
+};
+
+// Threads per entry in the HB sum of phase B, and the first thread of the
+// QB/QMpp entries (a warp boundary after the HB threads).
+template <int NTT>
+struct LightMap {
+  static constexpr int GHB = NTT >= 512 ? 8 : 4;
+  static constexpr int QB0 = (GHB * BLK + 31) / 32 * 32;
+  static_assert(QB0 + BLK <= NTT, "phase B needs one thread per QB entry");
+};
+
 template <typename T, int NTT>
 __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int x,
                                               unsigned char *smem_raw) {
+  using LM = LightMap<NTT>;
   T *S = (T *)smem_raw;                // [SI_N][36] staged inputs
-  T *O = S + (size_t)SI_N * BLK;       // outputs: CH, XI, QB, HB
-  T *YO = O + 4 * BLK;                 // [29][36] interior partial sums
-  T *RED = YO + NYY * BLK;             // [NTT] group partials of HB
-  T *RED2 = RED + NTT;                  // [4][36] partial terms of QB
+  T *O = S + (size_t)SI_N * BLK;       // [LO_N][36] phase A results
   __shared__ int sEd;
   __shared__ double smax[NTT / 32];
+  __shared__ int sE[96], sBx[3][NS], sBy[3][NS];
+  __shared__ T sEn[EN_N];
+  __shared__ __align__(8) unsigned long long sbar;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int y = x + d;
-  for (int s = t; s < SI_N; s += NTT) {
-    const T *src = s < SI_BIF ? in_slot_src(p, s, x, y, d) : in_slot_src2(p, bb, s, x, d);
-    if (src) stage_block(S + (size_t)s * BLK, src);
+  // per-cell context, each value loaded by its own thread before any copy is
+  // issued so that all loads are in flight together: exponents of diagonals
+  // d-47..d-1, bases of x-1..x+1 and y-1..y+1, energy factors, and the
+  // largest mantissa and exponent of diagonal d-1 (last thread)
+  static_assert(NTT > EN_N && NTT > 96 + 6 * NS, "one context value per thread");
+  int cE = 0, cB = 0;
+  T cEn = 0;
+  unsigned long long cMax = 0;
+  if (t < EN_N) cEn = p.en[t];
+  if (t < 96) {
+    const int k = d - 47 + t;
+    if (k >= 0 && k < d) cE = __ldcg(p.E + k);
+  } else if (t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    const int q = (side == 0 ? x : y) - 1 + r;
+    if (q >= 0 && q < n) cB = p.base[q * NS + a];
+  } else if (t == NTT - 1 && d > 0) {
+    cMax = __ldcg(p.dmax + d - 1);
+    cE = __ldcg(p.E + d - 1);
   }
-  // small per-cell context on chip: exponents around d, codon-state counts
-  // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
-  __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
-  __shared__ T sEn[EN_N];
-  for (int i = t; i < 96; i += NTT) {
-    const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < d) ? __ldcg(p.E + k) : 0;
+  if (t == 0) mbar_init(&sbar, 1);
+  __syncthreads();
+  // Staging: one TMA bulk copy per input block (the interior partial sums
+  // YY_{L-1}[x+1][y], L = 3..Lmax, are contiguous and go as one copy); slots
+  // this cell does not use are zero-filled.  Each issuing thread adds its
+  // bytes to the barrier's transaction count before its copy; thread 0 arrives
+  // once every thread has done so.
+  {
+    const int LmaxS = min(MAXLOOP, d - 4);
+    for (int s = t; s < SI_N; s += NTT) {
+      T *dst = S + (size_t)s * BLK;
+      if (s > SI_YYP && s < SI_XIL && d >= 6 && s - SI_YYP + 3 <= LmaxS) continue;  // part of the YY run
+      const T *src = s < SI_BIF ? in_slot_src(p, s, x, y, d) : in_slot_src2(p, bb, s, x, d);
+      if (src) {
+        const unsigned bytes = (s == SI_YYP ? (unsigned)(LmaxS - 2) : 1u) * BLK * (unsigned)sizeof(T);
+        mbar_expect(&sbar, bytes);
+        bulk_g2s(dst, src, bytes, &sbar);
+      } else {
+#pragma unroll
+        for (int q = 0; q < BLK; q++) dst[q] = (T)0;
+      }
+    }
   }
-  for (int i = t; i < 72; i += NTT) {
-    const int qx = x - 35 + i, qy = y - 35 + i;
-    sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
-    sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
-  }
-  for (int i = t; i < 3 * NS; i += NTT) {
-    const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
-    sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
-    sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
-  }
-  for (int i = t; i < EN_N; i += NTT) sEn[i] = p.en[i];
-  if (t == 0) {
+  if (t < EN_N) sEn[t] = cEn;
+  if (t < 96) {
+    sE[t] = cE;
+  } else if (t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    if (side == 0) sBx[r][a] = cB;
+    else sBy[r][a] = cB;
+  } else if (t == NTT - 1) {
     int e = 0;
     if (d > 0) {
-      double mx = __longlong_as_double((long long)__ldcg(p.dmax + d - 1));
-      e = __ldcg(p.E + d - 1);
+      const double mx = __longlong_as_double((long long)cMax);
+      e = cE;
       if (mx > 0) {
         if (isfinite(mx)) e += ilogb(mx);
         else atomicOr(p.err, 1);
@@ -251,203 +397,297 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     sEd = e;
     if (x == 0) p.E[d] = e;
   }
-  cp_async_wait_all();
   __syncthreads();
+  if (t == 0) mbar_arrive(&sbar);
+  if (!mbar_wait(&sbar, 0, p.err)) return;
   const int Ed = sEd;
-  const int Mx = MP(x), My = MP(y), MM = Mx * My;
-  const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
   const T *en = sEn;
   const size_t c = cidx(n, x, y);
   const T *Tx = S + SI_TX * BLK, *Ty1 = S + SI_TY1 * BLK;
-  T *CHo = O, *XIo = O + BLK, *QBo = O + 2 * BLK, *HBo = O + 3 * BLK;
+  const T *Xl = S + SI_XX * BLK, *Xr = S + SI_XY1 * BLK;
+  const int Lmax = min(MAXLOOP, d - 4);
   double lmax = 0.0;
-  // loop-length weights of this cell: interior eIn(L) 2^{E[d-L+2]-E[d]},
-  // bulge eBu(L) 2^{E[d-L]-E[d]}, hairpin eH(d+1) 2^{-E[d]}
-  __shared__ T wIn[MAXLOOP + 1], wBu[MAXLOOP + 1], wHp;
-  if (t <= MAXLOOP) {
-    const int L = t;
-    wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed) : (T)0;
-    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed) : (T)0;
-  } else if (t == 64 && d >= 2) {
-    wHp = p.eHL[d + 1] * clamp_p2<T>(-Ed);
-  }
-  __syncthreads();
 
-  // ---- P1: chain (threads 0..MM-1) and XI (128..128+MM-1)
-  if (t < MM) {
-    const int a = t / My, b = t % My, pe = a * NS + b;
-    T v;
-    if (d == 0) v = (a == b) ? (T)1 : (T)0;
-    else v = s2<false, false>(Tx, S + SI_CHN * BLK, a, b, M1);
-    CHo[pe] = v;
-    p.CH[c * BLK + pe] = v;
-  } else if (d >= 6 && t >= 128 && t < 128 + MM) {
-    const int e = t - 128, a = e / My, b = e % My, pe = a * NS + b;
-    const T f = clamp_p2<T>(EA(d - 2) - Ed);
-    T v = s3<false, false, false>(Tx, S + SI_QBI * BLK, Ty1, a, b, M1, Mv);
-    v *= f * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
-    XIo[pe] = v;
-    p.XI[c * BLK + pe] = v;
-    lmax = fmax(lmax, (double)fabs(v));
-  }
-  __syncthreads();
-
-  // ---- P2: interior partial sums and bulges, split over groups -> HB
-  const int GR = min(NTT / MM, 32);  // groups for the reductions below
-  if (d >= 2) {
-    const int G = GR, g = t / MM, e = t % MM;
-    if (g < G) {
-      const int a = e / My, b = e % My, pe = a * NS + b;
-      const T tmo = en[EN_TM + BASE(x, a) * 4 + BASE(y, b)];
-      const int Lmax = min(MAXLOOP, d - 4);
-      const int nyy = (d >= 6) ? Lmax - 1 : 0;
-      const int ntask = nyy + 2 * MAXLOOP;
-      T acc = 0;
-      for (int k = g; k < ntask; k += G) {
-        if (k < nyy) {
-          const int L = k + 2;
-          T v;
-          if (L == 2) {
-            v = XIo[pe];
-          } else {
-            v = s2<false, false>(Tx, S + (SI_YYP + L - 3) * BLK, a, b, M1);
-            const int yl = y - L + 2;
-            if (yl - x >= 6) v += s2<false, false>(S + (SI_XIL + L - 3) * BLK, S + (SI_CHL + L - 3) * BLK, a, b, MP(yl));
-          }
-          YO[(L - 2) * BLK + pe] = v;
-          p.YY[(c * NYY + (L - 2)) * BLK + pe] = v;
-          acc += wIn[L] * tmo * v;
-        } else {
-          const int q = k - nyy, L = q / 2 + 1;
-          if (d - L < 4) continue;
-          const T f = wBu[L];
-          if ((q & 1) == 0)
-            acc += f * s2<false, false>(S + (SI_BQ3 + L - 1) * BLK, S + (SI_BC3 + L - 1) * BLK, a, b, MP(y - L));
-          else
-            acc += f * s2<false, false>(S + (SI_BC5 + L - 1) * BLK, S + (SI_BQ5 + L - 1) * BLK, a, b, MP(x + L));
-        }
+  // ---------------- phase A: one block row per thread and step
+  for (int rt = t; rt < NS * NLT; rt += NTT) {
+    const int task = rt / NS, a = rt - task * NS;
+    T r[NS];
+    row_zero(r);
+    int oslot = -1;      // shared result slot
+    bool scaled = true;  // counts toward the diagonal maximum
+    if (task == LT_CH) {
+      if (d == 0) {
+        const int Mx = p.Mp[x];
+#pragma unroll
+        for (int b = 0; b < NS; b++) r[b] = (a == b && a < Mx) ? (T)1 : (T)0;
+      } else {
+        row_mm(r, Tx, S + SI_CHN * BLK, a, (T)1);
       }
-      if (g == 0) acc += wHp * tmo * CHo[pe];
-      RED[t] = acc;
-    }
-  }
-  __syncthreads();
-  if (d >= 2 && t < MM) {
-    const int a = t / My, b = t % My, pe = a * NS + b;
-    T v = 0;
-    for (int g = 0; g < GR; g++) v += RED[g * MM + t];
-    HBo[pe] = v;
-    p.HB[c * BLK + pe] = v;
-    lmax = fmax(lmax, (double)fabs(v));
-  }
-  // ---- P3: QB of the closing pair (x, y): four partial terms per entry
-  if (d >= 4 && t >= 64 && t < 64 + 4 * MM) {
-    const int sub = (t - 64) / MM, e = (t - 64) % MM, a = e / My, b = e % My;
-    const int pto = pair_type(BASE(x, a), BASE(y, b));
-    T v = 0;
-    if (pto >= 0) {
-      if (sub == 0) {
-        v = s3<false, false, false>(Tx, S + SI_HBI * BLK, Ty1, a, b, M1, Mv);
-      } else if (sub == 1) {
-        if (d >= 6) {
-          const T *qin = S + SI_QBI * BLK;
-          for (int a2 = 0; a2 < M1; a2++) {
-            const T tv = Tx[a * NS + a2];
-            if (tv == (T)0) continue;
+      oslot = LO_CH;
+      scaled = false;
+    } else if (task == LT_XI) {
+      if (d >= 6) {
+        row_mmm(r, Tx, S + SI_QBI * BLK, Ty1, a, clamp_p2<T>(EA(d - 2) - Ed));
+        const int bxa = BASE(x, a);
+#pragma unroll
+        for (int b = 0; b < NS; b++) r[b] *= en[EN_TM + BASE(y, b) * 4 + bxa];
+      }
+      oslot = LO_XI;
+    } else if (task < LT_BU) {
+      const int L = task - LT_YY + 3;
+      if (d >= 6 && L <= Lmax) {
+        row_mm(r, Tx, S + (SI_YYP + L - 3) * BLK, a, (T)1);
+        row_mm(r, S + (SI_XIL + L - 3) * BLK, S + (SI_CHL + L - 3) * BLK, a, (T)1);
+      }
+      oslot = LO_YY + L - 3;
+      scaled = false;  // relative to 2^{E[d-L+2]}
+    } else if (task < LT_QBH) {
+      // bulges: side 3' (QB[x][y-L] CH[y-L][y]) for even j, 5' (CH[x][x+L] QB[x+L][y]) for odd
+      const int j = task - LT_BU, side = j & 1, L0 = (j >> 1) * 5 + 1;
+#pragma unroll
+      for (int L = L0; L < L0 + 5; L++) {
+        if (d - L < 4) break;
+        const T f = en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed);
+        if (side == 0)
+          row_mm(r, S + (SI_BQ3 + L - 1) * BLK, S + (SI_BC3 + L - 1) * BLK, a, f);
+        else
+          row_mm(r, S + (SI_BC5 + L - 1) * BLK, S + (SI_BQ5 + L - 1) * BLK, a, f);
+      }
+      oslot = LO_BU + j;
+      scaled = false;
+    } else if (task == LT_QBH) {
+      if (d >= 4) row_mmm(r, Tx, S + SI_HBI * BLK, Ty1, a, (T)1);
+      oslot = LO_QBH;
+      scaled = false;
+    } else if (task < LT_QBM) {
+      // stack: sum over inner states (a2, b2) with the factor of the
+      // (outer, inner) pair types; this part takes a2 in {2j, 2j+1}
+      if (d >= 6) {
+        const T *qin = S + SI_QBI * BLK;
+        int pto[NS];
+        const int bxa = BASE(x, a);
+#pragma unroll
+        for (int b = 0; b < NS; b++) pto[b] = pair_type(bxa, BASE(y, b));
+        const int j = task - LT_QBS;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int a2 = 2 * j + q;
+          const T tv = Tx[a * NS + a2];
+          if (tv != (T)0) {
             const int ba = BASE((x + 1), a2);
-            for (int b2 = 0; b2 < Mv; b2++) {
+#pragma unroll
+            for (int b2 = 0; b2 < NS; b2++) {
               const int pti = pair_type(ba, BASE((y - 1), b2));
-              if (pti >= 0) v += tv * qin[a2 * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
+              const T u = tv * qin[a2 * NS + b2];
+              if (pti >= 0 && u != (T)0) {
+                T tyr[NS];
+                ld_row(tyr, Ty1 + b2 * NS);
+#pragma unroll
+                for (int b = 0; b < NS; b++)
+                  if (pto[b] >= 0) r[b] = fma(u * en[EN_STK + pto[b] * 6 + pti], tyr[b], r[b]);
+              }
             }
           }
         }
-      } else if (d >= 11) {
-        const T *Xl = S + SI_XX * BLK, *Xr = S + SI_XY1 * BLK, *q2 = S + SI_Q2I * BLK;
-        if (sub == 2)
-          v = s3<false, false, false>(Xl + XPU * BLK, q2 + 0 * BLK, Xr + XUP * BLK, a, b, M1, Mv) +
-              s3<false, false, false>(Xl + XPU * BLK, q2 + 1 * BLK, Xr + XPP * BLK, a, b, M1, Mv);
-        else
-          v = s3<false, false, false>(Xl + XPP * BLK, q2 + 2 * BLK, Xr + XUP * BLK, a, b, M1, Mv) +
-              s3<false, false, false>(Xl + XPP * BLK, q2 + 3 * BLK, Xr + XPP * BLK, a, b, M1, Mv);
-        v *= en[EN_EA] * en[EN_EC];
+      }
+      oslot = LO_QBS + task - LT_QBS;
+      scaled = false;
+    } else if (task < LT_QMPU) {
+      if (d >= 11) {
+        const T *q2 = S + SI_Q2I * BLK;
+        if (task == LT_QBM) {
+          row_mmm(r, Xl + XPU * BLK, q2 + 0 * BLK, Xr + XUP * BLK, a, (T)1);
+          row_mmm(r, Xl + XPU * BLK, q2 + 1 * BLK, Xr + XPP * BLK, a, (T)1);
+        } else {
+          row_mmm(r, Xl + XPP * BLK, q2 + 2 * BLK, Xr + XUP * BLK, a, (T)1);
+          row_mmm(r, Xl + XPP * BLK, q2 + 3 * BLK, Xr + XPP * BLK, a, (T)1);
+        }
+      }
+      oslot = LO_QBM + task - LT_QBM;
+      scaled = false;
+    } else if (task == LT_QMPU || task == LT_G) {
+      if (d >= 5) {
+        const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
+        const T *mpp = S + SI_ML * BLK, *mpu = S + (SI_ML + 1) * BLK;
+        if (task == LT_QMPU) {
+          const T f = en[EN_EB] * F1;
+          row_mm(r, mpp, Xr + XPU * BLK, a, f);
+          row_mm(r, mpu, Xr + XUU * BLK, a, f);
+        } else {
+          row_mm(r, mpp, Xr + XPP * BLK, a, F1);
+          row_mm(r, mpu, Xr + XUP * BLK, a, F1);
+        }
+      }
+      oslot = task == LT_QMPU ? LO_QMPU : LO_G;
+    } else if (task <= LT_M2UU) {
+      if (d >= 10) {
+        const T f = en[EN_EB] * clamp_p2<T>(EA(d - 1) - Ed);
+        if (task == LT_M2PU) {
+          row_mm(r, S + (SI_ML + 2) * BLK, Xr + XPU * BLK, a, f);
+          row_mm(r, S + (SI_ML + 3) * BLK, Xr + XUU * BLK, a, f);
+        } else if (task == LT_M2UP) {
+          row_mm(r, Xl + XUU * BLK, S + SI_MR * BLK, a, f);
+          row_mm(r, Xl + XUP * BLK, S + (SI_MR + 1) * BLK, a, f);
+        } else {
+          row_mm(r, Xl + XUU * BLK, S + (SI_MR + 2) * BLK, a, f);
+          row_mm(r, Xl + XUP * BLK, S + (SI_MR + 3) * BLK, a, f);
+        }
+      }
+      oslot = LO_M2PU + task - LT_M2PU;
+    } else if (task < NLT && x == 0) {
+      // exterior prefix [0, d]: rows are the states of position 0
+      const T *pu = S + SI_Q5U * BLK, *pp = S + SI_Q5P * BLK;
+      if (task == LT_GX) {
+        if (d >= 1) {
+          const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
+          row_mm(r, pu, Xr + XUP * BLK, a, F1);
+          row_mm(r, pp, Xr + XPP * BLK, a, F1);
+        }
+        oslot = LO_GX;
+      } else if (task == LT_Q5U) {
+        if (d == 0) {
+          const int M0 = p.Mp[0];
+#pragma unroll
+          for (int b = 0; b < NS; b++) r[b] = (a == b && a < M0) ? (T)1 : (T)0;
+        } else {
+          const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
+          row_mm(r, pu, Xr + XUU * BLK, a, F1);
+          row_mm(r, pp, Xr + XPU * BLK, a, F1);
+        }
+        oslot = LO_Q5U;
+      } else {
+        // split points k = 1..3 use QB[k][d] of diagonals d-1..d-3
+        for (int k = 1; k <= 3 && k <= d - 4; k++)
+          row_mm(r, S + (SI_GXK + k - 1) * BLK, S + (SI_QBK + k - 1) * BLK, a, clamp_p2<T>(EA(k) + EA(d - k) - Ed));
+        oslot = LO_Q5K;
+        scaled = false;
       }
     }
-    RED2[t - 64] = v;
-  }
-  __syncthreads();
-  if (d >= 4 && t < MM) {
-    const int a = t / My, b = t % My, pe = a * NS + b;
-    const T v = (RED2[t] + RED2[MM + t] + RED2[2 * MM + t] + RED2[3 * MM + t]) * clamp_p2<T>(EA(d - 2) - Ed);
-    QBo[pe] = v;
-    p.QB[c * BLK + pe] = v;
-    lmax = fmax(lmax, (double)fabs(v));
+    if (oslot >= 0) {
+      st_row(O + (size_t)oslot * BLK + a * NS, r);
+      if (scaled) lmax = fmax(lmax, (double)row_absmax(r));
+    }
   }
   __syncthreads();
 
-  // ---- P4: QMpp/QM2pp (0..MM), QMpu+G (64..), QM2pu/up/uu (128..), exterior (192..)
-  if (d >= 4 && t < MM) {
-    const int a = t / My, b = t % My, pe = a * NS + b;
-    (void)a;
-    (void)b;
-    const T s2v = nchunk_bif(d) > 0 ? S[SI_BIF * BLK + pe] * clamp_p2<T>(EA(d - 4) - Ed) : (T)0;
-    const T v = en[EN_EC] * QBo[pe] + s2v;
-    p.QM2pp[c * BLK + pe] = s2v;
-    p.QMpp[c * BLK + pe] = v;
-    lmax = fmax(lmax, fmax((double)fabs(v), (double)fabs(s2v)));
-  } else if (d >= 5 && t >= 64 && t < 64 + MM) {
-    const int e = t - 64, a = e / My, b = e % My, pe = a * NS + b;
-    const T F1 = clamp_p2<T>(EA(d - 1) - Ed), eb = en[EN_EB];
-    const T *Xr = S + SI_XY1 * BLK, *mpp = S + SI_ML * BLK, *mpu = S + (SI_ML + 1) * BLK;
-    const T u = eb * F1 * (s2<false, false>(mpp, Xr + XPU * BLK, a, b, Mv) + s2<false, false>(mpu, Xr + XUU * BLK, a, b, Mv));
-    const T gg = F1 * (s2<false, false>(mpp, Xr + XPP * BLK, a, b, Mv) + s2<false, false>(mpu, Xr + XUP * BLK, a, b, Mv));
-    p.QMpu[c * BLK + pe] = u;
-    p.G[c * BLK + pe] = gg;
-    lmax = fmax(lmax, fmax((double)fabs(u), (double)fabs(gg)));
-  } else if (d >= 10 && t >= 128 && t < 128 + MM) {
-    const int e = t - 128, a = e / My, b = e % My, pe = a * NS + b;
-    const T F1 = clamp_p2<T>(EA(d - 1) - Ed), eb = en[EN_EB];
-    const T *Xr = S + SI_XY1 * BLK, *Xl = S + SI_XX * BLK;
-    const T *q2pp = S + (SI_ML + 2) * BLK, *q2pu = S + (SI_ML + 3) * BLK;
-    const T *r_up = S + SI_MR * BLK, *r_pp = S + (SI_MR + 1) * BLK, *r_uu = S + (SI_MR + 2) * BLK,
-            *r_pu = S + (SI_MR + 3) * BLK;
-    const T pu = eb * F1 * (s2<false, false>(q2pp, Xr + XPU * BLK, a, b, Mv) + s2<false, false>(q2pu, Xr + XUU * BLK, a, b, Mv));
-    const T up = eb * F1 * (s2<false, false>(Xl + XUU * BLK, r_up, a, b, M1) + s2<false, false>(Xl + XUP * BLK, r_pp, a, b, M1));
-    const T uu = eb * F1 * (s2<false, false>(Xl + XUU * BLK, r_uu, a, b, M1) + s2<false, false>(Xl + XUP * BLK, r_pu, a, b, M1));
-    p.QM2pu[c * BLK + pe] = pu;
-    p.QM2up[c * BLK + pe] = up;
-    p.QM2uu[c * BLK + pe] = uu;
-    lmax = fmax(lmax, fmax((double)fabs(pu), fmax((double)fabs(up), (double)fabs(uu))));
-  } else if (x == 0 && t >= 192 && t < 192 + MP(0) * My) {
-    // ---- exterior prefix [0, d]
-    const int M0 = MP(0), e = t - 192, a = e / My, b = e % My, pe = a * NS + b;
-    T *q5u = p.Q5U + (size_t)d * BLK, *q5p = p.Q5P + (size_t)d * BLK;
-    if (d == 0) {
-      q5u[pe] = (a == b) ? (T)1 : (T)0;
-      q5p[pe] = 0;
-      lmax = fmax(lmax, 1.0);
-    } else {
-      const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
-      const T *Xr = S + SI_XY1 * BLK;
-      const T *pu = S + SI_Q5U * BLK, *pp = S + SI_Q5P * BLK;
-      const T gg = F1 * (s2<false, false>(pu, Xr + XUP * BLK, a, b, Mv) + s2<false, false>(pp, Xr + XPP * BLK, a, b, Mv));
-      const T u = F1 * (s2<false, false>(pu, Xr + XUU * BLK, a, b, Mv) + s2<false, false>(pp, Xr + XPU * BLK, a, b, Mv));
-      p.Gx[(size_t)d * BLK + pe] = gg;
-      q5u[pe] = u;
-      T v = (d >= 4 ? QBo[pe] : (T)0);
-      if (nchunk_ext(d) > 0) v += S[SI_BIFX * BLK + pe] * clamp_p2<T>(EA(d - 4) - Ed);
-      // split points k = 1..3 use QB[k][d] of diagonals d-1..d-3
-      for (int k = 1; k <= 3 && k <= d - 4; k++)
-        v += clamp_p2<T>(EA(k) + EA(d - k) - Ed) *
-             s2<false, false>(S + (SI_GXK + k - 1) * BLK, S + (SI_QBK + k - 1) * BLK, a, b, MP(k));
-      q5p[pe] = v;
-      lmax = fmax(lmax, fmax((double)fabs(gg), fmax((double)fabs(u), (double)fabs(v))));
+  // ---------------- phase B: HB, QB, QMpp, QM2pp, exterior Q5P per entry
+  // HB: GHB consecutive threads per entry split the interior sizes and bulge parts
+  {
+    constexpr int GHB = LM::GHB;
+    const int e = t / GHB, g = t % GHB, a = e / NS, b = e % NS;
+    T v = 0;
+    if (e < BLK && d >= 2) {
+      const T tmo = en[EN_TM + BASE(x, a) * 4 + BASE(y, b)];
+      for (int L = 2 + g; L <= Lmax; L += GHB) {
+        const T wl = en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed);
+        const T yv = (L == 2) ? O[LO_XI * BLK + e] : O[(LO_YY + L - 3) * BLK + e];
+        v = fma(wl * tmo, yv, v);
+      }
+      for (int j = g; j < NLT_BU; j += GHB) v += O[(LO_BU + j) * BLK + e];
+      if (g == 0) v = fma(p.eHL[d + 1] * clamp_p2<T>(-Ed) * tmo, O[LO_CH * BLK + e], v);
+    }
+#pragma unroll
+    for (int o = 1; o < GHB; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (e < BLK && g == 0) {
+      O[LO_HB * BLK + e] = v;
+      lmax = fmax(lmax, (double)fabs(v));
+    }
+  }
+  if (t >= LM::QB0 && t < LM::QB0 + BLK) {
+    const int e = t - LM::QB0, a = e / NS, b = e % NS;
+    T qb = 0;
+    if (d >= 4) {
+      const int pto = pair_type(BASE(x, a), BASE(y, b));
+      if (pto >= 0) {
+        T v = O[LO_QBH * BLK + e];
+#pragma unroll
+        for (int j = 0; j < NLT_QBS; j++) v += O[(LO_QBS + j) * BLK + e];
+        v += en[EN_EA] * en[EN_EC] * (O[LO_QBM * BLK + e] + O[(LO_QBM + 1) * BLK + e]);
+        qb = v * clamp_p2<T>(EA(d - 2) - Ed);
+      }
+      O[LO_QB * BLK + e] = qb;
+      const T s2v = S[SI_BIF * BLK + e] * clamp_p2<T>(EA(d - 4) - Ed);
+      const T mpp = en[EN_EC] * qb + s2v;
+      O[LO_QM2PP * BLK + e] = s2v;
+      O[LO_QMPP * BLK + e] = mpp;
+      lmax = fmax(lmax, fmax((double)fabs(qb), fmax((double)fabs(mpp), (double)fabs(s2v))));
+    }
+    if (x == 0) {
+      T v;
+      if (d == 0) {
+        v = 0;
+        lmax = fmax(lmax, 1.0);
+      } else {
+        v = qb + S[SI_BIFX * BLK + e] * clamp_p2<T>(EA(d - 4) - Ed) + O[LO_Q5K * BLK + e];
+        lmax = fmax(lmax, (double)fabs(v));
+      }
+      O[LO_Q5P * BLK + e] = v;
     }
   }
 
-  // ---- diagonal maximum for the next exponent
   lmax = warp_max(lmax);
   if (lane == 0) smax[w] = lmax;
   __syncthreads();
+
+  // ---------------- results to their tables, 16 bytes per thread and step
+  {
+    constexpr int CH16 = BLK * (int)sizeof(T) / 16;
+    using V = typename Vec16<T>::type;
+    for (int it = t; it < 45 * CH16; it += NTT) {
+      const int k = it / CH16, q = it - k * CH16;
+      int slot;
+      T *dst = nullptr;
+      if (k == 0) {
+        slot = LO_CH;
+        dst = p.CH + c * BLK;
+      } else if (k == 1) {
+        slot = LO_XI;
+        if (d >= 6) dst = p.XI + c * BLK;
+      } else if (k == 2) {  // YY_2 is XI itself
+        slot = LO_XI;
+        if (d >= 6) dst = p.YY + (c * NYY) * BLK;
+      } else if (k < 31) {  // YY_L, L = 3..30
+        const int L = k;
+        slot = LO_YY + L - 3;
+        if (d >= 6 && L <= Lmax) dst = p.YY + (c * NYY + (L - 2)) * BLK;
+      } else if (k == 31) {
+        slot = LO_HB;
+        if (d >= 2) dst = p.HB + c * BLK;
+      } else if (k == 32) {
+        slot = LO_QB;
+        if (d >= 4) dst = p.QB + c * BLK;
+      } else if (k == 33) {
+        slot = LO_QMPP;
+        if (d >= 4) dst = p.QMpp + c * BLK;
+      } else if (k == 34) {
+        slot = LO_QM2PP;
+        if (d >= 4) dst = p.QM2pp + c * BLK;
+      } else if (k == 35) {
+        slot = LO_QMPU;
+        if (d >= 5) dst = p.QMpu + c * BLK;
+      } else if (k == 36) {
+        slot = LO_G;
+        if (d >= 5) dst = p.G + c * BLK;
+      } else if (k < 40) {
+        slot = LO_M2PU + k - 37;
+        T *tab[3] = {p.QM2pu, p.QM2up, p.QM2uu};
+        if (d >= 10) dst = tab[k - 37] + c * BLK;
+      } else if (k == 40) {
+        slot = LO_GX;
+        if (x == 0 && d >= 1) dst = p.Gx + (size_t)d * BLK;
+      } else if (k == 41) {
+        slot = LO_Q5U;
+        if (x == 0) dst = p.Q5U + (size_t)d * BLK;
+      } else if (k == 42) {
+        slot = LO_Q5P;
+        if (x == 0) dst = p.Q5P + (size_t)d * BLK;
+      } else {
+        slot = 0;
+      }
+      if (dst) reinterpret_cast<V *>(dst)[q] = reinterpret_cast<const V *>(O + (size_t)slot * BLK)[q];
+    }
+  }
+  // ---- diagonal maximum for the next exponent
   if (t == 0) {
     double m = 0;
     for (int k = 0; k < NTT / 32; k++) m = fmax(m, smax[k]);
@@ -461,9 +701,9 @@ __global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) 
   in_light_cell<T, NTT>(p, bb, d, blockIdx.x, smem_raw);
 }
 
-template <typename T, int NTT = NT>
+template <typename T, int NTT = NT_IN>
 constexpr size_t in_light_smem() {
-  return ((size_t)(SI_N + 4 + NYY + 4) * BLK + NTT) * sizeof(T);
+  return (size_t)(SI_N + LO_N) * BLK * sizeof(T);
 }
 
 }  // namespace cf

@@ -299,10 +299,9 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gin) return CF_OK;
   const int n = p->n;
   const int cap_bif = offchain_ctas(p, 64);
-  const size_t smem = in_light_smem<T, NT>(), smemw = in_light_smem<T, NT_WIDE>();
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smemw));
+  const size_t smem = in_light_smem<T, NT_IN>();
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   cudaGraphNode_t mset;
@@ -337,11 +336,10 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     deps[nd++] = (d == 0) ? mset : k2[d - 1];
     if (d >= 8) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
-    const bool wide = false;  // the inside is fastest with NT threads on every diagonal
-    kp.func = wide ? (void *)k_in_light<T, NT_WIDE> : (void *)k_in_light<T, NT>;
+    kp.func = (void *)k_in_light<T, NT_IN>;
     kp.gridDim = dim3(n - d);
-    kp.blockDim = dim3(wide ? NT_WIDE : NT);
-    kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
+    kp.blockDim = dim3(NT_IN);
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
@@ -531,6 +529,7 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_in, p->ev[0], p->ev[1]));
   p->l_in = launches;
+  if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "inside: a bounded wait for staged inputs gave up");
   if (err || !(zm > 0) || !std::isfinite(zm))
     return fail(p, CF_ENUMERIC, "inside: non-finite or zero partition function after scaling");
   *logZ = std::log(zm) + e_last * std::log(2.0) - p->log_scale;

@@ -268,6 +268,45 @@ __device__ __forceinline__ void row_mmm(T (&r)[NS], const T *A, const T *B, cons
   row_mm(t, A, B, a, (T)1);
   row_acc(r, t, C, f);
 }
+// r += f * (row a of A^T) . B  = f * sum_s A[s][a] B[s][.]
+template <typename T>
+__device__ __forceinline__ void row_tmm(T (&r)[NS], const T *A, const T *B, int a, T f) {
+  T av[NS];
+#pragma unroll
+  for (int s = 0; s < NS; s++) av[s] = A[s * NS + a];
+  row_acc(r, av, B, f);
+}
+// r += f * (row a of A) . B^T  = f * sum_s A[a][s] B[.][s]
+template <typename T>
+__device__ __forceinline__ void row_mmt(T (&r)[NS], const T *A, const T *B, int a, T f) {
+  T av[NS];
+  ld_row(av, A + a * NS);
+#pragma unroll
+  for (int s = 0; s < NS; s++) av[s] *= f;
+#pragma unroll
+  for (int b = 0; b < NS; b++) {
+    T bv[NS];
+    ld_row(bv, B + b * NS);
+    T acc = r[b];
+#pragma unroll
+    for (int s = 0; s < NS; s++) acc = fma(av[s], bv[s], acc);
+    r[b] = acc;
+  }
+}
+// atomically add a block row to global memory, skipping exact-zero pairs
+__device__ __forceinline__ void red_row(float *dst, const float (&r)[NS]) {
+#pragma unroll
+  for (int i = 0; i < NS / 2; i++)
+    if (r[2 * i] != 0.f || r[2 * i + 1] != 0.f)
+      asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst + 2 * i), "f"(r[2 * i]), "f"(r[2 * i + 1])
+                   : "memory");
+}
+__device__ __forceinline__ void red_row(double *dst, const double (&r)[NS]) {
+#pragma unroll
+  for (int i = 0; i < NS; i++)
+    if (r[i] != 0.0) atomicAdd(dst + i, r[i]);
+}
+
 template <typename T>
 __device__ __forceinline__ void row_zero(T (&r)[NS]) {
 #pragma unroll

@@ -624,50 +624,44 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   __syncthreads();
   const T *hHB = S + SS_HHB * BLK, *HY = S + SS_HY * BLK;
 
-  // ---------------- bulge scatters into shorter chains
-  if (d >= 5) {
-    for (int it = t; it < 2 * MAXLOOP * BLK; it += NT3) {
-      const int q = it / BLK, e = it % BLK, L = q / 2 + 1;
-      if (d - L < 4) continue;
-      if ((q & 1) == 0) {
-        // HB += QB[x][y-L] CH[y-L][y]  ->  hCH[y-L][y] += f QB^T hHB
-        const int Mr = MP(y - L);
-        if (e >= Mr * My) continue;
-        const int r = e / My, s2i = e % My;
-        const T v = wBu[L] * s2<true, false>(S + (SS_BQ3 + L - 1) * BLK, hHB, r, s2i, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, y - L, y) * BLK + r * NS + s2i, v);
-      } else {
-        // HB += CH[x][x+L] QB[x+L][y]  ->  hCH[x][x+L] += f hHB QB^T
-        const int Ms = MP(x + L);
-        if (e >= Mx * Ms) continue;
-        const int r = e / Ms, s2i = e % Ms;
-        const T v = wBu[L] * s2<false, true>(hHB, S + (SS_BQ5 + L - 1) * BLK, r, s2i, My);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, x, x + L) * BLK + r * NS + s2i, v);
-      }
-    }
-  }
-  // ---------------- interior scatters: hXI of diagonals d-L+2 (L >= 6), chains (L >= 3)
-  if (d >= 6) {
+  // ---------------- bulge and interior scatters, one block row per thread and step
+  //   bulge 3' (L = 1..30):  hCH[y-L][y] += wBu(L) QB[x][y-L]^T hHB
+  //   bulge 5' (L = 1..30):  hCH[x][x+L] += wBu(L) hHB QB[x+L][y]^T
+  //   interior (L = 3..Lmax, yl = y-L+2, yl-x >= 6):
+  //     hCH[yl][y] += XI[x][yl]^T hYY_L,  hXI[x][yl] += hYY_L CH[yl][y]^T (L >= 6:
+  //     the light kernel takes L = 3..5)
+  // Blocks are zero-padded, so each row runs over the full padded size.
+  {
     const int Lmax = min(MAXLOOP, d - 4);
-    for (int it = t; it < 2 * (Lmax - 2) * BLK; it += NT3) {
-      const int q = it / BLK, e = it % BLK, L = q / 2 + 3;
-      const int yl = y - L + 2;
-      if (yl - x < 6) continue;
-      const int Ml = MP(yl);
-      const T *hy = HY + (L - 2) * BLK;
-      if ((q & 1) == 0) {
-        // YY_L += XI[x][yl] CH[yl][y]  ->  hXI[x][yl] += hYY CH^T (L <= 5 done by the light kernel)
-        if (L < 3 + NCHL_LIGHT || e >= Mx * Ml) continue;
-        const int r = e / Ml, s2i = e % Ml;
-        const T v = s2<false, true>(hy, S + (SS_CHL + L - 3) * BLK, r, s2i, My);
-        if (v != (T)0) atomicAdd(p.hXI + cidx(n, x, yl) * BLK + r * NS + s2i, v);
-      } else {
-        // hCH[yl][y] += XI^T hYY
-        if (e >= Ml * My) continue;
-        const int r = e / My, s2i = e % My;
-        const T v = s2<true, false>(S + (SS_XIL + L - 3) * BLK, hy, r, s2i, Mx);
-        if (v != (T)0) atomicAdd(p.hCH + cidx(n, yl, y) * BLK + r * NS + s2i, v);
+    constexpr int NPROD = 4 * MAXLOOP;
+    for (int rt = t; rt < NS * NPROD; rt += NT3) {
+      const int q = rt / NS, a = rt - q * NS;
+      const int kind = q / MAXLOOP, L = q % MAXLOOP + 1;
+      T r[NS];
+      row_zero(r);
+      T *dst = nullptr;
+      if (kind == 0) {
+        if (d >= 5 && d - L >= 4) {
+          row_tmm(r, S + (SS_BQ3 + L - 1) * BLK, hHB, a, wBu[L]);
+          dst = p.hCH + cidx(n, y - L, y) * BLK;
+        }
+      } else if (kind == 1) {
+        if (d >= 5 && d - L >= 4) {
+          row_mmt(r, hHB, S + (SS_BQ5 + L - 1) * BLK, a, wBu[L]);
+          dst = p.hCH + cidx(n, x, x + L) * BLK;
+        }
+      } else if (d >= 6 && L >= 3 && L <= Lmax && y - L + 2 - x >= 6) {
+        const int yl = y - L + 2;
+        const T *hy = HY + (L - 2) * BLK;
+        if (kind == 2) {
+          row_tmm(r, S + (SS_XIL + L - 3) * BLK, hy, a, (T)1);
+          dst = p.hCH + cidx(n, yl, y) * BLK;
+        } else if (L >= 3 + NCHL_LIGHT) {
+          row_mmt(r, hy, S + (SS_CHL + L - 3) * BLK, a, (T)1);
+          dst = p.hXI + cidx(n, x, yl) * BLK;
+        }
       }
+      if (dst) red_row(dst + a * NS, r);
     }
   }
 

@@ -254,6 +254,9 @@ __device__ __forceinline__ T s3(const T *A, const T *B, const T *C, int a, int b
 // Ed), codon-state counts of positions within 35 of x or y, bases of
 // x-1..x+1 and y-1..y+1.  Other indices fall back to global memory.
 #define EA(k) ((k) == d ? Ed : (((k) >= d - 47 && (k) <= d + 48) ? sE[(k) - (d - 47)] : __ldcg(p.E + (k))))
+// EA for indices known to lie in d-47..d (no global fallback, so that no load
+// of the exponent array is ever issued on the cell's critical path)
+#define EAS(k) ((k) == d ? Ed : sE[(k) - (d - 47)])
 #define MP(q) (((q) >= x - 35 && (q) <= x + 36) ? sMx[(q) - (x - 35)] : (((q) >= y - 35 && (q) <= y + 36) ? sMy[(q) - (y - 35)] : p.Mp[q]))
 #define BASE(q, a) (((q) >= x - 1 && (q) <= x + 1) ? sBx[(q) - (x - 1)][a] : sBy[(q) - (y - 1)][a])
 

@@ -332,23 +332,31 @@ __device__ __forceinline__ T row_absmax(const T (&r)[NS]) {
 //            QM2pp and the exterior Q5P, entry by entry.
 // Staged input slots that a diagonal does not use are zero-filled, so every
 // task runs unconditionally; loop weights that do not apply are zero.
-enum : int {
-  LT_CH = 0, LT_XI = 1, LT_YY = 2,            // YY_L, L = 3..30: tasks 2..29
-  LT_BU = 30, NLT_BU = 12,                    // bulges: tasks 30..41
-  LT_QBH = 42, LT_QBS = 43, NLT_QBS = 3,      // QB: hairpin-interior term, stack in 3 parts
-  LT_QBM = 46,                                // QB: multiloop, 2 parts (46, 47)
-  LT_QMPU = 48, LT_G = 49, LT_M2PU = 50, LT_M2UP = 51, LT_M2UU = 52,
-  LT_GX = 53, LT_Q5U = 54, LT_Q5K = 55,       // exterior (x == 0)
-  NLT = 56
-};
-// shared result slots (blocks): phase A writes 0..LO_Q5U, phase B the rest;
-// every final result is copied to its table at the end of the cell
+// Phase A runs 16 groups of 5 tasks, one warp per group (lanes 0..29: task
+// i = lane / 6, block row lane % 6), so that every warp follows one code path:
+//   groups 0..5   interior partial sums YY_L, L = 3 + 5g + i (L <= 30)
+//   groups 6..11  bulge pairs: task j = 5(g-6) + i, side j & 1 (0: 3', 1: 5'),
+//                 sizes L = 2(j >> 1) + 1 and the next one
+//   group 12      chain, XI, QB hairpin-interior term, QB multiloop (2 parts)
+//   group 13      QB stack for outer pair types P = 0..4 (P = 5 in group 15)
+//   group 14      QMpu, G, QM2pu, QM2up, QM2uu
+//   group 15      exterior Gx, Q5U, Q5P split points 1..3 (cell x = 0), stack P = 5
+constexpr int NGROUP = 16;
+// shared result slots (blocks); every final result is copied to its table at
+// the end of the cell
 enum : int {
   LO_CH = 0, LO_XI = 1, LO_YY = 2,            // YY_L at LO_YY + L - 3
-  LO_BU = 30, LO_QBH = 42, LO_QBS = 43, LO_QBM = 46, LO_Q5K = 48,
-  LO_QMPU = 49, LO_G = 50, LO_M2PU = 51, LO_M2UP = 52, LO_M2UU = 53, LO_GX = 54, LO_Q5U = 55,
-  LO_HB = 56, LO_QB = 57, LO_QMPP = 58, LO_QM2PP = 59, LO_Q5P = 60, LO_N = 61
+  LO_BU = 30, NLO_BU = 30, LO_QBH = 60, LO_QBS = 61, LO_QBM = 67, LO_Q5K = 69,
+  LO_QMPU = 70, LO_G = 71, LO_M2PU = 72, LO_M2UP = 73, LO_M2UU = 74, LO_GX = 75, LO_Q5U = 76,
+  LO_HB = 77, LO_QB = 78, LO_QMPP = 79, LO_QM2PP = 80, LO_Q5P = 81, LO_N = 82
 };
+
+// pair type of bases (x, y) from a packed table: 3 bits per entry, 7 = no pair
+__device__ __forceinline__ int pair_type_lut(int bx, int by) {
+  constexpr unsigned long long PT = 0xf7b9d7e7f1ffull;
+  const int v = (int)((PT >> (3 * (bx * 4 + by))) & 7ull);
+  return v;
+}
 
 // Threads per entry in the HB sum of phase B, and the first thread of the
 // QB/QMpp entries (a warp boundary after the HB threads).
@@ -359,6 +367,39 @@ struct LightMap {
   static_assert(QB0 + BLK <= NTT, "phase B needs one thread per QB entry");
 };
 
+// Results written by the light cell: entry k of the copy-out list reads
+// shared slot light_slot(k) and goes to light_dst(k) (nullptr: not written on
+// this diagonal).
+constexpr int NCOPY = 43;
+__device__ __forceinline__ int light_slot(int k) {
+  if (k <= 2) return k == 0 ? LO_CH : LO_XI;       // CH, XI, YY_2 (= XI)
+  if (k < 31) return LO_YY + k - 3;                // YY_L, L = 3..30
+  const int rest[12] = {LO_HB, LO_QB, LO_QMPP, LO_QM2PP, LO_QMPU, LO_G, LO_M2PU, LO_M2UP, LO_M2UU, LO_GX, LO_Q5U, LO_Q5P};
+  return rest[k - 31];
+}
+template <typename T>
+__device__ __forceinline__ T *light_dst(const DP<T> &p, int k, int x, int d, size_t c) {
+  const int Lmax = min(MAXLOOP, d - 4);
+  if (k == 0) return p.CH + c * BLK;
+  if (k == 1) return d >= 6 ? p.XI + c * BLK : nullptr;
+  if (k < 31) return (d >= 6 && k <= Lmax) ? p.YY + (c * NYY + (k - 2)) * BLK : nullptr;  // YY_k
+  switch (k) {
+    case 31: return d >= 2 ? p.HB + c * BLK : nullptr;
+    case 32: return d >= 4 ? p.QB + c * BLK : nullptr;
+    case 33: return d >= 4 ? p.QMpp + c * BLK : nullptr;
+    case 34: return d >= 4 ? p.QM2pp + c * BLK : nullptr;
+    case 35: return d >= 5 ? p.QMpu + c * BLK : nullptr;
+    case 36: return d >= 5 ? p.G + c * BLK : nullptr;
+    case 37: return d >= 10 ? p.QM2pu + c * BLK : nullptr;
+    case 38: return d >= 10 ? p.QM2up + c * BLK : nullptr;
+    case 39: return d >= 10 ? p.QM2uu + c * BLK : nullptr;
+    case 40: return (x == 0 && d >= 1) ? p.Gx + (size_t)d * BLK : nullptr;
+    case 41: return x == 0 ? p.Q5U + (size_t)d * BLK : nullptr;
+    case 42: return x == 0 ? p.Q5P + (size_t)d * BLK : nullptr;
+  }
+  return nullptr;
+}
+
 template <typename T, int NTT>
 __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int x,
                                               unsigned char *smem_raw) {
@@ -367,17 +408,22 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   T *O = S + (size_t)SI_N * BLK;       // [LO_N][36] phase A results
   __shared__ int sEd;
   __shared__ double smax[NTT / 32];
-  __shared__ int sE[96], sBx[3][NS], sBy[3][NS];
+  __shared__ int sE[96], sE0[4], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N];
   __shared__ __align__(8) unsigned long long sbar;
+  __shared__ T *sDst[NCOPY];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int y = x + d;
+  const size_t c = cidx(n, x, y);
   // per-cell context, each value loaded by its own thread before any copy is
   // issued so that all loads are in flight together: exponents of diagonals
   // d-47..d-1, bases of x-1..x+1 and y-1..y+1, energy factors, and the
   // largest mantissa and exponent of diagonal d-1 (last thread)
-  static_assert(NTT > EN_N && NTT > 96 + 6 * NS, "one context value per thread");
+  static_assert(NTT > EN_N && NTT > 100 + 6 * NS, "one context value per thread");
+  // the barrier is initialised first: its release fence would otherwise wait
+  // for the context loads below
+  if (t == 0) mbar_init(&sbar, 1);
   int cE = 0, cB = 0;
   T cEn = 0;
   unsigned long long cMax = 0;
@@ -389,11 +435,13 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
     const int q = (side == 0 ? x : y) - 1 + r;
     if (q >= 0 && q < n) cB = p.base[q * NS + a];
+  } else if (t >= 96 + 6 * NS && t < 100 + 6 * NS) {
+    const int k = t - 96 - 6 * NS;  // exponents of diagonals 0..3 (exterior split points)
+    if (k < d) cE = __ldcg(p.E + k);
   } else if (t == NTT - 1 && d > 0) {
     cMax = __ldcg(p.dmax + d - 1);
     cE = __ldcg(p.E + d - 1);
   }
-  if (t == 0) mbar_init(&sbar, 1);
   __syncthreads();
   // Staging: one TMA bulk copy per input block (the interior partial sums
   // YY_{L-1}[x+1][y], L = 3..Lmax, are contiguous and go as one copy); slots
@@ -416,6 +464,11 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
       }
     }
   }
+  // destinations of the results (copied out at the end of the cell)
+  if (t < NCOPY) sDst[t] = light_dst(p, t, x, d, c);
+  __syncthreads();
+  if (t == 0) mbar_arrive(&sbar);
+  // the context reaches shared memory while the copies are in flight
   if (t < EN_N) sEn[t] = cEn;
   if (t < 96) {
     sE[t] = cE;
@@ -423,6 +476,8 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
     if (side == 0) sBx[r][a] = cB;
     else sBy[r][a] = cB;
+  } else if (t < 100 + 6 * NS) {
+    sE0[t - 96 - 6 * NS] = cE;
   } else if (t == NTT - 1) {
     int e = 0;
     if (d > 0) {
@@ -436,176 +491,172 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     sEd = e;
     if (x == 0) p.E[d] = e;
   }
-  __syncthreads();
-  if (t == 0) mbar_arrive(&sbar);
-  if (!mbar_wait(&sbar, 0, p.err)) return;
+  if (!__syncthreads_and(mbar_wait(&sbar, 0, p.err))) return;
   const int Ed = sEd;
   const T *en = sEn;
-  const size_t c = cidx(n, x, y);
   const T *Tx = S + SI_TX * BLK, *Ty1 = S + SI_TY1 * BLK;
   const T *Xl = S + SI_XX * BLK, *Xr = S + SI_XY1 * BLK;
   const int Lmax = min(MAXLOOP, d - 4);
   double lmax = 0.0;
 
-  // ---------------- phase A: one block row per thread and step
-  for (int rt = t; rt < NS * NLT; rt += NTT) {
-    const int task = rt / NS, a = rt - task * NS;
+  // ---------------- phase A: one warp per group of tasks
+  // Every task but the stack is a sum of at most three terms
+  //   f * (row a of A) . B [. C]
+  // described by pointers, so that the product code exists once.
+  for (int vw = w; vw < NGROUP; vw += NTT / 32) {
+    const int i = lane / NS, a = lane - i * NS;
+    if (i >= 5) continue;
+    const T *A0 = nullptr, *B0 = nullptr, *C0 = nullptr, *A1 = nullptr, *B1 = nullptr, *C1 = nullptr;
+    const T *A2 = nullptr, *B2 = nullptr;
+    T f0 = 1, f1 = 1, f2 = 1;
+    int oslot = -1, post = 0;  // post: 1 identity (d = 0), 2 XI mismatch factor, 3 stack
+    bool scaled = false;       // counts toward the diagonal maximum
+    if (vw < 6) {
+      const int L = 3 + 5 * vw + i;
+      if (L > MAXLOOP) continue;
+      if (d >= 6 && L <= Lmax) {
+        A0 = Tx, B0 = S + (SI_YYP + L - 3) * BLK;
+        A1 = S + (SI_XIL + L - 3) * BLK, B1 = S + (SI_CHL + L - 3) * BLK;
+      }
+      oslot = LO_YY + L - 3;  // relative to 2^{E[d-L+2]}
+    } else if (vw < 12) {
+      const int j = 5 * (vw - 6) + i, side = j & 1, L = 2 * (j >> 1) + 1;
+      if (d - L >= 4) {
+        A0 = S + ((side ? SI_BC5 : SI_BQ3) + L - 1) * BLK, B0 = S + ((side ? SI_BQ5 : SI_BC3) + L - 1) * BLK;
+        f0 = en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed);
+      }
+      if (d - L - 1 >= 4) {
+        A1 = S + ((side ? SI_BC5 : SI_BQ3) + L) * BLK, B1 = S + ((side ? SI_BQ5 : SI_BC3) + L) * BLK;
+        f1 = en[EN_BU + L + 1] * clamp_p2<T>(EAS(d - L - 1) - Ed);
+      }
+      oslot = LO_BU + j;
+    } else if (vw == 12) {
+      if (i == 0) {  // chain
+        if (d == 0) post = 1;
+        else A0 = Tx, B0 = S + SI_CHN * BLK;
+        oslot = LO_CH;
+      } else if (i == 1) {  // XI
+        if (d >= 6) A0 = Tx, B0 = S + SI_QBI * BLK, C0 = Ty1, f0 = clamp_p2<T>(EAS(d - 2) - Ed), post = 2;
+        oslot = LO_XI;
+        scaled = true;
+      } else if (i == 2) {  // QB: hairpin-interior term
+        if (d >= 4) A0 = Tx, B0 = S + SI_HBI * BLK, C0 = Ty1;
+        oslot = LO_QBH;
+      } else {  // QB: multiloop
+        if (d >= 11) {
+          const T *q2 = S + SI_Q2I * BLK, *xl = Xl + (i == 3 ? XPU : XPP) * BLK;
+          A0 = xl, B0 = q2 + (i == 3 ? 0 : 2) * BLK, C0 = Xr + XUP * BLK;
+          A1 = xl, B1 = q2 + (i == 3 ? 1 : 3) * BLK, C1 = Xr + XPP * BLK;
+        }
+        oslot = LO_QBM + i - 3;
+      }
+    } else if (vw == 13 || (vw == 15 && i == 3)) {
+      oslot = LO_QBS + (vw == 13 ? i : 5);
+      if (d >= 6) post = 3;
+    } else if (vw == 14) {
+      // QMpu, G (inner state y-1), QM2pu, QM2up, QM2uu
+      const T F1 = clamp_p2<T>(EAS(d - 1) - Ed), eb = en[EN_EB];
+      if (i < 2) {
+        if (d >= 5) {
+          f0 = f1 = i == 0 ? eb * F1 : F1;
+          A0 = S + SI_ML * BLK, B0 = Xr + (i == 0 ? XPU : XPP) * BLK;
+          A1 = S + (SI_ML + 1) * BLK, B1 = Xr + (i == 0 ? XUU : XUP) * BLK;
+        }
+      } else if (d >= 10) {
+        f0 = f1 = eb * F1;
+        if (i == 2) {
+          A0 = S + (SI_ML + 2) * BLK, B0 = Xr + XPU * BLK;
+          A1 = S + (SI_ML + 3) * BLK, B1 = Xr + XUU * BLK;
+        } else {
+          A0 = Xl + XUU * BLK, B0 = S + (SI_MR + (i == 3 ? 0 : 2)) * BLK;
+          A1 = Xl + XUP * BLK, B1 = S + (SI_MR + (i == 3 ? 1 : 3)) * BLK;
+        }
+      }
+      oslot = LO_QMPU + i;
+      scaled = true;
+    } else {
+      // exterior prefix [0, d] (cell x = 0): rows are the states of position 0
+      if (x != 0 || i > 2) continue;
+      const T *pu = S + SI_Q5U * BLK, *pp = S + SI_Q5P * BLK;
+      const T F1 = clamp_p2<T>(EAS(d - 1) - Ed);
+      if (i < 2) {
+        if (d == 0 && i == 1) post = 1;
+        if (d >= 1) {
+          f0 = f1 = F1;
+          A0 = pu, B0 = Xr + (i == 0 ? XUP : XUU) * BLK;
+          A1 = pp, B1 = Xr + (i == 0 ? XPP : XPU) * BLK;
+        }
+        oslot = i == 0 ? LO_GX : LO_Q5U;
+        scaled = true;
+      } else {
+        // split points k = 1..3 use QB[k][d] of diagonals d-1..d-3
+        if (d >= 5) A0 = S + SI_GXK * BLK, B0 = S + SI_QBK * BLK, f0 = clamp_p2<T>(sE0[1] + EAS(d - 1) - Ed);
+        if (d >= 6) A1 = S + (SI_GXK + 1) * BLK, B1 = S + (SI_QBK + 1) * BLK, f1 = clamp_p2<T>(sE0[2] + EAS(d - 2) - Ed);
+        if (d >= 7) A2 = S + (SI_GXK + 2) * BLK, B2 = S + (SI_QBK + 2) * BLK, f2 = clamp_p2<T>(sE0[3] + EAS(d - 3) - Ed);
+        oslot = LO_Q5K;
+      }
+    }
     T r[NS];
     row_zero(r);
-    int oslot = -1;      // shared result slot
-    bool scaled = true;  // counts toward the diagonal maximum
-    if (task == LT_CH) {
-      if (d == 0) {
-        const int Mx = p.Mp[x];
+    if (post == 3) {
+      // QB stack for outer pair type P: sum over inner states (a2, b2) of
+      // Tx[a][a2] QBI[a2][b2] stk[P][pt(a2, b2)] Ty1[b2][b], kept where the
+      // outer pair (a, b) has type P
+      const int P = oslot - LO_QBS;
+      const int bxa = BASE(x, a);
+      bool any = false;
 #pragma unroll
-        for (int b = 0; b < NS; b++) r[b] = (a == b && a < Mx) ? (T)1 : (T)0;
-      } else {
-        row_mm(r, Tx, S + SI_CHN * BLK, a, (T)1);
+      for (int b = 0; b < NS; b++) any |= pair_type_lut(bxa, BASE(y, b)) == P;
+      if (any) {
+        const T *qin = S + SI_QBI * BLK;
+        T tx[NS], t1[NS];
+        ld_row(tx, Tx + a * NS);
+        row_zero(t1);
+#pragma unroll
+        for (int a2 = 0; a2 < NS; a2++) {
+          const int ba = BASE((x + 1), a2);
+          T qv[NS];
+          ld_row(qv, qin + a2 * NS);
+#pragma unroll
+          for (int b2 = 0; b2 < NS; b2++) {
+            const int pti = pair_type_lut(ba, BASE((y - 1), b2));
+            const T st = pti < 6 ? en[EN_STK + P * 6 + pti] : (T)0;
+            t1[b2] = fma(tx[a2] * qv[b2], st, t1[b2]);
+          }
+        }
+        row_acc(r, t1, Ty1, (T)1);
+#pragma unroll
+        for (int b = 0; b < NS; b++)
+          if (pair_type_lut(bxa, BASE(y, b)) != P) r[b] = (T)0;
       }
-      oslot = LO_CH;
-      scaled = false;
-    } else if (task == LT_XI) {
-      if (d >= 6) {
-        row_mmm(r, Tx, S + SI_QBI * BLK, Ty1, a, clamp_p2<T>(EA(d - 2) - Ed));
+    } else if (post == 1) {
+      const int M = p.Mp[x];
+#pragma unroll
+      for (int b = 0; b < NS; b++) r[b] = (a == b && a < M) ? (T)1 : (T)0;
+    } else {
+#pragma unroll 1
+      for (int q = 0; q < 3; q++) {
+        const T *A = q == 0 ? A0 : (q == 1 ? A1 : A2), *B = q == 0 ? B0 : (q == 1 ? B1 : B2);
+        const T *C = q == 0 ? C0 : (q == 1 ? C1 : nullptr);
+        const T f = q == 0 ? f0 : (q == 1 ? f1 : f2);
+        if (!A) continue;
+        if (C) {
+          T t[NS];
+          row_zero(t);
+          row_mm(t, A, B, a, f);
+          row_acc(r, t, C, (T)1);
+        } else {
+          row_mm(r, A, B, a, f);
+        }
+      }
+      if (post == 2) {
         const int bxa = BASE(x, a);
 #pragma unroll
         for (int b = 0; b < NS; b++) r[b] *= en[EN_TM + BASE(y, b) * 4 + bxa];
       }
-      oslot = LO_XI;
-    } else if (task < LT_BU) {
-      const int L = task - LT_YY + 3;
-      if (d >= 6 && L <= Lmax) {
-        row_mm(r, Tx, S + (SI_YYP + L - 3) * BLK, a, (T)1);
-        row_mm(r, S + (SI_XIL + L - 3) * BLK, S + (SI_CHL + L - 3) * BLK, a, (T)1);
-      }
-      oslot = LO_YY + L - 3;
-      scaled = false;  // relative to 2^{E[d-L+2]}
-    } else if (task < LT_QBH) {
-      // bulges: side 3' (QB[x][y-L] CH[y-L][y]) for even j, 5' (CH[x][x+L] QB[x+L][y]) for odd
-      const int j = task - LT_BU, side = j & 1, L0 = (j >> 1) * 5 + 1;
-#pragma unroll
-      for (int L = L0; L < L0 + 5; L++) {
-        if (d - L < 4) break;
-        const T f = en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed);
-        if (side == 0)
-          row_mm(r, S + (SI_BQ3 + L - 1) * BLK, S + (SI_BC3 + L - 1) * BLK, a, f);
-        else
-          row_mm(r, S + (SI_BC5 + L - 1) * BLK, S + (SI_BQ5 + L - 1) * BLK, a, f);
-      }
-      oslot = LO_BU + j;
-      scaled = false;
-    } else if (task == LT_QBH) {
-      if (d >= 4) row_mmm(r, Tx, S + SI_HBI * BLK, Ty1, a, (T)1);
-      oslot = LO_QBH;
-      scaled = false;
-    } else if (task < LT_QBM) {
-      // stack: sum over inner states (a2, b2) with the factor of the
-      // (outer, inner) pair types; this part takes a2 in {2j, 2j+1}
-      if (d >= 6) {
-        const T *qin = S + SI_QBI * BLK;
-        int pto[NS];
-        const int bxa = BASE(x, a);
-#pragma unroll
-        for (int b = 0; b < NS; b++) pto[b] = pair_type(bxa, BASE(y, b));
-        const int j = task - LT_QBS;
-#pragma unroll
-        for (int q = 0; q < 2; q++) {
-          const int a2 = 2 * j + q;
-          const T tv = Tx[a * NS + a2];
-          if (tv != (T)0) {
-            const int ba = BASE((x + 1), a2);
-#pragma unroll
-            for (int b2 = 0; b2 < NS; b2++) {
-              const int pti = pair_type(ba, BASE((y - 1), b2));
-              const T u = tv * qin[a2 * NS + b2];
-              if (pti >= 0 && u != (T)0) {
-                T tyr[NS];
-                ld_row(tyr, Ty1 + b2 * NS);
-#pragma unroll
-                for (int b = 0; b < NS; b++)
-                  if (pto[b] >= 0) r[b] = fma(u * en[EN_STK + pto[b] * 6 + pti], tyr[b], r[b]);
-              }
-            }
-          }
-        }
-      }
-      oslot = LO_QBS + task - LT_QBS;
-      scaled = false;
-    } else if (task < LT_QMPU) {
-      if (d >= 11) {
-        const T *q2 = S + SI_Q2I * BLK;
-        if (task == LT_QBM) {
-          row_mmm(r, Xl + XPU * BLK, q2 + 0 * BLK, Xr + XUP * BLK, a, (T)1);
-          row_mmm(r, Xl + XPU * BLK, q2 + 1 * BLK, Xr + XPP * BLK, a, (T)1);
-        } else {
-          row_mmm(r, Xl + XPP * BLK, q2 + 2 * BLK, Xr + XUP * BLK, a, (T)1);
-          row_mmm(r, Xl + XPP * BLK, q2 + 3 * BLK, Xr + XPP * BLK, a, (T)1);
-        }
-      }
-      oslot = LO_QBM + task - LT_QBM;
-      scaled = false;
-    } else if (task == LT_QMPU || task == LT_G) {
-      if (d >= 5) {
-        const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
-        const T *mpp = S + SI_ML * BLK, *mpu = S + (SI_ML + 1) * BLK;
-        if (task == LT_QMPU) {
-          const T f = en[EN_EB] * F1;
-          row_mm(r, mpp, Xr + XPU * BLK, a, f);
-          row_mm(r, mpu, Xr + XUU * BLK, a, f);
-        } else {
-          row_mm(r, mpp, Xr + XPP * BLK, a, F1);
-          row_mm(r, mpu, Xr + XUP * BLK, a, F1);
-        }
-      }
-      oslot = task == LT_QMPU ? LO_QMPU : LO_G;
-    } else if (task <= LT_M2UU) {
-      if (d >= 10) {
-        const T f = en[EN_EB] * clamp_p2<T>(EA(d - 1) - Ed);
-        if (task == LT_M2PU) {
-          row_mm(r, S + (SI_ML + 2) * BLK, Xr + XPU * BLK, a, f);
-          row_mm(r, S + (SI_ML + 3) * BLK, Xr + XUU * BLK, a, f);
-        } else if (task == LT_M2UP) {
-          row_mm(r, Xl + XUU * BLK, S + SI_MR * BLK, a, f);
-          row_mm(r, Xl + XUP * BLK, S + (SI_MR + 1) * BLK, a, f);
-        } else {
-          row_mm(r, Xl + XUU * BLK, S + (SI_MR + 2) * BLK, a, f);
-          row_mm(r, Xl + XUP * BLK, S + (SI_MR + 3) * BLK, a, f);
-        }
-      }
-      oslot = LO_M2PU + task - LT_M2PU;
-    } else if (task < NLT && x == 0) {
-      // exterior prefix [0, d]: rows are the states of position 0
-      const T *pu = S + SI_Q5U * BLK, *pp = S + SI_Q5P * BLK;
-      if (task == LT_GX) {
-        if (d >= 1) {
-          const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
-          row_mm(r, pu, Xr + XUP * BLK, a, F1);
-          row_mm(r, pp, Xr + XPP * BLK, a, F1);
-        }
-        oslot = LO_GX;
-      } else if (task == LT_Q5U) {
-        if (d == 0) {
-          const int M0 = p.Mp[0];
-#pragma unroll
-          for (int b = 0; b < NS; b++) r[b] = (a == b && a < M0) ? (T)1 : (T)0;
-        } else {
-          const T F1 = clamp_p2<T>(EA(d - 1) - Ed);
-          row_mm(r, pu, Xr + XUU * BLK, a, F1);
-          row_mm(r, pp, Xr + XPU * BLK, a, F1);
-        }
-        oslot = LO_Q5U;
-      } else {
-        // split points k = 1..3 use QB[k][d] of diagonals d-1..d-3
-        for (int k = 1; k <= 3 && k <= d - 4; k++)
-          row_mm(r, S + (SI_GXK + k - 1) * BLK, S + (SI_QBK + k - 1) * BLK, a, clamp_p2<T>(EA(k) + EA(d - k) - Ed));
-        oslot = LO_Q5K;
-        scaled = false;
-      }
     }
-    if (oslot >= 0) {
-      st_row(O + (size_t)oslot * BLK + a * NS, r);
-      if (scaled) lmax = fmax(lmax, (double)row_absmax(r));
-    }
+    st_row(O + (size_t)oslot * BLK + a * NS, r);
+    if (scaled) lmax = fmax(lmax, (double)row_absmax(r));
   }
   __syncthreads();
 
@@ -618,11 +669,11 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     if (e < BLK && d >= 2) {
       const T tmo = en[EN_TM + BASE(x, a) * 4 + BASE(y, b)];
       for (int L = 2 + g; L <= Lmax; L += GHB) {
-        const T wl = en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed);
+        const T wl = en[EN_IN + L] * clamp_p2<T>(EAS(d - L + 2) - Ed);
         const T yv = (L == 2) ? O[LO_XI * BLK + e] : O[(LO_YY + L - 3) * BLK + e];
         v = fma(wl * tmo, yv, v);
       }
-      for (int j = g; j < NLT_BU; j += GHB) v += O[(LO_BU + j) * BLK + e];
+      for (int j = g; j < NLO_BU; j += GHB) v += O[(LO_BU + j) * BLK + e];
       if (g == 0) v = fma(p.eHL[d + 1] * clamp_p2<T>(-Ed) * tmo, O[LO_CH * BLK + e], v);
     }
 #pragma unroll
@@ -640,12 +691,12 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
       if (pto >= 0) {
         T v = O[LO_QBH * BLK + e];
 #pragma unroll
-        for (int j = 0; j < NLT_QBS; j++) v += O[(LO_QBS + j) * BLK + e];
+        for (int j = 0; j < 6; j++) v += O[(LO_QBS + j) * BLK + e];
         v += en[EN_EA] * en[EN_EC] * (O[LO_QBM * BLK + e] + O[(LO_QBM + 1) * BLK + e]);
-        qb = v * clamp_p2<T>(EA(d - 2) - Ed);
+        qb = v * clamp_p2<T>(EAS(d - 2) - Ed);
       }
       O[LO_QB * BLK + e] = qb;
-      const T s2v = S[SI_BIF * BLK + e] * clamp_p2<T>(EA(d - 4) - Ed);
+      const T s2v = S[SI_BIF * BLK + e] * clamp_p2<T>(EAS(d - 4) - Ed);
       const T mpp = en[EN_EC] * qb + s2v;
       O[LO_QM2PP * BLK + e] = s2v;
       O[LO_QMPP * BLK + e] = mpp;
@@ -657,7 +708,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
         v = 0;
         lmax = fmax(lmax, 1.0);
       } else {
-        v = qb + S[SI_BIFX * BLK + e] * clamp_p2<T>(EA(d - 4) - Ed) + O[LO_Q5K * BLK + e];
+        v = qb + S[SI_BIFX * BLK + e] * clamp_p2<T>(EAS(d - 4) - Ed) + O[LO_Q5K * BLK + e];
         lmax = fmax(lmax, (double)fabs(v));
       }
       O[LO_Q5P * BLK + e] = v;
@@ -672,58 +723,10 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   {
     constexpr int CH16 = BLK * (int)sizeof(T) / 16;
     using V = typename Vec16<T>::type;
-    for (int it = t; it < 45 * CH16; it += NTT) {
+    for (int it = t; it < NCOPY * CH16; it += NTT) {
       const int k = it / CH16, q = it - k * CH16;
-      int slot;
-      T *dst = nullptr;
-      if (k == 0) {
-        slot = LO_CH;
-        dst = p.CH + c * BLK;
-      } else if (k == 1) {
-        slot = LO_XI;
-        if (d >= 6) dst = p.XI + c * BLK;
-      } else if (k == 2) {  // YY_2 is XI itself
-        slot = LO_XI;
-        if (d >= 6) dst = p.YY + (c * NYY) * BLK;
-      } else if (k < 31) {  // YY_L, L = 3..30
-        const int L = k;
-        slot = LO_YY + L - 3;
-        if (d >= 6 && L <= Lmax) dst = p.YY + (c * NYY + (L - 2)) * BLK;
-      } else if (k == 31) {
-        slot = LO_HB;
-        if (d >= 2) dst = p.HB + c * BLK;
-      } else if (k == 32) {
-        slot = LO_QB;
-        if (d >= 4) dst = p.QB + c * BLK;
-      } else if (k == 33) {
-        slot = LO_QMPP;
-        if (d >= 4) dst = p.QMpp + c * BLK;
-      } else if (k == 34) {
-        slot = LO_QM2PP;
-        if (d >= 4) dst = p.QM2pp + c * BLK;
-      } else if (k == 35) {
-        slot = LO_QMPU;
-        if (d >= 5) dst = p.QMpu + c * BLK;
-      } else if (k == 36) {
-        slot = LO_G;
-        if (d >= 5) dst = p.G + c * BLK;
-      } else if (k < 40) {
-        slot = LO_M2PU + k - 37;
-        T *tab[3] = {p.QM2pu, p.QM2up, p.QM2uu};
-        if (d >= 10) dst = tab[k - 37] + c * BLK;
-      } else if (k == 40) {
-        slot = LO_GX;
-        if (x == 0 && d >= 1) dst = p.Gx + (size_t)d * BLK;
-      } else if (k == 41) {
-        slot = LO_Q5U;
-        if (x == 0) dst = p.Q5U + (size_t)d * BLK;
-      } else if (k == 42) {
-        slot = LO_Q5P;
-        if (x == 0) dst = p.Q5P + (size_t)d * BLK;
-      } else {
-        slot = 0;
-      }
-      if (dst) reinterpret_cast<V *>(dst)[q] = reinterpret_cast<const V *>(O + (size_t)slot * BLK)[q];
+      T *dst = sDst[k];
+      if (dst) reinterpret_cast<V *>(dst)[q] = reinterpret_cast<const V *>(O + (size_t)light_slot(k) * BLK)[q];
     }
   }
   // ---- diagonal maximum for the next exponent
@@ -735,7 +738,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
 }
 
 template <typename T, int NTT>
-__global__ void __launch_bounds__(NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(NTT, 1024 / NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   in_light_cell<T, NTT>(p, bb, d, blockIdx.x, smem_raw);
 }

@@ -237,9 +237,10 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
   __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N];
+  __shared__ int sExy[2];
   for (int i = t; i < 96; i += NTT) {
     const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
+    sE[i] = (k >= 0 && k < n) ? p.E[k] : 0;
   }
   for (int i = t; i < 72; i += NTT) {
     const int qx = x - 35 + i, qy = y - 35 + i;
@@ -252,10 +253,11 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
     sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
   }
   for (int i = t; i < EN_N; i += NTT) sEn[i] = p.en[i];
+  if (t < 2) sExy[t] = p.E[t == 0 ? x : y];  // exponents of the prefixes [0, x] and [0, y]
   cp_async_wait_all();
   __syncthreads();
-    const T *en = sEn;
-  const int Ed = p.E[d];
+  const T *en = sEn;
+  const int Ed = sE[47];  // E[d], staged with its neighbours
   const int Mx = MP(x), My = MP(y), MM = Mx * My;
   const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
   const size_t c = cidx(n, x, y);
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   const bool hasL = x >= 1, hasR = y <= n - 2, encl = hasL && hasR;
   const int Mxl = hasL ? MP(x - 1) : 0, Myr = hasR ? MP(y + 1) : 0;
   const int M0 = MP(0);
-  const T F1u = (d + 1 < n) ? clamp_p2<T>(Ed - EA(d + 1)) : (T)0;
-  const T F2u = (d + 2 < n) ? clamp_p2<T>(Ed - EA(d + 2)) : (T)0;
+  const T F1u = (d + 1 < n) ? clamp_p2<T>(Ed - EAS(d + 1)) : (T)0;
+  const T F2u = (d + 2 < n) ? clamp_p2<T>(Ed - EAS(d + 2)) : (T)0;
   const T *gc = S + SO_GC * BLK;
   const T *Xxl = S + SO_XXL * BLK, *Xy = S + SO_XY * BLK;
   // loop-length weights: bulge users eBu(L) 2^{E[d]-E[d+L]}, own bulges
@@ -272,9 +274,9 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   __shared__ T wBuU[MAXLOOP + 1], wBu[MAXLOOP + 1], wIn[MAXLOOP + 1];
   if (t <= MAXLOOP) {
     const int L = t;
-    wBuU[L] = (L >= 1 && d + L < n) ? en[EN_BU + L] * clamp_p2<T>(Ed - EA(d + L)) : (T)0;
-    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed) : (T)0;
-    wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EA(d - L + 2) - Ed) : (T)0;
+    wBuU[L] = (L >= 1 && d + L < n) ? en[EN_BU + L] * clamp_p2<T>(Ed - EAS(d + L)) : (T)0;
+    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed) : (T)0;
+    wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EAS(d - L + 2) - Ed) : (T)0;
   }
   __syncthreads();
 
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
           v += ec * hMPP[pe];
           if (out_ncol(x, d) > 0) v += S[SO_HQC * BLK + pe];
           if (x == 0) v += hQ5Po[pe];  // computed above in this kernel
-          else v += clamp_p2<T>(EA(x) + Ed - EA(y)) * s2<true, false>(S + SO_GX * BLK, S + SO_HQ5P * BLK, a, b, M0);
+          else v += clamp_p2<T>(sExy[0] + Ed - sExy[1]) * s2<true, false>(S + SO_GX * BLK, S + SO_HQ5P * BLK, a, b, M0);
         } else if (k == 2 * MAXLOOP + 1) {
           if (!encl) continue;
           // XI[x-1][y+1] = F (T_{x-1} QB T_y) o tm
@@ -591,7 +593,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   }
   for (int i = t; i < 96; i += NT3) {
     const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < n && k != d) ? p.E[k] : 0;
+    sE[i] = (k >= 0 && k < n) ? p.E[k] : 0;
   }
   for (int i = t; i < 72; i += NT3) {
     const int qx = x - 35 + i, qy = y - 35 + i;
@@ -607,14 +609,14 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   cp_async_wait_all();
   __syncthreads();
   const T *en = sEn;
-  const int Ed = p.E[d];
+  const int Ed = sE[47];  // E[d], staged with its neighbours
   const int Mx = MP(x), My = MP(y), MM = Mx * My;
   const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
   const int M0 = MP(0);
   const T eb = en[EN_EB], sml = en[EN_EA] * en[EN_EC];
   if (t <= MAXLOOP) {
     const int L = t;
-    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EA(d - L) - Ed) : (T)0;
+    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed) : (T)0;
   }
   if (d >= 6 && t >= 64 && t < 64 + MM) {
     // adjoint of XI[x][y] (its own L = 2 term included) times the inner mismatch
@@ -672,7 +674,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   const T *Tx = S + SS_TX * BLK, *Ty1 = S + SS_TY1 * BLK;
   const T *hbi = S + SS_HBI * BLK, *qin = S + SS_QBI * BLK;
   const T *Xl = S + SS_XX * BLK, *Xr = S + SS_XY1 * BLK;
-  const T fq = clamp_p2<T>((d >= 2 ? EA(d - 2) : 0) - Ed);
+  const T fq = clamp_p2<T>((d >= 2 ? EAS(d - 2) : 0) - Ed);
   if (bx) {
     // dlogZ/dT_x: terms QB, XI, chain, and the interior partial sums L = 3..Lmax,
     // split over groups of threads
@@ -759,7 +761,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
       atomicAdd(hx + XPP * BLK + pe, (double)(fq * sml * sp));
     }
     if (d >= 10) {
-      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
       const T *r_up = S + SS_MR * BLK, *r_pp = S + (SS_MR + 1) * BLK, *r_uu = S + (SS_MR + 2) * BLK,
               *r_pu = S + (SS_MR + 3) * BLK;
       const T xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
@@ -785,7 +787,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
       xpp += (double)(fq * sml * sp);
     }
     if (d >= 5) {
-      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
       const T *mpp = S + SS_ML * BLK, *mpu = S + (SS_ML + 1) * BLK, *q2pp = S + (SS_ML + 2) * BLK,
               *q2pu = S + (SS_ML + 3) * BLK;
       T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
@@ -801,7 +803,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
     }
     if (x == 0) {
       // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
-      const T F = clamp_p2<T>(EA(d - 1) - Ed);
+      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
       const T *q5u = S + SS_Q5UM * BLK, *q5p = S + SS_Q5PM * BLK;
       const T *hu = S + SS_HQ5U * BLK, *hg = S + SS_HGX * BLK;
       xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));

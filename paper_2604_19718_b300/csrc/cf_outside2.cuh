@@ -27,7 +27,38 @@ struct OutBuf {
   T *hg;   // [BIFRING][n][36] row gathers (contribution to hG)
   T *hq;   // [BIFRING][n][36] column gathers (contribution to hQB)
   T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
+  float *far;  // [2 gathers][3 slots][n][OFD][36] far terms of a band (binary32; nullptr: none)
 };
+
+// ---------------------------------------------------------------- far bands
+// The gathers of a target cell on diagonal a read adjoints hQM2pp on
+// diagonals a+4 .. n-1.  For the targets of a band [alo, alo + OFD), the terms
+// whose adjoint lies on a diagonal >= c = alo + 2 OFD + 3 are "far": final a
+// whole band earlier, they are summed for the band at once by k_out_far (a
+// tiled product in which every loaded block serves up to 16 targets) while the
+// reverse light chain is still OFD diagonals away; the near terms (adjoint
+// diagonals a+4 .. c-1, at most 2 OFD + 1 per gather) stay in k_out_bif.
+// Far blocks are rescaled to a linear exponent with the chord s, e0 of E over
+// diagonals 5 .. n-1: forward blocks by 2^{E[D] - s D - e0}, adjoint blocks by
+// 2^{s D + e0 - E[D]}; every far term of a target on diagonal a is then
+// relative to the common factor ec 2^{E[a] - s a}.
+constexpr int OFD = 16;   // target diagonals per band
+constexpr int OFTX = 16;  // target rows per tile
+constexpr int OFKC = 4;   // summation indices staged per step
+constexpr int OFKS = 64;  // summation indices per CTA slice
+__host__ __device__ __forceinline__ int of_c(int alo) { return alo + 2 * OFD + 3; }
+__host__ __device__ __forceinline__ bool of_band(int n, int alo) { return of_c(alo) <= n - 1; }
+
+struct OChord {
+  double s, e0;
+};
+__device__ __forceinline__ OChord of_chord(const int *E, int n) {
+  const double e5 = (double)E[5], el = (double)E[n - 1];
+  OChord r;
+  r.s = (el - e5) / (double)(n - 6);
+  r.e0 = e5 - 5.0 * r.s;
+  return r;
+}
 
 __host__ __device__ __forceinline__ int out_nrow(int n, int x, int d) {  // hG terms y' = y+4..n-1
   int cnt = n - (x + d) - 4;
@@ -71,14 +102,20 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
     }
   } else {
     // row chunks 0..nr-1 and column chunks nr..nr+nq-1 dealt round-robin to
-    // all eight warps (a cell near either end has almost only one kind)
+    // all eight warps (a cell near either end has almost only one kind); with
+    // a far band only the near terms (adjoint diagonal < c) are summed here
     const int x = cb, y = x + d;
     Ma = p.Mp[x];
     Mb = p.Mp[y];
-    const int nr = out_nrow(n, x, d), nq = out_ncol(x, d);
+    const int alo = d / OFD * OFD;
+    const bool banded = ob.far != nullptr && of_band(n, alo);
+    const int ylim = banded ? min(n - 1, x + of_c(alo) - 1) : n - 1;  // row terms yy <= ylim
+    const int xlo = banded ? max(0, y - of_c(alo) + 1) : 0;          // column terms xx >= xlo
+    const int nr = ylim >= y + 4 ? (ylim - y - 4 + KCH) / KCH : 0;
+    const int nq = x - 5 >= xlo ? (x - 5 - xlo + KCH) / KCH : 0;
     for (int q = w; q < nr; q += 8) {
       const int yy = y + 4 + q * KCH + lane;
-      if (yy <= n - 1) {
+      if (yy <= ylim) {
         T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
         acc_mm_v<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
       }
@@ -93,7 +130,7 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
     const int q0 = ((w - nr) % 8 + 8) % 8;  // this warp owns the chunks nr + q with nr + q = w (mod 8)
     for (int q = q0; q < nq; q += 8) {
       const int xx = x - 5 - q * KCH - lane;
-      if (xx >= 0) {
+      if (xx >= xlo) {
         T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
         acc_mm_v<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
       }
@@ -125,6 +162,14 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
 #pragma unroll
       for (int k = 0; k < 8; k++) u += red[8 + k][e];
       const int x = cb;
+      const int alo = d / OFD * OFD;
+      if (ob.far != nullptr && of_band(n, alo)) {
+        const OChord ch = of_chord(E, n);
+        const double fac = (double)ec * exp2((double)Ed - ch.s * (double)d);
+        const size_t fo = (((size_t)((alo / OFD) % 3) * n + x) * OFD + (d - alo)) * BLK + e;
+        v += (T)(fac * (double)ob.far[fo]);
+        u += (T)(fac * (double)ob.far[(size_t)3 * n * OFD * BLK + fo]);
+      }
       ob.hg[((size_t)slot * n + x) * BLK + e] = v;
       ob.hq[((size_t)slot * n + x) * BLK + e] = u;
     }
@@ -139,6 +184,158 @@ __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
     out_bif_cell(p, ob, d, cb, red);
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------- K0': far band
+// Grid (tiles, slices), 256 threads: thread (tx, tj) owns the target
+// (x, y) = (x0 + tx, x0 + tx + alo + tj).  ROW: the row gather
+//   sum_{yy >= x + c} hQM2pp[x][yy] QB[y][yy]^T
+// staged per summation index yy as the tile's 16 adjoint rows and its
+// 31 QB rows; COL: the column gather
+//   sum_{xx <= y - c} G[xx][x]^T hQM2pp[xx][y]
+// staged per xx as 16 G columns and 31 adjoint columns.  Blocks arrive by TMA
+// bulk copies into two alternating stages; each CTA takes a slice of OFKS
+// summation indices and adds its sums into the band buffer (zeroed first).
+template <bool ROW>
+__global__ void __launch_bounds__(256) k_out_far(DP<float> p, OutBuf<float> ob, int alo) {
+  constexpr int TY = OFTX + OFD - 1, STAGE = OFKC * (OFTX + TY) * BLK;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *buf = (float *)smem_raw;          // [2][STAGE]: A [OFKC][OFTX][36], B [OFKC][TY][36]
+  float *fw = buf + 2 * STAGE;             // [n] 2^{E[D] - s D - e0} (forward blocks)
+  float *fh = fw + p.n;                    // [n] 2^{s D + e0 - E[D]} (adjoint blocks)
+  __shared__ __align__(8) unsigned long long sbar[2];
+  const int n = p.n, t = threadIdx.x, tx = t % OFTX, tj = t / OFTX;
+  const int x0 = blockIdx.x * OFTX, x = x0 + tx, y = x + alo + tj, c = of_c(alo);
+  // summation range of the tile and of this slice
+  const int lo = ROW ? x0 + c : 0, hi = ROW ? n - 1 : x0 + OFTX - 1 + alo + OFD - 1 - c;
+  const int kbeg = lo + blockIdx.y * OFKS, kend = min(hi, kbeg + OFKS - 1);
+  if (kbeg > kend) return;
+  const OChord ch = of_chord(p.E, n);
+  for (int D = t; D < n; D += 256) {
+    const double z = (double)p.E[D] - ch.s * D - ch.e0;
+    fw[D] = (float)exp2(z);
+    fh[D] = (float)exp2(-z);
+  }
+  if (t == 0) {
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
+  }
+  __syncthreads();
+  auto stage = [&](int k0, int bsel) {
+    float *As = buf + (size_t)bsel * STAGE, *Bs = As + OFKC * OFTX * BLK;
+    for (int q = t; q < OFKC * (OFTX + TY); q += 256) {
+      const float *src = nullptr;
+      float *dst;
+      if (q < OFKC * OFTX) {
+        const int kk = q / OFTX, r = q % OFTX, k = k0 + kk, xr = x0 + r;
+        dst = As + (size_t)q * BLK;
+        if (k <= kend && xr < n) {
+          if (ROW) {
+            if (k < n && k - xr >= 4) src = p.hQM2pp + cidx(n, xr, k) * BLK;
+          } else if (xr - k >= 5) {
+            src = p.G + cidx(n, k, xr) * BLK;
+          }
+        }
+      } else {
+        const int q2 = q - OFKC * OFTX, kk = q2 / TY, cq = q2 % TY, k = k0 + kk, yr = x0 + alo + cq;
+        dst = Bs + (size_t)q2 * BLK;
+        if (k <= kend && yr < n) {
+          if (ROW) {
+            if (k < n && k - yr >= 4) src = p.QB + cidx(n, yr, k) * BLK;
+          } else if (yr - k >= 0) {
+            src = p.hQM2pp + cidx(n, k, yr) * BLK;
+          }
+        }
+      }
+      if (src) {
+        mbar_expect(&sbar[bsel], BLK * 4);
+        bulk_g2s(dst, src, BLK * 4, &sbar[bsel]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < BLK; e++) dst[e] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (t == 0) mbar_arrive(&sbar[bsel]);
+  };
+  const bool live = y < n;
+  float acc[BLK];
+  zero_block(acc);
+  unsigned ph[2] = {0u, 0u};
+  stage(kbeg, 0);
+  int bsel = 0;
+  for (int k0 = kbeg; k0 <= kend; k0 += OFKC, bsel ^= 1) {
+    if (k0 + OFKC <= kend) stage(k0 + OFKC, bsel ^ 1);
+    if (!__syncthreads_and(mbar_wait(&sbar[bsel], ph[bsel], p.err))) return;
+    ph[bsel] ^= 1u;
+    const float *As = buf + (size_t)bsel * STAGE, *Bs = As + OFKC * OFTX * BLK;
+    if (live) {
+#pragma unroll 1
+      for (int kk = 0; kk < OFKC; kk++) {
+        const int k = k0 + kk;
+        if (k > kend) break;
+        if (ROW ? (k < x + c) : (k > y - c)) continue;
+        const float f = ROW ? fh[k - x] * fw[k - y] : fw[x - k] * fh[y - k];
+        const float *A = As + ((size_t)kk * OFTX + tx) * BLK;
+        const float *B = Bs + ((size_t)kk * TY + (tx + tj)) * BLK;
+#pragma unroll
+        for (int r = 0; r < NS; r++) {
+          float av[NS];
+          if (ROW) {
+            ld_row(av, A + r * NS);  // row r of the adjoint block
+          } else {
+#pragma unroll
+            for (int s2 = 0; s2 < NS; s2++) av[s2] = A[s2 * NS + r];  // column r of G
+          }
+#pragma unroll
+          for (int s2 = 0; s2 < NS; s2++) av[s2] *= f;
+          if (ROW) {
+            // acc[r][b] += sum_s h[r][s] QB[b][s]
+#pragma unroll
+            for (int b = 0; b < NS; b++) {
+              float bv[NS];
+              ld_row(bv, B + b * NS);
+              float v = acc[r * NS + b];
+#pragma unroll
+              for (int s2 = 0; s2 < NS; s2++) v = fmaf(av[s2], bv[s2], v);
+              acc[r * NS + b] = v;
+            }
+          } else {
+            // acc[r][b] += sum_s G[s][r] h[s][b]
+#pragma unroll
+            for (int s2 = 0; s2 < NS; s2++) {
+              float bv[NS];
+              ld_row(bv, B + s2 * NS);
+#pragma unroll
+              for (int b = 0; b < NS; b++) acc[r * NS + b] = fmaf(av[s2], bv[b], acc[r * NS + b]);
+            }
+          }
+        }
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();  // the next step's copies reuse this stage
+  }
+  if (live) {
+    float *dst = ob.far + (((size_t)(ROW ? 0 : 3) + (alo / OFD) % 3) * n + x) * OFD * BLK + (size_t)tj * BLK;
+#pragma unroll
+    for (int r = 0; r < NS; r++) {
+      float rr[NS];
+#pragma unroll
+      for (int b = 0; b < NS; b++) rr[b] = acc[r * NS + b];
+      red_row(dst + r * NS, rr);
+    }
+  }
+}
+
+__host__ __device__ constexpr size_t out_far_smem(int n) {
+  return ((size_t)2 * OFKC * (OFTX + OFTX + OFD - 1) * BLK + 2 * (size_t)n) * sizeof(float);
+}
+__host__ __device__ __forceinline__ int out_far_tiles(int n, int alo) { return (n - alo + OFTX - 1) / OFTX; }
+__host__ __device__ __forceinline__ int out_far_slices(int n, int alo, bool row) {
+  const int c = of_c(alo);
+  const int span = row ? n - c : (n - alo + OFTX) + alo + OFD - c;  // widest tile's range
+  return span > 0 ? (span + OFKS - 1) / OFKS : 0;
 }
 
 // ---------------------------------------------------------------- K2' staging

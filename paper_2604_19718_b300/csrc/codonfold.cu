@@ -387,6 +387,8 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, dalloc(L, &t.ob.hg, (size_t)BIFRING * n * BLK));
   CF_CUDA(p, dalloc(L, &t.ob.hq, (size_t)BIFRING * n * BLK));
   CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * BLK));
+  t.ob.far = nullptr;
+  if (sizeof(T) == sizeof(float) && of_band(n, 0)) CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
   t.outside_alloc = true;
   return CF_OK;
 }
@@ -427,10 +429,47 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double));
   if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float));
   std::vector<cudaGraphNode_t> k2(n), k1(n), k3(n, nullptr);
+  // far bands (binary32): both gathers of band alo hang off the light kernel
+  // of diagonal of_c(alo) and precede the bifurcation kernels of the band
+  const bool banded = ob.far != nullptr;
+  std::vector<cudaGraphNode_t> kfr((size_t)n / OFD + 1, nullptr), kfc((size_t)n / OFD + 1, nullptr);
+  if (banded) {
+    CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_far<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)out_far_smem(n)));
+    CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_far<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)out_far_smem(n)));
+  }
   int nodes = 0;
   for (int d = n - 1; d >= 0 && e == cudaSuccess; d--) {
     int dd = d;
     void *args[] = {&dp, &ob, &dd};
+    const int alo = d / OFD * OFD;
+    const bool fb = banded && of_band(n, alo);
+    if (fb && d == alo + OFD - 1) {
+      DP<float> dpf;
+      OutBuf<float> obf;
+      std::memcpy(&dpf, &dp, sizeof(dpf));
+      std::memcpy(&obf, &ob, sizeof(obf));
+      int a0 = alo;
+      void *fargs[] = {&dpf, &obf, &a0};
+      const size_t slot = (size_t)((alo / OFD) % 3) * n * OFD * BLK, len = (size_t)n * OFD * BLK * sizeof(float);
+      cudaGraphNode_t z[2];
+      e = add_memset(g, &z[0], &k2[of_c(alo)], 1, obf.far + slot, len);
+      if (e == cudaSuccess) e = add_memset(g, &z[1], &k2[of_c(alo)], 1, obf.far + (size_t)3 * n * OFD * BLK + slot, len);
+      for (int kind = 0; kind < 2 && e == cudaSuccess; kind++) {
+        cudaKernelNodeParams kp = {};
+        kp.func = kind == 0 ? (void *)k_out_far<true> : (void *)k_out_far<false>;
+        kp.gridDim = dim3(out_far_tiles(n, alo), std::max(1, out_far_slices(n, alo, kind == 0)));
+        kp.blockDim = dim3(256);
+        kp.sharedMemBytes = (unsigned)out_far_smem(n);
+        kp.kernelParams = fargs;
+        cudaGraphNode_t &kn = kind == 0 ? kfr[alo / OFD] : kfc[alo / OFD];
+        e = cudaGraphAddKernelNode(&kn, g, &z[kind], 1, &kp);
+        if (e == cudaSuccess) e = set_priority(kn, false);
+        nodes++;
+      }
+      if (e != cudaSuccess) break;
+    }
     const bool hasb = d <= n - 5 && d >= 1;
     if (hasb) {
       cudaKernelNodeParams kp = {};
@@ -438,7 +477,13 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
-      e = cudaGraphAddKernelNode(&k1[d], g, &k2[d + 4], 1, &kp);
+      cudaGraphNode_t bdeps[3] = {k2[d + 4], nullptr, nullptr};
+      int nb = 1;
+      if (fb) {
+        bdeps[nb++] = kfr[alo / OFD];
+        bdeps[nb++] = kfc[alo / OFD];
+      }
+      e = cudaGraphAddKernelNode(&k1[d], g, bdeps, nb, &kp);
       if (e == cudaSuccess) e = set_priority(k1[d], false);
       nodes++;
       if (e != cudaSuccess) break;

@@ -34,7 +34,51 @@ struct BifBuf {
   T *main;  // [BIFRING][n][36]  sum_k G[x][k] ec QB[k][y] relative to 2^{E[d-4]}
   T *ext;   // [BIFRING][36]     sum_{k>=4} Gx[k] QB[k][d] relative to 2^{E[d-4]}
   int ncmax;
+  float *far;     // [2][n][FARD][farslices][36] far split points of a band, per slice (binary32; nullptr: none)
+  int farslices;  // slices per cell in the far buffer
 };
+
+// ---------------------------------------------------------------- far bands
+// The bifurcation sum of cell (x, y) on diagonal d runs over split points
+// a = k - x with halves on diagonals a and d - a.  For the diagonals of a band
+// [d0, d0 + FARD), the split points whose halves both lie on diagonals
+// <= c = d0 - FARD - 1 are "far": final a whole band earlier, they are summed
+// for the band by k_in_far (a tiled product in which every loaded block serves
+// up to 16 cells) while the light chain is still FARD - 3 diagonals away; the
+// remaining "near" split points (at most 2 (2 FARD - 5) per cell) stay in the
+// per-diagonal kernel.  Far blocks are rescaled to a linear exponent with the
+// chord s = (E[c] - E[5]) / (c - 5), e0 = E[5] - 5 s: each half is multiplied
+// by 2^{E[a] - s a - e0}, so every product of two halves is relative to
+// 2^{s d + 2 e0}.  Each CTA of k_in_far sums one slice of split points and
+// stores it; the per-diagonal kernel adds the slices in order, so the result
+// does not depend on which slice ran first.
+constexpr int FARD = 16;   // diagonals per band
+constexpr int FARTX = 16;  // rows per far tile
+constexpr int FARKC = 8;   // split points staged per step
+constexpr int FARKS = 64;  // split points per CTA slice
+
+__host__ __device__ __forceinline__ int far_c(int d0) { return d0 - FARD - 1; }
+// does band d0 (a multiple of FARD) have far split points?
+__host__ __device__ __forceinline__ bool far_band(int d0) { return d0 >= 3 * FARD; }
+__host__ __device__ __forceinline__ int far_kmin(int x0) { return x0 + FARD + 1; }
+__host__ __device__ __forceinline__ int far_kmax(int n, int x0, int d0) {
+  return x0 + FARTX - 1 + far_c(d0) < n - 1 ? x0 + FARTX - 1 + far_c(d0) : n - 1;
+}
+// non-empty slices of the tile starting at row x0
+__host__ __device__ __forceinline__ int far_nslice(int n, int x0, int d0) {
+  return (far_kmax(n, x0, d0) - far_kmin(x0) + FARKS) / FARKS;
+}
+
+struct FarChord {
+  double s, e0;
+};
+__device__ __forceinline__ FarChord far_chord(const int *E, int c) {
+  const double e5 = (double)__ldcg(E + 5), ec = (double)__ldcg(E + c);
+  FarChord r;
+  r.s = (ec - e5) / (double)(c - 5);
+  r.e0 = e5 - 5.0 * r.s;
+  return r;
+}
 
 // ---------------------------------------------------------------- K1
 // One cell per block (the last unit of a diagonal: the exterior sum); warp w
@@ -51,13 +95,27 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   const int Ma = p.Mp[x], Mb = p.Mp[y];
   T acc[BLK];
   zero_block(acc);
+  // near split points a in [5, a1] and [a2, d-4]; with a far band the middle
+  // [a1+1, a2-1] comes from k_in_far
+  const int d0 = d / FARD * FARD;
+  const bool banded = bb.far != nullptr && far_band(d0);
+  int a1 = d - 4, a2 = d - 3;
+  if (banded) {
+    const int c = far_c(d0), alo = max(5, d - c), ahi = min(c, d - 4);
+    if (alo <= ahi) {
+      a1 = alo - 1;
+      a2 = ahi + 1;
+    }
+  }
   if (w < NW) {
     if (!ext) {
-      const int nc = nchunk_bif(d);
+      const int n1 = max(0, a1 - 4), n2 = max(0, d - 3 - a2);
+      const int nc = (n1 + n2 + KCH - 1) / KCH;
       const T ec = p.en[EN_EC];
       for (int c = w; c < nc; c += NW) {
-        const int k = x + 5 + c * KCH + lane;
-        if (k <= y - 4) {
+        const int q = c * KCH + lane;
+        if (q < n1 + n2) {
+          const int k = x + (q < n1 ? 5 + q : a2 + q - n1);
           T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
           acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
         }
@@ -85,6 +143,15 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
     T v = 0;
 #pragma unroll
     for (int k = 0; k < NW; k++) v += red[k][e];
+    if (banded && !ext) {
+      // far split points: the slices of the cell's tile in order, relative to 2^{s d + 2 e0}
+      const FarChord ch = far_chord(p.E, far_c(d0));
+      const int nsl = far_nslice(n, x / FARTX * FARTX, d0);
+      const float *fp = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + (d - d0)) * bb.farslices) * BLK + e;
+      float fv = 0.f;
+      for (int sl = 0; sl < nsl; sl++) fv += fp[(size_t)sl * BLK];
+      v += (T)((double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref) * (double)fv);
+    }
     T *dst = ext ? bb.ext + (size_t)slot * BLK : bb.main + ((size_t)slot * n + x) * BLK;
     dst[e] = v;
   }
@@ -318,6 +385,107 @@ __device__ __forceinline__ T row_absmax(const T (&r)[NS]) {
 #pragma unroll
   for (int b = 0; b < NS; b++) m = fmax(m, fabs(r[b]));
   return m;
+}
+
+// ---------------------------------------------------------------- K0: far band
+// Grid (tiles, slices), 256 threads: the CTA takes a tile of FARTX rows x and
+// the FARD diagonals of band d0 (thread (tx, tj) owns cell (x0 + tx,
+// x0 + tx + d0 + tj)) and a slice of FARKS split points k.  Split points are
+// staged FARKC at a time into two alternating stages: G[x][k] for the tile's
+// rows and QB[k][y] for its FARTX + FARD - 1 columns, one TMA bulk copy per
+// block; the linear-exponent factors of both halves are applied as the
+// blocks are used.  The slice's sums go to their own place in the band buffer.
+__global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, int d0) {
+  constexpr int TY = FARTX + FARD - 1, STAGE = FARKC * (FARTX + TY) * BLK;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *buf = (float *)smem_raw;  // [2][STAGE]: G [FARKC][FARTX][36], QB [FARKC][TY][36]
+  float *gf = buf + 2 * STAGE;     // [c + 1] factors 2^{E[a] - s a - e0}
+  __shared__ __align__(8) unsigned long long sbar[2];
+  const int n = p.n, t = threadIdx.x, tx = t % FARTX, tj = t / FARTX;
+  const int x0 = blockIdx.x * FARTX, x = x0 + tx, d = d0 + tj, y = x + d;
+  const int c = far_c(d0);
+  const int kbeg = far_kmin(x0) + blockIdx.y * FARKS;
+  const int kend = min(far_kmax(n, x0, d0), kbeg + FARKS - 1);
+  if (kbeg > kend) return;
+  const FarChord ch = far_chord(p.E, c);
+  for (int a = t; a <= c; a += 256) gf[a] = (float)exp2((double)__ldcg(p.E + a) - ch.s * a - ch.e0);
+  if (t == 0) {
+    mbar_init(&sbar[0], 1);
+    mbar_init(&sbar[1], 1);
+  }
+  __syncthreads();
+  auto stage = [&](int k0, int bsel) {
+    float *Gs = buf + (size_t)bsel * STAGE, *Qs = Gs + FARKC * FARTX * BLK;
+    for (int q = t; q < FARKC * (FARTX + TY); q += 256) {
+      const float *src = nullptr;
+      float *dst;
+      if (q < FARKC * FARTX) {
+        const int kk = q / FARTX, r = q % FARTX, xx = x0 + r, k = k0 + kk;
+        dst = Gs + (size_t)q * BLK;
+        if (k <= kend && xx < n && k - xx >= 5) src = p.G + cidx(n, xx, k) * BLK;
+      } else {
+        const int q2 = q - FARKC * FARTX, kk = q2 / TY, cy = q2 % TY, k = k0 + kk, yy = x0 + d0 + cy;
+        dst = Qs + (size_t)q2 * BLK;
+        if (k <= kend && yy < n && yy - k >= 4) src = p.QB + cidx(n, k, yy) * BLK;
+      }
+      if (src) {
+        mbar_expect(&sbar[bsel], BLK * 4);
+        bulk_g2s(dst, src, BLK * 4, &sbar[bsel]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < BLK; e++) dst[e] = 0.f;
+      }
+    }
+    __syncthreads();
+    if (t == 0) mbar_arrive(&sbar[bsel]);
+  };
+  const bool live = y < n;
+  const int alo = max(5, d - c), ahi = min(c, d - 4);
+  float acc[BLK];
+  zero_block(acc);
+  unsigned ph[2] = {0u, 0u};
+  stage(kbeg, 0);
+  int bsel = 0;
+  for (int k0 = kbeg; k0 <= kend; k0 += FARKC, bsel ^= 1) {
+    if (k0 + FARKC <= kend) stage(k0 + FARKC, bsel ^ 1);  // released at the end of the previous step
+    if (!__syncthreads_and(mbar_wait(&sbar[bsel], ph[bsel], p.err))) return;
+    ph[bsel] ^= 1u;
+    const float *Gs = buf + (size_t)bsel * STAGE, *Qs = Gs + FARKC * FARTX * BLK;
+    if (live) {
+#pragma unroll 1
+      for (int kk = 0; kk < FARKC; kk++) {
+        const int k = k0 + kk, a = k - x;
+        if (a < alo || a > ahi || k > kend) continue;
+        const float f = gf[a] * gf[d - a];
+        const float *A = Gs + ((size_t)kk * FARTX + tx) * BLK;
+        const float *B = Qs + ((size_t)kk * TY + (tx + tj)) * BLK;
+#pragma unroll
+        for (int r = 0; r < NS; r++) {
+          float av[NS];
+          ld_row(av, A + r * NS);
+#pragma unroll
+          for (int s2 = 0; s2 < NS; s2++) {
+            float bv[NS];
+            ld_row(bv, B + s2 * NS);
+            const float xa = av[s2] * f;
+#pragma unroll
+            for (int b = 0; b < NS; b++) acc[r * NS + b] = fmaf(xa, bv[b], acc[r * NS + b]);
+          }
+        }
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();  // the next step's copies reuse this stage
+  }
+  if (live) {
+    float *dst = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + tj) * bb.farslices + blockIdx.y) * BLK;
+#pragma unroll
+    for (int e = 0; e < BLK; e++) dst[e] = acc[e];
+  }
+}
+
+__host__ __device__ constexpr size_t in_far_smem(int c) {
+  return ((size_t)2 * FARKC * (FARTX + FARTX + FARD - 1) * BLK + (size_t)(c + 1)) * sizeof(float);
 }
 
 // ---------------------------------------------------------------- K2

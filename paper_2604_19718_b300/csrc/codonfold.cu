@@ -265,6 +265,10 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   t.bb.ncmax = 1;
   CF_CUDA(p, dalloc(L, &t.bb.main, (size_t)BIFRING * n * BLK));
   CF_CUDA(p, dalloc(L, &t.bb.ext, (size_t)BIFRING * BLK));
+  t.bb.far = nullptr;
+  t.bb.farslices = far_nslice(n, 0, std::max(0, (n - 1) / FARD * FARD));  // the widest band's slices
+  if (sizeof(T) == sizeof(float) && n > 3 * FARD)
+    CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
   t.inside_alloc = true;
   return CF_OK;
 }
@@ -317,16 +321,45 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   int nodes = 0;
   DP<T> dp = t.dp;
   BifBuf<T> bb = t.bb;
+  // far bands (binary32): band d0 hangs off the light kernel of d0 - FARD - 1
+  // and precedes the bifurcation kernels of its FARD diagonals
+  const bool banded = bb.far != nullptr;
+  std::vector<cudaGraphNode_t> kf((size_t)n / FARD + 1, nullptr);
+  if (banded)
+    CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_far, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)in_far_smem(n)));
   for (int d = 0; d < n && e == cudaSuccess; d++) {
     int dd = d;
     void *args[] = {&dp, &bb, &dd};
+    const int d0 = d / FARD * FARD;
+    if (banded && d == d0 && far_band(d0)) {
+      DP<float> dpf;
+      BifBuf<float> bbf;
+      std::memcpy(&dpf, &dp, sizeof(dpf));
+      std::memcpy(&bbf, &bb, sizeof(bbf));
+      int b0 = d0;
+      void *fargs[] = {&dpf, &bbf, &b0};
+      cudaKernelNodeParams kp = {};
+      kp.func = (void *)k_in_far;
+      kp.gridDim = dim3((n - d0 + FARTX - 1) / FARTX, far_nslice(n, 0, d0));
+      kp.blockDim = dim3(256);
+      kp.sharedMemBytes = (unsigned)in_far_smem(far_c(d0));
+      kp.kernelParams = fargs;
+      e = cudaGraphAddKernelNode(&kf[d0 / FARD], g, &k2[far_c(d0)], 1, &kp);
+      if (e == cudaSuccess) e = set_priority(kf[d0 / FARD], false);
+      nodes++;
+      if (e != cudaSuccess) break;
+    }
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_in_bif<T>;
       kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
-      e = cudaGraphAddKernelNode(&k1[d], g, &k2[d - 4], 1, &kp);
+      cudaGraphNode_t bdeps[2] = {k2[d - 4], nullptr};
+      int nb = 1;
+      if (banded && far_band(d0)) bdeps[nb++] = kf[d0 / FARD];
+      e = cudaGraphAddKernelNode(&k1[d], g, bdeps, nb, &kp);
       if (e == cudaSuccess) e = set_priority(k1[d], false);
       nodes++;
     }

@@ -776,7 +776,7 @@ struct SideCtx {
 template <typename T>
 __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu) {
   T *Hxi = S + (size_t)SS_N * BLK;   // [36]
-  T *RED = Hxi + BLK;                // [NT3]
+  T *RED = Hxi + BLK;                // [4][NT3] partial sums of the transfer gradients
   int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
   int (*sBx)[NS] = cx.sBx, (*sBy)[NS] = cx.sBy;
   const int t = threadIdx.x;
@@ -865,153 +865,202 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   }
 
   // ---------------- gradients of the boundary transfers T_x, T_{y-1}, X_x, X_{y-1}
+  // Four phases, one per gradient block; in each, the live entries of the
+  // block times groups of its summation terms are spread over all threads,
+  // and the group partial sums are added per entry before the binary64 add.
   if (!(bx || by1)) return;
   const T *hQB = S + SS_HGC * BLK, *hCHf = S + SS_HCH * BLK, *hM2 = S + SS_HM2 * BLK;
   const T *hMPU = S + SS_HMPU * BLK, *hGG = S + SS_HG * BLK;
   const T *Tx = S + SS_TX * BLK, *Ty1 = S + SS_TY1 * BLK;
   const T *hbi = S + SS_HBI * BLK, *qin = S + SS_QBI * BLK;
   const T *Xl = S + SS_XX * BLK, *Xr = S + SS_XY1 * BLK;
+  const T *q2 = S + SS_Q2I * BLK;  // QM2 uu, up, pu, pp of (x+1, y-1)
   const T fq = clamp_p2<T>((d >= 2 ? EAS(d - 2) : 0) - Ed);
+  const T F = clamp_p2<T>(EAS(d - 1) - Ed);
+  const int Lmax = min(MAXLOOP, d - 4);
+  T *R0 = RED, *R1 = RED + NT3, *R2 = RED + 2 * NT3, *R3 = RED + 3 * NT3;
   if (bx) {
-    // dlogZ/dT_x: terms QB, XI, chain, and the interior partial sums L = 3..Lmax,
-    // split over groups of threads
-    const int MMx = Mx * M1, G2 = min(NT3 / MMx, 16), g = t / MMx, e = t % MMx;
-    const int Lmax = min(MAXLOOP, d - 4);
-    const int nterm = 3 + ((d >= 6) ? Lmax - 2 : 0);
-    if (g < G2) {
+    // T_x[a][u]: terms QB (one per b), XI (one per z), chain, YY_L (L = 3..Lmax)
+    const int E1 = Mx * M1, nq = d >= 4 ? My : 0, nz = d >= 6 ? My : 0, nL = d >= 6 ? Lmax - 2 : 0;
+    const int nterm = nq + nz + 1 + nL, G = min(NT3 / E1, nterm), g = t / E1, e = t % E1;
+    if (g < G) {
       const int a = e / M1, u = e % M1;
       T sacc = 0;
-      for (int k = g; k < nterm; k += G2) {
-        if (k == 0) {
-          if (d < 4) continue;
-          for (int b = 0; b < My; b++) {
-            const T gq = hQB[a * NS + b];
-            if (gq == (T)0) continue;
-            T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
-            if (d >= 6) {
-              const int pto = pair_type(BASE(x, a), BASE(y, b));
-              const int bu = BASE((x + 1), u);
-              for (int b2 = 0; b2 < Mv; b2++) {
-                const int pti = pair_type(bu, BASE((y - 1), b2));
-                if (pti < 0 || pto < 0) continue;
-                tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
-              }
+      for (int k = g; k < nterm; k += G) {
+        if (k < nq) {
+          const int b = k;
+          const T gq = hQB[a * NS + b];
+          if (gq == (T)0) continue;
+          T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
+          if (d >= 6) {
+            const int pto = pair_type(BASE(x, a), BASE(y, b));
+            const int bu = BASE((x + 1), u);
+            for (int b2 = 0; b2 < Mv; b2++) {
+              const int pti = pair_type(bu, BASE((y - 1), b2));
+              if (pti < 0 || pto < 0) continue;
+              tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
             }
-            sacc += fq * gq * tt;
           }
-        } else if (k == 1) {
-          if (d < 6) continue;
-          for (int z = 0; z < My; z++) sacc += fq * Hxi[a * NS + z] * s2<false, false>(qin, Ty1, u, z, Mv);
-        } else if (k == 2) {
+          sacc += fq * gq * tt;
+        } else if (k < nq + nz) {
+          const int z = k - nq;
+          sacc += fq * Hxi[a * NS + z] * s2<false, false>(qin, Ty1, u, z, Mv);
+        } else if (k == nq + nz) {
           if (d >= 1) sacc += s2<false, true>(hCHf, S + SS_CHN * BLK, a, u, My);
         } else {
-          const int L = k;
+          const int L = k - nq - nz - 1 + 3;
           sacc += s2<false, true>(HY + (L - 2) * BLK, S + (SS_YYP + L - 3) * BLK, a, u, My);
         }
       }
-      RED[t] = sacc;
+      R0[t] = sacc;
     }
     __syncthreads();
-    if (t < MMx) {
+    if (t < E1) {
       T v = 0;
-      for (int gg = 0; gg < G2; gg++) v += RED[gg * MMx + t];
+      for (int gg = 0; gg < G; gg++) v += R0[gg * E1 + t];
       atomicAdd(p.hT + (size_t)x * BLK + (t / M1) * NS + (t % M1), (double)v);
     }
+    __syncthreads();
   }
-  if (by1 && t >= 64 && t < 64 + Mv * My) {
-    const int e = t - 64, v2 = e / My, b = e % My;
-    T sacc = 0;
-    if (d >= 4) {
-      for (int a = 0; a < Mx; a++) {
-        const T g = hQB[a * NS + b];
-        if (g == (T)0) continue;
-        T tt = s2<false, false>(Tx, hbi, a, v2, M1);
-        if (d >= 6) {
-          const int pto = pair_type(BASE(x, a), BASE(y, b));
-          const int bv = BASE((y - 1), v2);
-          for (int a2 = 0; a2 < M1; a2++) {
-            const int pti = pair_type(BASE((x + 1), a2), bv);
-            if (pti < 0 || pto < 0) continue;
-            tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
+  if (by1) {
+    // T_{y-1}[v2][b]: one term per a
+    const int E2 = Mv * My, G = min(NT3 / E2, max(Mx, 1)), g = t / E2, e = t % E2;
+    if (g < G) {
+      const int v2 = e / My, b = e % My;
+      T sacc = 0;
+      for (int a = g; a < Mx; a += G) {
+        if (d >= 4) {
+          const T gg = hQB[a * NS + b];
+          if (gg != (T)0) {
+            T tt = s2<false, false>(Tx, hbi, a, v2, M1);
+            if (d >= 6) {
+              const int pto = pair_type(BASE(x, a), BASE(y, b));
+              const int bv = BASE((y - 1), v2);
+              for (int a2 = 0; a2 < M1; a2++) {
+                const int pti = pair_type(BASE((x + 1), a2), bv);
+                if (pti < 0 || pto < 0) continue;
+                tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
+              }
+            }
+            sacc += fq * gg * tt;
           }
         }
-        sacc += fq * g * tt;
+        if (d >= 6) sacc += fq * s2<false, false>(Tx, qin, a, v2, M1) * Hxi[a * NS + b];
       }
+      R0[t] = sacc;
     }
-    if (d >= 6)
-      for (int wv = 0; wv < Mx; wv++) sacc += fq * s2<false, false>(Tx, qin, wv, v2, M1) * Hxi[wv * NS + b];
-    atomicAdd(p.hT + (size_t)(y - 1) * BLK + v2 * NS + b, (double)sacc);
+    __syncthreads();
+    if (t < E2) {
+      T v = 0;
+      for (int gg = 0; gg < G; gg++) v += R0[gg * E2 + t];
+      atomicAdd(p.hT + (size_t)(y - 1) * BLK + (t / My) * NS + (t % My), (double)v);
+    }
+    __syncthreads();
   }
-  if (bx && t >= 128 && t < 128 + Mx * M1) {
-    const int e = t - 128, a = e / M1, u = e % M1, pe = a * NS + u;
-    double *hx = p.hX + (size_t)x * 4 * BLK;
-    if (d >= 11) {
-      const T *q2 = S + SS_Q2I * BLK;
-      T su = 0, sp = 0;
-      for (int b = 0; b < My; b++) {
-        const T g = hQB[a * NS + b];
-        if (g == (T)0) continue;
-        su += g * (s2<false, false>(q2, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + BLK, Xr + XPP * BLK, u, b, Mv));
-        sp += g * (s2<false, false>(q2 + 2 * BLK, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + 3 * BLK, Xr + XPP * BLK, u, b, Mv));
+  if (bx && d >= 10) {
+    // X_x variants PU, PP (multiloop closing, d >= 11): one term per b; UU, UP (QM2 with an unpaired start)
+    const int E3 = Mx * M1, G = min(NT3 / E3, max(My, 1)), g = t / E3, e = t % E3;
+    if (g < G) {
+      const int a = e / M1, u = e % M1;
+      T su = 0, sp = 0, xuu = 0, xup = 0;
+      if (d >= 11) {
+        for (int b = g; b < My; b += G) {
+          const T gq = hQB[a * NS + b];
+          if (gq == (T)0) continue;
+          su += gq * (s2<false, false>(q2, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + BLK, Xr + XPP * BLK, u, b, Mv));
+          sp += gq * (s2<false, false>(q2 + 2 * BLK, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + 3 * BLK, Xr + XPP * BLK, u, b, Mv));
+        }
       }
-      atomicAdd(hx + XPU * BLK + pe, (double)(fq * sml * su));
-      atomicAdd(hx + XPP * BLK + pe, (double)(fq * sml * sp));
+      if (g == 0) {
+        const T *r_up = S + SS_MR * BLK, *r_pp = S + (SS_MR + 1) * BLK, *r_uu = S + (SS_MR + 2) * BLK,
+                *r_pu = S + (SS_MR + 3) * BLK;
+        xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
+        xup = eb * (s2<false, true>(hM2 + BLK, r_pp, a, u, My) + s2<false, true>(hM2, r_pu, a, u, My));
+      }
+      R0[t] = su;
+      R1[t] = sp;
+      R2[t] = xuu;
+      R3[t] = xup;
     }
-    if (d >= 10) {
-      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
-      const T *r_up = S + SS_MR * BLK, *r_pp = S + (SS_MR + 1) * BLK, *r_uu = S + (SS_MR + 2) * BLK,
-              *r_pu = S + (SS_MR + 3) * BLK;
-      const T xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
-      const T xup = eb * (s2<false, true>(hM2 + BLK, r_pp, a, u, My) + s2<false, true>(hM2, r_pu, a, u, My));
-      atomicAdd(hx + XUU * BLK + pe, (double)(F * xuu));
-      atomicAdd(hx + XUP * BLK + pe, (double)(F * xup));
+    __syncthreads();
+    if (t < E3) {
+      T su = 0, sp = 0;
+      for (int gg = 0; gg < G; gg++) {
+        su += R0[gg * E3 + t];
+        sp += R1[gg * E3 + t];
+      }
+      const int pe = (t / M1) * NS + (t % M1);
+      double *hx = p.hX + (size_t)x * 4 * BLK;
+      if (d >= 11) {
+        atomicAdd(hx + XPU * BLK + pe, (double)(fq * sml * su));
+        atomicAdd(hx + XPP * BLK + pe, (double)(fq * sml * sp));
+      }
+      atomicAdd(hx + XUU * BLK + pe, (double)(F * R2[t]));
+      atomicAdd(hx + XUP * BLK + pe, (double)(F * R3[t]));
     }
+    __syncthreads();
   }
-  if (by1 && t >= 192 && t < 192 + Mv * My) {
-    const int e = t - 192, v2 = e / My, b = e % My, pe = v2 * NS + b;
-    double *hx = p.hX + (size_t)(y - 1) * 4 * BLK;
-    double xpu = 0, xuu = 0, xpp = 0, xup = 0;
-    if (d >= 11) {
-      const T *q2 = S + SS_Q2I * BLK;
+  if (by1 && (d >= 5 || x == 0)) {
+    // X_{y-1} variants: UP, PP from the multiloop closing (d >= 11, one term
+    // per a); single products of QMpp/QMpu/QM2 adjoints (d >= 5) and of the
+    // exterior prefix (x = 0)
+    const int E4 = Mv * My, G = min(NT3 / E4, max(Mx, 1)), g = t / E4, e = t % E4;
+    if (g < G) {
+      const int v2 = e / My, b = e % My;
       T su = 0, sp = 0;
-      for (int a = 0; a < Mx; a++) {
-        const T g = hQB[a * NS + b];
-        if (g == (T)0) continue;
-        su += g * (s2<false, false>(Xl + XPU * BLK, q2, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 2 * BLK, a, v2, M1));
-        sp += g * (s2<false, false>(Xl + XPU * BLK, q2 + BLK, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 3 * BLK, a, v2, M1));
+      if (d >= 11) {
+        for (int a = g; a < Mx; a += G) {
+          const T gq = hQB[a * NS + b];
+          if (gq == (T)0) continue;
+          su += gq * (s2<false, false>(Xl + XPU * BLK, q2, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 2 * BLK, a, v2, M1));
+          sp += gq * (s2<false, false>(Xl + XPU * BLK, q2 + BLK, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 3 * BLK, a, v2, M1));
+        }
       }
-      xup += (double)(fq * sml * su);
-      xpp += (double)(fq * sml * sp);
+      R0[t] = su;
+      R1[t] = sp;
     }
-    if (d >= 5) {
-      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
-      const T *mpp = S + SS_ML * BLK, *mpu = S + (SS_ML + 1) * BLK, *q2pp = S + (SS_ML + 2) * BLK,
-              *q2pu = S + (SS_ML + 3) * BLK;
-      T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
-      T a3 = s2<true, false>(mpp, hGG, v2, b, Mx), a4 = s2<true, false>(mpu, hGG, v2, b, Mx);
-      if (d >= 10) {
-        a1 += eb * s2<true, false>(q2pp, hM2 + 2 * BLK, v2, b, Mx);
-        a2 += eb * s2<true, false>(q2pu, hM2 + 2 * BLK, v2, b, Mx);
+    __syncthreads();
+    if (t < E4) {
+      const int v2 = t / My, b = t % My, pe = v2 * NS + b;
+      T su = 0, sp = 0;
+      for (int gg = 0; gg < G; gg++) {
+        su += R0[gg * E4 + t];
+        sp += R1[gg * E4 + t];
       }
-      xpu += (double)(F * a1);
-      xuu += (double)(F * a2);
-      xpp += (double)(F * a3);
-      xup += (double)(F * a4);
+      double xpu = 0, xuu = 0, xpp = 0, xup = 0;
+      if (d >= 11) {
+        xup += (double)(fq * sml * su);
+        xpp += (double)(fq * sml * sp);
+      }
+      if (d >= 5) {
+        const T *mpp = S + SS_ML * BLK, *mpu = S + (SS_ML + 1) * BLK, *q2pp = S + (SS_ML + 2) * BLK,
+                *q2pu = S + (SS_ML + 3) * BLK;
+        T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
+        T a3 = s2<true, false>(mpp, hGG, v2, b, Mx), a4 = s2<true, false>(mpu, hGG, v2, b, Mx);
+        if (d >= 10) {
+          a1 += eb * s2<true, false>(q2pp, hM2 + 2 * BLK, v2, b, Mx);
+          a2 += eb * s2<true, false>(q2pu, hM2 + 2 * BLK, v2, b, Mx);
+        }
+        xpu += (double)(F * a1);
+        xuu += (double)(F * a2);
+        xpp += (double)(F * a3);
+        xup += (double)(F * a4);
+      }
+      if (x == 0) {
+        // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
+        const T *q5u = S + SS_Q5UM * BLK, *q5p = S + SS_Q5PM * BLK;
+        const T *hu = S + SS_HQ5U * BLK, *hg = S + SS_HGX * BLK;
+        xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));
+        xpu += (double)(F * s2<true, false>(q5p, hu, v2, b, M0));
+        xup += (double)(F * s2<true, false>(q5u, hg, v2, b, M0));
+        xpp += (double)(F * s2<true, false>(q5p, hg, v2, b, M0));
+      }
+      double *hx = p.hX + (size_t)(y - 1) * 4 * BLK;
+      atomicAdd(hx + XPU * BLK + pe, xpu);
+      atomicAdd(hx + XUU * BLK + pe, xuu);
+      atomicAdd(hx + XPP * BLK + pe, xpp);
+      atomicAdd(hx + XUP * BLK + pe, xup);
     }
-    if (x == 0) {
-      // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
-      const T F = clamp_p2<T>(EAS(d - 1) - Ed);
-      const T *q5u = S + SS_Q5UM * BLK, *q5p = S + SS_Q5PM * BLK;
-      const T *hu = S + SS_HQ5U * BLK, *hg = S + SS_HGX * BLK;
-      xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));
-      xpu += (double)(F * s2<true, false>(q5p, hu, v2, b, M0));
-      xup += (double)(F * s2<true, false>(q5u, hg, v2, b, M0));
-      xpp += (double)(F * s2<true, false>(q5p, hg, v2, b, M0));
-    }
-    atomicAdd(hx + XPU * BLK + pe, xpu);
-    atomicAdd(hx + XUU * BLK + pe, xuu);
-    atomicAdd(hx + XPP * BLK + pe, xpp);
-    atomicAdd(hx + XUP * BLK + pe, xup);
   }
 }
 
@@ -1030,7 +1079,7 @@ __global__ void __launch_bounds__(NT3) k_out_side(DP<T> p, int d) {
 
 template <typename T>
 constexpr size_t out_side_smem() {
-  return ((size_t)(SS_N + 1) * BLK + NT3) * sizeof(T);
+  return ((size_t)(SS_N + 1) * BLK + 4 * NT3) * sizeof(T);
 }
 
 template <typename T, int NTT = NT>

@@ -78,6 +78,12 @@ def algorithmic_flops(res):
     return inside, outside
 
 
+# DRAM traffic of one outside pass of this workload (read + write bytes summed
+# over its kernels), from the ncu launch list with warm caches in
+# profiles/launches_p300_dirichlet_fp32.md; taken on the kernels as committed
+OUTSIDE_DRAM_BYTES_PER_PASS = 9.50e9
+
+
 def sm_peak_tflops(clock_mhz, sms=148):
     return sms * 128 * 2 * clock_mhz * 1e6 / 1e12
 
@@ -471,9 +477,12 @@ def main():
         "accuracy": acc,
         "samples_per_s": samples_per_s,
         "inside_ms": tin / args.steps, "outside_ms": tout / args.steps,
-        "roofline": {"bound": "alu", "kernel": "outside pass (graph of k_out_light + k_out_bif)",
+        "roofline": {"bound": "alu",
+                     "kernel": "outside pass (one CUDA graph: k_out_light, k_out_side, k_out_bif, k_out_far)",
                      "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": OUTSIDE_DRAM_BYTES_PER_PASS if WORKLOAD == "p300_dirichlet" and not args.m else None,
+                     "traffic_unit": "bytes per outside pass (ncu, warm caches)",
                      "peak_basis": f"FP32 FFMA 148 SM x 128 lanes x 2 x {clock:.0f} MHz (median SM clock "
                                    "sampled during the timed region)"},
         "e2e": {"value": cells / e2e_s, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),

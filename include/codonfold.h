@@ -130,7 +130,8 @@ cf_status cf_inside(cf_problem *prob, cf_precision precision, double *logZ);
  *               = d log Z / d codon_logw[r][s] (Eq. marginal-codon).
  *   pair_grad:  61*61 doubles; d log Z / d pair_bonus[c][c'] = expected count
  *               of the adjacent codon pair (c, c') summed over residues.
- * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ECUDA.
+ * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ECUDA, CF_ETIMEOUT (a bounded
+ * device wait for staged inputs gave up; the outputs are then not valid).
  */
 cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, double *pair_grad);
 

@@ -1058,8 +1058,11 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
   std::vector<double> trans((size_t)std::max(m - 1, 1) * BLK), p0(NS);
   CF_CUDA(p, cudaMemcpyAsync(trans.data(), p->dtrans, sizeof(double) * trans.size(), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaMemcpyAsync(p0.data(), p->dp0, sizeof(double) * NS, cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_out, p->ev[2], p->ev[3]));
+  if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "outside: a bounded wait for staged inputs gave up");
   std::vector<double> cm((size_t)m * 6, 0.0), pg(61 * 61, 0.0);
   for (int a = 0; a < p->M[0]; a++) cm[a] = p0[a];
   for (int r = 0; r + 1 < m; r++) {

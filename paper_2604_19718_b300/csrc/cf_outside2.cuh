@@ -773,8 +773,14 @@ struct SideCtx {
   int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
 };
 
+// slots read only by the transfer gradients (cells at a residue boundary)
+__device__ __forceinline__ bool side_slot_tg(int s) {
+  return s < SS_HHB || s == SS_HCH || (s >= SS_HXI && s < SS_HY) || (s >= SS_YYP && s < SS_XIL);
+}
+
 template <typename T>
-__device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu) {
+__device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu,
+                                          unsigned long long *sbar, unsigned phase) {
   T *Hxi = S + (size_t)SS_N * BLK;   // [36]
   T *RED = Hxi + BLK;                // [4][NT3] partial sums of the transfer gradients
   int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
@@ -783,28 +789,57 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   const int n = p.n;
   const int y = x + d;
   const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[y - 1] != 0;
-  if (d < 5 && !(bx || by1)) return;  // no scatter below d = 5
+  if (d < 5 && !(bx || by1)) return true;  // no scatter below d = 5
+  // context values, one load per thread, in flight while the copies are issued
+  int cE = 0, cMx = 0, cMy = 0, cB = 0;
+  T cEn = 0;
+  if (t < 96) {
+    const int k = d - 47 + t;
+    if (k >= 0 && k < n) cE = p.E[k];
+  }
+  if (t < 72) {
+    const int qx = x - 35 + t, qy = y - 35 + t;
+    if (qx >= 0 && qx < n) cMx = p.Mp[qx];
+    if (qy >= 0 && qy < n) cMy = p.Mp[qy];
+  }
+  if (t >= 96 && t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    const int q = (side == 0 ? x : y) - 1 + r;
+    if (q >= 0 && q < n) cB = p.base[q * NS + a];
+  }
+  if (t < EN_N) cEn = p.en[t];
+  // staging: one TMA bulk copy per input block, the interior-loop adjoints
+  // hYY_L (L = 2..Lmax) and partial sums YY_{L-1}[x+1][y] (L = 3..Lmax) as one
+  // copy each; slots of the transfer gradients only for boundary cells
+  const bool tg = bx || by1;
+  const int Lmax = min(MAXLOOP, d - 4);
   for (int s = t; s < SS_N; s += NT3) {
+    if (!tg && side_slot_tg(s)) continue;
+    if (d >= 6 && s > SS_HY && s < SS_YYP && s - SS_HY + 2 <= Lmax) continue;   // part of the hYY run
+    if (d >= 6 && s > SS_YYP && s < SS_XIL && s - SS_YYP + 3 <= Lmax) continue;  // part of the YY run
     const T *src = side_slot_src(p, s, x, y, d);
-    if (src) stage_block(S + (size_t)s * BLK, src);
+    if (!src) continue;
+    unsigned nb = 1;
+    if (s == SS_HY) nb = (unsigned)(Lmax - 1);
+    else if (s == SS_YYP) nb = (unsigned)(Lmax - 2);
+    const unsigned bytes = nb * BLK * (unsigned)sizeof(T);
+    mbar_expect(sbar, bytes);
+    bulk_g2s(S + (size_t)s * BLK, src, bytes, sbar);
   }
-  for (int i = t; i < 96; i += NT3) {
-    const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < n) ? p.E[k] : 0;
-  }
-  for (int i = t; i < 72; i += NT3) {
-    const int qx = x - 35 + i, qy = y - 35 + i;
-    sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
-    sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
-  }
-  for (int i = t; i < 3 * NS; i += NT3) {
-    const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
-    sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
-    sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
-  }
-  for (int i = t; i < EN_N; i += NT3) sEn[i] = p.en[i];
-  cp_async_wait_all();
   __syncthreads();
+  if (t == 0) mbar_arrive(sbar);
+  if (t < 96) sE[t] = cE;
+  if (t < 72) {
+    sMx[t] = cMx;
+    sMy[t] = cMy;
+  }
+  if (t >= 96 && t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    if (side == 0) sBx[r][a] = cB;
+    else sBy[r][a] = cB;
+  }
+  if (t < EN_N) sEn[t] = cEn;
+  if (!__syncthreads_and(mbar_wait(sbar, phase, p.err))) return false;
   const T *en = sEn;
   const int Ed = sE[47];  // E[d], staged with its neighbours
   const int Mx = MP(x), My = MP(y), MM = Mx * My;
@@ -815,7 +850,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
     const int L = t;
     wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed) : (T)0;
   }
-  if (d >= 6 && t >= 64 && t < 64 + MM) {
+  if (tg && d >= 6 && t >= 64 && t < 64 + MM) {
     // adjoint of XI[x][y] (its own L = 2 term included) times the inner mismatch
     const int e = t - 64, a = e / My, b = e % My, pe = a * NS + b;
     Hxi[pe] = S[SS_HXI * BLK + pe] * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
@@ -868,7 +903,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   // Four phases, one per gradient block; in each, the live entries of the
   // block times groups of its summation terms are spread over all threads,
   // and the group partial sums are added per entry before the binary64 add.
-  if (!(bx || by1)) return;
+  if (!tg) return true;
   const T *hQB = S + SS_HGC * BLK, *hCHf = S + SS_HCH * BLK, *hM2 = S + SS_HM2 * BLK;
   const T *hMPU = S + SS_HMPU * BLK, *hGG = S + SS_HG * BLK;
   const T *Tx = S + SS_TX * BLK, *Ty1 = S + SS_TY1 * BLK;
@@ -877,7 +912,6 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
   const T *q2 = S + SS_Q2I * BLK;  // QM2 uu, up, pu, pp of (x+1, y-1)
   const T fq = clamp_p2<T>((d >= 2 ? EAS(d - 2) : 0) - Ed);
   const T F = clamp_p2<T>(EAS(d - 1) - Ed);
-  const int Lmax = min(MAXLOOP, d - 4);
   T *R0 = RED, *R1 = RED + NT3, *R2 = RED + 2 * NT3, *R3 = RED + 3 * NT3;
   if (bx) {
     // T_x[a][u]: terms QB (one per b), XI (one per z), chain, YY_L (L = 3..Lmax)
@@ -1062,6 +1096,7 @@ __device__ __forceinline__ void side_cell(const DP<T> &p, int d, int x, T *S, Si
       atomicAdd(hx + XUP * BLK + pe, xup);
     }
   }
+  return true;
 }
 
 
@@ -1071,10 +1106,39 @@ __global__ void __launch_bounds__(NT3) k_out_side(DP<T> p, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SideCtx cx;
   __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
+  __shared__ __align__(8) unsigned long long sbar;
+  if (threadIdx.x == 0) mbar_init(&sbar, 1);
+  __syncthreads();
+  unsigned phase = 0;
   for (int x = blockIdx.x; x < p.n - d; x += gridDim.x) {
-    side_cell(p, d, x, (T *)smem_raw, cx, sEn, wBu);
+    // cells with no scatter (d < 5, no boundary) issue no copies and use no phase
+    const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[x + d - 1] != 0;
+    const bool staged = !(d < 5 && !(bx || by1));
+    if (!side_cell(p, d, x, (T *)smem_raw, cx, sEn, wBu, &sbar, phase)) return;
+    if (staged) phase ^= 1u;
+    fence_proxy_async();
     __syncthreads();
   }
+}
+
+// The off-chain work that the light kernel of diagonal d waits for, as one
+// launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (cells
+// and exterior), the others the side work of the cells of diagonal d+4.  Both
+// parts start after the light kernel of d+4.
+template <typename T>
+__global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[16][BLK];
+  __shared__ SideCtx cx;
+  __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
+  __shared__ __align__(8) unsigned long long sbar;
+  if ((int)blockIdx.x < nbif) {
+    out_bif_cell(p, ob, d, blockIdx.x, red);
+    return;
+  }
+  if (threadIdx.x == 0) mbar_init(&sbar, 1);
+  __syncthreads();
+  side_cell(p, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u);
 }
 
 template <typename T>

@@ -451,6 +451,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smemw));
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_side<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   DP<T> dp = t.dp;
@@ -503,16 +504,22 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       }
       if (e != cudaSuccess) break;
     }
-    const bool hasb = d <= n - 5 && d >= 1;
-    if (hasb) {
+    // one off-chain launch per diagonal d: the bifurcation gathers of d and the
+    // side work of d+4 (its scatters land on diagonals <= d), both after the
+    // light kernel of d+4
+    const bool hasb = d <= n - 5 && d >= 1, hass = d + 4 <= n - 1;
+    if (hasb || hass) {
+      int nbif = hasb ? n - d + 1 : 0;
+      void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
-      kp.func = (void *)k_out_bif<T>;
-      kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
-      kp.blockDim = dim3(256);
-      kp.kernelParams = args;
+      kp.func = (void *)k_out_off<T>;
+      kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0));
+      kp.blockDim = dim3(NT3);
+      kp.sharedMemBytes = (unsigned)smem3;
+      kp.kernelParams = oargs;
       cudaGraphNode_t bdeps[3] = {k2[d + 4], nullptr, nullptr};
       int nb = 1;
-      if (fb) {
+      if (hasb && fb) {
         bdeps[nb++] = kfr[alo / OFD];
         bdeps[nb++] = kfc[alo / OFD];
       }
@@ -524,8 +531,8 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     cudaGraphNode_t deps[3];
     int nd = 0;
     deps[nd++] = (d == n - 1) ? m[4] : k2[d + 1];
-    if (hasb) deps[nd++] = k1[d];
-    if (d + 4 < n && k3[d + 4]) deps[nd++] = k3[d + 4];  // side work of d+4 lands on diagonals <= d
+    if (hasb || hass) deps[nd++] = k1[d];
+    if (d + 4 < n && k3[d + 4]) deps[nd++] = k3[d + 4];  // side work launched on its own (d+4 <= 3)
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;
     kp.func = wide ? (void *)k_out_light<T, NT_WIDE> : (void *)k_out_light<T, NT>;
@@ -536,7 +543,8 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
-    if (e == cudaSuccess && d >= 1) {
+    if (e == cudaSuccess && d >= 1 && d <= 3) {
+      // the side work of d = 1..3 has no bifurcation launch of d-4 to ride on
       void *args3[] = {&dp, &dd};
       cudaKernelNodeParams k3p = {};
       k3p.func = (void *)k_out_side<T>;

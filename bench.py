@@ -303,6 +303,49 @@ def bench_adjoint(stream):
             "max_gap_last": hist[-1]["max_gap"]}
 
 
+def bench_small_batch(nstreams=32, count=4096):
+    """Proteins/s on the 4,096-protein batch of 8-residue (24-nt) proteins:
+    inside + outside per protein, each worker thread with its own problem on
+    its own stream (a new protein of the same length reuses the problem's
+    tables and graphs), in the binary64 form and in the binary32 form."""
+    import torch
+
+    import paper_2604_19718_b300 as cf
+    prots = synth.batch_p8(count)
+    params = synth.nn_params(0)
+    out = {"proteins": count, "nt": 24, "streams": nstreams}
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    folds = [cf.CodonFold(params, stream=s.cuda_stream) for s in streams]
+    for prec, key in ((cf.CF_FP64, "fp64"), (cf.CF_FP32_SCALED, "fp32")):
+        lz = np.zeros(count)
+
+        def work(k):
+            f = folds[k]
+            for i in range(k, count, nstreams):
+                f.set_protein(prots[i])
+                lz[i] = f.inside(prec)
+                f.outside(True, True, False)
+
+        for k in range(nstreams):  # warm-up: tables and graphs of every problem
+            folds[k].set_protein(prots[k])
+            folds[k].inside(prec)
+            folds[k].outside(True, True, False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        threads = [threading.Thread(target=work, args=(k,)) for k in range(nstreams)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[key + "_proteins_per_s"] = count / dt
+        out[key + "_logZ_first"] = float(lz[0])
+    for f in folds:
+        f.close()
+    return out
+
+
 def bench_large(stream, nsamples=10_000):
     """The 1000-aa / 3000-nt soft-weighted protein in binary32."""
     import paper_2604_19718_b300 as cf
@@ -450,6 +493,7 @@ def main():
         del wdata
         forms["adjoint"] = bench_adjoint(stream.cuda_stream)
         forms["large"] = bench_large(stream.cuda_stream)
+        forms["small_batch"] = bench_small_batch()
 
     if rank != 0:
         return

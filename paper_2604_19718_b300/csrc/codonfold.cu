@@ -752,13 +752,39 @@ cf_status check_weights(cf_problem *p, int m, const double *lw, const double *pb
   return CF_OK;
 }
 
+// Zero every table of a precision (a new protein of the same length reuses
+// them: the kernels leave the padding of a block beyond the codon-state
+// counts untouched, so it must not keep the previous protein's values).
+template <typename T>
+cf_status clear_tables(cf_problem *p, PrecTables<T> &t) {
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  cudaStream_t st = p->stream;
+  DP<T> &d = t.dp;
+  if (t.inside_alloc) {
+    T *tabs[] = {d.CH, d.QB, d.XI, d.HB, d.QMpp, d.QMpu, d.G, d.QM2pp, d.QM2pu, d.QM2up, d.QM2uu};
+    for (T *q : tabs) CF_CUDA(p, cudaMemsetAsync(q, 0, nc * sizeof(T), st));
+    CF_CUDA(p, cudaMemsetAsync(d.YY, 0, nc * NYY * sizeof(T), st));
+    T *ext[] = {d.Q5U, d.Q5P, d.Gx};
+    for (T *q : ext) CF_CUDA(p, cudaMemsetAsync(q, 0, (size_t)n * BLK * sizeof(T), st));
+  }
+  if (t.outside_alloc) {
+    T *tabs[] = {d.hCH, d.hQB, d.hGc, d.hXI, d.hHB, d.hQMpp, d.hQMpu, d.hG, d.hQM2pp, d.hQM2pu, d.hQM2up, d.hQM2uu};
+    for (T *q : tabs) CF_CUDA(p, cudaMemsetAsync(q, 0, nc * sizeof(T), st));
+    CF_CUDA(p, cudaMemsetAsync(d.hYY, 0, (size_t)YRING * n * NYY * BLK * sizeof(T), st));
+    T *ext[] = {d.hQ5U, d.hQ5P, d.hGx};
+    for (T *q : ext) CF_CUDA(p, cudaMemsetAsync(q, 0, (size_t)n * BLK * sizeof(T), st));
+  }
+  return CF_OK;
+}
+
 template <typename T>
 cf_status upload_transfers(cf_problem *p, PrecTables<T> &t) {
   if (!t.inside_alloc) return CF_OK;  // uploaded when the tables are first made
-  std::vector<T> h(p->Tr.begin(), p->Tr.end());
-  CF_CUDA(p, cudaMemcpy((void *)t.dp.Tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-  h.assign(p->X.begin(), p->X.end());
-  CF_CUDA(p, cudaMemcpy((void *)t.dp.X, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  std::vector<T> h(p->Tr.begin(), p->Tr.end()), hx(p->X.begin(), p->X.end());
+  CF_CUDA(p, cudaMemcpyAsync((void *)t.dp.Tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+  CF_CUDA(p, cudaMemcpyAsync((void *)t.dp.X, hx.data(), hx.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+  CF_CUDA(p, cudaStreamSynchronize(p->stream));
   return CF_OK;
 }
 
@@ -977,7 +1003,15 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
   }
   if (check_weights(p, m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_protein: " + p->err);
   CF_CUDA(p, cudaSetDevice(p->device));
-  release_protein(p);
+  // a protein of the same length reuses the device tables and the pass graphs
+  // (they depend on the length only): no allocation, no device-wide sync
+  const bool reuse = p->n == 3 * m && p->dM != nullptr;
+  if (reuse) {
+    CF_CUDA(p, cudaStreamSynchronize(p->stream));  // no pass may still read the old protein
+    p->have_inside = false;
+  } else {
+    release_protein(p);
+  }
   const int n = 3 * m;
   p->n = n;
   p->m = m;
@@ -1003,23 +1037,36 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     double e = (L <= MAXLOOP) ? p->model->params[36 + L] : H30 + 1.07856 * std::log((double)L / MAXLOOP);
     p->eHL[L] = std::exp(-e / kT);
   }
-  auto &S = p->shared_allocs;
-  CF_CUDA(p, dalloc(S, &p->dM, (size_t)n));
-  CF_CUDA(p, dalloc(S, &p->dbase, (size_t)n * NS));
-  CF_CUDA(p, dalloc(S, &p->dbnd, (size_t)n));
-  CF_CUDA(p, dalloc(S, &p->dE, (size_t)n));
-  CF_CUDA(p, dalloc(S, &p->derr, (size_t)1));
-  CF_CUDA(p, dalloc(S, &p->ddmax, (size_t)n));
-  CF_CUDA(p, dalloc(S, &p->du0, (size_t)NS));
-  CF_CUDA(p, dalloc(S, &p->dZm, (size_t)1));
-  CF_CUDA(p, dalloc(S, &p->dtrans, (size_t)std::max(m - 1, 1) * BLK));
-  CF_CUDA(p, dalloc(S, &p->dp0, (size_t)NS));
-  CF_CUDA(p, dalloc(S, &p->dP, (size_t)n * n));
-  CF_CUDA(p, cudaMemcpy(p->dM, p->M.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-  CF_CUDA(p, cudaMemcpy(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice));
-  CF_CUDA(p, cudaMemcpy(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-  CF_CUDA(p, cudaMemcpy(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice));
-  CF_CUDA(p, cudaMemset(p->dE, 0, sizeof(int) * n));
+  if (!reuse) {
+    auto &S = p->shared_allocs;
+    CF_CUDA(p, dalloc(S, &p->dM, (size_t)n));
+    CF_CUDA(p, dalloc(S, &p->dbase, (size_t)n * NS));
+    CF_CUDA(p, dalloc(S, &p->dbnd, (size_t)n));
+    CF_CUDA(p, dalloc(S, &p->dE, (size_t)n));
+    CF_CUDA(p, dalloc(S, &p->derr, (size_t)1));
+    CF_CUDA(p, dalloc(S, &p->ddmax, (size_t)n));
+    CF_CUDA(p, dalloc(S, &p->du0, (size_t)NS));
+    CF_CUDA(p, dalloc(S, &p->dZm, (size_t)1));
+    CF_CUDA(p, dalloc(S, &p->dtrans, (size_t)std::max(m - 1, 1) * BLK));
+    CF_CUDA(p, dalloc(S, &p->dp0, (size_t)NS));
+    CF_CUDA(p, dalloc(S, &p->dP, (size_t)n * n));
+  }
+  cudaStream_t st = p->stream;
+  CF_CUDA(p, cudaMemcpyAsync(p->dM, p->M.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
+  if (reuse && p->smp_cap > 0)  // the sampler's codon ids of the new protein
+    CF_CUDA(p, cudaMemcpyAsync(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  if (reuse) {
+    cf_status s = clear_tables(p, p->f32);
+    if (s == CF_OK) s = clear_tables(p, p->f64);
+    if (s == CF_OK) s = upload_transfers(p, p->f32);
+    if (s == CF_OK) s = upload_transfers(p, p->f64);
+    if (s != CF_OK) return s;
+  }
   return CF_OK;
 }
 
@@ -1034,7 +1081,8 @@ cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
   cf_status s = upload_transfers(p, p->f32);
   if (s == CF_OK) s = upload_transfers(p, p->f64);
   if (s != CF_OK) return s;
-  CF_CUDA(p, cudaMemcpy(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpyAsync(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, p->stream));
+  CF_CUDA(p, cudaStreamSynchronize(p->stream));
   return CF_OK;
 }
 

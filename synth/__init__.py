@@ -102,6 +102,13 @@ def workload(name: str):
     raise KeyError(name)
 
 
+def batch_p8(count: int = 4096):
+    """The small-protein throughput batch: `count` proteins of 8 residues,
+    protein k drawn uniformly over the 20 amino acids with seed k (protein 0
+    is p8_uniform)."""
+    return [residues_uniform(8, k) for k in range(count)]
+
+
 # Standard genetic code, codons in lexicographic order over A, C, G, U
 # (AAA, AAC, ..., UUU); '*' marks the three stop codons.
 GENETIC_CODE = "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF"

@@ -142,3 +142,35 @@ def test_repeatable_and_device_outputs():
     assert np.array_equal(Pd.cpu().numpy(), P) or np.abs(Pd.cpu().numpy() - P).max() < 1e-6
     assert np.abs(cmd.cpu().numpy() - cm).max() < 1e-9
     f.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_same_length_protein_reuses_tables(prec):
+    """A second protein of the same length on the same problem (tables and
+    graphs reused) gives what a fresh problem gives, and matches the oracle."""
+    cf = _cf()
+    res, lw, pb = synth.workload("p300_weighted")
+    a, b = slice(0, 40), slice(40, 80)
+    f = cf.CodonFold(P0)
+    f.set_protein(res[a], lw[a], pb)
+    f.inside(prec)
+    f.outside()
+    f.sample(64, 5)
+    f.set_protein(res[b], lw[b], pb)
+    lz = f.inside(prec)
+    P, cm, pg = f.outside()
+    cod, par = f.sample(64, 5)
+    f.close()
+    g = cf.CodonFold(P0)
+    g.set_protein(res[b], lw[b], pb)
+    lz2 = g.inside(prec)
+    P2, cm2, pg2 = g.outside()
+    cod2, par2 = g.sample(64, 5)
+    g.close()
+    assert lz == lz2
+    assert np.abs(P - P2).max() < 1e-6 and np.abs(cm - cm2).max() < 1e-9
+    assert np.array_equal(cod, cod2) and np.array_equal(par, par2)
+    o = oracle.outside(P0, res[b], lw[b], pb)
+    tl, tm, tp = TOL[prec]
+    assert abs(lz - o["logZ"]) <= tl * max(1.0, abs(o["logZ"]))
+    assert np.abs(cm - o["codon"]).max() <= tm and np.abs(P - o["P"]).max() <= tp

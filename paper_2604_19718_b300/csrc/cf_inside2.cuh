@@ -157,6 +157,82 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   }
 }
 
+// Near split points of a banded diagonal are few (at most 2 (2 FARD - 5)):
+// two warps per cell, four cells per 256-thread CTA.  Same sums and order
+// of additions per cell as in_bif_cell with NW = 2.
+template <typename T>
+__device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb, int d, int cb0, T (*red)[BLK]) {
+  constexpr int NW = 2, NG = 4;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / NW, wg = w % NW;
+  const int n = p.n, ncell = n - d;
+  const int Eref = __ldcg(p.E + d - 4);
+  const int slot = d % BIFRING;
+  const int d0 = d / FARD * FARD;
+  const bool banded = bb.far != nullptr && far_band(d0);
+  int a1 = d - 4, a2 = d - 3;
+  if (banded) {
+    const int c = far_c(d0), alo = max(5, d - c), ahi = min(c, d - 4);
+    if (alo <= ahi) {
+      a1 = alo - 1;
+      a2 = ahi + 1;
+    }
+  }
+  const int cb = cb0 + g;
+  if (cb < ncell) {
+    const int x = cb, y = x + d;
+    const int Ma = p.Mp[x], Mb = p.Mp[y];
+    T acc[BLK];
+    zero_block(acc);
+    const int n1 = max(0, a1 - 4), n2 = max(0, d - 3 - a2);
+    const int nc = (n1 + n2 + KCH - 1) / KCH;
+    const T ec = p.en[EN_EC];
+    for (int c = wg; c < nc; c += NW) {
+      const int q = c * KCH + lane;
+      if (q < n1 + n2) {
+        const int k = x + (q < n1 ? 5 + q : a2 + q - n1);
+        T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
+        acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
+      }
+    }
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
+#pragma unroll
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[w][e] = acc[e];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NG * BLK) {
+    const int g2 = threadIdx.x / BLK, e = threadIdx.x % BLK, cb2 = cb0 + g2;
+    if (cb2 < ncell) {
+      const int x = cb2;
+      T v = red[g2 * NW][e] + red[g2 * NW + 1][e];
+      if (banded) {
+        // far split points: the slices of the cell's tile in order, relative to 2^{s d + 2 e0}
+        const FarChord ch = far_chord(p.E, far_c(d0));
+        const int nsl = far_nslice(n, x / FARTX * FARTX, d0);
+        const float *fp = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + (d - d0)) * bb.farslices) * BLK + e;
+        float fv = 0.f;
+        for (int sl = 0; sl < nsl; sl++) fv += fp[(size_t)sl * BLK];
+        v += (T)((double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref) * (double)fv);
+      }
+      bb.main[((size_t)slot * n + x) * BLK + e] = v;
+    }
+  }
+}
+
+// binary32 with far bands: CTA b < last takes cells 4b..4b+3, the last CTA the
+// exterior sum with all eight warps
+template <typename T>
+__global__ void __launch_bounds__(256) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
+  __shared__ T red[8][BLK];
+  if ((int)blockIdx.x == (int)gridDim.x - 1) {
+    in_bif_cell<T, 8>(p, bb, d, p.n - d, red);
+    return;
+  }
+  in_bif_group<T>(p, bb, d, blockIdx.x * 4, red);
+}
+
 // Grid-stride over the n-d cells and the exterior: launched with fewer CTAs
 // than cells, so that the light kernels of the critical path always find
 // room on the SMs.

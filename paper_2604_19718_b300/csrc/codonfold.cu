@@ -352,8 +352,13 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     }
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
-      kp.func = (void *)k_in_bif<T>;
-      kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
+      if (banded) {  // few near split points: two warps per cell
+        kp.func = (void *)k_in_bif_grp<T>;
+        kp.gridDim = dim3((n - d + 3) / 4 + 1);
+      } else {
+        kp.func = (void *)k_in_bif<T>;
+        kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
+      }
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
       cudaGraphNode_t bdeps[2] = {k2[d - 4], nullptr};

@@ -176,6 +176,72 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
   }
 }
 
+// binary32: at most one chunk of near terms per gather and cell (a banded
+// diagonal keeps fewer than KCH near terms; an unbanded one lies within
+// 2 OFD + 3 of the last diagonal), so a pair of warps per cell (row gather,
+// column gather) and four cells per 256-thread CTA; same sums as
+// out_bif_cell.
+template <typename T>
+__device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &ob, int d, int cb0, T (*red)[BLK]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w >> 1;
+  const int n = p.n, ncell = n - d;
+  const int *E = p.E;
+  const int Ed = E[d];
+  const int slot = d % BIFRING;
+  const T ec = p.en[EN_EC];
+  const int alo = d / OFD * OFD;
+  const bool banded = ob.far != nullptr && of_band(n, alo);
+  if (cb0 + g < ncell) {
+    const int x = cb0 + g, y = x + d;
+    const int Ma = p.Mp[x], Mb = p.Mp[y];
+    T acc[BLK];
+    zero_block(acc);
+    if ((w & 1) == 0) {
+      const int ylim = banded ? min(n - 1, x + of_c(alo) - 1) : n - 1;
+      const int nr = ylim >= y + 4 ? (ylim - y - 4 + KCH) / KCH : 0;
+      for (int q = 0; q < nr; q++) {
+        const int yy = y + 4 + q * KCH + lane;
+        if (yy <= ylim) {
+          T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
+          acc_mm_v<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+        }
+      }
+    } else {
+      const int xlo = banded ? max(0, y - of_c(alo) + 1) : 0;
+      const int nq = x - 5 >= xlo ? (x - 5 - xlo + KCH) / KCH : 0;
+      for (int q = 0; q < nq; q++) {
+        const int xx = x - 5 - q * KCH - lane;
+        if (xx >= xlo) {
+          T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
+          acc_mm_v<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
+        }
+      }
+    }
+    warp_reduce_block(acc, Ma, Mb);
+    if (lane < 2) {
+#pragma unroll
+      for (int e = 0; e < BLK; e++)
+        if ((e & 1) == lane) red[w][e] = acc[e];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 * BLK) {
+    const int g2 = threadIdx.x / BLK, e = threadIdx.x % BLK, x = cb0 + g2;
+    if (x < ncell) {
+      T v = red[2 * g2][e], u = red[2 * g2 + 1][e];
+      if (banded) {
+        const OChord ch = of_chord(E, n);
+        const double fac = (double)ec * exp2((double)Ed - ch.s * (double)d);
+        const size_t fo = (((size_t)((alo / OFD) % 3) * n + x) * OFD + (d - alo)) * BLK + e;
+        v += (T)(fac * (double)ob.far[fo]);
+        u += (T)(fac * (double)ob.far[(size_t)3 * n * OFD * BLK + fo]);
+      }
+      ob.hg[((size_t)slot * n + x) * BLK + e] = v;
+      ob.hq[((size_t)slot * n + x) * BLK + e] = u;
+    }
+  }
+}
+
 // Grid-stride over the cells and the exterior (see k_in_bif).
 template <typename T>
 __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
@@ -1122,9 +1188,10 @@ __global__ void __launch_bounds__(NT3) k_out_side(DP<T> p, int d) {
 }
 
 // The off-chain work that the light kernel of diagonal d waits for, as one
-// launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (cells
-// and exterior), the others the side work of the cells of diagonal d+4.  Both
-// parts start after the light kernel of d+4.
+// launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (one
+// cell per CTA, or with far bands four cells per CTA, then the exterior), the
+// others the side work of the cells of diagonal d+4.  Both parts start after
+// the light kernel of d+4.
 template <typename T>
 __global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1133,7 +1200,12 @@ __global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, i
   __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
   __shared__ __align__(8) unsigned long long sbar;
   if ((int)blockIdx.x < nbif) {
-    out_bif_cell(p, ob, d, blockIdx.x, red);
+    if (ob.far == nullptr)
+      out_bif_cell(p, ob, d, blockIdx.x, red);
+    else if ((int)blockIdx.x == nbif - 1)
+      out_bif_cell(p, ob, d, p.n - d, red);
+    else
+      out_bif_group(p, ob, d, blockIdx.x * 4, red);
     return;
   }
   if (threadIdx.x == 0) mbar_init(&sbar, 1);

@@ -514,7 +514,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     // light kernel of d+4
     const bool hasb = d <= n - 5 && d >= 1, hass = d + 4 <= n - 1;
     if (hasb || hass) {
-      int nbif = hasb ? n - d + 1 : 0;
+      int nbif = hasb ? (banded ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
       void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_out_off<T>;

@@ -87,6 +87,7 @@ struct DP {
   T *hCH, *hQB, *hGc, *hXI, *hHB, *hQMpp, *hQMpu, *hG, *hQM2pp, *hQM2pu, *hQM2up, *hQM2uu;
   T *hYY;           // ring [YRING][n][29*36]
   T *hQ5U, *hQ5P, *hGx; // [n*36]
+  T *tgY;           // [ncell*36] sum_L hYY_L[x][y] YY_{L-1}[x+1][y]^T of cells with a boundary at x
   double *hT;       // [n*36]   d log Z / d T_p (boundary positions)
   double *hX;       // [n*4*36] d log Z / d X_p (boundary positions)
   float *P;         // [n*n] pair probabilities (device)

@@ -847,15 +847,13 @@ __device__ __forceinline__ bool side_slot_tg(int s) {
 template <typename T>
 __device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu,
                                           unsigned long long *sbar, unsigned phase) {
-  T *Hxi = S + (size_t)SS_N * BLK;   // [36]
-  T *RED = Hxi + BLK;                // [4][NT3] partial sums of the transfer gradients
   int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
   int (*sBx)[NS] = cx.sBx, (*sBy)[NS] = cx.sBy;
   const int t = threadIdx.x;
   const int n = p.n;
   const int y = x + d;
-  const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[y - 1] != 0;
-  if (d < 5 && !(bx || by1)) return true;  // no scatter below d = 5
+  const bool bx = p.bnd[x] != 0;
+  if (d < 5) return true;  // no scatter below d = 5
   // context values, one load per thread, in flight while the copies are issued
   int cE = 0, cMx = 0, cMy = 0, cB = 0;
   T cEn = 0;
@@ -876,11 +874,12 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, Si
   if (t < EN_N) cEn = p.en[t];
   // staging: one TMA bulk copy per input block, the interior-loop adjoints
   // hYY_L (L = 2..Lmax) and partial sums YY_{L-1}[x+1][y] (L = 3..Lmax) as one
-  // copy each; slots of the transfer gradients only for boundary cells
-  const bool tg = bx || by1;
+  // copy each; the partial sums only for a boundary at x (the ring term of the
+  // transfer gradient T_x)
+  const bool ytg = bx && d >= 6;
   const int Lmax = min(MAXLOOP, d - 4);
   for (int s = t; s < SS_N; s += NT3) {
-    if (!tg && side_slot_tg(s)) continue;
+    if (side_slot_tg(s) && !(ytg && s >= SS_YYP && s < SS_XIL)) continue;
     if (d >= 6 && s > SS_HY && s < SS_YYP && s - SS_HY + 2 <= Lmax) continue;   // part of the hYY run
     if (d >= 6 && s > SS_YYP && s < SS_XIL && s - SS_YYP + 3 <= Lmax) continue;  // part of the YY run
     const T *src = side_slot_src(p, s, x, y, d);
@@ -908,21 +907,22 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, Si
   if (!__syncthreads_and(mbar_wait(sbar, phase, p.err))) return false;
   const T *en = sEn;
   const int Ed = sE[47];  // E[d], staged with its neighbours
-  const int Mx = MP(x), My = MP(y), MM = Mx * My;
-  const int M1 = (d >= 1) ? MP(x + 1) : 0, Mv = (d >= 1) ? MP(y - 1) : 0;
-  const int M0 = MP(0);
-  const T eb = en[EN_EB], sml = en[EN_EA] * en[EN_EC];
+  const int Mx = MP(x), My = MP(y), M1 = MP(x + 1);
   if (t <= MAXLOOP) {
     const int L = t;
     wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed) : (T)0;
   }
-  if (tg && d >= 6 && t >= 64 && t < 64 + MM) {
-    // adjoint of XI[x][y] (its own L = 2 term included) times the inner mismatch
-    const int e = t - 64, a = e / My, b = e % My, pe = a * NS + b;
-    Hxi[pe] = S[SS_HXI * BLK + pe] * en[EN_TM + BASE(y, b) * 4 + BASE(x, a)];
-  }
   __syncthreads();
   const T *hHB = S + SS_HHB * BLK, *HY = S + SS_HY * BLK;
+
+  T *YtP = S + (size_t)SS_N * BLK;  // [6][36] partial sums of the ring term of T_x
+  if (ytg && t >= NT3 - 6 * BLK) {
+    const int i = t - (NT3 - 6 * BLK), j = i / BLK, e = i % BLK, a = e / NS, u = e % NS;
+    T v = 0;
+    if (a < Mx && u < M1)
+      for (int L = 3 + j; L <= Lmax; L += 6) v += s2<false, true>(HY + (L - 2) * BLK, S + (SS_YYP + L - 3) * BLK, a, u, My);
+    YtP[i] = v;
+  }
 
   // ---------------- bulge and interior scatters, one block row per thread and step
   //   bulge 3' (L = 1..30):  hCH[y-L][y] += wBu(L) QB[x][y-L]^T hHB
@@ -965,227 +965,25 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, Si
     }
   }
 
-  // ---------------- gradients of the boundary transfers T_x, T_{y-1}, X_x, X_{y-1}
-  // Four phases, one per gradient block; in each, the live entries of the
-  // block times groups of its summation terms are spread over all threads,
-  // and the group partial sums are added per entry before the binary64 add.
-  if (!tg) return true;
-  const T *hQB = S + SS_HGC * BLK, *hCHf = S + SS_HCH * BLK, *hM2 = S + SS_HM2 * BLK;
-  const T *hMPU = S + SS_HMPU * BLK, *hGG = S + SS_HG * BLK;
-  const T *Tx = S + SS_TX * BLK, *Ty1 = S + SS_TY1 * BLK;
-  const T *hbi = S + SS_HBI * BLK, *qin = S + SS_QBI * BLK;
-  const T *Xl = S + SS_XX * BLK, *Xr = S + SS_XY1 * BLK;
-  const T *q2 = S + SS_Q2I * BLK;  // QM2 uu, up, pu, pp of (x+1, y-1)
-  const T fq = clamp_p2<T>((d >= 2 ? EAS(d - 2) : 0) - Ed);
-  const T F = clamp_p2<T>(EAS(d - 1) - Ed);
-  T *R0 = RED, *R1 = RED + NT3, *R2 = RED + 2 * NT3, *R3 = RED + 3 * NT3;
-  if (bx) {
-    // T_x[a][u]: terms QB (one per b), XI (one per z), chain, YY_L (L = 3..Lmax)
-    const int E1 = Mx * M1, nq = d >= 4 ? My : 0, nz = d >= 6 ? My : 0, nL = d >= 6 ? Lmax - 2 : 0;
-    const int nterm = nq + nz + 1 + nL, G = min(NT3 / E1, nterm), g = t / E1, e = t % E1;
-    if (g < G) {
-      const int a = e / M1, u = e % M1;
-      T sacc = 0;
-      for (int k = g; k < nterm; k += G) {
-        if (k < nq) {
-          const int b = k;
-          const T gq = hQB[a * NS + b];
-          if (gq == (T)0) continue;
-          T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
-          if (d >= 6) {
-            const int pto = pair_type(BASE(x, a), BASE(y, b));
-            const int bu = BASE((x + 1), u);
-            for (int b2 = 0; b2 < Mv; b2++) {
-              const int pti = pair_type(bu, BASE((y - 1), b2));
-              if (pti < 0 || pto < 0) continue;
-              tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
-            }
-          }
-          sacc += fq * gq * tt;
-        } else if (k < nq + nz) {
-          const int z = k - nq;
-          sacc += fq * Hxi[a * NS + z] * s2<false, false>(qin, Ty1, u, z, Mv);
-        } else if (k == nq + nz) {
-          if (d >= 1) sacc += s2<false, true>(hCHf, S + SS_CHN * BLK, a, u, My);
-        } else {
-          const int L = k - nq - nz - 1 + 3;
-          sacc += s2<false, true>(HY + (L - 2) * BLK, S + (SS_YYP + L - 3) * BLK, a, u, My);
-        }
-      }
-      R0[t] = sacc;
-    }
+  // ---------------- the one transfer-gradient term that reads the ring of
+  // interior-loop adjoints: sum_L hYY_L YY_{L-1}[x+1][y]^T for T_x (the rest
+  // of the transfer gradients is summed after the pass by k_out_tg); six
+  // partial sums over L = 3+j, 9+j, ... added in order
+  if (ytg) {
     __syncthreads();
-    if (t < E1) {
-      T v = 0;
-      for (int gg = 0; gg < G; gg++) v += R0[gg * E1 + t];
-      atomicAdd(p.hT + (size_t)x * BLK + (t / M1) * NS + (t % M1), (double)v);
-    }
-    __syncthreads();
-  }
-  if (by1) {
-    // T_{y-1}[v2][b]: one term per a
-    const int E2 = Mv * My, G = min(NT3 / E2, max(Mx, 1)), g = t / E2, e = t % E2;
-    if (g < G) {
-      const int v2 = e / My, b = e % My;
-      T sacc = 0;
-      for (int a = g; a < Mx; a += G) {
-        if (d >= 4) {
-          const T gg = hQB[a * NS + b];
-          if (gg != (T)0) {
-            T tt = s2<false, false>(Tx, hbi, a, v2, M1);
-            if (d >= 6) {
-              const int pto = pair_type(BASE(x, a), BASE(y, b));
-              const int bv = BASE((y - 1), v2);
-              for (int a2 = 0; a2 < M1; a2++) {
-                const int pti = pair_type(BASE((x + 1), a2), bv);
-                if (pti < 0 || pto < 0) continue;
-                tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
-              }
-            }
-            sacc += fq * gg * tt;
-          }
-        }
-        if (d >= 6) sacc += fq * s2<false, false>(Tx, qin, a, v2, M1) * Hxi[a * NS + b];
+    if (t < BLK) {
+      const int a = t / NS, u = t % NS;
+      if (a < Mx && u < M1) {
+        T v = 0;
+#pragma unroll
+        for (int j = 0; j < 6; j++) v += YtP[j * BLK + t];
+        p.tgY[cidx(n, x, y) * BLK + t] = v;
       }
-      R0[t] = sacc;
-    }
-    __syncthreads();
-    if (t < E2) {
-      T v = 0;
-      for (int gg = 0; gg < G; gg++) v += R0[gg * E2 + t];
-      atomicAdd(p.hT + (size_t)(y - 1) * BLK + (t / My) * NS + (t % My), (double)v);
-    }
-    __syncthreads();
-  }
-  if (bx && d >= 10) {
-    // X_x variants PU, PP (multiloop closing, d >= 11): one term per b; UU, UP (QM2 with an unpaired start)
-    const int E3 = Mx * M1, G = min(NT3 / E3, max(My, 1)), g = t / E3, e = t % E3;
-    if (g < G) {
-      const int a = e / M1, u = e % M1;
-      T su = 0, sp = 0, xuu = 0, xup = 0;
-      if (d >= 11) {
-        for (int b = g; b < My; b += G) {
-          const T gq = hQB[a * NS + b];
-          if (gq == (T)0) continue;
-          su += gq * (s2<false, false>(q2, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + BLK, Xr + XPP * BLK, u, b, Mv));
-          sp += gq * (s2<false, false>(q2 + 2 * BLK, Xr + XUP * BLK, u, b, Mv) + s2<false, false>(q2 + 3 * BLK, Xr + XPP * BLK, u, b, Mv));
-        }
-      }
-      if (g == 0) {
-        const T *r_up = S + SS_MR * BLK, *r_pp = S + (SS_MR + 1) * BLK, *r_uu = S + (SS_MR + 2) * BLK,
-                *r_pu = S + (SS_MR + 3) * BLK;
-        xuu = eb * (s2<false, true>(hM2 + BLK, r_up, a, u, My) + s2<false, true>(hM2, r_uu, a, u, My));
-        xup = eb * (s2<false, true>(hM2 + BLK, r_pp, a, u, My) + s2<false, true>(hM2, r_pu, a, u, My));
-      }
-      R0[t] = su;
-      R1[t] = sp;
-      R2[t] = xuu;
-      R3[t] = xup;
-    }
-    __syncthreads();
-    if (t < E3) {
-      T su = 0, sp = 0;
-      for (int gg = 0; gg < G; gg++) {
-        su += R0[gg * E3 + t];
-        sp += R1[gg * E3 + t];
-      }
-      const int pe = (t / M1) * NS + (t % M1);
-      double *hx = p.hX + (size_t)x * 4 * BLK;
-      if (d >= 11) {
-        atomicAdd(hx + XPU * BLK + pe, (double)(fq * sml * su));
-        atomicAdd(hx + XPP * BLK + pe, (double)(fq * sml * sp));
-      }
-      atomicAdd(hx + XUU * BLK + pe, (double)(F * R2[t]));
-      atomicAdd(hx + XUP * BLK + pe, (double)(F * R3[t]));
-    }
-    __syncthreads();
-  }
-  if (by1 && (d >= 5 || x == 0)) {
-    // X_{y-1} variants: UP, PP from the multiloop closing (d >= 11, one term
-    // per a); single products of QMpp/QMpu/QM2 adjoints (d >= 5) and of the
-    // exterior prefix (x = 0)
-    const int E4 = Mv * My, G = min(NT3 / E4, max(Mx, 1)), g = t / E4, e = t % E4;
-    if (g < G) {
-      const int v2 = e / My, b = e % My;
-      T su = 0, sp = 0;
-      if (d >= 11) {
-        for (int a = g; a < Mx; a += G) {
-          const T gq = hQB[a * NS + b];
-          if (gq == (T)0) continue;
-          su += gq * (s2<false, false>(Xl + XPU * BLK, q2, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 2 * BLK, a, v2, M1));
-          sp += gq * (s2<false, false>(Xl + XPU * BLK, q2 + BLK, a, v2, M1) + s2<false, false>(Xl + XPP * BLK, q2 + 3 * BLK, a, v2, M1));
-        }
-      }
-      R0[t] = su;
-      R1[t] = sp;
-    }
-    __syncthreads();
-    if (t < E4) {
-      const int v2 = t / My, b = t % My, pe = v2 * NS + b;
-      T su = 0, sp = 0;
-      for (int gg = 0; gg < G; gg++) {
-        su += R0[gg * E4 + t];
-        sp += R1[gg * E4 + t];
-      }
-      double xpu = 0, xuu = 0, xpp = 0, xup = 0;
-      if (d >= 11) {
-        xup += (double)(fq * sml * su);
-        xpp += (double)(fq * sml * sp);
-      }
-      if (d >= 5) {
-        const T *mpp = S + SS_ML * BLK, *mpu = S + (SS_ML + 1) * BLK, *q2pp = S + (SS_ML + 2) * BLK,
-                *q2pu = S + (SS_ML + 3) * BLK;
-        T a1 = eb * s2<true, false>(mpp, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(mpu, hMPU, v2, b, Mx);
-        T a3 = s2<true, false>(mpp, hGG, v2, b, Mx), a4 = s2<true, false>(mpu, hGG, v2, b, Mx);
-        if (d >= 10) {
-          a1 += eb * s2<true, false>(q2pp, hM2 + 2 * BLK, v2, b, Mx);
-          a2 += eb * s2<true, false>(q2pu, hM2 + 2 * BLK, v2, b, Mx);
-        }
-        xpu += (double)(F * a1);
-        xuu += (double)(F * a2);
-        xpp += (double)(F * a3);
-        xup += (double)(F * a4);
-      }
-      if (x == 0) {
-        // exterior: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
-        const T *q5u = S + SS_Q5UM * BLK, *q5p = S + SS_Q5PM * BLK;
-        const T *hu = S + SS_HQ5U * BLK, *hg = S + SS_HGX * BLK;
-        xuu += (double)(F * s2<true, false>(q5u, hu, v2, b, M0));
-        xpu += (double)(F * s2<true, false>(q5p, hu, v2, b, M0));
-        xup += (double)(F * s2<true, false>(q5u, hg, v2, b, M0));
-        xpp += (double)(F * s2<true, false>(q5p, hg, v2, b, M0));
-      }
-      double *hx = p.hX + (size_t)(y - 1) * 4 * BLK;
-      atomicAdd(hx + XPU * BLK + pe, xpu);
-      atomicAdd(hx + XUU * BLK + pe, xuu);
-      atomicAdd(hx + XPP * BLK + pe, xpp);
-      atomicAdd(hx + XUP * BLK + pe, xup);
     }
   }
   return true;
 }
 
-
-// Grid-stride over the cells of diagonal d (see k_in_bif).
-template <typename T>
-__global__ void __launch_bounds__(NT3) k_out_side(DP<T> p, int d) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ SideCtx cx;
-  __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
-  __shared__ __align__(8) unsigned long long sbar;
-  if (threadIdx.x == 0) mbar_init(&sbar, 1);
-  __syncthreads();
-  unsigned phase = 0;
-  for (int x = blockIdx.x; x < p.n - d; x += gridDim.x) {
-    // cells with no scatter (d < 5, no boundary) issue no copies and use no phase
-    const bool bx = p.bnd[x] != 0, by1 = d >= 1 && p.bnd[x + d - 1] != 0;
-    const bool staged = !(d < 5 && !(bx || by1));
-    if (!side_cell(p, d, x, (T *)smem_raw, cx, sEn, wBu, &sbar, phase)) return;
-    if (staged) phase ^= 1u;
-    fence_proxy_async();
-    __syncthreads();
-  }
-}
 
 // The off-chain work that the light kernel of diagonal d waits for, as one
 // launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (one
@@ -1215,7 +1013,287 @@ __global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, i
 
 template <typename T>
 constexpr size_t out_side_smem() {
-  return ((size_t)(SS_N + 1) * BLK + 4 * NT3) * sizeof(T);
+  return (size_t)(SS_N + 6) * BLK * sizeof(T);
+}
+
+// ---------------------------------------------------------------- K4': transfer gradients
+// After the reverse chain, d log Z / d T_q and d log Z / d X_q of every
+// boundary position q, summed over the cells that read them:
+//   role 0  cells (q, y), y > q, where T_q, X_q join the outer pair's left
+//           base to the next position (T_x, X_x of the cell);
+//   role 1  cells (x, q+1), x <= q, where they join the position before the
+//           right base to it (T_{y-1}, X_{y-1}).
+// Terms per cell (fq = 2^{E[d-2]-E[d]}, F = 2^{E[d-1]-E[d]}, Hxi = hXI with
+// the inner mismatch factor):
+//   T_x     fq hQB (HB[x+1][y-1] T_{y-1} + stack(QB[x+1][y-1]) T_{y-1})^T
+//           + fq Hxi (QB[x+1][y-1] T_{y-1})^T + hCH CH[x+1][y]^T + tgY
+//   T_{y-1} the same terms seen from the right;
+//   X       the multiloop-closing and unpaired-start terms, and the exterior
+//           prefix for x = 0.
+// Grid (chunks of TG_CELLS partner cells, q, role); one warp per cell at a
+// time stages the cell's blocks into its shared-memory slice, lanes over the
+// M_q x M_{q+1} entries; the CTA adds its warps' sums and issues one binary64
+// atomic per entry.
+constexpr int TG_CELLS = 64;
+constexpr int TG_NB = 22;  // staged blocks per cell
+template <typename T>
+constexpr size_t out_tg_smem() {  // two buffers per warp
+  return (size_t)16 * TG_NB * BLK * sizeof(T) > (size_t)8 * BLK * 5 * sizeof(double)
+             ? (size_t)16 * TG_NB * BLK * sizeof(T)
+             : (size_t)8 * BLK * 5 * sizeof(double);
+}
+
+template <typename T>
+__device__ __forceinline__ const T *tg_src(const DP<T> &p, int role, int k, int x, int y) {
+  const int n = p.n, d = y - x;
+  if (role == 0) {
+    switch (k) {
+      case 0: return d >= 4 ? p.hGc + cidx(n, x, y) * BLK : nullptr;
+      case 1: return d >= 4 ? p.HB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+      case 2: return p.Tr + (size_t)(y - 1) * BLK;
+      case 3: return d >= 6 ? p.QB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+      case 4: return d >= 6 ? p.hXI + cidx(n, x, y) * BLK : nullptr;
+      case 5: return p.hCH + cidx(n, x, y) * BLK;
+      case 6: return p.CH + cidx(n, x + 1, y) * BLK;
+      case 7: return d >= 6 ? p.tgY + cidx(n, x, y) * BLK : nullptr;
+      case 8: case 9: case 10: case 11: {
+        if (d < 11) return nullptr;
+        const T *t4[4] = {p.QM2uu, p.QM2up, p.QM2pu, p.QM2pp};
+        return t4[k - 8] + cidx(n, x + 1, y - 1) * BLK;
+      }
+      case 12: return p.X + ((size_t)(y - 1) * 4 + XUP) * BLK;
+      case 13: return p.X + ((size_t)(y - 1) * 4 + XPP) * BLK;
+      case 14: return d >= 10 ? p.hQM2uu + cidx(n, x, y) * BLK : nullptr;
+      case 15: return d >= 10 ? p.hQM2up + cidx(n, x, y) * BLK : nullptr;
+      case 16: case 17: case 18: case 19: {
+        if (d < 10) return nullptr;
+        const T *t4[4] = {p.QM2up, p.QM2pp, p.QM2uu, p.QM2pu};
+        return t4[k - 16] + cidx(n, x + 1, y) * BLK;
+      }
+      default: return nullptr;
+    }
+  }
+  switch (k) {
+    case 0: return d >= 4 ? p.hGc + cidx(n, x, y) * BLK : nullptr;
+    case 1: return p.Tr + (size_t)x * BLK;
+    case 2: return d >= 4 ? p.HB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+    case 3: return d >= 6 ? p.QB + cidx(n, x + 1, y - 1) * BLK : nullptr;
+    case 4: return d >= 6 ? p.hXI + cidx(n, x, y) * BLK : nullptr;
+    case 5: return p.X + ((size_t)x * 4 + XPU) * BLK;
+    case 6: return p.X + ((size_t)x * 4 + XPP) * BLK;
+    case 7: case 8: case 9: case 10: {
+      if (d < 11) return nullptr;
+      const T *t4[4] = {p.QM2uu, p.QM2up, p.QM2pu, p.QM2pp};
+      return t4[k - 7] + cidx(n, x + 1, y - 1) * BLK;
+    }
+    case 11: case 12: case 13: case 14: {
+      if (d < 5) return nullptr;
+      const T *t4[4] = {p.QMpp, p.QMpu, p.QM2pp, p.QM2pu};
+      return t4[k - 11] + cidx(n, x, y - 1) * BLK;
+    }
+    case 15: return d >= 5 ? p.hQMpu + cidx(n, x, y) * BLK : nullptr;
+    case 16: return d >= 5 ? p.hG + cidx(n, x, y) * BLK : nullptr;
+    case 17: return d >= 10 ? p.hQM2pu + cidx(n, x, y) * BLK : nullptr;
+    case 18: return x == 0 ? p.Q5U + (size_t)(d - 1) * BLK : nullptr;
+    case 19: return x == 0 ? p.Q5P + (size_t)(d - 1) * BLK : nullptr;
+    case 20: return x == 0 ? p.hQ5U + (size_t)d * BLK : nullptr;
+    case 21: return x == 0 ? p.hGx + (size_t)d * BLK : nullptr;
+    default: return nullptr;
+  }
+}
+
+// one warp stages the TG_NB blocks of cell (x, y) into dst with 16-byte
+// asynchronous copies (absent blocks zero-filled), as one commit group
+template <typename T>
+__device__ __forceinline__ void tg_issue(const DP<T> &p, int role, int x, int y, T *dst, int lane) {
+  constexpr int CH = BLK * sizeof(T) / 16;
+  const T *mine = lane < TG_NB ? tg_src(p, role, lane, x, y) : nullptr;
+#pragma unroll
+  for (int j0 = 0; j0 < TG_NB * CH; j0 += 32) {
+    const int j = j0 + lane;
+    const T *src = (const T *)__shfl_sync(0xffffffffu, (unsigned long long)mine, (j / CH) & 31);
+    if (j < TG_NB * CH) {
+      const char *g = src ? (const char *)src + 16 * (j % CH) : (const char *)p.Tr;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32((char *)dst + 16 * j)), "l"(g),
+                   "r"(src ? 16 : 0)
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = p.n, q = blockIdx.y, role = blockIdx.z;
+  if (q >= n - 1 || p.bnd[q] == 0) return;
+  const int ncell = role == 0 ? n - 1 - q : q + 1;  // role 0: y = q+1..n-1; role 1: x = 0..q
+  const int c0 = blockIdx.x * TG_CELLS;
+  if (c0 >= ncell) return;
+  const int c1 = min(ncell, c0 + TG_CELLS);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T *buf = (T *)smem_raw + (size_t)w * 2 * TG_NB * BLK;
+  const int Mr = p.Mp[q], Mc = p.Mp[q + 1], NE = Mr * Mc;
+  const T *en = p.en;
+  const T eb = en[EN_EB], sml = en[EN_EA] * en[EN_EC];
+  double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // T, X_UU, X_UP, X_PU, X_PP
+  // cells c0+w, c0+w+8, ...: the next cell's blocks are in flight while the
+  // current one is summed
+  if (c0 + w < c1) tg_issue(p, role, role == 0 ? q : c0 + w, role == 0 ? q + 1 + c0 + w : q + 1, buf, lane);
+  for (int i = c0 + w, it = 0; i < c1; i += 8, it++) {
+    const int x = role == 0 ? q : i, y = role == 0 ? q + 1 + i : q + 1, d = y - x;
+    const T *B = buf + (size_t)(it & 1) * TG_NB * BLK;
+    if (i + 8 < c1) {
+      const int i2 = i + 8;
+      tg_issue(p, role, role == 0 ? q : i2, role == 0 ? q + 1 + i2 : q + 1, buf + (size_t)((it + 1) & 1) * TG_NB * BLK, lane);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncwarp();
+    const int Ed = p.E[d];
+    const T fq = clamp_p2<T>((d >= 2 ? p.E[d - 2] : 0) - Ed), F = clamp_p2<T>(p.E[d - 1] - Ed);
+    const int Mx = p.Mp[x], My = p.Mp[y], M1 = p.Mp[x + 1], Mv = p.Mp[y - 1];
+    const int *bx0 = p.base + (size_t)x * NS, *bx1 = p.base + (size_t)(x + 1) * NS;
+    const int *by0 = p.base + (size_t)y * NS, *bv = p.base + (size_t)(y - 1) * NS;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const int e = lane + 32 * k;
+      if (e >= NE) continue;
+      T tv = 0, xuu = 0, xup = 0, xpu = 0, xpp = 0;
+      if (role == 0) {
+        const int a = e / Mc, u = e % Mc;  // T_x[a][u]
+        const T *hQB = B, *hbi = B + BLK, *Ty1 = B + 2 * BLK, *qin = B + 3 * BLK, *hXI = B + 4 * BLK;
+        const T *hCH = B + 5 * BLK, *CHN = B + 6 * BLK, *Yt = B + 7 * BLK, *q2 = B + 8 * BLK;
+        const T *XrUP = B + 12 * BLK, *XrPP = B + 13 * BLK, *hM2uu = B + 14 * BLK, *hM2up = B + 15 * BLK;
+        const T *MR = B + 16 * BLK;  // QM2 up, pp, uu, pu of (x+1, y)
+        if (d >= 4) {
+          const int pa = bx0[a], bu = bx1[u];
+          for (int b = 0; b < My; b++) {
+            const T gq = hQB[a * NS + b];
+            if (gq == (T)0) continue;
+            T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
+            if (d >= 6) {
+              const int pto = pair_type(pa, by0[b]);
+              for (int b2 = 0; b2 < Mv; b2++) {
+                const int pti = pair_type(bu, bv[b2]);
+                if (pti < 0 || pto < 0) continue;
+                tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
+              }
+            }
+            tv += fq * gq * tt;
+          }
+        }
+        if (d >= 6)
+          for (int z = 0; z < My; z++)
+            tv += fq * (hXI[a * NS + z] * en[EN_TM + by0[z] * 4 + bx0[a]]) * s2<false, false>(qin, Ty1, u, z, Mv);
+        tv += s2<false, true>(hCH, CHN, a, u, My);
+        if (d >= 6) tv += Yt[a * NS + u];
+        if (d >= 10) {
+          if (d >= 11) {
+            T su = 0, sp2 = 0;
+            for (int b = 0; b < My; b++) {
+              const T gq = hQB[a * NS + b];
+              if (gq == (T)0) continue;
+              su += gq * (s2<false, false>(q2, XrUP, u, b, Mv) + s2<false, false>(q2 + BLK, XrPP, u, b, Mv));
+              sp2 += gq * (s2<false, false>(q2 + 2 * BLK, XrUP, u, b, Mv) + s2<false, false>(q2 + 3 * BLK, XrPP, u, b, Mv));
+            }
+            xpu = fq * sml * su;
+            xpp = fq * sml * sp2;
+          }
+          xuu = F * (eb * (s2<false, true>(hM2up, MR, a, u, My) + s2<false, true>(hM2uu, MR + 2 * BLK, a, u, My)));
+          xup = F * (eb * (s2<false, true>(hM2up, MR + BLK, a, u, My) + s2<false, true>(hM2uu, MR + 3 * BLK, a, u, My)));
+        }
+      } else {
+        const int v2 = e / Mc, b = e % Mc;  // T_{y-1}[v2][b]
+        const T *hQB = B, *Tx = B + BLK, *hbi = B + 2 * BLK, *qin = B + 3 * BLK, *hXI = B + 4 * BLK;
+        const T *XlPU = B + 5 * BLK, *XlPP = B + 6 * BLK, *q2 = B + 7 * BLK, *ML = B + 11 * BLK;
+        const T *hMPU = B + 15 * BLK, *hGG = B + 16 * BLK, *hM2pu = B + 17 * BLK;
+        const int pb = by0[b], pv = bv[v2];
+        for (int a = 0; a < Mx; a++) {
+          if (d >= 4) {
+            const T gg = hQB[a * NS + b];
+            if (gg != (T)0) {
+              T tt = s2<false, false>(Tx, hbi, a, v2, M1);
+              if (d >= 6) {
+                const int pto = pair_type(bx0[a], pb);
+                for (int a2 = 0; a2 < M1; a2++) {
+                  const int pti = pair_type(bx1[a2], pv);
+                  if (pti < 0 || pto < 0) continue;
+                  tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
+                }
+              }
+              tv += fq * gg * tt;
+            }
+          }
+          if (d >= 6) tv += fq * s2<false, false>(Tx, qin, a, v2, M1) * (hXI[a * NS + b] * en[EN_TM + pb * 4 + bx0[a]]);
+        }
+        if (d >= 11) {
+          T su = 0, sp2 = 0;
+          for (int a = 0; a < Mx; a++) {
+            const T gq = hQB[a * NS + b];
+            if (gq == (T)0) continue;
+            su += gq * (s2<false, false>(XlPU, q2, a, v2, M1) + s2<false, false>(XlPP, q2 + 2 * BLK, a, v2, M1));
+            sp2 += gq * (s2<false, false>(XlPU, q2 + BLK, a, v2, M1) + s2<false, false>(XlPP, q2 + 3 * BLK, a, v2, M1));
+          }
+          xup = fq * sml * su;
+          xpp = fq * sml * sp2;
+        }
+        T xpu2 = 0, xuu2 = 0, xpp2 = 0, xup2 = 0;
+        if (d >= 5) {
+          // ML: QMpp, QMpu, QM2pp, QM2pu of (x, y-1)
+          T a1 = eb * s2<true, false>(ML, hMPU, v2, b, Mx), a2 = eb * s2<true, false>(ML + BLK, hMPU, v2, b, Mx);
+          const T a3 = s2<true, false>(ML, hGG, v2, b, Mx), a4 = s2<true, false>(ML + BLK, hGG, v2, b, Mx);
+          if (d >= 10) {
+            a1 += eb * s2<true, false>(ML + 2 * BLK, hM2pu, v2, b, Mx);
+            a2 += eb * s2<true, false>(ML + 3 * BLK, hM2pu, v2, b, Mx);
+          }
+          xpu2 = F * a1;
+          xuu2 = F * a2;
+          xpp2 = F * a3;
+          xup2 = F * a4;
+        }
+        if (x == 0) {
+          // exterior prefix: Q5U[d] and Gx[d] from Q5*[d-1] X_{d-1}
+          const T *q5u = B + 18 * BLK, *q5p = B + 19 * BLK, *hu = B + 20 * BLK, *hg = B + 21 * BLK;
+          xuu2 += F * s2<true, false>(q5u, hu, v2, b, Mx);
+          xpu2 += F * s2<true, false>(q5p, hu, v2, b, Mx);
+          xup2 += F * s2<true, false>(q5u, hg, v2, b, Mx);
+          xpp2 += F * s2<true, false>(q5p, hg, v2, b, Mx);
+        }
+        acc[k][1] += (double)xuu2;
+        acc[k][2] += (double)xup2;
+        acc[k][3] += (double)xpu2;
+        acc[k][4] += (double)xpp2;
+      }
+      acc[k][0] += (double)tv;
+      acc[k][1] += (double)xuu;
+      acc[k][2] += (double)xup;
+      acc[k][3] += (double)xpu;
+      acc[k][4] += (double)xpp;
+    }
+    __syncwarp();  // the buffer is refilled two cells later
+  }
+  // the CTA's sum per entry, one binary64 atomic each
+  __syncthreads();
+  double *R = (double *)smem_raw;  // [8][36][5]
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int e = lane + 32 * k;
+    if (e < BLK)
+      for (int v = 0; v < 5; v++) R[((size_t)w * BLK + e) * 5 + v] = e < NE ? acc[k][v] : 0.0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NE * 5; t += blockDim.x) {
+    const int e = t / 5, v = t % 5;
+    double s = 0;
+    for (int ww = 0; ww < 8; ww++) s += R[((size_t)ww * BLK + e) * 5 + v];
+    if (s == 0.0) continue;
+    const int pe = (e / Mc) * NS + e % Mc;
+    const int xk[4] = {XUU, XUP, XPU, XPP};
+    if (v == 0) atomicAdd(p.hT + (size_t)q * BLK + pe, s);
+    else atomicAdd(p.hX + ((size_t)q * 4 + xk[v - 1]) * BLK + pe, s);
+  }
 }
 
 template <typename T, int NTT = NT>

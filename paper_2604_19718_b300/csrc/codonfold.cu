@@ -420,6 +420,7 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
     CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
     CF_CUDA(p, cudaMemset(*q, 0, (size_t)n * BLK * sizeof(T)));
   }
+  CF_CUDA(p, dalloc(L, &d.tgY, nc));
   CF_CUDA(p, dalloc(L, &d.hT, (size_t)n * BLK));
   CF_CUDA(p, dalloc(L, &d.hX, (size_t)n * 4 * BLK));
   CF_CUDA(p, dalloc(L, &t.ob.hg, (size_t)BIFRING * n * BLK));
@@ -449,13 +450,14 @@ template <typename T>
 cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gout) return CF_OK;
   const int n = p->n;
-  const int cap_bif = offchain_ctas(p, 64), cap_side = offchain_ctas(p, 64);
+  const int cap_bif = offchain_ctas(p, 64);
   const size_t nc = ncells(n) * BLK;
   const size_t smem = out_light_smem<T, NT>(), smemw = out_light_smem<T, NT_WIDE>(), smem3 = out_side_smem<T>();
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smemw));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_side<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_tg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)out_tg_smem<T>()));
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
@@ -467,7 +469,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (e == cudaSuccess) e = add_memset(g, &m[2], &m[1], 1, dp.hT, (size_t)n * BLK * sizeof(double));
   if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double));
   if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float));
-  std::vector<cudaGraphNode_t> k2(n), k1(n), k3(n, nullptr);
+  std::vector<cudaGraphNode_t> k2(n), k1(n);
   // far bands (binary32): both gathers of band alo hang off the light kernel
   // of diagonal of_c(alo) and precede the bifurcation kernels of the band
   const bool banded = ob.far != nullptr;
@@ -512,7 +514,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     // one off-chain launch per diagonal d: the bifurcation gathers of d and the
     // side work of d+4 (its scatters land on diagonals <= d), both after the
     // light kernel of d+4
-    const bool hasb = d <= n - 5 && d >= 1, hass = d + 4 <= n - 1;
+    const bool hasb = d <= n - 5 && d >= 1, hass = d + 4 <= n - 1 && d >= 1;  // no side work below d = 5
     if (hasb || hass) {
       int nbif = hasb ? (banded ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
       void *oargs[] = {&dp, &ob, &dd, &nbif};
@@ -537,7 +539,6 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     int nd = 0;
     deps[nd++] = (d == n - 1) ? m[4] : k2[d + 1];
     if (hasb || hass) deps[nd++] = k1[d];
-    if (d + 4 < n && k3[d + 4]) deps[nd++] = k3[d + 4];  // side work launched on its own (d+4 <= 3)
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;
     kp.func = wide ? (void *)k_out_light<T, NT_WIDE> : (void *)k_out_light<T, NT>;
@@ -548,19 +549,19 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
-    if (e == cudaSuccess && d >= 1 && d <= 3) {
-      // the side work of d = 1..3 has no bifurcation launch of d-4 to ride on
-      void *args3[] = {&dp, &dd};
-      cudaKernelNodeParams k3p = {};
-      k3p.func = (void *)k_out_side<T>;
-      k3p.gridDim = dim3(std::min(n - d, cap_side));
-      k3p.blockDim = dim3(NT3);
-      k3p.sharedMemBytes = (unsigned)smem3;
-      k3p.kernelParams = args3;
-      e = cudaGraphAddKernelNode(&k3[d], g, &k2[d], 1, &k3p);
-      if (e == cudaSuccess) e = set_priority(k3[d], false);
-      nodes++;
-    }
+  }
+  // transfer gradients of every boundary position, after the whole chain
+  cudaGraphNode_t ktg = nullptr;
+  if (e == cudaSuccess) {
+    void *args[] = {&dp};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_out_tg<T>;
+    kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, n, 2);
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = (unsigned)out_tg_smem<T>();
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&ktg, g, &k2[0], 1, &kp);
+    nodes++;
   }
   cudaGraphNode_t fin = nullptr;
   if (e == cudaSuccess) {
@@ -571,12 +572,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     kp.gridDim = dim3((std::max(p->m - 1, 1) + 127) / 128);
     kp.blockDim = dim3(128);
     kp.kernelParams = args;
-    // the marginals read the transfer gradients of every side kernel; those of
-    // d >= 4 already precede the light kernel of d - 4
-    std::vector<cudaGraphNode_t> fdeps{k2[0]};
-    for (int d = 1; d < std::min(n, 4); d++)
-      if (k3[d]) fdeps.push_back(k3[d]);
-    e = cudaGraphAddKernelNode(&fin, g, fdeps.data(), fdeps.size(), &kp);
+    e = cudaGraphAddKernelNode(&fin, g, &ktg, 1, &kp);
     nodes++;
   }
   if (e == cudaSuccess) {

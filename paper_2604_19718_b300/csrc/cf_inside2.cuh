@@ -36,6 +36,8 @@ struct BifBuf {
   int ncmax;
   float *far;     // [2][n][FARD][farslices][36] far split points of a band, per slice (binary32; nullptr: none)
   int farslices;  // slices per cell in the far buffer
+  const T **stab; // [n][SI_N] source of every staged slot of the light cell x = 0 of each diagonal
+  T **dtab;       // [n][NCOPY] destination of every result of that cell
 };
 
 // ---------------------------------------------------------------- far bands
@@ -335,6 +337,17 @@ __device__ __forceinline__ const T *in_slot_src2(const DP<T> &p, const BifBuf<T>
   const int k = (s < SI_QBK ? s - SI_GXK : s - SI_QBK) + 1;
   if (k > d - 4) return nullptr;
   return s < SI_QBK ? p.Gx + (size_t)k * BLK : p.QB + cidx(n, k, d) * BLK;
+}
+
+// Along a diagonal every slot's source moves by a fixed stride per cell (the
+// tables are diagonal-major), so the light kernel finds it as the source of
+// cell x = 0 (a per-diagonal table) plus x times the stride; 0: the slot is
+// read by cell x = 0 only (exterior prefix).
+__host__ __device__ __forceinline__ int in_slot_stride(int s) {
+  if (s >= SI_XX && s < SI_CHN) return 4 * BLK;
+  if (s >= SI_YYP && s < SI_XIL) return NYY * BLK;
+  if (s > SI_BIF) return 0;
+  return BLK;
 }
 
 // ---------------------------------------------------------------- K2
@@ -644,6 +657,24 @@ __device__ __forceinline__ T *light_dst(const DP<T> &p, int k, int x, int d, siz
   return nullptr;
 }
 
+// stride of result k along a diagonal, as in_slot_stride
+__host__ __device__ __forceinline__ int light_dst_stride(int k) {
+  if (k >= 2 && k < 31) return NYY * BLK;
+  if (k >= 40) return 0;
+  return BLK;
+}
+
+// the per-diagonal tables of slot sources and result destinations of cell
+// x = 0 (once per problem: they hold only table addresses)
+template <typename T>
+__global__ void k_in_slot_tab(DP<T> p, BifBuf<T> bb) {
+  const int d = blockIdx.x;
+  for (int s = threadIdx.x; s < SI_N; s += blockDim.x)
+    bb.stab[(size_t)d * SI_N + s] = s < SI_BIF ? in_slot_src(p, s, 0, d, d) : in_slot_src2(p, bb, s, 0, d);
+  for (int k = threadIdx.x; k < NCOPY; k += blockDim.x)
+    bb.dtab[(size_t)d * NCOPY + k] = light_dst(p, k, 0, d, cidx(p.n, 0, d));
+}
+
 template <typename T, int NTT>
 __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int x,
                                               unsigned char *smem_raw) {
@@ -664,7 +695,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   // issued so that all loads are in flight together: exponents of diagonals
   // d-47..d-1, bases of x-1..x+1 and y-1..y+1, energy factors, and the
   // largest mantissa and exponent of diagonal d-1 (last thread)
-  static_assert(NTT > EN_N && NTT > 100 + 6 * NS, "one context value per thread");
+  static_assert(NTT > EN_N && NTT > 100 + 6 * NS && NTT >= SI_N, "one context value and slot per thread");
   // the barrier is initialised first: its release fence would otherwise wait
   // for the context loads below
   if (t == 0) mbar_init(&sbar, 1);
@@ -686,6 +717,8 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     cMax = __ldcg(p.dmax + d - 1);
     cE = __ldcg(p.E + d - 1);
   }
+  const T *src0 = t < SI_N ? bb.stab[(size_t)d * SI_N + t] : nullptr;
+  T *dst0 = t < NCOPY ? bb.dtab[(size_t)d * NCOPY + t] : nullptr;
   __syncthreads();
   // Staging: one TMA bulk copy per input block (the interior partial sums
   // YY_{L-1}[x+1][y], L = 3..Lmax, are contiguous and go as one copy); slots
@@ -694,10 +727,11 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   // once every thread has done so.
   {
     const int LmaxS = min(MAXLOOP, d - 4);
-    for (int s = t; s < SI_N; s += NTT) {
-      T *dst = S + (size_t)s * BLK;
-      if (s > SI_YYP && s < SI_XIL && d >= 6 && s - SI_YYP + 3 <= LmaxS) continue;  // part of the YY run
-      const T *src = s < SI_BIF ? in_slot_src(p, s, x, y, d) : in_slot_src2(p, bb, s, x, d);
+    const int s = t;
+    T *dst = S + (size_t)s * BLK;
+    if (s < SI_N && !(s > SI_YYP && s < SI_XIL && d >= 6 && s - SI_YYP + 3 <= LmaxS)) {  // not part of the YY run
+      const int st = in_slot_stride(s);
+      const T *src = src0 == nullptr ? nullptr : (st ? src0 + (size_t)x * st : (x == 0 ? src0 : nullptr));
       if (src) {
         const unsigned bytes = (s == SI_YYP ? (unsigned)(LmaxS - 2) : 1u) * BLK * (unsigned)sizeof(T);
         mbar_expect(&sbar, bytes);
@@ -709,7 +743,10 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     }
   }
   // destinations of the results (copied out at the end of the cell)
-  if (t < NCOPY) sDst[t] = light_dst(p, t, x, d, c);
+  if (t < NCOPY) {
+    const int st = light_dst_stride(t);
+    sDst[t] = dst0 == nullptr ? nullptr : (st ? dst0 + (size_t)x * st : (x == 0 ? dst0 : nullptr));
+  }
   __syncthreads();
   if (t == 0) mbar_arrive(&sbar);
   // the context reaches shared memory while the copies are in flight

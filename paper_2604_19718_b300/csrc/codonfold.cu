@@ -269,6 +269,12 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   t.bb.farslices = far_nslice(n, 0, std::max(0, (n - 1) / FARD * FARD));  // the widest band's slices
   if (sizeof(T) == sizeof(float) && n > 3 * FARD)
     CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
+  const T **stab = nullptr;
+  CF_CUDA(p, dalloc(L, &stab, (size_t)n * SI_N));
+  t.bb.stab = stab;
+  CF_CUDA(p, dalloc(L, &t.bb.dtab, (size_t)n * NCOPY));
+  k_in_slot_tab<T><<<n, 256, 0, p->stream>>>(t.dp, t.bb);
+  CF_CUDA(p, cudaGetLastError());
   t.inside_alloc = true;
   return CF_OK;
 }

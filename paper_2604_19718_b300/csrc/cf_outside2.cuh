@@ -22,12 +22,21 @@
 
 namespace cf {
 
+// source of a staged slot for the cells x = xlo..xhi of a diagonal (src is
+// the source of cell xlo; nullptr: no cell reads the slot)
+template <typename T>
+struct OSlot {
+  const T *src;
+  int xlo, xhi;
+};
+
 template <typename T>
 struct OutBuf {
   T *hg;   // [BIFRING][n][36] row gathers (contribution to hG)
   T *hq;   // [BIFRING][n][36] column gathers (contribution to hQB)
   T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
   float *far;  // [2 gathers][3 slots][n][OFD][36] far terms of a band (binary32; nullptr: none)
+  OSlot<T> *otab;  // [n][SO_N] sources of the light kernel's staged slots per diagonal
 };
 
 // ---------------------------------------------------------------- far bands
@@ -474,6 +483,50 @@ __device__ __forceinline__ const T *out_slot_src2(const DP<T> &p, const OutBuf<T
   return nullptr;
 }
 
+// The cells of diagonal d that read slot s form one range x = xlo..xhi (a
+// neighbour on the left or right, a bulge that fits, the exterior cell), and
+// the slot's source moves by a fixed stride per cell along the diagonal.
+__host__ __device__ __forceinline__ void out_slot_range(int n, int s, int d, int &xlo, int &xhi) {
+  xlo = 0;
+  xhi = n - 1 - d;
+  if (s == SO_TXL || (s >= SO_XXL && s < SO_XY) || s == SO_H2UU || s == SO_H2UP || s == SO_HCHL ||
+      (s >= SO_HYR && s < SO_CHL) || s == SO_GX || s == SO_HQ5P)
+    xlo = 1;  // a left neighbour
+  if (s == SO_TY || (s >= SO_XY && s < SO_QB) || s == SO_H2PU || s == SO_HMPU || s == SO_HG1)
+    xhi = n - 2 - d;  // a right neighbour
+  if (s == SO_GC || s == SO_HXIE) {  // an enclosing pair
+    xlo = 1;
+    xhi = n - 2 - d;
+  }
+  if (s >= SO_BC3U && s < SO_HGC) {  // bulges of length L around the cell
+    const int L = (s - SO_BC3U) % MAXLOOP + 1;
+    if (s < SO_BC5U || (s >= SO_BH3U && s < SO_BH5U)) xhi = n - 1 - L - d;
+    else xlo = L;
+  }
+  if (s == SO_HGC) xhi = n - d - 5;  // row gather terms
+  if (s == SO_HQC) xlo = 5;          // column gather terms
+  if (s >= SO_HGXC) xhi = 0;         // exterior
+}
+__host__ __device__ __forceinline__ int out_slot_stride(int s) {
+  if (s >= SO_XXL && s < SO_QB) return 4 * BLK;
+  if (s >= SO_HYR && s < SO_CHL) return NYY * BLK;
+  return BLK;
+}
+
+// per-diagonal table of slot sources (once per problem: table addresses only)
+template <typename T>
+__global__ void k_out_slot_tab(DP<T> p, OutBuf<T> ob) {
+  const int d = blockIdx.x;
+  for (int s = threadIdx.x; s < SO_N; s += blockDim.x) {
+    OSlot<T> e;
+    out_slot_range(p.n, s, d, e.xlo, e.xhi);
+    e.src = nullptr;
+    if (e.xlo <= e.xhi)
+      e.src = s < SO_HGC ? out_slot_src(p, s, e.xlo, e.xlo + d, d) : out_slot_src2(p, ob, s, e.xlo, d);
+    ob.otab[(size_t)d * SO_N + s] = e;
+  }
+}
+
 // ---------------------------------------------------------------- K2'
 // Thread mapping as in k_in_light: compact entries e = a*M_b + b, work lists
 // split into NT/(M_x*M_y) groups.
@@ -493,8 +546,8 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   const int n = p.n;
   const int x = blockIdx.x, y = x + d;
   for (int s = t; s < SO_N; s += NTT) {
-    const T *src = s < SO_HGC ? out_slot_src(p, s, x, y, d) : out_slot_src2(p, ob, s, x, d);
-    if (src) stage_block(S + (size_t)s * BLK, src);
+    const OSlot<T> e = ob.otab[(size_t)d * SO_N + s];
+    if (e.src && x >= e.xlo && x <= e.xhi) stage_block(S + (size_t)s * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(s));
   }
   // small per-cell context on chip: exponents around d, codon-state counts
   // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors

@@ -37,6 +37,7 @@ struct OutBuf {
   T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
   float *far;  // [2 gathers][3 slots][n][OFD][36] far terms of a band (binary32; nullptr: none)
   OSlot<T> *otab;  // [n][SO_N] sources of the light kernel's staged slots per diagonal
+  const T **stab;  // [n][SS_N] sources of the side work's staged slots for cell x = 0 (nullptr: not staged)
 };
 
 // ---------------------------------------------------------------- far bands
@@ -897,8 +898,28 @@ __device__ __forceinline__ bool side_slot_tg(int s) {
   return s < SS_HHB || s == SS_HCH || (s >= SS_HXI && s < SS_HY) || (s >= SS_YYP && s < SS_XIL);
 }
 
+// stride of a side slot's source per cell along a diagonal
+__host__ __device__ __forceinline__ int side_slot_stride(int s) {
+  if (s >= SS_XX && s < SS_QBI) return 4 * BLK;
+  if (s >= SS_HY && s < SS_XIL) return NYY * BLK;
+  return BLK;
+}
+
+// per-diagonal table of the side work's slot sources for cell x = 0; the
+// slots of the exterior cell and those read only by the transfer gradients
+// (summed after the pass) are not staged, except the partial sums
+// YY_{L-1}[x+1][y] of the ring term
 template <typename T>
-__device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu,
+__global__ void k_side_slot_tab(DP<T> p, OutBuf<T> ob) {
+  const int d = blockIdx.x;
+  for (int s = threadIdx.x; s < SS_N; s += blockDim.x) {
+    const bool staged = !side_slot_tg(s) || (s >= SS_YYP && s < SS_XIL);
+    ob.stab[(size_t)d * SS_N + s] = staged && d >= 5 ? side_slot_src(p, s, 0, d, d) : nullptr;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu,
                                           unsigned long long *sbar, unsigned phase) {
   int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
   int (*sBx)[NS] = cx.sBx, (*sBy)[NS] = cx.sBy;
@@ -925,24 +946,28 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, int d, int x, T *S, Si
     if (q >= 0 && q < n) cB = p.base[q * NS + a];
   }
   if (t < EN_N) cEn = p.en[t];
+  static_assert(NT3 >= SS_N, "one staged slot per thread");
+  const T *src0 = t < SS_N ? ob.stab[(size_t)d * SS_N + t] : nullptr;
   // staging: one TMA bulk copy per input block, the interior-loop adjoints
   // hYY_L (L = 2..Lmax) and partial sums YY_{L-1}[x+1][y] (L = 3..Lmax) as one
   // copy each; the partial sums only for a boundary at x (the ring term of the
   // transfer gradient T_x)
   const bool ytg = bx && d >= 6;
   const int Lmax = min(MAXLOOP, d - 4);
-  for (int s = t; s < SS_N; s += NT3) {
-    if (side_slot_tg(s) && !(ytg && s >= SS_YYP && s < SS_XIL)) continue;
-    if (d >= 6 && s > SS_HY && s < SS_YYP && s - SS_HY + 2 <= Lmax) continue;   // part of the hYY run
-    if (d >= 6 && s > SS_YYP && s < SS_XIL && s - SS_YYP + 3 <= Lmax) continue;  // part of the YY run
-    const T *src = side_slot_src(p, s, x, y, d);
-    if (!src) continue;
-    unsigned nb = 1;
-    if (s == SS_HY) nb = (unsigned)(Lmax - 1);
-    else if (s == SS_YYP) nb = (unsigned)(Lmax - 2);
-    const unsigned bytes = nb * BLK * (unsigned)sizeof(T);
-    mbar_expect(sbar, bytes);
-    bulk_g2s(S + (size_t)s * BLK, src, bytes, sbar);
+  {
+    const int s = t;
+    const bool skip = src0 == nullptr || (!ytg && s >= SS_YYP && s < SS_XIL) ||
+                      (d >= 6 && s > SS_HY && s < SS_YYP && s - SS_HY + 2 <= Lmax) ||  // part of the hYY run
+                      (d >= 6 && s > SS_YYP && s < SS_XIL && s - SS_YYP + 3 <= Lmax);   // part of the YY run
+    if (!skip) {
+      const T *src = src0 + (size_t)x * side_slot_stride(s);
+      unsigned nb = 1;
+      if (s == SS_HY) nb = (unsigned)(Lmax - 1);
+      else if (s == SS_YYP) nb = (unsigned)(Lmax - 2);
+      const unsigned bytes = nb * BLK * (unsigned)sizeof(T);
+      mbar_expect(sbar, bytes);
+      bulk_g2s(S + (size_t)s * BLK, src, bytes, sbar);
+    }
   }
   __syncthreads();
   if (t == 0) mbar_arrive(sbar);
@@ -1061,7 +1086,7 @@ __global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, i
   }
   if (threadIdx.x == 0) mbar_init(&sbar, 1);
   __syncthreads();
-  side_cell(p, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u);
+  side_cell(p, ob, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u);
 }
 
 template <typename T>

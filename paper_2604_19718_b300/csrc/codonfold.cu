@@ -435,7 +435,11 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   t.ob.far = nullptr;
   if (sizeof(T) == sizeof(float) && of_band(n, 0)) CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
   CF_CUDA(p, dalloc(L, &t.ob.otab, (size_t)n * SO_N));
+  const T **sstab = nullptr;
+  CF_CUDA(p, dalloc(L, &sstab, (size_t)n * SS_N));
+  t.ob.stab = sstab;
   k_out_slot_tab<T><<<n, 256, 0, p->stream>>>(t.dp, t.ob);
+  k_side_slot_tab<T><<<n, 256, 0, p->stream>>>(t.dp, t.ob);
   CF_CUDA(p, cudaGetLastError());
   t.outside_alloc = true;
   return CF_OK;

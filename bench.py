@@ -81,7 +81,7 @@ def algorithmic_flops(res):
 # DRAM traffic of one outside pass of this workload (read + write bytes summed
 # over its kernels), from the ncu launch list with warm caches in
 # profiles/launches_p300_dirichlet_fp32.md; taken on the kernels as committed
-OUTSIDE_DRAM_BYTES_PER_PASS = 9.50e9
+OUTSIDE_DRAM_BYTES_PER_PASS = 7.89e9
 
 
 def sm_peak_tflops(clock_mhz, sms=148):
@@ -522,7 +522,7 @@ def main():
         "samples_per_s": samples_per_s,
         "inside_ms": tin / args.steps, "outside_ms": tout / args.steps,
         "roofline": {"bound": "alu",
-                     "kernel": "outside pass (one CUDA graph: k_out_light, k_out_side, k_out_bif, k_out_far)",
+                     "kernel": "outside pass (one CUDA graph: k_out_light, k_out_off = bifurcation gathers + side work, k_out_far, k_out_tg)",
                      "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": OUTSIDE_DRAM_BYTES_PER_PASS if WORKLOAD == "p300_dirichlet" and not args.m else None,

@@ -294,6 +294,9 @@ def bench_adjoint(stream):
     step_s = (time.perf_counter() - t) / k
     aa = synth.to_string(res)
     fstar = adjoint.frequency_targets(aa, synth.ascent_targets(300))
+    # one untimed step first: torch loads its own kernels on their first use
+    adjoint.weight_ascent(f, aa, fstar, steps=1, lw0=lw, pb=pb, device="cuda")
+    torch.cuda.synchronize()
     t = time.perf_counter()
     _, hist = adjoint.weight_ascent(f, aa, fstar, steps=50, lw0=lw, pb=pb, device="cuda")
     asc_s = time.perf_counter() - t

@@ -546,31 +546,49 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int n = p.n;
   const int x = blockIdx.x, y = x + d;
-  for (int s = t; s < SO_N; s += NTT) {
-    const OSlot<T> e = ob.otab[(size_t)d * SO_N + s];
-    if (e.src && x >= e.xlo && x <= e.xhi) stage_block(S + (size_t)s * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(s));
-  }
   // small per-cell context on chip: exponents around d, codon-state counts
-  // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors
+  // around x and y, bases of x-1..x+1 and y-1..y+1, energy factors, the
+  // exponents of the prefixes [0, x] and [0, y]; every value is loaded into a
+  // register by its own thread, together with the thread's staged-slot entry,
+  // so that all loads are in flight at once
   __shared__ int sE[96], sMx[72], sMy[72], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N];
   __shared__ int sExy[2];
-  for (int i = t; i < 96; i += NTT) {
-    const int k = d - 47 + i;
-    sE[i] = (k >= 0 && k < n) ? p.E[k] : 0;
+  static_assert(NTT >= SO_N && NTT >= EN_N && NTT >= 96 + 6 * NS + 2, "one context value per thread and kind");
+  int cE = 0, cMx = 0, cMy = 0, cB = 0;
+  T cEn = 0;
+  if (t < 96) {
+    const int k = d - 47 + t;
+    if (k >= 0 && k < n) cE = p.E[k];
+  } else if (t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    const int q = (side == 0 ? x : y) - 1 + r;
+    if (q >= 0 && q < n) cB = p.base[q * NS + a];
+  } else if (t < 98 + 6 * NS) {
+    cE = p.E[t == 96 + 6 * NS ? x : y];
   }
-  for (int i = t; i < 72; i += NTT) {
-    const int qx = x - 35 + i, qy = y - 35 + i;
-    sMx[i] = (qx >= 0 && qx < n) ? p.Mp[qx] : 0;
-    sMy[i] = (qy >= 0 && qy < n) ? p.Mp[qy] : 0;
+  if (t < 72) {
+    const int qx = x - 35 + t, qy = y - 35 + t;
+    if (qx >= 0 && qx < n) cMx = p.Mp[qx];
+    if (qy >= 0 && qy < n) cMy = p.Mp[qy];
   }
-  for (int i = t; i < 3 * NS; i += NTT) {
-    const int r = i / NS, a = i % NS, qx = x - 1 + r, qy = y - 1 + r;
-    sBx[r][a] = (qx >= 0 && qx < n) ? p.base[qx * NS + a] : 0;
-    sBy[r][a] = (qy >= 0 && qy < n) ? p.base[qy * NS + a] : 0;
+  if (t < EN_N) cEn = p.en[t];
+  OSlot<T> e{nullptr, 0, -1};
+  if (t < SO_N) e = ob.otab[(size_t)d * SO_N + t];
+  if (e.src && x >= e.xlo && x <= e.xhi) stage_block(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t));
+  if (t < 96) sE[t] = cE;
+  else if (t < 96 + 6 * NS) {
+    const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
+    if (side == 0) sBx[r][a] = cB;
+    else sBy[r][a] = cB;
+  } else if (t < 98 + 6 * NS) {
+    sExy[t - 96 - 6 * NS] = cE;
   }
-  for (int i = t; i < EN_N; i += NTT) sEn[i] = p.en[i];
-  if (t < 2) sExy[t] = p.E[t == 0 ? x : y];  // exponents of the prefixes [0, x] and [0, y]
+  if (t < 72) {
+    sMx[t] = cMx;
+    sMy[t] = cMy;
+  }
+  if (t < EN_N) sEn[t] = cEn;
   cp_async_wait_all();
   __syncthreads();
   const T *en = sEn;
@@ -693,7 +711,11 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
     if (g < G) {
       const int a = e / My, b = e % My, pe = a * NS + b;
       T v = 0;
-      for (int k = g; k < 2 * MAXLOOP + 3; k += G) {
+      // terms: bulge users (2 per length), the own-cell terms, then the
+      // enclosing pair's interior (XI) and stack terms split by the outer
+      // state of x-1 so that the groups stay balanced
+      constexpr int KXI = 2 * MAXLOOP + 1, KST = KXI + NS, KEND = KST + NS;
+      for (int k = g; k < KEND; k += G) {
         if (k < 2 * MAXLOOP) {
           const int L = k / 2 + 1;
           if ((k & 1) == 0) {
@@ -710,36 +732,33 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
           if (out_ncol(x, d) > 0) v += S[SO_HQC * BLK + pe];
           if (x == 0) v += hQ5Po[pe];  // computed above in this kernel
           else v += clamp_p2<T>(sExy[0] + Ed - sExy[1]) * s2<true, false>(S + SO_GX * BLK, S + SO_HQ5P * BLK, a, b, M0);
-        } else if (k == 2 * MAXLOOP + 1) {
-          if (!encl) continue;
-          // XI[x-1][y+1] = F (T_{x-1} QB T_y) o tm
+        } else if (k < KST) {
+          // XI[x-1][y+1] = F (T_{x-1} QB T_y) o tm, outer state wv of x-1
+          const int wv = k - KXI;
+          if (!encl || wv >= Mxl) continue;
           const T *Txl = S + SO_TXL * BLK, *Ty = S + SO_TY * BLK, *hxi1 = S + SO_HXIE * BLK;
+          const T tl = Txl[wv * NS + a];
+          if (tl == (T)0) continue;
+          const int bw = BASE((x - 1), wv);
           T s2v = 0;
-          for (int wv = 0; wv < Mxl; wv++) {
-            const T tl = Txl[wv * NS + a];
-            if (tl == (T)0) continue;
-            const int bw = BASE((x - 1), wv);
-            for (int z = 0; z < Myr; z++)
-              s2v += tl * hxi1[wv * NS + z] * en[EN_TM + BASE((y + 1), z) * 4 + bw] * Ty[b * NS + z];
-          }
-          v += F2u * s2v;
+          for (int z = 0; z < Myr; z++) s2v += hxi1[wv * NS + z] * en[EN_TM + BASE((y + 1), z) * 4 + bw] * Ty[b * NS + z];
+          v += F2u * tl * s2v;
         } else {
-          if (!encl) continue;
-          // stack of the enclosing pair (x-1, y+1)
+          // stack of the enclosing pair (x-1, y+1), outer state a1 of x-1
+          const int a1 = k - KST;
+          if (!encl || a1 >= Mxl) continue;
           const int pti = pair_type(BASE(x, a), BASE(y, b));
           if (pti < 0) continue;
           const T *Txl = S + SO_TXL * BLK, *Ty = S + SO_TY * BLK;
+          const T tl = Txl[a1 * NS + a];
+          if (tl == (T)0) continue;
+          const int ba = BASE((x - 1), a1);
           T s2v = 0;
-          for (int a1 = 0; a1 < Mxl; a1++) {
-            const T tl = Txl[a1 * NS + a];
-            if (tl == (T)0) continue;
-            const int ba = BASE((x - 1), a1);
-            for (int b1 = 0; b1 < Myr; b1++) {
-              const int pto = pair_type(ba, BASE((y + 1), b1));
-              if (pto >= 0) s2v += tl * gc[a1 * NS + b1] * en[EN_STK + pto * 6 + pti] * Ty[b * NS + b1];
-            }
+          for (int b1 = 0; b1 < Myr; b1++) {
+            const int pto = pair_type(ba, BASE((y + 1), b1));
+            if (pto >= 0) s2v += gc[a1 * NS + b1] * en[EN_STK + pto * 6 + pti] * Ty[b * NS + b1];
           }
-          v += F2u * s2v;
+          v += F2u * tl * s2v;
         }
       }
       RED[t] = v;

@@ -230,22 +230,33 @@ __device__ __forceinline__ T e2(const T *A, const T *B, int a, int b, int Mu) {
   return s;
 }
 
-// Shared-memory versions with runtime trip counts (operands already on chip).
+// Shared-memory versions (operands already on chip): loops unrolled over the
+// padded size with the trip count as a predicate, so that the loads of a sum
+// issue together.
 template <bool TA, bool TB, typename T>
 __device__ __forceinline__ T s2(const T *A, const T *B, int a, int b, int Mu) {
   T s = 0;
-  for (int u = 0; u < Mu; u++) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
+#pragma unroll
+  for (int u = 0; u < NS; u++)
+    if (u < Mu) s += (TA ? A[u * NS + a] : A[a * NS + u]) * (TB ? B[b * NS + u] : B[u * NS + b]);
   return s;
 }
 template <bool TA, bool TB, bool TC, typename T>
 __device__ __forceinline__ T s3(const T *A, const T *B, const T *C, int a, int b, int Mu, int Mv) {
+  T cv[NS];
+#pragma unroll
+  for (int v = 0; v < NS; v++) cv[v] = v < Mv ? (TC ? C[b * NS + v] : C[v * NS + b]) : (T)0;
   T s = 0;
-  for (int u = 0; u < Mu; u++) {
-    const T av = TA ? A[u * NS + a] : A[a * NS + u];
-    if (av == (T)0) continue;
-    T t = 0;
-    for (int v = 0; v < Mv; v++) t += (TB ? B[v * NS + u] : B[u * NS + v]) * (TC ? C[b * NS + v] : C[v * NS + b]);
-    s += av * t;
+#pragma unroll
+  for (int u = 0; u < NS; u++) {
+    if (u < Mu) {
+      const T av = TA ? A[u * NS + a] : A[a * NS + u];
+      T t = 0;
+#pragma unroll
+      for (int v = 0; v < NS; v++)
+        if (v < Mv) t += (TB ? B[v * NS + u] : B[u * NS + v]) * cv[v];
+      s += av * t;
+    }
   }
   return s;
 }

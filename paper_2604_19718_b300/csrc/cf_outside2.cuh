@@ -741,7 +741,9 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
           if (tl == (T)0) continue;
           const int bw = BASE((x - 1), wv);
           T s2v = 0;
-          for (int z = 0; z < Myr; z++) s2v += hxi1[wv * NS + z] * en[EN_TM + BASE((y + 1), z) * 4 + bw] * Ty[b * NS + z];
+#pragma unroll
+          for (int z = 0; z < NS; z++)
+            if (z < Myr) s2v += hxi1[wv * NS + z] * en[EN_TM + BASE((y + 1), z) * 4 + bw] * Ty[b * NS + z];
           v += F2u * tl * s2v;
         } else {
           // stack of the enclosing pair (x-1, y+1), outer state a1 of x-1
@@ -754,8 +756,9 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
           if (tl == (T)0) continue;
           const int ba = BASE((x - 1), a1);
           T s2v = 0;
-          for (int b1 = 0; b1 < Myr; b1++) {
-            const int pto = pair_type(ba, BASE((y + 1), b1));
+#pragma unroll
+          for (int b1 = 0; b1 < NS; b1++) {
+            const int pto = b1 < Myr ? pair_type(ba, BASE((y + 1), b1)) : -1;
             if (pto >= 0) s2v += gc[a1 * NS + b1] * en[EN_STK + pto * 6 + pti] * Ty[b * NS + b1];
           }
           v += F2u * tl * s2v;
@@ -1272,8 +1275,9 @@ __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
             T tt = s2<false, false>(hbi, Ty1, u, b, Mv);
             if (d >= 6) {
               const int pto = pair_type(pa, by0[b]);
-              for (int b2 = 0; b2 < Mv; b2++) {
-                const int pti = pair_type(bu, bv[b2]);
+#pragma unroll
+              for (int b2 = 0; b2 < NS; b2++) {
+                const int pti = b2 < Mv ? pair_type(bu, bv[b2]) : -1;
                 if (pti < 0 || pto < 0) continue;
                 tt += qin[u * NS + b2] * Ty1[b2 * NS + b] * en[EN_STK + pto * 6 + pti];
               }
@@ -1314,8 +1318,9 @@ __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
               T tt = s2<false, false>(Tx, hbi, a, v2, M1);
               if (d >= 6) {
                 const int pto = pair_type(bx0[a], pb);
-                for (int a2 = 0; a2 < M1; a2++) {
-                  const int pti = pair_type(bx1[a2], pv);
+#pragma unroll
+                for (int a2 = 0; a2 < NS; a2++) {
+                  const int pti = a2 < M1 ? pair_type(bx1[a2], pv) : -1;
                   if (pti < 0 || pto < 0) continue;
                   tt += Tx[a * NS + a2] * qin[a2 * NS + v2] * en[EN_STK + pto * 6 + pti];
                 }

@@ -629,10 +629,15 @@ struct LightMap {
 // this diagonal).
 constexpr int NCOPY = 43;
 __device__ __forceinline__ int light_slot(int k) {
-  if (k <= 2) return k == 0 ? LO_CH : LO_XI;       // CH, XI, YY_2 (= XI)
-  if (k < 31) return LO_YY + k - 3;                // YY_L, L = 3..30
-  const int rest[12] = {LO_HB, LO_QB, LO_QMPP, LO_QM2PP, LO_QMPU, LO_G, LO_M2PU, LO_M2UP, LO_M2UU, LO_GX, LO_Q5U, LO_Q5P};
-  return rest[k - 31];
+  static_assert(LO_QB == LO_HB + 1 && LO_QMPP == LO_HB + 2 && LO_QM2PP == LO_HB + 3 && LO_G == LO_QMPU + 1 &&
+                    LO_M2PU == LO_QMPU + 2 && LO_M2UP == LO_QMPU + 3 && LO_M2UU == LO_QMPU + 4 &&
+                    LO_GX == LO_QMPU + 5 && LO_Q5U == LO_QMPU + 6,
+                "result slots in copy-out order");
+  if (k <= 2) return k == 0 ? LO_CH : LO_XI;  // CH, XI, YY_2 (= XI)
+  if (k < 31) return LO_YY + k - 3;           // YY_L, L = 3..30
+  if (k < 35) return LO_HB + k - 31;          // HB, QB, QMpp, QM2pp
+  if (k < 42) return LO_QMPU + k - 35;        // QMpu, G, QM2pu, QM2up, QM2uu, Gx, Q5U
+  return LO_Q5P;
 }
 template <typename T>
 __device__ __forceinline__ T *light_dst(const DP<T> &p, int k, int x, int d, size_t c) {

@@ -689,7 +689,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   __shared__ int sEd;
   __shared__ double smax[NTT / 32];
   __shared__ int sE[96], sE0[4], sBx[3][NS], sBy[3][NS];
-  __shared__ T sEn[EN_N];
+  __shared__ T sEn[EN_N], sHL, wIn[MAXLOOP + 1];
   __shared__ __align__(8) unsigned long long sbar;
   __shared__ T *sDst[NCOPY];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -722,6 +722,8 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     cMax = __ldcg(p.dmax + d - 1);
     cE = __ldcg(p.E + d - 1);
   }
+  T cHL = 0;
+  if (t == NTT - 2) cHL = p.eHL[d + 1];  // hairpin length factor of the cell
   const T *src0 = t < SI_N ? bb.stab[(size_t)d * SI_N + t] : nullptr;
   T *dst0 = t < NCOPY ? bb.dtab[(size_t)d * NCOPY + t] : nullptr;
   __syncthreads();
@@ -776,6 +778,8 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     }
     sEd = e;
     if (x == 0) p.E[d] = e;
+  } else if (t == NTT - 2) {
+    sHL = cHL;
   }
   if (!__syncthreads_and(mbar_wait(&sbar, 0, p.err))) return;
   const int Ed = sEd;
@@ -784,6 +788,8 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   const T *Xl = S + SI_XX * BLK, *Xr = S + SI_XY1 * BLK;
   const int Lmax = min(MAXLOOP, d - 4);
   double lmax = 0.0;
+  // interior-loop weights e^{-I(L)} 2^{E[d-L+2]-E[d]} for the HB sum of phase B
+  if (t >= 2 && t <= MAXLOOP) wIn[t] = en[EN_IN + t] * clamp_p2<T>(EAS(d - t + 2) - Ed);
 
   // ---------------- phase A: one warp per group of tasks
   // Every task but the stack is a sum of at most three terms
@@ -955,12 +961,11 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     if (e < BLK && d >= 2) {
       const T tmo = en[EN_TM + BASE(x, a) * 4 + BASE(y, b)];
       for (int L = 2 + g; L <= Lmax; L += GHB) {
-        const T wl = en[EN_IN + L] * clamp_p2<T>(EAS(d - L + 2) - Ed);
         const T yv = (L == 2) ? O[LO_XI * BLK + e] : O[(LO_YY + L - 3) * BLK + e];
-        v = fma(wl * tmo, yv, v);
+        v = fma(wIn[L] * tmo, yv, v);
       }
       for (int j = g; j < NLO_BU; j += GHB) v += O[(LO_BU + j) * BLK + e];
-      if (g == 0) v = fma(p.eHL[d + 1] * clamp_p2<T>(-Ed) * tmo, O[LO_CH * BLK + e], v);
+      if (g == 0) v = fma(sHL * clamp_p2<T>(-Ed) * tmo, O[LO_CH * BLK + e], v);
     }
 #pragma unroll
     for (int o = 1; o < GHB; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -159,13 +159,89 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   }
 }
 
+// acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f A B over the live rows,
+// summation index and columns
+template <typename T>
+__device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, const T *B, T f, int half, int Ma,
+                                             int Ms, int Mb) {
+  constexpr int HR = NS / 2;
+  T av[HR * NS];
+#pragma unroll
+  for (int e = 0; e < HR * NS; e++) av[e] = __ldg(A + half * HR * NS + e) * f;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    if (s < Ms) {
+      T bv[NS];
+#pragma unroll
+      for (int b = 0; b < NS; b++) bv[b] = __ldg(B + s * NS + b);
+#pragma unroll
+      for (int r = 0; r < HR; r++)
+        if (half * HR + r < Ma) {
+#pragma unroll
+          for (int b = 0; b < NS; b++)
+            if (b < Mb) acc[r * NS + b] = fma(av[r * NS + s], bv[b], acc[r * NS + b]);
+        }
+    }
+  }
+}
+
+// sum acc over the 16 lanes of each half-warp; lanes 0 and 16 store rows
+// 0..2 and 3..5 of the result into dst
+template <typename T>
+__device__ __forceinline__ void bif_half_reduce(T (&acc)[NS / 2 * NS], T *dst, int lane) {
+  constexpr int HR = NS / 2;
+#pragma unroll
+  for (int e = 0; e < HR * NS; e++) {
+    T v = acc[e];
+#pragma unroll
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc[e] = v;
+  }
+  if ((lane & 15) == 0) {
+#pragma unroll
+    for (int e = 0; e < HR * NS; e++) dst[(lane >> 4) * HR * NS + e] = acc[e];
+  }
+}
+
+// Exterior sum of diagonal d (split points k = 4..d-4 of [0, d]) by all eight
+// warps of the CTA, 16 split points per warp and step, in the layout of
+// bif_half_acc; the warps' sums are added in order.
+template <typename T>
+__device__ __forceinline__ void in_bif_ext_group(const DP<T> &p, const BifBuf<T> &bb, int d, T (*red)[BLK]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, half = lane >> 4, sl = lane & 15;
+  const int n = p.n;
+  const int Eref = __ldcg(p.E + d - 4);
+  const int Ma = p.Mp[0], Mb = p.Mp[d];
+  T acc[NS / 2 * NS];
+#pragma unroll
+  for (int e = 0; e < NS / 2 * NS; e++) acc[e] = (T)0;
+  const int nk = max(0, d - 7), nc = (nk + 15) / 16;
+  for (int c = w; c < nc; c += 8) {
+    const int k = 4 + c * 16 + sl;
+    if (k <= d - 4) {
+      const T f = clamp_p2<T>(__ldcg(p.E + k) + __ldcg(p.E + d - k) - Eref);
+      bif_half_acc(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, f, half, Ma, p.Mp[k], Mb);
+    }
+  }
+  bif_half_reduce(acc, red[w], lane);
+  __syncthreads();
+  if (threadIdx.x < BLK) {
+    T v = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
+    bb.ext[(size_t)(d % BIFRING) * BLK + threadIdx.x] = v;
+  }
+}
+
 // Near split points of a banded diagonal are few (at most 2 (2 FARD - 5)):
-// two warps per cell, four cells per 256-thread CTA.  Same sums and order
-// of additions per cell as in_bif_cell with NW = 2.
+// two warps per cell, four cells per 256-thread CTA.  Within a warp the two
+// half-warps take rows 0..2 and 3..5 of the products and their 16 lanes 16
+// split points, so that a lane holds three rows of A and of the sum.
 template <typename T>
 __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb, int d, int cb0, T (*red)[BLK]) {
-  constexpr int NW = 2, NG = 4;
+  constexpr int NW = 2, NG = 4, HR = NS / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w / NW, wg = w % NW;
+  const int half = lane >> 4, sl = lane & 15;
   const int n = p.n, ncell = n - d;
   const int Eref = __ldcg(p.E + d - 4);
   const int slot = d % BIFRING;
@@ -183,25 +259,21 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
   if (cb < ncell) {
     const int x = cb, y = x + d;
     const int Ma = p.Mp[x], Mb = p.Mp[y];
-    T acc[BLK];
-    zero_block(acc);
+    T acc[HR * NS];
+#pragma unroll
+    for (int e = 0; e < HR * NS; e++) acc[e] = (T)0;
     const int n1 = max(0, a1 - 4), n2 = max(0, d - 3 - a2);
-    const int nc = (n1 + n2 + KCH - 1) / KCH;
+    const int nc = (n1 + n2 + 15) / 16;
     const T ec = p.en[EN_EC];
     for (int c = wg; c < nc; c += NW) {
-      const int q = c * KCH + lane;
+      const int q = c * 16 + sl;
       if (q < n1 + n2) {
         const int k = x + (q < n1 ? 5 + q : a2 + q - n1);
-        T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
-        acc_mm_v<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, Ma, p.Mp[k], Mb, f);
+        const T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
+        bif_half_acc(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, f, half, Ma, p.Mp[k], Mb);
       }
     }
-    warp_reduce_block(acc, Ma, Mb);
-    if (lane < 2) {
-#pragma unroll
-      for (int e = 0; e < BLK; e++)
-        if ((e & 1) == lane) red[w][e] = acc[e];
-    }
+    bif_half_reduce(acc, red[w], lane);
   }
   __syncthreads();
   if (threadIdx.x < NG * BLK) {
@@ -215,7 +287,7 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
         const int nsl = far_nslice(n, x / FARTX * FARTX, d0);
         const float *fp = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + (d - d0)) * bb.farslices) * BLK + e;
         float fv = 0.f;
-        for (int sl = 0; sl < nsl; sl++) fv += fp[(size_t)sl * BLK];
+        for (int sl2 = 0; sl2 < nsl; sl2++) fv += fp[(size_t)sl2 * BLK];
         v += (T)((double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref) * (double)fv);
       }
       bb.main[((size_t)slot * n + x) * BLK + e] = v;
@@ -224,12 +296,13 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
 }
 
 // binary32 with far bands: CTA b < last takes cells 4b..4b+3, the last CTA the
-// exterior sum with all eight warps
+// exterior sum with all eight warps; 64 registers, so that a CTA leaves room
+// for the light kernel's CTAs on its SM
 template <typename T>
-__global__ void __launch_bounds__(256) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
-    in_bif_cell<T, 8>(p, bb, d, p.n - d, red);
+    in_bif_ext_group<T>(p, bb, d, red);
     return;
   }
   in_bif_group<T>(p, bb, d, blockIdx.x * 4, red);

@@ -159,28 +159,50 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   }
 }
 
-// acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f A B over the live rows,
-// summation index and columns
-template <typename T>
+// acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f op(A) op(B) over the live
+// rows (Ma), summation index (Ms) and columns (Mb); TA / TB read A / B
+// transposed.  A lane holds three rows of op(A) and one row of B at a time.
+template <bool TA, bool TB, typename T>
 __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, const T *B, T f, int half, int Ma,
                                              int Ms, int Mb) {
   constexpr int HR = NS / 2;
   T av[HR * NS];
 #pragma unroll
-  for (int e = 0; e < HR * NS; e++) av[e] = __ldg(A + half * HR * NS + e) * f;
+  for (int r = 0; r < HR; r++)
 #pragma unroll
-  for (int s = 0; s < NS; s++) {
-    if (s < Ms) {
-      T bv[NS];
+    for (int s = 0; s < NS; s++)
+      av[r * NS + s] = __ldg(TA ? A + s * NS + half * HR + r : A + (half * HR + r) * NS + s) * f;
+  if (!TB) {
 #pragma unroll
-      for (int b = 0; b < NS; b++) bv[b] = __ldg(B + s * NS + b);
+    for (int s = 0; s < NS; s++) {
+      if (s < Ms) {
+        T bv[NS];
 #pragma unroll
-      for (int r = 0; r < HR; r++)
-        if (half * HR + r < Ma) {
+        for (int b = 0; b < NS; b++) bv[b] = __ldg(B + s * NS + b);
 #pragma unroll
-          for (int b = 0; b < NS; b++)
-            if (b < Mb) acc[r * NS + b] = fma(av[r * NS + s], bv[b], acc[r * NS + b]);
-        }
+        for (int r = 0; r < HR; r++)
+          if (half * HR + r < Ma) {
+#pragma unroll
+            for (int b = 0; b < NS; b++)
+              if (b < Mb) acc[r * NS + b] = fma(av[r * NS + s], bv[b], acc[r * NS + b]);
+          }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < NS; b++) {
+      if (b < Mb) {
+        T bv[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) bv[s] = __ldg(B + b * NS + s);
+#pragma unroll
+        for (int r = 0; r < HR; r++)
+          if (half * HR + r < Ma) {
+#pragma unroll
+            for (int s = 0; s < NS; s++)
+              if (s < Ms) acc[r * NS + b] = fma(av[r * NS + s], bv[s], acc[r * NS + b]);
+          }
+      }
     }
   }
 }
@@ -220,7 +242,7 @@ __device__ __forceinline__ void in_bif_ext_group(const DP<T> &p, const BifBuf<T>
     const int k = 4 + c * 16 + sl;
     if (k <= d - 4) {
       const T f = clamp_p2<T>(__ldcg(p.E + k) + __ldcg(p.E + d - k) - Eref);
-      bif_half_acc(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, f, half, Ma, p.Mp[k], Mb);
+      bif_half_acc<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, f, half, Ma, p.Mp[k], Mb);
     }
   }
   bif_half_reduce(acc, red[w], lane);
@@ -270,7 +292,7 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
       if (q < n1 + n2) {
         const int k = x + (q < n1 ? 5 + q : a2 + q - n1);
         const T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
-        bif_half_acc(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, f, half, Ma, p.Mp[k], Mb);
+        bif_half_acc<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, f, half, Ma, p.Mp[k], Mb);
       }
     }
     bif_half_reduce(acc, red[w], lane);

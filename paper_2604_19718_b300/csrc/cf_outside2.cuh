@@ -186,14 +186,44 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
   }
 }
 
-// binary32: at most one chunk of near terms per gather and cell (a banded
-// diagonal keeps fewer than KCH near terms; an unbanded one lies within
+// binary32: at most 2 OFD - 1 near terms per gather and cell (a banded
+// diagonal keeps the adjoint diagonals below c; an unbanded one lies within
 // 2 OFD + 3 of the last diagonal), so a pair of warps per cell (row gather,
-// column gather) and four cells per 256-thread CTA; same sums as
-// out_bif_cell.
+// column gather) and four cells per 256-thread CTA; within a warp the two
+// half-warps take rows 0..2 and 3..5 of the sum (bif_half_acc) and their 16
+// lanes 16 terms.
+// Exterior gather hGx[d] = sum_{yy >= d+4} hQ5P[yy] QB[d][yy]^T by all eight
+// warps of the CTA, 16 terms per warp and step; the warps' sums are added in
+// order.
+template <typename T>
+__device__ __forceinline__ void out_bif_ext_group(const DP<T> &p, const OutBuf<T> &ob, int d, T (*red)[BLK]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, half = lane >> 4, sl = lane & 15;
+  const int n = p.n, Ed = p.E[d];
+  const int Ma = p.Mp[0], Mb = p.Mp[d];
+  T acc[NS / 2 * NS];
+#pragma unroll
+  for (int e = 0; e < NS / 2 * NS; e++) acc[e] = (T)0;
+  const int nk = d >= 1 ? max(0, n - d - 4) : 0, nc = (nk + 15) / 16;
+  for (int c = w; c < nc; c += 8) {
+    const int yy = d + 4 + c * 16 + sl;
+    if (yy <= n - 1) {
+      const T f = clamp_p2<T>(Ed + p.E[yy - d] - p.E[yy]);
+      bif_half_acc<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, f, half, Ma, p.Mp[yy], Mb);
+    }
+  }
+  bif_half_reduce(acc, red[w], lane);
+  __syncthreads();
+  if (threadIdx.x < BLK) {
+    T v = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
+    ob.hgx[(size_t)(d % BIFRING) * BLK + threadIdx.x] = v;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &ob, int d, int cb0, T (*red)[BLK]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w >> 1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = w >> 1, half = lane >> 4, sl = lane & 15;
   const int n = p.n, ncell = n - d;
   const int *E = p.E;
   const int Ed = E[d];
@@ -204,35 +234,33 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
   if (cb0 + g < ncell) {
     const int x = cb0 + g, y = x + d;
     const int Ma = p.Mp[x], Mb = p.Mp[y];
-    T acc[BLK];
-    zero_block(acc);
+    T acc[NS / 2 * NS];
+#pragma unroll
+    for (int e = 0; e < NS / 2 * NS; e++) acc[e] = (T)0;
     if ((w & 1) == 0) {
       const int ylim = banded ? min(n - 1, x + of_c(alo) - 1) : n - 1;
-      const int nr = ylim >= y + 4 ? (ylim - y - 4 + KCH) / KCH : 0;
+      const int nr = ylim >= y + 4 ? (ylim - y - 4 + 16) / 16 : 0;
       for (int q = 0; q < nr; q++) {
-        const int yy = y + 4 + q * KCH + lane;
+        const int yy = y + 4 + q * 16 + sl;
         if (yy <= ylim) {
-          T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
-          acc_mm_v<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, Ma, p.Mp[yy], Mb, f);
+          const T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
+          bif_half_acc<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, f, half, Ma,
+                                    p.Mp[yy], Mb);
         }
       }
     } else {
       const int xlo = banded ? max(0, y - of_c(alo) + 1) : 0;
-      const int nq = x - 5 >= xlo ? (x - 5 - xlo + KCH) / KCH : 0;
+      const int nq = x - 5 >= xlo ? (x - 5 - xlo + 16) / 16 : 0;
       for (int q = 0; q < nq; q++) {
-        const int xx = x - 5 - q * KCH - lane;
+        const int xx = x - 5 - q * 16 - sl;
         if (xx >= xlo) {
-          T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
-          acc_mm_v<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, Ma, p.Mp[xx], Mb, f);
+          const T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
+          bif_half_acc<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, f, half, Ma,
+                                    p.Mp[xx], Mb);
         }
       }
     }
-    warp_reduce_block(acc, Ma, Mb);
-    if (lane < 2) {
-#pragma unroll
-      for (int e = 0; e < BLK; e++)
-        if ((e & 1) == lane) red[w][e] = acc[e];
-    }
+    bif_half_reduce(acc, red[w], lane);
   }
   __syncthreads();
   if (threadIdx.x < 4 * BLK) {
@@ -1086,22 +1114,23 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 
 
 // The off-chain work that the light kernel of diagonal d waits for, as one
-// launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (one
-// cell per CTA, or with far bands four cells per CTA, then the exterior), the
+// launch: CTAs 0..nbif-1 take the bifurcation gathers of diagonal d (GRP, with
+// far bands: four cells per CTA, then the exterior, at 64 registers so that
+// the CTAs leave room for the light kernels; else one cell per CTA), the
 // others the side work of the cells of diagonal d+4.  Both parts start after
 // the light kernel of d+4.
-template <typename T>
-__global__ void __launch_bounds__(NT3) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+template <typename T, bool GRP>
+__global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[16][BLK];
   __shared__ SideCtx cx;
   __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
   __shared__ __align__(8) unsigned long long sbar;
   if ((int)blockIdx.x < nbif) {
-    if (ob.far == nullptr)
+    if constexpr (!GRP)
       out_bif_cell(p, ob, d, blockIdx.x, red);
     else if ((int)blockIdx.x == nbif - 1)
-      out_bif_cell(p, ob, d, p.n - d, red);
+      out_bif_ext_group(p, ob, d, red);
     else
       out_bif_group(p, ob, d, blockIdx.x * 4, red);
     return;

@@ -471,7 +471,8 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
                                   (int)smemw));
   CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_tg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)out_tg_smem<T>()));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   DP<T> dp = t.dp;
@@ -532,7 +533,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       int nbif = hasb ? (banded ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
       void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
-      kp.func = (void *)k_out_off<T>;
+      kp.func = banded ? (void *)k_out_off<T, true> : (void *)k_out_off<T, false>;  // far bands: grouped gathers
       kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0));
       kp.blockDim = dim3(NT3);
       kp.sharedMemBytes = (unsigned)smem3;

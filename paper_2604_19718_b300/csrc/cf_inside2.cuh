@@ -1021,7 +1021,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
 #pragma unroll
       for (int b = 0; b < NS; b++) r[b] = (a == b && a < M) ? (T)1 : (T)0;
     } else {
-#pragma unroll 1
+#pragma unroll
       for (int q = 0; q < 3; q++) {
         const T *A = q == 0 ? A0 : (q == 1 ? A1 : A2), *B = q == 0 ? B0 : (q == 1 ? B1 : B2);
         const T *C = q == 0 ? C0 : (q == 1 ? C1 : nullptr);

@@ -601,6 +601,16 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
     if (qy >= 0 && qy < n) cMy = p.Mp[qy];
   }
   if (t < EN_N) cEn = p.en[t];
+  // loop-length weights: bulge users eBu(L) 2^{E[d]-E[d+L]}, interior
+  // eIn(L) 2^{E[d-L+2]-E[d]}, from the thread's own loads (no extra phase)
+  __shared__ T wBuU[MAXLOOP + 1], wIn[MAXLOOP + 1];
+  T cwU = 0, cwI = 0;
+  if (t <= MAXLOOP) {
+    const int L = t, E0 = p.E[d];
+    const T bu = p.en[EN_BU + L], in = p.en[EN_IN + L];
+    if (L >= 1 && d + L < n) cwU = bu * clamp_p2<T>(E0 - p.E[d + L]);
+    if (L >= 2 && d - L + 2 >= 0) cwI = in * clamp_p2<T>(p.E[d - L + 2] - E0);
+  }
   OSlot<T> e{nullptr, 0, -1};
   if (t < SO_N) e = ob.otab[(size_t)d * SO_N + t];
   if (e.src && x >= e.xlo && x <= e.xhi) stage_block(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t));
@@ -617,6 +627,10 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
     sMy[t] = cMy;
   }
   if (t < EN_N) sEn[t] = cEn;
+  if (t <= MAXLOOP) {
+    wBuU[t] = cwU;
+    wIn[t] = cwI;
+  }
   cp_async_wait_all();
   __syncthreads();
   const T *en = sEn;
@@ -632,16 +646,6 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   const T F2u = (d + 2 < n) ? clamp_p2<T>(Ed - EAS(d + 2)) : (T)0;
   const T *gc = S + SO_GC * BLK;
   const T *Xxl = S + SO_XXL * BLK, *Xy = S + SO_XY * BLK;
-  // loop-length weights: bulge users eBu(L) 2^{E[d]-E[d+L]}, own bulges
-  // eBu(L) 2^{E[d-L]-E[d]}, interior eIn(L) 2^{E[d-L+2]-E[d]}
-  __shared__ T wBuU[MAXLOOP + 1], wBu[MAXLOOP + 1], wIn[MAXLOOP + 1];
-  if (t <= MAXLOOP) {
-    const int L = t;
-    wBuU[L] = (L >= 1 && d + L < n) ? en[EN_BU + L] * clamp_p2<T>(Ed - EAS(d + L)) : (T)0;
-    wBu[L] = (L >= 1 && d - L >= 4) ? en[EN_BU + L] * clamp_p2<T>(EAS(d - L) - Ed) : (T)0;
-    wIn[L] = (L >= 2 && d - L + 2 >= 0) ? en[EN_IN + L] * clamp_p2<T>(EAS(d - L + 2) - Ed) : (T)0;
-  }
-  __syncthreads();
 
   // ---------------- A: QM2 adjoints with unpaired ends; exterior prefix adjoint
   if (d >= 10 && (t < MM || (t >= 64 && t < 64 + MM) || (t >= 128 && t < 128 + MM))) {

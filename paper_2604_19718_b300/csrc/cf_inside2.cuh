@@ -36,6 +36,7 @@ struct BifBuf {
   int ncmax;
   float *far;     // [2][n][FARD][farslices][36] far split points of a band, per slice (binary32; nullptr: none)
   int farslices;  // slices per cell in the far buffer
+  float *gfac;    // [2][n] far-band rescale factors 2^{E[a] - s a - e0} per band parity (binary32)
   const T **stab; // [n][SI_N] source of every staged slot of the light cell x = 0 of each diagonal
   T **dtab;       // [n][NCOPY] destination of every result of that cell
 };
@@ -83,9 +84,10 @@ __device__ __forceinline__ FarChord far_chord(const int *E, int c) {
 }
 
 // ---------------------------------------------------------------- K1
-// One cell per block (the last unit of a diagonal: the exterior sum); warp w
-// of NW takes the chunks w, w+NW, ... of 32 split points, lanes over the split
-// point; per-lane sums are reduced once per warp, then across warps.
+// Without far bands (binary64, short proteins): one cell per block (the last
+// unit of a diagonal: the exterior sum); warp w of NW takes the chunks w,
+// w+NW, ... of 32 split points a = 5..d-4, lanes over the split point;
+// per-lane sums are reduced once per warp, then across warps.
 template <typename T, int NW>
 __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int cb, T (*red)[BLK]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -97,18 +99,7 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   const int Ma = p.Mp[x], Mb = p.Mp[y];
   T acc[BLK];
   zero_block(acc);
-  // near split points a in [5, a1] and [a2, d-4]; with a far band the middle
-  // [a1+1, a2-1] comes from k_in_far
-  const int d0 = d / FARD * FARD;
-  const bool banded = bb.far != nullptr && far_band(d0);
-  int a1 = d - 4, a2 = d - 3;
-  if (banded) {
-    const int c = far_c(d0), alo = max(5, d - c), ahi = min(c, d - 4);
-    if (alo <= ahi) {
-      a1 = alo - 1;
-      a2 = ahi + 1;
-    }
-  }
+  const int a1 = d - 4, a2 = d - 3;
   if (w < NW) {
     if (!ext) {
       const int n1 = max(0, a1 - 4), n2 = max(0, d - 3 - a2);
@@ -145,15 +136,6 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
     T v = 0;
 #pragma unroll
     for (int k = 0; k < NW; k++) v += red[k][e];
-    if (banded && !ext) {
-      // far split points: the slices of the cell's tile in order, relative to 2^{s d + 2 e0}
-      const FarChord ch = far_chord(p.E, far_c(d0));
-      const int nsl = far_nslice(n, x / FARTX * FARTX, d0);
-      const float *fp = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + (d - d0)) * bb.farslices) * BLK + e;
-      float fv = 0.f;
-      for (int sl = 0; sl < nsl; sl++) fv += fp[(size_t)sl * BLK];
-      v += (T)((double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref) * (double)fv);
-    }
     T *dst = ext ? bb.ext + (size_t)slot * BLK : bb.main + ((size_t)slot * n + x) * BLK;
     dst[e] = v;
   }
@@ -297,6 +279,12 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
     }
     bif_half_reduce(acc, red[w], lane);
   }
+  // far split points are relative to 2^{s d + 2 e0}: one factor per diagonal
+  __shared__ double sfar;
+  if (banded && threadIdx.x == 0) {
+    const FarChord ch = far_chord(p.E, far_c(d0));
+    sfar = (double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref);
+  }
   __syncthreads();
   if (threadIdx.x < NG * BLK) {
     const int g2 = threadIdx.x / BLK, e = threadIdx.x % BLK, cb2 = cb0 + g2;
@@ -304,13 +292,12 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
       const int x = cb2;
       T v = red[g2 * NW][e] + red[g2 * NW + 1][e];
       if (banded) {
-        // far split points: the slices of the cell's tile in order, relative to 2^{s d + 2 e0}
-        const FarChord ch = far_chord(p.E, far_c(d0));
+        // far split points: the slices of the cell's tile in order
         const int nsl = far_nslice(n, x / FARTX * FARTX, d0);
         const float *fp = bb.far + ((((size_t)((d0 / FARD) & 1) * n + x) * FARD + (d - d0)) * bb.farslices) * BLK + e;
         float fv = 0.f;
         for (int sl2 = 0; sl2 < nsl; sl2++) fv += fp[(size_t)sl2 * BLK];
-        v += (T)((double)p.en[EN_EC] * exp2(ch.s * (double)d + 2.0 * ch.e0 - (double)Eref) * (double)fv);
+        v += (T)(sfar * (double)fv);
       }
       bb.main[((size_t)slot * n + x) * BLK + e] = v;
     }
@@ -579,6 +566,16 @@ __device__ __forceinline__ T row_absmax(const T (&r)[NS]) {
 // rows and QB[k][y] for its FARTX + FARD - 1 columns, one TMA bulk copy per
 // block; the linear-exponent factors of both halves are applied as the
 // blocks are used.  The slice's sums go to their own place in the band buffer.
+// the rescale factors of band d0, once per band (binary64 exp2: the
+// exponents reach the thousands)
+__global__ void k_in_far_factors(DP<float> p, BifBuf<float> bb, int d0) {
+  const int c = far_c(d0);
+  const FarChord ch = far_chord(p.E, c);
+  float *dst = bb.gfac + (size_t)((d0 / FARD) & 1) * p.n;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= c; a += gridDim.x * blockDim.x)
+    dst[a] = (float)exp2((double)__ldcg(p.E + a) - ch.s * a - ch.e0);
+}
+
 __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, int d0) {
   constexpr int TY = FARTX + FARD - 1, STAGE = FARKC * (FARTX + TY) * BLK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -591,8 +588,8 @@ __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, i
   const int kbeg = far_kmin(x0) + blockIdx.y * FARKS;
   const int kend = min(far_kmax(n, x0, d0), kbeg + FARKS - 1);
   if (kbeg > kend) return;
-  const FarChord ch = far_chord(p.E, c);
-  for (int a = t; a <= c; a += 256) gf[a] = (float)exp2((double)__ldcg(p.E + a) - ch.s * a - ch.e0);
+  const float *gsrc = bb.gfac + (size_t)((d0 / FARD) & 1) * n;
+  for (int a = t; a <= c; a += 256) gf[a] = __ldcg(gsrc + a);
   if (t == 0) {
     mbar_init(&sbar[0], 1);
     mbar_init(&sbar[1], 1);

@@ -36,6 +36,7 @@ struct OutBuf {
   T *hq;   // [BIFRING][n][36] column gathers (contribution to hQB)
   T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
   float *far;  // [2 gathers][3 slots][n][OFD][36] far terms of a band (binary32; nullptr: none)
+  float *fwh;      // [2][n] far-band rescale factors 2^{E[D] - s D - e0} and their inverses (binary32)
   OSlot<T> *otab;  // [n][SO_N] sources of the light kernel's staged slots per diagonal
   const T **stab;  // [n][SS_N] sources of the side work's staged slots for cell x = 0 (nullptr: not staged)
 };
@@ -84,9 +85,9 @@ __host__ __device__ __forceinline__ int out_next(int n, int d) {  // hGx terms y
 }
 
 // ---------------------------------------------------------------- K1'
-// One 256-thread block per cell (last block: the exterior gather). Warps 0..3
-// take the row-gather chunks, warps 4..7 the column-gather chunks (all eight
-// take the exterior chunks); lanes over the summation index.
+// Without far bands (binary64, short proteins): one 256-thread block per cell
+// (last block: the exterior gather); the row- and column-gather chunks are
+// dealt to the eight warps; lanes over the summation index.
 template <typename T>
 __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob, int d, int cb, T (*red)[BLK]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -112,15 +113,11 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
     }
   } else {
     // row chunks 0..nr-1 and column chunks nr..nr+nq-1 dealt round-robin to
-    // all eight warps (a cell near either end has almost only one kind); with
-    // a far band only the near terms (adjoint diagonal < c) are summed here
+    // all eight warps (a cell near either end has almost only one kind)
     const int x = cb, y = x + d;
     Ma = p.Mp[x];
     Mb = p.Mp[y];
-    const int alo = d / OFD * OFD;
-    const bool banded = ob.far != nullptr && of_band(n, alo);
-    const int ylim = banded ? min(n - 1, x + of_c(alo) - 1) : n - 1;  // row terms yy <= ylim
-    const int xlo = banded ? max(0, y - of_c(alo) + 1) : 0;          // column terms xx >= xlo
+    const int ylim = n - 1, xlo = 0;  // no far bands here: every term
     const int nr = ylim >= y + 4 ? (ylim - y - 4 + KCH) / KCH : 0;
     const int nq = x - 5 >= xlo ? (x - 5 - xlo + KCH) / KCH : 0;
     for (int q = w; q < nr; q += 8) {
@@ -172,14 +169,6 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
 #pragma unroll
       for (int k = 0; k < 8; k++) u += red[8 + k][e];
       const int x = cb;
-      const int alo = d / OFD * OFD;
-      if (ob.far != nullptr && of_band(n, alo)) {
-        const OChord ch = of_chord(E, n);
-        const double fac = (double)ec * exp2((double)Ed - ch.s * (double)d);
-        const size_t fo = (((size_t)((alo / OFD) % 3) * n + x) * OFD + (d - alo)) * BLK + e;
-        v += (T)(fac * (double)ob.far[fo]);
-        u += (T)(fac * (double)ob.far[(size_t)3 * n * OFD * BLK + fo]);
-      }
       ob.hg[((size_t)slot * n + x) * BLK + e] = v;
       ob.hq[((size_t)slot * n + x) * BLK + e] = u;
     }
@@ -262,14 +251,19 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
     }
     bif_half_reduce(acc, red[w], lane);
   }
+  // far terms are relative to ec 2^{E[d] - s d}: one factor per diagonal
+  __shared__ double sfar;
+  if (banded && threadIdx.x == 0) {
+    const OChord ch = of_chord(E, n);
+    sfar = (double)ec * exp2((double)Ed - ch.s * (double)d);
+  }
   __syncthreads();
   if (threadIdx.x < 4 * BLK) {
     const int g2 = threadIdx.x / BLK, e = threadIdx.x % BLK, x = cb0 + g2;
     if (x < ncell) {
       T v = red[2 * g2][e], u = red[2 * g2 + 1][e];
       if (banded) {
-        const OChord ch = of_chord(E, n);
-        const double fac = (double)ec * exp2((double)Ed - ch.s * (double)d);
+        const double fac = sfar;
         const size_t fo = (((size_t)((alo / OFD) % 3) * n + x) * OFD + (d - alo)) * BLK + e;
         v += (T)(fac * (double)ob.far[fo]);
         u += (T)(fac * (double)ob.far[(size_t)3 * n * OFD * BLK + fo]);
@@ -300,6 +294,17 @@ __global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
 // staged per xx as 16 G columns and 31 adjoint columns.  Blocks arrive by TMA
 // bulk copies into two alternating stages; each CTA takes a slice of OFKS
 // summation indices and adds its sums into the band buffer (zeroed first).
+// the rescale factors of every far band of the pass (one chord over diagonals
+// 5..n-1), once per pass (binary64 exp2: the exponents reach the thousands)
+__global__ void k_out_far_factors(DP<float> p, OutBuf<float> ob) {
+  const OChord ch = of_chord(p.E, p.n);
+  for (int D = blockIdx.x * blockDim.x + threadIdx.x; D < p.n; D += gridDim.x * blockDim.x) {
+    const double z = (double)p.E[D] - ch.s * D - ch.e0;
+    ob.fwh[D] = (float)exp2(z);
+    ob.fwh[p.n + D] = (float)exp2(-z);
+  }
+}
+
 template <bool ROW>
 __global__ void __launch_bounds__(256) k_out_far(DP<float> p, OutBuf<float> ob, int alo) {
   constexpr int TY = OFTX + OFD - 1, STAGE = OFKC * (OFTX + TY) * BLK;
@@ -314,11 +319,9 @@ __global__ void __launch_bounds__(256) k_out_far(DP<float> p, OutBuf<float> ob, 
   const int lo = ROW ? x0 + c : 0, hi = ROW ? n - 1 : x0 + OFTX - 1 + alo + OFD - 1 - c;
   const int kbeg = lo + blockIdx.y * OFKS, kend = min(hi, kbeg + OFKS - 1);
   if (kbeg > kend) return;
-  const OChord ch = of_chord(p.E, n);
   for (int D = t; D < n; D += 256) {
-    const double z = (double)p.E[D] - ch.s * D - ch.e0;
-    fw[D] = (float)exp2(z);
-    fh[D] = (float)exp2(-z);
+    fw[D] = __ldcg(ob.fwh + D);
+    fh[D] = __ldcg(ob.fwh + n + D);
   }
   if (t == 0) {
     mbar_init(&sbar[0], 1);

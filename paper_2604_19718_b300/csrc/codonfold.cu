@@ -267,8 +267,11 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, dalloc(L, &t.bb.ext, (size_t)BIFRING * BLK));
   t.bb.far = nullptr;
   t.bb.farslices = far_nslice(n, 0, std::max(0, (n - 1) / FARD * FARD));  // the widest band's slices
-  if (sizeof(T) == sizeof(float) && n > 3 * FARD)
+  t.bb.gfac = nullptr;
+  if (sizeof(T) == sizeof(float) && n > 3 * FARD) {
     CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
+    CF_CUDA(p, dalloc(L, &t.bb.gfac, (size_t)2 * n));
+  }
   const T **stab = nullptr;
   CF_CUDA(p, dalloc(L, &stab, (size_t)n * SI_N));
   t.bb.stab = stab;
@@ -345,13 +348,26 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
       std::memcpy(&bbf, &bb, sizeof(bbf));
       int b0 = d0;
       void *fargs[] = {&dpf, &bbf, &b0};
+      // the band's rescale factors, after the light kernel of c and after the
+      // far kernel two bands back (same factor buffer)
+      cudaKernelNodeParams kq = {};
+      kq.func = (void *)k_in_far_factors;
+      kq.gridDim = dim3((far_c(d0) + 256) / 256);
+      kq.blockDim = dim3(256);
+      kq.kernelParams = fargs;
+      cudaGraphNode_t qdeps[2] = {k2[far_c(d0)], nullptr}, kfq;
+      int nq = 1;
+      if (d0 / FARD >= 2 && kf[d0 / FARD - 2]) qdeps[nq++] = kf[d0 / FARD - 2];
+      e = cudaGraphAddKernelNode(&kfq, g, qdeps, nq, &kq);
+      if (e == cudaSuccess) e = set_priority(kfq, false);
+      nodes++;
       cudaKernelNodeParams kp = {};
       kp.func = (void *)k_in_far;
       kp.gridDim = dim3((n - d0 + FARTX - 1) / FARTX, far_nslice(n, 0, d0));
       kp.blockDim = dim3(256);
       kp.sharedMemBytes = (unsigned)in_far_smem(far_c(d0));
       kp.kernelParams = fargs;
-      e = cudaGraphAddKernelNode(&kf[d0 / FARD], g, &k2[far_c(d0)], 1, &kp);
+      if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kf[d0 / FARD], g, &kfq, 1, &kp);
       if (e == cudaSuccess) e = set_priority(kf[d0 / FARD], false);
       nodes++;
       if (e != cudaSuccess) break;
@@ -433,7 +449,11 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, dalloc(L, &t.ob.hq, (size_t)BIFRING * n * BLK));
   CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * BLK));
   t.ob.far = nullptr;
-  if (sizeof(T) == sizeof(float) && of_band(n, 0)) CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
+  t.ob.fwh = nullptr;
+  if (sizeof(T) == sizeof(float) && of_band(n, 0)) {
+    CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
+    CF_CUDA(p, dalloc(L, &t.ob.fwh, (size_t)2 * n));
+  }
   CF_CUDA(p, dalloc(L, &t.ob.otab, (size_t)n * SO_N));
   const T **sstab = nullptr;
   CF_CUDA(p, dalloc(L, &sstab, (size_t)n * SS_N));
@@ -495,6 +515,22 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
                                     (int)out_far_smem(n)));
   }
   int nodes = 0;
+  // far-band rescale factors of the pass, before the first light kernel
+  cudaGraphNode_t first = m[4];
+  if (banded && e == cudaSuccess) {
+    DP<float> dpf;
+    OutBuf<float> obf;
+    std::memcpy(&dpf, &dp, sizeof(dpf));
+    std::memcpy(&obf, &ob, sizeof(obf));
+    void *qargs[] = {&dpf, &obf};
+    cudaKernelNodeParams kq = {};
+    kq.func = (void *)k_out_far_factors;
+    kq.gridDim = dim3((n + 255) / 256);
+    kq.blockDim = dim3(256);
+    kq.kernelParams = qargs;
+    e = cudaGraphAddKernelNode(&first, g, &m[4], 1, &kq);
+    nodes++;
+  }
   for (int d = n - 1; d >= 0 && e == cudaSuccess; d--) {
     int dd = d;
     void *args[] = {&dp, &ob, &dd};
@@ -551,7 +587,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     }
     cudaGraphNode_t deps[3];
     int nd = 0;
-    deps[nd++] = (d == n - 1) ? m[4] : k2[d + 1];
+    deps[nd++] = (d == n - 1) ? first : k2[d + 1];
     if (hasb || hass) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;

@@ -1052,11 +1052,20 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     T v = 0;
     if (e < BLK && d >= 2) {
       const T tmo = en[EN_TM + BASE(x, a) * 4 + BASE(y, b)];
-      for (int L = 2 + g; L <= Lmax; L += GHB) {
-        const T yv = (L == 2) ? O[LO_XI * BLK + e] : O[(LO_YY + L - 3) * BLK + e];
-        v = fma(wIn[L] * tmo, yv, v);
+      // unrolled with the trip count as a predicate: the loads issue together
+#pragma unroll
+      for (int i = 0; i < (MAXLOOP - 1 + GHB - 1) / GHB; i++) {
+        const int L = 2 + g + i * GHB;
+        if (L <= Lmax) {
+          const T yv = (L == 2) ? O[LO_XI * BLK + e] : O[(LO_YY + L - 3) * BLK + e];
+          v = fma(wIn[L] * tmo, yv, v);
+        }
       }
-      for (int j = g; j < NLO_BU; j += GHB) v += O[(LO_BU + j) * BLK + e];
+#pragma unroll
+      for (int i = 0; i < (NLO_BU + GHB - 1) / GHB; i++) {
+        const int j = g + i * GHB;
+        if (j < NLO_BU) v += O[(LO_BU + j) * BLK + e];
+      }
       if (g == 0) v = fma(sHL * clamp_p2<T>(-Ed) * tmo, O[LO_CH * BLK + e], v);
     }
 #pragma unroll

@@ -779,7 +779,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   T *S = (T *)smem_raw;                // [SI_N][36] staged inputs
   T *O = S + (size_t)SI_N * BLK;       // [LO_N][36] phase A results
   __shared__ int sEd;
-  __shared__ double smax[NTT / 32];
+  __shared__ T smax[NTT / 32];  // largest magnitude per warp (table precision suffices for ilogb)
   __shared__ int sE[96], sE0[4], sBx[3][NS], sBy[3][NS];
   __shared__ T sEn[EN_N], sHL, wIn[MAXLOOP + 1];
   __shared__ __align__(8) unsigned long long sbar;
@@ -879,7 +879,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   const T *Tx = S + SI_TX * BLK, *Ty1 = S + SI_TY1 * BLK;
   const T *Xl = S + SI_XX * BLK, *Xr = S + SI_XY1 * BLK;
   const int Lmax = min(MAXLOOP, d - 4);
-  double lmax = 0.0;
+  T lmax = 0;
   // interior-loop weights e^{-I(L)} 2^{E[d-L+2]-E[d]} for the HB sum of phase B
   if (t >= 2 && t <= MAXLOOP) wIn[t] = en[EN_IN + t] * clamp_p2<T>(EAS(d - t + 2) - Ed);
 
@@ -1040,7 +1040,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
       }
     }
     st_row(O + (size_t)oslot * BLK + a * NS, r);
-    if (scaled) lmax = fmax(lmax, (double)row_absmax(r));
+    if (scaled) lmax = fmax(lmax, row_absmax(r));
   }
   __syncthreads();
 
@@ -1072,7 +1072,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
     for (int o = 1; o < GHB; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (e < BLK && g == 0) {
       O[LO_HB * BLK + e] = v;
-      lmax = fmax(lmax, (double)fabs(v));
+      lmax = fmax(lmax, fabs(v));
     }
   }
   if (t >= LM::QB0 && t < LM::QB0 + BLK) {
@@ -1092,16 +1092,16 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
       const T mpp = en[EN_EC] * qb + s2v;
       O[LO_QM2PP * BLK + e] = s2v;
       O[LO_QMPP * BLK + e] = mpp;
-      lmax = fmax(lmax, fmax((double)fabs(qb), fmax((double)fabs(mpp), (double)fabs(s2v))));
+      lmax = fmax(lmax, fmax(fabs(qb), fmax(fabs(mpp), fabs(s2v))));
     }
     if (x == 0) {
       T v;
       if (d == 0) {
         v = 0;
-        lmax = fmax(lmax, 1.0);
+        lmax = fmax(lmax, (T)1);
       } else {
         v = qb + S[SI_BIFX * BLK + e] * clamp_p2<T>(EAS(d - 4) - Ed) + O[LO_Q5K * BLK + e];
-        lmax = fmax(lmax, (double)fabs(v));
+        lmax = fmax(lmax, fabs(v));
       }
       O[LO_Q5P * BLK + e] = v;
     }
@@ -1124,7 +1124,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   // ---- diagonal maximum for the next exponent
   if (t == 0) {
     double m = 0;
-    for (int k = 0; k < NTT / 32; k++) m = fmax(m, smax[k]);
+    for (int k = 0; k < NTT / 32; k++) m = fmax(m, (double)smax[k]);
     atomic_max_pos(&p.dmax[d], m);
   }
 }

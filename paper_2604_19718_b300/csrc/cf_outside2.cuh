@@ -1272,7 +1272,7 @@ __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
   const int Mr = p.Mp[q], Mc = p.Mp[q + 1], NE = Mr * Mc;
   const T *en = p.en;
   const T eb = en[EN_EB], sml = en[EN_EA] * en[EN_EC];
-  double acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // T, X_UU, X_UP, X_PU, X_PP
+  T acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};  // T, X_UU, X_UP, X_PU, X_PP (a lane's cells)
   // cells c0+w, c0+w+8, ...: the next cell's blocks are in flight while the
   // current one is summed
   if (c0 + w < c1) tg_issue(p, role, role == 0 ? q : c0 + w, role == 0 ? q + 1 + c0 + w : q + 1, buf, lane);
@@ -1399,16 +1399,16 @@ __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
           xup2 += F * s2<true, false>(q5u, hg, v2, b, Mx);
           xpp2 += F * s2<true, false>(q5p, hg, v2, b, Mx);
         }
-        acc[k][1] += (double)xuu2;
-        acc[k][2] += (double)xup2;
-        acc[k][3] += (double)xpu2;
-        acc[k][4] += (double)xpp2;
+        acc[k][1] += xuu2;
+        acc[k][2] += xup2;
+        acc[k][3] += xpu2;
+        acc[k][4] += xpp2;
       }
-      acc[k][0] += (double)tv;
-      acc[k][1] += (double)xuu;
-      acc[k][2] += (double)xup;
-      acc[k][3] += (double)xpu;
-      acc[k][4] += (double)xpp;
+      acc[k][0] += tv;
+      acc[k][1] += xuu;
+      acc[k][2] += xup;
+      acc[k][3] += xpu;
+      acc[k][4] += xpp;
     }
     __syncwarp();  // the buffer is refilled two cells later
   }
@@ -1419,7 +1419,7 @@ __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
   for (int k = 0; k < 2; k++) {
     const int e = lane + 32 * k;
     if (e < BLK)
-      for (int v = 0; v < 5; v++) R[((size_t)w * BLK + e) * 5 + v] = e < NE ? acc[k][v] : 0.0;
+      for (int v = 0; v < 5; v++) R[((size_t)w * BLK + e) * 5 + v] = e < NE ? (double)acc[k][v] : 0.0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < NE * 5; t += blockDim.x) {

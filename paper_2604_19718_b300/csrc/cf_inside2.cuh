@@ -58,7 +58,7 @@ struct BifBuf {
 constexpr int FARD = 16;   // diagonals per band
 constexpr int FARTX = 16;  // rows per far tile
 constexpr int FARKC = 8;   // split points staged per step
-constexpr int FARKS = 128;  // split points per CTA slice
+constexpr int FARKS = 64;   // split points per CTA slice
 
 __host__ __device__ __forceinline__ int far_c(int d0) { return d0 - FARD - 1; }
 // does band d0 (a multiple of FARD) have far split points?

@@ -13,7 +13,6 @@ constexpr int NS = 6;        // maximum codon states of one residue
 constexpr int BLK = NS * NS; // padded 6x6 block per table entry
 constexpr int MAXLOOP = 30;  // maximum bulge / interior loop size
 constexpr int NYY = 29;      // interior-loop partial sums, total loop size L = 2..30
-constexpr int WPB = 4;       // warps (cells) per block in the wavefront kernels
 constexpr int YRING = 8;     // diagonals of interior-loop adjoints kept in flight
 
 // typed transition variants, index (type at p) * 2 + (type at p+1), U = 0, P = 1

@@ -1,20 +1,21 @@
-// cf_outside2.cuh -- outside pass (hand-written adjoint of the inside pass) as
-// two kernels per anti-diagonal d, run as a CUDA graph from d = n-1 down to 0:
+// cf_outside2.cuh -- outside pass (hand-written adjoint of the inside pass)
+// as a CUDA graph from d = n-1 down to 0.  Per diagonal d:
+//   k_out_light<T>(d)  every reverse statement that diagonals d-1..d-3 read,
+//                      one CTA per cell, inputs staged into shared memory;
+//   k_out_off<T>(d)    after the light kernel of d+4: the near bifurcation
+//                      gathers of d
+//                        hG[x][y]  += sum_{y'} hQM2pp[x][y'] (ec QB[y][y'])^T   (row gather)
+//                        hQB[x][y] += sum_{x'} (ec G[x'][x])^T hQM2pp[x'][y]    (column gather)
+//                        hGx[d]     = sum_{y'} hQ5P[y'] QB[d][y']^T             (exterior)
+//                      and the side work (scatters) of diagonal d+4.
+// Per band of OFD target diagonals (binary32): k_out_far<ROW> sums the far
+// gather terms.  After the chain: k_out_tg (transfer gradients), then the
+// marginals of cf_outside.cuh.
 //
-//   k_out_bif<T>(d)   the transposed bifurcation gathers of diagonal d, in chunks
-//                     of 32 terms (one warp per chunk):
-//                       hG[x][y]  += sum_{y'} hQM2pp[x][y'] (ec QB[y][y'])^T    (row gather)
-//                       hQB[x][y] += sum_{x'} (ec G[x'][x])^T hQM2pp[x'][y]     (column gather)
-//                       hGx[d]     = sum_{y'} hQ5P[y'] QB[d][y']^T              (exterior)
-//                     Its inputs lie on diagonals >= d+4, so it runs while
-//                     d+3..d+1 are being finished.
-//   k_out_light<T>(d) every other reverse statement of diagonal d, one 128-thread
-//                     block per cell, inputs staged into shared memory.
-//
-// Adjoint scaling and the statements themselves are those of cf_outside.cuh:
-// hA = (dZ/dA_true) 2^{E[d]} / Z, every reverse statement reuses its forward
-// statement's power-of-two factor, gradients of the transfers accumulate in
-// binary64 at residue-boundary positions.
+// Adjoint scaling and the statements themselves are those described in
+// cf_outside.cuh: hA = (dZ/dA_true) 2^{E[d]} / Z, every reverse statement
+// reuses its forward statement's power-of-two factor, gradients of the
+// transfers accumulate in binary64 at residue-boundary positions.
 #pragma once
 #include "cf_common.cuh"
 #include "cf_inside.cuh"
@@ -48,7 +49,7 @@ struct OutBuf {
 // whole band earlier, they are summed for the band at once by k_out_far (a
 // tiled product in which every loaded block serves up to 16 targets) while the
 // reverse light chain is still OFD diagonals away; the near terms (adjoint
-// diagonals a+4 .. c-1, at most 2 OFD + 1 per gather) stay in k_out_bif.
+// diagonals a+4 .. c-1, at most 2 OFD + 1 per gather) stay in k_out_off.
 // Far blocks are rescaled to a linear exponent with the chord s, e0 of E over
 // diagonals 5 .. n-1: forward blocks by 2^{E[D] - s D - e0}, adjoint blocks by
 // 2^{s D + e0 - E[D]}; every far term of a target on diagonal a is then
@@ -274,15 +275,6 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
   }
 }
 
-// Grid-stride over the cells and the exterior (see k_in_bif).
-template <typename T>
-__global__ void __launch_bounds__(256) k_out_bif(DP<T> p, OutBuf<T> ob, int d) {
-  __shared__ T red[16][BLK];
-  for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
-    out_bif_cell(p, ob, d, cb, red);
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------- K0': far band
 // Grid (tiles, slices), 256 threads: thread (tx, tj) owns the target
@@ -502,7 +494,7 @@ __device__ __forceinline__ const T *out_slot_src(const DP<T> &p, int s, int x, i
   return up5 ? p.hHB + cidx(n, x - L, y) * BLK : nullptr;
 }
 
-// gather results of k_out_bif and the exterior inputs of the cell (0, d)
+// gather results of k_out_off and the exterior inputs of the cell (0, d)
 template <typename T>
 __device__ __forceinline__ const T *out_slot_src2(const DP<T> &p, const OutBuf<T> &ob, int s, int x, int d) {
   const int n = p.n, slot = d % BIFRING;
@@ -833,7 +825,8 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
 
   // ---------------- F: interior scatters into hXI that this and the next three
   // diagonals read (L = 2: the cell's own XI; L = 3..5); every other scatter
-  // and the transfer gradients run in k_out_side, off the critical path
+  // runs in the side work of k_out_off and the transfer gradients in k_out_tg,
+  // off the critical path
   if (d >= 6) {
     const int Lmax = min(MAXLOOP, d - 4);
     for (int it = t; it < (1 + NCHL_LIGHT) * BLK; it += NTT) {
@@ -865,14 +858,15 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
 }
 
 // ---------------------------------------------------------------- K3'
-// k_out_side(d): the parts of the adjoint of diagonal d that no diagonal
-// d-1..d-3 reads, run beside the light chain: the bulge scatters into the
-// chain adjoints of diagonals L <= d-4, the interior scatters into hXI of
-// diagonals <= d-4 and into the chain adjoints of diagonals <= 28, and the
-// gradients of the boundary transfers T_p, X_p (read only by the final
-// marginals).  It starts after the light kernel of d and must end before the
-// light kernel of d-4, the first reader of what it writes; the interior-loop
-// adjoint ring keeps YRING >= 5 diagonals so that its slot of d is intact.
+// Side work of diagonal d (side_cell, in the k_out_off launch of d-4): the
+// parts of the adjoint of diagonal d that no diagonal d-1..d-3 reads, run
+// beside the light chain: the bulge scatters into the chain adjoints of
+// diagonals L <= d-4, the interior scatters into hXI of diagonals <= d-4 and
+// into the chain adjoints of diagonals <= 28, and the ring term of the
+// transfer gradients.  It starts after the light kernel of d and must end
+// before the light kernel of d-4, the first reader of what it writes; the
+// interior-loop adjoint ring keeps YRING >= 5 diagonals so that its slot of d
+// is intact.
 enum : int {
   SS_TX = 0, SS_TY1 = 1, SS_XX = 2, SS_XY1 = 6, SS_QBI = 10, SS_HBI = 11, SS_CHN = 12, SS_Q2I = 13,
   SS_ML = 17, SS_MR = 21, SS_Q5UM = 25, SS_Q5PM = 26,
@@ -881,7 +875,7 @@ enum : int {
   SS_HY = 39, SS_YYP = 68, SS_XIL = 96, SS_CHL = 124, SS_BQ3 = 152, SS_BQ5 = 182,
   SS_N = 212
 };
-static_assert(YRING >= 5, "k_out_side reads the ring slot of its diagonal until the light kernel of d-4");
+static_assert(YRING >= 5, "the side work reads the ring slot of its diagonal until the light kernel of d-4");
 constexpr int NT3 = 256;
 
 template <typename T>

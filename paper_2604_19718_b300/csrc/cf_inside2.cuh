@@ -141,6 +141,26 @@ __device__ __forceinline__ void in_bif_cell(const DP<T> &p, const BifBuf<T> &bb,
   }
 }
 
+// one padded row (6 values) through the read-only path, 8 or 16 bytes at a time
+__device__ __forceinline__ void ldg_row6(float (&r)[NS], const float *src) {
+  const float2 *s = reinterpret_cast<const float2 *>(src);
+#pragma unroll
+  for (int i = 0; i < NS / 2; i++) {
+    const float2 v = __ldg(s + i);
+    r[2 * i] = v.x;
+    r[2 * i + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void ldg_row6(double (&r)[NS], const double *src) {
+  const double2 *s = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+  for (int i = 0; i < NS / 2; i++) {
+    const double2 v = __ldg(s + i);
+    r[2 * i] = v.x;
+    r[2 * i + 1] = v.y;
+  }
+}
+
 // acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f op(A) op(B) over the live
 // rows (Ma), summation index (Ms) and columns (Mb); TA / TB read A / B
 // transposed.  A lane holds three rows of op(A) and one row of B at a time.
@@ -150,17 +170,23 @@ __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, 
   constexpr int HR = NS / 2;
   T av[HR * NS];
 #pragma unroll
-  for (int r = 0; r < HR; r++)
+  for (int r = 0; r < HR; r++) {
+    T row[NS];
+    if (TA) {
 #pragma unroll
-    for (int s = 0; s < NS; s++)
-      av[r * NS + s] = __ldg(TA ? A + s * NS + half * HR + r : A + (half * HR + r) * NS + s) * f;
+      for (int s = 0; s < NS; s++) row[s] = __ldg(A + s * NS + half * HR + r);
+    } else {
+      ldg_row6(row, A + (half * HR + r) * NS);
+    }
+#pragma unroll
+    for (int s = 0; s < NS; s++) av[r * NS + s] = row[s] * f;
+  }
   if (!TB) {
 #pragma unroll
     for (int s = 0; s < NS; s++) {
       if (s < Ms) {
         T bv[NS];
-#pragma unroll
-        for (int b = 0; b < NS; b++) bv[b] = __ldg(B + s * NS + b);
+        ldg_row6(bv, B + s * NS);
 #pragma unroll
         for (int r = 0; r < HR; r++)
           if (half * HR + r < Ma) {
@@ -175,8 +201,7 @@ __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, 
     for (int b = 0; b < NS; b++) {
       if (b < Mb) {
         T bv[NS];
-#pragma unroll
-        for (int s = 0; s < NS; s++) bv[s] = __ldg(B + b * NS + s);
+        ldg_row6(bv, B + b * NS);
 #pragma unroll
         for (int r = 0; r < HR; r++)
           if (half * HR + r < Ma) {

@@ -411,7 +411,7 @@ def main():
 
     def step(prec):
         lz = cf.cf_inside(f.prob, prec)
-        cf.cf_outside(f.prob, Pd, cmd, pgd)
+        cf.cf_outside(f.prob, Pd, cmd, pair_grad=pgd)
         return lz
 
     if args.profile:
@@ -483,7 +483,7 @@ def main():
     for _ in range(ke):
         cf.cf_set_protein(f.prob, letters, lw, pb)
         cf.cf_inside(f.prob, cf.CF_FP32_SCALED)
-        cf.cf_outside(f.prob, Ph, cmh, pgh)
+        cf.cf_outside(f.prob, Ph, cmh, pair_grad=pgh)
     e2e_s = (time.perf_counter() - t) / ke
     h2d = len(letters) + (0 if lw is None else lw.nbytes) + (0 if pb is None else pb.nbytes)
     d2h = Ph.nbytes + cmh.nbytes + pgh.nbytes

@@ -128,12 +128,18 @@ cf_status cf_inside(cf_problem *prob, cf_precision precision, double *logZ);
  *               pair-probability), [i][i] = P(i unpaired).
  *   codon_marg: m*6 doubles; [r][s] = P(residue r uses its codon slot s)
  *               = d log Z / d codon_logw[r][s] (Eq. marginal-codon).
+ *   base_marg:  n*4 doubles; [i][b] = P(nucleotide i is base b), bases in the
+ *               order A, C, G, U: the sum of the codon marginals of residue
+ *               i/3 over its codons with base b at position i%3 (Eq.
+ *               marginal-base).
  *   pair_grad:  61*61 doubles; d log Z / d pair_bonus[c][c'] = expected count
  *               of the adjacent codon pair (c, c') summed over residues.
+ * Each output pointer may be host or device memory (detected per pointer);
+ * the library writes it and keeps no reference.
  * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ECUDA, CF_ETIMEOUT (a bounded
  * device wait for staged inputs gave up; the outputs are then not valid).
  */
-cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, double *pair_grad);
+cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, double *base_marg, double *pair_grad);
 
 /*
  * Draw `nsamples` exact i.i.d. samples of (codon sequence, structure) from

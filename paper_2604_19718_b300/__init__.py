@@ -39,7 +39,7 @@ def _load() -> ctypes.CDLL:
     lib.cf_set_protein.argtypes = [vp, ctypes.c_char_p, ctypes.c_int, dp, dp]
     lib.cf_set_weights.argtypes = [vp, dp, dp]
     lib.cf_inside.argtypes = [vp, ctypes.c_int, dp]
-    lib.cf_outside.argtypes = [vp, fp, vp, vp]
+    lib.cf_outside.argtypes = [vp, fp, vp, vp, vp]
     lib.cf_sample.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
     lib.cf_last_error.argtypes = [vp]
     lib.cf_last_error.restype = ctypes.c_char_p
@@ -132,8 +132,8 @@ def cf_inside(prob, precision: int = CF_FP32_SCALED) -> float:
     return out.value
 
 
-def cf_outside(prob, pair_prob=None, codon_marg=None, pair_grad=None) -> None:
-    _check(lib.cf_outside(prob, _ptr(pair_prob), _ptr(codon_marg), _ptr(pair_grad)), prob)
+def cf_outside(prob, pair_prob=None, codon_marg=None, base_marg=None, pair_grad=None) -> None:
+    _check(lib.cf_outside(prob, _ptr(pair_prob), _ptr(codon_marg), _ptr(base_marg), _ptr(pair_grad)), prob)
 
 
 def cf_sample(prob, nsamples: int, seed: int, codons, partner) -> None:
@@ -289,14 +289,18 @@ class CodonFold:
     def inside(self, precision: int = CF_FP32_SCALED) -> float:
         return cf_inside(self.prob, precision)
 
-    def outside(self, pair_prob=True, codon=True, pair_grad=True):
-        """Host numpy outputs (pass arrays/tensors to fill them in place instead)."""
+    def outside(self, pair_prob=True, codon=True, pair_grad=True, base=None):
+        """Host numpy outputs (pass arrays/tensors to fill them in place
+        instead; False skips an output).  Returns (P, codon marginals, pair
+        gradient), and the per-base marginals (n x 4) as a fourth item when
+        ``base`` is given (True or an array to fill)."""
         P = np.zeros((self.n, self.n), dtype=np.float32) if pair_prob is True else pair_prob
         cm = np.zeros((self.m, 6)) if codon is True else codon
         pg = np.zeros((61, 61)) if pair_grad is True else pair_grad
+        bm = np.zeros((self.n, 4)) if base is True else base
         cf_outside(self.prob, None if P is False else P, None if cm is False else cm,
-                   None if pg is False else pg)
-        return P, cm, pg
+                   None if bm is None or bm is False else bm, None if pg is False else pg)
+        return (P, cm, pg) if base is None else (P, cm, pg, bm)
 
     def sample(self, nsamples: int, seed: int):
         cod = np.zeros((nsamples, self.m), dtype=np.int32)

@@ -1150,7 +1150,7 @@ cf_status cf_inside(cf_problem *p, cf_precision prec, double *logZ) {
   return CF_OK;
 }
 
-cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double *pair_grad) {
+cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double *base_marg, double *pair_grad) {
   if (!p) return fail(p, CF_EINVAL, "cf_outside: NULL problem");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_outside: run cf_inside first");
   CF_CUDA(p, cudaSetDevice(p->device));
@@ -1183,6 +1183,15 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
   }
   if (codon_marg) {
     s = copy_out(p, codon_marg, cm.data(), sizeof(double) * cm.size(), false);
+    if (s != CF_OK) return s;
+  }
+  if (base_marg) {
+    // the state of position i is the codon choice of its residue: base of
+    // state a at i times the residue's codon marginal
+    std::vector<double> bm((size_t)n * 4, 0.0);
+    for (int i = 0; i < n; i++)
+      for (int a = 0; a < p->M[i]; a++) bm[(size_t)i * 4 + p->base[(size_t)i * NS + a]] += cm[(size_t)(i / 3) * 6 + a];
+    s = copy_out(p, base_marg, bm.data(), sizeof(double) * bm.size(), false);
     if (s != CF_OK) return s;
   }
   if (pair_grad) {

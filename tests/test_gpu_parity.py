@@ -136,13 +136,15 @@ def test_repeatable_and_device_outputs():
     n = f.n
     Pd = torch.zeros((n, n), dtype=torch.float32, device="cuda")
     cmd = torch.zeros((len(res), 6), dtype=torch.float64, device="cuda")
-    cf.cf_outside(f.prob, Pd, cmd, None)
+    bmd = torch.zeros((n, 4), dtype=torch.float64, device="cuda")
+    cf.cf_outside(f.prob, Pd, cmd, base_marg=bmd)
     torch.cuda.synchronize()
-    P, cm, _ = f.outside()
+    P, cm, _, bm = f.outside(base=True)
     # binary32: the adjoint scatters and the transfer-gradient sums use atomics,
     # whose order varies between runs (measured spread 1e-9 at this size)
     assert np.array_equal(Pd.cpu().numpy(), P) or np.abs(Pd.cpu().numpy() - P).max() < 1e-6
     assert np.abs(cmd.cpu().numpy() - cm).max() < 1e-7
+    assert np.abs(bmd.cpu().numpy() - bm).max() < 1e-7
     f.close()
 
 
@@ -176,3 +178,25 @@ def test_same_length_protein_reuses_tables(prec):
     tl, tm, tp = TOL[prec]
     assert abs(lz - o["logZ"]) <= tl * max(1.0, abs(o["logZ"]))
     assert np.abs(cm - o["codon"]).max() <= tm and np.abs(P - o["P"]).max() <= tp
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_base_marginals_vs_oracle(prec):
+    """Per-base marginals p_i(b) (Eq. marginal-base) against the oracle's, and
+    each position's four sum to one."""
+    cf = _cf()
+    res, wts = CASES["p47_weighted"]
+    m = len(res)
+    rng = np.random.default_rng(m)
+    lw = rng.normal(0, 0.5, (m, 6))
+    pb = rng.normal(0, 0.2, (61, 61))
+    o = oracle.outside(P0, res, lw, pb)
+    want = oracle.base_marginals(res, o["codon"])
+    f = cf.CodonFold(P0)
+    f.set_protein(res, lw, pb)
+    f.inside(prec)
+    _, _, _, bm = f.outside(base=True)
+    f.close()
+    assert bm.shape == (3 * m, 4)
+    assert np.abs(bm - want).max() <= TOL[prec][1]
+    assert np.abs(bm.sum(axis=1) - 1.0).max() <= TOL[prec][1]

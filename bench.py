@@ -40,6 +40,13 @@ def codon_counts(res):
     return np.repeat(np.array([per_aa[int(r)] for r in res], dtype=np.int64), 3)
 
 
+def state_cells(res):
+    """sum over cells (i <= j) of M_i M_j: the codon-state entries of one table."""
+    M = codon_counts(res).astype(np.float64)
+    tot = np.sum(M) ** 2
+    return float((tot + np.sum(M * M)) / 2)
+
+
 def algorithmic_flops(res):
     """Analytic count of the inside and outside floating-point operations of
     the recursions in their documented contraction order (2 per FMA), from
@@ -519,6 +526,7 @@ def main():
                    "cells_per_step": cells, "l2": "working set ~3 GB > 126 MB L2; no flush needed",
                    "parallelism": f"replicas x{ws}"},
         "proteins_per_s": ws * args.steps / (ms * 1e-3),
+        "state_cells_per_s": ws * args.steps * state_cells(res) / (ms * 1e-3),
         "fp64_form": {"value": ws * cells / (ms64 * 1e-3), "unit": "cells/s", "ms_per_step": ms64,
                       "speedup_fp32_over_fp64": ms64 / (ms / args.steps)},
         "accuracy": acc,

@@ -356,6 +356,45 @@ def bench_small_batch(nstreams=32, count=4096):
     return out
 
 
+def bench_concurrent(nprob=4, rounds=5):
+    """Proteins/s of the 900-nt workload with nprob independent problems at
+    once, each on its own stream and worker thread (one protein is a
+    latency-bound wavefront that leaves most SMs idle on its long diagonals)."""
+    import torch
+
+    import paper_2604_19718_b300 as cf
+    res, _, _ = synth.workload(WORKLOAD)
+    params = synth.nn_params(0)
+    streams = [torch.cuda.Stream() for _ in range(nprob)]
+    folds = [cf.CodonFold(params, stream=s.cuda_stream) for s in streams]
+    n = 3 * len(res)
+    lz = np.zeros(nprob)
+    for k, f in enumerate(folds):  # warm-up: tables and graphs of every problem
+        f.set_protein(res)
+        f.inside(cf.CF_FP32_SCALED)
+        f.outside(True, True, False)
+
+    def work(k):
+        f = folds[k]
+        for _ in range(rounds):
+            lz[k] = f.inside(cf.CF_FP32_SCALED)
+            f.outside(True, True, False)
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(nprob)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    for f in folds:
+        f.close()
+    return {"problems": nprob, "rounds": rounds, "nt": n, "proteins_per_s": nprob * rounds / dt,
+            "cells_per_s": nprob * rounds * n * (n + 1) / 2 / dt, "logZ_equal": bool(np.all(lz == lz[0]))}
+
+
 def bench_large(stream, nsamples=10_000):
     """The 1000-aa / 3000-nt soft-weighted protein in binary32."""
     import paper_2604_19718_b300 as cf
@@ -504,6 +543,7 @@ def main():
         forms["adjoint"] = bench_adjoint(stream.cuda_stream)
         forms["large"] = bench_large(stream.cuda_stream)
         forms["small_batch"] = bench_small_batch()
+        forms["concurrent"] = bench_concurrent()
 
     if rank != 0:
         return

@@ -359,20 +359,6 @@ __global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
   return (uint32_t)__cvta_generic_to_shared(ptr);
 }
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// copy one padded block (36 values) global -> shared with 16-byte async copies
-template <typename T>
-__device__ __forceinline__ void stage_block(T *dst, const T *src) {
-  constexpr int CH = BLK * sizeof(T) / 16;
-#pragma unroll
-  for (int q = 0; q < CH; q++) cp_async16((char *)dst + 16 * q, (const char *)src + 16 * q);
-}
 
 // slot layout of the light kernel's staged inputs (blocks of 36 values)
 enum : int {

@@ -608,7 +608,19 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
   }
   OSlot<T> e{nullptr, 0, -1};
   if (t < SO_N) e = ob.otab[(size_t)d * SO_N + t];
-  if (e.src && x >= e.xlo && x <= e.xhi) stage_block(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t));
+  // staging: one TMA bulk copy per input block, completing on a barrier at
+  // which every thread arrives once with its copy's bytes
+  __shared__ __align__(8) unsigned long long obar;
+  if (t == 0) mbar_init(&obar, NTT);
+  __syncthreads();
+  {
+    unsigned bytes = 0;
+    if (e.src && x >= e.xlo && x <= e.xhi) {
+      bytes = BLK * (unsigned)sizeof(T);
+      bulk_g2s(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t), bytes, &obar);
+    }
+    mbar_arrive_expect(&obar, bytes);
+  }
   if (t < 96) sE[t] = cE;
   else if (t < 96 + 6 * NS) {
     const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
@@ -626,8 +638,7 @@ __global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d)
     wBuU[t] = cwU;
     wIn[t] = cwI;
   }
-  cp_async_wait_all();
-  __syncthreads();
+  if (!__syncthreads_and(mbar_wait(&obar, 0, p.err))) return;
   const T *en = sEn;
   const int Ed = sE[47];  // E[d], staged with its neighbours
   const int Mx = MP(x), My = MP(y), MM = Mx * My;

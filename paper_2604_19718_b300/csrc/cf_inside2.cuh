@@ -804,9 +804,9 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   // d-47..d-1, bases of x-1..x+1 and y-1..y+1, energy factors, and the
   // largest mantissa and exponent of diagonal d-1 (last thread)
   static_assert(NTT > EN_N && NTT > 100 + 6 * NS && NTT >= SI_N, "one context value and slot per thread");
-  // the barrier is initialised first: its release fence would otherwise wait
-  // for the context loads below
-  if (t == 0) mbar_init(&sbar, 1);
+  // the barrier (one arrival per thread) is initialised first: its release
+  // fence would otherwise wait for the context loads below
+  if (t == 0) mbar_init(&sbar, NTT);
   int cE = 0, cB = 0;
   T cEn = 0;
   unsigned long long cMax = 0;
@@ -832,9 +832,10 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   __syncthreads();
   // Staging: one TMA bulk copy per input block (the interior partial sums
   // YY_{L-1}[x+1][y], L = 3..Lmax, are contiguous and go as one copy); slots
-  // this cell does not use are zero-filled.  Each issuing thread adds its
-  // bytes to the barrier's transaction count before its copy; thread 0 arrives
-  // once every thread has done so.
+  // this cell does not use are zero-filled.  Every thread arrives once at the
+  // barrier with the bytes of its copy (copies that complete earlier leave
+  // the transaction count transiently negative, which the barrier allows).
+  unsigned nbytes = 0;
   {
     const int LmaxS = min(MAXLOOP, d - 4);
     const int s = t;
@@ -844,21 +845,20 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
       const T *src = src0 == nullptr ? nullptr : (st ? src0 + (size_t)x * st : (x == 0 ? src0 : nullptr));
       if (src) {
         const unsigned bytes = (s == SI_YYP ? (unsigned)(LmaxS - 2) : 1u) * BLK * (unsigned)sizeof(T);
-        mbar_expect(&sbar, bytes);
         bulk_g2s(dst, src, bytes, &sbar);
+        nbytes = bytes;
       } else {
 #pragma unroll
         for (int q = 0; q < BLK; q++) dst[q] = (T)0;
       }
     }
   }
+  mbar_arrive_expect(&sbar, nbytes);
   // destinations of the results (copied out at the end of the cell)
   if (t < NCOPY) {
     const int st = light_dst_stride(t);
     sDst[t] = dst0 == nullptr ? nullptr : (st ? dst0 + (size_t)x * st : (x == 0 ? dst0 : nullptr));
   }
-  __syncthreads();
-  if (t == 0) mbar_arrive(&sbar);
   // the context reaches shared memory while the copies are in flight
   if (t < EN_N) sEn[t] = cEn;
   if (t < 96) {

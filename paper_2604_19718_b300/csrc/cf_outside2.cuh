@@ -1016,6 +1016,8 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
   // transfer gradient T_x)
   const bool ytg = bx && d >= 6;
   const int Lmax = min(MAXLOOP, d - 4);
+  // every thread arrives once at the barrier with the bytes of its copy
+  unsigned nbytes = 0;
   {
     const int s = t;
     const bool skip = src0 == nullptr || (!ytg && s >= SS_YYP && s < SS_XIL) ||
@@ -1026,13 +1028,11 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
       unsigned nb = 1;
       if (s == SS_HY) nb = (unsigned)(Lmax - 1);
       else if (s == SS_YYP) nb = (unsigned)(Lmax - 2);
-      const unsigned bytes = nb * BLK * (unsigned)sizeof(T);
-      mbar_expect(sbar, bytes);
-      bulk_g2s(S + (size_t)s * BLK, src, bytes, sbar);
+      nbytes = nb * BLK * (unsigned)sizeof(T);
+      bulk_g2s(S + (size_t)s * BLK, src, nbytes, sbar);
     }
   }
-  __syncthreads();
-  if (t == 0) mbar_arrive(sbar);
+  mbar_arrive_expect(sbar, nbytes);
   if (t < 96) sE[t] = cE;
   if (t < 72) {
     sMx[t] = cMx;
@@ -1147,7 +1147,7 @@ __global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T>
       out_bif_group(p, ob, d, blockIdx.x * 4, red);
     return;
   }
-  if (threadIdx.x == 0) mbar_init(&sbar, 1);
+  if (threadIdx.x == 0) mbar_init(&sbar, NT3);  // one arrival per thread (side work)
   __syncthreads();
   side_cell(p, ob, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u);
 }

@@ -139,30 +139,34 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def dist_setup():
+def dist_setup(backend="nccl"):
+    """Rank layout from the torchrun environment; a process group for N > 1
+    (NCCL on the GPU machine; the tests use gloo on CPU)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        dist.init_process_group(backend, init_method="env://")
     return ws, rank, local
 
 
-def barrier(ws):
+def barrier(ws, cuda=True):
     if ws > 1:
         import torch
         import torch.distributed as dist
         dist.barrier()
-        torch.cuda.synchronize()
+        if cuda:
+            torch.cuda.synchronize()
 
 
-def max_over_ranks(v, ws):
+def max_over_ranks(v, ws, device="cuda"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

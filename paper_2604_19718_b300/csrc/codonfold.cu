@@ -104,6 +104,7 @@ struct cf_model {
 template <typename T>
 struct PrecTables {
   bool inside_alloc = false, outside_alloc = false;
+  bool stale = false;  // hold a previous protein's values: cleared before the next inside pass
   DP<T> dp{};
   BifBuf<T> bb{};
   cudaGraphExec_t gin = nullptr;  // inside pass as one graph
@@ -646,6 +647,9 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
 }
 
 template <typename T>
+cf_status clear_tables(cf_problem *p, PrecTables<T> &t);
+
+template <typename T>
 cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   cf_status s = alloc_inside(p, t);
   if (s != CF_OK) return s;
@@ -653,6 +657,11 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   cudaStream_t st = p->stream;
   s = build_inside_graph(p, t);
   if (s != CF_OK) return s;
+  if (t.stale) {  // a new protein of the same length: its padding must be zero
+    s = clear_tables(p, t);
+    if (s != CF_OK) return s;
+    t.stale = false;
+  }
   CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   CF_CUDA(p, cudaGraphLaunch(t.gin, st));
@@ -1112,9 +1121,10 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     CF_CUDA(p, cudaMemcpyAsync(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   if (reuse) {
-    cf_status s = clear_tables(p, p->f32);
-    if (s == CF_OK) s = clear_tables(p, p->f64);
-    if (s == CF_OK) s = upload_transfers(p, p->f32);
+    // the tables of each precision are cleared by its next inside pass
+    p->f32.stale = p->f32.inside_alloc;
+    p->f64.stale = p->f64.inside_alloc;
+    cf_status s = upload_transfers(p, p->f32);
     if (s == CF_OK) s = upload_transfers(p, p->f64);
     if (s != CF_OK) return s;
   }

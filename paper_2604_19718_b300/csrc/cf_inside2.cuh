@@ -1,18 +1,23 @@
-// cf_inside2.cuh -- inside pass as two kernels per anti-diagonal d, run as a
-// CUDA graph (see codonfold.cu):
+// cf_inside2.cuh -- inside pass as a CUDA graph over the anti-diagonals d
+// (built in codonfold.cu).  Per diagonal d:
 //
-//   k_in_bif<T>(d)   the multiloop/exterior bifurcation sums of diagonal d,
-//                    sum_k G[x][k] QB[k][y] and sum_k Gx[k] QB[k][d], split in
-//                    chunks of 32 split points (one warp per chunk, lanes over k).
-//                    Its inputs lie on diagonals <= d-4, so the graph lets it run
-//                    while diagonals d-3..d-1 are still being filled.  Chunk
-//                    partials are relative to 2^{E[d-4]}.
-//   k_in_light<T>(d) everything else of diagonal d, one 128-thread block per
-//                    cell: the ~230 input blocks are staged into shared memory
-//                    with asynchronous 16-byte copies (one memory round trip),
-//                    then the chain, XI, the 29 interior partial sums, bulges,
-//                    hairpin, QB, multiloop tables and the exterior prefix are
-//                    computed from shared memory.
+//   k_in_light<T>(d)    every term that reads diagonals d-1..d-3, one 256-thread
+//                       CTA per cell: the ~240 input blocks arrive in shared
+//                       memory by TMA bulk copies (sources from a per-diagonal
+//                       table), then two phases of row products compute the
+//                       chain, XI, the 29 interior partial sums, bulges,
+//                       hairpin, QB, the multiloop tables and the exterior
+//                       prefix; results go out with 16-byte stores.
+//   k_in_bif_grp<T>(d)  the multiloop/exterior bifurcation sums of diagonal d,
+//   (binary32)          sum_k G[x][k] QB[k][y] and sum_k Gx[k] QB[k][d], over
+//                       the split points not in a far band, four cells per CTA;
+//                       its inputs lie on diagonals <= d-4, so it runs while
+//                       diagonals d-3..d-1 are being filled; sums are relative
+//                       to 2^{E[d-4]}.
+//   k_in_bif<T>(d)      the same without far bands (binary64, short proteins),
+//                       one CTA per cell.
+// Per band of FARD diagonals (binary32): k_in_far sums the far split points
+// of the whole band as tiled products, after the light kernel of d0 - 17.
 //
 // Tables, exponents and recursions are those of cf_inside.cuh.
 #pragma once

@@ -4,8 +4,9 @@
 // Host work is limited to building the per-position tensor-train data of the
 // protein (Eq. pair-tt with soft weights), choosing launch shapes, moving
 // inputs/outputs and turning device reductions into the returned numbers.
-// Every step of the dynamic program runs in the kernels of cf_inside.cuh,
-// cf_outside.cuh and cf_sample.cuh.
+// Every step of the dynamic program runs in the kernels of cf_inside2.cuh
+// (inside), cf_outside2.cuh and cf_outside.cuh (outside and marginals),
+// cf_sample.cuh (sampler) and cf_window.cuh (fixed-sequence windows).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -283,11 +284,11 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   return CF_OK;
 }
 
-// Grid size cap of the kernels that run beside the light chain (bifurcation
-// sums, side work of the adjoint), which loop over their cells grid-stride.
-// A cap of one CTA per SM leaves room for the light CTAs but starves the
-// off-chain kernels of their deadlines (measured: slower at 900 nt), so the
-// graphs use a cap above every diagonal's cell count: one CTA per cell.
+// Grid size cap of the per-cell bifurcation kernels without far bands, which
+// loop over their cells grid-stride.  A cap of one or two CTAs per SM leaves
+// room for the light CTAs but starves the off-chain kernels (measured: slower
+// at 900 nt), so the graphs use a cap above every diagonal's cell count: one
+// CTA per cell.
 int offchain_ctas(const cf_problem *p, int per_sm) {
   int sms = 148;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) cudaGetLastError();
@@ -307,7 +308,10 @@ cudaError_t set_priority(cudaGraphNode_t node, bool high) {
 
 // The inside pass as a CUDA graph: a chain of light kernels, one per
 // anti-diagonal, and the bifurcation kernel of diagonal d hanging off the light
-// kernel of diagonal d-4, so that it runs while d-3..d-1 are being filled.
+// kernel of diagonal d-4, so that it runs while d-3..d-1 are being filled;
+// with far bands (binary32) the far kernel of band d0 (after its factor table)
+// hangs off the light kernel of d0 - 17 and precedes the band's bifurcation
+// kernels.
 template <typename T>
 cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gin) return CF_OK;
@@ -478,8 +482,11 @@ cudaError_t add_memset(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode
 }
 
 // The outside pass as a CUDA graph: a chain of light kernels from d = n-1 down
-// to 0, with the transposed bifurcation kernel of diagonal d hanging off the
-// light kernel of diagonal d+4.
+// to 0; the off-chain launch of diagonal d (its transposed bifurcation gathers
+// and the side work of diagonal d+4) hangs off the light kernel of d+4 and
+// precedes the light kernel of d; the far gathers of a band hang off the light
+// kernel of a_lo + 35; the transfer gradients and the marginals follow the
+// chain.
 template <typename T>
 cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (t.gout) return CF_OK;

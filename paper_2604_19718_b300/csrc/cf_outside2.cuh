@@ -553,9 +553,10 @@ __global__ void k_out_slot_tab(DP<T> p, OutBuf<T> ob) {
 
 // ---------------------------------------------------------------- K2'
 // Thread mapping as in k_in_light: compact entries e = a*M_b + b, work lists
-// split into NT/(M_x*M_y) groups.
+// split into NT/(M_x*M_y) groups.  Registers bounded so that six 256-thread
+// CTAs fit an SM (their shared memory allows six as well).
 template <typename T, int NTT>
-__global__ void __launch_bounds__(NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
+__global__ void __launch_bounds__(NTT, 1536 / NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *S = (T *)smem_raw;            // [SO_N][36]
   T *HY = S + (size_t)SO_N * BLK;  // [29][36] interior partial-sum adjoints

@@ -55,6 +55,67 @@ __global__ void k_marginals(DP<T> p, double *trans, double *p0) {
     }
 }
 
+// Codon marginal of state a at residue r (Eq. marginal-codon): residue 0 from
+// p0, every later residue as the summed gradient of the transfers entering it
+// (each transfer T_q, q = 3r - 1, carries the residue's weight exactly once).
+__device__ __forceinline__ double codon_marg_of(const double *trans, const double *p0, int r, int a, int Mprev) {
+  if (r == 0) return p0[a];
+  const double *t = trans + (size_t)(r - 1) * BLK + a;
+  double s = 0;
+  for (int b = 0; b < Mprev; b++) s += t[b * NS];
+  return s;
+}
+
+// Outputs of the outside pass from the transfer gradients, each summed in a
+// fixed order (results independent of scheduling).  The first
+// ceil((6m + n) / blockDim) blocks take one thread per entry of
+//   cm[r][a]   codon marginals (m x 6, unused slots 0) and
+//   bm[i][b]   base marginals (n x 4), Eq. marginal-base: the state of
+//              position i is its residue's codon, so p_i(b) sums the codon
+//              marginals of the residue's codons with base b at i;
+// the remaining blocks one warp per entry of
+//   pg[x][y]   d log Z / d pb[x][y] over sense codon ids (61 x 61): the
+//              transfer gradients of every residue boundary whose two states
+//              are codons x and y, lanes striding over the boundaries.
+template <typename T>
+__global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, const int *cid, double *cm,
+                            double *bm, double *pg) {
+  const int n = p.n, m = p.m;
+  const int nb1 = (6 * m + n + blockDim.x - 1) / blockDim.x;
+  if ((int)blockIdx.x < nb1) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m * 6) {
+      const int r = t / 6, a = t % 6;
+      const int q = 3 * r;  // first position of residue r
+      cm[t] = (a < p.Mp[q]) ? codon_marg_of(trans, p0, r, a, r ? p.Mp[q - 1] : 0) : 0.0;
+      return;
+    }
+    const int u = t - m * 6;
+    if (u >= n) return;
+    const int r = u / 3, q = 3 * r;
+    double acc[4] = {0, 0, 0, 0};
+    for (int a = 0; a < p.Mp[u]; a++)
+      acc[p.base[(size_t)u * NS + a]] += codon_marg_of(trans, p0, r, a, r ? p.Mp[q - 1] : 0);
+    for (int b = 0; b < 4; b++) bm[(size_t)u * 4 + b] = acc[b];
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int u = (blockIdx.x - nb1) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (u >= 61 * 61) return;  // whole warps leave together
+  const int x = u / 61, y = u % 61;
+  double s = 0;
+  for (int r = lane; r + 1 < m; r += 32) {
+    const int q = 3 * r + 2;
+    for (int a = 0; a < p.Mp[q]; a++) {
+      if (cid[(size_t)q * NS + a] != x) continue;
+      for (int b = 0; b < p.Mp[q + 1]; b++)
+        if (cid[(size_t)(q + 1) * NS + b] == y) s += trans[(size_t)r * BLK + a * NS + b];
+    }
+  }
+  s = warp_sum(s);
+  if (lane == 0) pg[u] = s;
+}
+
 // Unpaired probability of every base: 1 - sum of its pair probabilities.
 __global__ void k_unpaired(float *P, int n) {
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);

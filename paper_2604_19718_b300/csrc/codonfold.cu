@@ -129,6 +129,8 @@ struct cf_problem {
   int *dM = nullptr, *dbase = nullptr, *dbnd = nullptr, *dE = nullptr, *derr = nullptr;
   unsigned long long *ddmax = nullptr;
   double *du0 = nullptr, *dZm = nullptr, *dtrans = nullptr, *dp0 = nullptr;
+  double *dcm = nullptr, *dbm = nullptr, *dpg = nullptr;  // codon, base marginals; pair-bonus gradient
+  int *dcid = nullptr;                                    // [n*6] sense codon id of state a at p
   float *dP = nullptr;
   std::vector<void *> shared_allocs;
   PrecTables<float> f32;
@@ -646,6 +648,20 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     e = cudaGraphAddKernelNode(&un, g, &fin, 1, &kp);
     nodes++;
   }
+  if (e == cudaSuccess) {
+    const double *trans = p->dtrans, *p0 = p->dp0;
+    const int *cid = p->dcid;
+    double *cm = p->dcm, *bm = p->dbm, *pg = p->dpg;
+    void *args[] = {&dp, &trans, &p0, &cid, &cm, &bm, &pg};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_codon_out<T>;
+    kp.gridDim = dim3((p->m * 6 + n + 127) / 128 + (61 * 61 + 3) / 4);  // threads, then 4 warps a block
+    kp.blockDim = dim3(128);
+    kp.kernelParams = args;
+    cudaGraphNode_t co;
+    e = cudaGraphAddKernelNode(&co, g, &fin, 1, &kp);
+    nodes++;
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&t.gout, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(p, e, "outside graph");
@@ -1038,6 +1054,8 @@ static void release_protein(cf_problem *p) {
   p->dM = p->dbase = p->dbnd = p->dE = p->derr = nullptr;
   p->ddmax = nullptr;
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
+  p->dcm = p->dbm = p->dpg = nullptr;
+  p->dcid = nullptr;
   p->dP = nullptr;
   p->have_inside = false;
   p->n = p->m = 0;
@@ -1117,12 +1135,17 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     CF_CUDA(p, dalloc(S, &p->dtrans, (size_t)std::max(m - 1, 1) * BLK));
     CF_CUDA(p, dalloc(S, &p->dp0, (size_t)NS));
     CF_CUDA(p, dalloc(S, &p->dP, (size_t)n * n));
+    CF_CUDA(p, dalloc(S, &p->dcm, (size_t)m * 6));
+    CF_CUDA(p, dalloc(S, &p->dbm, (size_t)n * 4));
+    CF_CUDA(p, dalloc(S, &p->dpg, (size_t)61 * 61));
+    CF_CUDA(p, dalloc(S, &p->dcid, (size_t)n * NS));
   }
   cudaStream_t st = p->stream;
   CF_CUDA(p, cudaMemcpyAsync(p->dM, p->M.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
   if (reuse && p->smp_cap > 0)  // the sampler's codon ids of the new protein
     CF_CUDA(p, cudaMemcpyAsync(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
@@ -1179,43 +1202,23 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
     s = copy_out(p, pair_prob, p->dP, sizeof(float) * (size_t)n * n, true);
     if (s != CF_OK) return s;
   }
-  std::vector<double> trans((size_t)std::max(m - 1, 1) * BLK), p0(NS);
-  CF_CUDA(p, cudaMemcpyAsync(trans.data(), p->dtrans, sizeof(double) * trans.size(), cudaMemcpyDeviceToHost, st));
-  CF_CUDA(p, cudaMemcpyAsync(p0.data(), p->dp0, sizeof(double) * NS, cudaMemcpyDeviceToHost, st));
+  if (codon_marg) {
+    s = copy_out(p, codon_marg, p->dcm, sizeof(double) * (size_t)m * 6, true);
+    if (s != CF_OK) return s;
+  }
+  if (base_marg) {
+    s = copy_out(p, base_marg, p->dbm, sizeof(double) * (size_t)n * 4, true);
+    if (s != CF_OK) return s;
+  }
+  if (pair_grad) {
+    s = copy_out(p, pair_grad, p->dpg, sizeof(double) * 61 * 61, true);
+    if (s != CF_OK) return s;
+  }
   int err = 0;
   CF_CUDA(p, cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_out, p->ev[2], p->ev[3]));
   if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "outside: a bounded wait for staged inputs gave up");
-  std::vector<double> cm((size_t)m * 6, 0.0), pg(61 * 61, 0.0);
-  for (int a = 0; a < p->M[0]; a++) cm[a] = p0[a];
-  for (int r = 0; r + 1 < m; r++) {
-    int q = 3 * r + 2;
-    for (int a = 0; a < p->M[q]; a++)
-      for (int b = 0; b < p->M[q + 1]; b++) {
-        double v = trans[(size_t)r * BLK + a * NS + b];
-        cm[(size_t)(r + 1) * 6 + b] += v;
-        pg[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]] += v;
-      }
-  }
-  if (codon_marg) {
-    s = copy_out(p, codon_marg, cm.data(), sizeof(double) * cm.size(), false);
-    if (s != CF_OK) return s;
-  }
-  if (base_marg) {
-    // the state of position i is the codon choice of its residue: base of
-    // state a at i times the residue's codon marginal
-    std::vector<double> bm((size_t)n * 4, 0.0);
-    for (int i = 0; i < n; i++)
-      for (int a = 0; a < p->M[i]; a++) bm[(size_t)i * 4 + p->base[(size_t)i * NS + a]] += cm[(size_t)(i / 3) * 6 + a];
-    s = copy_out(p, base_marg, bm.data(), sizeof(double) * bm.size(), false);
-    if (s != CF_OK) return s;
-  }
-  if (pair_grad) {
-    s = copy_out(p, pair_grad, pg.data(), sizeof(double) * pg.size(), false);
-    if (s != CF_OK) return s;
-  }
-  CF_CUDA(p, cudaStreamSynchronize(st));
   return CF_OK;
 }
 

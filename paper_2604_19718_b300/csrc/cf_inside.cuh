@@ -45,7 +45,6 @@ __device__ __forceinline__ double clamp_p2<double>(int e) {
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// store the warp-reduced block: entry e owned by lane e % 32
 // Z relative to 2^{E[n-1]}: sum_a u0[a] sum_b (Q5U + Q5P)[n-1][a][b]
 template <typename T>
 __global__ void k_inside_finish(DP<T> p) {
@@ -59,6 +58,78 @@ __global__ void k_inside_finish(DP<T> p) {
     z += p.u0[a] * s;
   }
   *p.Zm = z;
+}
+
+// Position transfers of the sequence tensor train (Eq. pair-tt), one thread
+// per position q, in binary64:
+//   T_q[a][b] = delta_ab                      inside a residue (q % 3 != 2),
+//   T_q[a][b] = s_r e^{lw[r+1][b] + pb[c_a][c_b]}  across the boundary from
+//               residue r to r+1 (q = 3r + 2), c_a, c_b the sense codon ids;
+// s_r = M_q / sum_ab e^{...} makes the average row sum one (an exact rescale,
+// log s_r is stored in ls[r] and undone in log Z).  The typed transitions add
+// the dangles of a paired end: X_UU = T, X_UP = T d5[b][a], X_PU = T d3[a][b],
+// X_PP = T d3 d5, with the bases of states a at q and b at q+1.  Entries beyond
+// the state counts, and the row of the last position, are zero.  Thread 0 also
+// writes u0[a] = e^{lw[0][a]} (residue 0's weights enter at the top).
+__global__ void k_transfers(int n, const int *Mp, const int *base, const int *cid, const double *en,
+                            const double *lw, const double *pb, double *Tr, double *X, double *u0, double *ls) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0)
+    for (int a = 0; a < NS; a++) u0[a] = a < Mp[0] ? exp(lw[a]) : 0.0;
+  if (q >= n) return;
+  double t[BLK];
+  for (int e = 0; e < BLK; e++) t[e] = 0.0;
+  const int Ma = Mp[q], Mb = q + 1 < n ? Mp[q + 1] : 0;
+  if (q + 1 < n) {
+    if (q % 3 != 2) {
+      for (int a = 0; a < Ma; a++) t[a * NS + a] = 1.0;
+    } else {
+      const int r1 = (q + 1) / 3;
+      double sum = 0;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) {
+          const double w = lw[(size_t)r1 * 6 + b] + pb[61 * cid[(size_t)q * NS + a] + cid[(size_t)(q + 1) * NS + b]];
+          t[a * NS + b] = exp(w);
+          sum += t[a * NS + b];
+        }
+      const double s = Ma / sum;
+      for (int a = 0; a < Ma; a++)
+        for (int b = 0; b < Mb; b++) t[a * NS + b] *= s;
+      ls[r1 - 1] = log(s);
+    }
+  }
+  double *tq = Tr + (size_t)q * BLK, *xq = X + (size_t)q * 4 * BLK;
+  for (int a = 0; a < NS; a++)
+    for (int b = 0; b < NS; b++) {
+      const int e = a * NS + b;
+      double d3 = 0, d5 = 0;
+      if (a < Ma && b < Mb) {
+        const int x0 = base[(size_t)q * NS + a], y0 = base[(size_t)(q + 1) * NS + b];
+        d3 = en[EN_D3 + x0 * 4 + y0];
+        d5 = en[EN_D5 + y0 * 4 + x0];
+      }
+      tq[e] = t[e];
+      xq[XUU * BLK + e] = t[e];
+      xq[XUP * BLK + e] = t[e] * d5;
+      xq[XPU * BLK + e] = t[e] * d3;
+      xq[XPP * BLK + e] = t[e] * d3 * d5;
+    }
+}
+
+// Copy of a binary64 table in the precision of a pass.
+template <typename T>
+__global__ void k_cast(const double *src, T *dst, size_t cnt) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < cnt; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = (T)src[k];
+}
+
+// log Z (natural log) in binary64: log of the scaled sum, plus the exponent
+// of the last diagonal, minus the transfer rescales, summed in residue order.
+__global__ void k_logz(const double *Zm, const int *E_last, const double *ls, int nls, double *logz) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double sc = 0;
+  for (int r = 0; r < nls; r++) sc += ls[r];
+  *logz = log(*Zm) + (double)*E_last * 0.69314718055994530942 - sc;
 }
 
 }  // namespace cf

@@ -123,14 +123,17 @@ struct cf_problem {
   std::string err;
   int n = 0, m = 0;
   std::vector<int> M, base, bnd, cid;
-  std::vector<double> Tr, X, u0, eHL;
-  double log_scale = 0;  // sum_p log s_p of the transfer scaling
+  std::vector<double> eHL;
   // device, shared by both precisions
   int *dM = nullptr, *dbase = nullptr, *dbnd = nullptr, *dE = nullptr, *derr = nullptr;
   unsigned long long *ddmax = nullptr;
   double *du0 = nullptr, *dZm = nullptr, *dtrans = nullptr, *dp0 = nullptr;
   double *dcm = nullptr, *dbm = nullptr, *dpg = nullptr;  // codon, base marginals; pair-bonus gradient
   int *dcid = nullptr;                                    // [n*6] sense codon id of state a at p
+  // binary64 masters of the position transfers (k_transfers), the weights
+  // they are made from, the per-boundary log rescales and log Z
+  double *dlw = nullptr, *dpb = nullptr, *dTr64 = nullptr, *dX64 = nullptr, *den64 = nullptr;
+  double *dls = nullptr, *dlogz = nullptr;
   float *dP = nullptr;
   std::vector<void *> shared_allocs;
   PrecTables<float> f32;
@@ -241,11 +244,11 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, dalloc(L, &x, (size_t)n * 4 * BLK));
   CF_CUDA(p, dalloc(L, &en, (size_t)EN_N));
   CF_CUDA(p, dalloc(L, &eh, (size_t)n + 2));
+  k_cast<T><<<148, 256, 0, p->stream>>>(p->dTr64, tr, (size_t)n * BLK);
+  k_cast<T><<<148, 256, 0, p->stream>>>(p->dX64, x, (size_t)n * 4 * BLK);
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaStreamSynchronize(p->stream));
   std::vector<T> h;
-  h.assign(p->Tr.begin(), p->Tr.end());
-  CF_CUDA(p, cudaMemcpy(tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-  h.assign(p->X.begin(), p->X.end());
-  CF_CUDA(p, cudaMemcpy(x, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   h.assign(p->model->en, p->model->en + EN_N);
   CF_CUDA(p, cudaMemcpy(en, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   h.assign(p->eHL.begin(), p->eHL.end());
@@ -689,11 +692,14 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   CF_CUDA(p, cudaGraphLaunch(t.gin, st));
   int launches = t.gin_nodes;
+  k_logz<<<1, 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, p->m - 1, p->dlogz);
+  launches++;
+  CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaEventRecord(p->ev[1], st));
-  double zm = 0;
-  int e_last = 0, err = 0;
+  double zm = 0, lz = 0;
+  int err = 0;
   CF_CUDA(p, cudaMemcpyAsync(&zm, p->dZm, sizeof(double), cudaMemcpyDeviceToHost, st));
-  CF_CUDA(p, cudaMemcpyAsync(&e_last, p->dE + (n - 1), sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(&lz, p->dlogz, sizeof(double), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_in, p->ev[0], p->ev[1]));
@@ -701,7 +707,7 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "inside: a bounded wait for staged inputs gave up");
   if (err || !(zm > 0) || !std::isfinite(zm))
     return fail(p, CF_ENUMERIC, "inside: non-finite or zero partition function after scaling");
-  *logZ = std::log(zm) + e_last * std::log(2.0) - p->log_scale;
+  *logZ = lz;
   return CF_OK;
 }
 
@@ -777,52 +783,22 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
   return CF_OK;
 }
 
-// Host construction of the codon-pair tensor train along the backbone (Eq.
-// pair-tt): T_p is the identity inside a residue and e^{lw[r+1][b] + pb[a][b]}
-// across the boundary into residue r+1, each boundary block rescaled so that
-// its average row sum is one (the scale is undone in log Z); X_p adds the
-// dangle factors of the typed ports; u0 carries residue 0's weights.
-void build_transfers(cf_problem *p, const double *lw, const double *pb) {
-  const int n = p->n;
-  const double *en = p->model->en;
-  p->Tr.assign((size_t)n * BLK, 0.0);
-  p->X.assign((size_t)n * 4 * BLK, 0.0);
-  p->log_scale = 0;
-  for (int q = 0; q + 1 < n; q++) {
-    int Ma = p->M[q], Mb = p->M[q + 1];
-    double *T = &p->Tr[(size_t)q * BLK];
-    if (q % 3 != 2) {
-      for (int a = 0; a < Ma; a++) T[a * NS + a] = 1.0;
-    } else {
-      p->bnd[q] = 1;
-      int r1 = (q + 1) / 3;
-      double sum = 0;
-      for (int a = 0; a < Ma; a++)
-        for (int b = 0; b < Mb; b++) {
-          double w = lw ? lw[(size_t)r1 * 6 + b] : 0.0;
-          if (pb) w += pb[61 * p->cid[(size_t)q * NS + a] + p->cid[(size_t)(q + 1) * NS + b]];
-          T[a * NS + b] = std::exp(w);
-          sum += T[a * NS + b];
-        }
-      // normalise the average row sum to one (exact rescale, undone in log Z)
-      double s = Ma / sum;
-      for (int a = 0; a < Ma; a++)
-        for (int b = 0; b < Mb; b++) T[a * NS + b] *= s;
-      p->log_scale += std::log(s);
-    }
-    for (int a = 0; a < Ma; a++)
-      for (int b = 0; b < Mb; b++) {
-        int x0 = p->base[(size_t)q * NS + a], y0 = p->base[(size_t)(q + 1) * NS + b];
-        double t = T[a * NS + b], d3 = en[EN_D3 + x0 * 4 + y0], d5 = en[EN_D5 + y0 * 4 + x0];
-        double *X = &p->X[(size_t)q * 4 * BLK];
-        X[XUU * BLK + a * NS + b] = t;
-        X[XUP * BLK + a * NS + b] = t * d5;
-        X[XPU * BLK + a * NS + b] = t * d3;
-        X[XPP * BLK + a * NS + b] = t * d3 * d5;
-      }
-  }
-  p->u0.assign(NS, 0.0);
-  for (int a = 0; a < p->M[0]; a++) p->u0[a] = std::exp(lw ? lw[a] : 0.0);
+// The codon-pair tensor train along the backbone (Eq. pair-tt), made on the
+// device by k_transfers from the weights (NULL = all zero): binary64 masters
+// of T_p and X_p, residue 0's weights u0 and the per-boundary log rescales.
+// The tables of each allocated precision are refreshed by upload_transfers.
+cf_status device_transfers(cf_problem *p, const double *lw, const double *pb) {
+  const int n = p->n, m = p->m;
+  cudaStream_t st = p->stream;
+  if (lw) CF_CUDA(p, cudaMemcpyAsync(p->dlw, lw, sizeof(double) * (size_t)m * 6, cudaMemcpyHostToDevice, st));
+  else CF_CUDA(p, cudaMemsetAsync(p->dlw, 0, sizeof(double) * (size_t)m * 6, st));
+  if (pb) CF_CUDA(p, cudaMemcpyAsync(p->dpb, pb, sizeof(double) * 61 * 61, cudaMemcpyHostToDevice, st));
+  else CF_CUDA(p, cudaMemsetAsync(p->dpb, 0, sizeof(double) * 61 * 61, st));
+  CF_CUDA(p, cudaMemsetAsync(p->dls, 0, sizeof(double) * (size_t)std::max(m - 1, 1), st));
+  k_transfers<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, p->den64, p->dlw, p->dpb, p->dTr64,
+                                               p->dX64, p->du0, p->dls);
+  CF_CUDA(p, cudaGetLastError());
+  return CF_OK;
 }
 
 cf_status check_weights(cf_problem *p, int m, const double *lw, const double *pb) {
@@ -863,10 +839,11 @@ cf_status clear_tables(cf_problem *p, PrecTables<T> &t) {
 
 template <typename T>
 cf_status upload_transfers(cf_problem *p, PrecTables<T> &t) {
-  if (!t.inside_alloc) return CF_OK;  // uploaded when the tables are first made
-  std::vector<T> h(p->Tr.begin(), p->Tr.end()), hx(p->X.begin(), p->X.end());
-  CF_CUDA(p, cudaMemcpyAsync((void *)t.dp.Tr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream));
-  CF_CUDA(p, cudaMemcpyAsync((void *)t.dp.X, hx.data(), hx.size() * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+  if (!t.inside_alloc) return CF_OK;  // cast when the tables are first made
+  const int n = p->n;
+  k_cast<T><<<148, 256, 0, p->stream>>>(p->dTr64, (T *)t.dp.Tr, (size_t)n * BLK);
+  k_cast<T><<<148, 256, 0, p->stream>>>(p->dX64, (T *)t.dp.X, (size_t)n * 4 * BLK);
+  CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaStreamSynchronize(p->stream));
   return CF_OK;
 }
@@ -1056,6 +1033,7 @@ static void release_protein(cf_problem *p) {
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
   p->dcm = p->dbm = p->dpg = nullptr;
   p->dcid = nullptr;
+  p->dlw = p->dpb = p->dTr64 = p->dX64 = p->den64 = p->dls = p->dlogz = nullptr;
   p->dP = nullptr;
   p->have_inside = false;
   p->n = p->m = 0;
@@ -1113,9 +1091,9 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
         p->base[(size_t)q * NS + a] = (cods[a] >> (2 * (2 - off))) & 3;
         p->cid[(size_t)q * NS + a] = gc.sense_id[cods[a]];
       }
+      p->bnd[q] = (off == 2 && q + 1 < n) ? 1 : 0;  // T_q crosses into residue r+1
     }
   }
-  build_transfers(p, lw, pb);
   p->eHL.assign((size_t)n + 2, 0.0);
   const double kT = p->model->kT, H30 = p->model->params[36 + MAXLOOP];
   for (int L = 0; L < n + 2; L++) {
@@ -1139,14 +1117,22 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     CF_CUDA(p, dalloc(S, &p->dbm, (size_t)n * 4));
     CF_CUDA(p, dalloc(S, &p->dpg, (size_t)61 * 61));
     CF_CUDA(p, dalloc(S, &p->dcid, (size_t)n * NS));
+    CF_CUDA(p, dalloc(S, &p->dlw, (size_t)m * 6));
+    CF_CUDA(p, dalloc(S, &p->dpb, (size_t)61 * 61));
+    CF_CUDA(p, dalloc(S, &p->dTr64, (size_t)n * BLK));
+    CF_CUDA(p, dalloc(S, &p->dX64, (size_t)n * 4 * BLK));
+    CF_CUDA(p, dalloc(S, &p->den64, (size_t)EN_N));
+    CF_CUDA(p, dalloc(S, &p->dls, (size_t)std::max(m - 1, 1)));
+    CF_CUDA(p, dalloc(S, &p->dlogz, (size_t)1));
+    CF_CUDA(p, cudaMemcpy(p->den64, p->model->en, sizeof(double) * EN_N, cudaMemcpyHostToDevice));
   }
   cudaStream_t st = p->stream;
   CF_CUDA(p, cudaMemcpyAsync(p->dM, p->M.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-  CF_CUDA(p, cudaMemcpyAsync(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
+  if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
   if (reuse && p->smp_cap > 0)  // the sampler's codon ids of the new protein
     CF_CUDA(p, cudaMemcpyAsync(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
@@ -1168,11 +1154,10 @@ cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
   CF_CUDA(p, cudaSetDevice(p->device));
   CF_CUDA(p, cudaStreamSynchronize(p->stream));  // no pass may still read the old transfers
   p->have_inside = false;
-  build_transfers(p, lw, pb);
+  if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
   cf_status s = upload_transfers(p, p->f32);
   if (s == CF_OK) s = upload_transfers(p, p->f64);
   if (s != CF_OK) return s;
-  CF_CUDA(p, cudaMemcpyAsync(p->du0, p->u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, p->stream));
   CF_CUDA(p, cudaStreamSynchronize(p->stream));
   return CF_OK;
 }

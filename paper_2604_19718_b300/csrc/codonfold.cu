@@ -1,12 +1,14 @@
 // codonfold.cu -- C ABI (include/codonfold.h) and host orchestration of the
 // codon-constrained partition-function kernels for sm_103a.
 //
-// Host work is limited to building the per-position tensor-train data of the
-// protein (Eq. pair-tt with soft weights), choosing launch shapes, moving
-// inputs/outputs and turning device reductions into the returned numbers.
-// Every step of the dynamic program runs in the kernels of cf_inside2.cuh
-// (inside), cf_outside2.cuh and cf_outside.cuh (outside and marginals),
-// cf_sample.cuh (sampler) and cf_window.cuh (fixed-sequence windows).
+// Host work is limited to validating inputs, listing the codon states of each
+// position (amino acid -> codons, bases, sense ids), the model's loop-length
+// factor tables, choosing launch shapes and moving inputs and outputs.  Every
+// step of the computation runs in kernels: the position transfers (Eq.
+// pair-tt with soft weights) and log Z in cf_inside.cuh, the inside wavefront
+// in cf_inside2.cuh, the outside pass and the marginals in cf_outside2.cuh and
+// cf_outside.cuh, the sampler in cf_sample.cuh and the fixed-sequence windows
+// in cf_window.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>

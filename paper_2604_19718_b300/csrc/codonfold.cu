@@ -149,7 +149,7 @@ struct cf_problem {
   std::vector<void *> smp_allocs;
   size_t smp_cap = 0;
   int2 *smp_stack = nullptr;
-  int *smp_state = nullptr, *smp_cid = nullptr, *smp_err = nullptr;
+  int *smp_state = nullptr, *smp_err = nullptr;
   // batched window DP: energy tables (once) and buffers grown on demand
   std::vector<void *> win_allocs, win_buf_allocs;
   float *win_en = nullptr, *win_ehl = nullptr;
@@ -751,9 +751,7 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
     free_list(p->smp_allocs);
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_stack, need_stack));
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_state, need_state));
-    CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_cid, (size_t)n * NS));
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_err, (size_t)1));
-    CF_CUDA(p, cudaMemcpy(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice));
     p->smp_cap = warps;
   }
   const bool dc = is_device_ptr(codons), dpn = is_device_ptr(partner);
@@ -764,7 +762,7 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
   CF_CUDA(p, cudaMemsetAsync(p->smp_err, 0, sizeof(int), st));
   SampleArgs<T> a;
   a.p = t.dp;
-  a.cid = p->smp_cid;
+  a.cid = p->dcid;
   a.nsamples = ns;
   a.seed = seed;
   a.stack = p->smp_stack;
@@ -1135,8 +1133,6 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
   CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
   if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
-  if (reuse && p->smp_cap > 0)  // the sampler's codon ids of the new protein
-    CF_CUDA(p, cudaMemcpyAsync(p->smp_cid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   if (reuse) {
     // the tables of each precision are cleared by its next inside pass

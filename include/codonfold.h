@@ -12,7 +12,10 @@
  *   - every call returns a cf_status; no C++ exception crosses the ABI;
  *   - output buffers are owned and allocated by the caller; a pointer may be
  *     host memory or device memory of the problem's device (the library asks
- *     the CUDA runtime which it is and copies accordingly);
+ *     the CUDA runtime which it is and copies accordingly); device memory of
+ *     another device is rejected with CF_EINVAL wherever a kernel would read
+ *     or write the buffer in place (cf_sample, cf_sample_noalloc,
+ *     cf_window_logz, the surrogate's window inputs);
  *   - one cf_problem is bound to one device and one CUDA stream; calls on one
  *     problem must not overlap (not thread-safe per problem), distinct
  *     problems are independent;
@@ -148,7 +151,8 @@ cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, dou
  * the same seed gives bit-identical output for any launch shape.
  *   codons:  nsamples*m int32, sense codon id per residue.
  *   partner: nsamples*n int32, pairing partner per position or -1.
- * Errors: CF_ESTATE (no inside), CF_EINVAL, CF_ENOMEM, CF_ECUDA.
+ * Errors: CF_ESTATE (no inside), CF_EINVAL (also: an output in device memory
+ * of another device), CF_ENOMEM, CF_ECUDA.
  */
 cf_status cf_sample(cf_problem *prob, int nsamples, uint64_t seed, int32_t *codons,
                     int32_t *partner);
@@ -251,6 +255,10 @@ float cf_surrogate_last_ms(const cf_surrogate *sur);
  *   problem's device.  The inside tables must exist (cf_inside first); they
  *   were allocated by cf_set_protein / cf_inside, not by this call.
  *   Limits: n = 3m <= CF_NOALLOC_MAX_N; CF_NOALLOC_WARPS warps draw samples.
+ *   The array holds an error word (256 bytes), the per-warp position states
+ *   (CF_NOALLOC_WARPS * CF_NOALLOC_MAX_N int32) and the per-warp traceback
+ *   stacks (CF_NOALLOC_WARPS * (CF_NOALLOC_MAX_N + 64) pairs of int32):
+ *   CF_NOALLOC_SCRATCH_BYTES = 4,673,792 bytes at the limits below.
  *   Errors: CF_EINVAL (n above the limit, host or NULL output pointers,
  *   nsamples < 0), CF_ESTATE (no inside), CF_ECUDA, CF_ENUMERIC.
  *   Set-up: the first call on a device looks up the array's device address
@@ -264,8 +272,51 @@ float cf_surrogate_last_ms(const cf_surrogate *sur);
  */
 #define CF_NOALLOC_MAX_N 3000
 #define CF_NOALLOC_WARPS 128
+#define CF_NOALLOC_SCRATCH_BYTES                                                              \
+  (256 + ((CF_NOALLOC_WARPS * CF_NOALLOC_MAX_N * 4 + 255) / 256) * 256 +                     \
+   CF_NOALLOC_WARPS * (CF_NOALLOC_MAX_N + 64) * 8)
 cf_status cf_sample_noalloc(cf_problem *prob, int nsamples, uint64_t seed, int32_t *codons,
                             int32_t *partner);
+
+/*
+ * Far-band diagnostics of the last binary32 passes (the paper has no
+ * counterpart: this reports how the library summed the bifurcation terms).
+ * The split points far from the wavefront are summed in tiles whose
+ * power-of-two factors follow a linear fit ("chord") of the per-diagonal
+ * exponents; a band whose exponents depart from the chord by more than 48
+ * (log2) is not tiled but summed term by term with exact factors.
+ *   in_max_dev / out_max_dev: largest departure seen by the inside bands and
+ *   by the outside pass; in_untiled: inside bands summed term by term;
+ *   out_untiled: 1 if the outside pass gathered every term per diagonal.
+ * Any pointer may be NULL.  Synchronises the problem's stream.
+ * Errors: CF_EINVAL (NULL problem), CF_ECUDA.
+ */
+cf_status cf_far_band_info(const cf_problem *prob, int *in_max_dev, int *in_untiled, int *out_max_dev,
+                           int *out_untiled);
+
+/*
+ * Test hooks (the paper has no counterpart).  They exist so that tests can
+ * drive the library's failure paths without faulting a GPU.
+ *   cf_debug_set_wait_polls: the number of polls after which the bounded
+ *     waits for staged inputs give up on `device` (default 2^22, about a
+ *     second).  With 0 every such wait gives up at once: the kernel records
+ *     the timeout, still waits (bounded) for its own copies in flight, and
+ *     returns, and cf_inside / cf_outside report CF_ETIMEOUT.  Synchronises
+ *     the device before and after; affects every problem on that device.
+ *   cf_debug_fail_alloc: after `after` further successful device allocations
+ *     of the library (process-wide), the next one fails as if the device were
+ *     out of memory (CF_ENOMEM); negative turns the hook off.  The failing
+ *     call leaves the problem usable: a failed cf_set_protein leaves no
+ *     protein, a failed cf_inside / cf_outside leaves no tables of that
+ *     precision.
+ *   cf_debug_classify_pointer: the rule by which caller buffers are accepted,
+ *     for a pointer with the given cudaMemoryType and device, seen from a
+ *     problem on problem_device: 0 host memory, 1 device memory the problem
+ *     may use in place, -1 device memory of another device (rejected).
+ */
+cf_status cf_debug_set_wait_polls(int device, unsigned long long polls);
+cf_status cf_debug_fail_alloc(long long after);
+int cf_debug_classify_pointer(int memory_type, int pointer_device, int problem_device);
 
 #ifdef __cplusplus
 }

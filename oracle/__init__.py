@@ -8,8 +8,9 @@ shares no code with it.
 
 Functions cite the paper's sections: log Z (Section "Probability
 distributions", Eq. amino-q), pair probabilities (Eq. pair-probability),
-codon marginals (Eq. marginal-codon), base marginals (Eq. marginal-base) and
-sampling (Section "Sequence sampling").
+codon marginals (Eq. marginal-codon), base marginals (Eq. marginal-base),
+sampling (Section "Sequence sampling") and the minimum free energy
+configuration (Section "Minimization", Eq. min-problem).
 """
 from __future__ import annotations
 
@@ -49,6 +50,7 @@ def _load():
         _lib.or_outside.argtypes = [dp, ip, ctypes.c_int, dp, dp, up, ctypes.c_int, dp, dp, dp, dp, dp]
         _lib.or_sample.argtypes = [dp, ip, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_uint64, ip, ip]
         _lib.or_codons_of.argtypes = [ctypes.c_int, ip]
+        _lib.or_mfe.argtypes = [dp, ip, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp, ip, ip]
     return _lib
 
 
@@ -148,3 +150,26 @@ def sample(params, residues, nsamples: int, seed: int, lw=None, pb=None):
     if rc:
         raise RuntimeError(f"oracle sampler failed with status {rc}")
     return cod, par
+
+
+Q_SCALE = 4294967296.0  # MFE costs are integers in units of 2^-32 kcal/mol
+
+
+def mfe(params, residues, lw=None, pb=None, traceback=True):
+    """Minimum over (codon sequence, structure) of E - kT (sum lw + sum pb) in
+    kcal/mol, by the min-sum recursions on integer costs (2^-32 kcal/mol).
+    Returns (mfe_q integer cost, mfe in kcal/mol, codons[m] sense ids,
+    partner[n]) of one minimiser (None, None without traceback)."""
+    params, res, m, lw, pb = _prep(params, residues, lw, pb)
+    n = 3 * m
+    q = ctypes.c_longlong()
+    kc = ctypes.c_double()
+    cod = np.zeros(m, dtype=np.int32) if traceback else None
+    par = np.zeros(n, dtype=np.int32) if traceback else None
+    ip = ctypes.POINTER(ctypes.c_int)
+    rc = _load().or_mfe(_dptr(params), res.ctypes.data_as(ip), m, _dptr(lw), _dptr(pb), ctypes.byref(q),
+                        ctypes.byref(kc), None if cod is None else cod.ctypes.data_as(ip),
+                        None if par is None else par.ctypes.data_as(ip))
+    if rc:
+        raise RuntimeError(f"oracle mfe failed with status {rc}")
+    return q.value, kc.value, cod, par

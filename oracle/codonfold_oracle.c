@@ -1623,30 +1623,694 @@ int or_codons_of(int aa, int *out) {
   return cnt;
 }
 
-/* Diagnostic: log of the largest entry of each QB[i][j] block (-inf if the
- * block is zero), n x n, row-major; used to study magnitude spreads. */
-int or_qb_logmax(const double *params, const int *res, int m, const double *lw, const double *pb,
-                 double *out) {
+/* ================================================================ MFE
+ * Minimum free energy over (codon sequence, structure): paper Section
+ * "Minimization" (Eq. min-problem) -- the zero-temperature limit obtained by
+ * replacing the sum-product semiring of the partition function with the
+ * min-sum (tropical) semiring (SI "Generalization via evaluation algebras").
+ * The recursions are those of the inside pass above, statement for
+ * statement, with every sum a minimum and every product a sum of costs.
+ *
+ * Costs are exact integers: every elementary energy term (stack, hairpin,
+ * bulge, interior, mismatch, dangle, a, b, c, and each codon log-weight and
+ * codon-pair bonus converted to kcal/mol as -kT w) is rounded to the nearest
+ * multiple of 2^-32 kcal/mol (round half away from zero) once, and all
+ * recursions add these integers.  The minimum is then exact and independent
+ * of the order of evaluation, so any implementation of the same model gives
+ * the identical value.  kT = 1.98717e-3 (T + 273.15) and -kT w are evaluated
+ * in binary64; the hairpin extrapolation H(30) + 1.07856 ln(L/30) too.
+ * ================================================================ */
+
+typedef long long Q;
+#define QINF (1LL << 60)
+
+static Q qcost(double e) { return llround(e * 4294967296.0); }
+static Q qadd(Q a, Q b) { return (a >= QINF || b >= QINF) ? QINF : a + b; }
+static Q qmin(Q a, Q b) { return a < b ? a : b; }
+
+typedef struct {
+  int n, m;
+  int *M;
+  int (*base)[NS];
+  int (*cid)[NS];
+  Q st[6][6], Hl[MAXLOOP + 1], Bu[MAXLOOP + 1], In[MAXLOOP + 1];
+  Q tm[4][4], d5[4][4], d3[4][4], ca, cb, cc;
+  double H30, kT;
+  Q (*T)[NS][NS];   /* transfer cost p -> p+1 */
+  Q (*X)[NPT][NPT]; /* typed transition cost */
+  Q u0[NS];
+  /* tables, triangular index as tri() */
+  Q (*C)[NS][NS];
+  Q (*QB)[NS][NS];
+  Q (*XI)[NS][NS];
+  Q (*QM1)[NS][NPT];
+  Q (*QM)[NPT][NPT];
+  Q (*QM2)[NPT][NPT];
+  Q (*Q5)[NS][NPT];
+  Q mfe;
+} mctx;
+
+/* ports of a position with M codon states: states a (type U) then a + 6 (type P) */
+static int ports_of_m(int M, int *out) {
+  int k = 0;
+  for (int t = 0; t < 2; t++)
+    for (int a = 0; a < M; a++) out[k++] = a + 6 * t;
+  return k;
+}
+
+static inline size_t mtri(const mctx *c, int i, int j) {
+  return (size_t)i * c->n - (size_t)i * (i - 1) / 2 + (size_t)(j - i);
+}
+
+static Q m_hairpin(const mctx *c, int L) {
+  if (L <= MAXLOOP) return c->Hl[L];
+  return qcost(c->H30 + 1.07856 * log((double)L / MAXLOOP));
+}
+
+static void m_free(mctx *c) {
+  free(c->M); free(c->base); free(c->cid); free(c->T); free(c->X);
+  free(c->C); free(c->QB); free(c->XI); free(c->QM1); free(c->QM); free(c->QM2); free(c->Q5);
+  memset(c, 0, sizeof(*c));
+}
+
+static void qfill(Q *p, size_t cnt) {
+  for (size_t k = 0; k < cnt; k++) p[k] = QINF;
+}
+
+static int m_setup(mctx *c, const double *params, const int *res, int m, const double *lw, const double *pb) {
+  memset(c, 0, sizeof(*c));
+  c->m = m;
+  c->n = 3 * m;
+  int n = c->n;
+  c->kT = 1.98717e-3 * (params[180] + 273.15);
+  for (int x = 0; x < 6; x++)
+    for (int y = 0; y < 6; y++) c->st[x][y] = qcost(params[6 * x + y]);
+  for (int L = 0; L <= MAXLOOP; L++) {
+    c->Hl[L] = qcost(params[36 + L]);
+    c->Bu[L] = qcost(params[67 + L]);
+    c->In[L] = qcost(params[98 + L]);
+  }
+  c->H30 = params[36 + MAXLOOP];
+  for (int x = 0; x < 4; x++)
+    for (int y = 0; y < 4; y++) {
+      c->tm[x][y] = qcost(params[129 + 4 * x + y]);
+      c->d5[x][y] = qcost(params[145 + 4 * x + y]);
+      c->d3[x][y] = qcost(params[161 + 4 * x + y]);
+    }
+  c->ca = qcost(params[177]);
+  c->cb = qcost(params[178]);
+  c->cc = qcost(params[179]);
+  c->M = calloc(n, sizeof(int));
+  c->base = calloc(n, sizeof(*c->base));
+  c->cid = calloc(n, sizeof(*c->cid));
+  c->T = malloc(n * sizeof(*c->T));
+  c->X = malloc(n * sizeof(*c->X));
+  if (!c->M || !c->base || !c->cid || !c->T || !c->X) return -2;
+  for (int r = 0; r < m; r++) {
+    if (res[r] < 0 || res[r] >= 20) return -1;
+    char aa = OR_AA[res[r]];
+    int cnt = 0, cods[NS];
+    for (int k = 0; k < 64; k++)
+      if (OR_CODE64[k] == aa) cods[cnt++] = k;
+    for (int off = 0; off < 3; off++) {
+      int p = 3 * r + off;
+      c->M[p] = cnt;
+      for (int a = 0; a < cnt; a++) {
+        c->base[p][a] = codon_base(cods[a], off);
+        c->cid[p][a] = sense_id(cods[a]);
+      }
+    }
+  }
+  qfill(&c->T[0][0][0], (size_t)n * NS * NS);
+  qfill(&c->X[0][0][0], (size_t)n * NPT * NPT);
+  for (int p = 0; p + 1 < n; p++) {
+    int r1 = (p + 1) / 3;
+    for (int a = 0; a < c->M[p]; a++)
+      for (int b = 0; b < c->M[p + 1]; b++) {
+        Q t;
+        if (p % 3 != 2) {
+          t = (a == b) ? 0 : QINF;
+        } else {
+          t = qcost(-(c->kT * (lw ? lw[6 * r1 + b] : 0.0)));
+          t += qcost(-(c->kT * (pb ? pb[61 * c->cid[p][a] + c->cid[p + 1][b]] : 0.0)));
+        }
+        c->T[p][a][b] = t;
+        int x = c->base[p][a], y = c->base[p + 1][b];
+        for (int t1 = 0; t1 < 2; t1++)
+          for (int t2 = 0; t2 < 2; t2++) {
+            Q f = t;
+            if (t1 == TP) f = qadd(f, c->d3[x][y]);
+            if (t2 == TP) f = qadd(f, c->d5[y][x]);
+            c->X[p][a + 6 * t1][b + 6 * t2] = f;
+          }
+      }
+  }
+  for (int a = 0; a < NS; a++) c->u0[a] = a < c->M[0] ? qcost(-(c->kT * (lw ? lw[a] : 0.0))) : QINF;
+  size_t ncell = (size_t)n * (n + 1) / 2;
+  c->C = malloc(ncell * sizeof(*c->C));
+  c->QB = malloc(ncell * sizeof(*c->QB));
+  c->XI = malloc(ncell * sizeof(*c->XI));
+  c->QM1 = malloc(ncell * sizeof(*c->QM1));
+  c->QM = malloc(ncell * sizeof(*c->QM));
+  c->QM2 = malloc(ncell * sizeof(*c->QM2));
+  c->Q5 = malloc(n * sizeof(*c->Q5));
+  if (!c->C || !c->QB || !c->XI || !c->QM1 || !c->QM || !c->QM2 || !c->Q5) return -2;
+  qfill(&c->C[0][0][0], ncell * NS * NS);
+  qfill(&c->QB[0][0][0], ncell * NS * NS);
+  qfill(&c->XI[0][0][0], ncell * NS * NS);
+  qfill(&c->QM1[0][0][0], ncell * NS * NPT);
+  qfill(&c->QM[0][0][0], ncell * NPT * NPT);
+  qfill(&c->QM2[0][0][0], ncell * NPT * NPT);
+  qfill(&c->Q5[0][0][0], (size_t)n * NS * NPT);
+  return 0;
+}
+
+static int m_pairable(const mctx *c, int i, int a, int j, int b) {
+  return j - i >= 4 && pair_type(c->base[i][a], c->base[j][b]) >= 0;
+}
+static Q m_tmo(const mctx *c, int x, int u, int y, int v) { return c->tm[c->base[x][u]][c->base[y][v]]; }
+static Q m_tmi(const mctx *c, int k, int w, int l, int z) { return c->tm[c->base[l + 1][z]][c->base[k - 1][w]]; }
+
+static void m_chain(mctx *c, int i, int j) {
+  Q(*Cij)[NS] = c->C[mtri(c, i, j)];
+  if (i == j) {
+    for (int a = 0; a < c->M[i]; a++) Cij[a][a] = 0;
+    return;
+  }
+  const Q(*Cn)[NS] = c->C[mtri(c, i + 1, j)];
+  for (int a = 0; a < c->M[i]; a++)
+    for (int s = 0; s < c->M[i + 1]; s++)
+      for (int b = 0; b < c->M[j]; b++) Cij[a][b] = qmin(Cij[a][b], qadd(c->T[i][a][s], Cn[s][b]));
+}
+
+/* hairpin + interior loops of the loop closed by (i,j), before the outer
+ * mismatch and transfers: M_{i+1} x M_{j-1} (inner_sum of the inside pass) */
+static void m_inner(const mctx *c, int i, int j, Q S[NS][NS]) {
+  int x = i + 1, y = j - 1;
+  Q h = m_hairpin(c, j - i - 1);
+  const Q(*Ch)[NS] = c->C[mtri(c, x, y)];
+  for (int u = 0; u < NS; u++)
+    for (int v = 0; v < NS; v++) S[u][v] = QINF;
+  for (int u = 0; u < c->M[x]; u++)
+    for (int v = 0; v < c->M[y]; v++) S[u][v] = qadd(h, Ch[u][v]);
+  for (int l1 = 1; l1 <= MAXLOOP; l1++)
+    for (int l2 = 1; l1 + l2 <= MAXLOOP; l2++) {
+      int k = i + 1 + l1, l = j - 1 - l2;
+      if (l - k < 4) continue;
+      Q w = c->In[l1 + l2];
+      const Q(*C1)[NS] = c->C[mtri(c, x, k - 1)];
+      const Q(*XI)[NS] = c->XI[mtri(c, k, l)];
+      const Q(*C2)[NS] = c->C[mtri(c, l + 1, y)];
+      for (int u = 0; u < c->M[x]; u++)
+        for (int w2 = 0; w2 < c->M[k - 1]; w2++)
+          for (int z = 0; z < c->M[l + 1]; z++)
+            for (int v = 0; v < c->M[y]; v++)
+              S[u][v] = qmin(S[u][v], qadd(qadd(w, C1[u][w2]), qadd(XI[w2][z], C2[z][v])));
+    }
+}
+
+static Q m_stack(const mctx *c, int i, int a, int j, int b, int a2, int b2) {
+  int o = pair_type(c->base[i][a], c->base[j][b]);
+  int in = pair_type(c->base[i + 1][a2], c->base[j - 1][b2]);
+  if (o < 0 || in < 0) return QINF;
+  return c->st[o][in];
+}
+
+static void m_qb(mctx *c, int i, int j) {
+  Q acc[NS][NS];
+  int Mi = c->M[i], Mj = c->M[j], Mx = c->M[i + 1], My = c->M[j - 1];
+  for (int a = 0; a < NS; a++)
+    for (int b = 0; b < NS; b++) acc[a][b] = QINF;
+  Q S[NS][NS];
+  m_inner(c, i, j, S);
+  for (int a = 0; a < Mi; a++)
+    for (int b = 0; b < Mj; b++)
+      for (int u = 0; u < Mx; u++)
+        for (int v = 0; v < My; v++) {
+          Q k = qadd(S[u][v], m_tmo(c, i + 1, u, j - 1, v));
+          acc[a][b] = qmin(acc[a][b], qadd(qadd(c->T[i][a][u], k), c->T[j - 1][v][b]));
+        }
+  if (j - i - 2 >= 4) { /* stack */
+    const Q(*Qin)[NS] = c->QB[mtri(c, i + 1, j - 1)];
+    for (int a = 0; a < Mi; a++)
+      for (int b = 0; b < Mj; b++)
+        for (int a2 = 0; a2 < Mx; a2++)
+          for (int b2 = 0; b2 < My; b2++)
+            acc[a][b] = qmin(acc[a][b], qadd(qadd(c->T[i][a][a2], Qin[a2][b2]),
+                                             qadd(c->T[j - 1][b2][b], m_stack(c, i, a, j, b, a2, b2))));
+  }
+  for (int L = 1; L <= MAXLOOP; L++) {
+    int l = j - 1 - L; /* 3' bulge: inner pair (i+1, l) */
+    if (l - (i + 1) >= 4) {
+      const Q(*Qi)[NS] = c->QB[mtri(c, i + 1, l)];
+      const Q(*Cr)[NS] = c->C[mtri(c, l, j)];
+      for (int a = 0; a < Mi; a++)
+        for (int a2 = 0; a2 < Mx; a2++)
+          for (int s = 0; s < c->M[l]; s++)
+            for (int b = 0; b < Mj; b++)
+              acc[a][b] = qmin(acc[a][b], qadd(qadd(c->Bu[L], c->T[i][a][a2]), qadd(Qi[a2][s], Cr[s][b])));
+    }
+    int k = i + 1 + L; /* 5' bulge: inner pair (k, j-1) */
+    if ((j - 1) - k >= 4) {
+      const Q(*Qi)[NS] = c->QB[mtri(c, k, j - 1)];
+      const Q(*Cl)[NS] = c->C[mtri(c, i, k)];
+      for (int a = 0; a < Mi; a++)
+        for (int s = 0; s < c->M[k]; s++)
+          for (int b2 = 0; b2 < My; b2++)
+            for (int b = 0; b < Mj; b++)
+              acc[a][b] = qmin(acc[a][b], qadd(qadd(c->Bu[L], Cl[a][s]), qadd(Qi[s][b2], c->T[j - 1][b2][b])));
+    }
+  }
+  if (j - i - 2 >= 9) { /* multiloop closed by (i,j) */
+    const Q(*Q2)[NPT] = c->QM2[mtri(c, i + 1, j - 1)];
+    int px[NPT], py[NPT];
+    int nx = ports_of_m(c->M[i + 1], px), ny = ports_of_m(c->M[j - 1], py);
+    Q w = qadd(c->ca, c->cc);
+    for (int a = 0; a < Mi; a++)
+      for (int b = 0; b < Mj; b++)
+        for (int pi = 0; pi < nx; pi++)
+          for (int qi = 0; qi < ny; qi++)
+            acc[a][b] = qmin(acc[a][b], qadd(qadd(w, c->X[i][a + 6][px[pi]]),
+                                             qadd(Q2[px[pi]][py[qi]], c->X[j - 1][py[qi]][b + 6])));
+  }
+  Q(*QBij)[NS] = c->QB[mtri(c, i, j)];
+  for (int a = 0; a < Mi; a++)
+    for (int b = 0; b < Mj; b++) QBij[a][b] = m_pairable(c, i, a, j, b) ? acc[a][b] : QINF;
+}
+
+static void m_xi(mctx *c, int k, int l) {
+  if (k < 1 || l > c->n - 2) return;
+  const Q(*Qk)[NS] = c->QB[mtri(c, k, l)];
+  Q(*XI)[NS] = c->XI[mtri(c, k, l)];
+  for (int w = 0; w < c->M[k - 1]; w++)
+    for (int z = 0; z < c->M[l + 1]; z++) {
+      Q s = QINF;
+      for (int a = 0; a < c->M[k]; a++)
+        for (int b = 0; b < c->M[l]; b++) s = qmin(s, qadd(qadd(c->T[k - 1][w][a], Qk[a][b]), c->T[l][b][z]));
+      XI[w][z] = qadd(s, m_tmi(c, k, w, l, z));
+    }
+}
+
+static void m_qm1(mctx *c, int i, int j) {
+  Q(*Q1)[NPT] = c->QM1[mtri(c, i, j)];
+  const Q(*QBij)[NS] = c->QB[mtri(c, i, j)];
+  for (int a = 0; a < c->M[i]; a++)
+    for (int b = 0; b < c->M[j]; b++) Q1[a][b + 6] = qadd(c->cc, QBij[a][b]);
+  for (int l = i + 4; l <= j - 1; l++) {
+    const Q(*Qil)[NS] = c->QB[mtri(c, i, l)];
+    const Q(*Cr)[NS] = c->C[mtri(c, l + 1, j)];
+    Q w = c->cc + (Q)(j - l) * c->cb;
+    for (int a = 0; a < c->M[i]; a++)
+      for (int s = 0; s < c->M[l]; s++)
+        for (int e = 0; e < c->M[l + 1]; e++)
+          for (int b = 0; b < c->M[j]; b++)
+            Q1[a][b] = qmin(Q1[a][b], qadd(qadd(w, Qil[a][s]), qadd(c->X[l][s + 6][e], Cr[e][b])));
+  }
+}
+
+static void m_qm(mctx *c, int i, int j) {
+  Q(*QM)[NPT] = c->QM[mtri(c, i, j)];
+  const Q(*Q1)[NPT] = c->QM1[mtri(c, i, j)];
+  int pi_[NPT], pj[NPT];
+  int ni = ports_of_m(c->M[i], pi_), nj = ports_of_m(c->M[j], pj);
+  for (int a = 0; a < c->M[i]; a++)
+    for (int qi = 0; qi < nj; qi++) QM[a + 6][pj[qi]] = qmin(QM[a + 6][pj[qi]], Q1[a][pj[qi]]);
+  for (int k = i + 1; k <= j - 4; k++) {
+    const Q(*Qp)[NPT] = c->QM[mtri(c, i, k - 1)];
+    const Q(*Cu)[NS] = c->C[mtri(c, i, k - 1)];
+    const Q(*Qk)[NPT] = c->QM1[mtri(c, k, j)];
+    int pq[NPT];
+    int nq = ports_of_m(c->M[k - 1], pq);
+    Q un = (Q)(k - i) * c->cb;
+    for (int ri = 0; ri < ni; ri++) {
+      int p = pi_[ri];
+      for (int qi = 0; qi < nq; qi++) {
+        int q = pq[qi];
+        Q left = Qp[p][q]; /* >= 1 branch in [i, k-1] */
+        if (p < 6 && q < 6) left = qmin(left, qadd(un, Cu[p][q])); /* [i, k-1] unpaired */
+        for (int b = 0; b < c->M[k]; b++) {
+          Q t = qadd(left, c->X[k - 1][q][b + 6]);
+          for (int si = 0; si < nj; si++) QM[p][pj[si]] = qmin(QM[p][pj[si]], qadd(t, Qk[b][pj[si]]));
+        }
+      }
+    }
+  }
+}
+
+static void m_qm2(mctx *c, int i, int j) {
+  Q(*Q2)[NPT] = c->QM2[mtri(c, i, j)];
+  int pi_[NPT], pj[NPT];
+  int ni = ports_of_m(c->M[i], pi_), nj = ports_of_m(c->M[j], pj);
+  for (int k = i + 5; k <= j - 4; k++) {
+    const Q(*Qp)[NPT] = c->QM[mtri(c, i, k - 1)];
+    const Q(*Qk)[NPT] = c->QM1[mtri(c, k, j)];
+    int pq[NPT];
+    int nq = ports_of_m(c->M[k - 1], pq);
+    for (int ri = 0; ri < ni; ri++)
+      for (int qi = 0; qi < nq; qi++)
+        for (int b = 0; b < c->M[k]; b++) {
+          Q t = qadd(Qp[pi_[ri]][pq[qi]], c->X[k - 1][pq[qi]][b + 6]);
+          for (int si = 0; si < nj; si++) Q2[pi_[ri]][pj[si]] = qmin(Q2[pi_[ri]][pj[si]], qadd(t, Qk[b][pj[si]]));
+        }
+  }
+}
+
+static void m_exterior(mctx *c) {
+  int n = c->n;
+  for (int a = 0; a < c->M[0]; a++) c->Q5[0][a][a] = 0;
+  for (int j = 1; j < n; j++) {
+    Q(*Q5j)[NPT] = c->Q5[j];
+    int pp[NPT];
+    int np = ports_of_m(c->M[j - 1], pp);
+    for (int a = 0; a < c->M[0]; a++)
+      for (int b = 0; b < c->M[j]; b++)
+        for (int qi = 0; qi < np; qi++)
+          Q5j[a][b] = qmin(Q5j[a][b], qadd(c->Q5[j - 1][a][pp[qi]], c->X[j - 1][pp[qi]][b]));
+    const Q(*QB0)[NS] = c->QB[mtri(c, 0, j)];
+    for (int a = 0; a < c->M[0]; a++)
+      for (int b = 0; b < c->M[j]; b++) Q5j[a][b + 6] = qmin(Q5j[a][b + 6], QB0[a][b]);
+    for (int k = 1; k <= j - 4; k++) {
+      int pq[NPT];
+      int nq = ports_of_m(c->M[k - 1], pq);
+      const Q(*QBk)[NS] = c->QB[mtri(c, k, j)];
+      for (int a = 0; a < c->M[0]; a++)
+        for (int qi = 0; qi < nq; qi++)
+          for (int s = 0; s < c->M[k]; s++) {
+            Q t = qadd(c->Q5[k - 1][a][pq[qi]], c->X[k - 1][pq[qi]][s + 6]);
+            for (int b = 0; b < c->M[j]; b++) Q5j[a][b + 6] = qmin(Q5j[a][b + 6], qadd(t, QBk[s][b]));
+          }
+    }
+  }
+  Q best = QINF;
+  int pp[NPT];
+  int np = ports_of_m(c->M[n - 1], pp);
+  for (int a = 0; a < c->M[0]; a++)
+    for (int qi = 0; qi < np; qi++) best = qmin(best, qadd(c->u0[a], c->Q5[n - 1][a][pp[qi]]));
+  c->mfe = best;
+}
+
+static void m_inside(mctx *c) {
+  int n = c->n;
+  for (int d = 0; d < n; d++) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int i = 0; i < n - d; i++) {
+      int j = i + d;
+      m_chain(c, i, j);
+      if (d >= 4) {
+        m_qb(c, i, j);
+        m_xi(c, i, j);
+        m_qm1(c, i, j);
+        m_qm(c, i, j);
+        if (d >= 9) m_qm2(c, i, j);
+      }
+    }
+  }
+  m_exterior(c);
+}
+
+/* ---------------------------------------------------------------- MFE traceback
+ * Follows the recursions back from the minimum: at every table entry the
+ * first alternative (in the order each routine states) whose cost equals the
+ * entry is taken.  Costs are exact integers, so the equality test is exact.
+ * Writes the codon state of every position and the pairing partner. */
+
+typedef struct {
+  mctx *c;
+  int *state, *partner;
+  int err;
+} mtrace;
+
+static void mt_state(mtrace *t, int p, int a) {
+  if (t->state[p] >= 0 && t->state[p] != a) t->err = 2;
+  t->state[p] = a;
+}
+
+static void mt_chain(mtrace *t, int x, int y, int a, int b) {
+  mctx *c = t->c;
+  mt_state(t, x, a);
+  int cur = a;
+  for (int p = x; p < y; p++) {
+    Q want = c->C[mtri(c, p, y)][cur][b];
+    int nxt = -1;
+    for (int s = 0; s < c->M[p + 1] && nxt < 0; s++)
+      if (qadd(c->T[p][cur][s], c->C[mtri(c, p + 1, y)][s][b]) == want) nxt = s;
+    if (nxt < 0) {
+      t->err = 3;
+      return;
+    }
+    cur = nxt;
+    mt_state(t, p + 1, cur);
+  }
+}
+
+static void mt_qb(mtrace *t, int i, int j, int a, int b);
+static void mt_qm(mtrace *t, int i, int j, int p1, int p2);
+
+static void mt_qm1(mtrace *t, int i, int j, int a, int p2) {
+  mctx *c = t->c;
+  if (p2 >= 6) { /* the branch ends at j */
+    mt_qb(t, i, j, a, p2 - 6);
+    return;
+  }
+  Q want = c->QM1[mtri(c, i, j)][a][p2];
+  /* branch (i, l) then j - l unpaired: l ascending, state s at l, e at l+1 */
+  for (int l = i + 4; l <= j - 1; l++) {
+    Q w = c->cc + (Q)(j - l) * c->cb;
+    for (int s = 0; s < c->M[l]; s++)
+      for (int e = 0; e < c->M[l + 1]; e++)
+        if (qadd(qadd(w, c->QB[mtri(c, i, l)][a][s]), qadd(c->X[l][s + 6][e], c->C[mtri(c, l + 1, j)][e][p2])) ==
+            want) {
+          mt_qb(t, i, l, a, s);
+          mt_chain(t, l + 1, j, e, p2);
+          return;
+        }
+  }
+  t->err = 4;
+}
+
+static void mt_qm2(mtrace *t, int i, int j, int p1, int p2) {
+  mctx *c = t->c;
+  Q want = c->QM2[mtri(c, i, j)][p1][p2];
+  /* last branch starts at k (ascending), port q at k-1, state b at k */
+  for (int k = i + 5; k <= j - 4; k++) {
+    int pq[NPT];
+    int nq = ports_of_m(c->M[k - 1], pq);
+    for (int qi = 0; qi < nq; qi++)
+      for (int b = 0; b < c->M[k]; b++)
+        if (qadd(qadd(c->QM[mtri(c, i, k - 1)][p1][pq[qi]], c->X[k - 1][pq[qi]][b + 6]),
+                 c->QM1[mtri(c, k, j)][b][p2]) == want) {
+          mt_qm(t, i, k - 1, p1, pq[qi]);
+          mt_qm1(t, k, j, b, p2);
+          return;
+        }
+  }
+  t->err = 5;
+}
+
+static void mt_qm(mtrace *t, int i, int j, int p1, int p2) {
+  mctx *c = t->c;
+  Q want = c->QM[mtri(c, i, j)][p1][p2];
+  if (p1 >= 6 && c->QM1[mtri(c, i, j)][p1 - 6][p2] == want) { /* one branch starting at i */
+    mt_qm1(t, i, j, p1 - 6, p2);
+    return;
+  }
+  /* k ascending; port q at k-1; prefix [i, k-1] unpaired, then with >= 1 branch; state b at k */
+  for (int k = i + 1; k <= j - 4; k++) {
+    int pq[NPT];
+    int nq = ports_of_m(c->M[k - 1], pq);
+    Q un = (Q)(k - i) * c->cb;
+    for (int qi = 0; qi < nq; qi++)
+      for (int kind = 0; kind < 2; kind++) {
+        Q left;
+        if (kind == 0) left = (p1 < 6 && pq[qi] < 6) ? qadd(un, c->C[mtri(c, i, k - 1)][p1][pq[qi]]) : QINF;
+        else left = c->QM[mtri(c, i, k - 1)][p1][pq[qi]];
+        for (int b = 0; b < c->M[k]; b++)
+          if (qadd(qadd(left, c->X[k - 1][pq[qi]][b + 6]), c->QM1[mtri(c, k, j)][b][p2]) == want) {
+            if (kind == 0) mt_chain(t, i, k - 1, p1, pq[qi]);
+            else mt_qm(t, i, k - 1, p1, pq[qi]);
+            mt_qm1(t, k, j, b, p2);
+            return;
+          }
+      }
+  }
+  t->err = 6;
+}
+
+static void mt_qb(mtrace *t, int i, int j, int a, int b) {
+  mctx *c = t->c;
+  int Mx = c->M[i + 1], My = c->M[j - 1];
+  Q want = c->QB[mtri(c, i, j)][a][b];
+  t->partner[i] = j;
+  t->partner[j] = i;
+  mt_state(t, i, a);
+  mt_state(t, j, b);
+  int x = i + 1, y = j - 1;
+  /* 1. hairpin, then interior loops (l1, l2 as in m_inner), over (u, v) ascending */
+  for (int u = 0; u < Mx; u++)
+    for (int v = 0; v < My; v++) {
+      Q outer = qadd(qadd(c->T[i][a][u], c->T[j - 1][v][b]), m_tmo(c, x, u, y, v));
+      if (outer >= QINF) continue;
+      if (qadd(outer, qadd(m_hairpin(c, j - i - 1), c->C[mtri(c, x, y)][u][v])) == want) {
+        mt_chain(t, x, y, u, v);
+        return;
+      }
+      for (int l1 = 1; l1 <= MAXLOOP; l1++)
+        for (int l2 = 1; l1 + l2 <= MAXLOOP; l2++) {
+          int k = i + 1 + l1, l = j - 1 - l2;
+          if (l - k < 4) continue;
+          for (int w2 = 0; w2 < c->M[k - 1]; w2++)
+            for (int z = 0; z < c->M[l + 1]; z++) {
+              Q v2 = qadd(qadd(c->In[l1 + l2], c->C[mtri(c, x, k - 1)][u][w2]),
+                          qadd(c->XI[mtri(c, k, l)][w2][z], c->C[mtri(c, l + 1, y)][z][v]));
+              if (qadd(outer, v2) != want) continue;
+              /* the inner pair (k, l): states a2 at k, b2 at l */
+              const Q xi = qadd(c->XI[mtri(c, k, l)][w2][z], 0);
+              for (int a2 = 0; a2 < c->M[k]; a2++)
+                for (int b2 = 0; b2 < c->M[l]; b2++)
+                  if (qadd(qadd(c->T[k - 1][w2][a2], c->QB[mtri(c, k, l)][a2][b2]),
+                           qadd(c->T[l][b2][z], m_tmi(c, k, w2, l, z))) == xi) {
+                    mt_chain(t, x, k - 1, u, w2);
+                    mt_chain(t, l + 1, y, z, v);
+                    mt_qb(t, k, l, a2, b2);
+                    return;
+                  }
+              t->err = 7;
+              return;
+            }
+        }
+    }
+  /* 2. stack: states (a2, b2) ascending */
+  if (j - i - 2 >= 4)
+    for (int a2 = 0; a2 < Mx; a2++)
+      for (int b2 = 0; b2 < My; b2++)
+        if (qadd(qadd(c->T[i][a][a2], c->QB[mtri(c, i + 1, j - 1)][a2][b2]),
+                 qadd(c->T[j - 1][b2][b], m_stack(c, i, a, j, b, a2, b2))) == want) {
+          mt_qb(t, i + 1, j - 1, a2, b2);
+          return;
+        }
+  /* 3. bulges: L ascending, the 3' bulge before the 5' bulge */
+  for (int L = 1; L <= MAXLOOP; L++) {
+    int l = j - 1 - L;
+    if (l - (i + 1) >= 4)
+      for (int a2 = 0; a2 < Mx; a2++)
+        for (int s = 0; s < c->M[l]; s++)
+          if (qadd(qadd(c->Bu[L], c->T[i][a][a2]), qadd(c->QB[mtri(c, i + 1, l)][a2][s], c->C[mtri(c, l, j)][s][b])) ==
+              want) {
+            mt_qb(t, i + 1, l, a2, s);
+            mt_chain(t, l, j, s, b);
+            return;
+          }
+    int k = i + 1 + L;
+    if ((j - 1) - k >= 4)
+      for (int s = 0; s < c->M[k]; s++)
+        for (int b2 = 0; b2 < My; b2++)
+          if (qadd(qadd(c->Bu[L], c->C[mtri(c, i, k)][a][s]), qadd(c->QB[mtri(c, k, j - 1)][s][b2], c->T[j - 1][b2][b])) ==
+              want) {
+            mt_chain(t, i, k, a, s);
+            mt_qb(t, k, j - 1, s, b2);
+            return;
+          }
+  }
+  /* 4. multiloop: ports at i+1 and j-1 in port order */
+  if (j - i - 2 >= 9) {
+    int px[NPT], py[NPT];
+    int nx = ports_of_m(Mx, px), ny = ports_of_m(My, py);
+    Q w = qadd(c->ca, c->cc);
+    for (int pi = 0; pi < nx; pi++)
+      for (int qi = 0; qi < ny; qi++)
+        if (qadd(qadd(w, c->X[i][a + 6][px[pi]]),
+                 qadd(c->QM2[mtri(c, x, y)][px[pi]][py[qi]], c->X[j - 1][py[qi]][b + 6])) == want) {
+          mt_state(t, x, px[pi] % 6);
+          mt_state(t, y, py[qi] % 6);
+          mt_qm2(t, x, y, px[pi], py[qi]);
+          return;
+        }
+  }
+  t->err = 8;
+}
+
+static void mt_ext(mtrace *t, int j, int a0, int port) {
+  mctx *c = t->c;
+  if (j == 0) {
+    mt_state(t, 0, a0);
+    if (port != a0) t->err = 9;
+    return;
+  }
+  Q want = c->Q5[j][a0][port];
+  int pp[NPT];
+  int np = ports_of_m(c->M[j - 1], pp);
+  if (port < 6) { /* j unpaired: port at j-1 in port order */
+    for (int qi = 0; qi < np; qi++)
+      if (qadd(c->Q5[j - 1][a0][pp[qi]], c->X[j - 1][pp[qi]][port]) == want) {
+        mt_state(t, j, port);
+        mt_ext(t, j - 1, a0, pp[qi]);
+        return;
+      }
+    t->err = 10;
+    return;
+  }
+  int b = port - 6;
+  if (c->QB[mtri(c, 0, j)][a0][b] == want) { /* a branch (0, j) */
+    mt_qb(t, 0, j, a0, b);
+    return;
+  }
+  for (int k = 1; k <= j - 4; k++) { /* last branch (k, j): k ascending, port at k-1, state at k */
+    int pq[NPT];
+    int nq = ports_of_m(c->M[k - 1], pq);
+    for (int qi = 0; qi < nq; qi++)
+      for (int s = 0; s < c->M[k]; s++)
+        if (qadd(qadd(c->Q5[k - 1][a0][pq[qi]], c->X[k - 1][pq[qi]][s + 6]), c->QB[mtri(c, k, j)][s][b]) == want) {
+          mt_qb(t, k, j, s, b);
+          mt_ext(t, k - 1, a0, pq[qi]);
+          return;
+        }
+  }
+  t->err = 11;
+}
+
+/* MFE of (codon sequence, structure): *mfe_q = the minimum in units of 2^-32
+ * kcal/mol (QINF if no configuration exists), *mfe_kcal the same in kcal/mol;
+ * codons[m] (sense codon ids) and partner[n] (-1 unpaired) of one minimiser,
+ * either may be NULL.  Returns 0, OR_EINVAL, OR_ENOMEM, or 100 + a traceback
+ * inconsistency code. */
+int or_mfe(const double *params, const int *res, int m, const double *lw, const double *pb, long long *mfe_q,
+           double *mfe_kcal, int *codons, int *partner) {
   if (m < 1) return OR_EINVAL;
-  octx c;
-  int rc = setup(&c, params, res, m, lw, pb, NULL, 0);
+  mctx c;
+  int rc = m_setup(&c, params, res, m, lw, pb);
   if (rc) {
-    free_ctx(&c);
+    m_free(&c);
     return rc == -1 ? OR_EINVAL : OR_ENOMEM;
   }
-  inside(&c);
-  int n = c.n;
-  for (int i = 0; i < n; i++)
-    for (int j = 0; j < n; j++) {
-      R mx = 0;
-      if (j >= i) {
-        const R(*Q)[NS] = c.QB[tri(&c, i, j)];
-        for (int a = 0; a < c.M[i]; a++)
-          for (int b = 0; b < c.M[j]; b++)
-            if (Q[a][b] > mx) mx = Q[a][b];
-      }
-      out[(size_t)i * n + j] = mx > 0 ? (double)logl(mx) : -INFINITY;
-    }
-  free_ctx(&c);
-  return OR_OK;
+  m_inside(&c);
+  *mfe_q = c.mfe;
+  *mfe_kcal = (double)c.mfe / 4294967296.0;
+  int err = 0;
+  if (codons || partner) {
+    int n = c.n;
+    int *state = malloc(n * sizeof(int)), *pt = malloc(n * sizeof(int));
+    for (int p = 0; p < n; p++) state[p] = pt[p] = -1;
+    mtrace t = {&c, state, pt, 0};
+    int done = 0;
+    int pp[NPT];
+    int np = ports_of_m(c.M[n - 1], pp);
+    for (int a = 0; a < c.M[0] && !done; a++)
+      for (int qi = 0; qi < np && !done; qi++)
+        if (qadd(c.u0[a], c.Q5[n - 1][a][pp[qi]]) == c.mfe) {
+          mt_ext(&t, n - 1, a, pp[qi]);
+          done = 1;
+        }
+    if (!done) t.err = 12;
+    for (int p = 0; p < n && !t.err; p++)
+      if (state[p] < 0) t.err = 13;
+    if (codons)
+      for (int r = 0; r < m; r++) codons[r] = t.err ? -1 : c.cid[3 * r][state[3 * r]];
+    if (partner)
+      for (int p = 0; p < n; p++) partner[p] = pt[p];
+    err = t.err;
+    free(state);
+    free(pt);
+  }
+  m_free(&c);
+  return err ? 100 + err : OR_OK;
 }

@@ -59,6 +59,15 @@ def _load() -> ctypes.CDLL:
     lib.cf_surrogate_train_step.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_float, vp]
     lib.cf_surrogate_last_ms.argtypes = [vp]
     lib.cf_surrogate_last_ms.restype = ctypes.c_float
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.cf_far_band_info.argtypes = [vp, ip, ip, ip, ip]
+    lib.cf_debug_set_wait_polls.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
+    lib.cf_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+    lib.cf_debug_classify_pointer.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.cf_debug_classify_pointer.restype = ctypes.c_int
+    lib.cf_sample_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
+    for name in ("cf_far_band_info", "cf_debug_set_wait_polls", "cf_debug_fail_alloc", "cf_sample_noalloc"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("cf_surrogate_create", "cf_surrogate_free", "cf_surrogate_set_params", "cf_surrogate_get_params",
                  "cf_surrogate_predict", "cf_surrogate_grad", "cf_surrogate_train_step"):
         getattr(lib, name).restype = ctypes.c_int
@@ -205,10 +214,31 @@ def cf_surrogate_last_ms(sur) -> float:
 def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:
     """Sampler for callers that cannot allocate device memory: outputs must be
     device tensors; scratch comes from the library's static device array."""
-    f = lib.cf_sample_noalloc
-    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
-    f.restype = ctypes.c_int
-    _check(f(prob, int(nsamples), ctypes.c_uint64(seed), _ptr(codons), _ptr(partner)), prob)
+    _check(lib.cf_sample_noalloc(prob, int(nsamples), ctypes.c_uint64(seed), _ptr(codons), _ptr(partner)), prob)
+
+
+def cf_far_band_info(prob):
+    """(inside largest chord departure, inside bands summed term by term,
+    outside largest departure, outside gathered term by term) of the last
+    binary32 passes."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib.cf_far_band_info(prob, *[ctypes.byref(x) for x in v]), prob)
+    return tuple(x.value for x in v)
+
+
+def cf_debug_set_wait_polls(device: int, polls: int) -> None:
+    _check(lib.cf_debug_set_wait_polls(int(device), ctypes.c_ulonglong(polls)))
+
+
+def cf_debug_fail_alloc(after: int) -> None:
+    _check(lib.cf_debug_fail_alloc(int(after)))
+
+
+def cf_debug_classify_pointer(memory_type: int, pointer_device: int, problem_device: int) -> int:
+    return int(lib.cf_debug_classify_pointer(int(memory_type), int(pointer_device), int(problem_device)))
+
+
+WAIT_POLLS_DEFAULT = 1 << 22
 
 
 # ---------------------------------------------------------------- convenience

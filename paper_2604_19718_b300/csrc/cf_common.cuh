@@ -309,12 +309,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
-// Bounded wait for a phase of the mbarrier (about a second of polling).  On
-// timeout bit 8 of the error word is set and false is returned; the copies
-// that were in flight are then waited for once more, again bounded.
+// Polls of the first wait of mbar_wait before it gives up (about a second at
+// the default).  A test lowers it (cf_debug_set_wait_polls) to make every
+// wait give up at once; the drain wait after a timeout keeps its full length,
+// so the copies in flight still land before the CTA exits.
+static __device__ unsigned long long g_cf_wait_polls = 1ull << 22;
+
+// Bounded wait for a phase of the mbarrier.  On timeout bit 8 of the error
+// word is set and false is returned; the copies that were in flight are then
+// waited for once more, again bounded.
 constexpr int ERR_STAGE_TIMEOUT = 8;
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err) {
-  for (unsigned long long it = 0; it < (1ull << 22); it++) {
+  const unsigned long long polls = *(volatile unsigned long long *)&g_cf_wait_polls;
+  for (unsigned long long it = 0; it < polls; it++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(128);
   }

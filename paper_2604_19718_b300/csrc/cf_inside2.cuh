@@ -42,6 +42,7 @@ struct BifBuf {
   float *far;     // [2][n][FARD][farslices][36] far split points of a band, per slice (binary32; nullptr: none)
   int farslices;  // slices per cell in the far buffer
   float *gfac;    // [2][n] far-band rescale factors 2^{E[a] - s a - e0} per band parity (binary32)
+  int *gdev;      // [n / FARD + 1] per band: ceil(max over a of |E[a] - s a - e0|), written by k_in_far_factors
   const T **stab; // [n][SI_N] source of every staged slot of the light cell x = 0 of each diagonal
   T **dtab;       // [n][NCOPY] destination of every result of that cell
 };
@@ -60,7 +61,17 @@ struct BifBuf {
 // 2^{s d + 2 e0}.  Each CTA of k_in_far sums one slice of split points and
 // stores it; the per-diagonal kernel adds the slices in order, so the result
 // does not depend on which slice ran first.
+// The chord is exact only where E is close to linear.  A protein whose
+// composition changes along its length bends E (the best interval of a given
+// length moves between regions of different strength), and a factor
+// 2^{E[a] - s a - e0} far from one would overflow binary32 or flush the terms
+// to zero.  So the factor kernel of each band records the largest deviation
+// |E[a] - s a - e0| over the band's split points; past FAR_DEV_MAX (log2) the
+// band is not summed in tiles: k_in_far returns at once and the per-diagonal
+// kernel takes every split point itself, each term with its own exact
+// power-of-two factor (slower, never wrong).
 constexpr int FARD = 16;   // diagonals per band
+constexpr int FAR_DEV_MAX = 48;  // largest |log2 factor| of a tiled band: a product of two stays within 2^{+-96}
 constexpr int FARTX = 16;  // rows per far tile
 constexpr int FARKC = 8;   // split points staged per step
 constexpr int FARKS = 64;   // split points per CTA slice
@@ -280,7 +291,8 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
   const int Eref = __ldcg(p.E + d - 4);
   const int slot = d % BIFRING;
   const int d0 = d / FARD * FARD;
-  const bool banded = bb.far != nullptr && far_band(d0);
+  // a band whose exponent chord bends too far is summed here in full
+  const bool banded = bb.far != nullptr && far_band(d0) && __ldcg(bb.gdev + d0 / FARD) <= FAR_DEV_MAX;
   int a1 = d - 4, a2 = d - 3;
   if (banded) {
     const int c = far_c(d0), alo = max(5, d - c), ahi = min(c, d - 4);
@@ -583,13 +595,24 @@ __device__ __forceinline__ T row_absmax(const T (&r)[NS]) {
 // block; the linear-exponent factors of both halves are applied as the
 // blocks are used.  The slice's sums go to their own place in the band buffer.
 // the rescale factors of band d0, once per band (binary64 exp2: the
-// exponents reach the thousands)
+// exponents reach the thousands), and the band's largest deviation from the
+// chord over its split points a = 5..c; one CTA
 __global__ void k_in_far_factors(DP<float> p, BifBuf<float> bb, int d0) {
+  __shared__ int sdev;
   const int c = far_c(d0);
   const FarChord ch = far_chord(p.E, c);
   float *dst = bb.gfac + (size_t)((d0 / FARD) & 1) * p.n;
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a <= c; a += gridDim.x * blockDim.x)
-    dst[a] = (float)exp2((double)__ldcg(p.E + a) - ch.s * a - ch.e0);
+  if (threadIdx.x == 0) sdev = 0;
+  __syncthreads();
+  int dev = 0;
+  for (int a = threadIdx.x; a <= c; a += blockDim.x) {
+    const double z = (double)__ldcg(p.E + a) - ch.s * a - ch.e0;
+    dst[a] = (float)exp2(z);
+    if (a >= 5) dev = max(dev, (int)ceil(fabs(z)));
+  }
+  atomicMax(&sdev, dev);
+  __syncthreads();
+  if (threadIdx.x == 0) bb.gdev[d0 / FARD] = sdev;
 }
 
 __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, int d0) {
@@ -604,6 +627,7 @@ __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, i
   const int kbeg = far_kmin(x0) + blockIdx.y * FARKS;
   const int kend = min(far_kmax(n, x0, d0), kbeg + FARKS - 1);
   if (kbeg > kend) return;
+  if (__ldcg(bb.gdev + d0 / FARD) > FAR_DEV_MAX) return;  // summed by the per-diagonal kernel
   const float *gsrc = bb.gfac + (size_t)((d0 / FARD) & 1) * n;
   for (int a = t; a <= c; a += 256) gf[a] = __ldcg(gsrc + a);
   if (t == 0) {

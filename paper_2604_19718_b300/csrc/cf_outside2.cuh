@@ -38,6 +38,7 @@ struct OutBuf {
   T *hgx;  // [BIFRING][36]    exterior gather hGx[d]
   float *far;  // [2 gathers][3 slots][n][OFD][36] far terms of a band (binary32; nullptr: none)
   float *fwh;      // [2][n] far-band rescale factors 2^{E[D] - s D - e0} and their inverses (binary32)
+  int *fdev;       // [1] ceil(max over D of |E[D] - s D - e0|), written by k_out_far_factors
   OSlot<T> *otab;  // [n][SO_N] sources of the light kernel's staged slots per diagonal
   const T **stab;  // [n][SS_N] sources of the side work's staged slots for cell x = 0 (nullptr: not staged)
 };
@@ -53,7 +54,10 @@ struct OutBuf {
 // Far blocks are rescaled to a linear exponent with the chord s, e0 of E over
 // diagonals 5 .. n-1: forward blocks by 2^{E[D] - s D - e0}, adjoint blocks by
 // 2^{s D + e0 - E[D]}; every far term of a target on diagonal a is then
-// relative to the common factor ec 2^{E[a] - s a}.
+// relative to the common factor ec 2^{E[a] - s a}.  As for the inside far
+// bands, the factor kernel records the largest deviation of E from the chord;
+// past FAR_DEV_MAX no band of the pass is tiled (k_out_far returns at once)
+// and the per-diagonal gathers take every term with its exact factor.
 constexpr int OFD = 16;   // target diagonals per band
 constexpr int OFTX = 16;  // target rows per tile
 constexpr int OFKC = 4;   // summation indices staged per step
@@ -220,7 +224,7 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
   const int slot = d % BIFRING;
   const T ec = p.en[EN_EC];
   const int alo = d / OFD * OFD;
-  const bool banded = ob.far != nullptr && of_band(n, alo);
+  const bool banded = ob.far != nullptr && of_band(n, alo) && __ldcg(ob.fdev) <= FAR_DEV_MAX;
   if (cb0 + g < ncell) {
     const int x = cb0 + g, y = x + d;
     const int Ma = p.Mp[x], Mb = p.Mp[y];
@@ -287,14 +291,23 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
 // bulk copies into two alternating stages; each CTA takes a slice of OFKS
 // summation indices and adds its sums into the band buffer (zeroed first).
 // the rescale factors of every far band of the pass (one chord over diagonals
-// 5..n-1), once per pass (binary64 exp2: the exponents reach the thousands)
+// 5..n-1), once per pass (binary64 exp2: the exponents reach the thousands),
+// and the largest deviation from the chord; one CTA
 __global__ void k_out_far_factors(DP<float> p, OutBuf<float> ob) {
+  __shared__ int sdev;
   const OChord ch = of_chord(p.E, p.n);
-  for (int D = blockIdx.x * blockDim.x + threadIdx.x; D < p.n; D += gridDim.x * blockDim.x) {
+  if (threadIdx.x == 0) sdev = 0;
+  __syncthreads();
+  int dev = 0;
+  for (int D = threadIdx.x; D < p.n; D += blockDim.x) {
     const double z = (double)p.E[D] - ch.s * D - ch.e0;
     ob.fwh[D] = (float)exp2(z);
     ob.fwh[p.n + D] = (float)exp2(-z);
+    if (D >= 5) dev = max(dev, (int)ceil(fabs(z)));
   }
+  atomicMax(&sdev, dev);
+  __syncthreads();
+  if (threadIdx.x == 0) *ob.fdev = sdev;
 }
 
 template <bool ROW>
@@ -311,6 +324,7 @@ __global__ void __launch_bounds__(256) k_out_far(DP<float> p, OutBuf<float> ob, 
   const int lo = ROW ? x0 + c : 0, hi = ROW ? n - 1 : x0 + OFTX - 1 + alo + OFD - 1 - c;
   const int kbeg = lo + blockIdx.y * OFKS, kend = min(hi, kbeg + OFKS - 1);
   if (kbeg > kend) return;
+  if (__ldcg(ob.fdev) > FAR_DEV_MAX) return;  // every term is gathered per diagonal
   for (int D = t; D < n; D += 256) {
     fw[D] = __ldcg(ob.fwh + D);
     fh[D] = __ldcg(ob.fwh + n + D);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -187,8 +188,16 @@ cf_status cuda_fail(cf_problem *p, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
   } while (0)
 
+// Test hook (cf_debug_fail_alloc): the number of further device allocations
+// that succeed before one is made to fail; negative = off.
+std::atomic<long long> g_fail_alloc_after{-1};
+
 template <typename V>
 cudaError_t dalloc(std::vector<void *> &list, V **ptr, size_t count) {
+  long long k = g_fail_alloc_after.load();
+  while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 0) return cudaErrorMemoryAllocation;  // forced failure, nothing allocated
   void *q = nullptr;
   cudaError_t e = cudaMalloc(&q, count * sizeof(V));
   if (e != cudaSuccess) return e;
@@ -211,6 +220,26 @@ void free_prec(PrecTables<T> &t) {
   free_list(t.allocs);
   t.inside_alloc = t.outside_alloc = false;
   t.dp = DP<T>{};
+}
+
+// Where a caller's buffer lives, seen from a problem on `device`: 0 host
+// memory (pageable or pinned), 1 device memory the problem's kernels may read
+// and write (memory of that device, or managed memory), -1 device memory of
+// another device (rejected: a kernel of this problem must not touch it).
+int classify_ptr(int type, int ptr_device, int device) {
+  if (type == cudaMemoryTypeManaged) return 1;
+  if (type == cudaMemoryTypeDevice) return ptr_device == device ? 1 : -1;
+  return 0;
+}
+
+int ptr_kind(const void *ptr, int device) {
+  if (!ptr) return 0;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return classify_ptr((int)a.type, a.device, device);
 }
 
 bool is_device_ptr(const void *ptr) {
@@ -277,9 +306,12 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   t.bb.far = nullptr;
   t.bb.farslices = far_nslice(n, 0, std::max(0, (n - 1) / FARD * FARD));  // the widest band's slices
   t.bb.gfac = nullptr;
+  t.bb.gdev = nullptr;
   if (sizeof(T) == sizeof(float) && n > 3 * FARD) {
     CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
     CF_CUDA(p, dalloc(L, &t.bb.gfac, (size_t)2 * n));
+    CF_CUDA(p, dalloc(L, &t.bb.gdev, (size_t)n / FARD + 1));
+    CF_CUDA(p, cudaMemset(t.bb.gdev, 0, ((size_t)n / FARD + 1) * sizeof(int)));
   }
   const T **stab = nullptr;
   CF_CUDA(p, dalloc(L, &stab, (size_t)n * SI_N));
@@ -364,8 +396,8 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
       // far kernel two bands back (same factor buffer)
       cudaKernelNodeParams kq = {};
       kq.func = (void *)k_in_far_factors;
-      kq.gridDim = dim3((far_c(d0) + 256) / 256);
-      kq.blockDim = dim3(256);
+      kq.gridDim = dim3(1);
+      kq.blockDim = dim3(512);
       kq.kernelParams = fargs;
       cudaGraphNode_t qdeps[2] = {k2[far_c(d0)], nullptr}, kfq;
       int nq = 1;
@@ -462,9 +494,12 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   CF_CUDA(p, dalloc(L, &t.ob.hgx, (size_t)BIFRING * BLK));
   t.ob.far = nullptr;
   t.ob.fwh = nullptr;
+  t.ob.fdev = nullptr;
   if (sizeof(T) == sizeof(float) && of_band(n, 0)) {
     CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
     CF_CUDA(p, dalloc(L, &t.ob.fwh, (size_t)2 * n));
+    CF_CUDA(p, dalloc(L, &t.ob.fdev, (size_t)1));
+    CF_CUDA(p, cudaMemset(t.ob.fdev, 0, sizeof(int)));
   }
   CF_CUDA(p, dalloc(L, &t.ob.otab, (size_t)n * SO_N));
   const T **sstab = nullptr;
@@ -540,8 +575,8 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     void *qargs[] = {&dpf, &obf};
     cudaKernelNodeParams kq = {};
     kq.func = (void *)k_out_far_factors;
-    kq.gridDim = dim3((n + 255) / 256);
-    kq.blockDim = dim3(256);
+    kq.gridDim = dim3(1);
+    kq.blockDim = dim3(512);
     kq.kernelParams = qargs;
     e = cudaGraphAddKernelNode(&first, g, &m[4], 1, &kq);
     nodes++;
@@ -680,7 +715,10 @@ cf_status clear_tables(cf_problem *p, PrecTables<T> &t);
 template <typename T>
 cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   cf_status s = alloc_inside(p, t);
-  if (s != CF_OK) return s;
+  if (s != CF_OK) {
+    free_prec(t);  // a failed allocation leaves no partial tables: the next call starts over
+    return s;
+  }
   const int n = p->n;
   cudaStream_t st = p->stream;
   s = build_inside_graph(p, t);
@@ -716,13 +754,20 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
 template <typename T>
 cf_status run_outside(cf_problem *p, PrecTables<T> &t) {
   cf_status s = alloc_outside(p, t);
-  if (s != CF_OK) return s;
+  if (s != CF_OK) {
+    // the outside tables share the precision's allocation list: release it
+    // whole, and the inside results with it
+    free_prec(t);
+    p->have_inside = false;
+    return s;
+  }
   const int n = p->n;
   const size_t nc = ncells(n) * BLK;
   DP<T> &d = t.dp;
   cudaStream_t st = p->stream;
   s = build_outside_graph(p, t);
   if (s != CF_OK) return s;
+  CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));  // the inside pass has read its flags
   CF_CUDA(p, cudaEventRecord(p->ev[2], st));
   CF_CUDA(p, cudaGraphLaunch(t.gout, st));
   int launches = t.gout_nodes;
@@ -749,16 +794,24 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
   const size_t need_stack = (size_t)warps * (n + 64), need_state = (size_t)warps * n;
   if (p->smp_cap < (size_t)warps) {
     free_list(p->smp_allocs);
+    p->smp_cap = 0;  // stays 0 if an allocation below fails
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_stack, need_stack));
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_state, need_state));
     CF_CUDA(p, dalloc(p->smp_allocs, &p->smp_err, (size_t)1));
     p->smp_cap = warps;
   }
-  const bool dc = is_device_ptr(codons), dpn = is_device_ptr(partner);
+  const int kc = ptr_kind(codons, p->device), kp = ptr_kind(partner, p->device);
+  if (kc < 0 || kp < 0) return fail(p, CF_EINVAL, "cf_sample: output is device memory of another device");
+  const bool dc = kc > 0, dpn = kp > 0;
   int32_t *ocod = codons, *opar = partner;
   std::vector<void *> tmp;
-  if (!dc) CF_CUDA(p, dalloc(tmp, &ocod, (size_t)ns * m));
-  if (!dpn) CF_CUDA(p, dalloc(tmp, &opar, (size_t)ns * n));
+  cudaError_t ea = cudaSuccess;
+  if (!dc) ea = dalloc(tmp, &ocod, (size_t)ns * m);
+  if (ea == cudaSuccess && !dpn) ea = dalloc(tmp, &opar, (size_t)ns * n);
+  if (ea != cudaSuccess) {
+    free_list(tmp);
+    return cuda_fail(p, ea, "cf_sample: output staging");
+  }
   CF_CUDA(p, cudaMemsetAsync(p->smp_err, 0, sizeof(int), st));
   SampleArgs<T> a;
   a.p = t.dp;
@@ -870,7 +923,10 @@ cf_status run_windows(cf_problem *p, const uint8_t *bases, const int64_t *offset
   cf_status s = window_tables(p);
   if (s != CF_OK) return s;
   cudaStream_t st = p->stream;
-  const bool off_dev = is_device_ptr(offsets), bases_dev = is_device_ptr(bases), out_dev = is_device_ptr(logz);
+  const int ko = ptr_kind(offsets, p->device), kb = ptr_kind(bases, p->device), kl = ptr_kind(logz, p->device);
+  if (ko < 0 || kb < 0 || kl < 0)
+    return fail(p, CF_EINVAL, "cf_window_logz: a buffer is device memory of another device");
+  const bool off_dev = ko > 0, bases_dev = kb > 0, out_dev = kl > 0;
   std::vector<int64_t> off((size_t)nwin + 1);
   if (off_dev) {
     CF_CUDA(p, cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, st));
@@ -1054,10 +1110,12 @@ cf_status cf_problem_free(cf_problem *p) {
   return CF_OK;
 }
 
+static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, const double *lw,
+                                    const double *pb);
+
 cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw, const double *pb) {
   if (!p || !aa) return fail(p, CF_EINVAL, "cf_set_protein: NULL argument");
   if (m < 1) return fail(p, CF_EINVAL, "cf_set_protein: m must be >= 1");
-  const GeneticCode &gc = gcode();
   std::vector<int> res(m);
   for (int r = 0; r < m; r++) {
     const char *q = std::strchr(kAminoAcids, aa[r]);
@@ -1066,6 +1124,22 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
   }
   if (check_weights(p, m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_protein: " + p->err);
   CF_CUDA(p, cudaSetDevice(p->device));
+  // past validation the old protein is gone: a failure below (an allocation
+  // that does not fit, a CUDA error) releases everything, so that the problem
+  // is empty and usable (the next cf_set_protein starts from scratch)
+  const cf_status s = set_protein_tables(p, res, lw, pb);
+  if (s != CF_OK) {
+    cudaStreamSynchronize(p->stream);
+    cudaGetLastError();
+    release_protein(p);
+  }
+  return s;
+}
+
+static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, const double *lw,
+                                    const double *pb) {
+  const int m = (int)res.size();
+  const GeneticCode &gc = gcode();
   // a protein of the same length reuses the device tables and the pass graphs
   // (they depend on the length only): no allocation, no device-wide sync
   const bool reuse = p->n == 3 * m && p->dM != nullptr;
@@ -1247,14 +1321,16 @@ cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
 
 // ------------------------------------------------------------------ no-allocation sampler
 // Static scratch of cf_sample_noalloc (see include/codonfold.h): error word,
-// codon ids per position, per-warp states and per-warp traceback stacks for
-// CF_NOALLOC_WARPS warps and sequences of up to CF_NOALLOC_MAX_N bases.
+// per-warp states and per-warp traceback stacks for CF_NOALLOC_WARPS warps and
+// sequences of up to CF_NOALLOC_MAX_N bases.  The codon ids of the positions
+// are read from the problem's own device copy.
 namespace {
 constexpr size_t kNaErrBytes = 256;
-constexpr size_t kNaCidBytes = ((size_t)CF_NOALLOC_MAX_N * NS * sizeof(int) + 255) / 256 * 256;
 constexpr size_t kNaStateBytes = ((size_t)CF_NOALLOC_WARPS * CF_NOALLOC_MAX_N * sizeof(int) + 255) / 256 * 256;
 constexpr size_t kNaStackBytes = (size_t)CF_NOALLOC_WARPS * (CF_NOALLOC_MAX_N + 64) * sizeof(int2);
-constexpr size_t kNaBytes = kNaErrBytes + kNaCidBytes + kNaStateBytes + kNaStackBytes;
+constexpr size_t kNaBytes = kNaErrBytes + kNaStateBytes + kNaStackBytes;
+static_assert(kNaBytes == CF_NOALLOC_SCRATCH_BYTES, "the header states the static scratch size");
+static_assert(sizeof(int2) == 8 && sizeof(int) == 4, "scratch layout");
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_cf_noalloc_scratch[kNaBytes];
@@ -1281,21 +1357,19 @@ cudaError_t noalloc_scratch(int device, unsigned char **out) {
 template <typename T>
 cf_status run_sample_noalloc(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int32_t *codons,
                              int32_t *partner) {
-  const int n = p->n;
   cudaStream_t st = p->stream;
   unsigned char *base = nullptr;
   CF_CUDA(p, noalloc_scratch(p->device, &base));
   int *err = (int *)base;
-  int *cid = (int *)(base + kNaErrBytes);
-  int *state = (int *)(base + kNaErrBytes + kNaCidBytes);
-  int2 *stack = (int2 *)(base + kNaErrBytes + kNaCidBytes + kNaStateBytes);
-  // the error word must start at zero; codon ids are rewritten for this protein
+  int *state = (int *)(base + kNaErrBytes);
+  int2 *stack = (int2 *)(base + kNaErrBytes + kNaStateBytes);
+  // the error word must start at zero (states and stacks are written before
+  // they are read by every sample)
   CF_CUDA(p, cudaMemsetAsync(err, 0, sizeof(int), st));
-  CF_CUDA(p, cudaMemcpyAsync(cid, p->cid.data(), sizeof(int) * (size_t)n * NS, cudaMemcpyHostToDevice, st));
   const int warps = std::min(ns, CF_NOALLOC_WARPS);
   SampleArgs<T> a;
   a.p = t.dp;
-  a.cid = cid;
+  a.cid = p->dcid;
   a.nsamples = ns;
   a.seed = seed;
   a.stack = stack;
@@ -1323,8 +1397,61 @@ extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t see
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample_noalloc: run cf_inside first");
   if (nsamples == 0) return CF_OK;
   CF_CUDA(p, cudaSetDevice(p->device));
-  if (!is_device_ptr(codons) || !is_device_ptr(partner))
-    return fail(p, CF_EINVAL, "cf_sample_noalloc: codons and partner must be device memory");
+  if (ptr_kind(codons, p->device) != 1 || ptr_kind(partner, p->device) != 1)
+    return fail(p, CF_EINVAL, "cf_sample_noalloc: codons and partner must be device memory of the problem's device");
   return (p->last_prec == CF_FP64) ? run_sample_noalloc(p, p->f64, nsamples, seed, codons, partner)
                                    : run_sample_noalloc(p, p->f32, nsamples, seed, codons, partner);
+}
+
+// ------------------------------------------------------------------ diagnostics and test hooks
+
+extern "C" cf_status cf_far_band_info(const cf_problem *p, int *in_max_dev, int *in_untiled, int *out_max_dev,
+                                      int *out_untiled) {
+  if (!p) return CF_EINVAL;
+  int idev = 0, iun = 0, odev = 0, oun = 0;
+  const PrecTables<float> &t = p->f32;
+  if (cudaSetDevice(p->device) != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: device not usable");
+  }
+  if (t.inside_alloc && t.bb.gdev) {
+    const int n = p->n;
+    std::vector<int> dev((size_t)n / FARD + 1, 0);
+    if (cudaMemcpy(dev.data(), t.bb.gdev, dev.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: copy");
+    for (int d0 = 0; d0 < n; d0 += FARD)
+      if (far_band(d0)) {
+        const int v = dev[(size_t)d0 / FARD];
+        idev = std::max(idev, v);
+        iun += v > FAR_DEV_MAX ? 1 : 0;
+      }
+  }
+  if (t.outside_alloc && t.ob.fdev) {
+    if (cudaMemcpy(&odev, t.ob.fdev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: copy");
+    oun = odev > FAR_DEV_MAX ? 1 : 0;
+  }
+  if (in_max_dev) *in_max_dev = idev;
+  if (in_untiled) *in_untiled = iun;
+  if (out_max_dev) *out_max_dev = odev;
+  if (out_untiled) *out_untiled = oun;
+  return CF_OK;
+}
+
+extern "C" cf_status cf_debug_set_wait_polls(int device, unsigned long long polls) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();  // no kernel of this process is still waiting
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cf_wait_polls, &polls, sizeof(polls));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cf_debug_set_wait_polls");
+  return CF_OK;
+}
+
+extern "C" cf_status cf_debug_fail_alloc(long long after) {
+  g_fail_alloc_after.store(after < 0 ? -1 : after);
+  return CF_OK;
+}
+
+extern "C" int cf_debug_classify_pointer(int memory_type, int pointer_device, int problem_device) {
+  return classify_ptr(memory_type, pointer_device, problem_device);
 }

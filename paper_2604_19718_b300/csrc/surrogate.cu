@@ -358,6 +358,18 @@ bool on_device(const void *ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// device memory of a device other than `device` (the kernels read the
+// window inputs in place, so such buffers are rejected)
+bool on_other_device(const void *ptr, int device) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device != device;
+}
+
 size_t conv_smem(int ci) { return (size_t)ci * K * C * 2 + (size_t)ci * LPH * 4; }
 size_t dw_smem(int ci) { return ((size_t)C * LPD + (size_t)ci * LPW) * 4; }
 
@@ -372,6 +384,8 @@ cf_status stage(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, i
                 const int64_t **doff, std::vector<int64_t> &hoff) {
   hoff.assign((size_t)nwin + 1, 0);
   cudaStream_t st = s->stream;
+  if (on_other_device(offsets, s->device) || on_other_device(bases, s->device))
+    return sfail(CF_EINVAL, "surrogate: window inputs are device memory of another device");
   const bool odev = on_device(offsets), bdev = on_device(bases);
   if (odev) {
     SG_CUDA(cudaMemcpyAsync(hoff.data(), offsets, sizeof(int64_t) * (nwin + 1), cudaMemcpyDeviceToHost, st));

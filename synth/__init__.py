@@ -99,6 +99,12 @@ def workload(name: str):
         res = rng.choice(20, 1000, p=freqs).astype(np.int32)
         lw = rng.normal(0.0, 0.5, (1000, 6))
         return res, lw, None
+    if name == "p200_bent":           # 100 lysines, then 100 aa of Dirichlet(1) composition, seed 5
+        # Lysine codons (AAA, AAG) cannot pair with each other, so the best
+        # interval of each length lies in the second half until the length
+        # passes 300 nt: the per-diagonal exponents bend there.
+        res = np.concatenate([np.full(100, AMINO_ACIDS.index("K")), residues_dirichlet(100, 5)])
+        return res.astype(np.int32), None, None
     raise KeyError(name)
 
 

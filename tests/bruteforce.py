@@ -215,3 +215,121 @@ def summary(params, residues, lw=None, pb=None, any_pair=False, allow=None):
                 pbase[3 * r + off, _IDX[cod[off]]] += pr
     return {"logZ": math.log(Z), "P": P, "codon": pc, "pair_grad": pg, "base": pbase,
             "ensemble": ens, "Z": Z}
+
+
+# ---------------------------------------------------------------- exact integer costs (MFE)
+# The minimum free energy form works on integer costs: every elementary energy
+# term, and every codon log-weight and pair bonus converted to kcal/mol as
+# -kT w, is rounded once to the nearest multiple of 2^-32 kcal/mol (half away
+# from zero); a configuration's cost is the sum of its terms.
+
+Q_SCALE = 2.0 ** 32
+
+
+def qcost(e: float) -> int:
+    v = e * Q_SCALE
+    return int(math.floor(v + 0.5)) if v >= 0 else -int(math.floor(-v + 0.5))
+
+
+def energy_q(p: Params, seq, pt):
+    """Integer cost of a structure by loop decomposition (same loops as
+    energy()); None outside the ensemble."""
+    n = len(seq)
+    E = 0
+    q = 0
+    while q < n:
+        if pt[q] > q:
+            k, l = q, pt[q]
+            if k > 0:
+                E += qcost(p.d5[seq[k], seq[k - 1]])
+            if l < n - 1:
+                E += qcost(p.d3[seq[l], seq[l + 1]])
+            q = l + 1
+        else:
+            q += 1
+    for i in range(n):
+        j = pt[i]
+        if j <= i:
+            continue
+        branches, unp, q = [], 0, i + 1
+        while q < j:
+            if pt[q] > q:
+                branches.append((q, pt[q]))
+                q = pt[q] + 1
+            else:
+                unp += 1
+                q += 1
+        if not branches:
+            E += qcost(hairpin_len(p, j - i - 1)) + qcost(p.tm[seq[i + 1], seq[j - 1]])
+        elif len(branches) == 1:
+            k, l = branches[0]
+            l1, l2 = k - i - 1, j - l - 1
+            if l1 == 0 and l2 == 0:
+                E += qcost(p.stack[PAIRS[(seq[i], seq[j])], PAIRS[(seq[k], seq[l])]])
+            elif l1 + l2 > 30:
+                return None
+            elif l1 == 0 or l2 == 0:
+                E += qcost(p.Bu[l1 + l2])
+            else:
+                E += qcost(p.In[l1 + l2]) + qcost(p.tm[seq[i + 1], seq[j - 1]]) + qcost(p.tm[seq[l + 1], seq[k - 1]])
+        else:
+            E += qcost(p.a) + qcost(p.c) * (len(branches) + 1) + qcost(p.b) * unp
+            E += qcost(p.d5[seq[j], seq[j - 1]]) + qcost(p.d3[seq[i], seq[i + 1]])
+            for k, l in branches:
+                E += qcost(p.d5[seq[k], seq[k - 1]]) + qcost(p.d3[seq[l], seq[l + 1]])
+    return E
+
+
+def weight_cost(p: Params, slots, cids, lw=None, pb=None) -> int:
+    """Integer cost of the soft constraints of a codon choice: -kT w per
+    codon log-weight and per adjacent codon-pair bonus, each rounded."""
+    tot = 0
+    m = len(slots)
+    for r in range(m):
+        tot += qcost(-(p.kT * (lw[r][slots[r]] if lw is not None else 0.0)))
+        if r + 1 < m:
+            tot += qcost(-(p.kT * (pb[cids[r]][cids[r + 1]] if pb is not None else 0.0)))
+    return tot
+
+
+def config_cost(params, residues, cids, partner, lw=None, pb=None):
+    """Cost of one (codon sequence, structure) given as sense codon ids and
+    a partner list; None if the structure is outside the ensemble."""
+    p = Params(params)
+    res = [int(r) for r in residues]
+    slots = []
+    for r, cid in zip(res, cids):
+        cods = codons_for(r)
+        c = SENSE[int(cid)]
+        if c not in cods:
+            return None
+        slots.append(cods.index(c))
+    seq = tuple(_IDX[b] for cid in cids for b in SENSE[int(cid)])
+    pt = [int(x) for x in partner]
+    for i, j in enumerate(pt):
+        if j >= 0 and (pt[j] != i or abs(j - i) < 4 or (seq[min(i, j)], seq[max(i, j)]) not in PAIRS):
+            return None
+    for i in range(len(pt)):  # no crossing pairs
+        j = pt[i]
+        if j > i and any(pt[k] > j or (0 <= pt[k] < i) for k in range(i + 1, j)):
+            return None
+    e = energy_q(p, seq, pt)
+    return None if e is None else e + weight_cost(p, slots, [int(c) for c in cids], lw, pb)
+
+
+def mfe_bruteforce(params, residues, lw=None, pb=None):
+    """Minimum integer cost over every codon sequence and structure."""
+    p = Params(params)
+    res = [int(r) for r in residues]
+    opts = [codons_for(r) for r in res]
+    best = None
+    for combo in itertools.product(*[range(len(o)) for o in opts]):
+        cods = [opts[r][combo[r]] for r in range(len(res))]
+        cids = [SENSE_ID[c] for c in cods]
+        seq = tuple(_IDX[b] for c in cods for b in c)
+        wc = weight_cost(p, combo, cids, lw, pb)
+        for pt in structures(seq):
+            e = energy_q(p, seq, pt)
+            if e is not None and (best is None or e + wc < best):
+                best = e + wc
+    return best

@@ -62,3 +62,31 @@ def test_cpu_side_argument_checks():
         raise AssertionError("expected CF_EINVAL")
     m = cf.cf_load_model(synth.nn_params(0))
     cf.cf_model_free(m)
+
+
+def test_pointer_rule_rejects_other_device_memory():
+    """The rule the library applies to caller buffers before any launch:
+    host memory is staged, device memory of the problem's device (or managed
+    memory) is used in place, device memory of another device is rejected
+    (CF_EINVAL) so that no kernel of the problem touches it."""
+    import paper_2604_19718_b300 as cf
+    host, device, managed = 1, 2, 3  # cudaMemoryType values
+    unregistered = 0
+    assert cf.cf_debug_classify_pointer(unregistered, -1, 0) == 0
+    assert cf.cf_debug_classify_pointer(host, 0, 0) == 0
+    assert cf.cf_debug_classify_pointer(device, 0, 0) == 1
+    assert cf.cf_debug_classify_pointer(device, 1, 1) == 1
+    assert cf.cf_debug_classify_pointer(device, 1, 0) == -1
+    assert cf.cf_debug_classify_pointer(device, 0, 3) == -1
+    assert cf.cf_debug_classify_pointer(managed, 1, 0) == 1
+
+
+def test_noalloc_scratch_size_matches_header():
+    """CF_NOALLOC_SCRATCH_BYTES as the header computes it: error word, per-warp
+    states and per-warp stacks at the stated limits."""
+    text = (ROOT / "include" / "codonfold.h").read_text()
+    max_n = int(re.search(r"#define CF_NOALLOC_MAX_N (\d+)", text).group(1))
+    warps = int(re.search(r"#define CF_NOALLOC_WARPS (\d+)", text).group(1))
+    want = 256 + (warps * max_n * 4 + 255) // 256 * 256 + warps * (max_n + 64) * 8
+    assert want == 4673792
+    assert "4,673,792" in text

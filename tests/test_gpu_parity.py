@@ -89,7 +89,10 @@ def test_full_size_golden(name, prec):
     tl, tp, tP = TOL[prec]
     assert abs(lz - float(g["logZ"])) <= tl * abs(float(g["logZ"]))
     assert np.abs(cm - g["codon"]).max() <= tp
-    assert np.abs(P[g["rows"]] - g["P_rows"]).max() <= tP
+    # every element of the pair-probability matrix (at 900 nt the outside
+    # chain runs its 256-thread cells on diagonals with more than 296 cells)
+    assert g["P"].shape == P.shape
+    assert np.abs(P - g["P"]).max() <= tP
     assert np.abs(np.diag(P) - g["unpaired"]).max() <= tP
     assert np.abs(pg - g["pair_grad"]).max() <= 10 * tp
 

@@ -86,9 +86,11 @@ def algorithmic_flops(res):
 
 
 # DRAM traffic of one outside pass of this workload (read + write bytes summed
-# over its kernels), from the ncu launch list with warm caches in
-# profiles/launches_p300_dirichlet_fp32.md; taken on the kernels as committed
+# over its kernels), from an ncu capture (profiles/); it describes the kernels
+# of the commit named beside it and is reported with that tag, not as a
+# measurement of this run
 OUTSIDE_DRAM_BYTES_PER_PASS = 7.98e9
+OUTSIDE_DRAM_BYTES_COMMIT = "c87a7d7"
 
 
 def sm_peak_tflops(clock_mhz, sms=148):
@@ -182,8 +184,9 @@ def cpu_oracle_rate(res, lw, pb, budget_m=60):
     cells = n * (n + 1) / 2
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": cells / dt, "unit": "cells/s", "cores": threads, "kind": "oracle",
-            "sample": f"inside+outside of the first {len(sub)} residues ({n} nt) of the 300-aa workload, "
-                      f"{dt:.1f} s; inside OpenMP over the cells of a diagonal, outside single-threaded"}
+            "sample": f"PREFIX FIGURE: inside+outside of the first {len(sub)} residues ({n} nt) of the 300-aa "
+                      f"workload, {dt:.1f} s; inside OpenMP over the cells of a diagonal, outside single-threaded. "
+                      "The oracle's cost per cell grows with n, so this overstates its rate on the full 900 nt"}
 
 
 def run_reference(args):
@@ -249,6 +252,20 @@ def bench_surrogate(ex, data, stream):
     train_s = time.perf_counter() - t
     b_h, o_h = screen.gather(bases, off, held)
     big = cf.Surrogate(sur.params(), stream=stream, max_batch=4096)
+    # prediction throughput on the whole 200,000-window batch, both paths
+    b_all, o_all = bases, off
+    paths = {}
+    for path, key in ((0, "cuda_cores"), (1, "tensor_cores")):
+        cf.cf_surrogate_set_path(big.h, path)
+        big.predict(b_all[:o_all[4096]], o_all[:4097])
+        p_all = big.predict(b_all, o_all)
+        ms_all = cf.cf_surrogate_last_ms(big.h)
+        paths[key] = {"ms": ms_all, "windows_per_s": (len(o_all) - 1) / (ms_all * 1e-3), "pred": p_all}
+    n_all = np.diff(o_all).astype(np.float64)
+    flops_all = float(np.sum(2 * 64 * (4 + 3 * 64) * 5 * n_all)) + float(np.sum(2 * 64 * n_all))
+    tc_vs_cc = float(np.max(np.abs(paths["tensor_cores"]["pred"] - paths["cuda_cores"]["pred"])
+                            / np.maximum(1.0, np.abs(paths["cuda_cores"]["pred"]))))
+    cf.cf_surrogate_set_path(big.h, 1)
     big.predict(b_h, o_h)
     pred = big.predict(b_h, o_h)
     pred_ms = cf.cf_surrogate_last_ms(big.h)
@@ -277,6 +294,9 @@ def bench_surrogate(ex, data, stream):
             "heldout_mse_kcal2": mse, "length_only_mse_kcal2": mse_b,
             "predict_windows_per_s": len(held) / (pred_ms * 1e-3),
             "predict_tflops": flops_fwd / (pred_ms * 1e-3) / 1e12,
+            "predict_all_200k": {k: {"ms": v["ms"], "windows_per_s": v["windows_per_s"],
+                                     "tflops": flops_all / (v["ms"] * 1e-3) / 1e12} for k, v in paths.items()},
+            "predict_tensor_vs_cuda_cores_max_rel": tc_vs_cc,
             "prescreen": {"windows": 16, "candidates": 1024, "top": 32, "candidates_kind": "uniform codons",
                           "gain_kcal_equal_exact_evals": float(np.mean(g_eval)),
                           "gain_kcal_equal_wall_time": float(np.mean(g_time)),
@@ -318,16 +338,32 @@ def bench_adjoint(stream):
 
 
 def bench_small_batch(nstreams=32, count=4096):
-    """Proteins/s on the 4,096-protein batch of 8-residue (24-nt) proteins:
-    inside + outside per protein, each worker thread with its own problem on
-    its own stream (a new protein of the same length reuses the problem's
-    tables and graphs), in the binary64 form and in the binary32 form."""
+    """Proteins/s on the 4,096-protein batch of 8-residue (24-nt) proteins,
+    inside + outside (pair probabilities and codon marginals) per protein,
+    in the binary64 and binary32 forms.  Batched: the whole batch in one
+    launch per kernel (cf_batch_*), timed on the device and end to end
+    (proteins uploaded, results copied back).  Per problem, for comparison:
+    each worker thread with its own problem on its own stream (a new protein
+    of the same length reuses the problem's tables and graphs)."""
     import torch
 
     import paper_2604_19718_b300 as cf
     prots = synth.batch_p8(count)
     params = synth.nn_params(0)
     out = {"proteins": count, "nt": 24, "streams": nstreams}
+    for prec, key in ((cf.CF_FP64, "fp64"), (cf.CF_FP32_SCALED, "fp32")):
+        b = cf.Batch(params, count, 8, prec)
+        b.set_proteins(prots)
+        b.run()  # warm-up: graphs
+        t = time.perf_counter()
+        b.set_proteins(prots)
+        lz, P, cm = b.run()
+        wall = time.perf_counter() - t
+        ms = b.last_ms()
+        b.close()
+        out[key + "_batched_proteins_per_s"] = count / (ms * 1e-3)
+        out[key + "_batched_e2e_proteins_per_s"] = count / wall
+        out[key + "_batched_logZ_first"] = float(lz[0])
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
     folds = [cf.CodonFold(params, stream=s.cuda_stream) for s in streams]
     for prec, key in ((cf.CF_FP64, "fp64"), (cf.CF_FP32_SCALED, "fp32")):
@@ -353,8 +389,8 @@ def bench_small_batch(nstreams=32, count=4096):
             th.join()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
-        out[key + "_proteins_per_s"] = count / dt
-        out[key + "_logZ_first"] = float(lz[0])
+        out[key + "_per_problem_proteins_per_s"] = count / dt
+        out[key + "_per_problem_logZ_first"] = float(lz[0])
     for f in folds:
         f.close()
     return out
@@ -399,6 +435,27 @@ def bench_concurrent(nprob=4, rounds=5):
             "cells_per_s": nprob * rounds * n * (n + 1) / 2 / dt, "logZ_equal": bool(np.all(lz == lz[0]))}
 
 
+def bench_mfe(stream):
+    """Minimum free energy (min-sum recursions on exact integer costs) with
+    traceback, on the 300-aa soft-weighted protein and the 1000-aa protein."""
+    import paper_2604_19718_b300 as cf
+    out = {}
+    for name in ("p300_weighted", "p1000_weighted"):
+        res, lw, pb = synth.workload(name)
+        f = cf.CodonFold(synth.nn_params(0), stream=stream)
+        f.set_protein(res, lw, pb)
+        f.mfe()  # warm-up: tables and graph
+        q, kc, cod, par = f.mfe()
+        ms_tb = cf.cf_mfe_last_ms(f.prob)
+        cf.cf_mfe(f.prob)
+        ms = cf.cf_mfe_last_ms(f.prob)
+        n = 3 * len(res)
+        f.close()
+        out[name] = {"mfe_kcal": kc, "ms": ms, "ms_with_traceback": ms_tb,
+                     "cells_per_s": n * (n + 1) / 2 / (ms * 1e-3), "pairs": int((par >= 0).sum() // 2)}
+    return out
+
+
 def bench_frequency(stream):
     """Frequency matching with Anderson mixing on the 900-nt workload: per-codon
     target bonuses exp(N(0,1)) (seed 3), r_tol = 0.002, binary32."""
@@ -440,6 +497,50 @@ def bench_large(stream, nsamples=10_000):
             "samples": nsamples, "samples_per_s": nsamples / ts, "launches": lin + lout}
 
 
+def profile_form(form, steps):
+    """One form on a small case, repeated `steps` times (profiler captures)."""
+    import torch
+
+    import paper_2604_19718_b300 as cf
+    from paper_2604_19718_b300 import screen
+    params = synth.nn_params(0)
+    out = {"profile_form": form}
+    if form == "surrogate":  # 4,096 windows: one batch of the tensor-core prediction path
+        _, _, bases, off = synth.windows(4096, seed=3)
+        sur = cf.Surrogate(synth.surrogate_init(0), max_batch=4096)
+        for _ in range(steps):
+            sur.predict(bases, off)
+        out["ms"] = cf.cf_surrogate_last_ms(sur.h)
+        sur.close()
+    elif form in ("mfe", "sample", "checkpoint"):
+        res, lw, pb = synth.workload("p300_weighted")
+        f = cf.CodonFold(params)
+        if form == "checkpoint":
+            cf.cf_set_checkpoint(f.prob, 1)
+        f.set_protein(res, lw, pb)
+        for _ in range(steps):
+            if form == "mfe":
+                f.mfe()
+                out["ms"] = cf.cf_mfe_last_ms(f.prob)
+            elif form == "sample":
+                f.inside(cf.CF_FP32_SCALED)
+                f.sample(10000, 2)
+            else:
+                f.inside(cf.CF_FP32_SCALED)
+                f.outside(False, True, False)
+                out["ms"] = f.timing()[:2]
+        f.close()
+    elif form == "windows":
+        ex = screen.Windows(params)
+        _, _, bases, off = synth.windows(20000, seed=3)
+        for _ in range(steps):
+            ex.logz(bases, off)
+        out["ms"] = ex.last_ms()
+        ex.close()
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,9 +554,13 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="use only the first M residues (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the window, surrogate, adjoint and 3000-nt measurements")
+    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint"],
+                    help="run one form on a small case (for profiler captures) and print its timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_form:
+        return profile_form(args.profile_form, args.steps)
     if not args.profile:
         args.warmup = max(args.warmup, 3)
 
@@ -511,6 +616,7 @@ def main():
     ms = max_over_ranks(ms, ws)
     P32 = Pd.cpu().numpy().copy()
     cm32 = cmd.cpu().numpy().copy()
+    far_info = cf.cf_far_band_info(f.prob)
     value = ws * args.steps * cells / (ms * 1e-3)
 
     # ---- binary64 form on the same GPU
@@ -568,6 +674,7 @@ def main():
         forms["small_batch"] = bench_small_batch()
         forms["concurrent"] = bench_concurrent()
         forms["frequency_matching"] = bench_frequency(stream.cuda_stream)
+        forms["mfe"] = bench_mfe(stream.cuda_stream)
 
     if rank != 0:
         return
@@ -602,11 +709,14 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": OUTSIDE_DRAM_BYTES_PER_PASS if WORKLOAD == "p300_dirichlet" and not args.m else None,
                      "traffic_unit": "bytes per outside pass (ncu, warm caches)",
+                     "traffic_measured_at_commit": OUTSIDE_DRAM_BYTES_COMMIT,
                      "peak_basis": f"FP32 FFMA 148 SM x 128 lanes x 2 x {clock:.0f} MHz (median SM clock "
                                    "sampled during the timed region)"},
         "e2e": {"value": cells / e2e_s, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(lin + lout),
+        "far_bands": dict(zip(("inside_max_departure_log2", "inside_bands_term_by_term",
+                               "outside_max_departure_log2", "outside_term_by_term"), far_info)),
         "clocks": clocks,
     }
     out.update(forms)

@@ -157,6 +157,82 @@ cf_status cf_outside(cf_problem *prob, float *pair_prob, double *codon_marg, dou
 cf_status cf_sample(cf_problem *prob, int nsamples, uint64_t seed, int32_t *codons,
                     int32_t *partner);
 
+/*
+ * Minimum free energy (paper Section "Minimization", Eq. min-problem): the
+ * minimum over codon sequences encoding the protein and structures of
+ *   E(sequence, structure) - kT (sum of codon log-weights + sum of codon-pair
+ *   bonuses)                                              [kcal/mol],
+ * computed by the recursions of cf_inside in the min-sum semiring (SI
+ * "Generalization via evaluation algebras"), and one configuration that
+ * attains it (traceback).  Uses the protein and weights of the last
+ * cf_set_protein / cf_set_weights; needs no cf_inside.
+ * Arithmetic is exact: every elementary energy term and every weight term
+ * -kT w (kT = 1.98717e-3 (T + 273.15), binary64) is rounded once, half away
+ * from zero, to a multiple of 2^-32 kcal/mol, and the recursions add these
+ * integers (int64), so the minimum does not depend on evaluation order.
+ *   cost:     the minimum as an integer count of 2^-32 kcal/mol (host), or NULL.
+ *   mfe_kcal: the same in kcal/mol (host), or NULL.
+ *   codons:   m int32 sense codon ids of a minimiser, host or device, or NULL.
+ *   partner:  n int32 pairing partners of the minimiser (-1 unpaired), host or
+ *             device, or NULL.  With both NULL no traceback runs.
+ * Where several configurations attain the minimum, the traceback returns the
+ * first in its fixed order of alternatives.  Allocates the pass's integer
+ * tables on the first call for a protein length (10 tables of n(n+1)/2 blocks
+ * of 36 int64, about 1.2 GB at n = 900).
+ * Errors: CF_EINVAL (NULL problem, an output on another device), CF_ESTATE (no
+ * protein), CF_ENOMEM, CF_ECUDA, CF_ENUMERIC (traceback inconsistency).
+ */
+cf_status cf_mfe(cf_problem *prob, int64_t *cost, double *mfe_kcal, int32_t *codons, int32_t *partner);
+
+/* Device time in milliseconds of the last cf_mfe (pass and traceback). */
+float cf_mfe_last_ms(const cf_problem *prob);
+
+/*
+ * Checkpointing of the interior-loop partial sums (the adjoint's largest
+ * intermediate: 29 blocks per cell, 19 GB in binary32 at 3000 nt when stored
+ * whole).  Checkpointed, the inside pass keeps them for two diagonals plus
+ * every 64th diagonal, and the outside pass recomputes each block of 64
+ * diagonals from its checkpoint just before it needs it (same recursion, same
+ * operation order: identical values), so the outside pass needs 2 blocks
+ * instead of the whole table; the sampler evaluates them from their
+ * definition.  mode: -1 (default) checkpointed from CF_CHECKPOINT_MIN_N bases
+ * on, 0 never, 1 always.  Takes effect at the next cf_inside (the tables of
+ * the current protein are released).  cf_checkpointed reports the form of the
+ * current tables (or the one the next cf_inside will use).
+ * Errors: CF_EINVAL (NULL problem, unknown mode), CF_ECUDA.
+ */
+#define CF_CHECKPOINT_MIN_N 3000
+cf_status cf_set_checkpoint(cf_problem *prob, int mode);
+int cf_checkpointed(const cf_problem *prob);
+
+/*
+ * Batches of small proteins of one length (the throughput form of short
+ * proteins: paper Section "Computational details" benchmarks random
+ * proteins): nprot proteins of m residues, inside and outside in one launch
+ * per kernel for the whole batch instead of one graph per protein.  Each
+ * protein's arrays occupy one slab of a single device allocation; results
+ * equal those of cf_inside / cf_outside on each protein alone.
+ *   cf_batch_create: 1 <= m <= CF_BATCH_MAX_M, nprot >= 1, one precision.
+ *     Allocates nprot slabs (about 2.6 MB each at m = 8 in binary32).
+ *   cf_batch_set_proteins: aa = nprot * m letters (host), codon_logw =
+ *     nprot * m * 6 doubles or NULL (layout of cf_set_protein, protein after
+ *     protein), pair_bonus = 61 * 61 doubles shared by all proteins or NULL.
+ *   cf_batch_run: logZ = nprot doubles (host); pair_prob = nprot * n * n
+ *     floats and codon_marg = nprot * m * 6 doubles (host or device), each
+ *     may be NULL.  Layouts per protein as in cf_outside.
+ *   cf_batch_last_ms: device time of the last run (inside + outside).
+ * Errors: CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ESTATE (run before set),
+ * CF_ENUMERIC, CF_ETIMEOUT; messages from cf_last_error(NULL).
+ */
+#define CF_BATCH_MAX_M 16
+typedef struct cf_batch cf_batch;
+cf_status cf_batch_create(const cf_model *model, int device, void *stream, int nprot, int m, cf_precision precision,
+                          cf_batch **out);
+cf_status cf_batch_set_proteins(cf_batch *batch, const char *aa, const double *codon_logw, const double *pair_bonus);
+cf_status cf_batch_run(cf_batch *batch, double *logZ, float *pair_prob, double *codon_marg);
+float cf_batch_last_ms(const cf_batch *batch);
+cf_status cf_batch_free(cf_batch *batch);
+
 /* One-line description of the last failure on `prob` (or of the last global
  * failure when prob is NULL).  Valid until the next call on that problem. */
 const char *cf_last_error(const cf_problem *prob);
@@ -237,6 +313,20 @@ cf_status cf_surrogate_train_step(cf_surrogate *sur, const uint8_t *bases, const
 float cf_surrogate_last_ms(const cf_surrogate *sur);
 
 /*
+ * Which units run cf_surrogate_predict (training always uses the CUDA-core
+ * kernels with FP32 activations):
+ *   1 (default) tensor cores: each 64-channel layer as 128-row tiles of a
+ *     5-tap GEMM on the 5th-generation tensor cores (tcgen05 MMA, FP32
+ *     accumulators in tensor memory, operands staged by TMA); activations
+ *     carried as two BF16 parts hi + lo (within 2^-18 relative of FP32);
+ *   0 CUDA cores: FP32 activations, FP32 FMA.
+ * Errors: CF_EINVAL (NULL surrogate, unknown path).  A bounded wait of the
+ * tensor-core pipeline that gives up makes cf_surrogate_predict return
+ * CF_ETIMEOUT.
+ */
+cf_status cf_surrogate_set_path(cf_surrogate *sur, int path);
+
+/*
  * cf_sample_noalloc -- the sampler of cf_sample for callers that cannot
  * allocate device memory.  (The paper has no counterpart: this is a library
  * service, not part of the method.)
@@ -287,12 +377,17 @@ cf_status cf_sample_noalloc(cf_problem *prob, int nsamples, uint64_t seed, int32
  * (log2) is not tiled but summed term by term with exact factors.
  *   in_max_dev / out_max_dev: largest departure seen by the inside bands and
  *   by the outside pass; in_untiled: inside bands summed term by term;
- *   out_untiled: 1 if the outside pass gathered every term per diagonal.
+ *   out_untiled: 1 if the outside pass gathered every term per diagonal;
+ *   spread_bits: the spread (log2) of the strengths of the intervals of one
+ *   length, estimated after the inside pass from the exterior prefix; past
+ *   100 bits the binary32 inside pass returns CF_ENUMERIC and asks for
+ *   CF_FP64 (a composition that changes strongly along the protein spreads
+ *   them beyond what binary32 holds).
  * Any pointer may be NULL.  Synchronises the problem's stream.
  * Errors: CF_EINVAL (NULL problem), CF_ECUDA.
  */
 cf_status cf_far_band_info(const cf_problem *prob, int *in_max_dev, int *in_untiled, int *out_max_dev,
-                           int *out_untiled);
+                           int *out_untiled, int *spread_bits);
 
 /*
  * Test hooks (the paper has no counterpart).  They exist so that tests can
@@ -303,6 +398,12 @@ cf_status cf_far_band_info(const cf_problem *prob, int *in_max_dev, int *in_unti
  *     the timeout, still waits (bounded) for its own copies in flight, and
  *     returns, and cf_inside / cf_outside report CF_ETIMEOUT.  Synchronises
  *     the device before and after; affects every problem on that device.
+ *   cf_debug_set_far_dev_max: the departure bound above which a far band is
+ *     summed term by term (default 48); 0 sends every band of every binary32
+ *     pass on `device` that way.  Synchronises the device.
+ *   cf_debug_set_range_limit: the spread (bits) above which the binary32
+ *     inside pass on `device` refuses, and the longest interval length the
+ *     spread is measured over (0: all).  Synchronises the device.
  *   cf_debug_fail_alloc: after `after` further successful device allocations
  *     of the library (process-wide), the next one fails as if the device were
  *     out of memory (CF_ENOMEM); negative turns the hook off.  The failing
@@ -315,6 +416,8 @@ cf_status cf_far_band_info(const cf_problem *prob, int *in_max_dev, int *in_unti
  *     may use in place, -1 device memory of another device (rejected).
  */
 cf_status cf_debug_set_wait_polls(int device, unsigned long long polls);
+cf_status cf_debug_set_far_dev_max(int device, int bound);
+cf_status cf_debug_set_range_limit(int device, int bits, int max_length);
 cf_status cf_debug_fail_alloc(long long after);
 int cf_debug_classify_pointer(int memory_type, int pointer_device, int problem_device);
 

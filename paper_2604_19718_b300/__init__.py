@@ -60,13 +60,36 @@ def _load() -> ctypes.CDLL:
     lib.cf_surrogate_last_ms.argtypes = [vp]
     lib.cf_surrogate_last_ms.restype = ctypes.c_float
     ip = ctypes.POINTER(ctypes.c_int)
-    lib.cf_far_band_info.argtypes = [vp, ip, ip, ip, ip]
+    lib.cf_far_band_info.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.cf_debug_set_range_limit.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.cf_debug_set_range_limit.restype = ctypes.c_int
     lib.cf_debug_set_wait_polls.argtypes = [ctypes.c_int, ctypes.c_ulonglong]
     lib.cf_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+    lib.cf_debug_set_far_dev_max.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.cf_debug_set_far_dev_max.restype = ctypes.c_int
+    lib.cf_surrogate_set_path.argtypes = [vp, ctypes.c_int]
+    lib.cf_surrogate_set_path.restype = ctypes.c_int
     lib.cf_debug_classify_pointer.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.cf_debug_classify_pointer.restype = ctypes.c_int
     lib.cf_sample_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_uint64, vp, vp]
-    for name in ("cf_far_band_info", "cf_debug_set_wait_polls", "cf_debug_fail_alloc", "cf_sample_noalloc"):
+    lib.cf_mfe.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), vp, vp]
+    lib.cf_set_checkpoint.argtypes = [vp, ctypes.c_int]
+    lib.cf_set_checkpoint.restype = ctypes.c_int
+    lib.cf_checkpointed.argtypes = [vp]
+    lib.cf_checkpointed.restype = ctypes.c_int
+    lib.cf_batch_create.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(vp)]
+    lib.cf_batch_set_proteins.argtypes = [vp, ctypes.c_char_p, vp, vp]
+    lib.cf_batch_run.argtypes = [vp, vp, vp, vp]
+    lib.cf_batch_last_ms.argtypes = [vp]
+    lib.cf_batch_last_ms.restype = ctypes.c_float
+    lib.cf_batch_free.argtypes = [vp]
+    for name in ("cf_batch_create", "cf_batch_set_proteins", "cf_batch_run", "cf_batch_free"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.cf_mfe_last_ms.argtypes = [vp]
+    lib.cf_mfe_last_ms.restype = ctypes.c_float
+    for name in ("cf_far_band_info", "cf_debug_set_wait_polls", "cf_debug_fail_alloc", "cf_sample_noalloc",
+                 "cf_mfe"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("cf_surrogate_create", "cf_surrogate_free", "cf_surrogate_set_params", "cf_surrogate_get_params",
                  "cf_surrogate_predict", "cf_surrogate_grad", "cf_surrogate_train_step"):
@@ -217,17 +240,63 @@ def cf_sample_noalloc(prob, nsamples: int, seed: int, codons, partner) -> None:
     _check(lib.cf_sample_noalloc(prob, int(nsamples), ctypes.c_uint64(seed), _ptr(codons), _ptr(partner)), prob)
 
 
+def cf_mfe(prob, codons=None, partner=None):
+    """Minimum free energy: (integer cost in 2^-32 kcal/mol, kcal/mol); codons
+    (m int32) and partner (n int32), host arrays or device tensors, are filled
+    with one minimiser when given."""
+    q = ctypes.c_int64()
+    k = ctypes.c_double()
+    _check(lib.cf_mfe(prob, ctypes.byref(q), ctypes.byref(k), _ptr(codons), _ptr(partner)), prob)
+    return q.value, k.value
+
+
+def cf_set_checkpoint(prob, mode: int) -> None:
+    """-1 automatic (from CF_CHECKPOINT_MIN_N bases), 0 store the interior
+    partial sums whole, 1 checkpoint them every 64 diagonals."""
+    _check(lib.cf_set_checkpoint(prob, int(mode)), prob)
+
+
+def cf_checkpointed(prob) -> bool:
+    return bool(lib.cf_checkpointed(prob))
+
+
+def cf_mfe_last_ms(prob) -> float:
+    return float(lib.cf_mfe_last_ms(prob))
+
+
 def cf_far_band_info(prob):
     """(inside largest chord departure, inside bands summed term by term,
-    outside largest departure, outside gathered term by term) of the last
-    binary32 passes."""
-    v = [ctypes.c_int() for _ in range(4)]
+    outside largest departure, outside gathered term by term, spread of the
+    interval strengths in bits) of the last binary32 passes."""
+    v = [ctypes.c_int() for _ in range(5)]
     _check(lib.cf_far_band_info(prob, *[ctypes.byref(x) for x in v]), prob)
     return tuple(x.value for x in v)
 
 
 def cf_debug_set_wait_polls(device: int, polls: int) -> None:
     _check(lib.cf_debug_set_wait_polls(int(device), ctypes.c_ulonglong(polls)))
+
+
+def cf_debug_set_far_dev_max(device: int, bound: int) -> None:
+    _check(lib.cf_debug_set_far_dev_max(int(device), int(bound)))
+
+
+def cf_surrogate_set_path(sur, path: int) -> None:
+    """Prediction path: 0 CUDA cores (FP32 activations), 1 tensor cores."""
+    _check(lib.cf_surrogate_set_path(sur, int(path)))
+
+
+FAR_DEV_MAX_DEFAULT = 48
+
+
+RANGE_MAXLEN_DEFAULT = 0
+
+
+def cf_debug_set_range_limit(device: int, bits: int, max_length: int = RANGE_MAXLEN_DEFAULT) -> None:
+    _check(lib.cf_debug_set_range_limit(int(device), int(bits), int(max_length)))
+
+
+RANGE_LIMIT_DEFAULT = 100
 
 
 def cf_debug_fail_alloc(after: int) -> None:
@@ -245,6 +314,53 @@ WAIT_POLLS_DEFAULT = 1 << 22
 
 def to_letters(residues) -> str:
     return "".join(AMINO_ACIDS[int(r)] for r in residues)
+
+
+class Batch:
+    """A batch of proteins of one length: inside and outside for all of them
+    in one launch per kernel (cf_batch_*)."""
+
+    def __init__(self, params, nprot: int, m: int, precision: int = CF_FP32_SCALED, device: int = 0,
+                 stream: int = 0):
+        self.model = cf_load_model(params)
+        self.h = ctypes.c_void_p()
+        _check(lib.cf_batch_create(self.model, int(device), ctypes.c_void_p(stream), int(nprot), int(m),
+                                   int(precision), ctypes.byref(self.h)))
+        self.nprot, self.m, self.n = nprot, m, 3 * m
+
+    def set_proteins(self, proteins, codon_logw=None, pair_bonus=None):
+        """proteins: nprot residue lists (or strings) of m residues."""
+        letters = "".join(p if isinstance(p, str) else to_letters(p) for p in proteins)
+        if len(letters) != self.nprot * self.m:
+            raise ValueError("expected nprot proteins of m residues")
+        lw = None if codon_logw is None else np.ascontiguousarray(codon_logw, dtype=np.float64).reshape(
+            self.nprot, self.m, 6)
+        pb = None if pair_bonus is None else np.ascontiguousarray(pair_bonus, dtype=np.float64).reshape(61, 61)
+        _check(lib.cf_batch_set_proteins(self.h, letters.encode(), _ptr(lw), _ptr(pb)))
+
+    def run(self, pair_prob=True, codon=True):
+        lz = np.zeros(self.nprot)
+        P = np.zeros((self.nprot, self.n, self.n), dtype=np.float32) if pair_prob is True else pair_prob
+        cm = np.zeros((self.nprot, self.m, 6)) if codon is True else codon
+        _check(lib.cf_batch_run(self.h, _ptr(lz), None if P is False else _ptr(P), None if cm is False else _ptr(cm)))
+        return lz, P, cm
+
+    def last_ms(self) -> float:
+        return float(lib.cf_batch_last_ms(self.h))
+
+    def close(self):
+        if self.h:
+            lib.cf_batch_free(self.h)
+            self.h = None
+        if self.model:
+            cf_model_free(self.model)
+            self.model = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Surrogate:
@@ -337,6 +453,14 @@ class CodonFold:
         par = np.zeros((nsamples, self.n), dtype=np.int32)
         cf_sample(self.prob, nsamples, seed, cod, par)
         return cod, par
+
+    def mfe(self, traceback: bool = True):
+        """(cost, kcal/mol, codons[m] sense ids, partner[n]) of the minimum
+        free energy configuration (None, None without traceback)."""
+        cod = np.zeros(self.m, dtype=np.int32) if traceback else None
+        par = np.zeros(self.n, dtype=np.int32) if traceback else None
+        q, k = cf_mfe(self.prob, cod, par)
+        return q, k, cod, par
 
     def timing(self):
         return cf_last_timing(self.prob)

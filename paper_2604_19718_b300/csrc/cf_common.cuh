@@ -79,7 +79,10 @@ struct DP {
   int *err;         // device error word
   // inside tables [ncell*36]
   T *CH, *QB, *XI, *HB, *QMpp, *QMpu, *G, *QM2pp, *QM2pu, *QM2up, *QM2uu;
-  T *YY;            // [ncell*29*36]
+  T *YY;            // stored: [ncell][29][36]; checkpointed: ring [2][n][29][36]
+  int yyck;         // 1: the interior partial sums are checkpointed (see yy_in)
+  T *YYck;          // checkpointed: every 64th diagonal (d % 64 == 63), [n/64 + 1][n][29][36]
+  T *YYb;           // checkpointed: the outside pass's recomputed blocks, [2][64][n][29][36]
   T *Q5U, *Q5P, *Gx; // [n*36]
   double *Zm;       // scalar: Z relative to 2^{E[n-1]} and the transfer scaling
   // adjoint tables
@@ -90,7 +93,50 @@ struct DP {
   double *hT;       // [n*36]   d log Z / d T_p (boundary positions)
   double *hX;       // [n*4*36] d log Z / d X_p (boundary positions)
   float *P;         // [n*n] pair probabilities (device)
+  // Batch of equal-length proteins: every array of protein b lies bstride
+  // bytes after protein 0's (one slab per protein); 0 for a single protein.
+  // A batched launch takes the protein from blockIdx.y (k_out_tg: z / 2).
+  long long bstride;
 };
+
+template <typename P>
+__host__ __device__ __forceinline__ P *bshift(P *ptr, long long off) {
+  return ptr ? (P *)((char *)ptr + off) : ptr;
+}
+// Protein b's view of a batch: every pointer moved by b slabs.
+template <typename T>
+__device__ __forceinline__ void dp_shift(DP<T> &p, long long off) {
+#define CF_SH(f) p.f = bshift(p.f, off)
+  CF_SH(Mp); CF_SH(base); CF_SH(bnd); CF_SH(Tr); CF_SH(X); CF_SH(en); CF_SH(eHL); CF_SH(u0); CF_SH(E);
+  CF_SH(dmax); CF_SH(err); CF_SH(CH); CF_SH(QB); CF_SH(XI); CF_SH(HB); CF_SH(QMpp); CF_SH(QMpu); CF_SH(G);
+  CF_SH(QM2pp); CF_SH(QM2pu); CF_SH(QM2up); CF_SH(QM2uu); CF_SH(YY); CF_SH(YYck); CF_SH(YYb); CF_SH(Q5U);
+  CF_SH(Q5P); CF_SH(Gx); CF_SH(Zm); CF_SH(hCH); CF_SH(hQB); CF_SH(hGc); CF_SH(hXI); CF_SH(hHB); CF_SH(hQMpp);
+  CF_SH(hQMpu); CF_SH(hG); CF_SH(hQM2pp); CF_SH(hQM2pu); CF_SH(hQM2up); CF_SH(hQM2uu); CF_SH(hYY); CF_SH(hQ5U);
+  CF_SH(hQ5P); CF_SH(hGx); CF_SH(tgY); CF_SH(hT); CF_SH(hX); CF_SH(P);
+#undef CF_SH
+}
+
+// Where the 29 interior partial sums YY_L of cell (x, x + d) live.  Stored
+// form: one table over all cells.  Checkpointed form (the outside pass
+// recomputes them in blocks of 64 diagonals): during the inside pass a ring of
+// two diagonals, except that every diagonal d with d % 64 == 63 goes to the
+// checkpoint store, from which the outside pass restarts the recursion of the
+// next block; yy_out gives the block buffers the outside pass reads.
+constexpr int YYCK_BLOCK = 64;
+template <typename T>
+__host__ __device__ __forceinline__ T *yy_in(const DP<T> &p, int x, int d) {
+  const size_t cell = (size_t)NYY * BLK;
+  if (!p.yyck) return p.YY + cidx(p.n, x, x + d) * cell;
+  if (d % YYCK_BLOCK == YYCK_BLOCK - 1) return p.YYck + ((size_t)(d / YYCK_BLOCK) * p.n + x) * cell;
+  return p.YY + ((size_t)(d & 1) * p.n + x) * cell;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T *yy_out(const DP<T> &p, int x, int d) {
+  const size_t cell = (size_t)NYY * BLK;
+  if (!p.yyck) return p.YY + cidx(p.n, x, x + d) * cell;
+  if (d % YYCK_BLOCK == YYCK_BLOCK - 1) return p.YYck + ((size_t)(d / YYCK_BLOCK) * p.n + x) * cell;
+  return p.YYb + ((size_t)(((d / YYCK_BLOCK) & 1) * YYCK_BLOCK + d % YYCK_BLOCK) * p.n + x) * cell;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -314,6 +360,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 // wait give up at once; the drain wait after a timeout keeps its full length,
 // so the copies in flight still land before the CTA exits.
 static __device__ unsigned long long g_cf_wait_polls = 1ull << 22;
+
+// Largest departure (log2) of the per-diagonal exponents from the far-band
+// chord for which a band is still summed in tiles (48 by default).  A test
+// lowers it (cf_debug_set_far_dev_max) to send every band through the
+// term-by-term path.
+static __device__ int g_cf_far_dev_max = 48;
+
+// Bits of the device error word besides ERR_STAGE_TIMEOUT: the binary32
+// inside pass found the dynamic range of its tables exceeded, or an output of
+// the outside pass was not finite.
+constexpr int ERR_RANGE_IN = 1 << 6, ERR_OUT_NONFINITE = 1 << 8;
 
 // Bounded wait for a phase of the mbarrier.  On timeout bit 8 of the error
 // word is set and false is returned; the copies that were in flight are then

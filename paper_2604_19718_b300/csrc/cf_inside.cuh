@@ -31,7 +31,9 @@
 namespace cf {
 
 // 2^e from its IEEE-754 bit pattern (exponent field e + bias, zero mantissa);
-// exponents below the normal range give 0, above 120 are clamped to 2^120.
+// exponents below the normal range give 0; above, binary32 clamps at 2^120
+// and binary64 at 2^1000 (a factor that large multiplies mantissas that are
+// correspondingly small, so the clamp is never reached by a term that counts).
 template <typename T>
 __device__ __forceinline__ T clamp_p2(int e);
 template <>
@@ -41,7 +43,7 @@ __device__ __forceinline__ float clamp_p2<float>(int e) {
 }
 template <>
 __device__ __forceinline__ double clamp_p2<double>(int e) {
-  e = e > 120 ? 120 : e;
+  e = e > 1000 ? 1000 : e;
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
@@ -49,6 +51,7 @@ __device__ __forceinline__ double clamp_p2<double>(int e) {
 template <typename T>
 __global__ void k_inside_finish(DP<T> p) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (p.bstride) dp_shift(p, (long long)blockIdx.y * p.bstride);
   int n = p.n, M0 = p.Mp[0], Ml = p.Mp[n - 1];
   const T *u = p.Q5U + (size_t)(n - 1) * BLK, *q = p.Q5P + (size_t)(n - 1) * BLK;
   double z = 0;
@@ -71,9 +74,16 @@ __global__ void k_inside_finish(DP<T> p) {
 // X_PP = T d3 d5, with the bases of states a at q and b at q+1.  Entries beyond
 // the state counts, and the row of the last position, are zero.  Thread 0 also
 // writes u0[a] = e^{lw[0][a]} (residue 0's weights enter at the top).
+// (Batch: blockIdx.y is the protein, every array bstride bytes per protein.)
 __global__ void k_transfers(int n, const int *Mp, const int *base, const int *cid, const double *en,
-                            const double *lw, const double *pb, double *Tr, double *X, double *u0, double *ls) {
+                            const double *lw, const double *pb, double *Tr, double *X, double *u0, double *ls,
+                            long long bstride = 0) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bstride) {
+    const long long o = (long long)blockIdx.y * bstride;
+    Mp = bshift(Mp, o), base = bshift(base, o), cid = bshift(cid, o), en = bshift(en, o), lw = bshift(lw, o);
+    pb = bshift(pb, o), Tr = bshift(Tr, o), X = bshift(X, o), u0 = bshift(u0, o), ls = bshift(ls, o);
+  }
   if (q == 0)
     for (int a = 0; a < NS; a++) u0[a] = a < Mp[0] ? exp(lw[a]) : 0.0;
   if (q >= n) return;
@@ -116,17 +126,27 @@ __global__ void k_transfers(int n, const int *Mp, const int *base, const int *ci
     }
 }
 
-// Copy of a binary64 table in the precision of a pass.
+// Copy of a binary64 table in the precision of a pass (batch: blockIdx.y).
 template <typename T>
-__global__ void k_cast(const double *src, T *dst, size_t cnt) {
+__global__ void k_cast(const double *src, T *dst, size_t cnt, long long bstride = 0) {
+  if (bstride) {
+    src = bshift(src, (long long)blockIdx.y * bstride);
+    dst = bshift(dst, (long long)blockIdx.y * bstride);
+  }
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < cnt; k += (size_t)gridDim.x * blockDim.x)
     dst[k] = (T)src[k];
 }
 
 // log Z (natural log) in binary64: log of the scaled sum, plus the exponent
 // of the last diagonal, minus the transfer rescales, summed in residue order.
-__global__ void k_logz(const double *Zm, const int *E_last, const double *ls, int nls, double *logz) {
+// (Batch: blockIdx.y is the protein.)
+__global__ void k_logz(const double *Zm, const int *E_last, const double *ls, int nls, double *logz,
+                       long long bstride = 0) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (bstride) {
+    const long long o = (long long)blockIdx.y * bstride;
+    Zm = bshift(Zm, o), E_last = bshift(E_last, o), ls = bshift(ls, o), logz = bshift(logz, o);
+  }
   double sc = 0;
   for (int r = 0; r < nls; r++) sc += ls[r];
   *logz = log(*Zm) + (double)*E_last * 0.69314718055994530942 - sc;

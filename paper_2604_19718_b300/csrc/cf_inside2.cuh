@@ -43,9 +43,24 @@ struct BifBuf {
   int farslices;  // slices per cell in the far buffer
   float *gfac;    // [2][n] far-band rescale factors 2^{E[a] - s a - e0} per band parity (binary32)
   int *gdev;      // [n / FARD + 1] per band: ceil(max over a of |E[a] - s a - e0|), written by k_in_far_factors
+  int *spread;    // [1] the spread of interval strengths (bits) found by k_in_range (single problems)
   const T **stab; // [n][SI_N] source of every staged slot of the light cell x = 0 of each diagonal
   T **dtab;       // [n][NCOPY] destination of every result of that cell
 };
+
+// Protein b's view of a batch (see DP::bstride); the slot tables hold
+// protein 0's addresses, moved by the same offset where they are read.
+template <typename T>
+__device__ __forceinline__ void bb_shift(BifBuf<T> &b, long long off) {
+  b.main = bshift(b.main, off);
+  b.ext = bshift(b.ext, off);
+  b.far = bshift(b.far, off);
+  b.gfac = bshift(b.gfac, off);
+  b.gdev = bshift(b.gdev, off);
+  b.spread = bshift(b.spread, off);
+  b.stab = bshift(b.stab, off);
+  b.dtab = bshift(b.dtab, off);
+}
 
 // ---------------------------------------------------------------- far bands
 // The bifurcation sum of cell (x, y) on diagonal d runs over split points
@@ -66,12 +81,14 @@ struct BifBuf {
 // length moves between regions of different strength), and a factor
 // 2^{E[a] - s a - e0} far from one would overflow binary32 or flush the terms
 // to zero.  So the factor kernel of each band records the largest deviation
-// |E[a] - s a - e0| over the band's split points; past FAR_DEV_MAX (log2) the
-// band is not summed in tiles: k_in_far returns at once and the per-diagonal
-// kernel takes every split point itself, each term with its own exact
-// power-of-two factor (slower, never wrong).
+// |E[a] - s a - e0| over the band's split points; past g_cf_far_dev_max
+// (log2, 48 unless a test lowers it) the band is not summed in tiles:
+// k_in_far returns at once and the per-diagonal kernel takes every split
+// point itself, each term with its own power-of-two factor split between its
+// two operands (slower; no chord).
 constexpr int FARD = 16;   // diagonals per band
-constexpr int FAR_DEV_MAX = 48;  // largest |log2 factor| of a tiled band: a product of two stays within 2^{+-96}
+// (with the default bound, a product of two tile factors stays within 2^{+-96})
+__device__ __forceinline__ int far_dev_max() { return *(volatile int *)&g_cf_far_dev_max; }
 constexpr int FARTX = 16;  // rows per far tile
 constexpr int FARKC = 8;   // split points staged per step
 constexpr int FARKS = 64;   // split points per CTA slice
@@ -97,6 +114,62 @@ __device__ __forceinline__ FarChord far_chord(const int *E, int c) {
   r.s = (ec - e5) / (double)(c - 5);
   r.e0 = e5 - 5.0 * r.s;
   return r;
+}
+
+// Range of the binary32 form.  With one exponent per diagonal, the intervals
+// of one length are held relative to the strongest of them; binary32 keeps
+// about 126 bits below it.  A composition that changes along the protein (a
+// block that cannot pair next to an ordinary region) spreads the strengths of
+// one diagonal's intervals further, and the weak ones underflow in the inside
+// pass (their adjoints overflow in the outside pass).  k_in_range estimates
+// that spread after the inside pass from the exterior prefix F(y) = log2 of
+// the partition function of [0, y] (its table entries times 2^{E[y]}): the
+// strength of an interval [x, x + a] is about F(x + a) - F(x), so
+//   spread = max over a of (max_x - min_x) (F(x + a) - F(x))
+// bits.  A prefix that underflowed to zero counts as out of range.  Past
+// g_cf_range_limit bits the binary32 inside pass returns CF_ENUMERIC (binary64
+// has the range).  The departure of E from a chord is no such measure: it
+// also grows with gentle curvature over thousands of diagonals.
+static __device__ int g_cf_range_limit = 100;
+static __device__ int g_cf_range_maxlen = 0;  // lengths a considered (0: all)
+__device__ __forceinline__ int range_limit() { return *(volatile int *)&g_cf_range_limit; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_in_range(DP<T> p, int *spread_out) {
+  extern __shared__ double F[];  // [n]
+  __shared__ int smax, sflush;
+  const int n = p.n, t = threadIdx.x;
+  if (t == 0) {
+    smax = 0;
+    sflush = 0;
+  }
+  __syncthreads();
+  for (int y = t; y < n; y += blockDim.x) {
+    const T *u = p.Q5U + (size_t)y * BLK, *q = p.Q5P + (size_t)y * BLK;
+    double s = 0;
+    for (int e = 0; e < BLK; e++) s += (double)u[e] + (double)q[e];
+    if (!(s > 0)) atomicOr(&sflush, 1);
+    F[y] = s > 0 ? log2(s) + (double)__ldcg(p.E + y) : 0.0;
+  }
+  __syncthreads();
+  int best = 0;
+  const int amax = *(volatile int *)&g_cf_range_maxlen > 0 ? min(n, *(volatile int *)&g_cf_range_maxlen + 1) : n;
+  for (int a = 1 + t; a < amax; a += blockDim.x) {
+    double mx = -1e300, mn = 1e300;
+    for (int x = 0; x + a < n; x++) {
+      const double v = F[x + a] - F[x];
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    best = max(best, (int)ceil(mx - mn));
+  }
+  atomicMax(&smax, best);
+  __syncthreads();
+  if (t == 0) {
+    const int v = sflush ? 100000 : smax;
+    *spread_out = v;
+    if (sizeof(T) == sizeof(float) && v > range_limit()) atomicOr(p.err, ERR_RANGE_IN);
+  }
 }
 
 // ---------------------------------------------------------------- K1
@@ -177,12 +250,15 @@ __device__ __forceinline__ void ldg_row6(double (&r)[NS], const double *src) {
   }
 }
 
-// acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f op(A) op(B) over the live
-// rows (Ma), summation index (Ms) and columns (Mb); TA / TB read A / B
+// acc (rows 3 half .. 3 half + 2 of a 6x6 sum) += f op(A) fb op(B) over the
+// live rows (Ma), summation index (Ms) and columns (Mb); TA / TB read A / B
 // transposed.  A lane holds three rows of op(A) and one row of B at a time.
-template <bool TA, bool TB, typename T>
+// SPLIT applies the term's power-of-two factor in two halves, f to A and fb
+// to B, so that neither scaled operand leaves the binary32 range when the
+// whole factor is large and one mantissa small (the term itself is in range).
+template <bool TA, bool TB, bool SPLIT = false, typename T>
 __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, const T *B, T f, int half, int Ma,
-                                             int Ms, int Mb) {
+                                             int Ms, int Mb, T fb = (T)1) {
   constexpr int HR = NS / 2;
   T av[HR * NS];
 #pragma unroll
@@ -203,6 +279,10 @@ __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, 
       if (s < Ms) {
         T bv[NS];
         ldg_row6(bv, B + s * NS);
+        if (SPLIT) {
+#pragma unroll
+          for (int b = 0; b < NS; b++) bv[b] *= fb;
+        }
 #pragma unroll
         for (int r = 0; r < HR; r++)
           if (half * HR + r < Ma) {
@@ -218,6 +298,10 @@ __device__ __forceinline__ void bif_half_acc(T (&acc)[NS / 2 * NS], const T *A, 
       if (b < Mb) {
         T bv[NS];
         ldg_row6(bv, B + b * NS);
+        if (SPLIT) {
+#pragma unroll
+          for (int s = 0; s < NS; s++) bv[s] *= fb;
+        }
 #pragma unroll
         for (int r = 0; r < HR; r++)
           if (half * HR + r < Ma) {
@@ -264,8 +348,9 @@ __device__ __forceinline__ void in_bif_ext_group(const DP<T> &p, const BifBuf<T>
   for (int c = w; c < nc; c += 8) {
     const int k = 4 + c * 16 + sl;
     if (k <= d - 4) {
-      const T f = clamp_p2<T>(__ldcg(p.E + k) + __ldcg(p.E + d - k) - Eref);
-      bif_half_acc<false, false>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, f, half, Ma, p.Mp[k], Mb);
+      const int e = __ldcg(p.E + k) + __ldcg(p.E + d - k) - Eref;
+      bif_half_acc<false, false, true>(acc, p.Gx + (size_t)k * BLK, p.QB + cidx(n, k, d) * BLK, clamp_p2<T>(e >> 1),
+                                       half, Ma, p.Mp[k], Mb, clamp_p2<T>(e - (e >> 1)));
     }
   }
   bif_half_reduce(acc, red[w], lane);
@@ -292,7 +377,7 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
   const int slot = d % BIFRING;
   const int d0 = d / FARD * FARD;
   // a band whose exponent chord bends too far is summed here in full
-  const bool banded = bb.far != nullptr && far_band(d0) && __ldcg(bb.gdev + d0 / FARD) <= FAR_DEV_MAX;
+  const bool banded = bb.far != nullptr && far_band(d0) && __ldcg(bb.gdev + d0 / FARD) <= far_dev_max();
   int a1 = d - 4, a2 = d - 3;
   if (banded) {
     const int c = far_c(d0), alo = max(5, d - c), ahi = min(c, d - 4);
@@ -315,8 +400,13 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
       const int q = c * 16 + sl;
       if (q < n1 + n2) {
         const int k = x + (q < n1 ? 5 + q : a2 + q - n1);
-        const T f = ec * clamp_p2<T>(__ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref);
-        bif_half_acc<false, false>(acc, p.G + cidx(n, x, k) * BLK, p.QB + cidx(n, k, y) * BLK, f, half, Ma, p.Mp[k], Mb);
+        const int e = __ldcg(p.E + k - x) + __ldcg(p.E + y - k) - Eref;
+        const T *A = p.G + cidx(n, x, k) * BLK, *B = p.QB + cidx(n, k, y) * BLK;
+        if (banded)  // near split points of a tiled band: small factors
+          bif_half_acc<false, false>(acc, A, B, ec * clamp_p2<T>(e), half, Ma, p.Mp[k], Mb);
+        else  // every split point, with factors as large as the exponents' bend
+          bif_half_acc<false, false, true>(acc, A, B, ec * clamp_p2<T>(e >> 1), half, Ma, p.Mp[k], Mb,
+                                           clamp_p2<T>(e - (e >> 1)));
       }
     }
     bif_half_reduce(acc, red[w], lane);
@@ -365,6 +455,11 @@ __global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, in
 template <typename T>
 __global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
+  if (p.bstride) {
+    const long long off = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, off);
+    bb_shift(bb, off);
+  }
   for (int cb = blockIdx.x; cb <= p.n - d; cb += gridDim.x) {
     in_bif_cell<T, 8>(p, bb, d, cb, red);
     __syncthreads();
@@ -414,7 +509,7 @@ __device__ __forceinline__ const T *in_slot_src(const DP<T> &p, int s, int x, in
   const int Lmax = min(MAXLOOP, d - 4);
   if (s < SI_XIL) {  // YY_{L-1}[x+1][y], L = 3..30
     int L = s - SI_YYP + 3;
-    return (d >= 6 && L <= Lmax) ? p.YY + (cidx(n, x + 1, y) * NYY + (L - 3)) * BLK : nullptr;
+    return (d >= 6 && L <= Lmax) ? yy_in(p, x + 1, d - 1) + (size_t)(L - 3) * BLK : nullptr;
   }
   if (s < SI_CHL) {  // XI[x][y-L+2]
     int L = s - SI_XIL + 3, yl = y - L + 2;
@@ -627,7 +722,7 @@ __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, i
   const int kbeg = far_kmin(x0) + blockIdx.y * FARKS;
   const int kend = min(far_kmax(n, x0, d0), kbeg + FARKS - 1);
   if (kbeg > kend) return;
-  if (__ldcg(bb.gdev + d0 / FARD) > FAR_DEV_MAX) return;  // summed by the per-diagonal kernel
+  if (__ldcg(bb.gdev + d0 / FARD) > far_dev_max()) return;  // summed by the per-diagonal kernel
   const float *gsrc = bb.gfac + (size_t)((d0 / FARD) & 1) * n;
   for (int a = t; a <= c; a += 256) gf[a] = __ldcg(gsrc + a);
   if (t == 0) {
@@ -705,6 +800,34 @@ __global__ void __launch_bounds__(256) k_in_far(DP<float> p, BifBuf<float> bb, i
   }
 }
 
+// ---------------------------------------------------------------- checkpointed YY
+// One diagonal D of the interior partial sums, recomputed for the outside pass
+// from diagonal D - 1 (the block buffer, or the checkpoint at the start of a
+// block) with the light kernel's own recursion and operation order:
+//   YY_2 = XI,  YY_L[x][y] = T_x YY_{L-1}[x+1][y] + XI[x][y-L+2] CH[y-L+2][y],
+// so the values equal those the inside pass computed, bit for bit.  One
+// thread per output row (cell, L, state a): 29 x 6 rows per cell.
+template <typename T>
+__global__ void __launch_bounds__(192) k_yy_step(DP<T> p, int D) {
+  const int n = p.n, x = blockIdx.x, y = x + D;
+  const int t = threadIdx.x;
+  if (t >= NYY * NS) return;
+  const int L = 2 + t / NS, a = t % NS;
+  const int Lmax = min(MAXLOOP, D - 4);
+  T r[NS];
+  row_zero(r);
+  if (D >= 6 && L <= Lmax) {
+    if (L == 2) {
+      ld_row(r, p.XI + cidx(n, x, y) * BLK + a * NS);
+    } else {
+      row_mm(r, p.Tr + (size_t)x * BLK, yy_out(p, x + 1, D - 1) + (size_t)(L - 3) * BLK, a, (T)1);
+      const int yl = y - L + 2;
+      if (yl - x >= 6) row_mm(r, p.XI + cidx(n, x, yl) * BLK, p.CH + cidx(n, yl, y) * BLK, a, (T)1);
+    }
+  }
+  st_row(yy_out(p, x, D) + (size_t)(L - 2) * BLK + a * NS, r);
+}
+
 __host__ __device__ constexpr size_t in_far_smem(int c) {
   return ((size_t)2 * FARKC * (FARTX + FARTX + FARD - 1) * BLK + (size_t)(c + 1)) * sizeof(float);
 }
@@ -776,7 +899,7 @@ __device__ __forceinline__ T *light_dst(const DP<T> &p, int k, int x, int d, siz
   const int Lmax = min(MAXLOOP, d - 4);
   if (k == 0) return p.CH + c * BLK;
   if (k == 1) return d >= 6 ? p.XI + c * BLK : nullptr;
-  if (k < 31) return (d >= 6 && k <= Lmax) ? p.YY + (c * NYY + (k - 2)) * BLK : nullptr;  // YY_k
+  if (k < 31) return (d >= 6 && k <= Lmax) ? yy_in(p, x, d) + (size_t)(k - 2) * BLK : nullptr;  // YY_k
   switch (k) {
     case 31: return d >= 2 ? p.HB + c * BLK : nullptr;
     case 32: return d >= 4 ? p.QB + c * BLK : nullptr;
@@ -856,8 +979,9 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   }
   T cHL = 0;
   if (t == NTT - 2) cHL = p.eHL[d + 1];  // hairpin length factor of the cell
-  const T *src0 = t < SI_N ? bb.stab[(size_t)d * SI_N + t] : nullptr;
-  T *dst0 = t < NCOPY ? bb.dtab[(size_t)d * NCOPY + t] : nullptr;
+  const long long boff = (long long)blockIdx.y * p.bstride;  // batch: protein 0's addresses + boff
+  const T *src0 = t < SI_N ? bshift(bb.stab[(size_t)d * SI_N + t], boff) : nullptr;
+  T *dst0 = t < NCOPY ? bshift(bb.dtab[(size_t)d * NCOPY + t], boff) : nullptr;
   __syncthreads();
   // Staging: one TMA bulk copy per input block (the interior partial sums
   // YY_{L-1}[x+1][y], L = 3..Lmax, are contiguous and go as one copy); slots
@@ -1172,6 +1296,11 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
 template <typename T, int NTT>
 __global__ void __launch_bounds__(NTT, 1024 / NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (p.bstride) {
+    const long long off = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, off);
+    bb_shift(bb, off);
+  }
   in_light_cell<T, NTT>(p, bb, d, blockIdx.x, smem_raw);
 }
 

@@ -26,6 +26,12 @@ namespace cf {
 // marginal from the top-level weights.
 template <typename T>
 __global__ void k_marginals(DP<T> p, double *trans, double *p0) {
+  if (p.bstride) {  // batch: blockIdx.y is the protein
+    const long long o = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, o);
+    trans = bshift(trans, o);
+    p0 = bshift(p0, o);
+  }
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = p.n;
   if (r == 0) {
@@ -80,6 +86,12 @@ __device__ __forceinline__ double codon_marg_of(const double *trans, const doubl
 template <typename T>
 __global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, const int *cid, double *cm,
                             double *bm, double *pg) {
+  if (p.bstride) {  // batch: blockIdx.y is the protein
+    const long long o = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, o);
+    trans = bshift(trans, o), p0 = bshift(p0, o), cid = bshift(cid, o);
+    cm = bshift(cm, o), bm = bshift(bm, o), pg = bshift(pg, o);
+  }
   const int n = p.n, m = p.m;
   const int nb1 = (6 * m + n + blockDim.x - 1) / blockDim.x;
   if ((int)blockIdx.x < nb1) {
@@ -88,6 +100,7 @@ __global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, cons
       const int r = t / 6, a = t % 6;
       const int q = 3 * r;  // first position of residue r
       cm[t] = (a < p.Mp[q]) ? codon_marg_of(trans, p0, r, a, r ? p.Mp[q - 1] : 0) : 0.0;
+      if (!isfinite(cm[t])) atomicOr(p.err, ERR_OUT_NONFINITE);
       return;
     }
     const int u = t - m * 6;
@@ -116,8 +129,13 @@ __global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, cons
   if (lane == 0) pg[u] = s;
 }
 
-// Unpaired probability of every base: 1 - sum of its pair probabilities.
-__global__ void k_unpaired(float *P, int n) {
+// Unpaired probability of every base: 1 - sum of its pair probabilities; a
+// row with a non-finite entry raises ERR_OUT_NONFINITE.
+__global__ void k_unpaired(float *P, int n, int *err, long long bstride = 0) {
+  if (bstride) {  // batch: blockIdx.y is the protein
+    P = bshift(P, (long long)blockIdx.y * bstride);
+    err = bshift(err, (long long)blockIdx.y * bstride);
+  }
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -125,7 +143,10 @@ __global__ void k_unpaired(float *P, int n) {
   for (int j = lane; j < n; j += 32)
     if (j != i) s += (double)P[(size_t)i * n + j];
   s = warp_sum(s);
-  if (lane == 0) P[(size_t)i * n + i] = (float)(1.0 - s);
+  if (lane == 0) {
+    if (!isfinite(s)) atomicOr(err, ERR_OUT_NONFINITE);
+    P[(size_t)i * n + i] = (float)(1.0 - s);
+  }
 }
 
 }  // namespace cf

@@ -43,6 +43,19 @@ struct OutBuf {
   const T **stab;  // [n][SS_N] sources of the side work's staged slots for cell x = 0 (nullptr: not staged)
 };
 
+// Protein b's view of a batch (see DP::bstride).
+template <typename T>
+__device__ __forceinline__ void ob_shift(OutBuf<T> &o, long long off) {
+  o.hg = bshift(o.hg, off);
+  o.hq = bshift(o.hq, off);
+  o.hgx = bshift(o.hgx, off);
+  o.far = bshift(o.far, off);
+  o.fwh = bshift(o.fwh, off);
+  o.fdev = bshift(o.fdev, off);
+  o.otab = bshift(o.otab, off);
+  o.stab = bshift(o.stab, off);
+}
+
 // ---------------------------------------------------------------- far bands
 // The gathers of a target cell on diagonal a read adjoints hQM2pp on
 // diagonals a+4 .. n-1.  For the targets of a band [alo, alo + OFD), the terms
@@ -56,7 +69,7 @@ struct OutBuf {
 // 2^{s D + e0 - E[D]}; every far term of a target on diagonal a is then
 // relative to the common factor ec 2^{E[a] - s a}.  As for the inside far
 // bands, the factor kernel records the largest deviation of E from the chord;
-// past FAR_DEV_MAX no band of the pass is tiled (k_out_far returns at once)
+// past g_cf_far_dev_max no band of the pass is tiled (k_out_far returns at once)
 // and the per-diagonal gathers take every term with its exact factor.
 constexpr int OFD = 16;   // target diagonals per band
 constexpr int OFTX = 16;  // target rows per tile
@@ -201,8 +214,9 @@ __device__ __forceinline__ void out_bif_ext_group(const DP<T> &p, const OutBuf<T
   for (int c = w; c < nc; c += 8) {
     const int yy = d + 4 + c * 16 + sl;
     if (yy <= n - 1) {
-      const T f = clamp_p2<T>(Ed + p.E[yy - d] - p.E[yy]);
-      bif_half_acc<false, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, f, half, Ma, p.Mp[yy], Mb);
+      const int e = Ed + p.E[yy - d] - p.E[yy];
+      bif_half_acc<false, true, true>(acc, p.hQ5P + (size_t)yy * BLK, p.QB + cidx(n, d, yy) * BLK, clamp_p2<T>(e >> 1),
+                                      half, Ma, p.Mp[yy], Mb, clamp_p2<T>(e - (e >> 1)));
     }
   }
   bif_half_reduce(acc, red[w], lane);
@@ -224,7 +238,7 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
   const int slot = d % BIFRING;
   const T ec = p.en[EN_EC];
   const int alo = d / OFD * OFD;
-  const bool banded = ob.far != nullptr && of_band(n, alo) && __ldcg(ob.fdev) <= FAR_DEV_MAX;
+  const bool banded = ob.far != nullptr && of_band(n, alo) && __ldcg(ob.fdev) <= far_dev_max();
   if (cb0 + g < ncell) {
     const int x = cb0 + g, y = x + d;
     const int Ma = p.Mp[x], Mb = p.Mp[y];
@@ -237,9 +251,13 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
       for (int q = 0; q < nr; q++) {
         const int yy = y + 4 + q * 16 + sl;
         if (yy <= ylim) {
-          const T f = ec * clamp_p2<T>(Ed + E[yy - y] - E[yy - x]);
-          bif_half_acc<false, true>(acc, p.hQM2pp + cidx(n, x, yy) * BLK, p.QB + cidx(n, y, yy) * BLK, f, half, Ma,
-                                    p.Mp[yy], Mb);
+          const int e = Ed + E[yy - y] - E[yy - x];
+          const T *A = p.hQM2pp + cidx(n, x, yy) * BLK, *B = p.QB + cidx(n, y, yy) * BLK;
+          if (banded)
+            bif_half_acc<false, true>(acc, A, B, ec * clamp_p2<T>(e), half, Ma, p.Mp[yy], Mb);
+          else  // every term, with factors as large as the exponents' bend: split between the operands
+            bif_half_acc<false, true, true>(acc, A, B, ec * clamp_p2<T>(e >> 1), half, Ma, p.Mp[yy], Mb,
+                                            clamp_p2<T>(e - (e >> 1)));
         }
       }
     } else {
@@ -248,9 +266,13 @@ __device__ __forceinline__ void out_bif_group(const DP<T> &p, const OutBuf<T> &o
       for (int q = 0; q < nq; q++) {
         const int xx = x - 5 - q * 16 - sl;
         if (xx >= xlo) {
-          const T f = ec * clamp_p2<T>(E[x - xx] + Ed - E[y - xx]);
-          bif_half_acc<true, false>(acc, p.G + cidx(n, xx, x) * BLK, p.hQM2pp + cidx(n, xx, y) * BLK, f, half, Ma,
-                                    p.Mp[xx], Mb);
+          const int e = E[x - xx] + Ed - E[y - xx];
+          const T *A = p.G + cidx(n, xx, x) * BLK, *B = p.hQM2pp + cidx(n, xx, y) * BLK;
+          if (banded)
+            bif_half_acc<true, false>(acc, A, B, ec * clamp_p2<T>(e), half, Ma, p.Mp[xx], Mb);
+          else
+            bif_half_acc<true, false, true>(acc, A, B, ec * clamp_p2<T>(e >> 1), half, Ma, p.Mp[xx], Mb,
+                                            clamp_p2<T>(e - (e >> 1)));
         }
       }
     }
@@ -324,7 +346,7 @@ __global__ void __launch_bounds__(256) k_out_far(DP<float> p, OutBuf<float> ob, 
   const int lo = ROW ? x0 + c : 0, hi = ROW ? n - 1 : x0 + OFTX - 1 + alo + OFD - 1 - c;
   const int kbeg = lo + blockIdx.y * OFKS, kend = min(hi, kbeg + OFKS - 1);
   if (kbeg > kend) return;
-  if (__ldcg(ob.fdev) > FAR_DEV_MAX) return;  // every term is gathered per diagonal
+  if (__ldcg(ob.fdev) > far_dev_max()) return;  // every term is gathered per diagonal
   for (int D = t; D < n; D += 256) {
     fw[D] = __ldcg(ob.fwh + D);
     fh[D] = __ldcg(ob.fwh + n + D);
@@ -572,6 +594,11 @@ __global__ void k_out_slot_tab(DP<T> p, OutBuf<T> ob) {
 template <typename T, int NTT>
 __global__ void __launch_bounds__(NTT, 1536 / NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const long long boff = (long long)blockIdx.y * p.bstride;  // batch: protein b's slab
+  if (boff) {
+    dp_shift(p, boff);
+    ob_shift(ob, boff);
+  }
   T *S = (T *)smem_raw;            // [SO_N][36]
   T *HY = S + (size_t)SO_N * BLK;  // [29][36] interior partial-sum adjoints
   T *W = HY + NYY * BLK;           // work blocks
@@ -622,7 +649,10 @@ __global__ void __launch_bounds__(NTT, 1536 / NTT) k_out_light(DP<T> p, OutBuf<T
     if (L >= 2 && d - L + 2 >= 0) cwI = in * clamp_p2<T>(p.E[d - L + 2] - E0);
   }
   OSlot<T> e{nullptr, 0, -1};
-  if (t < SO_N) e = ob.otab[(size_t)d * SO_N + t];
+  if (t < SO_N) {
+    e = ob.otab[(size_t)d * SO_N + t];
+    e.src = bshift(e.src, boff);  // the table holds protein 0's addresses
+  }
   // staging: one TMA bulk copy per input block, completing on a barrier at
   // which every thread arrives once with its copy's bytes
   __shared__ __align__(8) unsigned long long obar;
@@ -954,7 +984,7 @@ __device__ __forceinline__ const T *side_slot_src(const DP<T> &p, int s, int x, 
   }
   if (s < SS_XIL) {  // YY_{L-1}[x+1][y], L = 3..30
     const int L = s - SS_YYP + 3;
-    return (d >= 6 && L <= Lmax) ? p.YY + (cidx(n, x + 1, y) * NYY + (L - 3)) * BLK : nullptr;
+    return (d >= 6 && L <= Lmax) ? yy_out(p, x + 1, d - 1) + (size_t)(L - 3) * BLK : nullptr;
   }
   if (s < SS_BQ3) {  // XI[x][yl] and CH[yl][y], yl = y - L + 2, L = 3..30
     const int L = (s - SS_XIL) % 28 + 3, yl = y - L + 2;
@@ -1024,7 +1054,7 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
   }
   if (t < EN_N) cEn = p.en[t];
   static_assert(NT3 >= SS_N, "one staged slot per thread");
-  const T *src0 = t < SS_N ? ob.stab[(size_t)d * SS_N + t] : nullptr;
+  const T *src0 = t < SS_N ? bshift(ob.stab[(size_t)d * SS_N + t], (long long)blockIdx.y * p.bstride) : nullptr;
   // staging: one TMA bulk copy per input block, the interior-loop adjoints
   // hYY_L (L = 2..Lmax) and partial sums YY_{L-1}[x+1][y] (L = 3..Lmax) as one
   // copy each; the partial sums only for a boundary at x (the ring term of the
@@ -1149,6 +1179,11 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 template <typename T, bool GRP>
 __global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (p.bstride) {
+    const long long boff = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, boff);
+    ob_shift(ob, boff);
+  }
   __shared__ T red[16][BLK];
   __shared__ SideCtx cx;
   __shared__ T sEn[EN_N], wBu[MAXLOOP + 1];
@@ -1281,7 +1316,8 @@ __device__ __forceinline__ void tg_issue(const DP<T> &p, int role, int x, int y,
 template <typename T>
 __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = p.n, q = blockIdx.y, role = blockIdx.z;
+  if (p.bstride) dp_shift(p, (long long)(blockIdx.z >> 1) * p.bstride);  // batch: z = 2 protein + role
+  const int n = p.n, q = blockIdx.y, role = blockIdx.z & 1;
   if (q >= n - 1 || p.bnd[q] == 0) return;
   const int ncell = role == 0 ? n - 1 - q : q + 1;  // role 0: y = q+1..n-1; role 1: x = 0..q
   const int c0 = blockIdx.x * TG_CELLS;

@@ -97,6 +97,32 @@ __device__ __forceinline__ double dv(const T *blk, int a, int b) {
   return (double)blk[a * NS + b];
 }
 
+// Entry (a, b) of the interior partial sum YY_L of cell (x, y) from its
+// definition, for the checkpointed form (where YY is not kept for every
+// cell): the sum over the L - 1 placements j of the inner pair of
+//   CH[x][x+j] XI[x+j][y-L+2+j] CH[y-L+2+j][y]
+// (every term on XI's diagonal d - L + 2, the exponent of YY_L).
+template <typename T>
+__device__ __forceinline__ double yy_entry(const DP<T> &p, int x, int y, int L, int a, int b) {
+  const int n = p.n, d = y - x;
+  double s = 0;
+  for (int j = 0; j <= L - 2; j++) {
+    const int xi = x + j, yi = y - L + 2 + j;
+    if (yi - xi < 6) continue;
+    const T *c1 = p.CH + cidx(n, x, xi) * BLK, *xb = p.XI + cidx(n, xi, yi) * BLK, *c2 = p.CH + cidx(n, yi, y) * BLK;
+    const int Mu = p.Mp[xi], Mv = p.Mp[yi];
+    for (int u = 0; u < Mu; u++) {
+      const double cu = dv(c1, a, u);
+      if (cu == 0) continue;
+      double t = 0;
+      for (int v = 0; v < Mv; v++) t += dv(xb, u, v) * dv(c2, v, b);
+      s += cu * t;
+    }
+  }
+  (void)d;
+  return s;
+}
+
 __device__ __forceinline__ double dp2(int e) { return ldexp(1.0, e); }
 
 template <typename T>
@@ -262,7 +288,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs<T> s) {
             int LL = k + 1;
             if (d < 6 || LL > min(MAXLOOP, d - 4)) return 0.0;
             int ey = (LL == 2) ? Ed : E[d - LL + 2];
-            return (double)en[EN_IN + LL] * dp2(ey - Ed) * tmo * dv(p.YY + (c * NYY + (LL - 2)) * BLK, a, b);
+            const double yy = p.yyck ? yy_entry(p, x, y, LL, a, b) : dv(p.YY + (c * NYY + (LL - 2)) * BLK, a, b);
+            return (double)en[EN_IN + LL] * dp2(ey - Ed) * tmo * yy;
           }
           int r = k - 1 - NYY, LL = r / (2 * NS) + 1, side = (r / NS) & 1, sst = r % NS;
           if (d - LL < 4) return 0.0;
@@ -287,6 +314,26 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs<T> s) {
             push(el_pack(EL_B, x + LL, y, sst, b, 0));
           }
         }
+        continue;
+      }
+      if (kind == EL_YY && p.yyck) {
+        // checkpointed form: the placement j of the inner pair and the states
+        // (u at x+j, v at y-L+2+j) in one draw, from the definition of YY_L
+        const int a = p1, b = p2;
+        setst(x, a);
+        setst(y, b);
+        int k = warp_select((L - 1) * BLK, [&](int k) {
+          const int j = k / BLK, u = (k % BLK) / NS, v = k % NS;
+          const int xi = x + j, yi = y - L + 2 + j;
+          if (yi - xi < 6 || u >= p.Mp[xi] || v >= p.Mp[yi]) return 0.0;
+          return dv(p.CH + cidx(n, x, xi) * BLK, a, u) * dv(p.XI + cidx(n, xi, yi) * BLK, u, v) *
+                 dv(p.CH + cidx(n, yi, y) * BLK, v, b);
+        }, u, lane);
+        if (k < 0) { bad = 10; continue; }
+        const int j = k / BLK, uu = (k % BLK) / NS, vv = k % NS, xi = x + j, yi = y - L + 2 + j;
+        push(el_pack(EL_CH, x, xi, a, uu, 0));
+        push(el_pack(EL_XI, xi, yi, uu, vv, 0));
+        push(el_pack(EL_CH, yi, y, vv, b, 0));
         continue;
       }
       if (kind == EL_YY) {

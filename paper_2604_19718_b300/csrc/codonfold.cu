@@ -8,7 +8,8 @@
 // pair-tt with soft weights) and log Z in cf_inside.cuh, the inside wavefront
 // in cf_inside2.cuh, the outside pass and the marginals in cf_outside2.cuh and
 // cf_outside.cuh, the sampler in cf_sample.cuh and the fixed-sequence windows
-// in cf_window.cuh.
+// in cf_window.cuh, the minimum free energy pass and its traceback in
+// cf_mfe.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +26,7 @@
 #include "cf_common.cuh"
 #include "cf_inside.cuh"
 #include "cf_inside2.cuh"
+#include "cf_mfe.cuh"
 #include "cf_outside.cuh"
 #include "cf_outside2.cuh"
 #include "cf_sample.cuh"
@@ -119,6 +121,19 @@ struct PrecTables {
   std::vector<void *> allocs;
 };
 
+// Minimum free energy form: integer-cost tables, the pass as one graph, and
+// the traceback's scratch (per protein length).
+struct MfeTables {
+  bool alloc = false;
+  MfeDP dp{};
+  cudaGraphExec_t g = nullptr;
+  int nodes = 0;
+  int4 *stack = nullptr;
+  int *state = nullptr;
+  int32_t *codons = nullptr, *partner = nullptr;
+  std::vector<void *> allocs;
+};
+
 struct cf_problem {
   const cf_model *model = nullptr;
   int device = 0;
@@ -167,6 +182,11 @@ struct cf_problem {
   double *win_hlogz = nullptr;
   size_t win_hbases_cap = 0, win_hnwin_cap = 0;
   float t_win = 0;
+  MfeTables mfe;
+  float t_mfe = 0;
+  int ck_request = -1;  // -1: checkpoint the interior partial sums from CF_CHECKPOINT_MIN_N on; 0 never; 1 always
+  int batch = 1;        // proteins of a batch (cf_batch_*), one slab each
+  long long bstride = 0;  // bytes between the slabs of a batch
 };
 
 namespace {
@@ -192,12 +212,28 @@ cf_status cuda_fail(cf_problem *p, cudaError_t e, const char *where) {
 // that succeed before one is made to fail; negative = off.
 std::atomic<long long> g_fail_alloc_after{-1};
 
+// A batch of equal-length proteins places every array of its first protein in
+// one slab (bump allocation from this thread's arena while it is set); the
+// other proteins' slabs follow at a fixed stride.
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, used = 0;
+};
+thread_local Arena *g_arena = nullptr;
+
 template <typename V>
 cudaError_t dalloc(std::vector<void *> &list, V **ptr, size_t count) {
   long long k = g_fail_alloc_after.load();
   while (k >= 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
   }
   if (k == 0) return cudaErrorMemoryAllocation;  // forced failure, nothing allocated
+  if (g_arena) {
+    const size_t bytes = (count * sizeof(V) + 255) / 256 * 256;
+    if (g_arena->used + bytes > g_arena->cap) return cudaErrorMemoryAllocation;
+    *ptr = (V *)(g_arena->base + g_arena->used);
+    g_arena->used += bytes;
+    return cudaSuccess;  // owned by the batch buffer, not by the list
+  }
   void *q = nullptr;
   cudaError_t e = cudaMalloc(&q, count * sizeof(V));
   if (e != cudaSuccess) return e;
@@ -209,6 +245,13 @@ cudaError_t dalloc(std::vector<void *> &list, V **ptr, size_t count) {
 void free_list(std::vector<void *> &list) {
   for (void *q : list) cudaFree(q);
   list.clear();
+}
+
+void free_mfe(MfeTables &t) {
+  if (t.g) cudaGraphExecDestroy(t.g);
+  t.g = nullptr;
+  free_list(t.allocs);
+  t = MfeTables{};
 }
 
 template <typename T>
@@ -252,6 +295,18 @@ bool is_device_ptr(const void *ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Checkpointing of the interior partial sums (the outside pass recomputes
+// them in blocks of 64 diagonals instead of reading a table of 29 blocks per
+// cell): from this length on unless the problem asks otherwise.
+bool yy_checkpointed(const cf_problem *p) {
+  return p->ck_request == 1 || (p->ck_request < 0 && p->n >= CF_CHECKPOINT_MIN_N);
+}
+size_t yy_inside_elems(int n, int ck) {
+  return ck ? (size_t)2 * n * NYY * BLK : ncells(n) * NYY * BLK;
+}
+size_t yy_ck_elems(int n) { return ((size_t)n / YYCK_BLOCK + 1) * n * NYY * BLK; }
+size_t yy_block_elems(int n) { return (size_t)2 * YYCK_BLOCK * n * NYY * BLK; }
+
 template <typename T>
 cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   if (t.inside_alloc) return CF_OK;
@@ -293,8 +348,19 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
     CF_CUDA(p, dalloc(L, q, nc));
     CF_CUDA(p, cudaMemset(*q, 0, nc * sizeof(T)));
   }
-  CF_CUDA(p, dalloc(L, &d.YY, nc * NYY));
-  CF_CUDA(p, cudaMemset(d.YY, 0, nc * NYY * sizeof(T)));
+  // interior partial sums: stored whole, or checkpointed (a ring of two
+  // diagonals and every 64th diagonal; the outside pass recomputes blocks)
+  d.yyck = yy_checkpointed(p) ? 1 : 0;
+  const size_t yy_elems = yy_inside_elems(n, d.yyck);
+  d.YYck = nullptr;
+  d.YYb = nullptr;
+  CF_CUDA(p, dalloc(L, &d.YY, yy_elems));
+  CF_CUDA(p, cudaMemset(d.YY, 0, yy_elems * sizeof(T)));
+  if (d.yyck) {
+    const size_t ck = yy_ck_elems(n);
+    CF_CUDA(p, dalloc(L, &d.YYck, ck));
+    CF_CUDA(p, cudaMemset(d.YYck, 0, ck * sizeof(T)));
+  }
   T **ext[] = {&d.Q5U, &d.Q5P, &d.Gx};
   for (T **q : ext) {
     CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
@@ -307,6 +373,13 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   t.bb.farslices = far_nslice(n, 0, std::max(0, (n - 1) / FARD * FARD));  // the widest band's slices
   t.bb.gfac = nullptr;
   t.bb.gdev = nullptr;
+  t.bb.spread = nullptr;
+  if (n * sizeof(double) <= 200 * 1024 && p->batch == 1) {
+    CF_CUDA(p, dalloc(L, &t.bb.spread, (size_t)1));
+    CF_CUDA(p, cudaMemset(t.bb.spread, 0, sizeof(int)));
+    CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_range<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(n * sizeof(double))));
+  }
   if (sizeof(T) == sizeof(float) && n > 3 * FARD) {
     CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
     CF_CUDA(p, dalloc(L, &t.bb.gfac, (size_t)2 * n));
@@ -367,7 +440,8 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   ms.value = 0;
   ms.elementSize = 4;
   ms.width = (size_t)n * 2;
-  ms.height = 1;
+  ms.height = p->batch;
+  ms.pitch = p->batch > 1 ? (size_t)p->bstride : 0;
   cudaError_t e = cudaGraphAddMemsetNode(&mset, g, nullptr, 0, &ms);
   std::vector<cudaGraphNode_t> k2(n);
   std::vector<cudaGraphNode_t> k1(n);
@@ -423,7 +497,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
         kp.gridDim = dim3((n - d + 3) / 4 + 1);
       } else {
         kp.func = (void *)k_in_bif<T>;
-        kp.gridDim = dim3(std::min(n - d + 1, cap_bif));
+        kp.gridDim = dim3(std::min(n - d + 1, cap_bif), p->batch);
       }
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
@@ -441,7 +515,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     if (d >= 8) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_in_light<T, NT_IN>;
-    kp.gridDim = dim3(n - d);
+    kp.gridDim = dim3(n - d, p->batch);
     kp.blockDim = dim3(NT_IN);
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
@@ -453,12 +527,25 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     void *args[] = {&dp};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_inside_finish<T>;
-    kp.gridDim = dim3(1);
+    kp.gridDim = dim3(1, p->batch);
     kp.blockDim = dim3(32);
     kp.kernelParams = args;
     cudaGraphNode_t fin;
     e = cudaGraphAddKernelNode(&fin, g, &k2[n - 1], 1, &kp);
     nodes++;
+    if (e == cudaSuccess && t.bb.spread) {  // the range of the binary32 tables, after the pass
+      int *sp = t.bb.spread;
+      void *rargs[] = {&dp, &sp};
+      cudaKernelNodeParams kr = {};
+      kr.func = (void *)k_in_range<T>;
+      kr.gridDim = dim3(1, p->batch);
+      kr.blockDim = dim3(256);
+      kr.sharedMemBytes = (unsigned)(sizeof(double) * n);
+      kr.kernelParams = rargs;
+      cudaGraphNode_t rn;
+      e = cudaGraphAddKernelNode(&rn, g, &fin, 1, &kr);
+      nodes++;
+    }
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&t.gin, g, 0);
   cudaGraphDestroy(g);
@@ -481,6 +568,10 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   }
   CF_CUDA(p, dalloc(L, &d.hYY, (size_t)YRING * n * NYY * BLK));
   CF_CUDA(p, cudaMemset(d.hYY, 0, (size_t)YRING * n * NYY * BLK * sizeof(T)));
+  if (d.yyck) {
+    CF_CUDA(p, dalloc(L, &d.YYb, yy_block_elems(n)));
+    CF_CUDA(p, cudaMemset(d.YYb, 0, yy_block_elems(n) * sizeof(T)));
+  }
   T **ext[] = {&d.hQ5U, &d.hQ5P, &d.hGx};
   for (T **q : ext) {
     CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
@@ -495,7 +586,7 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   t.ob.far = nullptr;
   t.ob.fwh = nullptr;
   t.ob.fdev = nullptr;
-  if (sizeof(T) == sizeof(float) && of_band(n, 0)) {
+  if (sizeof(T) == sizeof(float) && of_band(n, 0) && p->batch == 1) {  // a batch gathers every term per diagonal
     CF_CUDA(p, dalloc(L, &t.ob.far, (size_t)6 * n * OFD * BLK));
     CF_CUDA(p, dalloc(L, &t.ob.fwh, (size_t)2 * n));
     CF_CUDA(p, dalloc(L, &t.ob.fdev, (size_t)1));
@@ -512,14 +603,16 @@ cf_status alloc_outside(cf_problem *p, PrecTables<T> &t) {
   return CF_OK;
 }
 
+// zero `bytes` at ptr, and at the same place of every slab of a batch
 cudaError_t add_memset(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *dep, int ndep, void *ptr,
-                       size_t bytes) {
+                       size_t bytes, int batch = 1, long long bstride = 0) {
   cudaMemsetParams ms = {};
   ms.dst = ptr;
   ms.value = 0;
   ms.elementSize = 4;
   ms.width = bytes / 4;
-  ms.height = 1;
+  ms.height = batch;
+  ms.pitch = batch > 1 ? (size_t)bstride : 0;
   return cudaGraphAddMemsetNode(node, g, dep, ndep, &ms);
 }
 
@@ -548,11 +641,13 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   DP<T> dp = t.dp;
   OutBuf<T> ob = t.ob;
   cudaGraphNode_t m[5];
-  cudaError_t e = add_memset(g, &m[0], nullptr, 0, dp.hCH, nc * sizeof(T));
-  if (e == cudaSuccess) e = add_memset(g, &m[1], &m[0], 1, dp.hXI, nc * sizeof(T));
-  if (e == cudaSuccess) e = add_memset(g, &m[2], &m[1], 1, dp.hT, (size_t)n * BLK * sizeof(double));
-  if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double));
-  if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float));
+  const int B = p->batch;
+  const long long bs = p->bstride;
+  cudaError_t e = add_memset(g, &m[0], nullptr, 0, dp.hCH, nc * sizeof(T), B, bs);
+  if (e == cudaSuccess) e = add_memset(g, &m[1], &m[0], 1, dp.hXI, nc * sizeof(T), B, bs);
+  if (e == cudaSuccess) e = add_memset(g, &m[2], &m[1], 1, dp.hT, (size_t)n * BLK * sizeof(double), B, bs);
+  if (e == cudaSuccess) e = add_memset(g, &m[3], &m[2], 1, dp.hX, (size_t)n * 4 * BLK * sizeof(double), B, bs);
+  if (e == cudaSuccess) e = add_memset(g, &m[4], &m[3], 1, dp.P, (size_t)n * n * sizeof(float), B, bs);
   std::vector<cudaGraphNode_t> k2(n), k1(n);
   // far bands (binary32): both gathers of band alo hang off the light kernel
   // of diagonal of_c(alo) and precede the bifurcation kernels of the band
@@ -620,7 +715,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
       kp.func = banded ? (void *)k_out_off<T, true> : (void *)k_out_off<T, false>;  // far bands: grouped gathers
-      kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0));
+      kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0), B);
       kp.blockDim = dim3(NT3);
       kp.sharedMemBytes = (unsigned)smem3;
       kp.kernelParams = oargs;
@@ -642,7 +737,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;
     kp.func = wide ? (void *)k_out_light<T, NT_WIDE> : (void *)k_out_light<T, NT>;
-    kp.gridDim = dim3(n - d);
+    kp.gridDim = dim3(n - d, B);
     kp.blockDim = dim3(wide ? NT_WIDE : NT);
     kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
     kp.kernelParams = args;
@@ -650,13 +745,46 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
   }
+  // checkpointed interior partial sums: block b (diagonals 64b .. 64b + 62;
+  // 64b + 63 is a checkpoint) is recomputed by a chain of one launch per
+  // diagonal, after the last reader of the previous block that used its
+  // buffer (block b + 2: the off-chain launch of 64b + 125) and before the
+  // light kernel of 64b + 64, after which the off-chain launches read it
+  if (e == cudaSuccess && dp.yyck) {
+    const int nblk = (n + YYCK_BLOCK - 1) / YYCK_BLOCK;
+    for (int b = nblk - 1; b >= 0 && e == cudaSuccess; b--) {
+      const int D0 = b * YYCK_BLOCK, D1 = std::min(n - 1, D0 + YYCK_BLOCK - 2);
+      cudaGraphNode_t prev = nullptr;
+      for (int D = D0; D <= D1 && e == cudaSuccess; D++) {
+        int DD = D;
+        void *args[] = {&dp, &DD};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)k_yy_step<T>;
+        kp.gridDim = dim3(n - D);
+        kp.blockDim = dim3(192);
+        kp.kernelParams = args;
+        cudaGraphNode_t deps[1];
+        int nd = 0;
+        if (prev) deps[nd++] = prev;
+        else if (D0 + 125 <= n - 1 && k1[D0 + 125]) deps[nd++] = k1[D0 + 125];
+        else deps[nd++] = first;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, g, deps, nd, &kp);
+        if (e == cudaSuccess) e = set_priority(node, false);
+        nodes++;
+        prev = node;
+      }
+      if (e == cudaSuccess && prev)
+        e = cudaGraphAddDependencies(g, &prev, &k2[std::min(n - 1, D0 + YYCK_BLOCK)], nullptr, 1);
+    }
+  }
   // transfer gradients of every boundary position, after the whole chain
   cudaGraphNode_t ktg = nullptr;
   if (e == cudaSuccess) {
     void *args[] = {&dp};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_out_tg<T>;
-    kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, n, 2);
+    kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, n, 2 * B);
     kp.blockDim = dim3(256);
     kp.sharedMemBytes = (unsigned)out_tg_smem<T>();
     kp.kernelParams = args;
@@ -669,7 +797,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     void *args[] = {&dp, &trans, &p0};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_marginals<T>;
-    kp.gridDim = dim3((std::max(p->m - 1, 1) + 127) / 128);
+    kp.gridDim = dim3((std::max(p->m - 1, 1) + 127) / 128, B);
     kp.blockDim = dim3(128);
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&fin, g, &ktg, 1, &kp);
@@ -678,10 +806,12 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (e == cudaSuccess) {
     float *P = dp.P;
     int nn = n;
-    void *args[] = {&P, &nn};
+    int *er = dp.err;
+    long long bsl = bs;
+    void *args[] = {&P, &nn, &er, &bsl};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_unpaired;
-    kp.gridDim = dim3((n + 7) / 8);
+    kp.gridDim = dim3((n + 7) / 8, B);
     kp.blockDim = dim3(256);
     kp.kernelParams = args;
     cudaGraphNode_t un;
@@ -695,7 +825,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     void *args[] = {&dp, &trans, &p0, &cid, &cm, &bm, &pg};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_codon_out<T>;
-    kp.gridDim = dim3((p->m * 6 + n + 127) / 128 + (61 * 61 + 3) / 4);  // threads, then 4 warps a block
+    kp.gridDim = dim3((p->m * 6 + n + 127) / 128 + (61 * 61 + 3) / 4, B);  // threads, then 4 warps a block
     kp.blockDim = dim3(128);
     kp.kernelParams = args;
     cudaGraphNode_t co;
@@ -732,7 +862,8 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   CF_CUDA(p, cudaGraphLaunch(t.gin, st));
   int launches = t.gin_nodes;
-  k_logz<<<1, 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, p->m - 1, p->dlogz);
+  k_logz<<<dim3(1, p->batch), 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, p->m - 1, p->dlogz,
+                                           p->batch > 1 ? p->bstride : 0);
   launches++;
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaEventRecord(p->ev[1], st));
@@ -745,6 +876,10 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   CF_CUDA(p, cudaEventElapsedTime(&p->t_in, p->ev[0], p->ev[1]));
   p->l_in = launches;
   if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "inside: a bounded wait for staged inputs gave up");
+  if (err & ERR_RANGE_IN)
+    return fail(p, CF_ENUMERIC,
+                "inside: binary32 range exceeded (the strengths of the intervals of one length spread over more "
+                "bits than binary32 holds: a composition that changes strongly along the protein); use CF_FP64");
   if (err || !(zm > 0) || !std::isfinite(zm))
     return fail(p, CF_ENUMERIC, "inside: non-finite or zero partition function after scaling");
   *logZ = lz;
@@ -876,7 +1011,9 @@ cf_status clear_tables(cf_problem *p, PrecTables<T> &t) {
   if (t.inside_alloc) {
     T *tabs[] = {d.CH, d.QB, d.XI, d.HB, d.QMpp, d.QMpu, d.G, d.QM2pp, d.QM2pu, d.QM2up, d.QM2uu};
     for (T *q : tabs) CF_CUDA(p, cudaMemsetAsync(q, 0, nc * sizeof(T), st));
-    CF_CUDA(p, cudaMemsetAsync(d.YY, 0, nc * NYY * sizeof(T), st));
+    CF_CUDA(p, cudaMemsetAsync(d.YY, 0, yy_inside_elems(n, d.yyck) * sizeof(T), st));
+    if (d.YYck) CF_CUDA(p, cudaMemsetAsync(d.YYck, 0, yy_ck_elems(n) * sizeof(T), st));
+    if (d.YYb) CF_CUDA(p, cudaMemsetAsync(d.YYb, 0, yy_block_elems(n) * sizeof(T), st));
     T *ext[] = {d.Q5U, d.Q5P, d.Gx};
     for (T *q : ext) CF_CUDA(p, cudaMemsetAsync(q, 0, (size_t)n * BLK * sizeof(T), st));
   }
@@ -898,6 +1035,185 @@ cf_status upload_transfers(cf_problem *p, PrecTables<T> &t) {
   k_cast<T><<<148, 256, 0, p->stream>>>(p->dX64, (T *)t.dp.X, (size_t)n * 4 * BLK);
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaStreamSynchronize(p->stream));
+  return CF_OK;
+}
+
+// ---- minimum free energy (min-sum recursions on integer costs)
+
+// cost of an energy in kcal/mol on the 2^-32 kcal/mol grid, rounded half away
+// from zero (the rounding every implementation of the model applies once per
+// elementary term)
+long long qcost(double e) { return std::llround(e * 4294967296.0); }
+
+cf_status mfe_alloc(cf_problem *p) {
+  MfeTables &t = p->mfe;
+  if (t.alloc) return CF_OK;
+  const int n = p->n;
+  const size_t nc = ncells(n) * BLK;
+  MfeDP &d = t.dp;
+  d.n = n;
+  d.m = p->m;
+  d.Mp = p->dM;
+  d.base = p->dbase;
+  d.cid = p->dcid;
+  d.err = p->derr;
+  auto &L = t.allocs;
+  mq *tau, *chi, *en, *hq, *u0;
+  CF_CUDA(p, dalloc(L, &tau, (size_t)n * BLK));
+  CF_CUDA(p, dalloc(L, &chi, (size_t)n * 4 * BLK));
+  CF_CUDA(p, dalloc(L, &en, (size_t)EN_N));
+  CF_CUDA(p, dalloc(L, &hq, (size_t)n + 2));
+  CF_CUDA(p, dalloc(L, &u0, (size_t)NS));
+  d.tau = tau;
+  d.chi = chi;
+  d.en = en;
+  d.hq = hq;
+  d.u0 = u0;
+  mq **tabs[] = {&d.CH, &d.QB, &d.XI, &d.QMP, &d.QMU, &d.GP, &d.BP, &d.M2PU, &d.M2UP, &d.M2UU};
+  for (mq **q : tabs) CF_CUDA(p, dalloc(L, q, nc));
+  CF_CUDA(p, dalloc(L, &d.W, (size_t)3 * n * MW * BLK));
+  CF_CUDA(p, dalloc(L, &d.R, (size_t)3 * n * MRF * BLK));
+  CF_CUDA(p, dalloc(L, &d.F, (size_t)3 * n * MRF * BLK));
+  mq **ext[] = {&d.Q5U, &d.Q5P, &d.GX, &d.X5};
+  for (mq **q : ext) CF_CUDA(p, dalloc(L, q, (size_t)n * BLK));
+  CF_CUDA(p, dalloc(L, &d.best, (size_t)1));
+  CF_CUDA(p, dalloc(L, &t.stack, (size_t)4 * n + 64));
+  CF_CUDA(p, dalloc(L, &t.state, (size_t)n));
+  CF_CUDA(p, dalloc(L, &t.codons, (size_t)p->m));
+  CF_CUDA(p, dalloc(L, &t.partner, (size_t)n));
+  // every table starts "infinite" (byte pattern 0x10 = MQINF); entries the
+  // pass never writes (bifurcations of short diagonals) keep that value
+  for (mq **q : tabs) CF_CUDA(p, cudaMemset(*q, 0x10, nc * sizeof(mq)));
+  for (mq **q : ext) CF_CUDA(p, cudaMemset(*q, 0x10, (size_t)n * BLK * sizeof(mq)));
+  // model costs: the energy-factor layout with each term as an integer cost
+  const double *pr = p->model->params;
+  std::vector<mq> ec(EN_N, 0), hc((size_t)n + 2, 0);
+  for (int k = 0; k < 36; k++) ec[EN_STK + k] = qcost(pr[k]);
+  for (int l = 0; l <= MAXLOOP; l++) {
+    ec[EN_BU + l] = qcost(pr[67 + l]);
+    ec[EN_IN + l] = qcost(pr[98 + l]);
+  }
+  for (int k = 0; k < 16; k++) {
+    ec[EN_TM + k] = qcost(pr[129 + k]);
+    ec[EN_D5 + k] = qcost(pr[145 + k]);
+    ec[EN_D3 + k] = qcost(pr[161 + k]);
+  }
+  ec[EN_EA] = qcost(pr[177]);
+  ec[EN_EB] = qcost(pr[178]);
+  ec[EN_EC] = qcost(pr[179]);
+  const double H30 = pr[36 + MAXLOOP];
+  for (int l = 0; l < n + 2; l++)
+    hc[l] = l <= MAXLOOP ? qcost(pr[36 + l]) : qcost(H30 + 1.07856 * std::log((double)l / MAXLOOP));
+  CF_CUDA(p, cudaMemcpy(en, ec.data(), sizeof(mq) * EN_N, cudaMemcpyHostToDevice));
+  CF_CUDA(p, cudaMemcpy(hq, hc.data(), sizeof(mq) * hc.size(), cudaMemcpyHostToDevice));
+  t.alloc = true;
+  return CF_OK;
+}
+
+// The pass as one CUDA graph: a chain of light kernels, one per diagonal, and
+// the bifurcation kernel of diagonal d hanging off the light kernel of d - 4.
+cf_status mfe_graph(cf_problem *p) {
+  MfeTables &t = p->mfe;
+  if (t.g) return CF_OK;
+  const int n = p->n;
+  cudaGraph_t g;
+  CF_CUDA(p, cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphNode_t> kl(n), kb(n);
+  MfeDP dp = t.dp;
+  cudaError_t e = cudaSuccess;
+  int nodes = 0;
+  for (int d = 0; d < n && e == cudaSuccess; d++) {
+    int dd = d;
+    void *args[] = {&dp, &dd};
+    if (d >= 8) {
+      cudaKernelNodeParams kp = {};
+      kp.func = (void *)k_mfe_bif;
+      kp.gridDim = dim3((n - d + 1 + 7) / 8);
+      kp.blockDim = dim3(256);
+      kp.kernelParams = args;
+      e = cudaGraphAddKernelNode(&kb[d], g, &kl[d - 4], 1, &kp);
+      if (e == cudaSuccess) e = set_priority(kb[d], false);
+      nodes++;
+    }
+    if (e != cudaSuccess) break;
+    cudaGraphNode_t deps[2];
+    int nd = 0;
+    if (d > 0) deps[nd++] = kl[d - 1];
+    if (d >= 8) deps[nd++] = kb[d];
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_mfe_light;
+    kp.gridDim = dim3(n - d);
+    kp.blockDim = dim3(MFE_NT);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&kl[d], g, deps, nd, &kp);
+    if (e == cudaSuccess) e = set_priority(kl[d], true);
+    nodes++;
+  }
+  if (e == cudaSuccess) {
+    void *args[] = {&dp};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_mfe_final;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    cudaGraphNode_t fin;
+    e = cudaGraphAddKernelNode(&fin, g, &kl[n - 1], 1, &kp);
+    nodes++;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&t.g, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(p, e, "mfe graph");
+  t.nodes = nodes;
+  return CF_OK;
+}
+
+cf_status run_mfe(cf_problem *p, int64_t *cost, double *kcal, int32_t *codons, int32_t *partner) {
+  const int kc = ptr_kind(codons, p->device), kp = ptr_kind(partner, p->device);
+  if (kc < 0 || kp < 0) return fail(p, CF_EINVAL, "cf_mfe: output is device memory of another device");
+  cf_status s = mfe_alloc(p);
+  if (s != CF_OK) {
+    free_mfe(p->mfe);
+    return s;
+  }
+  s = mfe_graph(p);
+  if (s != CF_OK) return s;
+  MfeTables &t = p->mfe;
+  cudaStream_t st = p->stream;
+  const int n = p->n, m = p->m;
+  CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  // the transfer costs of the current weights (cf_set_weights may have changed them)
+  k_mfe_transfers<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, t.dp.en, p->model->kT, p->dlw,
+                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0);
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaGraphLaunch(t.g, st));
+  const bool trace = codons || partner;
+  if (trace) {
+    MfeTrace tr;
+    tr.p = t.dp;
+    tr.stack = t.stack;
+    tr.cap = 4 * n + 64;
+    tr.state = t.state;
+    tr.codons = kc > 0 ? codons : t.codons;
+    tr.partner = kp > 0 ? partner : t.partner;
+    k_mfe_trace<<<1, 256, 0, st>>>(tr);
+    CF_CUDA(p, cudaGetLastError());
+  }
+  CF_CUDA(p, cudaEventRecord(p->ev[1], st));
+  long long q = 0;
+  int err = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&q, t.dp.best, sizeof(q), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (codons && kc == 0)
+    CF_CUDA(p, cudaMemcpyAsync(codons, t.codons, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
+  if (partner && kp == 0)
+    CF_CUDA(p, cudaMemcpyAsync(partner, t.partner, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&p->t_mfe, p->ev[0], p->ev[1]));
+  if (q >= MQHALF) return fail(p, CF_ENUMERIC, "cf_mfe: no configuration has a finite cost");
+  if (err) return fail(p, CF_ENUMERIC, "cf_mfe: traceback inconsistency (error word " + std::to_string(err) + ")");
+  if (cost) *cost = q;
+  if (kcal) *kcal = (double)q / 4294967296.0;
   return CF_OK;
 }
 
@@ -1081,6 +1397,7 @@ cf_status cf_problem_create(const cf_model *model, int device, void *stream, cf_
 static void release_protein(cf_problem *p) {
   free_prec(p->f32);
   free_prec(p->f64);
+  free_mfe(p->mfe);
   free_list(p->shared_allocs);
   free_list(p->smp_allocs);
   p->smp_cap = 0;
@@ -1276,6 +1593,7 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_out, p->ev[2], p->ev[3]));
   if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "outside: a bounded wait for staged inputs gave up");
+  if (err & ERR_OUT_NONFINITE) return fail(p, CF_ENUMERIC, "outside: a pair probability or marginal is not finite");
   return CF_OK;
 }
 
@@ -1305,6 +1623,35 @@ int cf_problem_length(const cf_problem *p) { return p ? p->n : 0; }
 const char *cf_last_error(const cf_problem *p) {
   if (p) return p->err.c_str();
   return g_last_error.c_str();
+}
+
+cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons, int32_t *partner) {
+  if (!p) return fail(p, CF_EINVAL, "cf_mfe: NULL problem");
+  if (p->n == 0) return fail(p, CF_ESTATE, "cf_mfe: no protein set");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  return run_mfe(p, cost, mfe_kcal, codons, partner);
+}
+
+float cf_mfe_last_ms(const cf_problem *p) { return p ? p->t_mfe : 0.f; }
+
+cf_status cf_set_checkpoint(cf_problem *p, int mode) {
+  if (!p || mode < -1 || mode > 1) return fail(p, CF_EINVAL, "cf_set_checkpoint: bad argument");
+  if (mode == p->ck_request) return CF_OK;
+  CF_CUDA(p, cudaSetDevice(p->device));
+  CF_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->ck_request = mode;
+  // the tables of both precisions are rebuilt in the requested form
+  free_prec(p->f32);
+  free_prec(p->f64);
+  p->have_inside = false;
+  return CF_OK;
+}
+
+int cf_checkpointed(const cf_problem *p) {
+  if (!p) return 0;
+  if (p->f32.inside_alloc) return p->f32.dp.yyck;
+  if (p->f64.inside_alloc) return p->f64.dp.yyck;
+  return yy_checkpointed(p) ? 1 : 0;
 }
 
 cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons, int32_t *partner) {
@@ -1406,13 +1753,18 @@ extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t see
 // ------------------------------------------------------------------ diagnostics and test hooks
 
 extern "C" cf_status cf_far_band_info(const cf_problem *p, int *in_max_dev, int *in_untiled, int *out_max_dev,
-                                      int *out_untiled) {
+                                      int *out_untiled, int *spread_bits) {
   if (!p) return CF_EINVAL;
-  int idev = 0, iun = 0, odev = 0, oun = 0;
+  int idev = 0, iun = 0, odev = 0, oun = 0, spr = 0;
   const PrecTables<float> &t = p->f32;
   if (cudaSetDevice(p->device) != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
     cudaGetLastError();
     return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: device not usable");
+  }
+  int far_max = 48;
+  if (cudaMemcpyFromSymbol(&far_max, g_cf_far_dev_max, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: bound");
   }
   if (t.inside_alloc && t.bb.gdev) {
     const int n = p->n;
@@ -1423,18 +1775,32 @@ extern "C" cf_status cf_far_band_info(const cf_problem *p, int *in_max_dev, int 
       if (far_band(d0)) {
         const int v = dev[(size_t)d0 / FARD];
         idev = std::max(idev, v);
-        iun += v > FAR_DEV_MAX ? 1 : 0;
+        iun += v > far_max ? 1 : 0;
       }
   }
   if (t.outside_alloc && t.ob.fdev) {
     if (cudaMemcpy(&odev, t.ob.fdev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: copy");
-    oun = odev > FAR_DEV_MAX ? 1 : 0;
+    oun = odev > far_max ? 1 : 0;
   }
   if (in_max_dev) *in_max_dev = idev;
   if (in_untiled) *in_untiled = iun;
+  if (t.inside_alloc && t.bb.spread &&
+      cudaMemcpy(&spr, t.bb.spread, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(const_cast<cf_problem *>(p), CF_ECUDA, "cf_far_band_info: copy");
   if (out_max_dev) *out_max_dev = odev;
   if (out_untiled) *out_untiled = oun;
+  if (spread_bits) *spread_bits = spr;
+  return CF_OK;
+}
+
+extern "C" cf_status cf_debug_set_range_limit(int device, int bits, int max_length) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cf_range_limit, &bits, sizeof(bits));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cf_range_maxlen, &max_length, sizeof(max_length));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cf_debug_set_range_limit");
   return CF_OK;
 }
 
@@ -1447,6 +1813,15 @@ extern "C" cf_status cf_debug_set_wait_polls(int device, unsigned long long poll
   return CF_OK;
 }
 
+extern "C" cf_status cf_debug_set_far_dev_max(int device, int bound) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_cf_far_dev_max, &bound, sizeof(bound));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cf_debug_set_far_dev_max");
+  return CF_OK;
+}
+
 extern "C" cf_status cf_debug_fail_alloc(long long after) {
   g_fail_alloc_after.store(after < 0 ? -1 : after);
   return CF_OK;
@@ -1454,4 +1829,264 @@ extern "C" cf_status cf_debug_fail_alloc(long long after) {
 
 extern "C" int cf_debug_classify_pointer(int memory_type, int pointer_device, int problem_device) {
   return classify_ptr(memory_type, pointer_device, problem_device);
+}
+
+// ------------------------------------------------------------------ batches of small proteins
+// B proteins of one length m <= CF_BATCH_MAX_M in one launch per kernel: every
+// array of protein 0 is placed in one slab (the same allocation sequence as a
+// single problem, bump-allocated from an arena), the other proteins' slabs
+// follow at a fixed stride, and each kernel of the inside and outside graphs
+// covers all proteins' cells of its diagonal (blockIdx.y = protein; the
+// kernels move their pointers by the protein's slab offset).
+
+namespace {
+
+__global__ void k_replicate(const uint4 *src, size_t n16, long long stride16, int nprot) {
+  const int b = blockIdx.y + 1;
+  if (b >= nprot) return;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n16; k += (size_t)gridDim.x * blockDim.x)
+    (const_cast<uint4 *>(src))[(size_t)b * stride16 + k] = src[k];
+}
+
+}  // namespace
+
+struct cf_batch {
+  cf_problem *p = nullptr;
+  char *buf = nullptr;
+  size_t slab = 0;
+  int B = 0, m = 0, n = 0, prec = 0;
+  bool have = false;
+  float t_ms = 0;
+};
+
+namespace {
+
+template <typename T>
+cf_status batch_layout(cf_problem *p, PrecTables<T> &t, int m) {
+  std::vector<int> res(m, 0);  // any letters: the layout depends on the length only
+  cf_status s = set_protein_tables(p, res, nullptr, nullptr);
+  if (s == CF_OK) s = alloc_inside(p, t);
+  if (s == CF_OK) s = alloc_outside(p, t);
+  return s;
+}
+
+template <typename T>
+cf_status batch_clear(cf_batch *b, PrecTables<T> &t) {
+  cf_problem *p = b->p;
+  const int n = b->n, B = b->B;
+  const size_t nc = ncells(n) * BLK, S = b->slab;
+  cudaStream_t st = p->stream;
+  DP<T> &d = t.dp;
+  auto z = [&](void *ptr, size_t bytes) { return cudaMemset2DAsync(ptr, S, 0, bytes, B, st); };
+  T *tabs[] = {d.CH, d.QB, d.XI, d.HB, d.QMpp, d.QMpu, d.G, d.QM2pp, d.QM2pu, d.QM2up, d.QM2uu,
+               d.hCH, d.hQB, d.hGc, d.hXI, d.hHB, d.hQMpp, d.hQMpu, d.hG, d.hQM2pp, d.hQM2pu, d.hQM2up, d.hQM2uu};
+  for (T *q : tabs) CF_CUDA(p, z(q, nc * sizeof(T)));
+  CF_CUDA(p, z(d.YY, yy_inside_elems(n, d.yyck) * sizeof(T)));
+  CF_CUDA(p, z(d.hYY, (size_t)YRING * n * NYY * BLK * sizeof(T)));
+  T *ext[] = {d.Q5U, d.Q5P, d.Gx, d.hQ5U, d.hQ5P, d.hGx};
+  for (T *q : ext) CF_CUDA(p, z(q, (size_t)n * BLK * sizeof(T)));
+  return CF_OK;
+}
+
+template <typename T>
+cf_status batch_run(cf_batch *b, PrecTables<T> &t, double *logZ, float *P, double *cm) {
+  cf_problem *p = b->p;
+  const int n = b->n, m = b->m, B = b->B;
+  const size_t S = b->slab;
+  cudaStream_t st = p->stream;
+  cf_status s = build_inside_graph(p, t);
+  if (s == CF_OK) s = build_outside_graph(p, t);
+  if (s != CF_OK) return s;
+  CF_CUDA(p, cudaMemset2DAsync(p->derr, S, 0, sizeof(int), B, st));
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  CF_CUDA(p, cudaGraphLaunch(t.gin, st));
+  k_logz<<<dim3(1, B), 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, m - 1, p->dlogz, (long long)S);
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaGraphLaunch(t.gout, st));
+  CF_CUDA(p, cudaEventRecord(p->ev[1], st));
+  std::vector<int> err(B);
+  std::vector<double> lz(B);
+  CF_CUDA(p, cudaMemcpy2DAsync(lz.data(), sizeof(double), p->dlogz, S, sizeof(double), B, cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpy2DAsync(err.data(), sizeof(int), p->derr, S, sizeof(int), B, cudaMemcpyDeviceToHost, st));
+  if (P) CF_CUDA(p, cudaMemcpy2DAsync(P, (size_t)n * n * 4, p->dP, S, (size_t)n * n * 4, B, cudaMemcpyDefault, st));
+  if (cm) CF_CUDA(p, cudaMemcpy2DAsync(cm, (size_t)m * 48, p->dcm, S, (size_t)m * 48, B, cudaMemcpyDefault, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&b->t_ms, p->ev[0], p->ev[1]));
+  for (int k = 0; k < B; k++) {
+    if (err[k] & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "cf_batch_run: a bounded wait for staged inputs gave up");
+    if (err[k] || !std::isfinite(lz[k]))
+      return fail(p, CF_ENUMERIC, "cf_batch_run: protein " + std::to_string(k) + ": non-finite result");
+  }
+  std::memcpy(logZ, lz.data(), sizeof(double) * B);
+  return CF_OK;
+}
+
+}  // namespace
+
+extern "C" cf_status cf_batch_create(const cf_model *model, int device, void *stream, int nprot, int m,
+                                     cf_precision prec, cf_batch **out) {
+  if (!model || !out || nprot < 1 || m < 1 || m > CF_BATCH_MAX_M || (prec != CF_FP64 && prec != CF_FP32_SCALED))
+    return fail(nullptr, CF_EINVAL, "cf_batch_create: bad argument (1 <= m <= CF_BATCH_MAX_M, nprot >= 1)");
+  *out = nullptr;
+  cf_problem *p = nullptr;
+  cf_status s = cf_problem_create(model, device, stream, &p);
+  if (s != CF_OK) return s;
+  cf_batch *b = new (std::nothrow) cf_batch;
+  if (!b) {
+    cf_problem_free(p);
+    return fail(nullptr, CF_ENOMEM, "cf_batch_create: host memory");
+  }
+  b->p = p;
+  b->B = nprot;
+  b->m = m;
+  b->n = 3 * m;
+  b->prec = (int)prec;
+  p->batch = nprot;
+  p->ck_request = 0;
+  // 1. the slab size: protein 0's allocation sequence in a scratch arena
+  char *scratch = nullptr;
+  const size_t scap = (size_t)256 << 20;
+  cudaError_t e = cudaMalloc(&scratch, scap);
+  if (e != cudaSuccess) {
+    cf_batch_free(b);
+    return cuda_fail(nullptr, e, "cf_batch_create: scratch arena");
+  }
+  Arena a1{scratch, scap, 0};
+  g_arena = &a1;
+  s = prec == CF_FP64 ? batch_layout(p, p->f64, m) : batch_layout(p, p->f32, m);
+  g_arena = nullptr;
+  cudaStreamSynchronize(p->stream);
+  release_protein(p);
+  cudaFree(scratch);
+  if (s != CF_OK) {
+    cf_batch_free(b);
+    return s;
+  }
+  b->slab = (a1.used + 4095) / 4096 * 4096;
+  // 2. the batch buffer, protein 0 laid out in its first slab, copied to all
+  e = cudaMalloc(&b->buf, b->slab * (size_t)nprot);
+  if (e == cudaSuccess) e = cudaMemset(b->buf, 0, b->slab * (size_t)nprot);
+  if (e != cudaSuccess) {
+    cf_batch_free(b);
+    return cuda_fail(nullptr, e, "cf_batch_create: batch buffer");
+  }
+  Arena a2{b->buf, b->slab, 0};
+  g_arena = &a2;
+  s = prec == CF_FP64 ? batch_layout(p, p->f64, m) : batch_layout(p, p->f32, m);
+  g_arena = nullptr;
+  if (s == CF_OK && a2.used != a1.used) s = fail(p, CF_ECUDA, "cf_batch_create: layout mismatch");
+  if (s != CF_OK) {
+    cf_batch_free(b);
+    return s;
+  }
+  p->bstride = (long long)b->slab;
+  p->f32.dp.bstride = p->f64.dp.bstride = (long long)b->slab;
+  if (nprot > 1) {
+    k_replicate<<<dim3(148, nprot - 1), 256, 0, p->stream>>>((const uint4 *)b->buf, b->slab / 16,
+                                                             (long long)(b->slab / 16), nprot);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    cf_batch_free(b);
+    return cuda_fail(nullptr, e, "cf_batch_create: replicate");
+  }
+  *out = b;
+  return CF_OK;
+}
+
+extern "C" cf_status cf_batch_set_proteins(cf_batch *b, const char *aa, const double *lw, const double *pb) {
+  if (!b || !aa) return fail(nullptr, CF_EINVAL, "cf_batch_set_proteins: NULL argument");
+  cf_problem *p = b->p;
+  const int B = b->B, m = b->m, n = b->n;
+  const size_t S = b->slab;
+  if (lw)
+    for (size_t k = 0; k < (size_t)B * m * 6; k++)
+      if (!std::isfinite(lw[k])) return fail(p, CF_EINVAL, "cf_batch_set_proteins: non-finite codon weight");
+  if (pb)
+    for (size_t k = 0; k < 61 * 61; k++)
+      if (!std::isfinite(pb[k])) return fail(p, CF_EINVAL, "cf_batch_set_proteins: non-finite pair bonus");
+  const GeneticCode &gc = gcode();
+  std::vector<int> M((size_t)B * n), base((size_t)B * n * NS, 0), cid((size_t)B * n * NS, -1), bnd((size_t)B * n);
+  for (int k = 0; k < B; k++)
+    for (int r = 0; r < m; r++) {
+      const char *q = aa[(size_t)k * m + r] ? std::strchr(kAminoAcids, aa[(size_t)k * m + r]) : nullptr;
+      if (!q) return fail(p, CF_EINVAL, "cf_batch_set_proteins: invalid amino acid");
+      const auto &cods = gc.codons[q - kAminoAcids];
+      for (int off = 0; off < 3; off++) {
+        const size_t i = (size_t)k * n + 3 * r + off;
+        M[i] = (int)cods.size();
+        for (size_t a = 0; a < cods.size(); a++) {
+          base[i * NS + a] = (cods[a] >> (2 * (2 - off))) & 3;
+          cid[i * NS + a] = gc.sense_id[cods[a]];
+        }
+        bnd[i] = (off == 2 && 3 * r + off + 1 < n) ? 1 : 0;
+      }
+    }
+  CF_CUDA(p, cudaSetDevice(p->device));
+  cudaStream_t st = p->stream;
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  b->have = false;
+  auto up = [&](void *dst, const void *src, size_t w) {
+    return cudaMemcpy2DAsync(dst, S, src, w, w, B, cudaMemcpyHostToDevice, st);
+  };
+  CF_CUDA(p, up(p->dM, M.data(), sizeof(int) * n));
+  CF_CUDA(p, up(p->dbase, base.data(), sizeof(int) * n * NS));
+  CF_CUDA(p, up(p->dcid, cid.data(), sizeof(int) * n * NS));
+  CF_CUDA(p, up(p->dbnd, bnd.data(), sizeof(int) * n));
+  if (lw) CF_CUDA(p, up(p->dlw, lw, sizeof(double) * m * 6));
+  else CF_CUDA(p, cudaMemset2DAsync(p->dlw, S, 0, sizeof(double) * m * 6, B, st));
+  if (pb) {
+    CF_CUDA(p, cudaMemcpyAsync(p->dpb, pb, sizeof(double) * 61 * 61, cudaMemcpyHostToDevice, st));
+    if (B > 1) {  // the same bonuses in every slab
+      // (the last 16-byte chunk reaches into the allocation's 256-byte padding)
+      k_replicate<<<dim3(8, B - 1), 256, 0, st>>>((const uint4 *)p->dpb, (61 * 61 * 8 + 15) / 16, (long long)(S / 16),
+                                                  B);
+      CF_CUDA(p, cudaGetLastError());
+    }
+  } else {
+    CF_CUDA(p, cudaMemset2DAsync(p->dpb, S, 0, sizeof(double) * 61 * 61, B, st));
+  }
+  CF_CUDA(p, cudaMemset2DAsync(p->dls, S, 0, sizeof(double) * std::max(m - 1, 1), B, st));
+  CF_CUDA(p, cudaMemset2DAsync(p->dE, S, 0, sizeof(int) * n, B, st));
+  k_transfers<<<dim3((n + 127) / 128, B), 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, p->den64, p->dlw, p->dpb,
+                                                         p->dTr64, p->dX64, p->du0, p->dls, (long long)S);
+  CF_CUDA(p, cudaGetLastError());
+  cf_status s;
+  if (b->prec == CF_FP64) {
+    k_cast<double><<<dim3(8, B), 256, 0, st>>>(p->dTr64, (double *)p->f64.dp.Tr, (size_t)n * BLK, (long long)S);
+    k_cast<double><<<dim3(8, B), 256, 0, st>>>(p->dX64, (double *)p->f64.dp.X, (size_t)n * 4 * BLK, (long long)S);
+    s = batch_clear(b, p->f64);
+  } else {
+    k_cast<float><<<dim3(8, B), 256, 0, st>>>(p->dTr64, (float *)p->f32.dp.Tr, (size_t)n * BLK, (long long)S);
+    k_cast<float><<<dim3(8, B), 256, 0, st>>>(p->dX64, (float *)p->f32.dp.X, (size_t)n * 4 * BLK, (long long)S);
+    s = batch_clear(b, p->f32);
+  }
+  if (s != CF_OK) return s;
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  b->have = true;
+  return CF_OK;
+}
+
+extern "C" cf_status cf_batch_run(cf_batch *b, double *logZ, float *pair_prob, double *codon_marg) {
+  if (!b || !logZ) return fail(nullptr, CF_EINVAL, "cf_batch_run: NULL argument");
+  if (!b->have) return fail(b->p, CF_ESTATE, "cf_batch_run: set the proteins first");
+  CF_CUDA(b->p, cudaSetDevice(b->p->device));
+  return b->prec == CF_FP64 ? batch_run(b, b->p->f64, logZ, pair_prob, codon_marg)
+                            : batch_run(b, b->p->f32, logZ, pair_prob, codon_marg);
+}
+
+extern "C" float cf_batch_last_ms(const cf_batch *b) { return b ? b->t_ms : 0.f; }
+
+extern "C" cf_status cf_batch_free(cf_batch *b) {
+  if (!b) return CF_OK;
+  if (b->p) {
+    cudaSetDevice(b->p->device);
+    cudaStreamSynchronize(b->p->stream);
+    cf_problem_free(b->p);  // the slab arrays belong to buf: the problem's lists are empty
+  }
+  if (b->buf) cudaFree(b->buf);
+  delete b;
+  return CF_OK;
 }

@@ -302,6 +302,8 @@ __global__ void k_adam(float *P, const float *G, float *m, float *v, float lr, f
 
 }  // namespace sg
 
+#include "surrogate_tc.cuh"
+
 // ------------------------------------------------------------------ host
 
 struct cf_surrogate {
@@ -313,6 +315,14 @@ struct cf_surrogate {
   __nv_bfloat16 *Wf = nullptr, *Wb = nullptr;
   float *h[4] = {}, *dp[2] = {}, *S = nullptr, *pred = nullptr, *dg = nullptr, *loss = nullptr, *tgt = nullptr;
   float *part = nullptr;
+  // tensor-core prediction path (surrogate_tc.cuh): weights, row frame,
+  // hi/lo activation rows (ping-pong), per-row head terms, error word
+  __nv_bfloat16 *Wtc = nullptr, *xh[2] = {nullptr, nullptr}, *xl[2] = {nullptr, nullptr};
+  int *rowwin = nullptr, *tcerr = nullptr;
+  float *srow = nullptr;
+  size_t rows_cap = 0;
+  int path = 1;  // prediction: 0 CUDA cores (FP32 activations), 1 tensor cores
+  int sms = 148;
   uint8_t *bases = nullptr;
   size_t bases_cap = 0;
   int64_t *off = nullptr;
@@ -375,6 +385,76 @@ size_t dw_smem(int ci) { return ((size_t)C * LPD + (size_t)ci * LPW) * 4; }
 
 cf_status refresh_bf16(cf_surrogate *s) {
   k_prep<<<(WF_N + 255) / 256, 256, 0, s->stream>>>(s->P, s->Wf, s->Wb);
+  k_prep_tc<<<(3 * 5 * 64 * 64 + 255) / 256, 256, 0, s->stream>>>(s->P, s->Wtc);
+  SG_CUDA(cudaGetLastError());
+  return CF_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver (looked up once through the runtime)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D BF16 row tensor [rows][64] (128-byte rows), box 64 x box_rows, 128-byte swizzle
+bool row_map(CUtensorMap *m, const void *base, size_t rows, unsigned box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The forward pass on the tensor cores for a staged batch of nb windows.
+cf_status forward_tc(cf_surrogate *s, const uint8_t *db, const int64_t *doff, int nb, const std::vector<int64_t> &hoff) {
+  cudaStream_t st = s->stream;
+  const int nrows = (int)(hoff[nb] - hoff[0]) + 4 * nb;
+  if ((size_t)nrows > s->rows_cap) return sfail(CF_EINVAL, "surrogate: batch exceeds the row buffers");
+  k_tc_rows<<<nb, 128, 0, st>>>(doff, nb, nrows, s->rowwin);
+  k_tc_layer1<<<(int)(((size_t)nrows * 64 + 255) / 256), 256, 0, st>>>(doff, db, s->rowwin, nrows, s->Wf + WF_OFF(0),
+                                                                        s->P + OB(0), s->xh[0], s->xl[0]);
+  SG_CUDA(cudaGetLastError());
+  CUtensorMap tw;
+  if (!row_map(&tw, s->Wtc, 3 * 5 * 64, 64)) return sfail(CF_ECUDA, "surrogate: weight tensor map");
+  const int ntiles = (nrows + TC_M - 1) / TC_M;
+  const int grid = std::max(1, std::min(ntiles, s->sms));
+  int cur = 0;
+  for (int l = 1; l <= 3; l++) {
+    CUtensorMap th, tl;
+    if (!row_map(&th, s->xh[cur], nrows, TC_HALO) || !row_map(&tl, s->xl[cur], nrows, TC_HALO))
+      return sfail(CF_ECUDA, "surrogate: activation tensor map");
+    TcArgs a;
+    a.nrows = nrows;
+    a.rowwin = s->rowwin;
+    a.bias = s->P + OB(l);
+    a.wh = s->P + OWH;
+    a.out_hi = s->xh[cur ^ 1];
+    a.out_lo = s->xl[cur ^ 1];
+    a.s_out = s->srow;
+    a.wrow0 = (l - 1) * 5 * 64;
+    a.last = l == 3;
+    a.err = s->tcerr;
+    k_conv_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(th, tl, tw, a);
+    SG_CUDA(cudaGetLastError());
+    cur ^= 1;
+  }
+  k_tc_head<<<(nb + 3) / 4, 128, 0, st>>>(doff, nb, s->srow, s->P, s->pred);
   SG_CUDA(cudaGetLastError());
   return CF_OK;
 }
@@ -500,6 +580,17 @@ cf_status cf_surrogate_create(int device, void *stream, int max_batch, cf_surrog
   if (e == cudaSuccess) e = salloc(L, &s->loss, (size_t)1);
   if (e == cudaSuccess) e = salloc(L, &s->part, (size_t)s->dw_grid * (C * 64 * K + C));
   if (e == cudaSuccess) e = salloc(L, &s->off, (size_t)max_batch + 1);
+  s->sms = sms;
+  s->rows_cap = (size_t)max_batch * (LP + 4);
+  if (e == cudaSuccess) e = salloc(L, &s->Wtc, (size_t)3 * 5 * 64 * 64);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    e = salloc(L, &s->xh[k], s->rows_cap * 64);
+    if (e == cudaSuccess) e = salloc(L, &s->xl[k], s->rows_cap * 64);
+  }
+  if (e == cudaSuccess) e = salloc(L, &s->rowwin, s->rows_cap);
+  if (e == cudaSuccess) e = salloc(L, &s->srow, s->rows_cap);
+  if (e == cudaSuccess) e = salloc(L, &s->tcerr, (size_t)1);
+  if (e == cudaSuccess) e = cudaMemset(s->tcerr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s->P, 0, sizeof(float) * NPARAM);
   if (e == cudaSuccess) e = cudaMemset(s->M, 0, sizeof(float) * NPARAM);
   if (e == cudaSuccess) e = cudaMemset(s->V, 0, sizeof(float) * NPARAM);
@@ -515,6 +606,8 @@ cf_status cf_surrogate_create(int device, void *stream, int max_batch, cf_surrog
     e = cudaFuncSetAttribute((const void *)k_dw<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(64));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void *)k_dw<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(4));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void *)k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) {
     cf_surrogate_free(s);
     return sfail(e == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA,
@@ -589,7 +682,8 @@ cf_status cf_surrogate_predict(cf_surrogate *s, const uint8_t *bases, const int6
     const int64_t *doff;
     std::vector<int64_t> hoff;
     SG_TRY(stage(s, src, o.data(), nb, &db, &doff, hoff));
-    SG_TRY(forward(s, db, doff, nb, nullptr));
+    if (s->path) SG_TRY(forward_tc(s, db, doff, nb, hoff));
+    else SG_TRY(forward(s, db, doff, nb, nullptr));
     SG_TRY(copy_out(s, G_out + w0, s->pred, sizeof(float) * nb));
     SG_CUDA(cudaStreamSynchronize(s->stream));  // host offsets / staging buffers reused by the next chunk
   }
@@ -597,6 +691,20 @@ cf_status cf_surrogate_predict(cf_surrogate *s, const uint8_t *bases, const int6
   SG_CUDA(cudaEventSynchronize(s->ev[1]));
   SG_CUDA(cudaEventElapsedTime(&total_ms, s->ev[0], s->ev[1]));
   s->last_ms = total_ms;
+  if (s->path) {
+    int err = 0;
+    SG_CUDA(cudaMemcpy(&err, s->tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      SG_CUDA(cudaMemset(s->tcerr, 0, sizeof(int)));
+      return sfail(CF_ETIMEOUT, "cf_surrogate_predict: a bounded wait of the tensor-core pipeline gave up");
+    }
+  }
+  return CF_OK;
+}
+
+cf_status cf_surrogate_set_path(cf_surrogate *s, int path) {
+  if (!s || path < 0 || path > 1) return sfail(CF_EINVAL, "cf_surrogate_set_path: bad argument");
+  s->path = path;
   return CF_OK;
 }
 

@@ -143,3 +143,30 @@ def test_training_and_prescreen_gain():
     assert np.mean(gain) > 0, gain
     sur.close()
     exact.close()
+
+
+def test_tensor_core_prediction_matches_cuda_cores_and_reference():
+    """Prediction on the 5th-generation tensor cores (tcgen05 MMA, 128-row
+    tiles straddling windows, BF16 hi/lo activations) against the CUDA-core
+    path with FP32 activations and against the float64 reference, on windows
+    of every length class (empty, shorter than a tap span, one tile, several
+    tiles) in batches that split across chunks."""
+    import paper_2604_19718_b300 as cf
+    p = _params(11)
+    rng = np.random.default_rng(12)
+    lens = [0, 1, 2, 4, 5, 127, 128, 129, 256, 255] + list(rng.integers(60, 241, 300))
+    ws, b, off = _windows(lens, 13)
+    sur = cf.Surrogate(p, max_batch=128)
+    cf.cf_surrogate_set_path(sur.h, 0)
+    cc = sur.predict(b, off)
+    cf.cf_surrogate_set_path(sur.h, 1)
+    tc = sur.predict(b, off)
+    tc2 = sur.predict(b, off)
+    sur.close()
+    nz = [i for i, w in enumerate(ws) if len(w) > 0]
+    ref = sg.predict(p, [ws[i] for i in nz])
+    scale = np.maximum(1.0, np.abs(cc))
+    assert np.array_equal(tc, tc2)  # deterministic
+    assert (np.abs(tc - cc) / scale).max() <= 1e-4
+    assert np.abs(tc[nz] - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert tc[0] == 0.0 and cc[0] == 0.0

@@ -379,8 +379,9 @@ cf_status cf_sample_noalloc(cf_problem *prob, int nsamples, uint64_t seed, int32
  *   by the outside pass; in_untiled: inside bands summed term by term;
  *   out_untiled: 1 if the outside pass gathered every term per diagonal;
  *   spread_bits: the spread (log2) of the strengths of the intervals of one
- *   length, estimated after the inside pass from the exterior prefix; past
- *   100 bits the binary32 inside pass returns CF_ENUMERIC and asks for
+ *   length (lengths up to 400 nt), estimated after the inside pass from the
+ *   exterior prefix; past 120 bits the binary32 inside pass returns
+ *   CF_ENUMERIC and asks for
  *   CF_FP64 (a composition that changes strongly along the protein spreads
  *   them beyond what binary32 holds).
  * Any pointer may be NULL.  Synchronises the problem's stream.
@@ -402,8 +403,9 @@ cf_status cf_far_band_info(const cf_problem *prob, int *in_max_dev, int *in_unti
  *     summed term by term (default 48); 0 sends every band of every binary32
  *     pass on `device` that way.  Synchronises the device.
  *   cf_debug_set_range_limit: the spread (bits) above which the binary32
- *     inside pass on `device` refuses, and the longest interval length the
- *     spread is measured over (0: all).  Synchronises the device.
+ *     inside pass on `device` refuses (default 120), and the longest
+ *     interval length the spread is measured over (default 400; 0: all).
+ *     Synchronises the device.
  *   cf_debug_fail_alloc: after `after` further successful device allocations
  *     of the library (process-wide), the next one fails as if the device were
  *     out of memory (CF_ENOMEM); negative turns the hook off.  The failing

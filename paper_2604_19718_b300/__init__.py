@@ -289,14 +289,12 @@ def cf_surrogate_set_path(sur, path: int) -> None:
 FAR_DEV_MAX_DEFAULT = 48
 
 
-RANGE_MAXLEN_DEFAULT = 0
+RANGE_LIMIT_DEFAULT = 120
+RANGE_MAXLEN_DEFAULT = 400
 
 
 def cf_debug_set_range_limit(device: int, bits: int, max_length: int = RANGE_MAXLEN_DEFAULT) -> None:
     _check(lib.cf_debug_set_range_limit(int(device), int(bits), int(max_length)))
-
-
-RANGE_LIMIT_DEFAULT = 100
 
 
 def cf_debug_fail_alloc(after: int) -> None:

@@ -716,7 +716,8 @@ def main():
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(lin + lout),
         "far_bands": dict(zip(("inside_max_departure_log2", "inside_bands_term_by_term",
-                               "outside_max_departure_log2", "outside_term_by_term"), far_info)),
+                               "outside_max_departure_log2", "outside_term_by_term", "range_spread_log2"),
+                              far_info)),
         "clocks": clocks,
     }
     out.update(forms)

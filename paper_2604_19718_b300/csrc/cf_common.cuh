@@ -359,13 +359,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 // the default).  A test lowers it (cf_debug_set_wait_polls) to make every
 // wait give up at once; the drain wait after a timeout keeps its full length,
 // so the copies in flight still land before the CTA exits.
-static __device__ unsigned long long g_cf_wait_polls = 1ull << 22;
+// (The test knobs live in constant memory: a kernel reads them from the
+// SM's constant cache, not with a round trip to L2 on its critical path.)
+static __constant__ unsigned long long g_cf_wait_polls = 1ull << 22;
 
 // Largest departure (log2) of the per-diagonal exponents from the far-band
 // chord for which a band is still summed in tiles (48 by default).  A test
 // lowers it (cf_debug_set_far_dev_max) to send every band through the
 // term-by-term path.
-static __device__ int g_cf_far_dev_max = 48;
+static __constant__ int g_cf_far_dev_max = 48;
 
 // Bits of the device error word besides ERR_STAGE_TIMEOUT: the binary32
 // inside pass found the dynamic range of its tables exceeded, or an output of
@@ -377,7 +379,7 @@ constexpr int ERR_RANGE_IN = 1 << 6, ERR_OUT_NONFINITE = 1 << 8;
 // waited for once more, again bounded.
 constexpr int ERR_STAGE_TIMEOUT = 8;
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int *err) {
-  const unsigned long long polls = *(volatile unsigned long long *)&g_cf_wait_polls;
+  const unsigned long long polls = g_cf_wait_polls;
   for (unsigned long long it = 0; it < polls; it++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(128);

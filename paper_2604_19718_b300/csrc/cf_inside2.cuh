@@ -88,7 +88,7 @@ __device__ __forceinline__ void bb_shift(BifBuf<T> &b, long long off) {
 // two operands (slower; no chord).
 constexpr int FARD = 16;   // diagonals per band
 // (with the default bound, a product of two tile factors stays within 2^{+-96})
-__device__ __forceinline__ int far_dev_max() { return *(volatile int *)&g_cf_far_dev_max; }
+__device__ __forceinline__ int far_dev_max() { return g_cf_far_dev_max; }
 constexpr int FARTX = 16;  // rows per far tile
 constexpr int FARKC = 8;   // split points staged per step
 constexpr int FARKS = 64;   // split points per CTA slice
@@ -139,15 +139,20 @@ __device__ __forceinline__ FarChord far_chord(const int *E, int c) {
 // proteins above the limit would still have been within the bar: the refusal
 // is conservative.  The departure of E from a chord is no such measure: it
 // also grows with gentle curvature over thousands of diagonals.
-static __device__ int g_cf_range_limit = 120;
-static __device__ int g_cf_range_maxlen = 400;  // lengths a considered (0: all)
-__device__ __forceinline__ int range_limit() { return *(volatile int *)&g_cf_range_limit; }
+static __constant__ int g_cf_range_limit = 120;
+static __constant__ int g_cf_range_maxlen = 400;  // lengths a considered (0: all)
+__device__ __forceinline__ int range_limit() { return g_cf_range_limit; }
 
+// F is summed and its log taken in binary64, then held in binary32: |F| grows
+// by a few bits per nucleotide (about 2 on the 900-nt workload), so below the
+// 51,200-nt bound of this check the rounding of F is under 0.01 bits, far
+// below the whole bits the refusal compares; the n x maxlen differences then
+// run on the binary32 pipes.
 template <typename T>
-__global__ void __launch_bounds__(256) k_in_range(DP<T> p, int *spread_out) {
-  extern __shared__ double F[];  // [n]
+__global__ void __launch_bounds__(1024) k_in_range(DP<T> p, int *spread_out) {
+  extern __shared__ float F[];  // [n]
   __shared__ int smax, sflush;
-  const int n = p.n, t = threadIdx.x;
+  const int n = p.n, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
   if (t == 0) {
     smax = 0;
     sflush = 0;
@@ -158,21 +163,28 @@ __global__ void __launch_bounds__(256) k_in_range(DP<T> p, int *spread_out) {
     double s = 0;
     for (int e = 0; e < BLK; e++) s += (double)u[e] + (double)q[e];
     if (!(s > 0)) atomicOr(&sflush, 1);
-    F[y] = s > 0 ? log2(s) + (double)__ldcg(p.E + y) : 0.0;
+    F[y] = s > 0 ? (float)(log2(s) + (double)__ldcg(p.E + y)) : 0.0f;
   }
   __syncthreads();
+  // one warp per length a, lanes over the start x (x = 0 exists for every a < n)
   int best = 0;
-  const int amax = *(volatile int *)&g_cf_range_maxlen > 0 ? min(n, *(volatile int *)&g_cf_range_maxlen + 1) : n;
-  for (int a = 1 + t; a < amax; a += blockDim.x) {
-    double mx = -1e300, mn = 1e300;
-    for (int x = 0; x + a < n; x++) {
-      const double v = F[x + a] - F[x];
-      mx = fmax(mx, v);
-      mn = fmin(mn, v);
+  const int ml = g_cf_range_maxlen;
+  const int amax = ml > 0 ? min(n, ml + 1) : n;
+  for (int a = 1 + w; a < amax; a += nw) {
+    float mx = -3e38f, mn = 3e38f;
+    for (int x = lane; x + a < n; x += 32) {
+      const float v = F[x + a] - F[x];
+      mx = fmaxf(mx, v);
+      mn = fminf(mn, v);
     }
-    best = max(best, (int)ceil(mx - mn));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    best = max(best, (int)ceilf(mx - mn));
   }
-  atomicMax(&smax, best);
+  if (lane == 0) atomicMax(&smax, best);
   __syncthreads();
   if (t == 0) {
     const int v = sflush ? 100000 : smax;
@@ -461,10 +473,13 @@ __global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, in
 // Grid-stride over the n-d cells and the exterior: launched with fewer CTAs
 // than cells, so that the light kernels of the critical path always find
 // room on the SMs.
-template <typename T>
+// (BT: a batch of proteins, blockIdx.y the protein; a compile-time switch so
+// that a single protein's kernels read their table pointers straight from the
+// parameter bank.)
+template <typename T, bool BT = false>
 __global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
-  if (p.bstride) {
+  if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;
     dp_shift(p, off);
     bb_shift(bb, off);
@@ -944,7 +959,7 @@ __global__ void k_in_slot_tab(DP<T> p, BifBuf<T> bb) {
     bb.dtab[(size_t)d * NCOPY + k] = light_dst(p, k, 0, d, cidx(p.n, 0, d));
 }
 
-template <typename T, int NTT>
+template <typename T, int NTT, bool BT>
 __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &bb, int d, int x,
                                               unsigned char *smem_raw) {
   using LM = LightMap<NTT>;
@@ -988,7 +1003,7 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   }
   T cHL = 0;
   if (t == NTT - 2) cHL = p.eHL[d + 1];  // hairpin length factor of the cell
-  const long long boff = (long long)blockIdx.y * p.bstride;  // batch: protein 0's addresses + boff
+  const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;  // batch: protein 0's addresses + boff
   const T *src0 = t < SI_N ? bshift(bb.stab[(size_t)d * SI_N + t], boff) : nullptr;
   T *dst0 = t < NCOPY ? bshift(bb.dtab[(size_t)d * NCOPY + t], boff) : nullptr;
   __syncthreads();
@@ -1302,15 +1317,15 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   }
 }
 
-template <typename T, int NTT>
+template <typename T, int NTT, bool BT = false>
 __global__ void __launch_bounds__(NTT, 1024 / NTT) k_in_light(DP<T> p, BifBuf<T> bb, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (p.bstride) {
+  if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;
     dp_shift(p, off);
     bb_shift(bb, off);
   }
-  in_light_cell<T, NTT>(p, bb, d, blockIdx.x, smem_raw);
+  in_light_cell<T, NTT, BT>(p, bb, d, blockIdx.x, smem_raw);
 }
 
 template <typename T, int NTT = NT_IN>

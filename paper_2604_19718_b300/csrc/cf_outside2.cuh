@@ -591,11 +591,13 @@ __global__ void k_out_slot_tab(DP<T> p, OutBuf<T> ob) {
 // Thread mapping as in k_in_light: compact entries e = a*M_b + b, work lists
 // split into NT/(M_x*M_y) groups.  Registers bounded so that six 256-thread
 // CTAs fit an SM (their shared memory allows six as well).
-template <typename T, int NTT>
+// (BT: a batch of proteins, blockIdx.y the protein; compile-time, so that a
+// single protein's kernels read their table pointers from the parameter bank.)
+template <typename T, int NTT, bool BT = false>
 __global__ void __launch_bounds__(NTT, 1536 / NTT) k_out_light(DP<T> p, OutBuf<T> ob, int d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long long boff = (long long)blockIdx.y * p.bstride;  // batch: protein b's slab
-  if (boff) {
+  const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;  // batch: protein b's slab
+  if (BT) {
     dp_shift(p, boff);
     ob_shift(ob, boff);
   }
@@ -1027,7 +1029,7 @@ __global__ void k_side_slot_tab(DP<T> p, OutBuf<T> ob) {
 
 template <typename T>
 __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, int d, int x, T *S, SideCtx &cx, T *sEn, T *wBu,
-                                          unsigned long long *sbar, unsigned phase) {
+                                          unsigned long long *sbar, unsigned phase, long long boff) {
   int *sE = cx.sE, *sMx = cx.sMx, *sMy = cx.sMy;
   int (*sBx)[NS] = cx.sBx, (*sBy)[NS] = cx.sBy;
   const int t = threadIdx.x;
@@ -1054,7 +1056,7 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
   }
   if (t < EN_N) cEn = p.en[t];
   static_assert(NT3 >= SS_N, "one staged slot per thread");
-  const T *src0 = t < SS_N ? bshift(ob.stab[(size_t)d * SS_N + t], (long long)blockIdx.y * p.bstride) : nullptr;
+  const T *src0 = t < SS_N ? bshift(ob.stab[(size_t)d * SS_N + t], boff) : nullptr;
   // staging: one TMA bulk copy per input block, the interior-loop adjoints
   // hYY_L (L = 2..Lmax) and partial sums YY_{L-1}[x+1][y] (L = 3..Lmax) as one
   // copy each; the partial sums only for a boundary at x (the ring term of the
@@ -1176,11 +1178,11 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 // the CTAs leave room for the light kernels; else one cell per CTA), the
 // others the side work of the cells of diagonal d+4.  Both parts start after
 // the light kernel of d+4.
-template <typename T, bool GRP>
+template <typename T, bool GRP, bool BT = false>
 __global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (p.bstride) {
-    const long long boff = (long long)blockIdx.y * p.bstride;
+  const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;
+  if (BT) {
     dp_shift(p, boff);
     ob_shift(ob, boff);
   }
@@ -1199,7 +1201,7 @@ __global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T>
   }
   if (threadIdx.x == 0) mbar_init(&sbar, NT3);  // one arrival per thread (side work)
   __syncthreads();
-  side_cell(p, ob, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u);
+  side_cell(p, ob, d + 4, blockIdx.x - nbif, (T *)smem_raw, cx, sEn, wBu, &sbar, 0u, boff);
 }
 
 template <typename T>
@@ -1313,10 +1315,10 @@ __device__ __forceinline__ void tg_issue(const DP<T> &p, int role, int x, int y,
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-template <typename T>
+template <typename T, bool BT = false>
 __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (p.bstride) dp_shift(p, (long long)(blockIdx.z >> 1) * p.bstride);  // batch: z = 2 protein + role
+  if (BT) dp_shift(p, (long long)(blockIdx.z >> 1) * p.bstride);  // batch: z = 2 protein + role
   const int n = p.n, q = blockIdx.y, role = blockIdx.z & 1;
   if (q >= n - 1 || p.bnd[q] == 0) return;
   const int ncell = role == 0 ? n - 1 - q : q + 1;  // role 0: y = q+1..n-1; role 1: x = 0..q

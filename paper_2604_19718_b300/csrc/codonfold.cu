@@ -374,11 +374,11 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   t.bb.gfac = nullptr;
   t.bb.gdev = nullptr;
   t.bb.spread = nullptr;
-  if (n * sizeof(double) <= 200 * 1024 && p->batch == 1) {
+  if (n * sizeof(float) <= 200 * 1024 && p->batch == 1) {
     CF_CUDA(p, dalloc(L, &t.bb.spread, (size_t)1));
     CF_CUDA(p, cudaMemset(t.bb.spread, 0, sizeof(int)));
     CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_range<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(n * sizeof(double))));
+                                    (int)(n * sizeof(float))));
   }
   if (sizeof(T) == sizeof(float) && n > 3 * FARD) {
     CF_CUDA(p, dalloc(L, &t.bb.far, (size_t)2 * n * FARD * t.bb.farslices * BLK));
@@ -430,8 +430,9 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
   const int n = p->n;
   const int cap_bif = offchain_ctas(p, 64);
   const size_t smem = in_light_smem<T, NT_IN>();
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_in_light<T, NT_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+  const bool BT = p->batch > 1;  // batched kernels move their pointers per protein
+  const void *klight = BT ? (const void *)k_in_light<T, NT_IN, true> : (const void *)k_in_light<T, NT_IN, false>;
+  CF_CUDA(p, cudaFuncSetAttribute(klight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   cudaGraphNode_t mset;
@@ -496,7 +497,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
         kp.func = (void *)k_in_bif_grp<T>;
         kp.gridDim = dim3((n - d + 3) / 4 + 1);
       } else {
-        kp.func = (void *)k_in_bif<T>;
+        kp.func = BT ? (void *)k_in_bif<T, true> : (void *)k_in_bif<T, false>;
         kp.gridDim = dim3(std::min(n - d + 1, cap_bif), p->batch);
       }
       kp.blockDim = dim3(256);
@@ -514,7 +515,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     deps[nd++] = (d == 0) ? mset : k2[d - 1];
     if (d >= 8) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_in_light<T, NT_IN>;
+    kp.func = (void *)klight;
     kp.gridDim = dim3(n - d, p->batch);
     kp.blockDim = dim3(NT_IN);
     kp.sharedMemBytes = (unsigned)smem;
@@ -539,8 +540,8 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
       cudaKernelNodeParams kr = {};
       kr.func = (void *)k_in_range<T>;
       kr.gridDim = dim3(1, p->batch);
-      kr.blockDim = dim3(256);
-      kr.sharedMemBytes = (unsigned)(sizeof(double) * n);
+      kr.blockDim = dim3(1024);
+      kr.sharedMemBytes = (unsigned)(sizeof(float) * n);
       kr.kernelParams = rargs;
       cudaGraphNode_t rn;
       e = cudaGraphAddKernelNode(&rn, g, &fin, 1, &kr);
@@ -629,13 +630,19 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   const int cap_bif = offchain_ctas(p, 64);
   const size_t nc = ncells(n) * BLK;
   const size_t smem = out_light_smem<T, NT>(), smemw = out_light_smem<T, NT_WIDE>(), smem3 = out_side_smem<T>();
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_light<T, NT_WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smemw));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_tg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)out_tg_smem<T>()));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
-  CF_CUDA(p, cudaFuncSetAttribute((const void *)k_out_off<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  // batched kernels move their pointers per protein; a single protein's keep
+  // them in the parameter bank
+  const bool BT = p->batch > 1;
+  const void *klight = BT ? (const void *)k_out_light<T, NT, true> : (const void *)k_out_light<T, NT, false>;
+  const void *klightw = BT ? (const void *)k_out_light<T, NT_WIDE, true> : (const void *)k_out_light<T, NT_WIDE, false>;
+  const void *ktgf = BT ? (const void *)k_out_tg<T, true> : (const void *)k_out_tg<T, false>;
+  const void *koff0 = BT ? (const void *)k_out_off<T, false, true> : (const void *)k_out_off<T, false, false>;
+  const void *koff1 = BT ? (const void *)k_out_off<T, true, true> : (const void *)k_out_off<T, true, false>;
+  CF_CUDA(p, cudaFuncSetAttribute(klight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CF_CUDA(p, cudaFuncSetAttribute(klightw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemw));
+  CF_CUDA(p, cudaFuncSetAttribute(ktgf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out_tg_smem<T>()));
+  CF_CUDA(p, cudaFuncSetAttribute(koff0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute(koff1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   DP<T> dp = t.dp;
@@ -714,7 +721,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
       int nbif = hasb ? (banded ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
       void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
-      kp.func = banded ? (void *)k_out_off<T, true> : (void *)k_out_off<T, false>;  // far bands: grouped gathers
+      kp.func = (void *)(banded ? koff1 : koff0);  // far bands: grouped gathers
       kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0), B);
       kp.blockDim = dim3(NT3);
       kp.sharedMemBytes = (unsigned)smem3;
@@ -736,7 +743,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     if (hasb || hass) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;
-    kp.func = wide ? (void *)k_out_light<T, NT_WIDE> : (void *)k_out_light<T, NT>;
+    kp.func = (void *)(wide ? klightw : klight);
     kp.gridDim = dim3(n - d, B);
     kp.blockDim = dim3(wide ? NT_WIDE : NT);
     kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
@@ -783,7 +790,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   if (e == cudaSuccess) {
     void *args[] = {&dp};
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_out_tg<T>;
+    kp.func = (void *)ktgf;
     kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, n, 2 * B);
     kp.blockDim = dim3(256);
     kp.sharedMemBytes = (unsigned)out_tg_smem<T>();

@@ -320,6 +320,17 @@ __device__ __forceinline__ T s3(const T *A, const T *B, const T *C, int a, int b
 // ---- TMA bulk copies (global -> shared) completing on an mbarrier
 __device__ __forceinline__ uint32_t smem_addr(const void *ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 
+// Programmatic dependent launch along a chain of wavefront kernels: a kernel
+// launched through a programmatic graph edge may start while its predecessor
+// is still running; griddep_wait blocks the calling thread until the
+// predecessor grid has completed and its writes are visible (a no-op for a
+// kernel launched without such an edge), and griddep_launch_dependents lets
+// the successor start once every CTA of this grid has called it or exited.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");

@@ -568,6 +568,17 @@ __device__ __forceinline__ const T *in_slot_src2(const DP<T> &p, const BifBuf<T>
   return s < SI_QBK ? p.Gx + (size_t)k * BLK : p.QB + cidx(n, k, d) * BLK;
 }
 
+// Slots whose source lies on diagonal d-1 (written by the previous light
+// kernel): CH[x+1][y], QM*[x][y-1], QM2*[x+1][y], the YY run from (x+1, y),
+// XI[x][y-1] (L = 3), the bulges QB[x][y-1] and QB[x+1][y] (L = 1), the
+// exterior prefix of d-1 and QB[1][d].  Every other source is on a diagonal
+// <= d-2, a fixed table, or the bifurcation sums of d (complete before the
+// kernel starts).
+__host__ __device__ __forceinline__ bool in_slot_late(int s) {
+  return s == SI_CHN || (s >= SI_ML && s <= SI_YYP) || s == SI_XIL || s == SI_BQ3 || s == SI_BQ5 || s == SI_Q5U ||
+         s == SI_Q5P || s == SI_QBK;
+}
+
 // Along a diagonal every slot's source moves by a fixed stride per cell (the
 // tables are diagonal-major), so the light kernel finds it as the source of
 // cell x = 0 (a per-diagonal table) plus x times the stride; 0: the slot is
@@ -986,20 +997,29 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   int cE = 0, cB = 0;
   T cEn = 0;
   unsigned long long cMax = 0;
+  // Values of diagonal d-1 come from the previous light kernel, which may
+  // still be running (programmatic launch): they are read after griddep_wait
+  // ("late"); every other input is final and is read before it.
+  bool lateE = false;
   if (t < EN_N) cEn = p.en[t];
   if (t < 96) {
     const int k = d - 47 + t;
-    if (k >= 0 && k < d) cE = __ldcg(p.E + k);
+    if (k >= 0 && k < d) {
+      if (k == d - 1) lateE = true;
+      else cE = __ldcg(p.E + k);
+    }
   } else if (t < 96 + 6 * NS) {
     const int i = t - 96, side = i / (3 * NS), r = (i / NS) % 3, a = i % NS;
     const int q = (side == 0 ? x : y) - 1 + r;
     if (q >= 0 && q < n) cB = p.base[q * NS + a];
   } else if (t >= 96 + 6 * NS && t < 100 + 6 * NS) {
     const int k = t - 96 - 6 * NS;  // exponents of diagonals 0..3 (exterior split points)
-    if (k < d) cE = __ldcg(p.E + k);
+    if (k < d) {
+      if (k == d - 1) lateE = true;
+      else cE = __ldcg(p.E + k);
+    }
   } else if (t == NTT - 1 && d > 0) {
-    cMax = __ldcg(p.dmax + d - 1);
-    cE = __ldcg(p.E + d - 1);
+    lateE = true;  // largest mantissa and exponent of diagonal d-1
   }
   T cHL = 0;
   if (t == NTT - 2) cHL = p.eHL[d + 1];  // hairpin length factor of the cell
@@ -1012,24 +1032,34 @@ __device__ __forceinline__ void in_light_cell(const DP<T> &p, const BifBuf<T> &b
   // this cell does not use are zero-filled.  Every thread arrives once at the
   // barrier with the bytes of its copy (copies that complete earlier leave
   // the transaction count transiently negative, which the barrier allows).
+  // Slots whose source lies on diagonal d-1 are issued after griddep_wait,
+  // the rest before it.
   unsigned nbytes = 0;
-  {
-    const int LmaxS = min(MAXLOOP, d - 4);
+  const int LmaxS = min(MAXLOOP, d - 4);
+  const bool stage = t < SI_N && !(t > SI_YYP && t < SI_XIL && d >= 6 && t - SI_YYP + 3 <= LmaxS);  // not in the YY run
+  const bool late = stage && in_slot_late(t);
+  auto issue = [&]() {
     const int s = t;
     T *dst = S + (size_t)s * BLK;
-    if (s < SI_N && !(s > SI_YYP && s < SI_XIL && d >= 6 && s - SI_YYP + 3 <= LmaxS)) {  // not part of the YY run
-      const int st = in_slot_stride(s);
-      const T *src = src0 == nullptr ? nullptr : (st ? src0 + (size_t)x * st : (x == 0 ? src0 : nullptr));
-      if (src) {
-        const unsigned bytes = (s == SI_YYP ? (unsigned)(LmaxS - 2) : 1u) * BLK * (unsigned)sizeof(T);
-        bulk_g2s(dst, src, bytes, &sbar);
-        nbytes = bytes;
-      } else {
+    const int st = in_slot_stride(s);
+    const T *src = src0 == nullptr ? nullptr : (st ? src0 + (size_t)x * st : (x == 0 ? src0 : nullptr));
+    if (src) {
+      const unsigned bytes = (s == SI_YYP ? (unsigned)(LmaxS - 2) : 1u) * BLK * (unsigned)sizeof(T);
+      bulk_g2s(dst, src, bytes, &sbar);
+      nbytes = bytes;
+    } else {
 #pragma unroll
-        for (int q = 0; q < BLK; q++) dst[q] = (T)0;
-      }
+      for (int q = 0; q < BLK; q++) dst[q] = (T)0;
     }
+  };
+  if (stage && !late) issue();
+  griddep_wait();
+  if (lateE) {
+    cE = __ldcg(p.E + d - 1);
+    if (t == NTT - 1) cMax = __ldcg(p.dmax + d - 1);
   }
+  if (late) issue();
+  griddep_launch_dependents();  // the next diagonal's kernel may start its own early part
   mbar_arrive_expect(&sbar, nbytes);
   // destinations of the results (copied out at the end of the cell)
   if (t < NCOPY) {

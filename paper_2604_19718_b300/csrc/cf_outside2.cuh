@@ -567,6 +567,18 @@ __host__ __device__ __forceinline__ void out_slot_range(int n, int s, int d, int
   if (s == SO_HQC) xlo = 5;          // column gather terms
   if (s >= SO_HGXC) xhi = 0;         // exterior
 }
+// Slots written by the light kernel of diagonal d+1: the adjoints of the
+// neighbours (x-1, y) and (x, y+1), hQ5P[y] (for x = 1, y = d+1), the
+// interior-loop adjoint ring of d+1, the L = 1 bulge adjoints hHB of
+// (x, y+1) and (x-1, y), and the exterior adjoints of d+1.  Every other
+// source is a forward table, an adjoint of a diagonal >= d+2, or a gather
+// result of the off-chain launch of d (complete before the kernel starts);
+// the light kernel of d+1 scatters into hXI of diagonals d+1..d-2 only, none
+// of which this kernel reads.
+__host__ __device__ __forceinline__ bool out_slot_late(int s) {
+  return (s >= SO_H2UU && s <= SO_HCHL) || s == SO_HQ5P || (s >= SO_HYR && s < SO_CHL) || s == SO_BH3U ||
+         s == SO_BH5U || s == SO_HQ5U1 || s == SO_HGX1;
+}
 __host__ __device__ __forceinline__ int out_slot_stride(int s) {
   if (s >= SO_XXL && s < SO_QB) return 4 * BLK;
   if (s >= SO_HYR && s < SO_CHL) return NYY * BLK;
@@ -661,11 +673,20 @@ __global__ void __launch_bounds__(NTT, 1536 / NTT) k_out_light(DP<T> p, OutBuf<T
   if (t == 0) mbar_init(&obar, NTT);
   __syncthreads();
   {
+    // slots written by the light kernel of d+1 (which may still be running:
+    // programmatic launch) are issued after griddep_wait, the rest before it
     unsigned bytes = 0;
-    if (e.src && x >= e.xlo && x <= e.xhi) {
-      bytes = BLK * (unsigned)sizeof(T);
-      bulk_g2s(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t), bytes, &obar);
-    }
+    const bool late = out_slot_late(t);
+    auto issue = [&]() {
+      if (e.src && x >= e.xlo && x <= e.xhi) {
+        bytes = BLK * (unsigned)sizeof(T);
+        bulk_g2s(S + (size_t)t * BLK, e.src + (size_t)(x - e.xlo) * out_slot_stride(t), bytes, &obar);
+      }
+    };
+    if (!late) issue();
+    griddep_wait();
+    if (late) issue();
+    griddep_launch_dependents();  // the next diagonal's kernel may start its own early part
     mbar_arrive_expect(&obar, bytes);
   }
   if (t < 96) sE[t] = cE;

@@ -418,8 +418,22 @@ cudaError_t set_priority(cudaGraphNode_t node, bool high) {
   return cudaGraphKernelNodeSetAttribute(node, cudaKernelNodeAttributePriority, &v);
 }
 
+// A programmatic edge between consecutive kernels of a chain: the successor
+// may start once every CTA of the predecessor has called
+// griddep_launch_dependents, so that the launch and the successor's early
+// part (loads of inputs the predecessor does not write) overlap the
+// predecessor's end; the successor's griddep_wait then waits for it to finish.
+cudaError_t add_programmatic_edge(cudaGraph_t g, cudaGraphNode_t from, cudaGraphNode_t to) {
+  cudaGraphEdgeData ed = {};
+  ed.from_port = cudaGraphKernelNodePortProgrammatic;
+  ed.to_port = cudaGraphKernelNodePortDefault;
+  ed.type = cudaGraphDependencyTypeProgrammatic;
+  return cudaGraphAddDependencies(g, &from, &to, &ed, 1);
+}
+
 // The inside pass as a CUDA graph: a chain of light kernels, one per
-// anti-diagonal, and the bifurcation kernel of diagonal d hanging off the light
+// anti-diagonal (consecutive ones joined by programmatic edges), and the
+// bifurcation kernel of diagonal d hanging off the light
 // kernel of diagonal d-4, so that it runs while d-3..d-1 are being filled;
 // with far bands (binary32) the far kernel of band d0 (after its factor table)
 // hangs off the light kernel of d0 - 17 and precedes the band's bifurcation
@@ -512,7 +526,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     if (e != cudaSuccess) break;
     cudaGraphNode_t deps[2];
     int nd = 0;
-    deps[nd++] = (d == 0) ? mset : k2[d - 1];
+    if (d == 0) deps[nd++] = mset;
     if (d >= 8) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
     kp.func = (void *)klight;
@@ -521,6 +535,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    if (e == cudaSuccess && d > 0) e = add_programmatic_edge(g, k2[d - 1], k2[d]);
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
   }
@@ -739,7 +754,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     }
     cudaGraphNode_t deps[3];
     int nd = 0;
-    deps[nd++] = (d == n - 1) ? first : k2[d + 1];
+    if (d == n - 1) deps[nd++] = first;
     if (hasb || hass) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
     const bool wide = n - d > WIDE_CELLS;
@@ -749,6 +764,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     kp.sharedMemBytes = (unsigned)(wide ? smemw : smem);
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&k2[d], g, deps, nd, &kp);
+    if (e == cudaSuccess && d < n - 1) e = add_programmatic_edge(g, k2[d + 1], k2[d]);  // the chain
     if (e == cudaSuccess) e = set_priority(k2[d], true);
     nodes++;
   }

@@ -300,7 +300,9 @@ cf_status cf_surrogate_free(cf_surrogate *sur);
 /* Replace the parameters (and reset the optimiser state). */
 cf_status cf_surrogate_set_params(cf_surrogate *sur, const float *params);
 cf_status cf_surrogate_get_params(const cf_surrogate *sur, float *params);
-/* Predicted G of nwin windows (any nwin; processed max_batch at a time). */
+/* Predicted G of nwin windows (any nwin; processed max_batch at a time on
+ * the CUDA cores, up to 65,536 windows at a time on the tensor cores, whose
+ * row buffers -- about 5 bytes per base -- grow on first use). */
 cf_status cf_surrogate_predict(cf_surrogate *sur, const uint8_t *bases, const int64_t *offsets, int nwin,
                                float *G_out);
 /* Loss and its gradient (CF_SURROGATE_NPARAMS floats) on one batch, no update. */
@@ -315,10 +317,12 @@ float cf_surrogate_last_ms(const cf_surrogate *sur);
 /*
  * Which units run cf_surrogate_predict (training always uses the CUDA-core
  * kernels with FP32 activations):
- *   1 (default) tensor cores: each 64-channel layer as 128-row tiles of a
- *     5-tap GEMM on the 5th-generation tensor cores (tcgen05 MMA, FP32
- *     accumulators in tensor memory, operands staged by TMA); activations
- *     carried as two BF16 parts hi + lo (within 2^-18 relative of FP32);
+ *   1 (default) tensor cores: the four layers and the head term of a tile
+ *     of 116 rows in one persistent kernel, each 64-channel layer a 5-tap
+ *     GEMM of 128 rows on the 5th-generation tensor cores (tcgen05 MMA, FP32
+ *     accumulator in tensor memory, weights staged by TMA, activations kept
+ *     in shared memory between layers); activations carried as two BF16
+ *     parts hi + lo (within 2^-18 relative of FP32);
  *   0 CUDA cores: FP32 activations, FP32 FMA.
  * Errors: CF_EINVAL (NULL surrogate, unknown path).  A bounded wait of the
  * tensor-core pipeline that gives up makes cf_surrogate_predict return

@@ -315,12 +315,17 @@ struct cf_surrogate {
   __nv_bfloat16 *Wf = nullptr, *Wb = nullptr;
   float *h[4] = {}, *dp[2] = {}, *S = nullptr, *pred = nullptr, *dg = nullptr, *loss = nullptr, *tgt = nullptr;
   float *part = nullptr;
-  // tensor-core prediction path (surrogate_tc.cuh): weights, row frame,
-  // hi/lo activation rows (ping-pong), per-row head terms, error word
-  __nv_bfloat16 *Wtc = nullptr, *xh[2] = {nullptr, nullptr}, *xl[2] = {nullptr, nullptr};
-  int *rowwin = nullptr, *tcerr = nullptr;
-  float *srow = nullptr;
-  size_t rows_cap = 0;
+  // tensor-core prediction path (surrogate_tc.cuh): weights of layers 2-4 and
+  // the error word; the row frame (base per row), per-row head terms,
+  // predictions and offsets of a chunk, grown on demand (the path keeps no
+  // per-window activations, so its chunks are not bounded by max_batch)
+  __nv_bfloat16 *Wtc = nullptr;
+  int *tcerr = nullptr;
+  int8_t *rowbase = nullptr;
+  float *srow = nullptr, *tpred = nullptr;
+  int64_t *toff = nullptr;
+  size_t rows_cap = 0, twin_cap = 0;
+  std::vector<void *> tc_allocs;
   int path = 1;  // prediction: 0 CUDA cores (FP32 activations), 1 tensor cores
   int sms = 148;
   uint8_t *bases = nullptr;
@@ -421,47 +426,54 @@ bool row_map(CUtensorMap *m, const void *base, size_t rows, unsigned box_rows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Windows per chunk of the tensor-core path.
+constexpr int TC_CHUNK = 1 << 16;
+
+// The tensor-core path's chunk buffers for up to nwin windows (grown, never shrunk).
+cf_status tc_reserve(cf_surrogate *s, int nwin) {
+  if ((size_t)nwin <= s->twin_cap) return CF_OK;
+  SG_CUDA(cudaStreamSynchronize(s->stream));
+  for (void *q : s->tc_allocs) cudaFree(q);
+  s->tc_allocs.clear();
+  s->twin_cap = s->rows_cap = 0;
+  const size_t rows = (size_t)nwin * (CF_SURROGATE_MAX_LEN + 4);
+  SG_CUDA(salloc(s->tc_allocs, &s->rowbase, rows));
+  SG_CUDA(salloc(s->tc_allocs, &s->srow, rows));
+  SG_CUDA(salloc(s->tc_allocs, &s->tpred, (size_t)nwin));
+  SG_CUDA(salloc(s->tc_allocs, &s->toff, (size_t)nwin + 1));
+  s->rows_cap = rows;
+  s->twin_cap = (size_t)nwin;
+  return CF_OK;
+}
+
 // The forward pass on the tensor cores for a staged batch of nb windows.
 cf_status forward_tc(cf_surrogate *s, const uint8_t *db, const int64_t *doff, int nb, const std::vector<int64_t> &hoff) {
   cudaStream_t st = s->stream;
   const int nrows = (int)(hoff[nb] - hoff[0]) + 4 * nb;
   if ((size_t)nrows > s->rows_cap) return sfail(CF_EINVAL, "surrogate: batch exceeds the row buffers");
-  k_tc_rows<<<nb, 128, 0, st>>>(doff, nb, nrows, s->rowwin);
-  k_tc_layer1<<<(int)(((size_t)nrows * 64 + 255) / 256), 256, 0, st>>>(doff, db, s->rowwin, nrows, s->Wf + WF_OFF(0),
-                                                                        s->P + OB(0), s->xh[0], s->xl[0]);
+  k_tc_rows<<<nb, 128, 0, st>>>(doff, db, nb, nrows, s->rowbase);
   SG_CUDA(cudaGetLastError());
   CUtensorMap tw;
   if (!row_map(&tw, s->Wtc, 3 * 5 * 64, 64)) return sfail(CF_ECUDA, "surrogate: weight tensor map");
-  const int ntiles = (nrows + TC_M - 1) / TC_M;
+  const int ntiles = (nrows + TC_OUT - 1) / TC_OUT;
   const int grid = std::max(1, std::min(ntiles, s->sms));
-  int cur = 0;
-  for (int l = 1; l <= 3; l++) {
-    CUtensorMap th, tl;
-    if (!row_map(&th, s->xh[cur], nrows, TC_HALO) || !row_map(&tl, s->xl[cur], nrows, TC_HALO))
-      return sfail(CF_ECUDA, "surrogate: activation tensor map");
-    TcArgs a;
-    a.nrows = nrows;
-    a.rowwin = s->rowwin;
-    a.bias = s->P + OB(l);
-    a.wh = s->P + OWH;
-    a.out_hi = s->xh[cur ^ 1];
-    a.out_lo = s->xl[cur ^ 1];
-    a.s_out = s->srow;
-    a.wrow0 = (l - 1) * 5 * 64;
-    a.last = l == 3;
-    a.err = s->tcerr;
-    k_conv_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(th, tl, tw, a);
-    SG_CUDA(cudaGetLastError());
-    cur ^= 1;
-  }
-  k_tc_head<<<(nb + 3) / 4, 128, 0, st>>>(doff, nb, s->srow, s->P, s->pred);
+  TcArgs a;
+  a.nrows = nrows;
+  a.rowbase = s->rowbase;
+  a.W1 = s->Wf + WF_OFF(0);
+  a.P = s->P;
+  a.s_out = s->srow;
+  a.err = s->tcerr;
+  k_surr_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(tw, a);
+  SG_CUDA(cudaGetLastError());
+  k_tc_head<<<(nb + 3) / 4, 128, 0, st>>>(doff, nb, s->srow, s->P, s->tpred);
   SG_CUDA(cudaGetLastError());
   return CF_OK;
 }
 
 // Stage a batch: copy host inputs to the device, validate window lengths.
 cf_status stage(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, int nwin, const uint8_t **db,
-                const int64_t **doff, std::vector<int64_t> &hoff) {
+                const int64_t **doff, std::vector<int64_t> &hoff, bool tc = false) {
   hoff.assign((size_t)nwin + 1, 0);
   cudaStream_t st = s->stream;
   if (on_other_device(offsets, s->device) || on_other_device(bases, s->device))
@@ -496,8 +508,9 @@ cf_status stage(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, i
   if (odev) {
     *doff = offsets;
   } else {
-    SG_CUDA(cudaMemcpyAsync(s->off, hoff.data(), sizeof(int64_t) * (nwin + 1), cudaMemcpyHostToDevice, st));
-    *doff = s->off;
+    int64_t *dst = tc ? s->toff : s->off;  // the tensor-core path's chunks exceed max_batch
+    SG_CUDA(cudaMemcpyAsync(dst, hoff.data(), sizeof(int64_t) * (nwin + 1), cudaMemcpyHostToDevice, st));
+    *doff = dst;
   }
   return CF_OK;
 }
@@ -581,14 +594,7 @@ cf_status cf_surrogate_create(int device, void *stream, int max_batch, cf_surrog
   if (e == cudaSuccess) e = salloc(L, &s->part, (size_t)s->dw_grid * (C * 64 * K + C));
   if (e == cudaSuccess) e = salloc(L, &s->off, (size_t)max_batch + 1);
   s->sms = sms;
-  s->rows_cap = (size_t)max_batch * (LP + 4);
   if (e == cudaSuccess) e = salloc(L, &s->Wtc, (size_t)3 * 5 * 64 * 64);
-  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
-    e = salloc(L, &s->xh[k], s->rows_cap * 64);
-    if (e == cudaSuccess) e = salloc(L, &s->xl[k], s->rows_cap * 64);
-  }
-  if (e == cudaSuccess) e = salloc(L, &s->rowwin, s->rows_cap);
-  if (e == cudaSuccess) e = salloc(L, &s->srow, s->rows_cap);
   if (e == cudaSuccess) e = salloc(L, &s->tcerr, (size_t)1);
   if (e == cudaSuccess) e = cudaMemset(s->tcerr, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(s->P, 0, sizeof(float) * NPARAM);
@@ -607,7 +613,7 @@ cf_status cf_surrogate_create(int device, void *stream, int max_batch, cf_surrog
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void *)k_dw<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dw_smem(4));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void *)k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    e = cudaFuncSetAttribute((const void *)k_surr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e != cudaSuccess) {
     cf_surrogate_free(s);
     return sfail(e == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA,
@@ -624,6 +630,7 @@ cf_status cf_surrogate_free(cf_surrogate *s) {
   else cudaDeviceSynchronize();
   for (void *q : s->allocs) cudaFree(q);
   for (void *q : s->base_allocs) cudaFree(q);
+  for (void *q : s->tc_allocs) cudaFree(q);
   for (auto &e : s->ev)
     if (e) cudaEventDestroy(e);
   delete s;
@@ -666,10 +673,12 @@ cf_status cf_surrogate_predict(cf_surrogate *s, const uint8_t *bases, const int6
   } else {
     std::copy(offsets, offsets + nwin + 1, all.begin());
   }
+  const int chunk = s->path ? std::max(s->max_batch, TC_CHUNK) : s->max_batch;
+  if (s->path) SG_TRY(tc_reserve(s, std::min(chunk, nwin)));
   SG_CUDA(cudaEventRecord(s->ev[0], s->stream));
   float total_ms = 0;
-  for (int w0 = 0; w0 < nwin; w0 += s->max_batch) {
-    const int nb = std::min(s->max_batch, nwin - w0);
+  for (int w0 = 0; w0 < nwin; w0 += chunk) {
+    const int nb = std::min(chunk, nwin - w0);
     // re-base this chunk's offsets so that its bases start at the chunk's first window
     std::vector<int64_t> o(all.begin() + w0, all.begin() + w0 + nb + 1);
     // device bases keep absolute offsets; host bases are staged from the chunk's first window
@@ -681,10 +690,10 @@ cf_status cf_surrogate_predict(cf_surrogate *s, const uint8_t *bases, const int6
     const uint8_t *db;
     const int64_t *doff;
     std::vector<int64_t> hoff;
-    SG_TRY(stage(s, src, o.data(), nb, &db, &doff, hoff));
+    SG_TRY(stage(s, src, o.data(), nb, &db, &doff, hoff, s->path != 0));
     if (s->path) SG_TRY(forward_tc(s, db, doff, nb, hoff));
     else SG_TRY(forward(s, db, doff, nb, nullptr));
-    SG_TRY(copy_out(s, G_out + w0, s->pred, sizeof(float) * nb));
+    SG_TRY(copy_out(s, G_out + w0, s->path ? s->tpred : s->pred, sizeof(float) * nb));
     SG_CUDA(cudaStreamSynchronize(s->stream));  // host offsets / staging buffers reused by the next chunk
   }
   SG_CUDA(cudaEventRecord(s->ev[1], s->stream));

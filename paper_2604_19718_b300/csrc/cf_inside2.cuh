@@ -143,11 +143,12 @@ static __constant__ int g_cf_range_limit = 120;
 static __constant__ int g_cf_range_maxlen = 400;  // lengths a considered (0: all)
 __device__ __forceinline__ int range_limit() { return g_cf_range_limit; }
 
-// F is summed and its log taken in binary64, then held in binary32: |F| grows
-// by a few bits per nucleotide (about 2 on the 900-nt workload), so below the
-// 51,200-nt bound of this check the rounding of F is under 0.01 bits, far
-// below the whole bits the refusal compares; the n x maxlen differences then
-// run on the binary32 pipes.
+// Everything runs in binary32 (the binary64 pipe of this GPU is a small
+// fraction of the binary32 one): a prefix's 72 table entries are binary32
+// mantissas, and |F| grows by a few bits per nucleotide (about 2 on the
+// 900-nt workload), so below the 51,200-nt bound of this check the rounding
+// of F is under 0.01 bits, far below the whole bits the refusal compares.
+// Only the binary32 inside pass runs it (binary64 has the range).
 template <typename T>
 __global__ void __launch_bounds__(1024) k_in_range(DP<T> p, int *spread_out) {
   extern __shared__ float F[];  // [n]
@@ -160,10 +161,10 @@ __global__ void __launch_bounds__(1024) k_in_range(DP<T> p, int *spread_out) {
   __syncthreads();
   for (int y = t; y < n; y += blockDim.x) {
     const T *u = p.Q5U + (size_t)y * BLK, *q = p.Q5P + (size_t)y * BLK;
-    double s = 0;
-    for (int e = 0; e < BLK; e++) s += (double)u[e] + (double)q[e];
+    float s = 0;
+    for (int e = 0; e < BLK; e++) s += (float)u[e] + (float)q[e];
     if (!(s > 0)) atomicOr(&sflush, 1);
-    F[y] = s > 0 ? (float)(log2(s) + (double)__ldcg(p.E + y)) : 0.0f;
+    F[y] = s > 0 ? log2f(s) + (float)__ldcg(p.E + y) : 0.0f;
   }
   __syncthreads();
   // one warp per length a, lanes over the start x (x = 0 exists for every a < n)

@@ -549,7 +549,7 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     cudaGraphNode_t fin;
     e = cudaGraphAddKernelNode(&fin, g, &k2[n - 1], 1, &kp);
     nodes++;
-    if (e == cudaSuccess && t.bb.spread) {  // the range of the binary32 tables, after the pass
+    if (e == cudaSuccess && t.bb.spread && sizeof(T) == sizeof(float)) {  // the range of the binary32 tables
       int *sp = t.bb.spread;
       void *rargs[] = {&dp, &sp};
       cudaKernelNodeParams kr = {};

@@ -494,6 +494,58 @@ def bench_frequency(stream):
             "r_tol": 0.002, "anderson_depth": 5}
 
 
+def tm_flops(res, gamma):
+    """Algorithmic flops of the tensor-model recursion (2 per FMA) with the
+    protein's actual block sides gamma * M_p: per cell [i, j+1) the unpaired
+    extension Q[i, j] X_j and one block product per split point k = i..j-4,
+    per pair (k, j) the two transfer products of the fold and its traces."""
+    M = codon_counts(res).astype(np.float64) * gamma
+    n = M.size
+    C = np.concatenate([[0.0], np.cumsum(M)])  # C[q] = sum of M[0..q-1]
+    tot = 0.0
+    for i in range(n):
+        j = np.arange(i + 1, n)
+        tot += 2 * np.sum(M[i] * M[j - 1] * M[j])
+        j = np.arange(i + 4, n)  # split points: k = i (side M[i]) and k = i+1..j-4
+        tot += 2 * np.sum(M[i] * M[j] * (M[i] + C[j - 3] - C[i + 1]))
+    for k in range(n - 4):
+        j = np.arange(k + 4, n)
+        tot += np.sum(2 * (M[k] * M[k + 1] * M[j - 1] + M[k] * M[j - 1] * M[j]) + 4 * M[k] * M[j] * gamma)
+    return float(tot)
+
+
+def bench_tm(stream):
+    """The paper's tensor-based model (synthetic gamma 4, two pair
+    conformations, renormalised) under the codon constraints of the first
+    100 and 300 residues of the 900-nt workload, both precisions."""
+    import paper_2604_19718_b300 as cf
+    V, B, S = synth.tm_params(0, 4, 2)
+    model = cf.TensorModel(V, B, S)
+    res_all, _, _ = synth.workload(WORKLOAD)
+    out = {"model": "synthetic tensor model (seed 0): gamma 4, 2 pair conformations, spectral-radius renormalised",
+           "workload": f"{WORKLOAD} prefixes, no codon weights"}
+    for m in (100, 300):
+        res = res_all[:m]
+        f = cf.CodonFold(synth.nn_params(0), stream=stream)
+        f.set_protein(res)
+        f.tm_inside(model, cf.CF_FP32_SCALED)  # warm-up: tables and graph
+        l32 = f.tm_inside(model, cf.CF_FP32_SCALED)
+        ms32 = cf.cf_tm_last_ms(f.prob)
+        f.tm_inside(model, cf.CF_FP64)
+        l64 = f.tm_inside(model, cf.CF_FP64)
+        ms64 = cf.cf_tm_last_ms(f.prob)
+        f.close()
+        n = 3 * m
+        cells = n * (n + 1) / 2
+        fl = tm_flops(res, 4)
+        out[f"m{m}"] = {"nt": n, "fp32_ms": ms32, "fp64_ms": ms64, "cells_per_s_fp32": cells / (ms32 * 1e-3),
+                        "algorithmic_tflops_fp32": fl / (ms32 * 1e-3) / 1e12,
+                        "abs_dlogZ_fp32_vs_fp64": abs(l32 - l64), "rel_dlogZ": abs(l32 - l64) / abs(l64),
+                        "logZ": l64}
+    model.close()
+    return out
+
+
 def bench_large(stream, nsamples=10_000):
     """The 1000-aa / 3000-nt soft-weighted protein in binary32."""
     import paper_2604_19718_b300 as cf
@@ -549,6 +601,17 @@ def profile_form(form, steps):
                 f.outside(False, True, False)
                 out["ms"] = f.timing()[:2]
         f.close()
+    elif form == "tm":  # the tensor-model pass on the first 100 residues (300 nt)
+        V, B, S = synth.tm_params(0, 4, 2)
+        model = cf.TensorModel(V, B, S)
+        res, _, _ = synth.workload(WORKLOAD)
+        f = cf.CodonFold(params)
+        f.set_protein(res[:100])
+        for _ in range(steps):
+            f.tm_inside(model, cf.CF_FP32_SCALED)
+        out["ms"] = cf.cf_tm_last_ms(f.prob)
+        f.close()
+        model.close()
     elif form == "windows":
         ex = screen.Windows(params)
         _, _, bases, off = synth.windows(8000, seed=3)
@@ -573,7 +636,7 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="use only the first M residues (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the window, surrogate, adjoint and 3000-nt measurements")
-    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint"],
+    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm"],
                     help="run one form on a small case (for profiler captures) and print its timing")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -694,6 +757,7 @@ def main():
         forms["concurrent"] = bench_concurrent()
         forms["frequency_matching"] = bench_frequency(stream.cuda_stream)
         forms["mfe"] = bench_mfe(stream.cuda_stream)
+        forms["tensor_model"] = bench_tm(stream.cuda_stream)
 
     if rank != 0:
         return

@@ -188,6 +188,52 @@ cf_status cf_mfe(cf_problem *prob, int64_t *cost, double *mfe_kcal, int32_t *cod
 float cf_mfe_last_ms(const cf_problem *prob);
 
 /*
+ * The paper's own tensor-based free energy model (SI "Tensor-based free
+ * energy models", Eq. general-model) under the codon constraints of the
+ * problem's protein: gamma x gamma matrices V_x for an unpaired base x
+ * (A, C, G, U = 0..3), B^rho_{x,y} for the two sides of a base pair
+ * (rho = 0..nrho-1) and S for the weighted trace Tr_S[X] = tr(S X).  A
+ * structure's weight is the sum over one rho per pair of the product over
+ * its loops (the exterior loop included) of Tr_S[the loop's matrices in
+ * backbone order]: V for an unpaired base, B^rho_{x,y} for a base x whose
+ * next base in the loop is its partner y, the identity otherwise; pairs
+ * closer than 4 positions have no weight.  Codon sequences weigh as in
+ * cf_set_protein / cf_set_weights (Eq. amino-q, codon-pair tensor train).
+ *
+ * cf_tm_spectral_radius: host only (no device use): the spectral radius of a
+ *   dim x dim row-major matrix (1 <= dim <= 64), by Gelfand's formula over 48
+ *   repeated squarings.  Errors: CF_EINVAL (NULL, bad dim, non-finite entry).
+ * cf_tm_model_create: V = 4 x gamma x gamma, B = nrho x 4 x 4 x gamma x gamma
+ *   (B[rho][x][y]: x the base whose next loop base is its partner y), S =
+ *   gamma x gamma, all row-major binary64 host arrays, copied; 1 <= gamma
+ *   <= 4, 1 <= nrho <= 4.  normalize != 0 applies the spectral-radius
+ *   renormalisation of SI "Free energy model renormalization": V_x / r_x and
+ *   B^rho_{x,y} / sqrt(r_x r_y), r_x the spectral radius of V_x (reported by
+ *   cf_tm_model_radius).  The model lives on `device`.  Errors: CF_EINVAL
+ *   (NULL, sizes, non-finite entry, a V_x with radius 0 when normalising),
+ *   CF_ENOMEM, CF_ECUDA.
+ * cf_tm_inside: log Z (natural log) of the problem's protein under the model
+ *   into *logZ (host), by the recursion of Eq. complicated-pf with the fold of
+ *   Eq. fold generalised to codon states (Eq. design-fold), evaluated by
+ *   interval length on the device; CF_FP32_SCALED keeps per-length
+ *   power-of-two exponents, CF_FP64 is plain binary64 with the same
+ *   exponents.  Tables of about 3 x n(n+1)/2 x 576 values of the precision
+ *   are allocated on the first call for a protein and freed with it.  Errors:
+ *   CF_EINVAL (NULL, unknown precision, model on another device, a batch),
+ *   CF_ESTATE (no protein), CF_ENUMERIC (non-finite or zero Z), CF_ENOMEM,
+ *   CF_ECUDA.
+ * cf_tm_last_ms: device time of the last cf_tm_inside.
+ */
+typedef struct cf_tm_model cf_tm_model;
+cf_status cf_tm_spectral_radius(const double *A, int dim, double *radius);
+cf_status cf_tm_model_create(int device, int gamma, int nrho, const double *V, const double *B, const double *S,
+                             int normalize, cf_tm_model **out);
+cf_status cf_tm_model_radius(const cf_tm_model *model, double *radius4);
+cf_status cf_tm_model_free(cf_tm_model *model);
+cf_status cf_tm_inside(cf_problem *prob, const cf_tm_model *model, cf_precision precision, double *logZ);
+float cf_tm_last_ms(const cf_problem *prob);
+
+/*
  * Checkpointing of the interior-loop partial sums (the adjoint's largest
  * intermediate: 29 blocks per cell, 19 GB in binary32 at 3000 nt when stored
  * whole).  Checkpointed, the inside pass keeps them for two diagonals plus

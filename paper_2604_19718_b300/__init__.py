@@ -88,6 +88,17 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = ctypes.c_int
     lib.cf_mfe_last_ms.argtypes = [vp]
     lib.cf_mfe_last_ms.restype = ctypes.c_float
+    lib.cf_tm_spectral_radius.argtypes = [dp, ctypes.c_int, dp]
+    lib.cf_tm_model_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int,
+                                       ctypes.POINTER(vp)]
+    lib.cf_tm_model_radius.argtypes = [vp, dp]
+    lib.cf_tm_model_free.argtypes = [vp]
+    lib.cf_tm_inside.argtypes = [vp, vp, ctypes.c_int, dp]
+    lib.cf_tm_last_ms.argtypes = [vp]
+    lib.cf_tm_last_ms.restype = ctypes.c_float
+    for name in ("cf_tm_spectral_radius", "cf_tm_model_create", "cf_tm_model_radius", "cf_tm_model_free",
+                 "cf_tm_inside"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("cf_far_band_info", "cf_debug_set_wait_polls", "cf_debug_fail_alloc", "cf_sample_noalloc",
                  "cf_mfe"):
         getattr(lib, name).restype = ctypes.c_int
@@ -262,6 +273,70 @@ def cf_checkpointed(prob) -> bool:
 
 def cf_mfe_last_ms(prob) -> float:
     return float(lib.cf_mfe_last_ms(prob))
+
+
+def _dbl(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def cf_tm_spectral_radius(A) -> float:
+    A, pa = _dbl(A)
+    out = ctypes.c_double()
+    _check(lib.cf_tm_spectral_radius(pa, int(A.shape[0]), ctypes.byref(out)))
+    return out.value
+
+
+def cf_tm_model_create(V, B, S, normalize: bool = True, device: int = 0) -> ctypes.c_void_p:
+    """V: 4 x g x g, B: nrho x 4 x 4 x g x g, S: g x g (binary64)."""
+    V, pv = _dbl(V)
+    B, pb = _dbl(B)
+    S, ps = _dbl(S)
+    h = ctypes.c_void_p()
+    _check(lib.cf_tm_model_create(int(device), int(V.shape[1]), int(B.shape[0]), pv, pb, ps, int(bool(normalize)),
+                                  ctypes.byref(h)))
+    return h
+
+
+def cf_tm_model_radius(model) -> np.ndarray:
+    out = np.zeros(4)
+    _check(lib.cf_tm_model_radius(model, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def cf_tm_model_free(model) -> None:
+    lib.cf_tm_model_free(model)
+
+
+def cf_tm_inside(prob, model, precision: int = CF_FP32_SCALED) -> float:
+    out = ctypes.c_double()
+    _check(lib.cf_tm_inside(prob, model, int(precision), ctypes.byref(out)), prob)
+    return out.value
+
+
+def cf_tm_last_ms(prob) -> float:
+    return float(lib.cf_tm_last_ms(prob))
+
+
+class TensorModel:
+    """A tensor-based free energy model on one device (owns the handle)."""
+
+    def __init__(self, V, B, S, normalize: bool = True, device: int = 0):
+        self.h = cf_tm_model_create(V, B, S, normalize, device)
+
+    def radius(self) -> np.ndarray:
+        return cf_tm_model_radius(self.h)
+
+    def close(self):
+        if self.h:
+            cf_tm_model_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cf_far_band_info(prob):
@@ -459,6 +534,10 @@ class CodonFold:
         par = np.zeros(self.n, dtype=np.int32) if traceback else None
         q, k = cf_mfe(self.prob, cod, par)
         return q, k, cod, par
+
+    def tm_inside(self, model: "TensorModel", precision: int = CF_FP32_SCALED) -> float:
+        """log Z of the protein under a tensor-based model (cf_tm_inside)."""
+        return cf_tm_inside(self.prob, model.h, precision)
 
     def timing(self):
         return cf_last_timing(self.prob)

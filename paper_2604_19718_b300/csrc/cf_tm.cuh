@@ -1,0 +1,272 @@
+// cf_tm.cuh -- log Z of a protein under the paper's own tensor-based free
+// energy model (SI "Tensor-based free energy models", Eq. general-model):
+// gamma x gamma matrices V_x (unpaired base x), B^rho_{x,y} (the two sides of
+// a base pair, rho = 0..nrho-1) and S (weighted trace Tr_S[X] = tr(S X)),
+// summed over every codon sequence of the protein with the codon-pair tensor
+// train of Eq. pair-tt (the same position transfers T_p as the
+// nearest-neighbour path).
+//
+// The recursion is Eq. complicated-pf with the fold of Eq. fold generalised
+// to codon states as in Eq. design-fold.  For an interval [i, j) the block
+// Q[i, j] is a matrix over (codon state at i, zeta) x (codon state at j-1,
+// zeta'), flattened state-major and padded to TM_D = 6 states x TM_G = 4:
+//   Q[i, i+1]  = delta_ab V_{x_i(a)}
+//   Q[i, j+1]  = Q[i, j] X_j + sum_{k=i}^{j-4} L[i, k] F[k, j]
+//   X_j        = T_{j-1} (x) V_j                 (base j unpaired)
+//   L[i, i]    = identity, L[i, k] = Q[i, k] (T_{k-1} (x) I)
+//   F[k, j]    = sum_rho B^rho_{k,j} Tr_S[B^rho_{j,k} Y],
+//   Y          = (T_k (x) I) Q[k+1, j] (T_{j-1} (x) I)   (k paired to j)
+//   Z          = sum_{a,c} u0[a] Tr_S[Q[0, n]_{a c}].
+// The paper evaluates the same sum column by column with a triangular
+// matrix product per column (Alg. fast-pf); here it runs by interval length
+// (anti-diagonals), like the nearest-neighbour path: per length L, the folds
+// of the pairs at distance L-1 (k_tm_fold) and then the cells of length L
+// (k_tm_cell, one CTA per cell), so that a per-length power-of-two exponent
+// E[L] keeps binary32 mantissas in range: Q and L of length L carry E[L], F
+// of distance D carries E[D-1], and every product term takes the exact
+// factor 2^{E[.] + E[.] - E[L]}.  E[L] is set from the largest mantissa of
+// length L-1.
+#pragma once
+#include "cf_common.cuh"
+#include "cf_inside.cuh"
+
+namespace cf {
+
+constexpr int TM_G = 4;             // largest structural dimension gamma
+constexpr int TM_R = 4;             // largest number of pair conformations rho
+constexpr int TM_D = NS * TM_G;     // padded block side (state, zeta)
+constexpr int TM_BLK = TM_D * TM_D;  // 576 entries per block
+constexpr int TM_NT = TM_BLK;       // threads of the cell and fold kernels: one per block entry
+constexpr int TM_KC = 4;            // split points staged per step of the cell kernel (binary32; 2 in binary64)
+
+// model on the device (binary64): V[x][g][g], B[rho][x][y][g][g], SB = S B, S[g][g]
+struct TmModelDev {
+  double V[4][TM_G][TM_G];
+  double B[TM_R][4][4][TM_G][TM_G];
+  double SB[TM_R][4][4][TM_G][TM_G];
+  double S[TM_G][TM_G];
+};
+
+template <typename T>
+struct TmArgs {
+  int n, nrho;
+  const int *Mp, *base;       // codon-state counts, base of state a at p [n*6]
+  const double *Tr;           // position transfers [n*36] (binary64 masters)
+  const double *u0, *ls;      // residue-0 weights, per-boundary log rescales
+  int nls;
+  const TmModelDev *mod;
+  T *Q, *L, *F;               // [ncell][TM_BLK], diagonal-major (cidx of [i, j-1])
+  int *E;                     // [n + 1] per-length exponents
+  unsigned long long *dmax;   // [n + 1] largest |mantissa| per length (binary64 bits)
+  double *Zm, *logz;
+  int *err;
+};
+
+__device__ __forceinline__ size_t tm_cell(int n, int i, int len) { return cidx(n, i, i + len - 1) * TM_BLK; }
+
+// Q[i, i+1] (block-diagonal V) and L[i, i+1] for every position; one CTA per position
+template <typename T>
+__global__ void __launch_bounds__(TM_NT) k_tm_init(TmArgs<T> a) {
+  const int i = blockIdx.x, t = threadIdx.x, n = a.n;
+  const int r = t / TM_D, c = t % TM_D, ar = r / TM_G, zr = r % TM_G, ac = c / TM_G, zc = c % TM_G;
+  const int M = a.Mp[i];
+  __shared__ T q[TM_BLK];
+  T v = 0;
+  if (ar == ac && ar < M) v = (T)a.mod->V[a.base[i * NS + ar]][zr][zc];
+  q[t] = v;
+  a.Q[tm_cell(n, i, 1) + t] = v;
+  __syncthreads();
+  if (i + 1 < n) {  // L[i, i+1] = Q[i, i+1] (T_i (x) I)
+    T s = 0;
+    const double *tr = a.Tr + (size_t)i * BLK;
+#pragma unroll
+    for (int b = 0; b < NS; b++) s += q[r * TM_D + b * TM_G + zc] * (T)tr[b * NS + ac];
+    a.L[tm_cell(n, i, 1) + t] = s;
+  }
+  // the largest |entry| of length 1
+  T m = fabs(v);
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((t & 31) == 0) atomic_max_pos(a.dmax + 1, (double)m);
+}
+
+// F of the pairs (k, k + D), D = len - 1 >= 4, from Q[k+1, k+D] (length D-1);
+// one CTA per k
+template <typename T>
+__global__ void __launch_bounds__(TM_NT) k_tm_fold(TmArgs<T> a, int len) {
+  const int n = a.n, D = len - 1, k = blockIdx.x, j = k + D, t = threadIdx.x;
+  const int r = t / TM_D, c = t % TM_D, ar = r / TM_G, zr = r % TM_G, ac = c / TM_G, zc = c % TM_G;
+  __shared__ T q[TM_BLK], y1[TM_BLK], tk[BLK], tj[BLK], tr[TM_R][BLK];
+  __shared__ int xk[NS], xj[NS];
+  q[t] = a.Q[tm_cell(n, k + 1, D - 1) + t];
+  if (t < BLK) {
+    tk[t] = (T)a.Tr[(size_t)k * BLK + t];
+    tj[t] = (T)a.Tr[(size_t)(j - 1) * BLK + t];
+  }
+  if (t < NS) {
+    xk[t] = t < a.Mp[k] ? a.base[k * NS + t] : 0;
+    xj[t] = t < a.Mp[j] ? a.base[j * NS + t] : 0;
+  }
+  __syncthreads();
+  // y1 = (T_k (x) I) Q
+  {
+    T s = 0;
+#pragma unroll
+    for (int b = 0; b < NS; b++) s += tk[ar * NS + b] * q[(b * TM_G + zr) * TM_D + c];
+    y1[t] = s;
+  }
+  __syncthreads();
+  // Y = y1 (T_{j-1} (x) I), into q
+  {
+    T s = 0;
+#pragma unroll
+    for (int e = 0; e < NS; e++) s += y1[r * TM_D + e * TM_G + zc] * tj[e * NS + ac];
+    q[t] = s;
+  }
+  __syncthreads();
+  // the closed loop's trace per (state at k, state at j, rho): Tr_S[B^rho_{j,k} Y_{ac}]
+  if (t < BLK * a.nrho) {
+    const int rho = t / BLK, ak = (t % BLK) / NS, cj = t % NS;
+    const double(*sb)[TM_G] = a.mod->SB[rho][xj[cj]][xk[ak]];
+    T s = 0;
+#pragma unroll
+    for (int e1 = 0; e1 < TM_G; e1++)
+#pragma unroll
+      for (int e2 = 0; e2 < TM_G; e2++) s += (T)sb[e2][e1] * q[(ak * TM_G + e1) * TM_D + cj * TM_G + e2];
+    tr[rho][ak * NS + cj] = s;
+  }
+  __syncthreads();
+  T f = 0;
+  if (ar < a.Mp[k] && ac < a.Mp[j])
+    for (int rho = 0; rho < a.nrho; rho++) f += (T)a.mod->B[rho][xk[ar]][xj[ac]][zr][zc] * tr[rho][ar * NS + ac];
+  a.F[cidx(n, k, j) * TM_BLK + t] = f;
+}
+
+// the cells of length len >= 2; one CTA per cell i
+template <typename T>
+__global__ void __launch_bounds__(TM_NT) k_tm_cell(TmArgs<T> a, int len) {
+  const int n = a.n, i = blockIdx.x, t = threadIdx.x;
+  const int j = i + len - 1;  // the new last base
+  const int r = t / TM_D, c = t % TM_D, ac = c / TM_G, zc = c % TM_G;
+  constexpr int KC = sizeof(T) == sizeof(float) ? TM_KC : 2;  // within 48 KB of static shared memory
+  __shared__ T sL[2][KC][TM_BLK], sF[2][KC][TM_BLK];
+  __shared__ T q[TM_BLK], x[TM_BLK], tq[BLK];
+  __shared__ int sEL;
+  __shared__ T smx[TM_NT / 32];
+  // this length's exponent from the largest mantissa of length len - 1
+  if (t == 0) {
+    const double mx = __longlong_as_double((long long)__ldcg(a.dmax + len - 1));
+    int e = __ldcg(a.E + len - 1);
+    if (mx > 0) {
+      if (isfinite(mx)) e += ilogb(mx);
+      else atomicOr(a.err, 1);
+    }
+    sEL = e;
+    if (i == 0) a.E[len] = e;
+  }
+  // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1)
+  {
+    const int br = r / TM_G, zr = r % TM_G;
+    T xv = 0;
+    if (ac < a.Mp[j]) xv = (T)a.Tr[(size_t)(j - 1) * BLK + br * NS + ac] * (T)a.mod->V[a.base[j * NS + ac]][zr][zc];
+    x[t] = xv;
+    q[t] = a.Q[tm_cell(n, i, len - 1) + t];
+  }
+  __syncthreads();
+  const int EL = sEL;
+  T acc = 0;
+  {
+    T s = 0;
+#pragma unroll 8
+    for (int u = 0; u < TM_D; u++) s += q[r * TM_D + u] * x[u * TM_D + c];
+    acc = s * clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
+  }
+  // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
+  if (j - i >= 4) acc += a.F[cidx(n, i, j) * TM_BLK + t] * clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
+  // k = i+1 .. j-4: L[i, k] F[k, j], KC split points per step; the next
+  // step's blocks are loaded into registers before this step's products and
+  // stored to the other buffer after them
+  const int k0 = i + 1, k1 = j - 4;
+  __shared__ T sFac[2][KC];
+  T nl[KC], nf[KC];
+  auto load = [&](int kb) {
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      const int k = kb + u;
+      nl[u] = k <= k1 ? __ldcg(a.L + tm_cell(n, i, k - i) + t) : (T)0;
+      nf[u] = k <= k1 ? __ldcg(a.F + cidx(n, k, j) * TM_BLK + t) : (T)0;
+    }
+  };
+  auto store = [&](int buf, int kb) {
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      sL[buf][u][t] = nl[u];
+      sF[buf][u][t] = nf[u];
+    }
+    if (t < KC) {  // the split point's factor 2^{E[k-i] + E[j-k-1] - E[len]}
+      const int k = kb + t;
+      sFac[buf][t] = k <= k1 ? clamp_p2<T>(__ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) - EL) : (T)0;
+    }
+  };
+  if (k0 <= k1) {
+    load(k0);
+    store(0, k0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int kb = k0; kb <= k1; kb += KC, buf ^= 1) {
+    const bool more = kb + KC <= k1;
+    if (more) load(kb + KC);
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      const T *Lb = sL[buf][u], *Fb = sF[buf][u];
+      T s = 0;
+#pragma unroll 8
+      for (int v = 0; v < TM_D; v++) s += Lb[r * TM_D + v] * Fb[v * TM_D + c];
+      acc += s * sFac[buf][u];  // zero past the last split point
+    }
+    if (more) store(buf ^ 1, kb + KC);
+    __syncthreads();
+  }
+  a.Q[tm_cell(n, i, len) + t] = acc;
+  q[t] = acc;
+  // the largest |mantissa| of this length
+  T m = fabs(acc);
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((t & 31) == 0) smx[t >> 5] = m;
+  if (t < BLK) tq[t] = i + len < n ? (T)a.Tr[(size_t)(i + len - 1) * BLK + t] : (T)0;
+  __syncthreads();
+  if (t == 0) {
+    double mm = 0;
+    for (int w = 0; w < TM_NT / 32; w++) mm = fmax(mm, (double)smx[w]);
+    atomic_max_pos(a.dmax + len, mm);
+  }
+  if (i + len < n) {  // L[i, i+len] = Q[i, i+len] (T_{i+len-1} (x) I)
+    T s = 0;
+#pragma unroll
+    for (int b = 0; b < NS; b++) s += q[r * TM_D + b * TM_G + zc] * tq[b * NS + ac];
+    a.L[tm_cell(n, i, len) + t] = s;
+  }
+}
+
+// Z relative to 2^{E[n]}: sum_{a,c} u0[a] Tr_S[Q[0, n]_{a c}], then log Z
+template <typename T>
+__global__ void k_tm_finish(TmArgs<T> a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n = a.n;
+  const T *q = a.Q + tm_cell(n, 0, n);
+  double z = 0;
+  for (int ar = 0; ar < a.Mp[0]; ar++)
+    for (int ac = 0; ac < a.Mp[n - 1]; ac++) {
+      double s = 0;
+      for (int e1 = 0; e1 < TM_G; e1++)
+        for (int e2 = 0; e2 < TM_G; e2++) s += a.mod->S[e2][e1] * (double)q[(ar * TM_G + e1) * TM_D + ac * TM_G + e2];
+      z += a.u0[ar] * s;
+    }
+  *a.Zm = z;
+  double sc = 0;
+  for (int k = 0; k < a.nls; k++) sc += a.ls[k];
+  *a.logz = log(z) + (double)a.E[n] * 0.69314718055994530942 - sc;
+  if (!(z > 0) || !isfinite(*a.logz)) atomicOr(a.err, 2);
+}
+
+}  // namespace cf

@@ -31,6 +31,7 @@
 #include "cf_outside2.cuh"
 #include "cf_sample.cuh"
 #include "cf_window.cuh"
+#include "cf_tm.cuh"
 
 using namespace cf;
 
@@ -134,6 +135,21 @@ struct MfeTables {
   std::vector<void *> allocs;
 };
 
+// Tensor-model tables of one precision (cf_tm.cuh), allocated on the first
+// cf_tm_inside of a protein, with the pass captured as a CUDA graph for the
+// model it was built for.
+template <typename T>
+struct TmTables {
+  T *Q = nullptr, *L = nullptr, *F = nullptr;
+  int *E = nullptr, *err = nullptr;
+  unsigned long long *dmax = nullptr;
+  double *Zm = nullptr, *logz = nullptr;
+  bool alloc = false;
+  cudaGraphExec_t g = nullptr;
+  const void *gmodel = nullptr;  // the model's device copy and rho count the graph was built for
+  int gnrho = 0;
+};
+
 struct cf_problem {
   const cf_model *model = nullptr;
   int device = 0;
@@ -184,6 +200,11 @@ struct cf_problem {
   float t_win = 0;
   MfeTables mfe;
   float t_mfe = 0;
+  // tensor-based model (cf_tm_inside)
+  std::vector<void *> tm_allocs;
+  TmTables<float> tm32;
+  TmTables<double> tm64;
+  float t_tm = 0;
   int ck_request = -1;  // -1: checkpoint the interior partial sums from CF_CHECKPOINT_MIN_N on; 0 never; 1 always
   int batch = 1;        // proteins of a batch (cf_batch_*), one slab each
   long long bstride = 0;  // bytes between the slabs of a batch
@@ -1417,10 +1438,21 @@ cf_status cf_problem_create(const cf_model *model, int device, void *stream, cf_
   return CF_OK;
 }
 
+extern "C++" {
+template <typename T>
+static void free_tm(TmTables<T> &t) {
+  if (t.g) cudaGraphExecDestroy(t.g);
+  t = TmTables<T>();
+}
+}
+
 static void release_protein(cf_problem *p) {
   free_prec(p->f32);
   free_prec(p->f64);
   free_mfe(p->mfe);
+  free_tm(p->tm32);
+  free_tm(p->tm64);
+  free_list(p->tm_allocs);
   free_list(p->shared_allocs);
   free_list(p->smp_allocs);
   p->smp_cap = 0;
@@ -1656,6 +1688,230 @@ cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons
 }
 
 float cf_mfe_last_ms(const cf_problem *p) { return p ? p->t_mfe : 0.f; }
+
+// ------------------------------------------------------------------ tensor-based model
+
+struct cf_tm_model {
+  int device = 0, gamma = 0, nrho = 0;
+  TmModelDev *d = nullptr;
+  double radius[4] = {0, 0, 0, 0};
+};
+
+// Spectral radius by Gelfand's formula r = lim ||A^m||^(1/m) over m = 2^s:
+// repeated squaring of A scaled to unit norm (max row sum of |entries|), the
+// logarithm of the scale carried separately, 48 squarings.
+cf_status cf_tm_spectral_radius(const double *A, int dim, double *radius) {
+  if (!A || !radius || dim < 1 || dim > 64) return fail(nullptr, CF_EINVAL, "cf_tm_spectral_radius: bad argument");
+  std::vector<double> M(A, A + (size_t)dim * dim), P((size_t)dim * dim);
+  for (double v : M)
+    if (!std::isfinite(v)) return fail(nullptr, CF_EINVAL, "cf_tm_spectral_radius: non-finite entry");
+  auto norm = [&](const std::vector<double> &X) {
+    double m = 0;
+    for (int i = 0; i < dim; i++) {
+      double s = 0;
+      for (int j = 0; j < dim; j++) s += std::fabs(X[(size_t)i * dim + j]);
+      m = std::max(m, s);
+    }
+    return m;
+  };
+  double nrm = norm(M);
+  if (nrm == 0) {
+    *radius = 0;
+    return CF_OK;
+  }
+  for (double &v : M) v /= nrm;
+  double logc = std::log(nrm);  // log of ||A^(2^s)|| as (scale) * ||M|| with ||M|| = 1
+  double m = 1;                 // 2^s
+  for (int s = 0; s < 48; s++) {
+    for (int i = 0; i < dim; i++)
+      for (int j = 0; j < dim; j++) {
+        double acc = 0;
+        for (int k = 0; k < dim; k++) acc += M[(size_t)i * dim + k] * M[(size_t)k * dim + j];
+        P[(size_t)i * dim + j] = acc;
+      }
+    const double np = norm(P);
+    if (np == 0) {
+      *radius = 0;
+      return CF_OK;
+    }
+    for (size_t q = 0; q < P.size(); q++) M[q] = P[q] / np;
+    logc = 2 * logc + std::log(np);
+    m *= 2;
+  }
+  *radius = std::exp(logc / m);
+  return CF_OK;
+}
+
+cf_status cf_tm_model_create(int device, int gamma, int nrho, const double *V, const double *B, const double *S,
+                             int normalize, cf_tm_model **out) {
+  if (!out || !V || !B || !S || gamma < 1 || gamma > TM_G || nrho < 1 || nrho > TM_R)
+    return fail(nullptr, CF_EINVAL, "cf_tm_model_create: bad argument (1 <= gamma <= 4, 1 <= nrho <= 4)");
+  *out = nullptr;
+  const size_t g2 = (size_t)gamma * gamma;
+  for (size_t q = 0; q < 4 * g2; q++)
+    if (!std::isfinite(V[q])) return fail(nullptr, CF_EINVAL, "cf_tm_model_create: non-finite V");
+  for (size_t q = 0; q < (size_t)nrho * 16 * g2; q++)
+    if (!std::isfinite(B[q])) return fail(nullptr, CF_EINVAL, "cf_tm_model_create: non-finite B");
+  for (size_t q = 0; q < g2; q++)
+    if (!std::isfinite(S[q])) return fail(nullptr, CF_EINVAL, "cf_tm_model_create: non-finite S");
+  cf_tm_model *m = new (std::nothrow) cf_tm_model;
+  if (!m) return fail(nullptr, CF_ENOMEM, "cf_tm_model_create: host memory");
+  m->device = device;
+  m->gamma = gamma;
+  m->nrho = nrho;
+  double r[4] = {1, 1, 1, 1};
+  if (normalize)
+    for (int x = 0; x < 4; x++) {
+      cf_status st = cf_tm_spectral_radius(V + x * g2, gamma, &r[x]);
+      if (st != CF_OK || !(r[x] > 0)) {
+        delete m;
+        return fail(nullptr, CF_EINVAL, "cf_tm_model_create: an unpaired matrix has spectral radius 0");
+      }
+    }
+  for (int x = 0; x < 4; x++) m->radius[x] = r[x];
+  // padded to TM_G with zeros; V / r_x and B / sqrt(r_x r_y) when normalising
+  TmModelDev h;
+  std::memset(&h, 0, sizeof(h));
+  for (int x = 0; x < 4; x++)
+    for (int a = 0; a < gamma; a++)
+      for (int b = 0; b < gamma; b++) h.V[x][a][b] = V[x * g2 + a * gamma + b] / r[x];
+  for (int a = 0; a < gamma; a++)
+    for (int b = 0; b < gamma; b++) h.S[a][b] = S[a * gamma + b];
+  for (int k = 0; k < nrho; k++)
+    for (int x = 0; x < 4; x++)
+      for (int y = 0; y < 4; y++) {
+        const double sc = 1.0 / std::sqrt(r[x] * r[y]);
+        for (int a = 0; a < gamma; a++)
+          for (int b = 0; b < gamma; b++)
+            h.B[k][x][y][a][b] = B[(((size_t)k * 4 + x) * 4 + y) * g2 + a * gamma + b] * sc;
+        for (int a = 0; a < gamma; a++)
+          for (int b = 0; b < gamma; b++) {
+            double s = 0;
+            for (int c = 0; c < gamma; c++) s += h.S[a][c] * h.B[k][x][y][c][b];
+            h.SB[k][x][y][a][b] = s;
+          }
+      }
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d, sizeof(TmModelDev));
+  if (e == cudaSuccess) e = cudaMemcpy(m->d, &h, sizeof(TmModelDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->d) cudaFree(m->d);
+    delete m;
+    return cuda_fail(nullptr, e, "cf_tm_model_create");
+  }
+  *out = m;
+  return CF_OK;
+}
+
+cf_status cf_tm_model_radius(const cf_tm_model *m, double *radius4) {
+  if (!m || !radius4) return fail(nullptr, CF_EINVAL, "cf_tm_model_radius: NULL argument");
+  for (int x = 0; x < 4; x++) radius4[x] = m->radius[x];
+  return CF_OK;
+}
+
+cf_status cf_tm_model_free(cf_tm_model *m) {
+  if (!m) return CF_OK;
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  if (m->d) cudaFree(m->d);
+  delete m;
+  return CF_OK;
+}
+
+extern "C++" {
+template <typename T>
+static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, double *logZ) {
+  const int n = p->n;
+  cudaStream_t st = p->stream;
+  if (!t.alloc) {
+    const size_t cells = ncells(n) * TM_BLK;
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.Q, cells));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.L, cells));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.F, cells));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.E, (size_t)n + 1));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.dmax, (size_t)n + 1));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.err, (size_t)1));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.Zm, (size_t)1));
+    CF_CUDA(p, dalloc(p->tm_allocs, &t.logz, (size_t)1));
+    CF_CUDA(p, cudaMemsetAsync(t.F, 0, cells * sizeof(T), st));  // pairs closer than 4 are never written
+    t.alloc = true;
+  }
+  if (!t.g || t.gmodel != (const void *)mod->d || t.gnrho != mod->nrho) {
+    if (t.g) {
+      cudaGraphExecDestroy(t.g);
+      t.g = nullptr;
+    }
+    TmArgs<T> a;
+    a.n = n;
+    a.nrho = mod->nrho;
+    a.Mp = p->dM;
+    a.base = p->dbase;
+    a.Tr = p->dTr64;
+    a.u0 = p->du0;
+    a.ls = p->dls;
+    a.nls = p->m - 1;
+    a.mod = mod->d;
+    a.Q = t.Q;
+    a.L = t.L;
+    a.F = t.F;
+    a.E = t.E;
+    a.dmax = t.dmax;
+    a.Zm = t.Zm;
+    a.logz = t.logz;
+    a.err = t.err;
+    // captured on a private stream (the problem's may be the legacy default
+    // stream, which cannot be captured); the graph runs on the problem's
+    cudaStream_t cs = nullptr;
+    CF_CUDA(p, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaMemsetAsync(t.E, 0, sizeof(int) * (n + 1), cs);
+      cudaMemsetAsync(t.dmax, 0, sizeof(unsigned long long) * (n + 1), cs);
+      cudaMemsetAsync(t.err, 0, sizeof(int), cs);
+      k_tm_init<T><<<n, TM_NT, 0, cs>>>(a);
+      for (int len = 2; len <= n; len++) {
+        if (len - 1 >= 4) k_tm_fold<T><<<n - (len - 1), TM_NT, 0, cs>>>(a, len);
+        k_tm_cell<T><<<n - len + 1, TM_NT, 0, cs>>>(a, len);
+      }
+      k_tm_finish<T><<<1, 32, 0, cs>>>(a);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&t.g, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cf_tm_inside: graph");
+    t.gmodel = mod->d;
+    t.gnrho = mod->nrho;
+  }
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  CF_CUDA(p, cudaGraphLaunch(t.g, st));
+  CF_CUDA(p, cudaEventRecord(p->ev[1], st));
+  double lz = 0;
+  int err = 0;
+  CF_CUDA(p, cudaMemcpyAsync(&lz, t.logz, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaMemcpyAsync(&err, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(p, cudaStreamSynchronize(st));
+  CF_CUDA(p, cudaEventElapsedTime(&p->t_tm, p->ev[0], p->ev[1]));
+  if (err || !std::isfinite(lz))
+    return fail(p, CF_ENUMERIC, "cf_tm_inside: non-finite or zero partition function (try CF_FP64)");
+  *logZ = lz;
+  return CF_OK;
+}
+
+}  // extern "C++"
+
+cf_status cf_tm_inside(cf_problem *p, const cf_tm_model *mod, cf_precision prec, double *logZ) {
+  if (!p || !mod || !logZ) return fail(p, CF_EINVAL, "cf_tm_inside: NULL argument");
+  if (prec != CF_FP64 && prec != CF_FP32_SCALED) return fail(p, CF_EINVAL, "cf_tm_inside: unknown precision");
+  if (mod->device != p->device) return fail(p, CF_EINVAL, "cf_tm_inside: model and problem on different devices");
+  if (p->n == 0) return fail(p, CF_ESTATE, "cf_tm_inside: no protein set");
+  if (p->batch > 1) return fail(p, CF_EINVAL, "cf_tm_inside: not available on a batch");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  return prec == CF_FP64 ? tm_run(p, mod, p->tm64, logZ) : tm_run(p, mod, p->tm32, logZ);
+}
+
+float cf_tm_last_ms(const cf_problem *p) { return p ? p->t_tm : 0.f; }
 
 cf_status cf_set_checkpoint(cf_problem *p, int mode) {
   if (!p || mode < -1 || mode > 1) return fail(p, CF_EINVAL, "cf_set_checkpoint: bad argument");

@@ -187,3 +187,24 @@ def surrogate_init(seed: int = 0) -> np.ndarray:
 def ascent_targets(m: int, seed: int = 3) -> np.ndarray:
     """Independent N(0,1) logits per (residue, slot) for frequency targets."""
     return np.random.default_rng(seed).normal(0.0, 1.0, (m, 6))
+
+
+# canonical and wobble pairs (A, C, G, U = 0..3): AU, CG, GC, UA, GU, UG
+_PAIRS = ((0, 3), (1, 2), (2, 1), (3, 0), (2, 3), (3, 2))
+
+
+def tm_params(seed: int = 0, gamma: int = 4, nrho: int = 2, pair_scale: float = 2.0):
+    """A synthetic tensor-based model (the paper's trained tensors are not
+    available): V[4][g][g] ~ U(0.2, 1.0); B[rho][x][y][g][g] ~ pair_scale *
+    U(0, 1) for the six canonical and wobble pairs (x, y), zero for every
+    other base pair; S[g][g] ~ U(0.1, 1.0); drawn in that order from
+    default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    V = rng.uniform(0.2, 1.0, (4, gamma, gamma))
+    Braw = pair_scale * rng.uniform(0.0, 1.0, (nrho, 4, 4, gamma, gamma))
+    mask = np.zeros((4, 4))
+    for x, y in _PAIRS:
+        mask[x, y] = 1.0
+    B = Braw * mask[None, :, :, None, None]
+    S = rng.uniform(0.1, 1.0, (gamma, gamma))
+    return V, B, S

@@ -37,7 +37,6 @@ constexpr int TM_R = 4;             // largest number of pair conformations rho
 constexpr int TM_D = NS * TM_G;     // padded block side (state, zeta)
 constexpr int TM_BLK = TM_D * TM_D;  // 576 entries per block
 constexpr int TM_NT = TM_BLK;       // threads of the cell and fold kernels: one per block entry
-constexpr int TM_KC = 4;            // split points staged per step of the cell kernel (binary32; 2 in binary64)
 
 // model on the device (binary64): V[x][g][g], B[rho][x][y][g][g], SB = S B, S[g][g]
 struct TmModelDev {
@@ -141,17 +140,73 @@ __global__ void __launch_bounds__(TM_NT) k_tm_fold(TmArgs<T> a, int len) {
   a.F[cidx(n, k, j) * TM_BLK + t] = f;
 }
 
-// the cells of length len >= 2; one CTA per cell i
+// four consecutive values (16-byte aligned) to and from registers
 template <typename T>
-__global__ void __launch_bounds__(TM_NT) k_tm_cell(TmArgs<T> a, int len) {
+__device__ __forceinline__ void ld4(T (&v)[4], const T *p);
+template <>
+__device__ __forceinline__ void ld4<float>(float (&v)[4], const float *p) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(double (&v)[4], const double *p) {
+  const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+  v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+template <typename T>
+__device__ __forceinline__ void ldcg4(T (&v)[4], const T *p);
+template <>
+__device__ __forceinline__ void ldcg4<float>(float (&v)[4], const float *p) {
+  const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+  v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ldcg4<double>(double (&v)[4], const double *p) {
+  const double2 q0 = __ldcg(reinterpret_cast<const double2 *>(p)), q1 = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+  v[0] = q0.x, v[1] = q0.y, v[2] = q1.x, v[3] = q1.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, const float (&v)[4]) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// The cells of length len >= 2; one CTA per cell i.  Thread t owns output
+// row r = t / 6 (state at i, zeta) and the four columns of the codon state
+// qs = t % 6 at j (its four zeta'), so that a block product reads 16-byte
+// rows: per state b of the summation index, one 4-vector of the left block
+// and four of the right block give 16 FMAs; the summation runs over the real
+// states of the split point only.  The split points are staged tm_kc at a
+// time through two buffers of dynamic shared memory.
+constexpr int TM_NC = TM_D * NS;  // 144 threads
+template <typename T>
+__host__ __device__ constexpr int tm_kc() {
+  return sizeof(T) == sizeof(float) ? 4 : 2;  // 8 was slower at 900 nt (125 registers)
+}
+template <typename T>
+__host__ __device__ constexpr size_t tm_cell_smem() {
+  return (size_t)2 * 2 * tm_kc<T>() * TM_BLK * sizeof(T);
+}
+template <typename T>
+__global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len) {
   const int n = a.n, i = blockIdx.x, t = threadIdx.x;
   const int j = i + len - 1;  // the new last base
-  const int r = t / TM_D, c = t % TM_D, ac = c / TM_G, zc = c % TM_G;
-  constexpr int KC = sizeof(T) == sizeof(float) ? TM_KC : 2;  // within 48 KB of static shared memory
-  __shared__ T sL[2][KC][TM_BLK], sF[2][KC][TM_BLK];
-  __shared__ T q[TM_BLK], x[TM_BLK], tq[BLK];
-  __shared__ int sEL;
-  __shared__ T smx[TM_NT / 32];
+  const int r = t / NS, qs = t % NS;
+  constexpr int KC = tm_kc<T>();
+  extern __shared__ __align__(16) unsigned char tm_smem[];  // [2][KC] blocks of L, then of F
+  T(*sL)[KC][TM_BLK] = reinterpret_cast<T(*)[KC][TM_BLK]>(tm_smem);
+  T(*sF)[KC][TM_BLK] = reinterpret_cast<T(*)[KC][TM_BLK]>(tm_smem + (size_t)2 * KC * TM_BLK * sizeof(T));
+  __shared__ __align__(16) T q[TM_BLK];
+  __shared__ __align__(16) T x[TM_BLK];
+  __shared__ T tq[BLK], sFac[2][KC];
+  __shared__ int sEL, sMk[2][KC];
+  __shared__ T smx[(TM_NC + 31) / 32];
   // this length's exponent from the largest mantissa of length len - 1
   if (t == 0) {
     const double mx = __longlong_as_double((long long)__ldcg(a.dmax + len - 1));
@@ -163,48 +218,75 @@ __global__ void __launch_bounds__(TM_NT) k_tm_cell(TmArgs<T> a, int len) {
     sEL = e;
     if (i == 0) a.E[len] = e;
   }
-  // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1)
+  // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1), four entries per thread
+  const int Mj1 = a.Mp[j - 1], Mj = a.Mp[j];
   {
-    const int br = r / TM_G, zr = r % TM_G;
-    T xv = 0;
-    if (ac < a.Mp[j]) xv = (T)a.Tr[(size_t)(j - 1) * BLK + br * NS + ac] * (T)a.mod->V[a.base[j * NS + ac]][zr][zc];
-    x[t] = xv;
-    q[t] = a.Q[tm_cell(n, i, len - 1) + t];
+    T v4[4];
+#pragma unroll
+    for (int z = 0; z < 4; z++) {
+      const int e = 4 * t + z, u = e / TM_D, c = e % TM_D, br = u / TM_G, zr = u % TM_G, ac = c / TM_G, zc = c % TM_G;
+      v4[z] = ac < Mj ? (T)a.Tr[(size_t)(j - 1) * BLK + br * NS + ac] * (T)a.mod->V[a.base[j * NS + ac]][zr][zc]
+                      : (T)0;
+    }
+    st4(x + 4 * t, v4);
+    ldcg4(v4, a.Q + tm_cell(n, i, len - 1) + 4 * t);
+    st4(q + 4 * t, v4);
   }
   __syncthreads();
   const int EL = sEL;
-  T acc = 0;
+  T acc[4] = {0, 0, 0, 0};
   {
-    T s = 0;
-#pragma unroll 8
-    for (int u = 0; u < TM_D; u++) s += q[r * TM_D + u] * x[u * TM_D + c];
-    acc = s * clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
+    for (int b = 0; b < Mj1; b++) {  // states at j - 1
+      T l4[4];
+      ld4(l4, q + r * TM_D + 4 * b);
+#pragma unroll
+      for (int z1 = 0; z1 < 4; z1++) {
+        T f4[4];
+        ld4(f4, x + (4 * b + z1) * TM_D + 4 * qs);
+#pragma unroll
+        for (int z = 0; z < 4; z++) acc[z] = fma(l4[z1], f4[z], acc[z]);
+      }
+    }
+    const T f = clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
+#pragma unroll
+    for (int z = 0; z < 4; z++) acc[z] *= f;
   }
   // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
-  if (j - i >= 4) acc += a.F[cidx(n, i, j) * TM_BLK + t] * clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
+  if (j - i >= 4) {
+    T f4[4];
+    ldcg4(f4, a.F + cidx(n, i, j) * TM_BLK + r * TM_D + 4 * qs);
+    const T f = clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
+#pragma unroll
+    for (int z = 0; z < 4; z++) acc[z] = fma(f4[z], f, acc[z]);
+  }
   // k = i+1 .. j-4: L[i, k] F[k, j], KC split points per step; the next
   // step's blocks are loaded into registers before this step's products and
   // stored to the other buffer after them
   const int k0 = i + 1, k1 = j - 4;
-  __shared__ T sFac[2][KC];
-  T nl[KC], nf[KC];
+  T nl[KC][4], nf[KC][4];
   auto load = [&](int kb) {
 #pragma unroll
     for (int u = 0; u < KC; u++) {
       const int k = kb + u;
-      nl[u] = k <= k1 ? __ldcg(a.L + tm_cell(n, i, k - i) + t) : (T)0;
-      nf[u] = k <= k1 ? __ldcg(a.F + cidx(n, k, j) * TM_BLK + t) : (T)0;
+      if (k <= k1) {
+        ldcg4(nl[u], a.L + tm_cell(n, i, k - i) + 4 * t);
+        ldcg4(nf[u], a.F + cidx(n, k, j) * TM_BLK + 4 * t);
+      } else {
+#pragma unroll
+        for (int z = 0; z < 4; z++) nl[u][z] = nf[u][z] = (T)0;
+      }
     }
   };
   auto store = [&](int buf, int kb) {
 #pragma unroll
     for (int u = 0; u < KC; u++) {
-      sL[buf][u][t] = nl[u];
-      sF[buf][u][t] = nf[u];
+      st4(&sL[buf][u][4 * t], nl[u]);
+      st4(&sF[buf][u][4 * t], nf[u]);
     }
-    if (t < KC) {  // the split point's factor 2^{E[k-i] + E[j-k-1] - E[len]}
+    if (t < KC) {  // the split point's factor 2^{E[k-i] + E[j-k-1] - E[len]} and state count
       const int k = kb + t;
       sFac[buf][t] = k <= k1 ? clamp_p2<T>(__ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) - EL) : (T)0;
+      sMk[buf][t] = k <= k1 ? a.Mp[k] : 0;
     }
   };
   if (k0 <= k1) {
@@ -219,32 +301,49 @@ __global__ void __launch_bounds__(TM_NT) k_tm_cell(TmArgs<T> a, int len) {
 #pragma unroll
     for (int u = 0; u < KC; u++) {
       const T *Lb = sL[buf][u], *Fb = sF[buf][u];
-      T s = 0;
-#pragma unroll 8
-      for (int v = 0; v < TM_D; v++) s += Lb[r * TM_D + v] * Fb[v * TM_D + c];
-      acc += s * sFac[buf][u];  // zero past the last split point
+      const int Mk = sMk[buf][u];
+      T s[4] = {0, 0, 0, 0};
+      for (int b = 0; b < Mk; b++) {
+        T l4[4];
+        ld4(l4, Lb + r * TM_D + 4 * b);
+#pragma unroll
+        for (int z1 = 0; z1 < 4; z1++) {
+          T f4[4];
+          ld4(f4, Fb + (4 * b + z1) * TM_D + 4 * qs);
+#pragma unroll
+          for (int z = 0; z < 4; z++) s[z] = fma(l4[z1], f4[z], s[z]);
+        }
+      }
+      const T f = sFac[buf][u];
+#pragma unroll
+      for (int z = 0; z < 4; z++) acc[z] = fma(s[z], f, acc[z]);
     }
     if (more) store(buf ^ 1, kb + KC);
     __syncthreads();
   }
-  a.Q[tm_cell(n, i, len) + t] = acc;
-  q[t] = acc;
+  st4(a.Q + tm_cell(n, i, len) + r * TM_D + 4 * qs, acc);
+  st4(q + r * TM_D + 4 * qs, acc);
   // the largest |mantissa| of this length
-  T m = fabs(acc);
+  T m = fmax(fmax(fabs(acc[0]), fabs(acc[1])), fmax(fabs(acc[2]), fabs(acc[3])));
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((t & 31) == 0) smx[t >> 5] = m;
   if (t < BLK) tq[t] = i + len < n ? (T)a.Tr[(size_t)(i + len - 1) * BLK + t] : (T)0;
   __syncthreads();
   if (t == 0) {
     double mm = 0;
-    for (int w = 0; w < TM_NT / 32; w++) mm = fmax(mm, (double)smx[w]);
+    for (int w = 0; w < (TM_NC + 31) / 32; w++) mm = fmax(mm, (double)smx[w]);
     atomic_max_pos(a.dmax + len, mm);
   }
-  if (i + len < n) {  // L[i, i+len] = Q[i, i+len] (T_{i+len-1} (x) I)
-    T s = 0;
+  if (i + len < n) {  // L[i, i+len] = Q[i, i+len] (T_{i+len-1} (x) I): column state qs at i + len
+    T l4[4] = {0, 0, 0, 0};
+    for (int b = 0; b < Mj; b++) {
+      const T tb = tq[b * NS + qs];
+      T q4[4];
+      ld4(q4, q + r * TM_D + 4 * b);
 #pragma unroll
-    for (int b = 0; b < NS; b++) s += q[r * TM_D + b * TM_G + zc] * tq[b * NS + ac];
-    a.L[tm_cell(n, i, len) + t] = s;
+      for (int z = 0; z < 4; z++) l4[z] = fma(q4[z], tb, l4[z]);
+    }
+    st4(a.L + tm_cell(n, i, len) + r * TM_D + 4 * qs, l4);
   }
 }
 

@@ -1859,6 +1859,8 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
     a.Zm = t.Zm;
     a.logz = t.logz;
     a.err = t.err;
+    CF_CUDA(p, cudaFuncSetAttribute((const void *)k_tm_cell<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tm_cell_smem<T>()));
     // captured on a private stream (the problem's may be the legacy default
     // stream, which cannot be captured); the graph runs on the problem's
     cudaStream_t cs = nullptr;
@@ -1872,7 +1874,7 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
       k_tm_init<T><<<n, TM_NT, 0, cs>>>(a);
       for (int len = 2; len <= n; len++) {
         if (len - 1 >= 4) k_tm_fold<T><<<n - (len - 1), TM_NT, 0, cs>>>(a, len);
-        k_tm_cell<T><<<n - len + 1, TM_NT, 0, cs>>>(a, len);
+        k_tm_cell<T><<<n - len + 1, TM_NC, tm_cell_smem<T>(), cs>>>(a, len);
       }
       k_tm_finish<T><<<1, 32, 0, cs>>>(a);
       e = cudaStreamEndCapture(cs, &g);

@@ -546,6 +546,37 @@ def bench_tm(stream):
     return out
 
 
+def bench_layout(stream, steps=10):
+    """The 900-nt step (binary32 inside + outside) in the single-codon layout
+    (paper Eq. single-tt; the workload has no codon-pair bonuses), against
+    the codon-state layout on the same GPU."""
+    import torch
+
+    import paper_2604_19718_b300 as cf
+    res, lw, pb = synth.workload(WORKLOAD)
+    out = {}
+    for layout, key in ((0, "codon_states"), (1, "single_codon")):
+        f = cf.CodonFold(synth.nn_params(0), stream=stream)
+        cf.cf_set_layout(f.prob, layout)
+        f.set_protein(res, lw, pb)
+        for _ in range(3):
+            lz = f.inside(cf.CF_FP32_SCALED)
+            f.outside(False, True, False)
+        tin = tout = 0.0
+        for _ in range(steps):
+            lz = f.inside(cf.CF_FP32_SCALED)
+            f.outside(False, True, False)
+            a, b, _, _ = f.timing()
+            tin, tout = tin + a, tout + b
+        _, st = cf.cf_layout_states(f.prob, f.n)
+        f.close()
+        out[key] = {"inside_ms": tin / steps, "outside_ms": tout / steps, "ms_per_step": (tin + tout) / steps,
+                    "mean_states_per_position": float(np.mean(st)), "logZ": lz}
+    torch.cuda.synchronize()
+    out["speedup"] = out["codon_states"]["ms_per_step"] / out["single_codon"]["ms_per_step"]
+    return out
+
+
 def bench_large(stream, nsamples=10_000):
     """The 1000-aa / 3000-nt soft-weighted protein in binary32."""
     import paper_2604_19718_b300 as cf
@@ -758,6 +789,7 @@ def main():
         forms["frequency_matching"] = bench_frequency(stream.cuda_stream)
         forms["mfe"] = bench_mfe(stream.cuda_stream)
         forms["tensor_model"] = bench_tm(stream.cuda_stream)
+        forms["single_codon_layout"] = bench_layout(stream.cuda_stream)
 
     if rank != 0:
         return

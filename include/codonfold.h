@@ -188,6 +188,27 @@ cf_status cf_mfe(cf_problem *prob, int64_t *cost, double *mfe_kcal, int32_t *cod
 float cf_mfe_last_ms(const cf_problem *prob);
 
 /*
+ * Position-state layout (paper Eq. single-tt, Section "Incorporating hard
+ * constraints"): 0 (default) codon states, the codon-pair tensor train of
+ * Eq. pair-tt (every position of a residue carries the residue's codon);
+ * 1 the single-codon tensor train: the first position of a residue carries
+ * its distinct first bases, the second its distinct (second, third) base
+ * pairs, the third its distinct third bases, and the codon (with its
+ * weight lw) is fixed by the transfer from the first position to the
+ * second.  Layout 1 has fewer states per position (2.15 against 2.84 on a
+ * Dirichlet(1) composition) and the same log Z, pair probabilities, codon
+ * and base marginals; it has no codon-pair bonuses (cf_set_protein and
+ * cf_set_weights reject pair_bonus != NULL, cf_outside a pair_grad output),
+ * and cf_sample, cf_sample_noalloc and cf_mfe return CF_EINVAL in it.
+ * cf_set_layout takes effect at the next cf_set_protein; a batch keeps
+ * layout 0.  cf_layout_states reports the current protein's layout and, if
+ * states != NULL, its n per-position state counts.
+ * Errors: CF_EINVAL (NULL problem, unknown layout, layout 1 on a batch).
+ */
+cf_status cf_set_layout(cf_problem *prob, int layout);
+cf_status cf_layout_states(const cf_problem *prob, int *layout, int *states);
+
+/*
  * The paper's own tensor-based free energy model (SI "Tensor-based free
  * energy models", Eq. general-model) under the codon constraints of the
  * problem's protein: gamma x gamma matrices V_x for an unpaired base x

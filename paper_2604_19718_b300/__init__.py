@@ -88,6 +88,10 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = ctypes.c_int
     lib.cf_mfe_last_ms.argtypes = [vp]
     lib.cf_mfe_last_ms.restype = ctypes.c_float
+    lib.cf_set_layout.argtypes = [vp, ctypes.c_int]
+    lib.cf_layout_states.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+    lib.cf_set_layout.restype = ctypes.c_int
+    lib.cf_layout_states.restype = ctypes.c_int
     lib.cf_tm_spectral_radius.argtypes = [dp, ctypes.c_int, dp]
     lib.cf_tm_model_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int,
                                        ctypes.POINTER(vp)]
@@ -273,6 +277,20 @@ def cf_checkpointed(prob) -> bool:
 
 def cf_mfe_last_ms(prob) -> float:
     return float(lib.cf_mfe_last_ms(prob))
+
+
+def cf_set_layout(prob, layout: int) -> None:
+    """0 codon states (default), 1 the single-codon layout; takes effect at
+    the next cf_set_protein."""
+    _check(lib.cf_set_layout(prob, int(layout)), prob)
+
+
+def cf_layout_states(prob, n: int):
+    """(layout of the current protein, per-position state counts)."""
+    lay = ctypes.c_int()
+    st = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib.cf_layout_states(prob, ctypes.byref(lay), ctypes.c_void_p(st.ctypes.data)), prob)
+    return lay.value, st[:n]
 
 
 def _dbl(a):

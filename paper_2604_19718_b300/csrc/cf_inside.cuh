@@ -126,6 +126,32 @@ __global__ void k_transfers(int n, const int *Mp, const int *base, const int *ci
     }
 }
 
+// Typed transitions of given position transfers T (binary64, [n][36]), as in
+// k_transfers: X_UU = T, X_UP = T d5[b][a], X_PU = T d3[a][b], X_PP = T d3 d5
+// with the bases of states a at q and b at q+1; one thread per position
+// (the single-codon layout, whose transfers the host builds).
+__global__ void k_typed_x(int n, const int *Mp, const int *base, const double *en, const double *Tr, double *X) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int Ma = Mp[q], Mb = q + 1 < n ? Mp[q + 1] : 0;
+  const double *tq = Tr + (size_t)q * BLK;
+  double *xq = X + (size_t)q * 4 * BLK;
+  for (int a = 0; a < NS; a++)
+    for (int b = 0; b < NS; b++) {
+      const int e = a * NS + b;
+      double d3 = 0, d5 = 0;
+      if (a < Ma && b < Mb) {
+        const int x0 = base[(size_t)q * NS + a], y0 = base[(size_t)(q + 1) * NS + b];
+        d3 = en[EN_D3 + x0 * 4 + y0];
+        d5 = en[EN_D5 + y0 * 4 + x0];
+      }
+      xq[XUU * BLK + e] = tq[e];
+      xq[XUP * BLK + e] = tq[e] * d5;
+      xq[XPU * BLK + e] = tq[e] * d3;
+      xq[XPP * BLK + e] = tq[e] * d3 * d5;
+    }
+}
+
 // Copy of a binary64 table in the precision of a pass (batch: blockIdx.y).
 template <typename T>
 __global__ void k_cast(const double *src, T *dst, size_t cnt, long long bstride = 0) {

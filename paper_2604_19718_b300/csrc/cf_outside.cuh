@@ -129,6 +129,45 @@ __global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, cons
   if (lane == 0) pg[u] = s;
 }
 
+// Codon and base marginals in the single-codon layout (Eq. single-tt): the
+// codon of residue r is fixed by the transfer from its first position (state
+// = first base) to its second (state = second and third base), which also
+// carries the codon's weight, so its marginal is T o (hT + sum_k hX_k o
+// dangle_k) at q = 3r for the codon's state pair.  smap[r][s] packs, for
+// codon slot s, the two states (bits 0-3, 4-7) and the three bases (bits
+// 8-9, 10-11, 12-13); -1 past the residue's codons.  One thread per codon
+// slot, then one per (position, base).
+template <typename T>
+__device__ __forceinline__ double sc_codon_marg(const DP<T> &p, int r, int sm) {
+  const int q = 3 * r, a = sm & 15, b = (sm >> 4) & 15;
+  const int x0 = p.base[q * NS + a], y0 = p.base[(q + 1) * NS + b];
+  const double d3 = (double)p.en[EN_D3 + x0 * 4 + y0], d5 = (double)p.en[EN_D5 + y0 * 4 + x0];
+  double g = p.hT[(size_t)q * BLK + a * NS + b];
+  const double *hx = p.hX + (size_t)q * 4 * BLK + a * NS + b;
+  g += hx[XUU * BLK] + hx[XUP * BLK] * d5 + hx[XPU * BLK] * d3 + hx[XPP * BLK] * d3 * d5;
+  return (double)p.Tr[(size_t)q * BLK + a * NS + b] * g;
+}
+template <typename T>
+__global__ void k_codon_out_sc(DP<T> p, const int *smap, double *cm, double *bm) {
+  const int n = p.n, m = p.m, t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 6 * m) {
+    const int sm = smap[t];
+    const double v = sm >= 0 ? sc_codon_marg(p, t / 6, sm) : 0.0;
+    if (!isfinite(v)) atomicOr(p.err, ERR_OUT_NONFINITE);
+    cm[t] = v;
+    return;
+  }
+  const int u = t - 6 * m;
+  if (u >= n) return;
+  const int r = u / 3, off = u % 3;
+  double acc[4] = {0, 0, 0, 0};
+  for (int s = 0; s < 6; s++) {
+    const int sm = smap[r * 6 + s];
+    if (sm >= 0) acc[(sm >> (8 + 2 * off)) & 3] += sc_codon_marg(p, r, sm);
+  }
+  for (int b = 0; b < 4; b++) bm[(size_t)u * 4 + b] = acc[b];
+}
+
 // Unpaired probability of every base: 1 - sum of its pair probabilities; a
 // row with a non-finite entry raises ERR_OUT_NONFINITE.
 __global__ void k_unpaired(float *P, int n, int *err, long long bstride = 0) {

@@ -200,6 +200,13 @@ struct cf_problem {
   float t_win = 0;
   MfeTables mfe;
   float t_mfe = 0;
+  // position-state layout: 0 codon states (codon-pair tensor train), 1 the
+  // single-codon layout (first base; second and third base; third base)
+  int layout_req = 0, layout = 0;
+  std::vector<int> smap;   // single-codon layout: [m][6] packed states and bases of each codon slot
+  std::vector<int> sc3;    // single-codon layout: third base of each state at a residue's second position
+  int *dsmap = nullptr;
+  int nls = 0;             // per-transfer log rescales undone in log Z
   // tensor-based model (cf_tm_inside)
   std::vector<void *> tm_allocs;
   TmTables<float> tm32;
@@ -836,7 +843,18 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     nodes++;
   }
   cudaGraphNode_t fin = nullptr;
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && p->layout == 1) {  // single-codon layout: codon and base marginals at q = 3r
+    const int *smap = p->dsmap;
+    double *cm = p->dcm, *bm = p->dbm;
+    void *args[] = {&dp, &smap, &cm, &bm};
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_codon_out_sc<T>;
+    kp.gridDim = dim3((p->m * 6 + n + 127) / 128);
+    kp.blockDim = dim3(128);
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(&fin, g, &ktg, 1, &kp);
+    nodes++;
+  } else if (e == cudaSuccess) {
     double *trans = p->dtrans, *p0 = p->dp0;
     void *args[] = {&dp, &trans, &p0};
     cudaKernelNodeParams kp = {};
@@ -862,7 +880,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     e = cudaGraphAddKernelNode(&un, g, &fin, 1, &kp);
     nodes++;
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && p->layout == 0) {
     const double *trans = p->dtrans, *p0 = p->dp0;
     const int *cid = p->dcid;
     double *cm = p->dcm, *bm = p->dbm, *pg = p->dpg;
@@ -906,7 +924,7 @@ cf_status run_inside(cf_problem *p, PrecTables<T> &t, double *logZ) {
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   CF_CUDA(p, cudaGraphLaunch(t.gin, st));
   int launches = t.gin_nodes;
-  k_logz<<<dim3(1, p->batch), 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, p->m - 1, p->dlogz,
+  k_logz<<<dim3(1, p->batch), 32, 0, st>>>(p->dZm, p->dE + (n - 1), p->dls, p->nls, p->dlogz,
                                            p->batch > 1 ? p->bstride : 0);
   launches++;
   CF_CUDA(p, cudaGetLastError());
@@ -1022,6 +1040,46 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
 cf_status device_transfers(cf_problem *p, const double *lw, const double *pb) {
   const int n = p->n, m = p->m;
   cudaStream_t st = p->stream;
+  if (p->layout == 1) {
+    // single-codon layout: T_{3r}[a][b] = s_r e^{lw[r][codon]} for the codon
+    // whose first base is state a at 3r and whose second and third bases are
+    // state b at 3r+1 (s_r makes the average row sum one; exact, undone in
+    // log Z), T_{3r+1}[b][c] = 1 where state b's third base is state c's base
+    // at 3r+2, T_{3r+2} = 1 into every state of the next residue; u0 = 1
+    std::vector<double> T((size_t)n * BLK, 0.0), u0(NS, 0.0), ls((size_t)std::max(m, 1), 0.0);
+    for (int r = 0; r < m; r++) {
+      const int q = 3 * r;
+      double sum = 0;
+      for (int s2 = 0; s2 < 6; s2++) {
+        const int sm = p->smap[(size_t)r * 6 + s2];
+        if (sm < 0) continue;
+        const double w = std::exp(lw ? lw[(size_t)r * 6 + s2] : 0.0);
+        T[(size_t)q * BLK + (sm & 15) * NS + ((sm >> 4) & 15)] = w;
+        sum += w;
+      }
+      const double sr = p->M[q] / sum;
+      for (int e = 0; e < BLK; e++) T[(size_t)q * BLK + e] *= sr;
+      ls[r] = std::log(sr);
+      for (int b2 = 0; b2 < p->M[q + 1]; b2++)
+        for (int c = 0; c < p->M[q + 2]; c++)
+          if (p->sc3[(size_t)(q + 1) * NS + b2] == p->base[(size_t)(q + 2) * NS + c]) T[(size_t)(q + 1) * BLK + b2 * NS + c] = 1.0;
+      if (r + 1 < m)
+        for (int c = 0; c < p->M[q + 2]; c++)
+          for (int d = 0; d < p->M[q + 3]; d++) T[(size_t)(q + 2) * BLK + c * NS + d] = 1.0;
+    }
+    for (int a0 = 0; a0 < p->M[0]; a0++) u0[a0] = 1.0;
+    if (lw) CF_CUDA(p, cudaMemcpyAsync(p->dlw, lw, sizeof(double) * (size_t)m * 6, cudaMemcpyHostToDevice, st));
+    else CF_CUDA(p, cudaMemsetAsync(p->dlw, 0, sizeof(double) * (size_t)m * 6, st));
+    CF_CUDA(p, cudaMemsetAsync(p->dpb, 0, sizeof(double) * 61 * 61, st));
+    CF_CUDA(p, cudaMemcpyAsync(p->dTr64, T.data(), sizeof(double) * T.size(), cudaMemcpyHostToDevice, st));
+    CF_CUDA(p, cudaMemcpyAsync(p->du0, u0.data(), sizeof(double) * NS, cudaMemcpyHostToDevice, st));
+    CF_CUDA(p, cudaMemcpyAsync(p->dls, ls.data(), sizeof(double) * ls.size(), cudaMemcpyHostToDevice, st));
+    k_typed_x<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->den64, p->dTr64, p->dX64);
+    CF_CUDA(p, cudaGetLastError());
+    CF_CUDA(p, cudaStreamSynchronize(st));  // the host arrays go out of scope
+    (void)pb;
+    return CF_OK;
+  }
   if (lw) CF_CUDA(p, cudaMemcpyAsync(p->dlw, lw, sizeof(double) * (size_t)m * 6, cudaMemcpyHostToDevice, st));
   else CF_CUDA(p, cudaMemsetAsync(p->dlw, 0, sizeof(double) * (size_t)m * 6, st));
   if (pb) CF_CUDA(p, cudaMemcpyAsync(p->dpb, pb, sizeof(double) * 61 * 61, cudaMemcpyHostToDevice, st));
@@ -1461,6 +1519,7 @@ static void release_protein(cf_problem *p) {
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
   p->dcm = p->dbm = p->dpg = nullptr;
   p->dcid = nullptr;
+  p->dsmap = nullptr;
   p->dlw = p->dpb = p->dTr64 = p->dX64 = p->den64 = p->dls = p->dlogz = nullptr;
   p->dP = nullptr;
   p->have_inside = false;
@@ -1495,6 +1554,8 @@ cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw,
     res[r] = (int)(q - kAminoAcids);
   }
   if (check_weights(p, m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_protein: " + p->err);
+  if (pb && p->layout_req == 1)
+    return fail(p, CF_EINVAL, "cf_set_protein: the single-codon layout has no codon-pair bonuses");
   CF_CUDA(p, cudaSetDevice(p->device));
   // past validation the old protein is gone: a failure below (an allocation
   // that does not fit, a CUDA error) releases everything, so that the problem
@@ -1514,7 +1575,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   const GeneticCode &gc = gcode();
   // a protein of the same length reuses the device tables and the pass graphs
   // (they depend on the length only): no allocation, no device-wide sync
-  const bool reuse = p->n == 3 * m && p->dM != nullptr;
+  const bool reuse = p->n == 3 * m && p->dM != nullptr && p->layout == p->layout_req;
   if (reuse) {
     CF_CUDA(p, cudaStreamSynchronize(p->stream));  // no pass may still read the old protein
     p->have_inside = false;
@@ -1524,22 +1585,62 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   const int n = 3 * m;
   p->n = n;
   p->m = m;
+  p->layout = p->layout_req;
   p->M.assign(n, 0);
   p->base.assign((size_t)n * NS, 0);
   p->cid.assign((size_t)n * NS, -1);
   p->bnd.assign(n, 0);
+  p->smap.assign((size_t)m * 6, -1);
+  p->sc3.assign((size_t)n * NS, -1);
   for (int r = 0; r < m; r++) {
     const auto &cods = gc.codons[res[r]];
-    for (int off = 0; off < 3; off++) {
-      int q = 3 * r + off;
-      p->M[q] = (int)cods.size();
-      for (size_t a = 0; a < cods.size(); a++) {
-        p->base[(size_t)q * NS + a] = (cods[a] >> (2 * (2 - off))) & 3;
-        p->cid[(size_t)q * NS + a] = gc.sense_id[cods[a]];
+    if (p->layout == 0) {
+      for (int off = 0; off < 3; off++) {
+        int q = 3 * r + off;
+        p->M[q] = (int)cods.size();
+        for (size_t a = 0; a < cods.size(); a++) {
+          p->base[(size_t)q * NS + a] = (cods[a] >> (2 * (2 - off))) & 3;
+          p->cid[(size_t)q * NS + a] = gc.sense_id[cods[a]];
+        }
+        p->bnd[q] = (off == 2 && q + 1 < n) ? 1 : 0;  // T_q crosses into residue r+1
       }
-      p->bnd[q] = (off == 2 && q + 1 < n) ? 1 : 0;  // T_q crosses into residue r+1
+    } else {
+      // single-codon layout (Eq. single-tt): the states of the first position
+      // are the distinct first bases, of the second the distinct (second,
+      // third) base pairs, of the third the distinct third bases, in
+      // ascending order; the codon is fixed by the transfer 3r -> 3r+1
+      std::vector<int> f, pr, l;
+      for (int c : cods) {
+        f.push_back(c >> 4 & 3);
+        pr.push_back(c & 15);
+        l.push_back(c & 3);
+      }
+      auto uniq = [](std::vector<int> v) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        return v;
+      };
+      const std::vector<int> F = uniq(f), PR = uniq(pr), L = uniq(l);
+      const int q = 3 * r;
+      p->M[q] = (int)F.size();
+      p->M[q + 1] = (int)PR.size();
+      p->M[q + 2] = (int)L.size();
+      for (size_t a = 0; a < F.size(); a++) p->base[(size_t)q * NS + a] = F[a];
+      for (size_t a = 0; a < PR.size(); a++) {
+        p->base[(size_t)(q + 1) * NS + a] = PR[a] >> 2;
+        p->sc3[(size_t)(q + 1) * NS + a] = PR[a] & 3;
+      }
+      for (size_t a = 0; a < L.size(); a++) p->base[(size_t)(q + 2) * NS + a] = L[a];
+      p->bnd[q] = 1;  // T_q carries the codon and its weight
+      for (size_t s2 = 0; s2 < cods.size(); s2++) {
+        const int c = cods[s2];
+        const int a = (int)(std::lower_bound(F.begin(), F.end(), c >> 4 & 3) - F.begin());
+        const int b = (int)(std::lower_bound(PR.begin(), PR.end(), c & 15) - PR.begin());
+        p->smap[(size_t)r * 6 + s2] = a | (b << 4) | ((c >> 4 & 3) << 8) | ((c >> 2 & 3) << 10) | ((c & 3) << 12);
+      }
     }
   }
+  p->nls = p->layout == 0 ? m - 1 : m;
   p->eHL.assign((size_t)n + 2, 0.0);
   const double kT = p->model->kT, H30 = p->model->params[36 + MAXLOOP];
   for (int L = 0; L < n + 2; L++) {
@@ -1568,7 +1669,8 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
     CF_CUDA(p, dalloc(S, &p->dTr64, (size_t)n * BLK));
     CF_CUDA(p, dalloc(S, &p->dX64, (size_t)n * 4 * BLK));
     CF_CUDA(p, dalloc(S, &p->den64, (size_t)EN_N));
-    CF_CUDA(p, dalloc(S, &p->dls, (size_t)std::max(m - 1, 1)));
+    CF_CUDA(p, dalloc(S, &p->dls, (size_t)std::max(m, 1)));
+    CF_CUDA(p, dalloc(S, &p->dsmap, (size_t)m * 6));
     CF_CUDA(p, dalloc(S, &p->dlogz, (size_t)1));
     CF_CUDA(p, cudaMemcpy(p->den64, p->model->en, sizeof(double) * EN_N, cudaMemcpyHostToDevice));
   }
@@ -1577,6 +1679,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   CF_CUDA(p, cudaMemcpyAsync(p->dbase, p->base.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dsmap, p->smap.data(), sizeof(int) * m * 6, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
   if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
   CF_CUDA(p, cudaStreamSynchronize(st));
@@ -1595,6 +1698,7 @@ cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
   if (!p) return fail(p, CF_EINVAL, "cf_set_weights: NULL problem");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_set_weights: no protein set");
   if (check_weights(p, p->m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_weights: " + p->err);
+  if (pb && p->layout == 1) return fail(p, CF_EINVAL, "cf_set_weights: the single-codon layout has no codon-pair bonuses");
   CF_CUDA(p, cudaSetDevice(p->device));
   CF_CUDA(p, cudaStreamSynchronize(p->stream));  // no pass may still read the old transfers
   p->have_inside = false;
@@ -1622,6 +1726,8 @@ cf_status cf_inside(cf_problem *p, cf_precision prec, double *logZ) {
 cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double *base_marg, double *pair_grad) {
   if (!p) return fail(p, CF_EINVAL, "cf_outside: NULL problem");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_outside: run cf_inside first");
+  if (pair_grad && p->layout == 1)
+    return fail(p, CF_EINVAL, "cf_outside: no codon-pair gradient in the single-codon layout");
   CF_CUDA(p, cudaSetDevice(p->device));
   cf_status s = (p->last_prec == CF_FP64) ? run_outside(p, p->f64) : run_outside(p, p->f32);
   if (s != CF_OK) return s;
@@ -1683,6 +1789,7 @@ const char *cf_last_error(const cf_problem *p) {
 cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons, int32_t *partner) {
   if (!p) return fail(p, CF_EINVAL, "cf_mfe: NULL problem");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_mfe: no protein set");
+  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_mfe: not available in the single-codon layout");
   CF_CUDA(p, cudaSetDevice(p->device));
   return run_mfe(p, cost, mfe_kcal, codons, partner);
 }
@@ -1849,7 +1956,7 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
     a.Tr = p->dTr64;
     a.u0 = p->du0;
     a.ls = p->dls;
-    a.nls = p->m - 1;
+    a.nls = p->nls;
     a.mod = mod->d;
     a.Q = t.Q;
     a.L = t.L;
@@ -1928,6 +2035,21 @@ cf_status cf_set_checkpoint(cf_problem *p, int mode) {
   return CF_OK;
 }
 
+cf_status cf_set_layout(cf_problem *p, int layout) {
+  if (!p || layout < 0 || layout > 1) return fail(p, CF_EINVAL, "cf_set_layout: bad argument");
+  if (p->batch > 1 && layout != 0) return fail(p, CF_EINVAL, "cf_set_layout: a batch keeps codon states");
+  p->layout_req = layout;  // the next cf_set_protein builds the states
+  return CF_OK;
+}
+
+cf_status cf_layout_states(const cf_problem *p, int *layout, int *states) {
+  if (!p) return fail(nullptr, CF_EINVAL, "cf_layout_states: NULL problem");
+  if (layout) *layout = p->layout;
+  if (states)
+    for (int q = 0; q < p->n; q++) states[q] = p->M[q];
+  return CF_OK;
+}
+
 int cf_checkpointed(const cf_problem *p) {
   if (!p) return 0;
   if (p->f32.inside_alloc) return p->f32.dp.yyck;
@@ -1939,6 +2061,7 @@ cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
   if (!p) return fail(p, CF_EINVAL, "cf_sample: NULL problem");
   if (nsamples < 0 || (nsamples > 0 && (!codons || !partner))) return fail(p, CF_EINVAL, "cf_sample: bad arguments");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample: run cf_inside first");
+  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_sample: not available in the single-codon layout");
   if (nsamples == 0) return CF_OK;
   CF_CUDA(p, cudaSetDevice(p->device));
   return (p->last_prec == CF_FP64) ? run_sample(p, p->f64, nsamples, seed, codons, partner)
@@ -2018,6 +2141,7 @@ cf_status run_sample_noalloc(cf_problem *p, PrecTables<T> &t, int ns, uint64_t s
 extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
                                        int32_t *partner) {
   if (!p) return fail(p, CF_EINVAL, "cf_sample_noalloc: NULL problem");
+  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_sample_noalloc: not available in the single-codon layout");
   if (p->n > CF_NOALLOC_MAX_N)
     return fail(p, CF_EINVAL, "cf_sample_noalloc: sequence length " + std::to_string(p->n) +
                                   " exceeds CF_NOALLOC_MAX_N = " + std::to_string(CF_NOALLOC_MAX_N));

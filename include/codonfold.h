@@ -188,6 +188,27 @@ cf_status cf_mfe(cf_problem *prob, int64_t *cost, double *mfe_kcal, int32_t *cod
 float cf_mfe_last_ms(const cf_problem *prob);
 
 /*
+ * Suboptimal configurations (paper SI "Suboptimal sequence generation", Alg.
+ * subopt, over the min-sum recursions of cf_mfe): every (codon sequence,
+ * structure) of the current protein whose integer cost is at most the
+ * minimum plus floor(gap_kcal * 2^32) (the 2^-32 kcal/mol grid of cf_mfe),
+ * each exactly once, in depth-first order of the recursions.  Up to max_out
+ * of them are written to host arrays: cost[max_out] (may be NULL), codons
+ * [max_out][m] sense codon ids (may be NULL), partner [max_out][n] (-1
+ * unpaired; may be NULL); *count receives the number found, max_out + 1 if
+ * there are more (the enumeration stops there).  The MFE tables are
+ * computed on the device and one CTA enumerates, for at most 30 s of device
+ * time or 5e7 steps (else CF_ENUMERIC; a smaller gap or max_out keeps it
+ * short); cf_mfe_last_ms reports the time.  Errors: CF_EINVAL (NULL problem
+ * or count, gap < 0 or > 1e6,
+ * max_out < 0, device outputs, the single-codon layout), CF_ESTATE (no
+ * protein), CF_ENUMERIC (no finite configuration, an inconsistency),
+ * CF_ENOMEM, CF_ECUDA.
+ */
+cf_status cf_subopt(cf_problem *prob, double gap_kcal, int max_out, int64_t *cost, int32_t *codons,
+                    int32_t *partner, int *count);
+
+/*
  * Position-state layout (paper Eq. single-tt, Section "Incorporating hard
  * constraints"): 0 (default) codon states, the codon-pair tensor train of
  * Eq. pair-tt (every position of a residue carries the residue's codon);

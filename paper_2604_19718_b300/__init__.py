@@ -88,6 +88,8 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = ctypes.c_int
     lib.cf_mfe_last_ms.argtypes = [vp]
     lib.cf_mfe_last_ms.restype = ctypes.c_float
+    lib.cf_subopt.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.cf_subopt.restype = ctypes.c_int
     lib.cf_set_layout.argtypes = [vp, ctypes.c_int]
     lib.cf_layout_states.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     lib.cf_set_layout.restype = ctypes.c_int
@@ -277,6 +279,20 @@ def cf_checkpointed(prob) -> bool:
 
 def cf_mfe_last_ms(prob) -> float:
     return float(lib.cf_mfe_last_ms(prob))
+
+
+def cf_subopt(prob, m: int, n: int, gap_kcal: float, max_out: int):
+    """(count, costs [k], codons [k][m], partners [k][n]) of the configurations
+    within gap_kcal of the minimum (k = min(count, max_out); count is
+    max_out + 1 when there are more)."""
+    cost = np.zeros(max(max_out, 1), dtype=np.int64)
+    cod = np.zeros((max(max_out, 1), m), dtype=np.int32)
+    par = np.zeros((max(max_out, 1), n), dtype=np.int32)
+    cnt = ctypes.c_int()
+    _check(lib.cf_subopt(prob, float(gap_kcal), int(max_out), ctypes.c_void_p(cost.ctypes.data),
+                         ctypes.c_void_p(cod.ctypes.data), ctypes.c_void_p(par.ctypes.data), ctypes.byref(cnt)), prob)
+    k = min(cnt.value, max_out)
+    return cnt.value, cost[:k], cod[:k], par[:k]
 
 
 def cf_set_layout(prob, layout: int) -> None:
@@ -552,6 +568,10 @@ class CodonFold:
         par = np.zeros(self.n, dtype=np.int32) if traceback else None
         q, k = cf_mfe(self.prob, cod, par)
         return q, k, cod, par
+
+    def subopt(self, gap_kcal: float, max_out: int = 1000):
+        """Configurations within gap_kcal of the minimum free energy (cf_subopt)."""
+        return cf_subopt(self.prob, self.m, self.n, gap_kcal, max_out)
 
     def tm_inside(self, model: "TensorModel", precision: int = CF_FP32_SCALED) -> float:
         """log Z of the protein under a tensor-based model (cf_tm_inside)."""

@@ -1,0 +1,426 @@
+// cf_subopt.cuh -- every (codon sequence, structure) whose cost is within a
+// gap of the minimum free energy (paper SI "Suboptimal sequence generation",
+// Alg. subopt, here over the min-sum tables of the nearest-neighbour model in
+// cf_mfe.cuh).
+//
+// Depth-first over partial configurations: a partial configuration is a
+// list of recursion elements still to be decomposed, the codon states and
+// pairs fixed so far, and the slack left of the gap.  Expanding its last
+// element E (table value v) runs through E's alternatives in a fixed order
+// (the traceback's order, k_mfe_trace); an alternative of cost c with
+// c <= v + slack gives a child whose slack is slack - (c - v) and whose list
+// holds E's list with the alternative's sub-elements pushed.  A child with an
+// empty list is a complete configuration of cost MFE + gap - slack.  The
+// recursions are unambiguous (each configuration has one derivation), so
+// every configuration within the gap is found exactly once.  One CTA: the
+// threads evaluate 256 alternatives at a time and the smallest feasible index
+// at or after the element's cursor is taken; thread 0 keeps the frames (one
+// per depth, each with its own copy of the list, states and pairs) in global
+// memory.  Chains and the inner pair of an interior loop are elements of
+// their own, so that their state choices branch as well.
+#pragma once
+#include "cf_mfe.cuh"
+
+namespace cf {
+
+enum : int { MT_TOP = 16, MT_XIN = 17 };  // the root; the inner pair of an interior loop inside XI
+
+__device__ __forceinline__ int4 el_make(int kind, int x, int y, int a, int b) {
+  return make_int4(kind | (a << 8) | (b << 16), x, y, 0);
+}
+
+// The element's own table value.
+__device__ __forceinline__ mq el_want(const MfeDP &p, int4 E, mq best) {
+  const int n = p.n, kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
+  switch (kind) {
+    case MT_TOP: return best;
+    case MT_EXT: return (a < NS ? p.Q5U : p.Q5P)[(size_t)x * BLK + y * NS + a % NS];  // x = j, y = a0, a = port
+    case MT_QB: return p.QB[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_CH: return p.CH[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_QMP: return p.QMP[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_QMU: return p.QMU[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_GP: return p.GP[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_BP: return p.BP[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_M2PU: return p.M2PU[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_M2UP: return p.M2UP[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_M2UU: return p.M2UU[cidx(n, x, y) * BLK + a * NS + b];
+    case MT_XIN: return p.XI[cidx(n, x, y) * BLK + a * NS + b];
+  }
+  return MQINF;
+}
+
+// QB alternatives: stack, bulges, multiloop, hairpin and interior loops
+constexpr int SB_STACK = BLK, SB_BULGE = MAXLOOP * 2 * BLK, SB_ML = 4 * BLK, SB_HI = BLK * (1 + NINTERIOR * BLK);
+constexpr int SB_QB = SB_STACK + SB_BULGE + SB_ML + SB_HI;
+
+__device__ __forceinline__ int el_count(const MfeDP &p, int4 E) {
+  const int kind = E.x & 255, a = (E.x >> 8) & 255, x = E.y, y = E.z;
+  switch (kind) {
+    case MT_TOP: return NS * 2 * p.Mp[p.n - 1];
+    case MT_EXT:
+      if (x == 0) return 1;
+      if (a < NS) return 2 * p.Mp[x - 1];
+      return 1 + max(0, x - 4) * 2 * NS * NS;
+    case MT_CH: return x == y ? 1 : NS;
+    case MT_QB: return SB_QB;
+    case MT_QMP: return 2;
+    case MT_QMU: case MT_M2PU: case MT_GP: case MT_M2UP: case MT_M2UU: return 2 * NS;
+    case MT_BP: return max(0, y - x - 8) * NS;
+    case MT_XIN: return BLK;
+  }
+  return 0;
+}
+
+// Cost of alternative k of E, and (kids != nullptr) its sub-elements in push
+// order (the last one is decomposed first); returns the number of kids.
+__device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
+  const int n = p.n, kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
+  const mq *en = p.en;
+  int c = 0;
+  mq v = MQINF;
+  switch (kind) {
+    case MT_TOP: {  // residue 0's state and the port of position n-1, (a, type, b) ascending
+      const int Ml = p.Mp[n - 1], a0 = k / (2 * Ml), r = k % (2 * Ml), tp = r / Ml, bb = r % Ml;
+      v = p.u0[a0] + (tp ? p.Q5P : p.Q5U)[(size_t)(n - 1) * BLK + a0 * NS + bb];
+      if (kids) kids[c++] = el_make(MT_EXT, n - 1, a0, bb + NS * tp, 0);
+      break;
+    }
+    case MT_EXT: {
+      const int j = x, a0 = y, port = a;
+      if (j == 0) {
+        v = port == a0 ? el_want(p, E, 0) : MQINF;
+      } else if (port < NS) {  // j unpaired: (type, state) at j-1
+        const int Mp = p.Mp[j - 1], tp = k / Mp, s = k % Mp;
+        v = (tp ? p.Q5P : p.Q5U)[(size_t)(j - 1) * BLK + a0 * NS + s] +
+            p.chi[(size_t)(j - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + port];
+        if (kids) kids[c++] = el_make(MT_EXT, j - 1, a0, s + NS * tp, 0);
+      } else {  // j paired: the branch (0, j), then the last branch (kk, j)
+        const int bb = port - NS;
+        if (k == 0) {
+          v = p.QB[cidx(n, 0, j) * BLK + a0 * NS + bb];
+          if (kids) kids[c++] = el_make(MT_QB, 0, j, a0, bb);
+        } else {
+          const int q = k - 1, kk = 1 + q / (2 * NS * NS), r = q % (2 * NS * NS), tp = r / (NS * NS),
+                    s1 = (r / NS) % NS, s = r % NS;
+          const mq *ch = p.chi + (size_t)(kk - 1) * 4 * BLK;
+          v = (tp ? p.Q5P : p.Q5U)[(size_t)(kk - 1) * BLK + a0 * NS + s1] + ch[(tp ? XPP : XUP) * BLK + s1 * NS + s] +
+              p.QB[cidx(n, kk, j) * BLK + s * NS + bb];
+          if (kids) {
+            kids[c++] = el_make(MT_QB, kk, j, s, bb);
+            kids[c++] = el_make(MT_EXT, kk - 1, a0, s1 + NS * tp, 0);
+          }
+        }
+      }
+      break;
+    }
+    case MT_CH: {  // chain x..y with end states a, b: the next state
+      if (x == y) {
+        v = a == b ? 0 : MQINF;
+      } else {
+        v = p.tau[(size_t)x * BLK + a * NS + k] + p.CH[cidx(n, x + 1, y) * BLK + k * NS + b];
+        if (kids) kids[c++] = el_make(MT_CH, x + 1, y, k, b);
+      }
+      break;
+    }
+    case MT_QB: {
+      const int i = x, j = y, d = j - i;
+      const mq *ti = p.tau + (size_t)i * BLK, *tj1 = p.tau + (size_t)(j - 1) * BLK;
+      int q = k;
+      if (q < SB_STACK) {  // stack: (a2, b2)
+        const int a2 = q / NS, b2 = q % NS;
+        if (d >= 6) {
+          const int po = pair_type(p.base[i * NS + a], p.base[j * NS + b]);
+          const int pi = pair_type(p.base[(i + 1) * NS + a2], p.base[(j - 1) * NS + b2]);
+          if (po >= 0 && pi >= 0)
+            v = ti[a * NS + a2] + p.QB[cidx(n, i + 1, j - 1) * BLK + a2 * NS + b2] + tj1[b2 * NS + b] +
+                en[EN_STK + po * 6 + pi];
+        }
+        if (kids) kids[c++] = el_make(MT_QB, i + 1, j - 1, a2, b2);
+        break;
+      }
+      q -= SB_STACK;
+      if (q < SB_BULGE) {  // bulges: size L, 3' before 5', then the two free states
+        const int L = 1 + q / (2 * BLK), side = (q / BLK) & 1, s1 = (q % BLK) / NS, s2 = q % NS;
+        if (side == 0) {
+          const int l = j - 1 - L;
+          if (l - (i + 1) >= 4)
+            v = en[EN_BU + L] + ti[a * NS + s1] + p.QB[cidx(n, i + 1, l) * BLK + s1 * NS + s2] +
+                p.CH[cidx(n, l, j) * BLK + s2 * NS + b];
+          if (kids) {
+            kids[c++] = el_make(MT_CH, l, j, s2, b);
+            kids[c++] = el_make(MT_QB, i + 1, l, s1, s2);
+          }
+        } else {
+          const int kk = i + 1 + L;
+          if ((j - 1) - kk >= 4)
+            v = en[EN_BU + L] + p.CH[cidx(n, i, kk) * BLK + a * NS + s1] + p.QB[cidx(n, kk, j - 1) * BLK + s1 * NS + s2] +
+                tj1[s2 * NS + b];
+          if (kids) {
+            kids[c++] = el_make(MT_CH, i, kk, a, s1);
+            kids[c++] = el_make(MT_QB, kk, j - 1, s1, s2);
+          }
+        }
+        break;
+      }
+      q -= SB_BULGE;
+      if (q < SB_ML) {  // multiloop: (type at i+1, type at j-1, state at i+1, state at j-1)
+        const int t1 = q / (2 * BLK), t2 = (q / BLK) & 1, s = (q % BLK) / NS, s2 = q % NS;
+        if (d >= 11) {
+          const mq *cx = p.chi + (size_t)i * 4 * BLK, *cy = p.chi + (size_t)(j - 1) * 4 * BLK;
+          const mq *Q2 = t1 ? (t2 ? p.BP : p.M2PU) : (t2 ? p.M2UP : p.M2UU);
+          v = en[EN_EA] + en[EN_EC] + cx[(t1 ? XPP : XPU) * BLK + a * NS + s] +
+              Q2[cidx(n, i + 1, j - 1) * BLK + s * NS + s2] + cy[(t2 ? XPP : XUP) * BLK + s2 * NS + b];
+        }
+        if (kids) kids[c++] = el_make(t1 ? (t2 ? MT_BP : MT_M2PU) : (t2 ? MT_M2UP : MT_M2UU), i + 1, j - 1, s, s2);
+        break;
+      }
+      q -= SB_ML;
+      {  // hairpin, then interior loops (l1 then l2), over (u at i+1, v at j-1), then (w at k-1, z at l+1)
+        const int xi = i + 1, yi = j - 1;
+        const int u = (q % BLK) / NS, vv = q % NS, sh = q / BLK;
+        const mq outer = ti[a * NS + u] + tj1[vv * NS + b] + en[EN_TM + p.base[xi * NS + u] * 4 + p.base[yi * NS + vv]];
+        if (sh == 0) {
+          if (outer < MQHALF) v = outer + p.hq[d - 1] + p.CH[cidx(n, xi, yi) * BLK + u * NS + vv];
+          if (kids) kids[c++] = el_make(MT_CH, xi, yi, u, vv);
+        } else {
+          const int qq = (sh - 1) / BLK, w = ((sh - 1) % BLK) / NS, z = (sh - 1) % NS;
+          int l1, l2;
+          interior_shape(qq, l1, l2);
+          const int kk = i + 1 + l1, l = j - 1 - l2;
+          if (outer < MQHALF && l - kk >= 4)
+            v = outer + en[EN_IN + l1 + l2] + p.CH[cidx(n, xi, kk - 1) * BLK + u * NS + w] +
+                p.XI[cidx(n, kk - 1, l + 1) * BLK + w * NS + z] + p.CH[cidx(n, l + 1, yi) * BLK + z * NS + vv];
+          if (kids) {
+            kids[c++] = el_make(MT_CH, xi, kk - 1, u, w);
+            kids[c++] = el_make(MT_CH, l + 1, yi, z, vv);
+            kids[c++] = el_make(MT_XIN, kk - 1, l + 1, w, z);
+          }
+        }
+      }
+      break;
+    }
+    case MT_XIN: {  // the inner pair (x+1, y-1) inside XI[x][y]: states (a2, b2)
+      const int a2 = k / NS, b2 = k % NS;
+      const mq tmi = en[EN_TM + p.base[y * NS + b] * 4 + p.base[x * NS + a]];
+      v = p.tau[(size_t)x * BLK + a * NS + a2] + p.QB[cidx(n, x + 1, y - 1) * BLK + a2 * NS + b2] +
+          p.tau[(size_t)(y - 1) * BLK + b2 * NS + b] + tmi;
+      if (kids) kids[c++] = el_make(MT_QB, x + 1, y - 1, a2, b2);
+      break;
+    }
+    case MT_QMP: {  // a branch (x, y), then >= 2 branches
+      if (k == 0) {
+        v = en[EN_EC] + p.QB[cidx(n, x, y) * BLK + a * NS + b];
+        if (kids) kids[c++] = el_make(MT_QB, x, y, a, b);
+      } else {
+        v = p.BP[cidx(n, x, y) * BLK + a * NS + b];
+        if (kids) kids[c++] = el_make(MT_BP, x, y, a, b);
+      }
+      break;
+    }
+    case MT_QMU: case MT_M2PU: {  // y unpaired: (type at y-1, state at y-1)
+      const bool one = kind == MT_QMU;
+      const int tp = k / NS, s = k % NS;
+      const mq *Pt = tp ? (one ? p.QMP : p.BP) : (one ? p.QMU : p.M2PU);
+      v = en[EN_EB] + Pt[cidx(n, x, y - 1) * BLK + a * NS + s] +
+          p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + b];
+      if (kids) kids[c++] = el_make(tp ? (one ? MT_QMP : MT_BP) : kind, x, y - 1, a, s);
+      break;
+    }
+    case MT_GP: {  // the branch start at y: (type at y-1, state at y-1)
+      const int tp = k / NS, s = k % NS;
+      v = (tp ? p.QMP : p.QMU)[cidx(n, x, y - 1) * BLK + a * NS + s] +
+          p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPP : XUP) * BLK + s * NS + b];
+      if (kids) kids[c++] = el_make(tp ? MT_QMP : MT_QMU, x, y - 1, a, s);
+      break;
+    }
+    case MT_BP: {  // last branch (kk, y): kk ascending, state at kk
+      const int kk = x + 5 + k / NS, s = k % NS;
+      v = en[EN_EC] + p.GP[cidx(n, x, kk) * BLK + a * NS + s] + p.QB[cidx(n, kk, y) * BLK + s * NS + b];
+      if (kids) {
+        kids[c++] = el_make(MT_QB, kk, y, s, b);
+        kids[c++] = el_make(MT_GP, x, kk, a, s);
+      }
+      break;
+    }
+    default: {  // MT_M2UP / MT_M2UU: x unpaired: (type at x+1, state at x+1)
+      const bool lastp = kind == MT_M2UP;
+      const int tp = k / NS, s = k % NS;
+      const mq *Pt = tp ? (lastp ? p.BP : p.M2PU) : (lastp ? p.M2UP : p.M2UU);
+      v = en[EN_EB] + p.chi[(size_t)x * 4 * BLK + (tp ? XUP : XUU) * BLK + a * NS + s] +
+          Pt[cidx(n, x + 1, y) * BLK + s * NS + b];
+      if (kids) kids[c++] = el_make(tp ? (lastp ? MT_BP : MT_M2PU) : kind, x + 1, y, s, b);
+      break;
+    }
+  }
+  if (nk) *nk = c;
+  return mclamp(v);
+}
+
+struct SubArgs {
+  MfeDP p;
+  mq gap;
+  int max_out, pcap;
+  size_t fsz;             // bytes per frame: header, pending list [pcap], states [n], partners [n]
+  unsigned char *frames;  // [depth cap][fsz]
+  int depth_cap;
+  long long max_steps;
+  unsigned long long max_ns;  // the enumeration stops (with an error) past this device time
+  int32_t *codons, *partner;  // [max_out][m], [max_out][n]
+  long long *cost;            // [max_out]
+  long long *count;           // [2]: configurations found (capped at max_out + 1), steps taken
+};
+
+struct SubHdr {
+  int4 elem;
+  long long slack;
+  int npend, cursor;
+};
+
+__device__ __forceinline__ SubHdr *sf_hdr(const SubArgs &s, int f) { return (SubHdr *)(s.frames + (size_t)f * s.fsz); }
+__device__ __forceinline__ int4 *sf_pend(const SubArgs &s, int f) {
+  return (int4 *)(s.frames + (size_t)f * s.fsz + 64);
+}
+__device__ __forceinline__ int *sf_state(const SubArgs &s, int f) {
+  return (int *)(s.frames + (size_t)f * s.fsz + 64 + (size_t)s.pcap * sizeof(int4));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
+  const MfeDP &p = s.p;
+  const unsigned long long t0 = global_ns();
+  const int n = p.n, t = threadIdx.x;
+  __shared__ int sfirst, sdepth, sbad, sdone;
+  __shared__ long long sfound;
+  const mq best = *p.best;
+  if (t == 0) {
+    SubHdr *h = sf_hdr(s, 0);
+    h->elem = el_make(MT_TOP, 0, 0, 0, 0);
+    h->slack = s.gap;
+    h->npend = 0;
+    h->cursor = 0;
+    sdepth = 1;
+    sbad = 0;
+    sdone = 0;
+    sfound = 0;
+  }
+  {
+    int *st = sf_state(s, 0);
+    for (int q = t; q < 2 * n; q += blockDim.x) st[q] = -1;
+  }
+  __syncthreads();
+  long long steps = 0;
+  while (true) {
+    __syncthreads();
+    const int depth = sdepth;
+    if (depth == 0 || sbad || sdone || best >= MQHALF) break;
+    if (++steps > s.max_steps || (t == 0 && (steps & 255) == 0 && global_ns() - t0 > s.max_ns)) {
+      if (t == 0) sbad = 2;  // bounded: the other threads see it at the next step
+      if (steps > s.max_steps) break;
+    }
+    const int f = depth - 1;
+    SubHdr *h = sf_hdr(s, f);
+    const int4 E = h->elem;
+    const long long slack = h->slack;
+    const int cur = h->cursor;
+    const mq want = el_want(p, E, best);
+    const mq limit = want + slack;
+    const int K = el_count(p, E);
+    // the first feasible alternative at or after the cursor
+    int kf = -1;
+    for (int b0 = cur; b0 < K; b0 += blockDim.x) {
+      if (t == 0) sfirst = INT_MAX;
+      __syncthreads();
+      const int k = b0 + t;
+      if (k < K && el_alt(p, E, k, nullptr, nullptr) <= limit) atomicMin(&sfirst, k);
+      __syncthreads();
+      const int fk = sfirst;
+      __syncthreads();
+      if (fk != INT_MAX) {
+        kf = fk;
+        break;
+      }
+    }
+    if (kf < 0) {  // no more alternatives: back to the parent
+      if (t == 0) sdepth = depth - 1;
+      continue;
+    }
+    if (f + 1 >= s.depth_cap) {
+      if (t == 0) sbad = 3;
+      break;
+    }
+    // the child: the parent's list, states and pairs, E's own decisions, the alternative's sub-elements
+    const int np = h->npend;
+    int4 *pp = sf_pend(s, f), *cp = sf_pend(s, f + 1);
+    const int *ps = sf_state(s, f);
+    int *cs = sf_state(s, f + 1);
+    for (int q = t; q < np; q += blockDim.x) cp[q] = pp[q];
+    for (int q = t; q < 2 * n; q += blockDim.x) cs[q] = ps[q];
+    __syncthreads();
+    if (t == 0) {
+      h->cursor = kf + 1;
+      int4 kids[3];
+      int nk = 0;
+      const mq c = el_alt(p, E, kf, kids, &nk);
+      const long long nslack = slack - (c - want);
+      const int kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
+      auto setst = [&](int q, int v) {
+        if (cs[q] >= 0 && cs[q] != v) sbad = 4;
+        cs[q] = v;
+      };
+      switch (kind) {  // the element's own decisions
+        case MT_EXT:
+          if (x == 0) setst(0, y);
+          else if (a < NS) setst(x, a);
+          break;
+        case MT_CH: setst(x, a); break;
+        case MT_QB:
+          cs[n + x] = y;
+          cs[n + y] = x;
+          setst(x, a);
+          setst(y, b);
+          break;
+        case MT_QMU: case MT_M2PU: setst(y, b); break;
+        case MT_M2UP: case MT_M2UU: setst(x, a); break;
+        default: break;
+      }
+      int m2 = np;
+      for (int q = 0; q < nk; q++) {
+        if (m2 < s.pcap) cp[m2++] = kids[q];
+        else sbad = 5;
+      }
+      if (m2 == 0) {  // complete: MFE + gap - slack
+        const long long idx = sfound;
+        if (idx < s.max_out) {
+          for (int r = 0; r < p.m; r++) {
+            const int st = cs[3 * r];
+            s.codons[(size_t)idx * p.m + r] = st >= 0 ? p.cid[3 * r * NS + st] : -1;
+          }
+          for (int q = 0; q < n; q++) s.partner[(size_t)idx * n + q] = cs[n + q];
+          s.cost[idx] = best + (s.gap - nslack);
+        }
+        sfound = idx + 1;
+        if (sfound > s.max_out) sdone = 1;
+      } else {
+        SubHdr *g = sf_hdr(s, f + 1);
+        g->elem = cp[m2 - 1];
+        g->npend = m2 - 1;
+        g->slack = nslack;
+        g->cursor = 0;
+        sdepth = depth + 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    s.count[0] = sfound;
+    s.count[1] = steps;
+    if (sbad) atomicOr(p.err, 1 << (8 + sbad));
+  }
+}
+
+}  // namespace cf

@@ -32,6 +32,7 @@
 #include "cf_sample.cuh"
 #include "cf_window.cuh"
 #include "cf_tm.cuh"
+#include "cf_subopt.cuh"
 
 using namespace cf;
 
@@ -1319,6 +1320,76 @@ cf_status run_mfe(cf_problem *p, int64_t *cost, double *kcal, int32_t *codons, i
   return CF_OK;
 }
 
+// Every configuration within `gap` (integer cost) of the minimum, depth first
+// (cf_subopt.cuh): the MFE tables first, then one CTA enumerates.
+cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost, int32_t *codons, int32_t *partner,
+                     int *count) {
+  cf_status s = mfe_alloc(p);
+  if (s != CF_OK) {
+    free_mfe(p->mfe);
+    return s;
+  }
+  s = mfe_graph(p);
+  if (s != CF_OK) return s;
+  MfeTables &t = p->mfe;
+  cudaStream_t st = p->stream;
+  const int n = p->n, m = p->m;
+  CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  CF_CUDA(p, cudaEventRecord(p->ev[0], st));
+  k_mfe_transfers<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, t.dp.en, p->model->kT, p->dlw,
+                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0);
+  CF_CUDA(p, cudaGetLastError());
+  CF_CUDA(p, cudaGraphLaunch(t.g, st));
+  SubArgs a;
+  a.p = t.dp;
+  a.gap = gap;
+  a.max_out = max_out;
+  a.pcap = 4 * n + 64;
+  a.depth_cap = 4 * n + 64;
+  a.fsz = ((size_t)64 + (size_t)a.pcap * sizeof(int4) + (size_t)2 * n * sizeof(int) + 15) / 16 * 16;
+  a.max_steps = 50000000ll;
+  a.max_ns = 30ull * 1000000000ull;  // 30 s
+  std::vector<void *> tmp;
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    free_list(tmp);
+  };
+  cudaError_t e = dalloc(tmp, &a.frames, a.fsz * a.depth_cap);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.codons, (size_t)std::max(max_out, 1) * m);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.partner, (size_t)std::max(max_out, 1) * n);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.cost, (size_t)std::max(max_out, 1));
+  if (e == cudaSuccess) e = dalloc(tmp, &a.count, (size_t)2);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(p, e, "cf_subopt: scratch");
+  }
+  k_mfe_subopt<<<1, 256, 0, st>>>(a);
+  e = cudaGetLastError();
+  long long cnt[2] = {0, 0};
+  int err = 0;
+  long long best = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, a.count, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&best, t.dp.best, sizeof(best), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const long long nw = std::min<long long>(cnt[0], max_out);
+  if (e == cudaSuccess && nw > 0) {
+    if (cost) e = cudaMemcpy(cost, a.cost, sizeof(long long) * nw, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && codons) e = cudaMemcpy(codons, a.codons, sizeof(int32_t) * nw * m, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && partner)
+      e = cudaMemcpy(partner, a.partner, sizeof(int32_t) * nw * n, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev[1], st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(p->ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&p->t_mfe, p->ev[0], p->ev[1]);
+  release();
+  if (e != cudaSuccess) return cuda_fail(p, e, "cf_subopt");
+  if (best >= MQHALF) return fail(p, CF_ENUMERIC, "cf_subopt: no configuration has a finite cost");
+  if (err) return fail(p, CF_ENUMERIC, "cf_subopt: enumeration inconsistency (error word " + std::to_string(err) + ")");
+  *count = (int)std::min<long long>(cnt[0], (long long)max_out + 1);
+  return CF_OK;
+}
+
 // ---- batched fixed-sequence windows
 
 cf_status window_tables(cf_problem *p) {
@@ -1795,6 +1866,19 @@ cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons
 }
 
 float cf_mfe_last_ms(const cf_problem *p) { return p ? p->t_mfe : 0.f; }
+
+cf_status cf_subopt(cf_problem *p, double gap_kcal, int max_out, int64_t *cost, int32_t *codons, int32_t *partner,
+                    int *count) {
+  if (!p || !count) return fail(p, CF_EINVAL, "cf_subopt: NULL argument");
+  if (!(gap_kcal >= 0) || gap_kcal > 1e6 || max_out < 0) return fail(p, CF_EINVAL, "cf_subopt: bad gap or max_out");
+  if (p->n == 0) return fail(p, CF_ESTATE, "cf_subopt: no protein set");
+  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_subopt: not available in the single-codon layout");
+  if (ptr_kind(cost, p->device) > 0 || ptr_kind(codons, p->device) > 0 || ptr_kind(partner, p->device) > 0)
+    return fail(p, CF_EINVAL, "cf_subopt: outputs must be host memory");
+  CF_CUDA(p, cudaSetDevice(p->device));
+  const long long gap = (long long)std::floor(gap_kcal * 4294967296.0);  // on the 2^-32 kcal/mol grid
+  return run_subopt(p, gap, max_out, (long long *)cost, codons, partner, count);
+}
 
 // ------------------------------------------------------------------ tensor-based model
 

@@ -213,11 +213,13 @@ cf_status cf_subopt(cf_problem *prob, double gap_kcal, int max_out, int64_t *cos
  * constraints"): 0 (default) codon states, the codon-pair tensor train of
  * Eq. pair-tt (every position of a residue carries the residue's codon);
  * 1 the single-codon tensor train: the first position of a residue carries
- * its distinct first bases, the second its distinct (second, third) base
+ * its distinct first bases, the second its distinct (first, second) base
  * pairs, the third its distinct third bases, and the codon (with its
- * weight lw) is fixed by the transfer from the first position to the
- * second.  Layout 1 has fewer states per position (2.15 against 2.84 on a
- * Dirichlet(1) composition) and the same log Z, pair probabilities, codon
+ * weight lw) is fixed by the transfer from the second position to the
+ * third.  Layout 1 has fewer states per position (1.61 against 2.84 on a
+ * Dirichlet(1) composition, 1.68 on a uniform one; every position needs at
+ * least its number of distinct bases, 1.59 and 1.65) and the same log Z,
+ * pair probabilities, codon
  * and base marginals; it has no codon-pair bonuses (cf_set_protein and
  * cf_set_weights reject pair_bonus != NULL, cf_outside a pair_grad output),
  * and cf_sample, cf_sample_noalloc and cf_mfe return CF_EINVAL in it.

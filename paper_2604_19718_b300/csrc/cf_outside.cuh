@@ -130,16 +130,16 @@ __global__ void k_codon_out(DP<T> p, const double *trans, const double *p0, cons
 }
 
 // Codon and base marginals in the single-codon layout (Eq. single-tt): the
-// codon of residue r is fixed by the transfer from its first position (state
-// = first base) to its second (state = second and third base), which also
-// carries the codon's weight, so its marginal is T o (hT + sum_k hX_k o
-// dangle_k) at q = 3r for the codon's state pair.  smap[r][s] packs, for
+// codon of residue r is fixed by the transfer from its second position
+// (state = first and second base) to its third (state = third base), which
+// also carries the codon's weight, so its marginal is T o (hT + sum_k hX_k o
+// dangle_k) at q = 3r+1 for the codon's state pair.  smap[r][s] packs, for
 // codon slot s, the two states (bits 0-3, 4-7) and the three bases (bits
 // 8-9, 10-11, 12-13); -1 past the residue's codons.  One thread per codon
 // slot, then one per (position, base).
 template <typename T>
 __device__ __forceinline__ double sc_codon_marg(const DP<T> &p, int r, int sm) {
-  const int q = 3 * r, a = sm & 15, b = (sm >> 4) & 15;
+  const int q = 3 * r + 1, a = sm & 15, b = (sm >> 4) & 15;
   const int x0 = p.base[q * NS + a], y0 = p.base[(q + 1) * NS + b];
   const double d3 = (double)p.en[EN_D3 + x0 * 4 + y0], d5 = (double)p.en[EN_D5 + y0 * 4 + x0];
   double g = p.hT[(size_t)q * BLK + a * NS + b];

@@ -202,10 +202,10 @@ struct cf_problem {
   MfeTables mfe;
   float t_mfe = 0;
   // position-state layout: 0 codon states (codon-pair tensor train), 1 the
-  // single-codon layout (first base; second and third base; third base)
+  // single-codon layout (first base; first and second base; third base)
   int layout_req = 0, layout = 0;
   std::vector<int> smap;   // single-codon layout: [m][6] packed states and bases of each codon slot
-  std::vector<int> sc3;    // single-codon layout: third base of each state at a residue's second position
+  std::vector<int> sc1;    // single-codon layout: first base of each state at a residue's second position
   int *dsmap = nullptr;
   int nls = 0;             // per-transfer log rescales undone in log Z
   // tensor-based model (cf_tm_inside)
@@ -844,7 +844,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     nodes++;
   }
   cudaGraphNode_t fin = nullptr;
-  if (e == cudaSuccess && p->layout == 1) {  // single-codon layout: codon and base marginals at q = 3r
+  if (e == cudaSuccess && p->layout == 1) {  // single-codon layout: codon and base marginals at q = 3r+1
     const int *smap = p->dsmap;
     double *cm = p->dcm, *bm = p->dbm;
     void *args[] = {&dp, &smap, &cm, &bm};
@@ -1042,11 +1042,12 @@ cf_status device_transfers(cf_problem *p, const double *lw, const double *pb) {
   const int n = p->n, m = p->m;
   cudaStream_t st = p->stream;
   if (p->layout == 1) {
-    // single-codon layout: T_{3r}[a][b] = s_r e^{lw[r][codon]} for the codon
-    // whose first base is state a at 3r and whose second and third bases are
-    // state b at 3r+1 (s_r makes the average row sum one; exact, undone in
-    // log Z), T_{3r+1}[b][c] = 1 where state b's third base is state c's base
-    // at 3r+2, T_{3r+2} = 1 into every state of the next residue; u0 = 1
+    // single-codon layout: T_{3r}[a][b] = 1 where state a's base at 3r is
+    // state b's first base at 3r+1, T_{3r+1}[b][c] = s_r e^{lw[r][codon]} for
+    // the codon whose first and second bases are state b at 3r+1 and whose
+    // third base is state c at 3r+2 (s_r makes the average row sum one;
+    // exact, undone in log Z), T_{3r+2} = 1 into every state of the next
+    // residue; u0 = 1
     std::vector<double> T((size_t)n * BLK, 0.0), u0(NS, 0.0), ls((size_t)std::max(m, 1), 0.0);
     for (int r = 0; r < m; r++) {
       const int q = 3 * r;
@@ -1055,15 +1056,15 @@ cf_status device_transfers(cf_problem *p, const double *lw, const double *pb) {
         const int sm = p->smap[(size_t)r * 6 + s2];
         if (sm < 0) continue;
         const double w = std::exp(lw ? lw[(size_t)r * 6 + s2] : 0.0);
-        T[(size_t)q * BLK + (sm & 15) * NS + ((sm >> 4) & 15)] = w;
+        T[(size_t)(q + 1) * BLK + (sm & 15) * NS + ((sm >> 4) & 15)] = w;
         sum += w;
       }
-      const double sr = p->M[q] / sum;
-      for (int e = 0; e < BLK; e++) T[(size_t)q * BLK + e] *= sr;
+      const double sr = p->M[q + 1] / sum;
+      for (int e = 0; e < BLK; e++) T[(size_t)(q + 1) * BLK + e] *= sr;
       ls[r] = std::log(sr);
-      for (int b2 = 0; b2 < p->M[q + 1]; b2++)
-        for (int c = 0; c < p->M[q + 2]; c++)
-          if (p->sc3[(size_t)(q + 1) * NS + b2] == p->base[(size_t)(q + 2) * NS + c]) T[(size_t)(q + 1) * BLK + b2 * NS + c] = 1.0;
+      for (int a = 0; a < p->M[q]; a++)
+        for (int b2 = 0; b2 < p->M[q + 1]; b2++)
+          if (p->base[(size_t)q * NS + a] == p->sc1[(size_t)(q + 1) * NS + b2]) T[(size_t)q * BLK + a * NS + b2] = 1.0;
       if (r + 1 < m)
         for (int c = 0; c < p->M[q + 2]; c++)
           for (int d = 0; d < p->M[q + 3]; d++) T[(size_t)(q + 2) * BLK + c * NS + d] = 1.0;
@@ -1662,7 +1663,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   p->cid.assign((size_t)n * NS, -1);
   p->bnd.assign(n, 0);
   p->smap.assign((size_t)m * 6, -1);
-  p->sc3.assign((size_t)n * NS, -1);
+  p->sc1.assign((size_t)n * NS, -1);
   for (int r = 0; r < m; r++) {
     const auto &cods = gc.codons[res[r]];
     if (p->layout == 0) {
@@ -1677,13 +1678,17 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
       }
     } else {
       // single-codon layout (Eq. single-tt): the states of the first position
-      // are the distinct first bases, of the second the distinct (second,
-      // third) base pairs, of the third the distinct third bases, in
-      // ascending order; the codon is fixed by the transfer 3r -> 3r+1
+      // are the distinct first bases, of the second the distinct (first,
+      // second) base pairs, of the third the distinct third bases, in
+      // ascending order; the codon is fixed by the transfer 3r+1 -> 3r+2.
+      // A position state must fix its base (the loop energies read it), so
+      // each position has at least as many states as distinct bases; the
+      // (first, second) pair never has more states than the (second, third)
+      // pair under the standard code (serine: 2 against 6)
       std::vector<int> f, pr, l;
       for (int c : cods) {
         f.push_back(c >> 4 & 3);
-        pr.push_back(c & 15);
+        pr.push_back(c >> 2 & 15);
         l.push_back(c & 3);
       }
       auto uniq = [](std::vector<int> v) {
@@ -1698,15 +1703,15 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
       p->M[q + 2] = (int)L.size();
       for (size_t a = 0; a < F.size(); a++) p->base[(size_t)q * NS + a] = F[a];
       for (size_t a = 0; a < PR.size(); a++) {
-        p->base[(size_t)(q + 1) * NS + a] = PR[a] >> 2;
-        p->sc3[(size_t)(q + 1) * NS + a] = PR[a] & 3;
+        p->base[(size_t)(q + 1) * NS + a] = PR[a] & 3;
+        p->sc1[(size_t)(q + 1) * NS + a] = PR[a] >> 2;
       }
       for (size_t a = 0; a < L.size(); a++) p->base[(size_t)(q + 2) * NS + a] = L[a];
-      p->bnd[q] = 1;  // T_q carries the codon and its weight
+      p->bnd[q + 1] = 1;  // T_{q+1} carries the codon and its weight
       for (size_t s2 = 0; s2 < cods.size(); s2++) {
         const int c = cods[s2];
-        const int a = (int)(std::lower_bound(F.begin(), F.end(), c >> 4 & 3) - F.begin());
-        const int b = (int)(std::lower_bound(PR.begin(), PR.end(), c & 15) - PR.begin());
+        const int a = (int)(std::lower_bound(PR.begin(), PR.end(), c >> 2 & 15) - PR.begin());
+        const int b = (int)(std::lower_bound(L.begin(), L.end(), c & 3) - L.begin());
         p->smap[(size_t)r * 6 + s2] = a | (b << 4) | ((c >> 4 & 3) << 8) | ((c >> 2 & 3) << 10) | ((c & 3) << 12);
       }
     }

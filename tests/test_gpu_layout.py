@@ -2,8 +2,8 @@
 same protein gives the same log Z, pair probabilities, codon and base
 marginals as the codon-state layout and the oracle, in both precisions, with
 codon weights; the tensor-based model's log Z is the same in both layouts;
-the state counts are the distinct first bases, (second, third) pairs and
-third bases; the calls the layout does not serve are refused."""
+the state counts are the distinct first bases, (first, second) pairs and
+third bases, 1.5-1.8 per position; the calls the layout does not serve are refused."""
 import numpy as np
 import pytest
 
@@ -59,9 +59,12 @@ def test_state_counts():
     expect = []
     for r in res:
         cods = tm.codon_states(r)
-        expect += [len({c[1] for c in cods}), len({(c[2], c[3]) for c in cods}), len({c[3] for c in cods})]
+        expect += [len({c[1] for c in cods}), len({(c[1], c[2]) for c in cods}), len({c[3] for c in cods})]
     assert lay == 1 and list(st) == expect
-    assert list(st) == [2, 4, 4, 2, 4, 4, 2, 6, 4, 1, 1, 1, 1, 1, 1]
+    assert list(st) == [2, 2, 4, 2, 2, 4, 2, 2, 4, 1, 1, 1, 1, 1, 1]
+    res = synth.residues_dirichlet(300, 1)
+    st = _run(res, None, 1, 1)[5]
+    assert 1.5 <= np.mean(st) <= 1.8
 
 
 def test_tensor_model_same_in_both_layouts():

@@ -13,11 +13,13 @@
 // empty list is a complete configuration of cost MFE + gap - slack.  The
 // recursions are unambiguous (each configuration has one derivation), so
 // every configuration within the gap is found exactly once.  One CTA: the
-// threads evaluate 256 alternatives at a time and the smallest feasible index
-// at or after the element's cursor is taken; thread 0 keeps the frames (one
-// per depth, each with its own copy of the list, states and pairs) in global
-// memory.  Chains and the inner pair of an interior loop are elements of
-// their own, so that their state choices branch as well.
+// alternatives come in groups with a lower bound each (k_sub_mins), the
+// threads test 256 groups at a time, evaluate the alternatives of the groups
+// within the limit 256 at a time, and the smallest feasible index at or after
+// the element's cursor is taken; thread 0 keeps the frames (one per depth,
+// each with its own copy of the list, states and pairs) in global memory.
+// Chains and the inner pair of an interior loop are elements of their own, so
+// that their state choices branch as well.
 #pragma once
 #include "cf_mfe.cuh"
 
@@ -256,8 +258,150 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
   return mclamp(v);
 }
 
+// Lower bounds for groups of alternatives.  An element's index space splits
+// into contiguous groups (a QB element: the stack, each bulge (L, side), the
+// multiloop, the hairpin, each interior shape (l1, l2); a paired exterior
+// element: each start kk of the last branch; a last multiloop branch: each
+// kk), and each group has a lower bound on its alternatives' costs from
+// per-cell minima of the tables, so that a group above the limit is skipped
+// without evaluating its alternatives.  The minima are exact minima over a
+// cell's 36 entries (or a position's), so a bound is never above a cost.
+struct SubMins {
+  mq *QB, *CH, *XI, *GP;  // [ncells]
+  mq *tau, *chie;         // [n]: min of tau_p; min of chi_p over the XPP and XUP transitions
+  mq *q5;                 // [n][6]: min over s and both tables of Q5U/Q5P[p][a0][s]
+};
+
+// one thread per cell, the first n threads also per position
+__global__ void k_sub_mins(MfeDP p, SubMins mn) {
+  const int n = p.n;
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncells(n)) {
+    const mq *qb = p.QB + c * BLK, *ch = p.CH + c * BLK, *xi = p.XI + c * BLK, *gp = p.GP + c * BLK;
+    mq a = MQINF, b = MQINF, x = MQINF, g = MQINF;
+    for (int e = 0; e < BLK; e++) {
+      a = mmin(a, qb[e]);
+      b = mmin(b, ch[e]);
+      x = mmin(x, xi[e]);
+      g = mmin(g, gp[e]);
+    }
+    mn.QB[c] = mclamp(a);
+    mn.CH[c] = mclamp(b);
+    mn.XI[c] = mclamp(x);
+    mn.GP[c] = mclamp(g);
+  }
+  if (c < (size_t)n) {
+    const mq *t = p.tau + c * BLK, *ch = p.chi + c * 4 * BLK;
+    mq a = MQINF, e2 = MQINF;
+    for (int e = 0; e < BLK; e++) {
+      a = mmin(a, t[e]);
+      e2 = mmin(e2, mmin(ch[XPP * BLK + e], ch[XUP * BLK + e]));
+    }
+    mn.tau[c] = mclamp(a);
+    mn.chie[c] = mclamp(e2);
+    for (int a0 = 0; a0 < NS; a0++) {
+      mq v = MQINF;
+      for (int s = 0; s < NS; s++)
+        v = mmin(v, mmin(p.Q5U[c * BLK + a0 * NS + s], p.Q5P[c * BLK + a0 * NS + s]));
+      mn.q5[c * NS + a0] = mclamp(v);
+    }
+  }
+}
+
+constexpr int SG_BULGE0 = 1, SG_ML = 1 + MAXLOOP * 2, SG_HP = SG_ML + 1, SG_IN0 = SG_HP + 1;
+constexpr int SB_IN0 = SB_STACK + SB_BULGE + SB_ML + BLK;  // first interior-loop index of a QB element
+constexpr mq MQ_NOBOUND = -MQINF;
+
+__device__ __forceinline__ bool ext_paired(int4 E) { return (E.x & 255) == MT_EXT && E.y > 0 && ((E.x >> 8) & 255) >= NS; }
+
+__device__ __forceinline__ int el_ngroups(const MfeDP &p, int4 E) {
+  const int kind = E.x & 255;
+  if (kind == MT_QB) return SG_IN0 + NINTERIOR;
+  if (ext_paired(E)) return 1 + max(0, E.y - 4);
+  if (kind == MT_BP) return max(0, E.z - E.y - 8);
+  return 1;
+}
+
+// the group holding index k
+__device__ __forceinline__ int el_group_of(const MfeDP &p, int4 E, int k) {
+  const int kind = E.x & 255;
+  if (kind == MT_QB) {
+    if (k < SB_STACK) return 0;
+    if (k < SB_STACK + SB_BULGE) return SG_BULGE0 + (k - SB_STACK) / BLK;
+    if (k < SB_STACK + SB_BULGE + SB_ML) return SG_ML;
+    if (k < SB_IN0) return SG_HP;
+    return SG_IN0 + (k - SB_IN0) / (BLK * BLK);
+  }
+  if (ext_paired(E)) return k == 0 ? 0 : 1 + (k - 1) / (2 * BLK);
+  if (kind == MT_BP) return k / NS;
+  return 0;
+}
+
+// index range [k0, k1) of group g
+__device__ __forceinline__ void el_group(const MfeDP &p, int4 E, int g, int &k0, int &k1) {
+  const int kind = E.x & 255;
+  if (kind == MT_QB) {
+    if (g == 0) k0 = 0, k1 = SB_STACK;
+    else if (g < SG_ML) k0 = SB_STACK + (g - SG_BULGE0) * BLK, k1 = k0 + BLK;
+    else if (g == SG_ML) k0 = SB_STACK + SB_BULGE, k1 = k0 + SB_ML;
+    else if (g == SG_HP) k0 = SB_STACK + SB_BULGE + SB_ML, k1 = SB_IN0;
+    else k0 = SB_IN0 + (g - SG_IN0) * BLK * BLK, k1 = k0 + BLK * BLK;
+  } else if (ext_paired(E)) {
+    if (g == 0) k0 = 0, k1 = 1;
+    else k0 = 1 + (g - 1) * 2 * BLK, k1 = k0 + 2 * BLK;
+  } else if (kind == MT_BP) {
+    k0 = g * NS, k1 = k0 + NS;
+  } else {
+    k0 = 0, k1 = el_count(p, E);
+  }
+}
+
+// a lower bound on the cost of every alternative of group g (MQ_NOBOUND: none
+// known); `outer` is the QB element's minimum over (u, v) of the closing
+// pair's terms of a hairpin or interior loop
+__device__ __forceinline__ mq el_group_lb(const MfeDP &p, const SubMins &mn, int4 E, int g, mq outer) {
+  const int n = p.n, kind = E.x & 255, a = (E.x >> 8) & 255, x = E.y, y = E.z;
+  const mq *en = p.en;
+  if (kind == MT_QB) {
+    const int i = x, j = y;
+    if (g >= SG_BULGE0 && g < SG_ML) {
+      const int L = 1 + (g - SG_BULGE0) / 2, side = (g - SG_BULGE0) & 1;
+      if (side == 0) {
+        const int l = j - 1 - L;
+        if (l - (i + 1) < 4) return MQINF;
+        return en[EN_BU + L] + mn.tau[i] + mn.QB[cidx(n, i + 1, l)] + mn.CH[cidx(n, l, j)];
+      }
+      const int kk = i + 1 + L;
+      if ((j - 1) - kk < 4) return MQINF;
+      return en[EN_BU + L] + mn.CH[cidx(n, i, kk)] + mn.QB[cidx(n, kk, j - 1)] + mn.tau[j - 1];
+    }
+    if (g >= SG_IN0) {
+      if (outer >= MQHALF) return MQINF;
+      int l1, l2;
+      interior_shape(g - SG_IN0, l1, l2);
+      const int kk = i + 1 + l1, l = j - 1 - l2;
+      if (l - kk < 4) return MQINF;
+      return outer + en[EN_IN + l1 + l2] + mn.CH[cidx(n, i + 1, kk - 1)] + mn.XI[cidx(n, kk - 1, l + 1)] +
+             mn.CH[cidx(n, l + 1, j - 1)];
+    }
+    return MQ_NOBOUND;
+  }
+  if (ext_paired(E)) {
+    if (g == 0) return MQ_NOBOUND;
+    const int kk = g;
+    return mn.q5[(size_t)(kk - 1) * NS + E.z] + mn.chie[kk - 1] + mn.QB[cidx(n, kk, x)];
+  }
+  if (kind == MT_BP) {
+    const int kk = x + 5 + g;
+    return en[EN_EC] + mn.GP[cidx(n, x, kk)] + mn.QB[cidx(n, kk, y)];
+  }
+  (void)a;
+  return MQ_NOBOUND;
+}
+
 struct SubArgs {
   MfeDP p;
+  SubMins mn;
   mq gap;
   int max_out, pcap;
   size_t fsz;             // bytes per frame: header, pending list [pcap], states [n], partners [n]
@@ -296,6 +440,8 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
   const int n = p.n, t = threadIdx.x;
   __shared__ int sfirst, sdepth, sbad, sdone;
   __shared__ long long sfound;
+  __shared__ mq souter;
+  __shared__ int swsum[8], spref[257], sk0[256];  // blockDim.x = 256
   const mq best = *p.best;
   if (t == 0) {
     SubHdr *h = sf_hdr(s, 0);
@@ -329,21 +475,73 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
     const int cur = h->cursor;
     const mq want = el_want(p, E, best);
     const mq limit = want + slack;
-    const int K = el_count(p, E);
-    // the first feasible alternative at or after the cursor
+    const int K = el_count(p, E), G = el_ngroups(p, E), kind = E.x & 255;
+    // a QB element's closing-pair minimum for the hairpin and interior bounds
+    if (t == 0) souter = MQINF;
+    __syncthreads();
+    if (kind == MT_QB && t < BLK) {
+      const int i = E.y, j = E.z, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, u = t / NS, vv = t % NS;
+      const mq o = p.tau[(size_t)i * BLK + a * NS + u] + p.tau[(size_t)(j - 1) * BLK + vv * NS + b] +
+                   p.en[EN_TM + p.base[(i + 1) * NS + u] * 4 + p.base[(j - 1) * NS + vv]];
+      atomicMin(&souter, mclamp(o));
+    }
+    __syncthreads();
+    const mq outer = souter;
+    // the first feasible alternative at or after the cursor: groups in chunks
+    // of one per thread; the live ones (bound within the limit) are packed in
+    // ascending order and their indices scanned one per thread
     int kf = -1;
-    for (int b0 = cur; b0 < K; b0 += blockDim.x) {
-      if (t == 0) sfirst = INT_MAX;
-      __syncthreads();
-      const int k = b0 + t;
-      if (k < K && el_alt(p, E, k, nullptr, nullptr) <= limit) atomicMin(&sfirst, k);
-      __syncthreads();
-      const int fk = sfirst;
-      __syncthreads();
-      if (fk != INT_MAX) {
-        kf = fk;
-        break;
+    const int gcur = cur < K ? el_group_of(p, E, cur) : G;
+    for (int gb = gcur; gb < G && kf < 0; gb += blockDim.x) {
+      const int g = gb + t;
+      int k0 = 0, k1 = 0;
+      if (g < G) {
+        el_group(p, E, g, k0, k1);
+        k0 = max(k0, cur);
+        if (k0 < k1 && el_group_lb(p, s.mn, E, g, outer) > limit) k1 = k0;
       }
+      const int len = max(0, k1 - k0);
+      // exclusive prefix of len over the block (warp scans, then the warp totals)
+      int incl = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if ((t & 31) >= o) incl += v;
+      }
+      if ((t & 31) == 31) swsum[t >> 5] = incl;
+      __syncthreads();
+      int wbase = 0, total = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        if (w < (t >> 5)) wbase += swsum[w];
+        total += swsum[w];
+      }
+      const int excl = wbase + incl - len;
+      spref[t] = excl;
+      sk0[t] = k0;
+      if (t == 0) spref[blockDim.x] = total;
+      __syncthreads();
+      for (int v0 = 0; v0 < total; v0 += blockDim.x) {
+        if (t == 0) sfirst = INT_MAX;
+        __syncthreads();
+        const int v = v0 + t;
+        if (v < total) {
+          int lo = 0, hi = blockDim.x;  // the last slot with spref <= v
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (spref[mid] <= v) lo = mid;
+            else hi = mid;
+          }
+          const int k = sk0[lo] + (v - spref[lo]);
+          if (el_alt(p, E, k, nullptr, nullptr) <= limit) atomicMin(&sfirst, k);
+        }
+        __syncthreads();
+        const int fk = sfirst;
+        __syncthreads();
+        if (fk != INT_MAX) {
+          kf = fk;
+          break;
+        }
+      }
+      __syncthreads();  // spref / sk0 reused by the next chunk
     }
     if (kf < 0) {  // no more alternatives: back to the parent
       if (t == 0) sdepth = depth - 1;

@@ -1360,12 +1360,22 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   if (e == cudaSuccess) e = dalloc(tmp, &a.partner, (size_t)std::max(max_out, 1) * n);
   if (e == cudaSuccess) e = dalloc(tmp, &a.cost, (size_t)std::max(max_out, 1));
   if (e == cudaSuccess) e = dalloc(tmp, &a.count, (size_t)2);
+  const size_t nc = ncells(n);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.QB, nc);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.CH, nc);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.XI, nc);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.GP, nc);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.tau, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.chie, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.mn.q5, (size_t)n * NS);
   if (e != cudaSuccess) {
     release();
     return cuda_fail(p, e, "cf_subopt: scratch");
   }
-  k_mfe_subopt<<<1, 256, 0, st>>>(a);
+  k_sub_mins<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(t.dp, a.mn);
   e = cudaGetLastError();
+  if (e == cudaSuccess) k_mfe_subopt<<<1, 256, 0, st>>>(a);
+  if (e == cudaSuccess) e = cudaGetLastError();
   long long cnt[2] = {0, 0};
   int err = 0;
   long long best = 0;

@@ -491,7 +491,7 @@ def bench_subopt(stream):
         cnt, cost, _, _ = f.subopt(gap, 10_000)
         ms = cf.cf_mfe_last_ms(f.prob)
         k = min(cnt, 10_000)
-        out[f"gap_{gap}"] = {"count": cnt, "truncated": cnt > 10_000, "ms": ms,
+        out[f"gap_{gap}"] = {"count": cnt, "truncated": cnt > 10_000, "ms": ms, "steps": cf.cf_subopt_steps(f.prob),
                              "configs_per_s": k / max(ms - ms_tables, 1e-3) * 1e3,
                              "cost_span_kcal": float((cost.max() - cost.min()) / 2**32) if k else 0.0}
     f.close()

@@ -207,6 +207,9 @@ float cf_mfe_last_ms(const cf_problem *prob);
  */
 cf_status cf_subopt(cf_problem *prob, double gap_kcal, int max_out, int64_t *cost, int32_t *codons,
                     int32_t *partner, int *count);
+/* Element expansions (search steps) of the last successful cf_subopt; 0 for
+ * a NULL problem or before the first call. */
+long long cf_subopt_steps(const cf_problem *prob);
 
 /*
  * Position-state layout (paper Eq. single-tt, Section "Incorporating hard

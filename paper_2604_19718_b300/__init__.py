@@ -88,6 +88,8 @@ def _load() -> ctypes.CDLL:
         getattr(lib, name).restype = ctypes.c_int
     lib.cf_mfe_last_ms.argtypes = [vp]
     lib.cf_mfe_last_ms.restype = ctypes.c_float
+    lib.cf_subopt_steps.argtypes = [vp]
+    lib.cf_subopt_steps.restype = ctypes.c_longlong
     lib.cf_subopt.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_int)]
     lib.cf_subopt.restype = ctypes.c_int
     lib.cf_set_layout.argtypes = [vp, ctypes.c_int]
@@ -279,6 +281,11 @@ def cf_checkpointed(prob) -> bool:
 
 def cf_mfe_last_ms(prob) -> float:
     return float(lib.cf_mfe_last_ms(prob))
+
+
+def cf_subopt_steps(prob) -> int:
+    """Search steps (element expansions) of the last cf_subopt."""
+    return int(lib.cf_subopt_steps(prob))
 
 
 def cf_subopt(prob, m: int, n: int, gap_kcal: float, max_out: int):

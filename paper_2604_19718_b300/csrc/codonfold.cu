@@ -201,6 +201,7 @@ struct cf_problem {
   float t_win = 0;
   MfeTables mfe;
   float t_mfe = 0;
+  long long sub_steps = 0;  // element expansions of the last cf_subopt
   // position-state layout: 0 codon states (codon-pair tensor train), 1 the
   // single-codon layout (first base; first and second base; third base)
   int layout_req = 0, layout = 0;
@@ -1398,6 +1399,7 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   if (best >= MQHALF) return fail(p, CF_ENUMERIC, "cf_subopt: no configuration has a finite cost");
   if (err) return fail(p, CF_ENUMERIC, "cf_subopt: enumeration inconsistency (error word " + std::to_string(err) + ")");
   *count = (int)std::min<long long>(cnt[0], (long long)max_out + 1);
+  p->sub_steps = cnt[1];
   return CF_OK;
 }
 
@@ -1881,6 +1883,7 @@ cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons
 }
 
 float cf_mfe_last_ms(const cf_problem *p) { return p ? p->t_mfe : 0.f; }
+long long cf_subopt_steps(const cf_problem *p) { return p ? p->sub_steps : 0; }
 
 cf_status cf_subopt(cf_problem *p, double gap_kcal, int max_out, int64_t *cost, int32_t *codons, int32_t *partner,
                     int *count) {

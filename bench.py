@@ -517,12 +517,13 @@ def bench_frequency(stream):
             "r_tol": 0.002, "anderson_depth": 5}
 
 
-def tm_flops(res, gamma):
+def tm_flops(states, gamma):
     """Algorithmic flops of the tensor-model recursion (2 per FMA) with the
-    protein's actual block sides gamma * M_p: per cell [i, j+1) the unpaired
+    protein's actual block sides gamma * M_p (M_p = states[p], the states of
+    position p in the layout used): per cell [i, j+1) the unpaired
     extension Q[i, j] X_j and one block product per split point k = i..j-4,
     per pair (k, j) the two transfer products of the fold and its traces."""
-    M = codon_counts(res).astype(np.float64) * gamma
+    M = np.asarray(states, dtype=np.float64) * gamma
     n = M.size
     C = np.concatenate([[0.0], np.cumsum(M)])  # C[q] = sum of M[0..q-1]
     tot = 0.0
@@ -560,11 +561,29 @@ def bench_tm(stream):
         f.close()
         n = 3 * m
         cells = n * (n + 1) / 2
-        fl = tm_flops(res, 4)
+        fl = tm_flops(codon_counts(res), 4)
         out[f"m{m}"] = {"nt": n, "fp32_ms": ms32, "fp64_ms": ms64, "cells_per_s_fp32": cells / (ms32 * 1e-3),
                         "algorithmic_tflops_fp32": fl / (ms32 * 1e-3) / 1e12,
                         "abs_dlogZ_fp32_vs_fp64": abs(l32 - l64), "rel_dlogZ": abs(l32 - l64) / abs(l64),
                         "logZ": l64}
+    # the 900-nt prefix in the single-codon layout (paper Eq. single-tt)
+    res = res_all[:300]
+    f = cf.CodonFold(synth.nn_params(0), stream=stream)
+    cf.cf_set_layout(f.prob, 1)
+    f.set_protein(res)
+    f.tm_inside(model, cf.CF_FP32_SCALED)
+    l32 = f.tm_inside(model, cf.CF_FP32_SCALED)
+    ms32 = cf.cf_tm_last_ms(f.prob)
+    f.tm_inside(model, cf.CF_FP64)
+    l64 = f.tm_inside(model, cf.CF_FP64)
+    ms64 = cf.cf_tm_last_ms(f.prob)
+    _, st = cf.cf_layout_states(f.prob, f.n)
+    f.close()
+    fl = tm_flops(st, 4)
+    out["m300_single_codon"] = {"nt": 900, "states_per_position": float(np.mean(st)), "fp32_ms": ms32, "fp64_ms": ms64,
+                                "algorithmic_tflops_fp32": fl / (ms32 * 1e-3) / 1e12,
+                                "abs_dlogZ_vs_codon_states": abs(l64 - out["m300"]["logZ"]),
+                                "abs_dlogZ_fp32_vs_fp64": abs(l32 - l64)}
     model.close()
     return out
 
@@ -622,7 +641,7 @@ def bench_large(stream, nsamples=10_000):
             "samples": nsamples, "samples_per_s": nsamples / ts, "launches": lin + lout}
 
 
-def profile_form(form, steps):
+def profile_form(form, steps, m=0):
     """One form on a small case, repeated `steps` times (profiler captures)."""
     import torch
 
@@ -655,12 +674,12 @@ def profile_form(form, steps):
                 f.outside(False, True, False)
                 out["ms"] = f.timing()[:2]
         f.close()
-    elif form == "tm":  # the tensor-model pass on the first 100 residues (300 nt)
+    elif form == "tm":  # the tensor-model pass on the first 100 residues (300 nt), or the first m
         V, B, S = synth.tm_params(0, 4, 2)
         model = cf.TensorModel(V, B, S)
         res, _, _ = synth.workload(WORKLOAD)
         f = cf.CodonFold(params)
-        f.set_protein(res[:100])
+        f.set_protein(res[:m or 100])
         for _ in range(steps):
             f.tm_inside(model, cf.CF_FP32_SCALED)
         out["ms"] = cf.cf_tm_last_ms(f.prob)
@@ -696,7 +715,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_form:
-        return profile_form(args.profile_form, args.steps)
+        return profile_form(args.profile_form, args.steps, args.m)
     if not args.profile:
         args.warmup = max(args.warmup, 3)
 

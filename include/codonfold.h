@@ -267,8 +267,9 @@ cf_status cf_layout_states(const cf_problem *prob, int *layout, int *states);
  *   exponents.  Tables of about 3 x n(n+1)/2 x 576 values of the precision
  *   are allocated on the first call for a protein and freed with it.  Errors:
  *   CF_EINVAL (NULL, unknown precision, model on another device, a batch),
- *   CF_ESTATE (no protein), CF_ENUMERIC (non-finite or zero Z), CF_ENOMEM,
- *   CF_ECUDA.
+ *   CF_ESTATE (no protein), CF_ENUMERIC (non-finite or zero Z), CF_ETIMEOUT
+ *   (a bounded wait for staged blocks gave up; the problem stays usable),
+ *   CF_ENOMEM, CF_ECUDA.
  * cf_tm_last_ms: device time of the last cf_tm_inside.
  */
 typedef struct cf_tm_model cf_tm_model;

@@ -182,31 +182,58 @@ __device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
 // qs = t % 6 at j (its four zeta'), so that a block product reads 16-byte
 // rows: per state b of the summation index, one 4-vector of the left block
 // and four of the right block give 16 FMAs; the summation runs over the real
-// states of the split point only.  The split points are staged tm_kc at a
-// time through two buffers of dynamic shared memory.
+// states of the split point only, and rows past the real states of i are
+// left at zero.  The split points come tm_kc at a time (a group) through a
+// pipeline of up to TM_NST stages of dynamic shared memory: thread 0 copies
+// a group's blocks with one bulk copy each, of their real rows only (4 M_i
+// rows of L[i, k], 4 M_k rows of F[k, j]), completing on the stage's
+// mbarrier, and refills a stage once the block has finished with it.
 constexpr int TM_NC = TM_D * NS;  // 144 threads
+constexpr int TM_NST = 8;         // most pipeline stages of a CTA
 template <typename T>
 __host__ __device__ constexpr int tm_kc() {
-  return sizeof(T) == sizeof(float) ? 4 : 2;  // 8 was slower at 900 nt (125 registers)
+  return sizeof(T) == sizeof(float) ? 4 : 2;  // 18 KB per stage in both precisions
 }
+template <typename T>
+__host__ __device__ constexpr size_t tm_stage_bytes() {
+  return (size_t)2 * tm_kc<T>() * TM_BLK * sizeof(T);
+}
+// Stages of the launch for the cells of length len (n - len + 1 CTAs): as
+// many as keep all its CTAs resident at once within about 200 KB of shared
+// memory per SM (148 SMs), at least one, at most TM_NST and its number of
+// groups.  Few long cells get a deep pipeline each, many short ones more CTAs.
+template <typename T>
+inline int tm_cell_stages(int n, int len) {
+  const int ns = len - 5;  // split points k = i+1 .. i+len-5
+  if (ns <= 0) return 0;
+  const int ng = (ns + tm_kc<T>() - 1) / tm_kc<T>();
+  const int per_sm = (n - len + 1 + 147) / 148;
+  const long long budget = 200 * 1024 / per_sm - 1024 - (long long)(2 * TM_BLK + BLK) * sizeof(T);
+  const int fit = (int)std::max(1ll, budget / (long long)tm_stage_bytes<T>());
+  return std::min(std::min(fit, TM_NST), ng);
+}
+// the most dynamic shared memory a launch takes (at most 200 KB of stages)
 template <typename T>
 __host__ __device__ constexpr size_t tm_cell_smem() {
-  return (size_t)2 * 2 * tm_kc<T>() * TM_BLK * sizeof(T);
+  return (size_t)(TM_NST < 200 * 1024 / tm_stage_bytes<T>() ? TM_NST : 200 * 1024 / tm_stage_bytes<T>()) *
+         tm_stage_bytes<T>();
 }
 template <typename T>
-__global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len) {
+__global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len, int nst) {
   const int n = a.n, i = blockIdx.x, t = threadIdx.x;
   const int j = i + len - 1;  // the new last base
   const int r = t / NS, qs = t % NS;
   constexpr int KC = tm_kc<T>();
-  extern __shared__ __align__(16) unsigned char tm_smem[];  // [2][KC] blocks of L, then of F
-  T(*sL)[KC][TM_BLK] = reinterpret_cast<T(*)[KC][TM_BLK]>(tm_smem);
-  T(*sF)[KC][TM_BLK] = reinterpret_cast<T(*)[KC][TM_BLK]>(tm_smem + (size_t)2 * KC * TM_BLK * sizeof(T));
+  extern __shared__ __align__(128) unsigned char tm_smem[];  // [nst] stages: KC blocks of L, then KC of F
   __shared__ __align__(16) T q[TM_BLK];
   __shared__ __align__(16) T x[TM_BLK];
-  __shared__ T tq[BLK], sFac[2][KC];
-  __shared__ int sEL, sMk[2][KC];
+  __shared__ T tq[BLK], sFac[TM_NST][KC];
+  __shared__ int sEL, sMk[TM_NST][KC];
   __shared__ T smx[(TM_NC + 31) / 32];
+  __shared__ __align__(8) unsigned long long sbar[TM_NST];
+  const int Mi = a.Mp[i];
+  const bool live = r < TM_G * Mi;  // a real row of the output
+  const int k0 = i + 1, k1 = j - 4, ng = k1 >= k0 ? (k1 - k0 + KC) / KC : 0;
   // this length's exponent from the largest mantissa of length len - 1
   if (t == 0) {
     const double mx = __longlong_as_double((long long)__ldcg(a.dmax + len - 1));
@@ -217,7 +244,48 @@ __global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len) {
     }
     sEL = e;
     if (i == 0) a.E[len] = e;
+    for (int s = 0; s < nst; s++) mbar_init(&sbar[s], 1);
   }
+  __syncthreads();
+  const int EL = sEL;
+  // group g of split points into stage s: per split point its factor
+  // 2^{E[k-i] + E[j-k-1] - E[len]} and state count (fetched ahead into
+  // registers by fetch, so that the refill after a group does not wait on
+  // them), then one bulk copy per block
+  int pm[KC], pe[KC];
+  auto fetch = [&](int g) {
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      const int k = k0 + g * KC + u;
+      pm[u] = k <= k1 ? __ldg(a.Mp + k) : 0;
+      pe[u] = k <= k1 ? __ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) : 0;
+    }
+  };
+  auto issue = [&](int g, int s) {
+    T *sL = reinterpret_cast<T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
+    T *sF = sL + (size_t)KC * TM_BLK;
+    unsigned bytes = 0;
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      sMk[s][u] = pm[u];
+      sFac[s][u] = pm[u] ? clamp_p2<T>(pe[u] - EL) : (T)0;
+      if (pm[u]) bytes += (unsigned)((Mi + pm[u]) * TM_G * TM_D * sizeof(T));
+    }
+    mbar_arrive_expect(&sbar[s], bytes);
+#pragma unroll
+    for (int u = 0; u < KC; u++) {
+      const int k = k0 + g * KC + u;
+      if (!pm[u]) continue;
+      bulk_g2s(sL + (size_t)u * TM_BLK, a.L + tm_cell(n, i, k - i), (unsigned)(Mi * TM_G * TM_D * sizeof(T)), &sbar[s]);
+      bulk_g2s(sF + (size_t)u * TM_BLK, a.F + cidx(n, k, j) * TM_BLK, (unsigned)(pm[u] * TM_G * TM_D * sizeof(T)),
+               &sbar[s]);
+    }
+  };
+  if (t == 0)
+    for (int g = 0; g < nst && g < ng; g++) {
+      fetch(g);
+      issue(g, g);
+    }
   // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1), four entries per thread
   const int Mj1 = a.Mp[j - 1], Mj = a.Mp[j];
   {
@@ -233,9 +301,8 @@ __global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len) {
     st4(q + 4 * t, v4);
   }
   __syncthreads();
-  const int EL = sEL;
   T acc[4] = {0, 0, 0, 0};
-  {
+  if (live) {
     for (int b = 0; b < Mj1; b++) {  // states at j - 1
       T l4[4];
       ld4(l4, q + r * TM_D + 4 * b);
@@ -250,77 +317,61 @@ __global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len) {
     const T f = clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
 #pragma unroll
     for (int z = 0; z < 4; z++) acc[z] *= f;
-  }
-  // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
-  if (j - i >= 4) {
-    T f4[4];
-    ldcg4(f4, a.F + cidx(n, i, j) * TM_BLK + r * TM_D + 4 * qs);
-    const T f = clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
+    // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
+    if (j - i >= 4) {
+      T f4[4];
+      ldcg4(f4, a.F + cidx(n, i, j) * TM_BLK + r * TM_D + 4 * qs);
+      const T fe = clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
 #pragma unroll
-    for (int z = 0; z < 4; z++) acc[z] = fma(f4[z], f, acc[z]);
-  }
-  // k = i+1 .. j-4: L[i, k] F[k, j], KC split points per step; the next
-  // step's blocks are loaded into registers before this step's products and
-  // stored to the other buffer after them
-  const int k0 = i + 1, k1 = j - 4;
-  T nl[KC][4], nf[KC][4];
-  auto load = [&](int kb) {
-#pragma unroll
-    for (int u = 0; u < KC; u++) {
-      const int k = kb + u;
-      if (k <= k1) {
-        ldcg4(nl[u], a.L + tm_cell(n, i, k - i) + 4 * t);
-        ldcg4(nf[u], a.F + cidx(n, k, j) * TM_BLK + 4 * t);
-      } else {
-#pragma unroll
-        for (int z = 0; z < 4; z++) nl[u][z] = nf[u][z] = (T)0;
-      }
+      for (int z = 0; z < 4; z++) acc[z] = fma(f4[z], fe, acc[z]);
     }
-  };
-  auto store = [&](int buf, int kb) {
-#pragma unroll
-    for (int u = 0; u < KC; u++) {
-      st4(&sL[buf][u][4 * t], nl[u]);
-      st4(&sF[buf][u][4 * t], nf[u]);
-    }
-    if (t < KC) {  // the split point's factor 2^{E[k-i] + E[j-k-1] - E[len]} and state count
-      const int k = kb + t;
-      sFac[buf][t] = k <= k1 ? clamp_p2<T>(__ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) - EL) : (T)0;
-      sMk[buf][t] = k <= k1 ? a.Mp[k] : 0;
-    }
-  };
-  if (k0 <= k1) {
-    load(k0);
-    store(0, k0);
   }
-  __syncthreads();
-  int buf = 0;
-  for (int kb = k0; kb <= k1; kb += KC, buf ^= 1) {
-    const bool more = kb + KC <= k1;
-    if (more) load(kb + KC);
+  // k = i+1 .. j-4: L[i, k] F[k, j], one group of KC split points per stage.
+  // Each thread waits for the stage's copies itself; the one block barrier
+  // per group frees the stage for its refill and agrees on giving up after
+  // a wait that ran out.
+  for (int g = 0; g < ng; g++) {
+    const int s = g % nst;
+    const unsigned par = (unsigned)(g / nst) & 1u;
+    const bool refill = t == 0 && g + nst < ng;
+    if (refill) fetch(g + nst);
+    const bool ok = mbar_wait(&sbar[s], par, a.err);
+    if (live && ok) {
+      const T *sL = reinterpret_cast<const T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
+      const T *sF = sL + (size_t)KC * TM_BLK;
 #pragma unroll
-    for (int u = 0; u < KC; u++) {
-      const T *Lb = sL[buf][u], *Fb = sF[buf][u];
-      const int Mk = sMk[buf][u];
-      T s[4] = {0, 0, 0, 0};
-      for (int b = 0; b < Mk; b++) {
-        T l4[4];
-        ld4(l4, Lb + r * TM_D + 4 * b);
+      for (int u = 0; u < KC; u++) {
+        const T *Lb = sL + (size_t)u * TM_BLK, *Fb = sF + (size_t)u * TM_BLK;
+        const int Mk = sMk[s][u];
+        T sm[4] = {0, 0, 0, 0};
+        for (int b = 0; b < Mk; b++) {
+          T l4[4];
+          ld4(l4, Lb + r * TM_D + 4 * b);
 #pragma unroll
-        for (int z1 = 0; z1 < 4; z1++) {
-          T f4[4];
-          ld4(f4, Fb + (4 * b + z1) * TM_D + 4 * qs);
+          for (int z1 = 0; z1 < 4; z1++) {
+            T f4[4];
+            ld4(f4, Fb + (4 * b + z1) * TM_D + 4 * qs);
 #pragma unroll
-          for (int z = 0; z < 4; z++) s[z] = fma(l4[z1], f4[z], s[z]);
+            for (int z = 0; z < 4; z++) sm[z] = fma(l4[z1], f4[z], sm[z]);
+          }
         }
-      }
-      const T f = sFac[buf][u];
+        const T f = sFac[s][u];
 #pragma unroll
-      for (int z = 0; z < 4; z++) acc[z] = fma(s[z], f, acc[z]);
+        for (int z = 0; z < 4; z++) acc[z] = fma(sm[z], f, acc[z]);
+      }
     }
-    if (more) store(buf ^ 1, kb + KC);
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      // give up: every other stage still in flight lands before the CTA exits
+      if (t == 0)
+        for (int h = g + 1; h < ng && h < g + nst; h++) mbar_wait(&sbar[h % nst], (unsigned)(h / nst) & 1u, a.err);
+      return;
+    }
+    if (refill) {
+      fence_proxy_async();
+      issue(g + nst, s);
+    }
   }
+  __syncthreads();  // every thread is past its reads of q (lengths 2..5 have no split-point loop)
   st4(a.Q + tm_cell(n, i, len) + r * TM_D + 4 * qs, acc);
   st4(q + r * TM_D + 4 * qs, acc);
   // the largest |mantissa| of this length

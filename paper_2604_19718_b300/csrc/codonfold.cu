@@ -2083,7 +2083,8 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
       k_tm_init<T><<<n, TM_NT, 0, cs>>>(a);
       for (int len = 2; len <= n; len++) {
         if (len - 1 >= 4) k_tm_fold<T><<<n - (len - 1), TM_NT, 0, cs>>>(a, len);
-        k_tm_cell<T><<<n - len + 1, TM_NC, tm_cell_smem<T>(), cs>>>(a, len);
+        const int nst = tm_cell_stages<T>(n, len);
+        k_tm_cell<T><<<n - len + 1, TM_NC, (size_t)nst * tm_stage_bytes<T>(), cs>>>(a, len, nst);
       }
       k_tm_finish<T><<<1, 32, 0, cs>>>(a);
       e = cudaStreamEndCapture(cs, &g);
@@ -2104,6 +2105,7 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
   CF_CUDA(p, cudaMemcpyAsync(&err, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(p, cudaStreamSynchronize(st));
   CF_CUDA(p, cudaEventElapsedTime(&p->t_tm, p->ev[0], p->ev[1]));
+  if (err & ERR_STAGE_TIMEOUT) return fail(p, CF_ETIMEOUT, "cf_tm_inside: a bounded wait for staged inputs gave up");
   if (err || !std::isfinite(lz))
     return fail(p, CF_ENUMERIC, "cf_tm_inside: non-finite or zero partition function (try CF_FP64)");
   *logZ = lz;

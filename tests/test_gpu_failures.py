@@ -58,6 +58,30 @@ def test_wait_timeout_then_reuse(prec):
     assert np.abs(cm - o["codon"]).max() <= 1e-5
 
 
+def test_tm_wait_timeout_then_reuse():
+    """The tensor-model cell kernel's bounded waits for its staged blocks."""
+    from oracle import tensor_model as tm
+    cf = _cf()
+    V, B, S = synth.tm_params(1, 3, 2)
+    res = [4, 12, 0, 17, 9, 2]
+    model = cf.TensorModel(V, B, S)
+    f = cf.CodonFold(P0)
+    f.set_protein(res)
+    try:
+        cf.cf_debug_set_wait_polls(0, 0)
+        for prec in (cf.CF_FP32_SCALED, cf.CF_FP64):
+            with pytest.raises(cf.CFError) as e:
+                f.tm_inside(model, prec)
+            assert e.value.status == cf.CF_ETIMEOUT
+    finally:
+        cf.cf_debug_set_wait_polls(0, cf.WAIT_POLLS_DEFAULT)
+    Vn, Bn = tm.normalize(V, B)
+    ref = tm.logz(Vn, Bn, S, res)
+    assert abs(f.tm_inside(model, cf.CF_FP64) - ref) <= 1e-11 * abs(ref)
+    f.close()
+    model.close()
+
+
 def test_forced_allocation_failures_leave_problem_usable():
     cf = _cf()
     res, lw, pb = _case()

@@ -8,7 +8,10 @@ against the oracle (oracle/tensor_model.py, pinned in tests/test_tm_oracle.py):
   ragged last step);
 * the renormalisation's radii equal the eigenvalue routine's;
 * new codon weights on the same problem (cf_set_weights) give the oracle's
-  value for them; a repeated call gives the same bits; the argument checks.
+  value for them; a repeated call gives the same bits; the argument checks;
+* at 450 nt (more cells per length than one wave of CTAs): repeated calls
+  give the same bits in both precisions, binary32 agrees with binary64, and
+  both layouts give the same binary64 log Z.
 Tolerances: binary64 1e-11 relative (the recursion's sums in another
 order); binary32 1e-6 relative to max(1, |log Z|) (the accuracy bar of the
 nearest-neighbour path)."""
@@ -78,6 +81,31 @@ def test_40_residues_and_new_weights():
     assert abs(f.tm_inside(model, cf.CF_FP64) - ref2) <= 1e-11 * abs(ref2)
     f.close()
     model.close()
+
+
+def test_450_nt_repeatable_and_layout_independent():
+    """At 150 residues each length's launch has more cells than one wave of
+    CTAs; the binary64 log Z repeats to the bit, binary32 agrees within the
+    bar, and the single-codon layout gives the same binary64 log Z (exact
+    arithmetic on the same sums, up to rounding order)."""
+    cf = _cf()
+    V, B, S = synth.tm_params(0, 4, 2)
+    model = cf.TensorModel(V, B, S)
+    res = synth.residues_dirichlet(150, 1)
+    out = {}
+    for layout in (0, 1):
+        f = cf.CodonFold(P0)
+        cf.cf_set_layout(f.prob, layout)
+        f.set_protein(res)
+        a = f.tm_inside(model, cf.CF_FP64)
+        assert f.tm_inside(model, cf.CF_FP64) == a
+        b = f.tm_inside(model, cf.CF_FP32_SCALED)
+        assert f.tm_inside(model, cf.CF_FP32_SCALED) == b
+        f.close()
+        assert abs(a - b) <= 1e-6 * abs(a)
+        out[layout] = a
+    model.close()
+    assert abs(out[0] - out[1]) <= 1e-11 * abs(out[0])
 
 
 def test_radius_and_argument_checks():

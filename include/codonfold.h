@@ -199,12 +199,14 @@ float cf_mfe_last_ms(const cf_problem *prob);
  * there are more (the enumeration stops there).  The MFE tables are
  * computed on the device and one CTA enumerates, for at most 30 s of device
  * time or 5e7 steps (else CF_ENUMERIC; a smaller gap or max_out keeps it
- * short); cf_mfe_last_ms reports the time.  Errors: CF_EINVAL (NULL problem
- * or count, gap < 0 or > 1e6,
- * max_out < 0, device outputs, the single-codon layout), CF_ESTATE (no
- * protein), CF_ENUMERIC (no finite configuration, an inconsistency),
- * CF_ENOMEM, CF_ECUDA.
+ * short); cf_mfe_last_ms reports the time.  The search keeps the states
+ * and partners of the configuration it builds (8 n bytes) and its 512
+ * deepest frames in shared memory, hence n <= CF_SUBOPT_MAX_N.  Errors: CF_EINVAL (NULL problem or count,
+ * gap < 0 or > 1e6, max_out < 0, device outputs, the single-codon layout,
+ * n > CF_SUBOPT_MAX_N), CF_ESTATE (no protein), CF_ENUMERIC (no finite
+ * configuration, an inconsistency), CF_ENOMEM, CF_ECUDA.
  */
+#define CF_SUBOPT_MAX_N 20000
 cf_status cf_subopt(cf_problem *prob, double gap_kcal, int max_out, int64_t *cost, int32_t *codons,
                     int32_t *partner, int *count);
 /* Element expansions (search steps) of the last successful cf_subopt; 0 for

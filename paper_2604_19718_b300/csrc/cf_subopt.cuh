@@ -74,17 +74,26 @@ __device__ __forceinline__ int el_count(const MfeDP &p, int4 E) {
 }
 
 // Cost of alternative k of E, and (kids != nullptr) its sub-elements in push
-// order (the last one is decomposed first); returns the number of kids.
-__device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
+// order (the last one is decomposed first) with their own table values
+// (kw, the terms of the cost that they stand for); returns the number of kids.
+__device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk, mq *kw = nullptr) {
   const int n = p.n, kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
   const mq *en = p.en;
   int c = 0;
   mq v = MQINF;
+  auto kid = [&](int4 e, mq w) {
+    if (kids) {
+      kids[c] = e;
+      if (kw) kw[c] = w;
+      c++;
+    }
+  };
   switch (kind) {
     case MT_TOP: {  // residue 0's state and the port of position n-1, (a, type, b) ascending
       const int Ml = p.Mp[n - 1], a0 = k / (2 * Ml), r = k % (2 * Ml), tp = r / Ml, bb = r % Ml;
-      v = p.u0[a0] + (tp ? p.Q5P : p.Q5U)[(size_t)(n - 1) * BLK + a0 * NS + bb];
-      if (kids) kids[c++] = el_make(MT_EXT, n - 1, a0, bb + NS * tp, 0);
+      const mq q5 = (tp ? p.Q5P : p.Q5U)[(size_t)(n - 1) * BLK + a0 * NS + bb];
+      v = p.u0[a0] + q5;
+      kid(el_make(MT_EXT, n - 1, a0, bb + NS * tp, 0), q5);
       break;
     }
     case MT_EXT: {
@@ -93,24 +102,23 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
         v = port == a0 ? el_want(p, E, 0) : MQINF;
       } else if (port < NS) {  // j unpaired: (type, state) at j-1
         const int Mp = p.Mp[j - 1], tp = k / Mp, s = k % Mp;
-        v = (tp ? p.Q5P : p.Q5U)[(size_t)(j - 1) * BLK + a0 * NS + s] +
-            p.chi[(size_t)(j - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + port];
-        if (kids) kids[c++] = el_make(MT_EXT, j - 1, a0, s + NS * tp, 0);
+        const mq q5 = (tp ? p.Q5P : p.Q5U)[(size_t)(j - 1) * BLK + a0 * NS + s];
+        v = q5 + p.chi[(size_t)(j - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + port];
+        kid(el_make(MT_EXT, j - 1, a0, s + NS * tp, 0), q5);
       } else {  // j paired: the branch (0, j), then the last branch (kk, j)
         const int bb = port - NS;
         if (k == 0) {
           v = p.QB[cidx(n, 0, j) * BLK + a0 * NS + bb];
-          if (kids) kids[c++] = el_make(MT_QB, 0, j, a0, bb);
+          kid(el_make(MT_QB, 0, j, a0, bb), v);
         } else {
           const int q = k - 1, kk = 1 + q / (2 * NS * NS), r = q % (2 * NS * NS), tp = r / (NS * NS),
                     s1 = (r / NS) % NS, s = r % NS;
           const mq *ch = p.chi + (size_t)(kk - 1) * 4 * BLK;
-          v = (tp ? p.Q5P : p.Q5U)[(size_t)(kk - 1) * BLK + a0 * NS + s1] + ch[(tp ? XPP : XUP) * BLK + s1 * NS + s] +
-              p.QB[cidx(n, kk, j) * BLK + s * NS + bb];
-          if (kids) {
-            kids[c++] = el_make(MT_QB, kk, j, s, bb);
-            kids[c++] = el_make(MT_EXT, kk - 1, a0, s1 + NS * tp, 0);
-          }
+          const mq q5 = (tp ? p.Q5P : p.Q5U)[(size_t)(kk - 1) * BLK + a0 * NS + s1];
+          const mq qb = p.QB[cidx(n, kk, j) * BLK + s * NS + bb];
+          v = q5 + ch[(tp ? XPP : XUP) * BLK + s1 * NS + s] + qb;
+          kid(el_make(MT_QB, kk, j, s, bb), qb);
+          kid(el_make(MT_EXT, kk - 1, a0, s1 + NS * tp, 0), q5);
         }
       }
       break;
@@ -119,8 +127,9 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
       if (x == y) {
         v = a == b ? 0 : MQINF;
       } else {
-        v = p.tau[(size_t)x * BLK + a * NS + k] + p.CH[cidx(n, x + 1, y) * BLK + k * NS + b];
-        if (kids) kids[c++] = el_make(MT_CH, x + 1, y, k, b);
+        const mq cw = p.CH[cidx(n, x + 1, y) * BLK + k * NS + b];
+        v = p.tau[(size_t)x * BLK + a * NS + k] + cw;
+        kid(el_make(MT_CH, x + 1, y, k, b), cw);
       }
       break;
     }
@@ -130,50 +139,55 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
       int q = k;
       if (q < SB_STACK) {  // stack: (a2, b2)
         const int a2 = q / NS, b2 = q % NS;
+        mq qb = MQINF;
         if (d >= 6) {
           const int po = pair_type(p.base[i * NS + a], p.base[j * NS + b]);
           const int pi = pair_type(p.base[(i + 1) * NS + a2], p.base[(j - 1) * NS + b2]);
-          if (po >= 0 && pi >= 0)
-            v = ti[a * NS + a2] + p.QB[cidx(n, i + 1, j - 1) * BLK + a2 * NS + b2] + tj1[b2 * NS + b] +
-                en[EN_STK + po * 6 + pi];
+          if (po >= 0 && pi >= 0) {
+            qb = p.QB[cidx(n, i + 1, j - 1) * BLK + a2 * NS + b2];
+            v = ti[a * NS + a2] + qb + tj1[b2 * NS + b] + en[EN_STK + po * 6 + pi];
+          }
         }
-        if (kids) kids[c++] = el_make(MT_QB, i + 1, j - 1, a2, b2);
+        kid(el_make(MT_QB, i + 1, j - 1, a2, b2), qb);
         break;
       }
       q -= SB_STACK;
       if (q < SB_BULGE) {  // bulges: size L, 3' before 5', then the two free states
         const int L = 1 + q / (2 * BLK), side = (q / BLK) & 1, s1 = (q % BLK) / NS, s2 = q % NS;
+        mq qb = MQINF, cw = MQINF;
         if (side == 0) {
           const int l = j - 1 - L;
-          if (l - (i + 1) >= 4)
-            v = en[EN_BU + L] + ti[a * NS + s1] + p.QB[cidx(n, i + 1, l) * BLK + s1 * NS + s2] +
-                p.CH[cidx(n, l, j) * BLK + s2 * NS + b];
-          if (kids) {
-            kids[c++] = el_make(MT_CH, l, j, s2, b);
-            kids[c++] = el_make(MT_QB, i + 1, l, s1, s2);
+          if (l - (i + 1) >= 4) {
+            qb = p.QB[cidx(n, i + 1, l) * BLK + s1 * NS + s2];
+            cw = p.CH[cidx(n, l, j) * BLK + s2 * NS + b];
+            v = en[EN_BU + L] + ti[a * NS + s1] + qb + cw;
           }
+          kid(el_make(MT_CH, l, j, s2, b), cw);
+          kid(el_make(MT_QB, i + 1, l, s1, s2), qb);
         } else {
           const int kk = i + 1 + L;
-          if ((j - 1) - kk >= 4)
-            v = en[EN_BU + L] + p.CH[cidx(n, i, kk) * BLK + a * NS + s1] + p.QB[cidx(n, kk, j - 1) * BLK + s1 * NS + s2] +
-                tj1[s2 * NS + b];
-          if (kids) {
-            kids[c++] = el_make(MT_CH, i, kk, a, s1);
-            kids[c++] = el_make(MT_QB, kk, j - 1, s1, s2);
+          if ((j - 1) - kk >= 4) {
+            cw = p.CH[cidx(n, i, kk) * BLK + a * NS + s1];
+            qb = p.QB[cidx(n, kk, j - 1) * BLK + s1 * NS + s2];
+            v = en[EN_BU + L] + cw + qb + tj1[s2 * NS + b];
           }
+          kid(el_make(MT_CH, i, kk, a, s1), cw);
+          kid(el_make(MT_QB, kk, j - 1, s1, s2), qb);
         }
         break;
       }
       q -= SB_BULGE;
       if (q < SB_ML) {  // multiloop: (type at i+1, type at j-1, state at i+1, state at j-1)
         const int t1 = q / (2 * BLK), t2 = (q / BLK) & 1, s = (q % BLK) / NS, s2 = q % NS;
+        mq q2 = MQINF;
         if (d >= 11) {
           const mq *cx = p.chi + (size_t)i * 4 * BLK, *cy = p.chi + (size_t)(j - 1) * 4 * BLK;
           const mq *Q2 = t1 ? (t2 ? p.BP : p.M2PU) : (t2 ? p.M2UP : p.M2UU);
-          v = en[EN_EA] + en[EN_EC] + cx[(t1 ? XPP : XPU) * BLK + a * NS + s] +
-              Q2[cidx(n, i + 1, j - 1) * BLK + s * NS + s2] + cy[(t2 ? XPP : XUP) * BLK + s2 * NS + b];
+          q2 = Q2[cidx(n, i + 1, j - 1) * BLK + s * NS + s2];
+          v = en[EN_EA] + en[EN_EC] + cx[(t1 ? XPP : XPU) * BLK + a * NS + s] + q2 +
+              cy[(t2 ? XPP : XUP) * BLK + s2 * NS + b];
         }
-        if (kids) kids[c++] = el_make(t1 ? (t2 ? MT_BP : MT_M2PU) : (t2 ? MT_M2UP : MT_M2UU), i + 1, j - 1, s, s2);
+        kid(el_make(t1 ? (t2 ? MT_BP : MT_M2PU) : (t2 ? MT_M2UP : MT_M2UU), i + 1, j - 1, s, s2), q2);
         break;
       }
       q -= SB_ML;
@@ -182,21 +196,27 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
         const int u = (q % BLK) / NS, vv = q % NS, sh = q / BLK;
         const mq outer = ti[a * NS + u] + tj1[vv * NS + b] + en[EN_TM + p.base[xi * NS + u] * 4 + p.base[yi * NS + vv]];
         if (sh == 0) {
-          if (outer < MQHALF) v = outer + p.hq[d - 1] + p.CH[cidx(n, xi, yi) * BLK + u * NS + vv];
-          if (kids) kids[c++] = el_make(MT_CH, xi, yi, u, vv);
+          mq cw = MQINF;
+          if (outer < MQHALF) {
+            cw = p.CH[cidx(n, xi, yi) * BLK + u * NS + vv];
+            v = outer + p.hq[d - 1] + cw;
+          }
+          kid(el_make(MT_CH, xi, yi, u, vv), cw);
         } else {
           const int qq = (sh - 1) / BLK, w = ((sh - 1) % BLK) / NS, z = (sh - 1) % NS;
           int l1, l2;
           interior_shape(qq, l1, l2);
           const int kk = i + 1 + l1, l = j - 1 - l2;
-          if (outer < MQHALF && l - kk >= 4)
-            v = outer + en[EN_IN + l1 + l2] + p.CH[cidx(n, xi, kk - 1) * BLK + u * NS + w] +
-                p.XI[cidx(n, kk - 1, l + 1) * BLK + w * NS + z] + p.CH[cidx(n, l + 1, yi) * BLK + z * NS + vv];
-          if (kids) {
-            kids[c++] = el_make(MT_CH, xi, kk - 1, u, w);
-            kids[c++] = el_make(MT_CH, l + 1, yi, z, vv);
-            kids[c++] = el_make(MT_XIN, kk - 1, l + 1, w, z);
+          mq c1 = MQINF, xw = MQINF, c2 = MQINF;
+          if (outer < MQHALF && l - kk >= 4) {
+            c1 = p.CH[cidx(n, xi, kk - 1) * BLK + u * NS + w];
+            xw = p.XI[cidx(n, kk - 1, l + 1) * BLK + w * NS + z];
+            c2 = p.CH[cidx(n, l + 1, yi) * BLK + z * NS + vv];
+            v = outer + en[EN_IN + l1 + l2] + c1 + xw + c2;
           }
+          kid(el_make(MT_CH, xi, kk - 1, u, w), c1);
+          kid(el_make(MT_CH, l + 1, yi, z, vv), c2);
+          kid(el_make(MT_XIN, kk - 1, l + 1, w, z), xw);
         }
       }
       break;
@@ -204,18 +224,19 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
     case MT_XIN: {  // the inner pair (x+1, y-1) inside XI[x][y]: states (a2, b2)
       const int a2 = k / NS, b2 = k % NS;
       const mq tmi = en[EN_TM + p.base[y * NS + b] * 4 + p.base[x * NS + a]];
-      v = p.tau[(size_t)x * BLK + a * NS + a2] + p.QB[cidx(n, x + 1, y - 1) * BLK + a2 * NS + b2] +
-          p.tau[(size_t)(y - 1) * BLK + b2 * NS + b] + tmi;
-      if (kids) kids[c++] = el_make(MT_QB, x + 1, y - 1, a2, b2);
+      const mq qb = p.QB[cidx(n, x + 1, y - 1) * BLK + a2 * NS + b2];
+      v = p.tau[(size_t)x * BLK + a * NS + a2] + qb + p.tau[(size_t)(y - 1) * BLK + b2 * NS + b] + tmi;
+      kid(el_make(MT_QB, x + 1, y - 1, a2, b2), qb);
       break;
     }
     case MT_QMP: {  // a branch (x, y), then >= 2 branches
       if (k == 0) {
-        v = en[EN_EC] + p.QB[cidx(n, x, y) * BLK + a * NS + b];
-        if (kids) kids[c++] = el_make(MT_QB, x, y, a, b);
+        const mq qb = p.QB[cidx(n, x, y) * BLK + a * NS + b];
+        v = en[EN_EC] + qb;
+        kid(el_make(MT_QB, x, y, a, b), qb);
       } else {
         v = p.BP[cidx(n, x, y) * BLK + a * NS + b];
-        if (kids) kids[c++] = el_make(MT_BP, x, y, a, b);
+        kid(el_make(MT_BP, x, y, a, b), v);
       }
       break;
     }
@@ -223,34 +244,33 @@ __device__ mq el_alt(const MfeDP &p, int4 E, int k, int4 *kids, int *nk) {
       const bool one = kind == MT_QMU;
       const int tp = k / NS, s = k % NS;
       const mq *Pt = tp ? (one ? p.QMP : p.BP) : (one ? p.QMU : p.M2PU);
-      v = en[EN_EB] + Pt[cidx(n, x, y - 1) * BLK + a * NS + s] +
-          p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + b];
-      if (kids) kids[c++] = el_make(tp ? (one ? MT_QMP : MT_BP) : kind, x, y - 1, a, s);
+      const mq pw = Pt[cidx(n, x, y - 1) * BLK + a * NS + s];
+      v = en[EN_EB] + pw + p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPU : XUU) * BLK + s * NS + b];
+      kid(el_make(tp ? (one ? MT_QMP : MT_BP) : kind, x, y - 1, a, s), pw);
       break;
     }
     case MT_GP: {  // the branch start at y: (type at y-1, state at y-1)
       const int tp = k / NS, s = k % NS;
-      v = (tp ? p.QMP : p.QMU)[cidx(n, x, y - 1) * BLK + a * NS + s] +
-          p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPP : XUP) * BLK + s * NS + b];
-      if (kids) kids[c++] = el_make(tp ? MT_QMP : MT_QMU, x, y - 1, a, s);
+      const mq pw = (tp ? p.QMP : p.QMU)[cidx(n, x, y - 1) * BLK + a * NS + s];
+      v = pw + p.chi[(size_t)(y - 1) * 4 * BLK + (tp ? XPP : XUP) * BLK + s * NS + b];
+      kid(el_make(tp ? MT_QMP : MT_QMU, x, y - 1, a, s), pw);
       break;
     }
     case MT_BP: {  // last branch (kk, y): kk ascending, state at kk
       const int kk = x + 5 + k / NS, s = k % NS;
-      v = en[EN_EC] + p.GP[cidx(n, x, kk) * BLK + a * NS + s] + p.QB[cidx(n, kk, y) * BLK + s * NS + b];
-      if (kids) {
-        kids[c++] = el_make(MT_QB, kk, y, s, b);
-        kids[c++] = el_make(MT_GP, x, kk, a, s);
-      }
+      const mq gw = p.GP[cidx(n, x, kk) * BLK + a * NS + s], qb = p.QB[cidx(n, kk, y) * BLK + s * NS + b];
+      v = en[EN_EC] + gw + qb;
+      kid(el_make(MT_QB, kk, y, s, b), qb);
+      kid(el_make(MT_GP, x, kk, a, s), gw);
       break;
     }
     default: {  // MT_M2UP / MT_M2UU: x unpaired: (type at x+1, state at x+1)
       const bool lastp = kind == MT_M2UP;
       const int tp = k / NS, s = k % NS;
       const mq *Pt = tp ? (lastp ? p.BP : p.M2PU) : (lastp ? p.M2UP : p.M2UU);
-      v = en[EN_EB] + p.chi[(size_t)x * 4 * BLK + (tp ? XUP : XUU) * BLK + a * NS + s] +
-          Pt[cidx(n, x + 1, y) * BLK + s * NS + b];
-      if (kids) kids[c++] = el_make(tp ? (lastp ? MT_BP : MT_M2PU) : kind, x + 1, y, s, b);
+      const mq pw = Pt[cidx(n, x + 1, y) * BLK + s * NS + b];
+      v = en[EN_EB] + p.chi[(size_t)x * 4 * BLK + (tp ? XUP : XUU) * BLK + a * NS + s] + pw;
+      kid(el_make(tp ? (lastp ? MT_BP : MT_M2PU) : kind, x + 1, y, s, b), pw);
       break;
     }
   }
@@ -399,13 +419,32 @@ __device__ __forceinline__ mq el_group_lb(const MfeDP &p, const SubMins &mn, int
   return MQ_NOBOUND;
 }
 
+// One level of the depth-first search.  The pending list lives in one array
+// kept in place: the frame's element was taken from position npend, and its
+// children push their sub-elements from there on; leaving the frame puts the
+// element back at npend, so that the list below a frame is its parent's
+// again (each descendant restores the entry it took in turn).  The element's
+// own decisions (codon states and the pair it fixes) do not depend on the
+// alternative taken, so they are made when the frame is entered and undone
+// (the positions it set, at most four) when it is left.
+struct SubFrame {
+  int4 elem;
+  long long slack;    // what is left of the gap
+  long long want;     // the element's table value
+  int npend, cursor;  // pending elements below it; its next alternative
+  int nch, ch[4];     // positions its decisions set
+};
+
+constexpr int SUB_RING = 512;  // frames kept in shared memory (the deepest ones), the rest in global memory
+
 struct SubArgs {
   MfeDP p;
   SubMins mn;
   mq gap;
   int max_out, pcap;
-  size_t fsz;             // bytes per frame: header, pending list [pcap], states [n], partners [n]
-  unsigned char *frames;  // [depth cap][fsz]
+  int4 *pend;          // [pcap] pending elements
+  mq *pendw;           // [pcap] their table values
+  SubFrame *frames;    // [depth cap] frames pushed out of the ring
   int depth_cap;
   long long max_steps;
   unsigned long long max_ns;  // the enumeration stops (with an error) past this device time
@@ -414,18 +453,10 @@ struct SubArgs {
   long long *count;           // [2]: configurations found (capped at max_out + 1), steps taken
 };
 
-struct SubHdr {
-  int4 elem;
-  long long slack;
-  int npend, cursor;
-};
-
-__device__ __forceinline__ SubHdr *sf_hdr(const SubArgs &s, int f) { return (SubHdr *)(s.frames + (size_t)f * s.fsz); }
-__device__ __forceinline__ int4 *sf_pend(const SubArgs &s, int f) {
-  return (int4 *)(s.frames + (size_t)f * s.fsz + 64);
-}
-__device__ __forceinline__ int *sf_state(const SubArgs &s, int f) {
-  return (int *)(s.frames + (size_t)f * s.fsz + 64 + (size_t)s.pcap * sizeof(int4));
+// dynamic shared memory of k_mfe_subopt: the states and partners (2n ints),
+// then the frame ring and its depth tags
+__host__ __device__ constexpr size_t sub_smem(int n) {
+  return ((size_t)2 * n * sizeof(int) + 15) / 16 * 16 + (size_t)SUB_RING * (sizeof(SubFrame) + sizeof(int));
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -434,32 +465,92 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return v;
 }
 
+// The smallest k over the block for which ok holds (INT_MAX if none), k
+// increasing with the thread index; one block barrier, the per-warp minima
+// double-buffered by round parity.
+__device__ __forceinline__ int block_first(bool ok, int k, int (*swmin)[8], int &par) {
+  const unsigned b = __ballot_sync(0xffffffffu, ok);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kw = b ? __shfl_sync(0xffffffffu, k, __ffs(b) - 1) : INT_MAX;
+  if (lane == 0) swmin[par][w] = kw;
+  __syncthreads();
+  int m = INT_MAX;
+#pragma unroll
+  for (int i = 0; i < 8; i++) m = min(m, swmin[par][i]);
+  par ^= 1;
+  return m;
+}
+
+// The element's own decisions into the states and partners (scs), the
+// positions set recorded in the frame; a position already decided otherwise
+// is an inconsistency (bit 4 of the error).
+__device__ __forceinline__ void el_decide(int n, int4 E, int *scs, SubFrame &f, int &bad) {
+  const int kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
+  f.nch = 0;
+  auto set = [&](int q, int v) {
+    if (scs[q] >= 0) {
+      if (scs[q] != v) bad = 4;
+    } else {
+      scs[q] = v;
+      f.ch[f.nch++] = q;
+    }
+  };
+  switch (kind) {
+    case MT_EXT:
+      if (x == 0) set(0, y);
+      else if (a < NS) set(x, a);
+      break;
+    case MT_CH: set(x, a); break;
+    case MT_QB:
+      set(x, a);
+      set(y, b);
+      set(n + x, y);
+      set(n + y, x);
+      break;
+    case MT_QMU: case MT_M2PU: set(y, b); break;
+    case MT_M2UP: case MT_M2UU: set(x, a); break;
+    default: break;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
   const MfeDP &p = s.p;
   const unsigned long long t0 = global_ns();
   const int n = p.n, t = threadIdx.x;
-  __shared__ int sfirst, sdepth, sbad, sdone;
-  __shared__ long long sfound;
+  extern __shared__ __align__(16) unsigned char sub_smem_raw[];
+  int *scs = reinterpret_cast<int *>(sub_smem_raw);  // [n] state of each position, then [n] partner (-1: not yet)
+  SubFrame *ring = reinterpret_cast<SubFrame *>(sub_smem_raw + ((size_t)2 * n * sizeof(int) + 15) / 16 * 16);
+  int *rtag = reinterpret_cast<int *>(ring + SUB_RING);  // the frame index each ring slot holds
+  __shared__ int sdepth, sbad, sdone, scur, swmin[2][8];
+  __shared__ int4 sE;
+  __shared__ long long sfound, sslack, swant;
   __shared__ mq souter;
   __shared__ int swsum[8], spref[257], sk0[256];  // blockDim.x = 256
   const mq best = *p.best;
+  for (int q = t; q < 2 * n; q += blockDim.x) scs[q] = -1;
+  for (int q = t; q < SUB_RING; q += blockDim.x) rtag[q] = -1;
+  __syncthreads();
   if (t == 0) {
-    SubHdr *h = sf_hdr(s, 0);
-    h->elem = el_make(MT_TOP, 0, 0, 0, 0);
-    h->slack = s.gap;
-    h->npend = 0;
-    h->cursor = 0;
+    SubFrame f0;
+    f0.elem = el_make(MT_TOP, 0, 0, 0, 0);
+    f0.slack = s.gap;
+    f0.want = best;
+    f0.npend = 0;
+    f0.cursor = 0;
+    f0.nch = 0;
+    ring[0] = f0;
+    rtag[0] = 0;
+    sE = f0.elem;
+    sslack = f0.slack;
+    swant = best;
+    scur = 0;
     sdepth = 1;
     sbad = 0;
     sdone = 0;
     sfound = 0;
   }
-  {
-    int *st = sf_state(s, 0);
-    for (int q = t; q < 2 * n; q += blockDim.x) st[q] = -1;
-  }
-  __syncthreads();
   long long steps = 0;
+  int par = 0;
   while (true) {
     __syncthreads();
     const int depth = sdepth;
@@ -468,150 +559,172 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
       if (t == 0) sbad = 2;  // bounded: the other threads see it at the next step
       if (steps > s.max_steps) break;
     }
-    const int f = depth - 1;
-    SubHdr *h = sf_hdr(s, f);
-    const int4 E = h->elem;
-    const long long slack = h->slack;
-    const int cur = h->cursor;
-    const mq want = el_want(p, E, best);
+    const int4 E = sE;
+    const long long slack = sslack;
+    const int cur = scur;
+    const mq want = swant;
     const mq limit = want + slack;
     const int K = el_count(p, E), G = el_ngroups(p, E), kind = E.x & 255;
-    // a QB element's closing-pair minimum for the hairpin and interior bounds
-    if (t == 0) souter = MQINF;
-    __syncthreads();
-    if (kind == MT_QB && t < BLK) {
-      const int i = E.y, j = E.z, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, u = t / NS, vv = t % NS;
-      const mq o = p.tau[(size_t)i * BLK + a * NS + u] + p.tau[(size_t)(j - 1) * BLK + vv * NS + b] +
-                   p.en[EN_TM + p.base[(i + 1) * NS + u] * 4 + p.base[(j - 1) * NS + vv]];
-      atomicMin(&souter, mclamp(o));
-    }
-    __syncthreads();
-    const mq outer = souter;
-    // the first feasible alternative at or after the cursor: groups in chunks
-    // of one per thread; the live ones (bound within the limit) are packed in
-    // ascending order and their indices scanned one per thread
+    // this thread's last evaluated alternative
+    int mk = INT_MAX, mnk = 0;
+    mq mc = MQINF;
+    int4 mkids[3];
+    mq mkw[3];
     int kf = -1;
-    const int gcur = cur < K ? el_group_of(p, E, cur) : G;
-    for (int gb = gcur; gb < G && kf < 0; gb += blockDim.x) {
-      const int g = gb + t;
-      int k0 = 0, k1 = 0;
-      if (g < G) {
-        el_group(p, E, g, k0, k1);
-        k0 = max(k0, cur);
-        if (k0 < k1 && el_group_lb(p, s.mn, E, g, outer) > limit) k1 = k0;
+    if (G == 1) {  // one group: its alternatives one per thread
+      for (int b0 = cur; b0 < K && kf < 0; b0 += blockDim.x) {
+        const int k = b0 + t;
+        bool ok = false;
+        mk = INT_MAX;
+        if (k < K) {
+          mk = k;
+          mc = el_alt(p, E, k, mkids, &mnk, mkw);
+          ok = mc <= limit;
+        }
+        const int fk = block_first(ok, k, swmin, par);
+        if (fk != INT_MAX) kf = fk;
       }
-      const int len = max(0, k1 - k0);
-      // exclusive prefix of len over the block (warp scans, then the warp totals)
-      int incl = len;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if ((t & 31) >= o) incl += v;
-      }
-      if ((t & 31) == 31) swsum[t >> 5] = incl;
-      __syncthreads();
-      int wbase = 0, total = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-        if (w < (t >> 5)) wbase += swsum[w];
-        total += swsum[w];
-      }
-      const int excl = wbase + incl - len;
-      spref[t] = excl;
-      sk0[t] = k0;
-      if (t == 0) spref[blockDim.x] = total;
-      __syncthreads();
-      for (int v0 = 0; v0 < total; v0 += blockDim.x) {
-        if (t == 0) sfirst = INT_MAX;
+    } else {
+      // a QB element's closing-pair minimum for the hairpin and interior bounds
+      if (kind == MT_QB) {
+        if (t == 0) souter = MQINF;
         __syncthreads();
-        const int v = v0 + t;
-        if (v < total) {
-          int lo = 0, hi = blockDim.x;  // the last slot with spref <= v
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (spref[mid] <= v) lo = mid;
-            else hi = mid;
+        if (t < BLK) {
+          const int i = E.y, j = E.z, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, u = t / NS, vv = t % NS;
+          const mq o = p.tau[(size_t)i * BLK + a * NS + u] + p.tau[(size_t)(j - 1) * BLK + vv * NS + b] +
+                       p.en[EN_TM + p.base[(i + 1) * NS + u] * 4 + p.base[(j - 1) * NS + vv]];
+          atomicMin(&souter, mclamp(o));
+        }
+        __syncthreads();
+      }
+      const mq outer = kind == MT_QB ? souter : MQINF;
+      // groups in chunks of one per thread; the live ones (bound within the
+      // limit) are packed in ascending order and their indices scanned one
+      // per thread
+      const int gcur = cur < K ? el_group_of(p, E, cur) : G;
+      for (int gb = gcur; gb < G && kf < 0; gb += blockDim.x) {
+        const int g = gb + t;
+        int k0 = 0, k1 = 0;
+        if (g < G) {
+          el_group(p, E, g, k0, k1);
+          k0 = max(k0, cur);
+          if (k0 < k1 && el_group_lb(p, s.mn, E, g, outer) > limit) k1 = k0;
+        }
+        const int len = max(0, k1 - k0);
+        int incl = len;  // inclusive prefix of len: warp scans, then the warp totals
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((t & 31) >= o) incl += v;
+        }
+        if ((t & 31) == 31) swsum[t >> 5] = incl;
+        __syncthreads();
+        int wbase = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+          if (w < (t >> 5)) wbase += swsum[w];
+          total += swsum[w];
+        }
+        spref[t] = wbase + incl - len;
+        sk0[t] = k0;
+        if (t == 0) spref[blockDim.x] = total;
+        __syncthreads();
+        for (int v0 = 0; v0 < total && kf < 0; v0 += blockDim.x) {
+          const int v = v0 + t;
+          int k = INT_MAX;
+          bool ok = false;
+          mk = INT_MAX;
+          if (v < total) {
+            int lo = 0, hi = blockDim.x;  // the last slot with spref <= v
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (spref[mid] <= v) lo = mid;
+              else hi = mid;
+            }
+            k = sk0[lo] + (v - spref[lo]);
+            mk = k;
+            mc = el_alt(p, E, k, mkids, &mnk, mkw);
+            ok = mc <= limit;
           }
-          const int k = sk0[lo] + (v - spref[lo]);
-          if (el_alt(p, E, k, nullptr, nullptr) <= limit) atomicMin(&sfirst, k);
+          const int fk = block_first(ok, k, swmin, par);
+          if (fk != INT_MAX) kf = fk;
         }
-        __syncthreads();
-        const int fk = sfirst;
-        __syncthreads();
-        if (fk != INT_MAX) {
-          kf = fk;
-          break;
-        }
+        __syncthreads();  // spref / sk0 / swsum reused by the next chunk
       }
-      __syncthreads();  // spref / sk0 reused by the next chunk
     }
-    if (kf < 0) {  // no more alternatives: back to the parent
-      if (t == 0) sdepth = depth - 1;
+    // the search's bookkeeping, by one thread: the one that evaluated the
+    // alternative taken, or thread 0 when none is left (the others wait at
+    // the next step's barrier)
+    const int fi = depth - 1;  // the current frame's index (always in the ring)
+    SubFrame &h = ring[fi % SUB_RING];
+    if (kf < 0) {
+      if (t != 0) continue;
+      for (int c = 0; c < h.nch; c++) scs[h.ch[c]] = -1;
+      if (fi > 0) {
+        s.pend[h.npend] = E;  // the parent's list again
+        s.pendw[h.npend] = want;
+        const int pi = fi - 1, ps = pi % SUB_RING;
+        if (rtag[ps] != pi) {
+          ring[ps] = s.frames[pi];
+          rtag[ps] = pi;
+        }
+        sE = ring[ps].elem;
+        sslack = ring[ps].slack;
+        swant = ring[ps].want;
+        scur = ring[ps].cursor;
+      }
+      sdepth = depth - 1;
       continue;
     }
-    if (f + 1 >= s.depth_cap) {
-      if (t == 0) sbad = 3;
-      break;
-    }
-    // the child: the parent's list, states and pairs, E's own decisions, the alternative's sub-elements
-    const int np = h->npend;
-    int4 *pp = sf_pend(s, f), *cp = sf_pend(s, f + 1);
-    const int *ps = sf_state(s, f);
-    int *cs = sf_state(s, f + 1);
-    for (int q = t; q < np; q += blockDim.x) cp[q] = pp[q];
-    for (int q = t; q < 2 * n; q += blockDim.x) cs[q] = ps[q];
-    __syncthreads();
-    if (t == 0) {
-      h->cursor = kf + 1;
-      int4 kids[3];
-      int nk = 0;
-      const mq c = el_alt(p, E, kf, kids, &nk);
-      const long long nslack = slack - (c - want);
-      const int kind = E.x & 255, a = (E.x >> 8) & 255, b = (E.x >> 16) & 255, x = E.y, y = E.z;
-      auto setst = [&](int q, int v) {
-        if (cs[q] >= 0 && cs[q] != v) sbad = 4;
-        cs[q] = v;
-      };
-      switch (kind) {  // the element's own decisions
-        case MT_EXT:
-          if (x == 0) setst(0, y);
-          else if (a < NS) setst(x, a);
-          break;
-        case MT_CH: setst(x, a); break;
-        case MT_QB:
-          cs[n + x] = y;
-          cs[n + y] = x;
-          setst(x, a);
-          setst(y, b);
-          break;
-        case MT_QMU: case MT_M2PU: setst(y, b); break;
-        case MT_M2UP: case MT_M2UU: setst(x, a); break;
-        default: break;
-      }
-      int m2 = np;
-      for (int q = 0; q < nk; q++) {
-        if (m2 < s.pcap) cp[m2++] = kids[q];
-        else sbad = 5;
-      }
-      if (m2 == 0) {  // complete: MFE + gap - slack
-        const long long idx = sfound;
-        if (idx < s.max_out) {
-          for (int r = 0; r < p.m; r++) {
-            const int st = cs[3 * r];
-            s.codons[(size_t)idx * p.m + r] = st >= 0 ? p.cid[3 * r * NS + st] : -1;
-          }
-          for (int q = 0; q < n; q++) s.partner[(size_t)idx * n + q] = cs[n + q];
-          s.cost[idx] = best + (s.gap - nslack);
-        }
-        sfound = idx + 1;
-        if (sfound > s.max_out) sdone = 1;
+    if (mk != kf) continue;
+    h.cursor = kf + 1;
+    const long long nslack = slack - (mc - want);
+    const int np = h.npend;
+    int m2 = np;
+    for (int q = 0; q < mnk; q++) {
+      if (m2 < s.pcap) {
+        s.pend[m2] = mkids[q];
+        s.pendw[m2] = mkw[q];
+        m2++;
       } else {
-        SubHdr *g = sf_hdr(s, f + 1);
-        g->elem = cp[m2 - 1];
-        g->npend = m2 - 1;
-        g->slack = nslack;
-        g->cursor = 0;
-        sdepth = depth + 1;
+        sbad = 5;
       }
     }
+    if (m2 == 0) {  // complete: MFE + gap - slack
+      const long long idx = sfound;
+      if (idx < s.max_out) {
+        for (int r = 0; r < p.m; r++) {
+          const int st = scs[3 * r];
+          s.codons[(size_t)idx * p.m + r] = st >= 0 ? p.cid[3 * r * NS + st] : -1;
+        }
+        for (int q = 0; q < n; q++) s.partner[(size_t)idx * n + q] = scs[n + q];
+        s.cost[idx] = best + (s.gap - nslack);
+      }
+      sfound = idx + 1;
+      if (sfound > s.max_out) sdone = 1;
+      scur = kf + 1;
+      continue;
+    }
+    if (depth >= s.depth_cap) {
+      sbad = 3;
+      continue;
+    }
+    SubFrame g;
+    g.elem = mnk > 0 ? mkids[mnk - 1] : s.pend[np - 1];
+    g.want = mnk > 0 ? mkw[mnk - 1] : s.pendw[np - 1];
+    g.npend = m2 - 1;
+    g.slack = nslack;
+    g.cursor = 0;
+    int bad = 0;
+    el_decide(n, g.elem, scs, g, bad);
+    if (bad) sbad = bad;
+    const int ci = fi + 1, cs = ci % SUB_RING;
+    if (rtag[cs] >= 0 && rtag[cs] == ci - SUB_RING) s.frames[ci - SUB_RING] = ring[cs];  // a live ancestor
+    ring[cs] = g;
+    rtag[cs] = ci;
+    sE = g.elem;
+    sslack = nslack;
+    swant = g.want;
+    scur = 0;
+    sdepth = depth + 1;
   }
   __syncthreads();
   if (t == 0) {

@@ -1348,7 +1348,6 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   a.max_out = max_out;
   a.pcap = 4 * n + 64;
   a.depth_cap = 4 * n + 64;
-  a.fsz = ((size_t)64 + (size_t)a.pcap * sizeof(int4) + (size_t)2 * n * sizeof(int) + 15) / 16 * 16;
   a.max_steps = 50000000ll;
   a.max_ns = 30ull * 1000000000ull;  // 30 s
   std::vector<void *> tmp;
@@ -1356,7 +1355,9 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
     cudaStreamSynchronize(st);
     free_list(tmp);
   };
-  cudaError_t e = dalloc(tmp, &a.frames, a.fsz * a.depth_cap);
+  cudaError_t e = dalloc(tmp, &a.frames, (size_t)a.depth_cap);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.pend, (size_t)a.pcap);
+  if (e == cudaSuccess) e = dalloc(tmp, &a.pendw, (size_t)a.pcap);
   if (e == cudaSuccess) e = dalloc(tmp, &a.codons, (size_t)std::max(max_out, 1) * m);
   if (e == cudaSuccess) e = dalloc(tmp, &a.partner, (size_t)std::max(max_out, 1) * n);
   if (e == cudaSuccess) e = dalloc(tmp, &a.cost, (size_t)std::max(max_out, 1));
@@ -1375,7 +1376,9 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   }
   k_sub_mins<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(t.dp, a.mn);
   e = cudaGetLastError();
-  if (e == cudaSuccess) k_mfe_subopt<<<1, 256, 0, st>>>(a);
+  const size_t ssm = sub_smem(n);  // the states and partners, the frame ring
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void *)k_mfe_subopt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+  if (e == cudaSuccess) k_mfe_subopt<<<1, 256, ssm, st>>>(a);
   if (e == cudaSuccess) e = cudaGetLastError();
   long long cnt[2] = {0, 0};
   int err = 0;
@@ -1891,8 +1894,9 @@ cf_status cf_subopt(cf_problem *p, double gap_kcal, int max_out, int64_t *cost, 
   if (!(gap_kcal >= 0) || gap_kcal > 1e6 || max_out < 0) return fail(p, CF_EINVAL, "cf_subopt: bad gap or max_out");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_subopt: no protein set");
   if (p->layout == 1) return fail(p, CF_EINVAL, "cf_subopt: not available in the single-codon layout");
-  if (ptr_kind(cost, p->device) > 0 || ptr_kind(codons, p->device) > 0 || ptr_kind(partner, p->device) > 0)
+  if (ptr_kind(cost, p->device) != 0 || ptr_kind(codons, p->device) != 0 || ptr_kind(partner, p->device) != 0)
     return fail(p, CF_EINVAL, "cf_subopt: outputs must be host memory");
+  if (p->n > CF_SUBOPT_MAX_N) return fail(p, CF_EINVAL, "cf_subopt: protein longer than CF_SUBOPT_MAX_N nt");
   CF_CUDA(p, cudaSetDevice(p->device));
   const long long gap = (long long)std::floor(gap_kcal * 4294967296.0);  // on the 2^-32 kcal/mol grid
   return run_subopt(p, gap, max_out, (long long *)cost, codons, partner, count);

@@ -401,6 +401,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
   return false;
 }
 
+// Bounded wait for a phase that other threads of the CTA complete by their
+// arrivals (no copies to drain): on timeout the error bit is set and false
+// is returned at once.
+__device__ __forceinline__ bool mbar_wait_peer(unsigned long long *bar, unsigned parity, int *err) {
+  const unsigned long long polls = g_cf_wait_polls;
+  for (unsigned long long it = 0; it < polls; it++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(128);
+  }
+  atomicOr(err, ERR_STAGE_TIMEOUT);
+  return false;
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
   if (v > 0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }

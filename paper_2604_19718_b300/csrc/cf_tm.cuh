@@ -177,19 +177,25 @@ __device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
   reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
-// The cells of length len >= 2; one CTA per cell i.  Thread t owns output
-// row r = t / 6 (state at i, zeta) and the four columns of the codon state
-// qs = t % 6 at j (its four zeta'), so that a block product reads 16-byte
-// rows: per state b of the summation index, one 4-vector of the left block
-// and four of the right block give 16 FMAs; the summation runs over the real
-// states of the split point only, and rows past the real states of i are
-// left at zero.  The split points come tm_kc at a time (a group) through a
-// pipeline of up to TM_NST stages of dynamic shared memory: thread 0 copies
-// a group's blocks with one bulk copy each, of their real rows only (4 M_i
-// rows of L[i, k], 4 M_k rows of F[k, j]), completing on the stage's
-// mbarrier, and refills a stage once the block has finished with it.
-constexpr int TM_NC = TM_D * NS;  // 144 threads
-constexpr int TM_NST = 8;         // most pipeline stages of a CTA
+// The cells of length len >= 2; one CTA per cell i, warp-specialised.
+// Warp 0 is the producer: its lane 0 streams the split points, tm_kc at a
+// time (a group), through a ring of up to TM_NST stages of dynamic shared
+// memory, one bulk copy per block of its real rows only (4 M_i rows of
+// L[i, k], 4 M_k rows of F[k, j]), each stage completing on its "full"
+// mbarrier.  Warps 1-5 are the consumers: consumer c = t - 32 < 144 owns
+// output row r = c / 6 (state at i, zeta) and the four columns of the codon
+// state qs = c % 6 at j (its four zeta'), so that a block product reads
+// 16-byte rows: per state b of the summation index, one 4-vector of the left
+// block and four of the right block give 16 FMAs, over the real states of
+// the split point only; rows past the real states of i stay zero.  Each
+// consumer warp arrives on the stage's "empty" mbarrier when it is done
+// with it, and the producer waits for all five before refilling it, so no
+// block barrier runs per group.  A wait that runs out sets the error and a
+// shared stop flag; the producer then drains its copies in flight.
+constexpr int TM_NC = TM_D * NS;       // 144 consumer threads
+constexpr int TM_NCW = 5;              // consumer warps (the last has 16 idle lanes)
+constexpr int TM_NTH = 32 * (1 + TM_NCW);  // 192 threads
+constexpr int TM_NST = 8;              // most pipeline stages of a CTA
 template <typename T>
 __host__ __device__ constexpr int tm_kc() {
   return sizeof(T) == sizeof(float) ? 4 : 2;  // 18 KB per stage in both precisions
@@ -218,21 +224,25 @@ __host__ __device__ constexpr size_t tm_cell_smem() {
   return (size_t)(TM_NST < 200 * 1024 / tm_stage_bytes<T>() ? TM_NST : 200 * 1024 / tm_stage_bytes<T>()) *
          tm_stage_bytes<T>();
 }
+// barrier 1 among the consumer warps only
+__device__ __forceinline__ void tm_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TM_NCW) : "memory"); }
+
 template <typename T>
-__global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len, int nst) {
-  const int n = a.n, i = blockIdx.x, t = threadIdx.x;
+__global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int nst) {
+  const int n = a.n, i = blockIdx.x, t = threadIdx.x, w = t >> 5, c = t - 32;
   const int j = i + len - 1;  // the new last base
-  const int r = t / NS, qs = t % NS;
+  const bool cons = c >= 0 && c < TM_NC;
+  const int r = cons ? c / NS : 0, qs = cons ? c % NS : 0;
   constexpr int KC = tm_kc<T>();
   extern __shared__ __align__(128) unsigned char tm_smem[];  // [nst] stages: KC blocks of L, then KC of F
   __shared__ __align__(16) T q[TM_BLK];
   __shared__ __align__(16) T x[TM_BLK];
   __shared__ T tq[BLK], sFac[TM_NST][KC];
-  __shared__ int sEL, sMk[TM_NST][KC];
-  __shared__ T smx[(TM_NC + 31) / 32];
-  __shared__ __align__(8) unsigned long long sbar[TM_NST];
+  __shared__ int sEL, sMk[TM_NST][KC], sstop;
+  __shared__ T smx[TM_NCW];
+  __shared__ __align__(8) unsigned long long sfull[TM_NST], sempty[TM_NST];
   const int Mi = a.Mp[i];
-  const bool live = r < TM_G * Mi;  // a real row of the output
+  const bool live = cons && r < TM_G * Mi;  // a real row of the output
   const int k0 = i + 1, k1 = j - 4, ng = k1 >= k0 ? (k1 - k0 + KC) / KC : 0;
   // this length's exponent from the largest mantissa of length len - 1
   if (t == 0) {
@@ -244,148 +254,160 @@ __global__ void __launch_bounds__(TM_NC) k_tm_cell(TmArgs<T> a, int len, int nst
     }
     sEL = e;
     if (i == 0) a.E[len] = e;
-    for (int s = 0; s < nst; s++) mbar_init(&sbar[s], 1);
+    sstop = 0;
+    for (int s = 0; s < nst; s++) {
+      mbar_init(&sfull[s], 1);
+      mbar_init(&sempty[s], TM_NCW);
+    }
   }
   __syncthreads();
   const int EL = sEL;
-  // group g of split points into stage s: per split point its factor
-  // 2^{E[k-i] + E[j-k-1] - E[len]} and state count (fetched ahead into
-  // registers by fetch, so that the refill after a group does not wait on
-  // them), then one bulk copy per block
-  int pm[KC], pe[KC];
-  auto fetch = [&](int g) {
-#pragma unroll
-    for (int u = 0; u < KC; u++) {
-      const int k = k0 + g * KC + u;
-      pm[u] = k <= k1 ? __ldg(a.Mp + k) : 0;
-      pe[u] = k <= k1 ? __ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) : 0;
-    }
-  };
-  auto issue = [&](int g, int s) {
-    T *sL = reinterpret_cast<T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
-    T *sF = sL + (size_t)KC * TM_BLK;
-    unsigned bytes = 0;
-#pragma unroll
-    for (int u = 0; u < KC; u++) {
-      sMk[s][u] = pm[u];
-      sFac[s][u] = pm[u] ? clamp_p2<T>(pe[u] - EL) : (T)0;
-      if (pm[u]) bytes += (unsigned)((Mi + pm[u]) * TM_G * TM_D * sizeof(T));
-    }
-    mbar_arrive_expect(&sbar[s], bytes);
-#pragma unroll
-    for (int u = 0; u < KC; u++) {
-      const int k = k0 + g * KC + u;
-      if (!pm[u]) continue;
-      bulk_g2s(sL + (size_t)u * TM_BLK, a.L + tm_cell(n, i, k - i), (unsigned)(Mi * TM_G * TM_D * sizeof(T)), &sbar[s]);
-      bulk_g2s(sF + (size_t)u * TM_BLK, a.F + cidx(n, k, j) * TM_BLK, (unsigned)(pm[u] * TM_G * TM_D * sizeof(T)),
-               &sbar[s]);
-    }
-  };
-  if (t == 0)
-    for (int g = 0; g < nst && g < ng; g++) {
-      fetch(g);
-      issue(g, g);
-    }
-  // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1), four entries per thread
-  const int Mj1 = a.Mp[j - 1], Mj = a.Mp[j];
-  {
-    T v4[4];
-#pragma unroll
-    for (int z = 0; z < 4; z++) {
-      const int e = 4 * t + z, u = e / TM_D, c = e % TM_D, br = u / TM_G, zr = u % TM_G, ac = c / TM_G, zc = c % TM_G;
-      v4[z] = ac < Mj ? (T)a.Tr[(size_t)(j - 1) * BLK + br * NS + ac] * (T)a.mod->V[a.base[j * NS + ac]][zr][zc]
-                      : (T)0;
-    }
-    st4(x + 4 * t, v4);
-    ldcg4(v4, a.Q + tm_cell(n, i, len - 1) + 4 * t);
-    st4(q + 4 * t, v4);
-  }
-  __syncthreads();
   T acc[4] = {0, 0, 0, 0};
-  if (live) {
-    for (int b = 0; b < Mj1; b++) {  // states at j - 1
-      T l4[4];
-      ld4(l4, q + r * TM_D + 4 * b);
+  int issued = 0;  // producer: groups issued
+  if (w == 0) {
+    if (t == 0) {
+      // group g into stage g % nst once the consumers have released it
+      for (int g = 0; g < ng; g++) {
+        const int s = g % nst;
+        int pm[KC], pe[KC];
 #pragma unroll
-      for (int z1 = 0; z1 < 4; z1++) {
-        T f4[4];
-        ld4(f4, x + (4 * b + z1) * TM_D + 4 * qs);
-#pragma unroll
-        for (int z = 0; z < 4; z++) acc[z] = fma(l4[z1], f4[z], acc[z]);
-      }
-    }
-    const T f = clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
-#pragma unroll
-    for (int z = 0; z < 4; z++) acc[z] *= f;
-    // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
-    if (j - i >= 4) {
-      T f4[4];
-      ldcg4(f4, a.F + cidx(n, i, j) * TM_BLK + r * TM_D + 4 * qs);
-      const T fe = clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
-#pragma unroll
-      for (int z = 0; z < 4; z++) acc[z] = fma(f4[z], fe, acc[z]);
-    }
-  }
-  // k = i+1 .. j-4: L[i, k] F[k, j], one group of KC split points per stage.
-  // Each thread waits for the stage's copies itself; the one block barrier
-  // per group frees the stage for its refill and agrees on giving up after
-  // a wait that ran out.
-  for (int g = 0; g < ng; g++) {
-    const int s = g % nst;
-    const unsigned par = (unsigned)(g / nst) & 1u;
-    const bool refill = t == 0 && g + nst < ng;
-    if (refill) fetch(g + nst);
-    const bool ok = mbar_wait(&sbar[s], par, a.err);
-    if (live && ok) {
-      const T *sL = reinterpret_cast<const T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
-      const T *sF = sL + (size_t)KC * TM_BLK;
-#pragma unroll
-      for (int u = 0; u < KC; u++) {
-        const T *Lb = sL + (size_t)u * TM_BLK, *Fb = sF + (size_t)u * TM_BLK;
-        const int Mk = sMk[s][u];
-        T sm[4] = {0, 0, 0, 0};
-        for (int b = 0; b < Mk; b++) {
-          T l4[4];
-          ld4(l4, Lb + r * TM_D + 4 * b);
-#pragma unroll
-          for (int z1 = 0; z1 < 4; z1++) {
-            T f4[4];
-            ld4(f4, Fb + (4 * b + z1) * TM_D + 4 * qs);
-#pragma unroll
-            for (int z = 0; z < 4; z++) sm[z] = fma(l4[z1], f4[z], sm[z]);
-          }
+        for (int u = 0; u < KC; u++) {  // in flight while the stage is awaited
+          const int k = k0 + g * KC + u;
+          pm[u] = k <= k1 ? __ldg(a.Mp + k) : 0;
+          pe[u] = k <= k1 ? __ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) : 0;
         }
-        const T f = sFac[s][u];
+        if (g >= nst && !mbar_wait_peer(&sempty[s], (unsigned)(g / nst - 1) & 1u, a.err)) {
+          sstop = 1;
+          break;
+        }
+        if (*(volatile int *)&sstop) break;
+        T *sL = reinterpret_cast<T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
+        T *sF = sL + (size_t)KC * TM_BLK;
+        unsigned bytes = 0;
 #pragma unroll
-        for (int z = 0; z < 4; z++) acc[z] = fma(sm[z], f, acc[z]);
+        for (int u = 0; u < KC; u++) {
+          sMk[s][u] = pm[u];
+          sFac[s][u] = pm[u] ? clamp_p2<T>(pe[u] - EL) : (T)0;
+          if (pm[u]) bytes += (unsigned)((Mi + pm[u]) * TM_G * TM_D * sizeof(T));
+        }
+        fence_proxy_async();
+        mbar_arrive_expect(&sfull[s], bytes);
+#pragma unroll
+        for (int u = 0; u < KC; u++) {
+          const int k = k0 + g * KC + u;
+          if (!pm[u]) continue;
+          bulk_g2s(sL + (size_t)u * TM_BLK, a.L + tm_cell(n, i, k - i), (unsigned)(Mi * TM_G * TM_D * sizeof(T)),
+                   &sfull[s]);
+          bulk_g2s(sF + (size_t)u * TM_BLK, a.F + cidx(n, k, j) * TM_BLK, (unsigned)(pm[u] * TM_G * TM_D * sizeof(T)),
+                   &sfull[s]);
+        }
+        issued = g + 1;
       }
     }
-    if (__syncthreads_or(!ok)) {
-      // give up: every other stage still in flight lands before the CTA exits
-      if (t == 0)
-        for (int h = g + 1; h < ng && h < g + nst; h++) mbar_wait(&sbar[h % nst], (unsigned)(h / nst) & 1u, a.err);
-      return;
+  } else {
+    // X_j = T_{j-1} (x) V_j and Q[i, j] (length len - 1), four entries per consumer
+    const int Mj1 = a.Mp[j - 1], Mj = a.Mp[j];
+    if (cons) {
+      T v4[4];
+#pragma unroll
+      for (int z = 0; z < 4; z++) {
+        const int e = 4 * c + z, u = e / TM_D, cc = e % TM_D, br = u / TM_G, zr = u % TM_G, ac = cc / TM_G,
+                  zc = cc % TM_G;
+        v4[z] = ac < Mj ? (T)a.Tr[(size_t)(j - 1) * BLK + br * NS + ac] * (T)a.mod->V[a.base[j * NS + ac]][zr][zc]
+                        : (T)0;
+      }
+      st4(x + 4 * c, v4);
+      ldcg4(v4, a.Q + tm_cell(n, i, len - 1) + 4 * c);
+      st4(q + 4 * c, v4);
     }
-    if (refill) {
-      fence_proxy_async();
-      issue(g + nst, s);
+    tm_consumer_sync();
+    if (live) {
+      for (int b = 0; b < Mj1; b++) {  // states at j - 1
+        T l4[4];
+        ld4(l4, q + r * TM_D + 4 * b);
+#pragma unroll
+        for (int z1 = 0; z1 < 4; z1++) {
+          T f4[4];
+          ld4(f4, x + (4 * b + z1) * TM_D + 4 * qs);
+#pragma unroll
+          for (int z = 0; z < 4; z++) acc[z] = fma(l4[z1], f4[z], acc[z]);
+        }
+      }
+      const T f = clamp_p2<T>(__ldcg(a.E + len - 1) - EL);
+#pragma unroll
+      for (int z = 0; z < 4; z++) acc[z] *= f;
+      // k = i: the pair (i, j) closes the interval's first base (L[i, i] = identity)
+      if (j - i >= 4) {
+        T f4[4];
+        ldcg4(f4, a.F + cidx(n, i, j) * TM_BLK + r * TM_D + 4 * qs);
+        const T fe = clamp_p2<T>(__ldcg(a.E + len - 2) - EL);
+#pragma unroll
+        for (int z = 0; z < 4; z++) acc[z] = fma(f4[z], fe, acc[z]);
+      }
+    }
+    // k = i+1 .. j-4: L[i, k] F[k, j], one group of KC split points per stage
+    for (int g = 0; g < ng; g++) {
+      const int s = g % nst;
+      const bool ok = mbar_wait(&sfull[s], (unsigned)(g / nst) & 1u, a.err);
+      // the whole warp leaves together (its __syncwarp below needs every lane)
+      if (__any_sync(0xffffffffu, !ok || *(volatile int *)&sstop)) {
+        sstop = 1;
+        break;
+      }
+      if (live) {
+        const T *sL = reinterpret_cast<const T *>(tm_smem + (size_t)s * tm_stage_bytes<T>());
+        const T *sF = sL + (size_t)KC * TM_BLK;
+#pragma unroll
+        for (int u = 0; u < KC; u++) {
+          const T *Lb = sL + (size_t)u * TM_BLK, *Fb = sF + (size_t)u * TM_BLK;
+          const int Mk = sMk[s][u];
+          T sm[4] = {0, 0, 0, 0};
+          for (int b = 0; b < Mk; b++) {
+            T l4[4];
+            ld4(l4, Lb + r * TM_D + 4 * b);
+#pragma unroll
+            for (int z1 = 0; z1 < 4; z1++) {
+              T f4[4];
+              ld4(f4, Fb + (4 * b + z1) * TM_D + 4 * qs);
+#pragma unroll
+              for (int z = 0; z < 4; z++) sm[z] = fma(l4[z1], f4[z], sm[z]);
+            }
+          }
+          const T f = sFac[s][u];
+#pragma unroll
+          for (int z = 0; z < 4; z++) acc[z] = fma(sm[z], f, acc[z]);
+        }
+      }
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&sempty[s]);  // this warp is done with the stage
     }
   }
-  __syncthreads();  // every thread is past its reads of q (lengths 2..5 have no split-point loop)
-  st4(a.Q + tm_cell(n, i, len) + r * TM_D + 4 * qs, acc);
-  st4(q + r * TM_D + 4 * qs, acc);
-  // the largest |mantissa| of this length
-  T m = fmax(fmax(fabs(acc[0]), fabs(acc[1])), fmax(fabs(acc[2]), fabs(acc[3])));
-  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((t & 31) == 0) smx[t >> 5] = m;
-  if (t < BLK) tq[t] = i + len < n ? (T)a.Tr[(size_t)(i + len - 1) * BLK + t] : (T)0;
+  __syncthreads();  // every consumer is past its reads of q and of the stages
+  if (sstop) {
+    // a wait ran out: the copies still in flight land before the CTA exits
+    if (t == 0)
+      for (int h = issued - 1; h >= 0 && h >= issued - nst; h--) mbar_wait(&sfull[h % nst], (unsigned)(h / nst) & 1u, a.err);
+    return;
+  }
+  if (cons) {
+    st4(a.Q + tm_cell(n, i, len) + r * TM_D + 4 * qs, acc);
+    st4(q + r * TM_D + 4 * qs, acc);
+  }
+  // the largest |mantissa| of this length (idle lanes hold zeros)
+  if (w > 0) {
+    T m = fmax(fmax(fabs(acc[0]), fabs(acc[1])), fmax(fabs(acc[2]), fabs(acc[3])));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((t & 31) == 0) smx[w - 1] = m;
+  }
+  if (cons && c < BLK) tq[c] = i + len < n ? (T)a.Tr[(size_t)(i + len - 1) * BLK + c] : (T)0;
   __syncthreads();
   if (t == 0) {
     double mm = 0;
-    for (int w = 0; w < (TM_NC + 31) / 32; w++) mm = fmax(mm, (double)smx[w]);
+    for (int v = 0; v < TM_NCW; v++) mm = fmax(mm, (double)smx[v]);
     atomic_max_pos(a.dmax + len, mm);
   }
-  if (i + len < n) {  // L[i, i+len] = Q[i, i+len] (T_{i+len-1} (x) I): column state qs at i + len
+  if (cons && i + len < n) {  // L[i, i+len] = Q[i, i+len] (T_{i+len-1} (x) I): column state qs at i + len
+    const int Mj = a.Mp[j];
     T l4[4] = {0, 0, 0, 0};
     for (int b = 0; b < Mj; b++) {
       const T tb = tq[b * NS + qs];

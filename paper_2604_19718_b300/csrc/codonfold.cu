@@ -2088,7 +2088,7 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
       for (int len = 2; len <= n; len++) {
         if (len - 1 >= 4) k_tm_fold<T><<<n - (len - 1), TM_NT, 0, cs>>>(a, len);
         const int nst = tm_cell_stages<T>(n, len);
-        k_tm_cell<T><<<n - len + 1, TM_NC, (size_t)nst * tm_stage_bytes<T>(), cs>>>(a, len, nst);
+        k_tm_cell<T><<<n - len + 1, TM_NTH, (size_t)nst * tm_stage_bytes<T>(), cs>>>(a, len, nst);
       }
       k_tm_finish<T><<<1, 32, 0, cs>>>(a);
       e = cudaStreamEndCapture(cs, &g);

@@ -209,11 +209,11 @@ __host__ __device__ constexpr size_t tm_stage_bytes() {
 // memory per SM (148 SMs), at least one, at most TM_NST and its number of
 // groups.  Few long cells get a deep pipeline each, many short ones more CTAs.
 template <typename T>
-inline int tm_cell_stages(int n, int len) {
+inline int tm_cell_stages(int n, int len, int split = 1) {
   const int ns = len - 5;  // split points k = i+1 .. i+len-5
   if (ns <= 0) return 0;
-  const int ng = (ns + tm_kc<T>() - 1) / tm_kc<T>();
-  const int per_sm = (n - len + 1 + 147) / 148;
+  const int ng = ((ns + tm_kc<T>() - 1) / tm_kc<T>() + split - 1) / split;  // groups of one CTA
+  const int per_sm = ((n - len + 1) * split + 147) / 148;
   const long long budget = 200 * 1024 / per_sm - 1024 - (long long)(2 * TM_BLK + BLK) * sizeof(T);
   const int fit = (int)std::max(1ll, budget / (long long)tm_stage_bytes<T>());
   return std::min(std::min(fit, TM_NST), ng);
@@ -226,10 +226,39 @@ __host__ __device__ constexpr size_t tm_cell_smem() {
 }
 // barrier 1 among the consumer warps only
 __device__ __forceinline__ void tm_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TM_NCW) : "memory"); }
+// Launches with few cells split each cell's groups over a cluster of two
+// CTAs (TM_SPLIT_CELLS cells or fewer, TM_SPLIT_GROUPS groups or more).
+constexpr int TM_SPLIT_CELLS = 444, TM_SPLIT_GROUPS = 8;
+// every thread of both CTAs of the cluster
+__device__ __forceinline__ void tm_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// four consecutive values from the shared memory of CTA `rank` of the cluster
+template <typename T>
+__device__ __forceinline__ void ld4_peer(T (&v)[4], const T *local, unsigned rank);
+template <>
+__device__ __forceinline__ void ld4_peer<float>(float (&v)[4], const float *local, unsigned rank) {
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+               : "r"(ra)
+               : "memory");
+}
+template <>
+__device__ __forceinline__ void ld4_peer<double>(double (&v)[4], const double *local, unsigned rank) {
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(ra) : "r"(smem_addr(local)), "r"(rank));
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];\n" : "=d"(v[0]), "=d"(v[1]) : "r"(ra) : "memory");
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];\n" : "=d"(v[2]), "=d"(v[3]) : "r"(ra + 16u) : "memory");
+}
 
 template <typename T>
-__global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int nst) {
-  const int n = a.n, i = blockIdx.x, t = threadIdx.x, w = t >> 5, c = t - 32;
+__global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int nst, int split) {
+  // split 2: blockIdx.x = 2 cell + rank, the two CTAs of a cell one cluster
+  const int rank = split > 1 ? (int)(blockIdx.x & 1) : 0;
+  const int n = a.n, i = blockIdx.x / split, t = threadIdx.x, w = t >> 5, c = t - 32;
   const int j = i + len - 1;  // the new last base
   const bool cons = c >= 0 && c < TM_NC;
   const int r = cons ? c / NS : 0, qs = cons ? c % NS : 0;
@@ -240,10 +269,13 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
   __shared__ T tq[BLK], sFac[TM_NST][KC];
   __shared__ int sEL, sMk[TM_NST][KC], sstop;
   __shared__ T smx[TM_NCW];
+  __shared__ __align__(16) T part[TM_BLK];  // split 2: rank 1's partial sums, read by rank 0
   __shared__ __align__(8) unsigned long long sfull[TM_NST], sempty[TM_NST];
   const int Mi = a.Mp[i];
   const bool live = cons && r < TM_G * Mi;  // a real row of the output
-  const int k0 = i + 1, k1 = j - 4, ng = k1 >= k0 ? (k1 - k0 + KC) / KC : 0;
+  const int k0 = i + 1, k1 = j - 4, ngt = k1 >= k0 ? (k1 - k0 + KC) / KC : 0;
+  // this CTA's groups [gb, gb + ng): all, or rank 0 the first half and rank 1 the rest
+  const int gh = split > 1 ? (ngt + 1) / 2 : ngt, gb = rank ? gh : 0, ng = rank ? ngt - gh : gh;
   // this length's exponent from the largest mantissa of length len - 1
   if (t == 0) {
     const double mx = __longlong_as_double((long long)__ldcg(a.dmax + len - 1));
@@ -253,7 +285,7 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
       else atomicOr(a.err, 1);
     }
     sEL = e;
-    if (i == 0) a.E[len] = e;
+    if (i == 0 && rank == 0) a.E[len] = e;
     sstop = 0;
     for (int s = 0; s < nst; s++) {
       mbar_init(&sfull[s], 1);
@@ -272,7 +304,7 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
         int pm[KC], pe[KC];
 #pragma unroll
         for (int u = 0; u < KC; u++) {  // in flight while the stage is awaited
-          const int k = k0 + g * KC + u;
+          const int k = k0 + (gb + g) * KC + u;
           pm[u] = k <= k1 ? __ldg(a.Mp + k) : 0;
           pe[u] = k <= k1 ? __ldcg(a.E + (k - i)) + __ldcg(a.E + (j - k - 1)) : 0;
         }
@@ -294,7 +326,7 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
         mbar_arrive_expect(&sfull[s], bytes);
 #pragma unroll
         for (int u = 0; u < KC; u++) {
-          const int k = k0 + g * KC + u;
+          const int k = k0 + (gb + g) * KC + u;
           if (!pm[u]) continue;
           bulk_g2s(sL + (size_t)u * TM_BLK, a.L + tm_cell(n, i, k - i), (unsigned)(Mi * TM_G * TM_D * sizeof(T)),
                    &sfull[s]);
@@ -321,7 +353,7 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
       st4(q + 4 * c, v4);
     }
     tm_consumer_sync();
-    if (live) {
+    if (live && rank == 0) {
       for (int b = 0; b < Mj1; b++) {  // states at j - 1
         T l4[4];
         ld4(l4, q + r * TM_D + 4 * b);
@@ -383,12 +415,25 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
     }
   }
   __syncthreads();  // every consumer is past its reads of q and of the stages
-  if (sstop) {
-    // a wait ran out: the copies still in flight land before the CTA exits
-    if (t == 0)
-      for (int h = issued - 1; h >= 0 && h >= issued - nst; h--) mbar_wait(&sfull[h % nst], (unsigned)(h / nst) & 1u, a.err);
-    return;
+  const bool stop = sstop;
+  // a wait ran out: the copies still in flight land before the CTA exits
+  if (stop && t == 0)
+    for (int h = issued - 1; h >= 0 && h >= issued - nst; h--) mbar_wait(&sfull[h % nst], (unsigned)(h / nst) & 1u, a.err);
+  if (split > 1) {
+    // rank 0 adds rank 1's partial sums; both CTAs pass both cluster barriers
+    // on every path (rank 1's shared memory lives until rank 0 has read it)
+    if (rank == 1 && cons) st4(part + 4 * c, acc);
+    tm_cluster_sync();
+    if (rank == 0 && cons) {
+      T o4[4];
+      ld4_peer(o4, part + 4 * c, 1u);
+#pragma unroll
+      for (int z = 0; z < 4; z++) acc[z] += o4[z];
+    }
+    tm_cluster_sync();
+    if (rank == 1) return;
   }
+  if (stop) return;
   if (cons) {
     st4(a.Q + tm_cell(n, i, len) + r * TM_D + 4 * qs, acc);
     st4(q + r * TM_D + 4 * qs, acc);

@@ -685,6 +685,17 @@ def profile_form(form, steps, m=0):
         out["ms"] = cf.cf_tm_last_ms(f.prob)
         f.close()
         model.close()
+    elif form == "subopt":  # every configuration within 1 kcal/mol, first 60 residues (or m) of p300_weighted
+        res, lw, pb = synth.workload("p300_weighted")
+        mm = m or 60
+        f = cf.CodonFold(params)
+        f.set_protein(res[:mm], lw[:mm], pb)
+        for _ in range(steps):
+            cnt, _, _, _ = f.subopt(1.0, 100_000)
+        out["ms"] = cf.cf_mfe_last_ms(f.prob)
+        out["count"] = cnt
+        out["steps"] = cf.cf_subopt_steps(f.prob)
+        f.close()
     elif form == "windows":
         ex = screen.Windows(params)
         _, _, bases, off = synth.windows(8000, seed=3)
@@ -709,7 +720,7 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="use only the first M residues (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the window, surrogate, adjoint and 3000-nt measurements")
-    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm"],
+    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm", "subopt"],
                     help="run one form on a small case (for profiler captures) and print its timing")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -415,15 +415,17 @@ __device__ int cta_first(int K, mq target, const F &cost, int *sfirst) {
   return -1;
 }
 
-// the 435 interior loop shapes (l1, l2 >= 1, l1 + l2 <= 30), by l1 then l2
+// the 435 interior loop shapes (l1, l2 >= 1, l1 + l2 <= 30), by l1 then l2:
+// the shapes with l1 = a + 1 start at index a (59 - a) / 2, so a is the
+// smaller root of a^2 - 59 a + 2 q = 0 rounded down (corrected by one
+// where the binary32 square root lands on the other side)
 __device__ __forceinline__ void interior_shape(int q, int &l1, int &l2) {
-  int r = q;
-  l1 = 1;
-  while (r >= MAXLOOP - l1) {
-    r -= MAXLOOP - l1;
-    l1++;
-  }
-  l2 = 1 + r;
+  static_assert(MAXLOOP == 30, "closed form for loops of at most 30 bases");
+  int a = (int)((59.0f - sqrtf((float)(3481 - 8 * q))) * 0.5f);
+  if (a * (59 - a) / 2 > q) a--;
+  else if ((a + 1) * (58 - a) / 2 <= q) a++;
+  l1 = a + 1;
+  l2 = 1 + q - a * (59 - a) / 2;
 }
 constexpr int NINTERIOR = 435;
 

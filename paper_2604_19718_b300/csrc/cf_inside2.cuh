@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, in
 // that a single protein's kernels read their table pointers straight from the
 // parameter bank.)
 template <typename T, bool BT = false>
-__global__ void __launch_bounds__(256) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? 2 : 1) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;

@@ -1200,7 +1200,7 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 // others the side work of the cells of diagonal d+4.  Both parts start after
 // the light kernel of d+4.
 template <typename T, bool GRP, bool BT = false>
-__global__ void __launch_bounds__(NT3, GRP ? 4 : 1) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+__global__ void __launch_bounds__(NT3, GRP ? 4 : 2) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;
   if (BT) {

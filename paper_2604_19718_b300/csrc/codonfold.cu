@@ -787,7 +787,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     if (d == n - 1) deps[nd++] = first;
     if (hasb || hass) deps[nd++] = k1[d];
     cudaKernelNodeParams kp = {};
-    const bool wide = n - d > WIDE_CELLS;
+    const bool wide = (long long)(n - d) * B > WIDE_CELLS;  // the launch's cells, over every protein of a batch
     kp.func = (void *)(wide ? klightw : klight);
     kp.gridDim = dim3(n - d, B);
     kp.blockDim = dim3(wide ? NT_WIDE : NT);
@@ -889,7 +889,9 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     void *args[] = {&dp, &trans, &p0, &cid, &cm, &bm, &pg};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_codon_out<T>;
-    kp.gridDim = dim3((p->m * 6 + n + 127) / 128 + (61 * 61 + 3) / 4, B);  // threads, then 4 warps a block
+    // threads, then 4 warps a block for the codon-pair gradient (a batch
+    // returns none, so its graph launches the marginal blocks only)
+    kp.gridDim = dim3((p->m * 6 + n + 127) / 128 + (B > 1 ? 0 : (61 * 61 + 3) / 4), B);
     kp.blockDim = dim3(128);
     kp.kernelParams = args;
     cudaGraphNode_t co;

@@ -696,6 +696,14 @@ def profile_form(form, steps, m=0):
         out["count"] = cnt
         out["steps"] = cf.cf_subopt_steps(f.prob)
         f.close()
+    elif form == "batch":  # the 4,096-protein batch of 24-nt proteins, binary32, run `steps` times
+        b = cf.Batch(params, 4096, 8, cf.CF_FP32_SCALED)
+        prots = synth.batch_p8(4096)
+        for _ in range(steps):
+            b.set_proteins(prots)
+            b.run()
+        out["ms"] = b.last_ms()
+        b.close()
     elif form == "windows":
         ex = screen.Windows(params)
         _, _, bases, off = synth.windows(8000, seed=3)
@@ -720,7 +728,7 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="use only the first M residues (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the window, surrogate, adjoint and 3000-nt measurements")
-    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm", "subopt"],
+    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm", "subopt", "batch"],
                     help="run one form on a small case (for profiler captures) and print its timing")
     args = ap.parse_args()
     if args.impl == "reference":

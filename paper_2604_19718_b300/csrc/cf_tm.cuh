@@ -227,8 +227,10 @@ __host__ __device__ constexpr size_t tm_cell_smem() {
 // barrier 1 among the consumer warps only
 __device__ __forceinline__ void tm_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TM_NCW) : "memory"); }
 // Launches with few cells split each cell's groups over a cluster of two
-// CTAs (TM_SPLIT_CELLS cells or fewer, TM_SPLIT_GROUPS groups or more).
-constexpr int TM_SPLIT_CELLS = 444, TM_SPLIT_GROUPS = 8;
+// CTAs (TM_SPLIT_CELLS cells or fewer, TM_SPLIT_GROUPS groups or more), or
+// of four (TM_SPLIT4_CELLS cells or fewer, TM_SPLIT4_GROUPS groups or more).
+constexpr int TM_SPLIT_CELLS = 444, TM_SPLIT_GROUPS = 8, TM_SPLIT4_CELLS = 148, TM_SPLIT4_GROUPS = 16;
+constexpr int TM_SPLIT8_CELLS = 74, TM_SPLIT8_GROUPS = 32;
 // every thread of both CTAs of the cluster
 __device__ __forceinline__ void tm_cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
@@ -256,8 +258,8 @@ __device__ __forceinline__ void ld4_peer<double>(double (&v)[4], const double *l
 
 template <typename T>
 __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int nst, int split) {
-  // split 2: blockIdx.x = 2 cell + rank, the two CTAs of a cell one cluster
-  const int rank = split > 1 ? (int)(blockIdx.x & 1) : 0;
+  // split s > 1: blockIdx.x = s cell + rank, the s CTAs of a cell one cluster
+  const int rank = split > 1 ? (int)(blockIdx.x % split) : 0;
   const int n = a.n, i = blockIdx.x / split, t = threadIdx.x, w = t >> 5, c = t - 32;
   const int j = i + len - 1;  // the new last base
   const bool cons = c >= 0 && c < TM_NC;
@@ -269,13 +271,13 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
   __shared__ T tq[BLK], sFac[TM_NST][KC];
   __shared__ int sEL, sMk[TM_NST][KC], sstop;
   __shared__ T smx[TM_NCW];
-  __shared__ __align__(16) T part[TM_BLK];  // split 2: rank 1's partial sums, read by rank 0
+  __shared__ __align__(16) T part[TM_BLK];  // split > 1: a rank's partial sums, read by rank 0
   __shared__ __align__(8) unsigned long long sfull[TM_NST], sempty[TM_NST];
   const int Mi = a.Mp[i];
   const bool live = cons && r < TM_G * Mi;  // a real row of the output
   const int k0 = i + 1, k1 = j - 4, ngt = k1 >= k0 ? (k1 - k0 + KC) / KC : 0;
-  // this CTA's groups [gb, gb + ng): all, or rank 0 the first half and rank 1 the rest
-  const int gh = split > 1 ? (ngt + 1) / 2 : ngt, gb = rank ? gh : 0, ng = rank ? ngt - gh : gh;
+  // this CTA's groups [gb, gb + ng): all, or rank r its r-th share of ceil(ngt / split)
+  const int gq = (ngt + split - 1) / split, gb = min(ngt, rank * gq), ng = min(ngt, gb + gq) - gb;
   // this length's exponent from the largest mantissa of length len - 1
   if (t == 0) {
     const double mx = __longlong_as_double((long long)__ldcg(a.dmax + len - 1));
@@ -420,18 +422,20 @@ __global__ void __launch_bounds__(TM_NTH) k_tm_cell(TmArgs<T> a, int len, int ns
   if (stop && t == 0)
     for (int h = issued - 1; h >= 0 && h >= issued - nst; h--) mbar_wait(&sfull[h % nst], (unsigned)(h / nst) & 1u, a.err);
   if (split > 1) {
-    // rank 0 adds rank 1's partial sums; both CTAs pass both cluster barriers
-    // on every path (rank 1's shared memory lives until rank 0 has read it)
-    if (rank == 1 && cons) st4(part + 4 * c, acc);
+    // rank 0 adds the other ranks' partial sums in rank order; every CTA of
+    // the cluster passes both cluster barriers on every path (a rank's
+    // shared memory lives until rank 0 has read it)
+    if (rank > 0 && cons) st4(part + 4 * c, acc);
     tm_cluster_sync();
-    if (rank == 0 && cons) {
-      T o4[4];
-      ld4_peer(o4, part + 4 * c, 1u);
+    if (rank == 0 && cons)
+      for (int q = 1; q < split; q++) {
+        T o4[4];
+        ld4_peer(o4, part + 4 * c, (unsigned)q);
 #pragma unroll
-      for (int z = 0; z < 4; z++) acc[z] += o4[z];
-    }
+        for (int z = 0; z < 4; z++) acc[z] += o4[z];
+      }
     tm_cluster_sync();
-    if (rank == 1) return;
+    if (rank > 0) return;
   }
   if (stop) return;
   if (cons) {

@@ -2091,24 +2091,27 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
         if (len - 1 >= 4) k_tm_fold<T><<<n - (len - 1), TM_NT, 0, cs>>>(a, len);
         // few long cells: each cell's groups split over a cluster of two CTAs
         const int cells = n - len + 1, ngroups = std::max(0, (len - 5 + tm_kc<T>() - 1) / tm_kc<T>());
-        const int split = cells <= TM_SPLIT_CELLS && ngroups >= TM_SPLIT_GROUPS ? 2 : 1;
+        const int split = cells <= TM_SPLIT8_CELLS && ngroups >= TM_SPLIT8_GROUPS   ? 8
+                          : cells <= TM_SPLIT4_CELLS && ngroups >= TM_SPLIT4_GROUPS ? 4
+                          : cells <= TM_SPLIT_CELLS && ngroups >= TM_SPLIT_GROUPS   ? 2
+                                                                                     : 1;
         const int nst = tm_cell_stages<T>(n, len, split);
         if (split == 1) {
           k_tm_cell<T><<<cells, TM_NTH, (size_t)nst * tm_stage_bytes<T>(), cs>>>(a, len, nst, 1);
         } else {
           cudaLaunchConfig_t cfg = {};
-          cfg.gridDim = dim3((unsigned)(2 * cells));
+          cfg.gridDim = dim3((unsigned)(split * cells));
           cfg.blockDim = dim3(TM_NTH);
           cfg.dynamicSmemBytes = (size_t)nst * tm_stage_bytes<T>();
           cfg.stream = cs;
           cudaLaunchAttribute at[1];
           at[0].id = cudaLaunchAttributeClusterDimension;
-          at[0].val.clusterDim.x = 2;
+          at[0].val.clusterDim.x = (unsigned)split;
           at[0].val.clusterDim.y = 1;
           at[0].val.clusterDim.z = 1;
           cfg.attrs = at;
           cfg.numAttrs = 1;
-          cudaLaunchKernelEx(&cfg, k_tm_cell<T>, a, len, nst, 2);
+          cudaLaunchKernelEx(&cfg, k_tm_cell<T>, a, len, nst, split);
         }
       }
       k_tm_finish<T><<<1, 32, 0, cs>>>(a);

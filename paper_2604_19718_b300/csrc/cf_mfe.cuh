@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(MFE_NT) k_mfe_light(MfeDP p, int d) {
 // warp, the exterior X5[d] = min_{k = 4..d-4} GX[k] . QB[k][d].  Inputs lie on
 // diagonals <= d - 4.  One warp per cell, lanes over split points, then a
 // warp minimum per entry.
-__global__ void __launch_bounds__(256) k_mfe_bif(MfeDP p, int d) {
+__global__ void __launch_bounds__(256, 2) k_mfe_bif(MfeDP p, int d) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, n = p.n;
   const int x = blockIdx.x * 8 + w;
   if (x > n - d) return;

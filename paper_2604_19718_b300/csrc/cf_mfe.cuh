@@ -330,7 +330,11 @@ __global__ void __launch_bounds__(MFE_NT) k_mfe_light(MfeDP p, int d) {
 // warp, the exterior X5[d] = min_{k = 4..d-4} GX[k] . QB[k][d].  Inputs lie on
 // diagonals <= d - 4.  One warp per cell, lanes over split points, then a
 // warp minimum per entry.
-__global__ void __launch_bounds__(256, 2) k_mfe_bif(MfeDP p, int d) {
+// MINB CTAs per SM: two (128 registers) up to MFE_BIF2_MAXN nt, one beyond
+// (measured: 900 nt 95.9 -> 79.8 ms with two, 3000 nt 1339 -> 1443 ms)
+constexpr int MFE_BIF2_MAXN = 2000;
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_mfe_bif(MfeDP p, int d) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, n = p.n;
   const int x = blockIdx.x * 8 + w;
   if (x > n - d) return;

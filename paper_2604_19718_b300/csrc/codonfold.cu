@@ -1234,7 +1234,7 @@ cf_status mfe_graph(cf_problem *p) {
     void *args[] = {&dp, &dd};
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
-      kp.func = (void *)k_mfe_bif;
+      kp.func = n <= MFE_BIF2_MAXN ? (void *)k_mfe_bif<2> : (void *)k_mfe_bif<1>;
       kp.gridDim = dim3((n - d + 1 + 7) / 8);
       kp.blockDim = dim3(256);
       kp.kernelParams = args;

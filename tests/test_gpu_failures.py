@@ -82,6 +82,31 @@ def test_tm_wait_timeout_then_reuse():
     model.close()
 
 
+def test_tm_wait_timeout_in_clusters_then_reuse():
+    """The same at 150 nt, where the longest lengths split each cell over
+    clusters of 2, 4 and 8 CTAs: every CTA of a cluster leaves through both
+    cluster barriers, and the problem then gives its earlier log Z exactly."""
+    cf = _cf()
+    V, B, S = synth.tm_params(2, 4, 2)
+    res = synth.residues_dirichlet(50, 6)
+    model = cf.TensorModel(V, B, S)
+    f = cf.CodonFold(P0)
+    f.set_protein(res)
+    ref = {prec: f.tm_inside(model, prec) for prec in (cf.CF_FP32_SCALED, cf.CF_FP64)}
+    try:
+        cf.cf_debug_set_wait_polls(0, 0)
+        for prec in (cf.CF_FP32_SCALED, cf.CF_FP64):
+            with pytest.raises(cf.CFError) as e:
+                f.tm_inside(model, prec)
+            assert e.value.status == cf.CF_ETIMEOUT
+    finally:
+        cf.cf_debug_set_wait_polls(0, cf.WAIT_POLLS_DEFAULT)
+    for prec in (cf.CF_FP32_SCALED, cf.CF_FP64):
+        assert f.tm_inside(model, prec) == ref[prec]
+    f.close()
+    model.close()
+
+
 def test_forced_allocation_failures_leave_problem_usable():
     cf = _cf()
     res, lw, pb = _case()

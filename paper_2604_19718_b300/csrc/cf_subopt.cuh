@@ -571,7 +571,20 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
     int4 mkids[3];
     mq mkw[3];
     int kf = -1;
-    if (G == 1) {  // one group: its alternatives one per thread
+    if (G == 1 && K - cur <= 32) {
+      // at most 32 alternatives left: warp 0 alone scans and decides (warp
+      // ballot, no block barrier); the other warps go on to the next step
+      if ((t >> 5) != 0) continue;
+      const int k = cur + (t & 31);
+      bool ok = false;
+      if (k < K) {
+        mk = k;
+        mc = el_alt(p, E, k, mkids, &mnk, mkw);
+        ok = mc <= limit;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      kf = bal ? cur + __ffs(bal) - 1 : -1;
+    } else if (G == 1) {  // one group: its alternatives one per thread
       for (int b0 = cur; b0 < K && kf < 0; b0 += blockDim.x) {
         const int k = b0 + t;
         bool ok = false;

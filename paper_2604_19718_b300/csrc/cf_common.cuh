@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cf_nvtx.h"
+
 namespace cf {
 
 constexpr int NS = 6;        // maximum codon states of one residue

@@ -1634,6 +1634,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
                                     const double *pb);
 
 cf_status cf_set_protein(cf_problem *p, const char *aa, int m, const double *lw, const double *pb) {
+  CfRange nvtx_range("cf_set_protein");
   if (!p || !aa) return fail(p, CF_EINVAL, "cf_set_protein: NULL argument");
   if (m < 1) return fail(p, CF_EINVAL, "cf_set_protein: m must be >= 1");
   std::vector<int> res(m);
@@ -1788,6 +1789,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
 }
 
 cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
+  CfRange nvtx_range("cf_set_weights");
   if (!p) return fail(p, CF_EINVAL, "cf_set_weights: NULL problem");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_set_weights: no protein set");
   if (check_weights(p, p->m, lw, pb) != CF_OK) return fail(p, CF_EINVAL, "cf_set_weights: " + p->err);
@@ -1804,6 +1806,7 @@ cf_status cf_set_weights(cf_problem *p, const double *lw, const double *pb) {
 }
 
 cf_status cf_inside(cf_problem *p, cf_precision prec, double *logZ) {
+  CfRange nvtx_range("cf_inside");
   if (!p || !logZ) return fail(p, CF_EINVAL, "cf_inside: NULL argument");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_inside: no protein set");
   if (prec != CF_FP64 && prec != CF_FP32_SCALED) return fail(p, CF_EINVAL, "cf_inside: unknown precision");
@@ -1817,6 +1820,7 @@ cf_status cf_inside(cf_problem *p, cf_precision prec, double *logZ) {
 }
 
 cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double *base_marg, double *pair_grad) {
+  CfRange nvtx_range("cf_outside");
   if (!p) return fail(p, CF_EINVAL, "cf_outside: NULL problem");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_outside: run cf_inside first");
   if (pair_grad && p->layout == 1)
@@ -1852,6 +1856,7 @@ cf_status cf_outside(cf_problem *p, float *pair_prob, double *codon_marg, double
 }
 
 cf_status cf_window_logz(cf_problem *p, const uint8_t *bases, const int64_t *offsets, int nwin, double *logz) {
+  CfRange nvtx_range("cf_window_logz");
   if (!p) return fail(p, CF_EINVAL, "cf_window_logz: NULL problem");
   if (nwin < 0) return fail(p, CF_EINVAL, "cf_window_logz: nwin < 0");
   if (nwin == 0) return CF_OK;
@@ -1880,6 +1885,7 @@ const char *cf_last_error(const cf_problem *p) {
 }
 
 cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons, int32_t *partner) {
+  CfRange nvtx_range("cf_mfe");
   if (!p) return fail(p, CF_EINVAL, "cf_mfe: NULL problem");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_mfe: no protein set");
   if (p->layout == 1) return fail(p, CF_EINVAL, "cf_mfe: not available in the single-codon layout");
@@ -1892,6 +1898,7 @@ long long cf_subopt_steps(const cf_problem *p) { return p ? p->sub_steps : 0; }
 
 cf_status cf_subopt(cf_problem *p, double gap_kcal, int max_out, int64_t *cost, int32_t *codons, int32_t *partner,
                     int *count) {
+  CfRange nvtx_range("cf_subopt");
   if (!p || !count) return fail(p, CF_EINVAL, "cf_subopt: NULL argument");
   if (!(gap_kcal >= 0) || gap_kcal > 1e6 || max_out < 0) return fail(p, CF_EINVAL, "cf_subopt: bad gap or max_out");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_subopt: no protein set");
@@ -2143,6 +2150,7 @@ static cf_status tm_run(cf_problem *p, const cf_tm_model *mod, TmTables<T> &t, d
 }  // extern "C++"
 
 cf_status cf_tm_inside(cf_problem *p, const cf_tm_model *mod, cf_precision prec, double *logZ) {
+  CfRange nvtx_range("cf_tm_inside");
   if (!p || !mod || !logZ) return fail(p, CF_EINVAL, "cf_tm_inside: NULL argument");
   if (prec != CF_FP64 && prec != CF_FP32_SCALED) return fail(p, CF_EINVAL, "cf_tm_inside: unknown precision");
   if (mod->device != p->device) return fail(p, CF_EINVAL, "cf_tm_inside: model and problem on different devices");
@@ -2190,6 +2198,7 @@ int cf_checkpointed(const cf_problem *p) {
 }
 
 cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons, int32_t *partner) {
+  CfRange nvtx_range("cf_sample");
   if (!p) return fail(p, CF_EINVAL, "cf_sample: NULL problem");
   if (nsamples < 0 || (nsamples > 0 && (!codons || !partner))) return fail(p, CF_EINVAL, "cf_sample: bad arguments");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample: run cf_inside first");
@@ -2272,6 +2281,7 @@ cf_status run_sample_noalloc(cf_problem *p, PrecTables<T> &t, int ns, uint64_t s
 
 extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
                                        int32_t *partner) {
+  CfRange nvtx_range("cf_sample_noalloc");
   if (!p) return fail(p, CF_EINVAL, "cf_sample_noalloc: NULL problem");
   if (p->layout == 1) return fail(p, CF_EINVAL, "cf_sample_noalloc: not available in the single-codon layout");
   if (p->n > CF_NOALLOC_MAX_N)
@@ -2533,6 +2543,7 @@ extern "C" cf_status cf_batch_create(const cf_model *model, int device, void *st
 }
 
 extern "C" cf_status cf_batch_set_proteins(cf_batch *b, const char *aa, const double *lw, const double *pb) {
+  CfRange nvtx_range("cf_batch_set_proteins");
   if (!b || !aa) return fail(nullptr, CF_EINVAL, "cf_batch_set_proteins: NULL argument");
   cf_problem *p = b->p;
   const int B = b->B, m = b->m, n = b->n;
@@ -2607,6 +2618,7 @@ extern "C" cf_status cf_batch_set_proteins(cf_batch *b, const char *aa, const do
 }
 
 extern "C" cf_status cf_batch_run(cf_batch *b, double *logZ, float *pair_prob, double *codon_marg) {
+  CfRange nvtx_range("cf_batch_run");
   if (!b || !logZ) return fail(nullptr, CF_EINVAL, "cf_batch_run: NULL argument");
   if (!b->have) return fail(b->p, CF_ESTATE, "cf_batch_run: set the proteins first");
   CF_CUDA(b->p, cudaSetDevice(b->p->device));

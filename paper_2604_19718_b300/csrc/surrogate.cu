@@ -21,6 +21,7 @@
 // read per tap).  Weight gradients run persistent CTAs that accumulate in
 // registers over their windows and write per-CTA partials, summed in a fixed
 // order (deterministic gradients).
+#include "cf_nvtx.h"
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -661,6 +662,7 @@ cf_status cf_surrogate_get_params(const cf_surrogate *s, float *params) {
 
 cf_status cf_surrogate_predict(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, int nwin,
                                float *G_out) {
+  cf::CfRange nvtx_range("cf_surrogate_predict");
   if (!s || nwin < 0) return sfail(CF_EINVAL, "cf_surrogate_predict: bad argument");
   if (nwin == 0) return CF_OK;
   if (!bases || !offsets || !G_out) return sfail(CF_EINVAL, "cf_surrogate_predict: NULL argument");
@@ -736,6 +738,7 @@ static cf_status grad_common(cf_surrogate *s, const uint8_t *bases, const int64_
 
 cf_status cf_surrogate_grad(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, int nwin,
                             const float *G_target, float *loss_out, float *grad_out) {
+  cf::CfRange nvtx_range("cf_surrogate_grad");
   if (!s) return sfail(CF_EINVAL, "cf_surrogate_grad: NULL surrogate");
   SG_TRY(grad_common(s, bases, offsets, nwin, G_target));
   if (loss_out) SG_TRY(copy_out(s, loss_out, s->loss, sizeof(float)));
@@ -746,6 +749,7 @@ cf_status cf_surrogate_grad(cf_surrogate *s, const uint8_t *bases, const int64_t
 
 cf_status cf_surrogate_train_step(cf_surrogate *s, const uint8_t *bases, const int64_t *offsets, int nwin,
                                   const float *G_target, float lr, float *loss_out) {
+  cf::CfRange nvtx_range("cf_surrogate_train_step");
   if (!s) return sfail(CF_EINVAL, "cf_surrogate_train_step: NULL surrogate");
   if (!(lr > 0.f) || !std::isfinite(lr)) return sfail(CF_EINVAL, "cf_surrogate_train_step: lr must be > 0");
   SG_CUDA(cudaSetDevice(s->device));

@@ -656,6 +656,14 @@ def profile_form(form, steps, m=0):
             sur.predict(bases, off)
         out["ms"] = cf.cf_surrogate_last_ms(sur.h)
         sur.close()
+    elif form == "surrogate_train":  # training steps on one batch of 4,096 windows (own forward and backward kernels)
+        _, _, bases, off = synth.windows(4096, seed=3)
+        G = np.random.default_rng(3).normal(0.0, 1.0, 4096).astype(np.float32)
+        sur = cf.Surrogate(synth.surrogate_init(0), max_batch=4096)
+        for _ in range(steps):
+            out["loss"] = sur.train_step(bases, off, G, 1e-3)
+        out["ms"] = cf.cf_surrogate_last_ms(sur.h)
+        sur.close()
     elif form in ("mfe", "sample", "checkpoint"):
         res, lw, pb = synth.workload("p300_weighted")
         f = cf.CodonFold(params)
@@ -728,7 +736,7 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="use only the first M residues (profiling)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the window, surrogate, adjoint and 3000-nt measurements")
-    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "mfe", "sample", "windows", "checkpoint", "tm", "subopt", "batch"],
+    ap.add_argument("--profile-form", default="", choices=["", "surrogate", "surrogate_train", "mfe", "sample", "windows", "checkpoint", "tm", "subopt", "batch"],
                     help="run one form on a small case (for profiler captures) and print its timing")
     args = ap.parse_args()
     if args.impl == "reference":

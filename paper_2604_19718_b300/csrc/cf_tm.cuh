@@ -191,7 +191,9 @@ __device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
 // consumer warp arrives on the stage's "empty" mbarrier when it is done
 // with it, and the producer waits for all five before refilling it, so no
 // block barrier runs per group.  A wait that runs out sets the error and a
-// shared stop flag; the producer then drains its copies in flight.
+// shared stop flag; the producer then drains its copies in flight.  Launches
+// with few long cells split each cell's groups over a cluster of 2, 4 or 8
+// CTAs, whose partial sums rank 0 adds over distributed shared memory.
 constexpr int TM_NC = TM_D * NS;       // 144 consumer threads
 constexpr int TM_NCW = 5;              // consumer warps (the last has 16 idle lanes)
 constexpr int TM_NTH = 32 * (1 + TM_NCW);  // 192 threads
@@ -227,11 +229,11 @@ __host__ __device__ constexpr size_t tm_cell_smem() {
 // barrier 1 among the consumer warps only
 __device__ __forceinline__ void tm_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TM_NCW) : "memory"); }
 // Launches with few cells split each cell's groups over a cluster of two
-// CTAs (TM_SPLIT_CELLS cells or fewer, TM_SPLIT_GROUPS groups or more), or
-// of four (TM_SPLIT4_CELLS cells or fewer, TM_SPLIT4_GROUPS groups or more).
+// CTAs (TM_SPLIT_CELLS cells or fewer, TM_SPLIT_GROUPS groups or more), of
+// four (TM_SPLIT4_*) or of eight (TM_SPLIT8_*).
 constexpr int TM_SPLIT_CELLS = 444, TM_SPLIT_GROUPS = 8, TM_SPLIT4_CELLS = 148, TM_SPLIT4_GROUPS = 16;
 constexpr int TM_SPLIT8_CELLS = 74, TM_SPLIT8_GROUPS = 32;
-// every thread of both CTAs of the cluster
+// every thread of every CTA of the cluster
 __device__ __forceinline__ void tm_cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
   asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");

@@ -21,7 +21,8 @@
 // matrix product per column (Alg. fast-pf); here it runs by interval length
 // (anti-diagonals), like the nearest-neighbour path: per length L, the folds
 // of the pairs at distance L-1 (k_tm_fold) and then the cells of length L
-// (k_tm_cell, one CTA per cell), so that a per-length power-of-two exponent
+// (k_tm_cell, one CTA per cell, or a cluster of CTAs per cell when a length
+// has few cells), so that a per-length power-of-two exponent
 // E[L] keeps binary32 mantissas in range: Q and L of length L carry E[L], F
 // of distance D carries E[D-1], and every product term takes the exact
 // factor 2^{E[.] + E[.] - E[L]}.  E[L] is set from the largest mantissa of

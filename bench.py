@@ -611,9 +611,15 @@ def bench_layout(stream, steps=10):
             a, b, _, _ = f.timing()
             tin, tout = tin + a, tout + b
         _, st = cf.cf_layout_states(f.prob, f.n)
+        f.sample(1000, 3)  # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        f.sample(10_000, 7)
+        torch.cuda.synchronize()
+        sps = 10_000 / (time.perf_counter() - t)
         f.close()
         out[key] = {"inside_ms": tin / steps, "outside_ms": tout / steps, "ms_per_step": (tin + tout) / steps,
-                    "mean_states_per_position": float(np.mean(st)), "logZ": lz}
+                    "mean_states_per_position": float(np.mean(st)), "logZ": lz, "samples_per_s": sps}
     torch.cuda.synchronize()
     out["speedup"] = out["codon_states"]["ms_per_step"] / out["single_codon"]["ms_per_step"]
     return out

@@ -227,7 +227,9 @@ long long cf_subopt_steps(const cf_problem *prob);
  * pair probabilities, codon
  * and base marginals; it has no codon-pair bonuses (cf_set_protein and
  * cf_set_weights reject pair_bonus != NULL, cf_outside a pair_grad output),
- * and cf_sample, cf_sample_noalloc and cf_mfe return CF_EINVAL in it.
+ * and cf_mfe and cf_subopt return CF_EINVAL in it.  The samplers serve
+ * both layouts: in layout 1 a residue's codon is read off the states of
+ * its second and third positions.
  * cf_set_layout takes effect at the next cf_set_protein; a batch keeps
  * layout 0.  cf_layout_states reports the current protein's layout and, if
  * states != NULL, its n per-position state counts.

@@ -83,6 +83,7 @@ template <typename T>
 struct SampleArgs {
   DP<T> p;
   const int *cid;   // [n*6] sense codon id of state a at position p
+  const int *sctab; // single-codon layout: [m][36] codon of the states at 3r+1, 3r+2 (see below); else null
   int nsamples;
   uint64_t seed;
   int2 *stack;      // [warps][n + 64]
@@ -487,9 +488,20 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs<T> s) {
     __threadfence_block();
     for (int r = lane; r < m; r += 32) {
       int q = 3 * r;
-      int a = st[q];
-      if (a < 0 || st[q + 1] != a || st[q + 2] != a) bad = bad ? bad : 21;
-      s.codons[(size_t)smp * m + r] = (a >= 0) ? s.cid[q * NS + a] : -1;
+      int cod = -1;
+      if (s.sctab) {
+        // single-codon layout: the states at 3r+1 (first and second base)
+        // and 3r+2 (third base) fix the codon, which fixes the state at 3r
+        const int a1 = st[q + 1], a2 = st[q + 2];
+        const int e = (a1 >= 0 && a2 >= 0) ? s.sctab[(size_t)r * BLK + a1 * NS + a2] : -1;
+        if (e < 0 || st[q] != (e >> 8)) bad = bad ? bad : 21;
+        cod = e >= 0 ? (e & 255) : -1;
+      } else {
+        const int a = st[q];
+        if (a < 0 || st[q + 1] != a || st[q + 2] != a) bad = bad ? bad : 21;
+        cod = (a >= 0) ? s.cid[q * NS + a] : -1;
+      }
+      s.codons[(size_t)smp * m + r] = cod;
     }
     bad = __reduce_max_sync(0xffffffffu, bad);
     if (bad && lane == 0) atomicCAS(s.err, 0, bad);

@@ -208,6 +208,10 @@ struct cf_problem {
   std::vector<int> smap;   // single-codon layout: [m][6] packed states and bases of each codon slot
   std::vector<int> sc1;    // single-codon layout: first base of each state at a residue's second position
   int *dsmap = nullptr;
+  // single-codon layout: per residue and (state at 3r+1, state at 3r+2) the
+  // sense codon id | (the state it needs at 3r) << 8, -1 for no codon
+  std::vector<int> sctab;
+  int *dsctab = nullptr;
   int nls = 0;             // per-transfer log rescales undone in log Z
   // tensor-based model (cf_tm_inside)
   std::vector<void *> tm_allocs;
@@ -1017,6 +1021,7 @@ cf_status run_sample(cf_problem *p, PrecTables<T> &t, int ns, uint64_t seed, int
   SampleArgs<T> a;
   a.p = t.dp;
   a.cid = p->dcid;
+  a.sctab = p->layout == 1 ? p->dsctab : nullptr;
   a.nsamples = ns;
   a.seed = seed;
   a.stack = p->smp_stack;
@@ -1608,7 +1613,7 @@ static void release_protein(cf_problem *p) {
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
   p->dcm = p->dbm = p->dpg = nullptr;
   p->dcid = nullptr;
-  p->dsmap = nullptr;
+  p->dsmap = p->dsctab = nullptr;
   p->dlw = p->dpb = p->dTr64 = p->dX64 = p->den64 = p->dls = p->dlogz = nullptr;
   p->dP = nullptr;
   p->have_inside = false;
@@ -1682,6 +1687,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   p->bnd.assign(n, 0);
   p->smap.assign((size_t)m * 6, -1);
   p->sc1.assign((size_t)n * NS, -1);
+  p->sctab.assign((size_t)m * BLK, -1);
   for (int r = 0; r < m; r++) {
     const auto &cods = gc.codons[res[r]];
     if (p->layout == 0) {
@@ -1731,6 +1737,8 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
         const int a = (int)(std::lower_bound(PR.begin(), PR.end(), c >> 2 & 15) - PR.begin());
         const int b = (int)(std::lower_bound(L.begin(), L.end(), c & 3) - L.begin());
         p->smap[(size_t)r * 6 + s2] = a | (b << 4) | ((c >> 4 & 3) << 8) | ((c >> 2 & 3) << 10) | ((c & 3) << 12);
+        const int a0 = (int)(std::lower_bound(F.begin(), F.end(), c >> 4 & 3) - F.begin());
+        p->sctab[(size_t)r * BLK + a * NS + b] = gc.sense_id[c] | (a0 << 8);
       }
     }
   }
@@ -1765,6 +1773,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
     CF_CUDA(p, dalloc(S, &p->den64, (size_t)EN_N));
     CF_CUDA(p, dalloc(S, &p->dls, (size_t)std::max(m, 1)));
     CF_CUDA(p, dalloc(S, &p->dsmap, (size_t)m * 6));
+    CF_CUDA(p, dalloc(S, &p->dsctab, (size_t)m * BLK));
     CF_CUDA(p, dalloc(S, &p->dlogz, (size_t)1));
     CF_CUDA(p, cudaMemcpy(p->den64, p->model->en, sizeof(double) * EN_N, cudaMemcpyHostToDevice));
   }
@@ -1774,6 +1783,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   CF_CUDA(p, cudaMemcpyAsync(p->dbnd, p->bnd.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dsmap, p->smap.data(), sizeof(int) * m * 6, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dsctab, p->sctab.data(), sizeof(int) * m * BLK, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
   if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
   CF_CUDA(p, cudaStreamSynchronize(st));
@@ -2202,7 +2212,6 @@ cf_status cf_sample(cf_problem *p, int nsamples, uint64_t seed, int32_t *codons,
   if (!p) return fail(p, CF_EINVAL, "cf_sample: NULL problem");
   if (nsamples < 0 || (nsamples > 0 && (!codons || !partner))) return fail(p, CF_EINVAL, "cf_sample: bad arguments");
   if (!p->have_inside) return fail(p, CF_ESTATE, "cf_sample: run cf_inside first");
-  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_sample: not available in the single-codon layout");
   if (nsamples == 0) return CF_OK;
   CF_CUDA(p, cudaSetDevice(p->device));
   return (p->last_prec == CF_FP64) ? run_sample(p, p->f64, nsamples, seed, codons, partner)
@@ -2262,6 +2271,7 @@ cf_status run_sample_noalloc(cf_problem *p, PrecTables<T> &t, int ns, uint64_t s
   SampleArgs<T> a;
   a.p = t.dp;
   a.cid = p->dcid;
+  a.sctab = p->layout == 1 ? p->dsctab : nullptr;
   a.nsamples = ns;
   a.seed = seed;
   a.stack = stack;
@@ -2283,7 +2293,6 @@ extern "C" cf_status cf_sample_noalloc(cf_problem *p, int nsamples, uint64_t see
                                        int32_t *partner) {
   CfRange nvtx_range("cf_sample_noalloc");
   if (!p) return fail(p, CF_EINVAL, "cf_sample_noalloc: NULL problem");
-  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_sample_noalloc: not available in the single-codon layout");
   if (p->n > CF_NOALLOC_MAX_N)
     return fail(p, CF_EINVAL, "cf_sample_noalloc: sequence length " + std::to_string(p->n) +
                                   " exceeds CF_NOALLOC_MAX_N = " + std::to_string(CF_NOALLOC_MAX_N));

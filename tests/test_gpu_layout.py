@@ -3,7 +3,8 @@ same protein gives the same log Z, pair probabilities, codon and base
 marginals as the codon-state layout and the oracle, in both precisions, with
 codon weights; the tensor-based model's log Z is the same in both layouts;
 the state counts are the distinct first bases, (first, second) pairs and
-third bases, 1.5-1.8 per position; the calls the layout does not serve are refused."""
+third bases, 1.5-1.8 per position; the sampler draws the brute-force
+distribution and the oracle's codon marginals in this layout too; the calls the layout does not serve are refused."""
 import numpy as np
 import pytest
 
@@ -53,6 +54,69 @@ def test_same_results_as_codon_states(prec, m, seed):
         assert np.abs(b[2] - o["codon"]).max() <= 1e-5
 
 
+def _layout1_fold(res, lw, prec):
+    cf = _cf()
+    f = cf.CodonFold(P0)
+    cf.cf_set_layout(f.prob, 1)
+    f.set_protein(res, lw)
+    f.inside(prec)
+    return f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sampler_exact_distribution(prec):
+    """The sampler in the single-codon layout draws (codon sequence,
+    structure) with the brute-force probabilities (chi-square, 3 residues
+    with codon weights)."""
+    import math
+    import bruteforce as bf
+    res = [1, 15, 10]  # R, S, L: six codons each, the layout's (first, second) pairs differ most
+    lw = np.random.default_rng(11).normal(0, 0.5, (3, 6))
+    b = bf.summary(P0, res, lw, None)
+    probs = {}
+    for _, cids, pt, w in b["ensemble"]:
+        probs[(cids, pt)] = probs.get((cids, pt), 0.0) + w / b["Z"]
+    f = _layout1_fold(res, lw, prec)
+    N = 200000
+    cod, par = f.sample(N, 17)
+    f.close()
+    cnt = {}
+    for c, x in zip(map(tuple, cod), map(tuple, par)):
+        cnt[(c, x)] = cnt.get((c, x), 0) + 1
+    assert all(k in probs for k in cnt), "sample outside the ensemble"
+    chi, dof = 0.0, 0
+    for k, pr in probs.items():
+        e = N * pr
+        if e >= 5:
+            chi += (cnt.get(k, 0) - e) ** 2 / e
+            dof += 1
+    z = ((chi / dof) ** (1 / 3) - (1 - 2 / (9 * dof))) / math.sqrt(2 / (9 * dof))
+    assert z < 3.8, (chi, dof)
+
+
+def test_sampler_marginals_reproducible():
+    """30 residues in the single-codon layout: codon frequencies match the
+    oracle's marginals within 4.5 sigma, every codon belongs to its residue,
+    and the same seed gives the same samples."""
+    import math
+    res = synth.residues_dirichlet(30, 8)
+    lw = np.random.default_rng(8).normal(0, 0.5, (30, 6))
+    o = oracle.outside(P0, res, lw, None)
+    f = _layout1_fold(res, lw, 1)
+    N = 20000
+    cod, par = f.sample(N, 5)
+    cod2, par2 = f.sample(N, 5)
+    f.close()
+    assert np.array_equal(cod, cod2) and np.array_equal(par, par2)
+    for r in range(len(res)):
+        allowed = oracle.codons_of(res[r])
+        assert set(np.unique(cod[:, r])) <= set(allowed)
+        for s_, cid in enumerate(allowed):
+            p = o["codon"][r, s_]
+            fr = np.mean(cod[:, r] == cid)
+            assert abs(fr - p) <= 4.5 * math.sqrt(p * (1 - p) / N) + 1e-9
+
+
 def test_state_counts():
     res = [10, 1, 15, 12, 17]  # L, R, S, M, W
     lay, st = _run(res, None, 1, 1)[4:]
@@ -95,7 +159,7 @@ def test_refusals():
     assert e.value.status == cf.CF_EINVAL
     f.set_protein([1, 2, 3, 4, 5])
     f.inside(1)
-    for call in (lambda: f.sample(4, 1), lambda: f.mfe(), lambda: f.outside(True, True, True),
+    for call in (lambda: f.subopt(0.5, 10), lambda: f.mfe(), lambda: f.outside(True, True, True),
                  lambda: f.set_weights(None, np.zeros((61, 61)))):
         with pytest.raises(cf.CFError) as e:
             call()

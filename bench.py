@@ -617,9 +617,13 @@ def bench_layout(stream, steps=10):
         f.sample(10_000, 7)
         torch.cuda.synchronize()
         sps = 10_000 / (time.perf_counter() - t)
+        f.mfe()  # warm-up: tables and graph
+        f.mfe()
+        mfe_ms = cf.cf_mfe_last_ms(f.prob)
         f.close()
         out[key] = {"inside_ms": tin / steps, "outside_ms": tout / steps, "ms_per_step": (tin + tout) / steps,
-                    "mean_states_per_position": float(np.mean(st)), "logZ": lz, "samples_per_s": sps}
+                    "mean_states_per_position": float(np.mean(st)), "logZ": lz, "samples_per_s": sps,
+                    "mfe_ms_with_traceback": mfe_ms}
     torch.cuda.synchronize()
     out["speedup"] = out["codon_states"]["ms_per_step"] / out["single_codon"]["ms_per_step"]
     return out

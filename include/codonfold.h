@@ -202,8 +202,7 @@ float cf_mfe_last_ms(const cf_problem *prob);
  * short); cf_mfe_last_ms reports the time.  The search keeps the states
  * and partners of the configuration it builds (8 n bytes) and its 512
  * deepest frames in shared memory, hence n <= CF_SUBOPT_MAX_N.  Errors: CF_EINVAL (NULL problem or count,
- * gap < 0 or > 1e6, max_out < 0, device outputs, the single-codon layout,
- * n > CF_SUBOPT_MAX_N), CF_ESTATE (no protein), CF_ENUMERIC (no finite
+ * gap < 0 or > 1e6, max_out < 0, device outputs, n > CF_SUBOPT_MAX_N), CF_ESTATE (no protein), CF_ENUMERIC (no finite
  * configuration, an inconsistency), CF_ENOMEM, CF_ECUDA.
  */
 #define CF_SUBOPT_MAX_N 20000
@@ -227,9 +226,10 @@ long long cf_subopt_steps(const cf_problem *prob);
  * pair probabilities, codon
  * and base marginals; it has no codon-pair bonuses (cf_set_protein and
  * cf_set_weights reject pair_bonus != NULL, cf_outside a pair_grad output),
- * and cf_mfe and cf_subopt return CF_EINVAL in it.  The samplers serve
- * both layouts: in layout 1 a residue's codon is read off the states of
- * its second and third positions.
+ * and every other call serves both layouts: in layout 1 the samplers, the
+ * MFE traceback and the suboptimal search read a residue's codon off the
+ * states of its second and third positions, and the MFE and its
+ * suboptimal sets are the same as with codon states (integer costs).
  * cf_set_layout takes effect at the next cf_set_protein; a batch keeps
  * layout 0.  cf_layout_states reports the current protein's layout and, if
  * states != NULL, its n per-position state counts.

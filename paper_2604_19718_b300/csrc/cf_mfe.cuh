@@ -86,13 +86,19 @@ __device__ __forceinline__ mq mm2(const mq *A, const mq *B, int a, int b) {
 // residue r to r+1 (q = 3r + 2): cost(lw[r+1][b]) + cost(pb[c_a][c_b]); the
 // typed transitions add the dangle costs of a paired end (3' dangle of a
 // paired base at q, 5' dangle of a paired base at q+1).  One thread per q.
+// Single-codon layout (smap, sc1 non-null): tau_3r joins a first base to the
+// (first, second) pairs that start with it at cost 0, tau_3r+1 joins a pair
+// to a third base at the cost of the codon's weight (smap[r][slot] packs the
+// codon's two states), tau_3r+2 joins any two states at cost 0 (the layout
+// has no pair bonuses), and residue 0's states cost nothing.
 __device__ __forceinline__ mq mq_weight(double kT, double w) { return llround(__dmul_rn(-__dmul_rn(kT, w), 4294967296.0)); }
 
 __global__ void k_mfe_transfers(int n, const int *Mp, const int *base, const int *cid, const mq *en, double kT,
-                                const double *lw, const double *pb, mq *tau, mq *chi, mq *u0) {
+                                const double *lw, const double *pb, mq *tau, mq *chi, mq *u0,
+                                const int *smap = nullptr, const int *sc1 = nullptr) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q == 0)
-    for (int a = 0; a < NS; a++) u0[a] = a < Mp[0] ? mq_weight(kT, lw[a]) : MQINF;
+    for (int a = 0; a < NS; a++) u0[a] = a < Mp[0] ? (smap ? 0 : mq_weight(kT, lw[a])) : MQINF;
   if (q >= n) return;
   const int Ma = Mp[q], Mb = q + 1 < n ? Mp[q + 1] : 0;
   for (int a = 0; a < NS; a++)
@@ -100,7 +106,19 @@ __global__ void k_mfe_transfers(int n, const int *Mp, const int *base, const int
       const int e = a * NS + b;
       mq t = MQINF, d3 = 0, d5 = 0;
       if (a < Ma && b < Mb) {
-        if (q % 3 != 2) {
+        if (smap) {
+          const int r = q / 3;
+          if (q % 3 == 0) {
+            t = base[(size_t)q * NS + a] == sc1[(size_t)(q + 1) * NS + b] ? 0 : MQINF;
+          } else if (q % 3 == 1) {
+            for (int s2 = 0; s2 < 6; s2++) {
+              const int sm = smap[(size_t)r * 6 + s2];
+              if (sm >= 0 && (sm & 15) == a && ((sm >> 4) & 15) == b) t = mq_weight(kT, lw[(size_t)r * 6 + s2]);
+            }
+          } else {
+            t = 0;
+          }
+        } else if (q % 3 != 2) {
           t = a == b ? 0 : MQINF;
         } else {
           const int r1 = (q + 1) / 3;
@@ -402,7 +420,19 @@ struct MfeTrace {
   int cap;
   int *state;    // [n] codon state per position
   int32_t *codons, *partner;
+  const int *sctab;  // single-codon layout: [m][36] codon | (state at 3r) << 8 of the states at 3r+1, 3r+2; else null
 };
+
+// the codon of residue r from the traced states: the state at 3r (codon
+// states), or, in the single-codon layout, the states at 3r+1 and 3r+2
+// (checked against the state at 3r); -1 if they do not form one
+__device__ __forceinline__ int traced_codon(const int *cid, const int *sctab, const int *state, int r) {
+  const int q = 3 * r;
+  if (!sctab) return state[q] >= 0 ? cid[q * NS + state[q]] : -1;
+  const int a1 = state[q + 1], a2 = state[q + 2];
+  const int e = (a1 >= 0 && a2 >= 0) ? sctab[(size_t)r * BLK + a1 * NS + a2] : -1;
+  return (e >= 0 && state[q] == (e >> 8)) ? (e & 255) : -1;
+}
 
 template <typename F>
 __device__ int cta_first(int K, mq target, const F &cost, int *sfirst) {
@@ -723,8 +753,9 @@ __global__ void __launch_bounds__(256) k_mfe_trace(MfeTrace T) {
     if (T.state[q] < 0 && !sbad) atomicOr(p.err, 1 << 5);
   __syncthreads();
   for (int r = t; r < p.m; r += blockDim.x) {
-    const int s = T.state[3 * r];
-    T.codons[r] = (sbad || s < 0) ? -1 : p.cid[3 * r * NS + s];
+    const int c = traced_codon(p.cid, T.sctab, T.state, r);
+    if (c < 0 && !sbad) atomicOr(p.err, 1 << 5);
+    T.codons[r] = sbad ? -1 : c;
   }
   if (t == 0 && sbad) atomicOr(p.err, 1 << 4);
 }

@@ -449,6 +449,7 @@ struct SubArgs {
   long long max_steps;
   unsigned long long max_ns;  // the enumeration stops (with an error) past this device time
   int32_t *codons, *partner;  // [max_out][m], [max_out][n]
+  const int *sctab;           // single-codon layout: the codon table of traced_codon; else null
   long long *cost;            // [max_out]
   long long *count;           // [2]: configurations found (capped at max_out + 1), steps taken
 };
@@ -705,8 +706,9 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
       const long long idx = sfound;
       if (idx < s.max_out) {
         for (int r = 0; r < p.m; r++) {
-          const int st = scs[3 * r];
-          s.codons[(size_t)idx * p.m + r] = st >= 0 ? p.cid[3 * r * NS + st] : -1;
+          const int c = traced_codon(p.cid, s.sctab, scs, r);
+          if (c < 0) sbad = 6;
+          s.codons[(size_t)idx * p.m + r] = c;
         }
         for (int q = 0; q < n; q++) s.partner[(size_t)idx * n + q] = scs[n + q];
         s.cost[idx] = best + (s.gap - nslack);

@@ -212,6 +212,7 @@ struct cf_problem {
   // sense codon id | (the state it needs at 3r) << 8, -1 for no codon
   std::vector<int> sctab;
   int *dsctab = nullptr;
+  int *dsc1 = nullptr;  // sc1 on the device (the MFE's transfer costs)
   int nls = 0;             // per-transfer log rescales undone in log Z
   // tensor-based model (cf_tm_inside)
   std::vector<void *> tm_allocs;
@@ -1296,7 +1297,8 @@ cf_status run_mfe(cf_problem *p, int64_t *cost, double *kcal, int32_t *codons, i
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   // the transfer costs of the current weights (cf_set_weights may have changed them)
   k_mfe_transfers<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, t.dp.en, p->model->kT, p->dlw,
-                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0);
+                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0,
+                                                    p->layout == 1 ? p->dsmap : nullptr, p->layout == 1 ? p->dsc1 : nullptr);
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaGraphLaunch(t.g, st));
   const bool trace = codons || partner;
@@ -1308,6 +1310,7 @@ cf_status run_mfe(cf_problem *p, int64_t *cost, double *kcal, int32_t *codons, i
     tr.state = t.state;
     tr.codons = kc > 0 ? codons : t.codons;
     tr.partner = kp > 0 ? partner : t.partner;
+    tr.sctab = p->layout == 1 ? p->dsctab : nullptr;
     k_mfe_trace<<<1, 256, 0, st>>>(tr);
     CF_CUDA(p, cudaGetLastError());
   }
@@ -1346,11 +1349,13 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   CF_CUDA(p, cudaMemsetAsync(p->derr, 0, sizeof(int), st));
   CF_CUDA(p, cudaEventRecord(p->ev[0], st));
   k_mfe_transfers<<<(n + 127) / 128, 128, 0, st>>>(n, p->dM, p->dbase, p->dcid, t.dp.en, p->model->kT, p->dlw,
-                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0);
+                                                    p->dpb, (mq *)t.dp.tau, (mq *)t.dp.chi, (mq *)t.dp.u0,
+                                                    p->layout == 1 ? p->dsmap : nullptr, p->layout == 1 ? p->dsc1 : nullptr);
   CF_CUDA(p, cudaGetLastError());
   CF_CUDA(p, cudaGraphLaunch(t.g, st));
   SubArgs a;
   a.p = t.dp;
+  a.sctab = p->layout == 1 ? p->dsctab : nullptr;
   a.gap = gap;
   a.max_out = max_out;
   a.pcap = 4 * n + 64;
@@ -1613,7 +1618,7 @@ static void release_protein(cf_problem *p) {
   p->du0 = p->dZm = p->dtrans = p->dp0 = nullptr;
   p->dcm = p->dbm = p->dpg = nullptr;
   p->dcid = nullptr;
-  p->dsmap = p->dsctab = nullptr;
+  p->dsmap = p->dsctab = p->dsc1 = nullptr;
   p->dlw = p->dpb = p->dTr64 = p->dX64 = p->den64 = p->dls = p->dlogz = nullptr;
   p->dP = nullptr;
   p->have_inside = false;
@@ -1774,6 +1779,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
     CF_CUDA(p, dalloc(S, &p->dls, (size_t)std::max(m, 1)));
     CF_CUDA(p, dalloc(S, &p->dsmap, (size_t)m * 6));
     CF_CUDA(p, dalloc(S, &p->dsctab, (size_t)m * BLK));
+    CF_CUDA(p, dalloc(S, &p->dsc1, (size_t)n * NS));
     CF_CUDA(p, dalloc(S, &p->dlogz, (size_t)1));
     CF_CUDA(p, cudaMemcpy(p->den64, p->model->en, sizeof(double) * EN_N, cudaMemcpyHostToDevice));
   }
@@ -1784,6 +1790,7 @@ static cf_status set_protein_tables(cf_problem *p, const std::vector<int> &res, 
   CF_CUDA(p, cudaMemcpyAsync(p->dcid, p->cid.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dsmap, p->smap.data(), sizeof(int) * m * 6, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemcpyAsync(p->dsctab, p->sctab.data(), sizeof(int) * m * BLK, cudaMemcpyHostToDevice, st));
+  CF_CUDA(p, cudaMemcpyAsync(p->dsc1, p->sc1.data(), sizeof(int) * n * NS, cudaMemcpyHostToDevice, st));
   CF_CUDA(p, cudaMemsetAsync(p->dE, 0, sizeof(int) * n, st));
   if (cf_status ts = device_transfers(p, lw, pb); ts != CF_OK) return ts;
   CF_CUDA(p, cudaStreamSynchronize(st));
@@ -1898,7 +1905,6 @@ cf_status cf_mfe(cf_problem *p, int64_t *cost, double *mfe_kcal, int32_t *codons
   CfRange nvtx_range("cf_mfe");
   if (!p) return fail(p, CF_EINVAL, "cf_mfe: NULL problem");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_mfe: no protein set");
-  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_mfe: not available in the single-codon layout");
   CF_CUDA(p, cudaSetDevice(p->device));
   return run_mfe(p, cost, mfe_kcal, codons, partner);
 }
@@ -1912,7 +1918,6 @@ cf_status cf_subopt(cf_problem *p, double gap_kcal, int max_out, int64_t *cost, 
   if (!p || !count) return fail(p, CF_EINVAL, "cf_subopt: NULL argument");
   if (!(gap_kcal >= 0) || gap_kcal > 1e6 || max_out < 0) return fail(p, CF_EINVAL, "cf_subopt: bad gap or max_out");
   if (p->n == 0) return fail(p, CF_ESTATE, "cf_subopt: no protein set");
-  if (p->layout == 1) return fail(p, CF_EINVAL, "cf_subopt: not available in the single-codon layout");
   if (ptr_kind(cost, p->device) != 0 || ptr_kind(codons, p->device) != 0 || ptr_kind(partner, p->device) != 0)
     return fail(p, CF_EINVAL, "cf_subopt: outputs must be host memory");
   if (p->n > CF_SUBOPT_MAX_N) return fail(p, CF_EINVAL, "cf_subopt: protein longer than CF_SUBOPT_MAX_N nt");

@@ -4,7 +4,9 @@ marginals as the codon-state layout and the oracle, in both precisions, with
 codon weights; the tensor-based model's log Z is the same in both layouts;
 the state counts are the distinct first bases, (first, second) pairs and
 third bases, 1.5-1.8 per position; the sampler draws the brute-force
-distribution and the oracle's codon marginals in this layout too; the calls the layout does not serve are refused."""
+distribution and the oracle's codon marginals in this layout too; the MFE,
+its configuration and the suboptimal sets equal those with codon states; the
+calls the layout does not serve are refused."""
 import numpy as np
 import pytest
 
@@ -117,6 +119,31 @@ def test_sampler_marginals_reproducible():
             assert abs(fr - p) <= 4.5 * math.sqrt(p * (1 - p) / N) + 1e-9
 
 
+@pytest.mark.parametrize("m,seed,gap", [(4, 21, 1.5), (40, 22, 0.3)])
+def test_mfe_and_subopt_same_in_both_layouts(m, seed, gap):
+    """Integer costs do not depend on which transfer carries a codon's
+    weight: the minimum, its configuration and every suboptimal set are the
+    same in both layouts."""
+    cf = _cf()
+    res = synth.residues_dirichlet(m, seed)
+    lw = np.random.default_rng(seed).normal(0, 0.5, (m, 6))
+    out = {}
+    for layout in (0, 1):
+        f = cf.CodonFold(P0)
+        cf.cf_set_layout(f.prob, layout)
+        f.set_protein(res, lw)
+        q, kc, cod, par = f.mfe()
+        cnt, cost, scod, spar = f.subopt(gap, 5000)
+        f.close()
+        sub = sorted((int(cost[i]), tuple(int(x) for x in scod[i]), tuple(int(x) for x in spar[i]))
+                     for i in range(min(cnt, 5000)))
+        out[layout] = (q, tuple(int(x) for x in cod), tuple(int(x) for x in par), cnt, sub)
+    assert out[0][0] == out[1][0]
+    assert out[0][1:3] == out[1][1:3]
+    assert out[0][3] == out[1][3] and out[0][4] == out[1][4]
+    assert out[0][3] >= 1
+
+
 def test_state_counts():
     res = [10, 1, 15, 12, 17]  # L, R, S, M, W
     lay, st = _run(res, None, 1, 1)[4:]
@@ -159,8 +186,7 @@ def test_refusals():
     assert e.value.status == cf.CF_EINVAL
     f.set_protein([1, 2, 3, 4, 5])
     f.inside(1)
-    for call in (lambda: f.subopt(0.5, 10), lambda: f.mfe(), lambda: f.outside(True, True, True),
-                 lambda: f.set_weights(None, np.zeros((61, 61)))):
+    for call in (lambda: f.outside(True, True, True), lambda: f.set_weights(None, np.zeros((61, 61)))):
         with pytest.raises(cf.CFError) as e:
             call()
         assert e.value.status == cf.CF_EINVAL

@@ -436,6 +436,8 @@ struct SubFrame {
 };
 
 constexpr int SUB_RING = 512;  // frames kept in shared memory (the deepest ones), the rest in global memory
+constexpr int SUB_NT = 256;    // threads of the search CTA (512 was slower: 4.23 against 4.13 s at 900 nt)
+constexpr int SUB_NW = SUB_NT / 32;
 
 struct SubArgs {
   MfeDP p;
@@ -469,7 +471,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // The smallest k over the block for which ok holds (INT_MAX if none), k
 // increasing with the thread index; one block barrier, the per-warp minima
 // double-buffered by round parity.
-__device__ __forceinline__ int block_first(bool ok, int k, int (*swmin)[8], int &par) {
+__device__ __forceinline__ int block_first(bool ok, int k, int (*swmin)[SUB_NW], int &par) {
   const unsigned b = __ballot_sync(0xffffffffu, ok);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int kw = b ? __shfl_sync(0xffffffffu, k, __ffs(b) - 1) : INT_MAX;
@@ -477,7 +479,7 @@ __device__ __forceinline__ int block_first(bool ok, int k, int (*swmin)[8], int 
   __syncthreads();
   int m = INT_MAX;
 #pragma unroll
-  for (int i = 0; i < 8; i++) m = min(m, swmin[par][i]);
+  for (int i = 0; i < SUB_NW; i++) m = min(m, swmin[par][i]);
   par ^= 1;
   return m;
 }
@@ -514,7 +516,7 @@ __device__ __forceinline__ void el_decide(int n, int4 E, int *scs, SubFrame &f, 
   }
 }
 
-__global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
+__global__ void __launch_bounds__(SUB_NT) k_mfe_subopt(SubArgs s) {
   const MfeDP &p = s.p;
   const unsigned long long t0 = global_ns();
   const int n = p.n, t = threadIdx.x;
@@ -522,11 +524,11 @@ __global__ void __launch_bounds__(256) k_mfe_subopt(SubArgs s) {
   int *scs = reinterpret_cast<int *>(sub_smem_raw);  // [n] state of each position, then [n] partner (-1: not yet)
   SubFrame *ring = reinterpret_cast<SubFrame *>(sub_smem_raw + ((size_t)2 * n * sizeof(int) + 15) / 16 * 16);
   int *rtag = reinterpret_cast<int *>(ring + SUB_RING);  // the frame index each ring slot holds
-  __shared__ int sdepth, sbad, sdone, scur, swmin[2][8];
+  __shared__ int sdepth, sbad, sdone, scur, swmin[2][SUB_NW];
   __shared__ int4 sE;
   __shared__ long long sfound, sslack, swant;
   __shared__ mq souter;
-  __shared__ int swsum[8], spref[257], sk0[256];  // blockDim.x = 256
+  __shared__ int swsum[SUB_NW], spref[SUB_NT + 1], sk0[SUB_NT];  // blockDim.x = SUB_NT
   const mq best = *p.best;
   for (int q = t; q < 2 * n; q += blockDim.x) scs[q] = -1;
   for (int q = t; q < SUB_RING; q += blockDim.x) rtag[q] = -1;

@@ -1390,7 +1390,7 @@ cf_status run_subopt(cf_problem *p, long long gap, int max_out, long long *cost,
   e = cudaGetLastError();
   const size_t ssm = sub_smem(n);  // the states and partners, the frame ring
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void *)k_mfe_subopt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-  if (e == cudaSuccess) k_mfe_subopt<<<1, 256, ssm, st>>>(a);
+  if (e == cudaSuccess) k_mfe_subopt<<<1, SUB_NT, ssm, st>>>(a);
   if (e == cudaSuccess) e = cudaGetLastError();
   long long cnt[2] = {0, 0};
   int err = 0;

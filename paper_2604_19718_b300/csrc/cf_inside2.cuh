@@ -460,9 +460,9 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
 
 // binary32 with far bands: CTA b < last takes cells 4b..4b+3, the last CTA the
 // exterior sum with all eight warps; 64 registers, so that a CTA leaves room
-// for the light kernel's CTAs on its SM
+// for the light kernel's CTAs on its SM (binary64: 128, since 64 spilled)
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, 4 / (sizeof(T) / sizeof(float))) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
     in_bif_ext_group<T>(p, bb, d, red);
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, in
 // that a single protein's kernels read their table pointers straight from the
 // parameter bank.)
 template <typename T, bool BT = false>
-__global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? 2 : 1) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? (BT ? 3 : 2) : 1) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;

@@ -1198,9 +1198,13 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 // far bands: four cells per CTA, then the exterior, at 64 registers so that
 // the CTAs leave room for the light kernels; else one cell per CTA), the
 // others the side work of the cells of diagonal d+4.  Both parts start after
-// the light kernel of d+4.
+// the light kernel of d+4.  Binary32 batches of small proteins (no far bands)
+// take three CTAs per SM (80 registers, a few spills: the latency of the tiny
+// cells needs the occupancy); binary64 takes two in both forms (at four the
+// grouped form spilled 1.8 KB a thread, and one CTA per SM was slower for
+// batches than two with spills).
 template <typename T, bool GRP, bool BT = false>
-__global__ void __launch_bounds__(NT3, GRP ? 4 : 2) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+__global__ void __launch_bounds__(NT3, sizeof(T) == sizeof(float) ? (GRP ? 4 : (BT ? 3 : 2)) : (GRP || BT ? 2 : 1)) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;
   if (BT) {

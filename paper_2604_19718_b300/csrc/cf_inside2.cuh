@@ -10,12 +10,12 @@
 //                       prefix; results go out with 16-byte stores.
 //   k_in_bif_grp<T>(d)  the multiloop/exterior bifurcation sums of diagonal d,
 //   (binary32)          sum_k G[x][k] QB[k][y] and sum_k Gx[k] QB[k][d], over
-//                       the split points not in a far band, four cells per CTA;
+//                       the split points not in a far band (every split point
+//                       of a short protein or a batch), four cells per CTA;
 //                       its inputs lie on diagonals <= d-4, so it runs while
 //                       diagonals d-3..d-1 are being filled; sums are relative
 //                       to 2^{E[d-4]}.
-//   k_in_bif<T>(d)      the same without far bands (binary64, short proteins),
-//                       one CTA per cell.
+//   k_in_bif<T>(d)      the same in binary64, one CTA per cell.
 // Per band of FARD diagonals (binary32): k_in_far sums the far split points
 // of the whole band as tiled products, after the light kernel of d0 - 17.
 //
@@ -458,12 +458,18 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
   }
 }
 
-// binary32 with far bands: CTA b < last takes cells 4b..4b+3, the last CTA the
-// exterior sum with all eight warps; 64 registers, so that a CTA leaves room
-// for the light kernel's CTAs on its SM (binary64: 128, since 64 spilled)
-template <typename T>
-__global__ void __launch_bounds__(256, 4 / (sizeof(T) / sizeof(float))) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
+// binary32 (with or without far bands; a batch, blockIdx.y the protein, has
+// none): CTA b < last takes cells 4b..4b+3, the last CTA the exterior sum with
+// all eight warps; 64 registers, so that a CTA leaves room for the light
+// kernel's CTAs on its SM
+template <typename T, bool BT = false>
+__global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
+  if (BT) {
+    const long long off = (long long)blockIdx.y * p.bstride;
+    dp_shift(p, off);
+    bb_shift(bb, off);
+  }
   if ((int)blockIdx.x == (int)gridDim.x - 1) {
     in_bif_ext_group<T>(p, bb, d, red);
     return;
@@ -471,14 +477,15 @@ __global__ void __launch_bounds__(256, 4 / (sizeof(T) / sizeof(float))) k_in_bif
   in_bif_group<T>(p, bb, d, blockIdx.x * 4, red);
 }
 
-// Grid-stride over the n-d cells and the exterior: launched with fewer CTAs
+// Binary64: grid-stride over the n-d cells and the exterior (one CTA per SM,
+// 255 registers): launched with fewer CTAs
 // than cells, so that the light kernels of the critical path always find
 // room on the SMs.
 // (BT: a batch of proteins, blockIdx.y the protein; a compile-time switch so
 // that a single protein's kernels read their table pointers straight from the
 // parameter bank.)
 template <typename T, bool BT = false>
-__global__ void __launch_bounds__(256, sizeof(T) == sizeof(float) ? (BT ? 3 : 2) : 1) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, 1) k_in_bif(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;

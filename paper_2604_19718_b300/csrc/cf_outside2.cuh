@@ -103,7 +103,7 @@ __host__ __device__ __forceinline__ int out_next(int n, int d) {  // hGx terms y
 }
 
 // ---------------------------------------------------------------- K1'
-// Without far bands (binary64, short proteins): one 256-thread block per cell
+// Binary64: one 256-thread block per cell
 // (last block: the exterior gather); the row- and column-gather chunks are
 // dealt to the eight warps; lanes over the summation index.
 template <typename T>
@@ -198,7 +198,8 @@ __device__ __forceinline__ void out_bif_cell(const DP<T> &p, const OutBuf<T> &ob
 // 2 OFD + 3 of the last diagonal), so a pair of warps per cell (row gather,
 // column gather) and four cells per 256-thread CTA; within a warp the two
 // half-warps take rows 0..2 and 3..5 of the sum (bif_half_acc) and their 16
-// lanes 16 terms.
+// lanes 16 terms.  Without far bands (a short protein, a batch) a warp takes
+// every term of its gather, 16 per step.
 // Exterior gather hGx[d] = sum_{yy >= d+4} hQ5P[yy] QB[d][yy]^T by all eight
 // warps of the CTA, 16 terms per warp and step; the warps' sums are added in
 // order.
@@ -1198,13 +1199,11 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 // far bands: four cells per CTA, then the exterior, at 64 registers so that
 // the CTAs leave room for the light kernels; else one cell per CTA), the
 // others the side work of the cells of diagonal d+4.  Both parts start after
-// the light kernel of d+4.  Binary32 batches of small proteins (no far bands)
-// take three CTAs per SM (80 registers, a few spills: the latency of the tiny
-// cells needs the occupancy); binary64 takes two in both forms (at four the
-// grouped form spilled 1.8 KB a thread, and one CTA per SM was slower for
-// batches than two with spills).
+// the light kernel of d+4.  GRP is the binary32 form; the binary64 form takes
+// one CTA per SM for a single protein (254 registers, no spills) and two for
+// a batch (spills, but one was slower there).
 template <typename T, bool GRP, bool BT = false>
-__global__ void __launch_bounds__(NT3, sizeof(T) == sizeof(float) ? (GRP ? 4 : (BT ? 3 : 2)) : (GRP || BT ? 2 : 1)) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+__global__ void __launch_bounds__(NT3, GRP ? 4 : (BT ? 2 : 1)) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;
   if (BT) {

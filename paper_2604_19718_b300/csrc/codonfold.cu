@@ -542,9 +542,9 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     }
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
-      if (banded) {  // few near split points: two warps per cell
-        kp.func = (void *)k_in_bif_grp<T>;
-        kp.gridDim = dim3((n - d + 3) / 4 + 1);
+      if constexpr (sizeof(T) == sizeof(float)) {  // few near split points, or a short protein: two warps per cell
+        kp.func = BT ? (void *)k_in_bif_grp<T, true> : (void *)k_in_bif_grp<T, false>;
+        kp.gridDim = dim3((n - d + 3) / 4 + 1, p->batch);
       } else {
         kp.func = BT ? (void *)k_in_bif<T, true> : (void *)k_in_bif<T, false>;
         kp.gridDim = dim3(std::min(n - d + 1, cap_bif), p->batch);
@@ -686,13 +686,14 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   const void *klight = BT ? (const void *)k_out_light<T, NT, true> : (const void *)k_out_light<T, NT, false>;
   const void *klightw = BT ? (const void *)k_out_light<T, NT_WIDE, true> : (const void *)k_out_light<T, NT_WIDE, false>;
   const void *ktgf = BT ? (const void *)k_out_tg<T, true> : (const void *)k_out_tg<T, false>;
-  const void *koff0 = BT ? (const void *)k_out_off<T, false, true> : (const void *)k_out_off<T, false, false>;
-  const void *koff1 = BT ? (const void *)k_out_off<T, true, true> : (const void *)k_out_off<T, true, false>;
+  // binary32 (far bands, or a short protein or a batch without them): grouped
+  // gathers, two warps per cell; binary64: one CTA per cell
+  constexpr bool GRP = sizeof(T) == sizeof(float);
+  const void *koff = BT ? (const void *)k_out_off<T, GRP, true> : (const void *)k_out_off<T, GRP, false>;
   CF_CUDA(p, cudaFuncSetAttribute(klight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CF_CUDA(p, cudaFuncSetAttribute(klightw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemw));
   CF_CUDA(p, cudaFuncSetAttribute(ktgf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out_tg_smem<T>()));
-  CF_CUDA(p, cudaFuncSetAttribute(koff0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
-  CF_CUDA(p, cudaFuncSetAttribute(koff1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
+  CF_CUDA(p, cudaFuncSetAttribute(koff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3));
   cudaGraph_t g;
   CF_CUDA(p, cudaGraphCreate(&g, 0));
   DP<T> dp = t.dp;
@@ -768,10 +769,10 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     // light kernel of d+4
     const bool hasb = d <= n - 5 && d >= 1, hass = d + 4 <= n - 1 && d >= 1;  // no side work below d = 5
     if (hasb || hass) {
-      int nbif = hasb ? (banded ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
+      int nbif = hasb ? (GRP ? (n - d + 3) / 4 + 1 : n - d + 1) : 0;
       void *oargs[] = {&dp, &ob, &dd, &nbif};
       cudaKernelNodeParams kp = {};
-      kp.func = (void *)(banded ? koff1 : koff0);  // far bands: grouped gathers
+      kp.func = (void *)koff;
       kp.gridDim = dim3(nbif + (hass ? n - d - 4 : 0), B);
       kp.blockDim = dim3(NT3);
       kp.sharedMemBytes = (unsigned)smem3;

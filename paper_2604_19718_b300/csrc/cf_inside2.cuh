@@ -15,7 +15,8 @@
 //                       its inputs lie on diagonals <= d-4, so it runs while
 //                       diagonals d-3..d-1 are being filled; sums are relative
 //                       to 2^{E[d-4]}.
-//   k_in_bif<T>(d)      the same in binary64, one CTA per cell.
+//   k_in_bif<T>(d)      the same for binary64 proteins over 48 nt, one CTA per
+//                       cell.
 // Per band of FARD diagonals (binary32): k_in_far sums the far split points
 // of the whole band as tiled products, after the light kernel of d0 - 17.
 //
@@ -459,11 +460,12 @@ __device__ __forceinline__ void in_bif_group(const DP<T> &p, const BifBuf<T> &bb
 }
 
 // binary32 (with or without far bands; a batch, blockIdx.y the protein, has
-// none): CTA b < last takes cells 4b..4b+3, the last CTA the exterior sum with
-// all eight warps; 64 registers, so that a CTA leaves room for the light
-// kernel's CTAs on its SM
+// none) and short binary64 proteins: CTA b < last takes cells 4b..4b+3, the
+// last CTA the exterior sum with all eight warps; 64 registers, so that a CTA
+// leaves room for the light kernel's CTAs on its SM (binary64: 128, since 64
+// spilled)
 template <typename T, bool BT = false>
-__global__ void __launch_bounds__(256, 4) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
+__global__ void __launch_bounds__(256, 4 / (sizeof(T) / sizeof(float))) k_in_bif_grp(DP<T> p, BifBuf<T> bb, int d) {
   __shared__ T red[8][BLK];
   if (BT) {
     const long long off = (long long)blockIdx.y * p.bstride;

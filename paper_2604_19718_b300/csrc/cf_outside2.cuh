@@ -103,7 +103,7 @@ __host__ __device__ __forceinline__ int out_next(int n, int d) {  // hGx terms y
 }
 
 // ---------------------------------------------------------------- K1'
-// Binary64: one 256-thread block per cell
+// Binary64 over 48 nt: one 256-thread block per cell
 // (last block: the exterior gather); the row- and column-gather chunks are
 // dealt to the eight warps; lanes over the summation index.
 template <typename T>
@@ -1199,11 +1199,11 @@ __device__ __forceinline__ bool side_cell(const DP<T> &p, const OutBuf<T> &ob, i
 // far bands: four cells per CTA, then the exterior, at 64 registers so that
 // the CTAs leave room for the light kernels; else one cell per CTA), the
 // others the side work of the cells of diagonal d+4.  Both parts start after
-// the light kernel of d+4.  GRP is the binary32 form; the binary64 form takes
-// one CTA per SM for a single protein (254 registers, no spills) and two for
-// a batch (spills, but one was slower there).
+// the light kernel of d+4.  GRP is the form of binary32 and of short binary64
+// proteins (binary64: two CTAs per SM, at four it spilled 1.8 KB a thread);
+// the other binary64 form takes one CTA per SM (254 registers, no spills).
 template <typename T, bool GRP, bool BT = false>
-__global__ void __launch_bounds__(NT3, GRP ? 4 : (BT ? 2 : 1)) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
+__global__ void __launch_bounds__(NT3, GRP ? 4 / (sizeof(T) / sizeof(float)) : 1) k_out_off(DP<T> p, OutBuf<T> ob, int d, int nbif) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const long long boff = BT ? (long long)blockIdx.y * p.bstride : 0;
   if (BT) {
@@ -1343,7 +1343,9 @@ template <typename T, bool BT = false>
 __global__ void __launch_bounds__(256) k_out_tg(DP<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (BT) dp_shift(p, (long long)(blockIdx.z >> 1) * p.bstride);  // batch: z = 2 protein + role
-  const int n = p.n, q = blockIdx.y, role = blockIdx.z & 1;
+  // a batch (codon-state layout) has its boundaries at q = 3r + 2 only: one
+  // grid row per boundary instead of one per position
+  const int n = p.n, q = BT ? 3 * (int)blockIdx.y + 2 : (int)blockIdx.y, role = blockIdx.z & 1;
   if (q >= n - 1 || p.bnd[q] == 0) return;
   const int ncell = role == 0 ? n - 1 - q : q + 1;  // role 0: y = q+1..n-1; role 1: x = 0..q
   const int c0 = blockIdx.x * TG_CELLS;

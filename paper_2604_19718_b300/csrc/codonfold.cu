@@ -436,6 +436,11 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
 // room for the light CTAs but starves the off-chain kernels (measured: slower
 // at 900 nt), so the graphs use a cap above every diagonal's cell count: one
 // CTA per cell.
+// Binary64 proteins up to this length (every batch) take the grouped
+// bifurcation gathers: a gather has at most n - 4 terms, a few steps of
+// 16 for two warps.
+constexpr int GRP64_MAXN = 48;
+
 int offchain_ctas(const cf_problem *p, int per_sm) {
   int sms = 148;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) cudaGetLastError();
@@ -542,12 +547,14 @@ cf_status build_inside_graph(cf_problem *p, PrecTables<T> &t) {
     }
     if (d >= 8) {
       cudaKernelNodeParams kp = {};
-      if constexpr (sizeof(T) == sizeof(float)) {  // few near split points, or a short protein: two warps per cell
-        kp.func = BT ? (void *)k_in_bif_grp<T, true> : (void *)k_in_bif_grp<T, false>;
-        kp.gridDim = dim3((n - d + 3) / 4 + 1, p->batch);
-      } else {
-        kp.func = BT ? (void *)k_in_bif<T, true> : (void *)k_in_bif<T, false>;
-        kp.gridDim = dim3(std::min(n - d + 1, cap_bif), p->batch);
+      // few near split points, or a short protein: two warps per cell
+      kp.func = BT ? (void *)k_in_bif_grp<T, true> : (void *)k_in_bif_grp<T, false>;
+      kp.gridDim = dim3((n - d + 3) / 4 + 1, p->batch);
+      if constexpr (sizeof(T) != sizeof(float)) {
+        if (n > GRP64_MAXN) {  // binary64 (no far bands): one CTA per cell
+          kp.func = BT ? (void *)k_in_bif<T, true> : (void *)k_in_bif<T, false>;
+          kp.gridDim = dim3(std::min(n - d + 1, cap_bif), p->batch);
+        }
       }
       kp.blockDim = dim3(256);
       kp.kernelParams = args;
@@ -686,10 +693,13 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
   const void *klight = BT ? (const void *)k_out_light<T, NT, true> : (const void *)k_out_light<T, NT, false>;
   const void *klightw = BT ? (const void *)k_out_light<T, NT_WIDE, true> : (const void *)k_out_light<T, NT_WIDE, false>;
   const void *ktgf = BT ? (const void *)k_out_tg<T, true> : (const void *)k_out_tg<T, false>;
-  // binary32 (far bands, or a short protein or a batch without them): grouped
-  // gathers, two warps per cell; binary64: one CTA per cell
-  constexpr bool GRP = sizeof(T) == sizeof(float);
-  const void *koff = BT ? (const void *)k_out_off<T, GRP, true> : (const void *)k_out_off<T, GRP, false>;
+  // binary32 (far bands, or a short protein or a batch without them) and
+  // short binary64 proteins: grouped gathers, two warps per cell; longer
+  // binary64 proteins: one CTA per cell
+  const bool GRP = sizeof(T) == sizeof(float) || n <= GRP64_MAXN;
+  const void *koff = BT ? (const void *)k_out_off<T, true, true> : (const void *)k_out_off<T, true, false>;
+  if constexpr (sizeof(T) != sizeof(float))
+    if (!GRP) koff = BT ? (const void *)k_out_off<T, false, true> : (const void *)k_out_off<T, false, false>;
   CF_CUDA(p, cudaFuncSetAttribute(klight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CF_CUDA(p, cudaFuncSetAttribute(klightw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemw));
   CF_CUDA(p, cudaFuncSetAttribute(ktgf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out_tg_smem<T>()));
@@ -843,7 +853,7 @@ cf_status build_outside_graph(cf_problem *p, PrecTables<T> &t) {
     void *args[] = {&dp};
     cudaKernelNodeParams kp = {};
     kp.func = (void *)ktgf;
-    kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, n, 2 * B);
+    kp.gridDim = dim3((n + TG_CELLS - 1) / TG_CELLS, BT ? std::max(1, n / 3 - 1) : n, 2 * B);
     kp.blockDim = dim3(256);
     kp.sharedMemBytes = (unsigned)out_tg_smem<T>();
     kp.kernelParams = args;

@@ -431,16 +431,16 @@ cf_status alloc_inside(cf_problem *p, PrecTables<T> &t) {
   return CF_OK;
 }
 
-// Grid size cap of the per-cell bifurcation kernels without far bands, which
-// loop over their cells grid-stride.  A cap of one or two CTAs per SM leaves
-// room for the light CTAs but starves the off-chain kernels (measured: slower
-// at 900 nt), so the graphs use a cap above every diagonal's cell count: one
-// CTA per cell.
 // Binary64 proteins up to this length (every batch) take the grouped
 // bifurcation gathers: a gather has at most n - 4 terms, a few steps of
 // 16 for two warps.
 constexpr int GRP64_MAXN = 48;
 
+// Grid size cap of the per-cell bifurcation kernels without far bands, which
+// loop over their cells grid-stride.  A cap of one or two CTAs per SM leaves
+// room for the light CTAs but starves the off-chain kernels (measured: slower
+// at 900 nt), so the graphs use a cap above every diagonal's cell count: one
+// CTA per cell.
 int offchain_ctas(const cf_problem *p, int per_sm) {
   int sms = 148;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) cudaGetLastError();

@@ -345,38 +345,46 @@ __global__ void __launch_bounds__(MFE_NT) k_mfe_light(MfeDP p, int d) {
 
 // ---------------------------------------------------------------- bifurcation
 // BP[x][y] = c + min_{k = x+5..y-4} GP[x][k] . QB[k][y] and, for the last
-// warp, the exterior X5[d] = min_{k = 4..d-4} GX[k] . QB[k][d].  Inputs lie on
-// diagonals <= d - 4.  One warp per cell, lanes over split points, then a
-// warp minimum per entry.
+// cell of the launch, the exterior X5[d] = min_{k = 4..d-4} GX[k] . QB[k][d].
+// Inputs lie on diagonals <= d - 4.  wpc warps per cell (1, 2, 4 or 8, chosen
+// per diagonal so that a long diagonal's few cells still fill the SMs), lanes
+// and warps over the split points, then a warp minimum per entry and, for
+// wpc > 1, the minimum of the cell's warps in shared memory (integer minima:
+// the same result in any order).
 // MINB CTAs per SM: two (128 registers) up to MFE_BIF2_MAXN nt, one beyond
-// (measured: 900 nt 95.9 -> 79.8 ms with two, 3000 nt 1339 -> 1443 ms)
+// (measured with one warp per cell: 900 nt 95.9 -> 79.8 ms with two, 3000 nt
+// 1339 -> 1443 ms)
 constexpr int MFE_BIF2_MAXN = 2000;
 template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_mfe_bif(MfeDP p, int d) {
+__global__ void __launch_bounds__(256, MINB) k_mfe_bif(MfeDP p, int d, int wpc) {
+  __shared__ mq red[8][BLK];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, n = p.n;
-  const int x = blockIdx.x * 8 + w;
-  if (x > n - d) return;
+  const int sub = w % wpc;
+  const int x = blockIdx.x * (8 / wpc) + w / wpc;
+  const bool valid = x <= n - d;
   const bool ext = x == n - d;
   const int y = ext ? d : x + d;
   mq acc[BLK];
 #pragma unroll
   for (int e = 0; e < BLK; e++) acc[e] = MQINF;
-  const int k0 = ext ? 4 : x + 5, k1 = y - 4;
-  for (int k = k0 + lane; k <= k1; k += 32) {
-    const mq *A = ext ? p.GX + (size_t)k * BLK : mblk(p.GP, n, x, k);
-    const mq *B = mblk(p.QB, n, k, y);
+  if (valid) {
+    const int k0 = ext ? 4 : x + 5, k1 = y - 4;
+    for (int k = k0 + sub * 32 + lane; k <= k1; k += 32 * wpc) {
+      const mq *A = ext ? p.GX + (size_t)k * BLK : mblk(p.GP, n, x, k);
+      const mq *B = mblk(p.QB, n, k, y);
 #pragma unroll
-    for (int s = 0; s < NS; s++) {
-      mq bv[NS], av[NS];
+      for (int s = 0; s < NS; s++) {
+        mq bv[NS], av[NS];
 #pragma unroll
-      for (int j = 0; j < NS; j++) {
-        bv[j] = __ldg(B + s * NS + j);
-        av[j] = __ldg(A + j * NS + s);
+        for (int j = 0; j < NS; j++) {
+          bv[j] = __ldg(B + s * NS + j);
+          av[j] = __ldg(A + j * NS + s);
+        }
+#pragma unroll
+        for (int a = 0; a < NS; a++)
+#pragma unroll
+          for (int b = 0; b < NS; b++) acc[a * NS + b] = mmin(acc[a * NS + b], av[a] + bv[b]);
       }
-#pragma unroll
-      for (int a = 0; a < NS; a++)
-#pragma unroll
-        for (int b = 0; b < NS; b++) acc[a * NS + b] = mmin(acc[a * NS + b], av[a] + bv[b]);
     }
   }
 #pragma unroll
@@ -387,10 +395,25 @@ __global__ void __launch_bounds__(256, MINB) k_mfe_bif(MfeDP p, int d) {
     acc[e] = v;
   }
   const mq c = ext ? 0 : p.en[EN_EC];
-  mq *dst = ext ? p.X5 + (size_t)d * BLK : mblkw(p.BP, n, x, y);
+  mq *dst = !valid ? nullptr : ext ? p.X5 + (size_t)d * BLK : mblkw(p.BP, n, x, y);
+  if (wpc == 1) {  // uniform over the launch
+    if (valid) {
+#pragma unroll
+      for (int e = 0; e < BLK; e++)
+        if (lane == (e & 31)) dst[e] = mclamp(acc[e] + c);
+    }
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < BLK; e++)
-    if (lane == (e & 31)) dst[e] = mclamp(acc[e] + c);
+    if (lane == (e & 31)) red[w][e] = acc[e];
+  __syncthreads();
+  if (valid && sub == 0)
+    for (int e = lane; e < BLK; e += 32) {
+      mq v = red[w][e];
+      for (int j = 1; j < wpc; j++) v = mmin(v, red[w + j][e]);
+      dst[e] = mclamp(v + c);
+    }
 }
 
 __global__ void k_mfe_final(MfeDP p) {

@@ -1246,15 +1246,23 @@ cf_status mfe_graph(cf_problem *p) {
   MfeDP dp = t.dp;
   cudaError_t e = cudaSuccess;
   int nodes = 0;
+  const int slots = offchain_ctas(p, 2);  // two bifurcation CTAs per SM
   for (int d = 0; d < n && e == cudaSuccess; d++) {
     int dd = d;
     void *args[] = {&dp, &dd};
     if (d >= 8) {
+      // warps per cell: more on the long diagonals, until the launch fills
+      // the SMs or a warp would have fewer than 32 split points
+      const int cells = n - d + 1;
+      int wpc = 1;
+      while (wpc < 8 && (long long)cells * wpc < 8LL * slots && 64 * wpc <= d - 8) wpc *= 2;
+      int wp = wpc;
+      void *bargs[] = {&dp, &dd, &wp};
       cudaKernelNodeParams kp = {};
       kp.func = n <= MFE_BIF2_MAXN ? (void *)k_mfe_bif<2> : (void *)k_mfe_bif<1>;
-      kp.gridDim = dim3((n - d + 1 + 7) / 8);
+      kp.gridDim = dim3((cells + 8 / wpc - 1) / (8 / wpc));
       kp.blockDim = dim3(256);
-      kp.kernelParams = args;
+      kp.kernelParams = bargs;
       e = cudaGraphAddKernelNode(&kb[d], g, &kl[d - 4], 1, &kp);
       if (e == cudaSuccess) e = set_priority(kb[d], false);
       nodes++;

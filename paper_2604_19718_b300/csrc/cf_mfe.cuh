@@ -271,11 +271,16 @@ __device__ __forceinline__ mq mfe_task(const MfeDP &p, int op, int x, int y, int
   return MQINF;
 }
 
+// Launched by a programmatic edge from the light kernel of d - 1: every task
+// reads diagonals up to d - 1, so the kernel waits for its predecessor first
+// (the launch itself overlaps the predecessor's end).
 __global__ void __launch_bounds__(MFE_NT) k_mfe_light(MfeDP p, int d) {
   __shared__ mq O[MO_N][BLK];
   __shared__ mq QBs[BLK], XIs[BLK];
   const int t = threadIdx.x, n = p.n;
   const int x = blockIdx.x, y = x + d;
+  griddep_wait();
+  griddep_launch_dependents();
   for (int task = t; task < MO_N * BLK; task += MFE_NT) {
     const int op = task / BLK, e = task % BLK;
     O[op][e] = mclamp(mfe_task(p, op, x, y, d, e / NS, e % NS));

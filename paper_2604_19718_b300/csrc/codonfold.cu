@@ -1234,8 +1234,9 @@ cf_status mfe_alloc(cf_problem *p) {
   return CF_OK;
 }
 
-// The pass as one CUDA graph: a chain of light kernels, one per diagonal, and
-// the bifurcation kernel of diagonal d hanging off the light kernel of d - 4.
+// The pass as one CUDA graph: a chain of light kernels, one per diagonal
+// (consecutive ones joined by programmatic edges), and the bifurcation kernel
+// of diagonal d hanging off the light kernel of d - 4.
 cf_status mfe_graph(cf_problem *p) {
   MfeTables &t = p->mfe;
   if (t.g) return CF_OK;
@@ -1268,9 +1269,8 @@ cf_status mfe_graph(cf_problem *p) {
       nodes++;
     }
     if (e != cudaSuccess) break;
-    cudaGraphNode_t deps[2];
+    cudaGraphNode_t deps[1];
     int nd = 0;
-    if (d > 0) deps[nd++] = kl[d - 1];
     if (d >= 8) deps[nd++] = kb[d];
     cudaKernelNodeParams kp = {};
     kp.func = (void *)k_mfe_light;
@@ -1278,6 +1278,7 @@ cf_status mfe_graph(cf_problem *p) {
     kp.blockDim = dim3(MFE_NT);
     kp.kernelParams = args;
     e = cudaGraphAddKernelNode(&kl[d], g, deps, nd, &kp);
+    if (e == cudaSuccess && d > 0) e = add_programmatic_edge(g, kl[d - 1], kl[d]);  // the chain
     if (e == cudaSuccess) e = set_priority(kl[d], true);
     nodes++;
   }

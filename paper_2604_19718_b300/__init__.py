@@ -430,6 +430,9 @@ def to_letters(residues) -> str:
     return "".join(AMINO_ACIDS[int(r)] for r in residues)
 
 
+_AA_BYTES = np.frombuffer(AMINO_ACIDS.encode(), dtype=np.uint8)
+
+
 class Batch:
     """A batch of proteins of one length: inside and outside for all of them
     in one launch per kernel (cf_batch_*)."""
@@ -443,19 +446,39 @@ class Batch:
         self.nprot, self.m, self.n = nprot, m, 3 * m
 
     def set_proteins(self, proteins, codon_logw=None, pair_bonus=None):
-        """proteins: nprot residue lists (or strings) of m residues."""
-        letters = "".join(p if isinstance(p, str) else to_letters(p) for p in proteins)
+        """proteins: nprot residue lists (or strings) of m residues, or one
+        (nprot, m) integer array of residue indices."""
+        if isinstance(proteins, np.ndarray) or (len(proteins) and not isinstance(proteins[0], str)):
+            idx = np.asarray(proteins)
+            if idx.shape != (self.nprot, self.m) or idx.dtype.kind not in "iu":
+                raise ValueError("expected nprot proteins of m residues")
+            if idx.size and (idx.min() < 0 or idx.max() >= len(AMINO_ACIDS)):
+                raise ValueError("residue index out of range")
+            letters = _AA_BYTES[idx].tobytes()
+        else:
+            letters = "".join(proteins).encode()
         if len(letters) != self.nprot * self.m:
             raise ValueError("expected nprot proteins of m residues")
         lw = None if codon_logw is None else np.ascontiguousarray(codon_logw, dtype=np.float64).reshape(
             self.nprot, self.m, 6)
         pb = None if pair_bonus is None else np.ascontiguousarray(pair_bonus, dtype=np.float64).reshape(61, 61)
-        _check(lib.cf_batch_set_proteins(self.h, letters.encode(), _ptr(lw), _ptr(pb)))
+        _check(lib.cf_batch_set_proteins(self.h, letters, _ptr(lw), _ptr(pb)))
 
     def run(self, pair_prob=True, codon=True):
+        """Inside and outside of every protein.  pair_prob / codon: True (new
+        arrays), False (not copied out), or the caller's C-contiguous output
+        array ((nprot, n, n) float32 / (nprot, m, 6) float64, host or this
+        device's memory), reused across runs."""
         lz = np.zeros(self.nprot)
         P = np.zeros((self.nprot, self.n, self.n), dtype=np.float32) if pair_prob is True else pair_prob
         cm = np.zeros((self.nprot, self.m, 6)) if codon is True else codon
+        for arr, shape, dt in ((P, (self.nprot, self.n, self.n), "float32"), (cm, (self.nprot, self.m, 6), "float64")):
+            if arr is False:
+                continue
+            ok = tuple(arr.shape) == shape and str(arr.dtype).endswith(dt)
+            ok = ok and (arr.is_contiguous() if hasattr(arr, "is_contiguous") else arr.flags.c_contiguous)
+            if not ok:
+                raise ValueError(f"output array must be C-contiguous {dt} of shape {shape}")
         _check(lib.cf_batch_run(self.h, _ptr(lz), None if P is False else _ptr(P), None if cm is False else _ptr(cm)))
         return lz, P, cm
 

@@ -80,3 +80,38 @@ def test_batch_new_proteins_same_buffers_and_errors():
 
 def cf_max_m():
     return 16
+
+
+def test_batch_input_forms_and_caller_outputs():
+    """Residues as letter strings, index lists or one index array give the
+    same results; pair probabilities and codon marginals land in the caller's
+    arrays (host or device) exactly as in new ones; malformed arrays are
+    refused before any launch."""
+    import torch
+
+    import paper_2604_19718_b300 as cf
+    prots = synth.batch_p8(24)
+    idx = np.asarray(prots)
+    b = cf.Batch(P0, 24, 8, cf.CF_FP64)
+    b.set_proteins([cf.to_letters(p) for p in prots])
+    lz, P, cm = b.run()
+    b.set_proteins(idx)
+    lz2, P2, cm2 = b.run()
+    # log Z bit for bit; the outside's binary64 atomic scatters may reorder
+    assert np.array_equal(lz, lz2)
+    assert np.abs(P - P2).max() <= 1e-12 and np.abs(cm - cm2).max() <= 1e-12
+    Ph = np.full_like(P, -1.0)
+    cmd = torch.full((24, 8, 6), -1.0, dtype=torch.float64, device="cuda")
+    lz3, P3, cm3 = b.run(Ph, cmd)
+    assert P3 is Ph and cm3 is cmd
+    assert np.array_equal(lz, lz3)
+    assert np.abs(P - Ph).max() <= 1e-12 and np.abs(cm - cmd.cpu().numpy()).max() <= 1e-12
+    with pytest.raises(ValueError):
+        b.run(np.zeros((24, 24, 23), dtype=np.float32))
+    with pytest.raises(ValueError):
+        b.run(True, np.zeros((24, 8, 6), dtype=np.float32))
+    with pytest.raises(ValueError):
+        b.set_proteins(np.full((24, 8), 20))
+    with pytest.raises(ValueError):
+        b.set_proteins(idx[:, :7])
+    b.close()

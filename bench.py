@@ -844,10 +844,12 @@ def main():
     torch.cuda.synchronize()
     samples_per_s = args.samples / (s0.elapsed_time(s1) * 1e-3)
 
-    # ---- end to end through the public API with host buffers
-    Ph = np.zeros((n, n), dtype=np.float32)
-    cmh = np.zeros((len(res), 6))
-    pgh = np.zeros((61, 61))
+    # ---- end to end through the public API with host buffers (the caller's
+    # pinned output arrays, reused from step to step)
+    Pt = torch.zeros((n, n), dtype=torch.float32, pin_memory=True)
+    cmt = torch.zeros((len(res), 6), dtype=torch.float64, pin_memory=True)
+    pgt = torch.zeros((61, 61), dtype=torch.float64, pin_memory=True)
+    Ph, cmh, pgh = Pt.numpy(), cmt.numpy(), pgt.numpy()
     letters = cf.to_letters(res)
     ke = max(2, args.steps // 3)
     torch.cuda.synchronize()

@@ -47,7 +47,11 @@ constexpr mq MQINF = 0x1010101010101010LL;  // the byte pattern cudaMemset(0x10)
 constexpr mq MQHALF = MQINF / 2;
 constexpr int MW = 29;   // W_L, L = 2..30
 constexpr int MRF = 31;  // R_L and F_L, L = 1..31
-constexpr int MFE_NT = 128;
+// threads per cell of the light kernel: each thread's one-step tasks run
+// one after the other, each waiting on its table reads, so more threads per
+// cell shorten the cell (measured, MFE pass at 900 / 3000 nt: 128 threads
+// 58.4 / 1310 ms, 256 52.5 / 968 ms, 512 61.2 / 1098 ms)
+constexpr int MFE_NT = 256;
 
 __device__ __forceinline__ mq mclamp(mq v) { return v >= MQHALF ? MQINF : v; }
 __device__ __forceinline__ mq mmin(mq a, mq b) { return a < b ? a : b; }

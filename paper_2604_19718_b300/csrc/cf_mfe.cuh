@@ -278,7 +278,12 @@ __device__ __forceinline__ mq mfe_task(const MfeDP &p, int op, int x, int y, int
 // Launched by a programmatic edge from the light kernel of d - 1: every task
 // reads diagonals up to d - 1, so the kernel waits for its predecessor first
 // (the launch itself overlaps the predecessor's end).
-__global__ void __launch_bounds__(MFE_NT) k_mfe_light(MfeDP p, int d) {
+// MINB CTAs per SM: five (48 registers) up to MFE_BIF2_MAXN nt, four (64
+// registers) beyond, where the bifurcation kernel needs the room (measured,
+// against no bound, 62 registers: 900 nt 52.5 -> 50.2 ms with five, 3000 nt
+// 970 -> 1009 ms with five, 935 ms with four)
+template <int MINB>
+__global__ void __launch_bounds__(MFE_NT, MINB) k_mfe_light(MfeDP p, int d) {
   __shared__ mq O[MO_N][BLK];
   __shared__ mq QBs[BLK], XIs[BLK];
   const int t = threadIdx.x, n = p.n;

@@ -1273,7 +1273,7 @@ cf_status mfe_graph(cf_problem *p) {
     int nd = 0;
     if (d >= 8) deps[nd++] = kb[d];
     cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_mfe_light;
+    kp.func = n <= MFE_BIF2_MAXN ? (void *)k_mfe_light<5> : (void *)k_mfe_light<4>;
     kp.gridDim = dim3(n - d);
     kp.blockDim = dim3(MFE_NT);
     kp.kernelParams = args;
